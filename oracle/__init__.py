@@ -1,0 +1,305 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library under
+``paper_2001_05523_gb300`` never does: it has no CPU fallback.
+
+The arithmetic lives in ``h2oracle.c`` (plain C, FP64, OpenMP over rows);
+this module only compiles it with gcc and marshals numpy arrays through
+ctypes.  The specification each function follows is written out in
+``h2oracle.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "h2oracle.c")
+_HDR = os.path.join(_HERE, "h2oracle.h")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SLP, DLP, TEST_POLY = 0, 1, 2
+PART_FAR, PART_NEAR, PART_ALL = 1, 2, 3
+IDENTICAL, EDGE, VERTEX = 3, 2, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, so that the tree's
+    floating-point decisions match the written specification bit for bit)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            d, i32, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+            L.or_gauss_legendre01.argtypes = [i32, vp, vp]
+            L.or_radon7.argtypes = [vp, vp]
+            L.or_collapsed_rule.argtypes = [i32, vp, vp]
+            L.or_collapsed_rule.restype = i32
+            L.or_tri_geom.argtypes = [vp, vp, vp, vp, vp]
+            L.or_pair_regular.argtypes = [i32, vp, vp]
+            L.or_pair_regular.restype = d
+            L.or_ss_pair.argtypes = [i32, i32, vp, vp, vp, d, i32]
+            L.or_ss_pair.restype = d
+            L.or_entry.argtypes = [i32, vp, i64, i64, i32]
+            L.or_entry.restype = d
+            L.or_shared_vertices.argtypes = [vp, i64, i64]
+            L.or_orient_pair.argtypes = [vp, i64, i64, vp, vp, vp]
+            L.or_dense_matvec.argtypes = [i32, vp, i32, vp, i32, vp, i32]
+            L.or_dense_rows.argtypes = [i32, vp, i32, vp, i64, vp, i32, vp]
+            L.or_dense_matrix.argtypes = [i32, vp, i32, vp]
+            L.or_h2_create.argtypes = [vp, i64, vp, i64, i32, i32, d, i32, i32]
+            L.or_h2_create.restype = vp
+            L.or_h2_destroy.argtypes = [vp]
+            L.or_h2_sizes.argtypes = [vp, vp]
+            L.or_h2_tree.argtypes = [vp] * 8
+            L.or_h2_blocks.argtypes = [vp] * 5
+            L.or_h2_leaf_basis.argtypes = [vp, i64, vp, vp]
+            L.or_h2_leaf_basis.restype = i32
+            L.or_h2_transfer.argtypes = [vp, i64, vp]
+            L.or_h2_transfer.restype = i32
+            L.or_h2_nodes.argtypes = [vp, vp]
+            L.or_h2_matvec.argtypes = [vp, vp, i32, vp, i32, i32]
+            L.or_ss_moment.argtypes = [i32, i32, i32, i32, i32, i32]
+            L.or_ss_moment.restype = d
+            L.or_test_poly_P.argtypes = [vp]
+            L.or_test_poly_P.restype = d
+            L.or_test_poly_Q.argtypes = [vp]
+            L.or_test_poly_Q.restype = d
+            L.or_h2_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.or_num_threads.restype = i32
+            L.or_set_threads.argtypes = [i32]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+# ---------------------------------------------------------------- quadrature
+def gauss_legendre01(q: int):
+    x = np.zeros(q)
+    w = np.zeros(q)
+    if lib().or_gauss_legendre01(q, _p(x), _p(w)):
+        raise ValueError("bad q")
+    return x, w
+
+
+def radon7():
+    uv = np.zeros((7, 2))
+    w = np.zeros(7)
+    lib().or_radon7(_p(uv), _p(w))
+    return uv, w
+
+
+def collapsed_rule(q: int):
+    uv = np.zeros((q * q, 2))
+    w = np.zeros(q * q)
+    n = lib().or_collapsed_rule(q, _p(uv), _p(w))
+    return uv[:n], w[:n]
+
+
+def tri_geom(a, b, c):
+    a, b, c = _f64(a), _f64(b), _f64(c)
+    area = np.zeros(1)
+    nrm = np.zeros(3)
+    lib().or_tri_geom(_p(a), _p(b), _p(c), _p(area), _p(nrm))
+    return float(area[0]), nrm
+
+
+def ss_moment(kind: int, q: int, a: int, b: int, c: int, d: int) -> float:
+    return float(lib().or_ss_moment(kind, q, a, b, c, d))
+
+
+def test_poly_PQ(pts: np.ndarray):
+    pts = _f64(pts).reshape(-1, 3)
+    P = np.array([lib().or_test_poly_P(_p(np.ascontiguousarray(p))) for p in pts])
+    Q = np.array([lib().or_test_poly_Q(_p(np.ascontiguousarray(p))) for p in pts])
+    return P, Q
+
+
+def pair_regular(kernel: int, X, Y) -> float:
+    X, Y = _f64(X).reshape(9), _f64(Y).reshape(9)
+    return float(lib().or_pair_regular(kernel, _p(X), _p(Y)))
+
+
+def ss_pair(kernel: int, kind: int, P, Q, q: int, nrm=None, sgn: float = 1.0) -> float:
+    P, Q = _f64(P).reshape(9), _f64(Q).reshape(9)
+    n = _f64(nrm if nrm is not None else np.zeros(3))
+    return float(lib().or_ss_pair(kernel, kind, _p(P), _p(Q), _p(n), sgn, q))
+
+
+class _MeshC(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("tri", ctypes.c_void_p), ("nv", ctypes.c_int64), ("nt", ctypes.c_int64)]
+
+
+class MeshRef:
+    """Keeps the numpy buffers alive while C holds pointers to them."""
+
+    def __init__(self, vertices, triangles):
+        self.v = _f64(vertices)
+        self.t = np.ascontiguousarray(triangles, dtype=np.int32)
+        self.c = _MeshC(_p(self.v).value, _p(self.t).value, self.v.shape[0], self.t.shape[0])
+
+    @property
+    def ptr(self):
+        return ctypes.cast(ctypes.pointer(self.c), ctypes.c_void_p)
+
+
+def _mesh(mesh) -> MeshRef:
+    return MeshRef(mesh.vertices, mesh.triangles)
+
+
+def entry(kernel: int, mesh, i: int, j: int, q_ss: int = 5) -> float:
+    M = _mesh(mesh)
+    return float(lib().or_entry(kernel, M.ptr, i, j, q_ss))
+
+
+def shared_vertices(mesh, i: int, j: int) -> int:
+    M = _mesh(mesh)
+    return int(lib().or_shared_vertices(M.ptr, i, j))
+
+
+def orient_pair(mesh, lo: int, hi: int):
+    M = _mesh(mesh)
+    t = ctypes.c_int(0)
+    P = np.zeros(9)
+    Q = np.zeros(9)
+    lib().or_orient_pair(M.ptr, lo, hi, ctypes.byref(t), _p(P), _p(Q))
+    return int(t.value), P.reshape(3, 3), Q.reshape(3, 3)
+
+
+def dense_matrix(kernel: int, mesh, q_ss: int = 5) -> np.ndarray:
+    M = _mesh(mesh)
+    A = np.zeros((mesh.nt, mesh.nt))
+    lib().or_dense_matrix(kernel, M.ptr, q_ss, _p(A))
+    return A
+
+
+def dense_matvec(kernel: int, mesh, x: np.ndarray, q_ss: int = 5, transpose: bool = False) -> np.ndarray:
+    """x: (nrhs, n) -> y: (nrhs, n)."""
+    M = _mesh(mesh)
+    x = _f64(x)
+    nrhs = x.shape[0]
+    y = np.zeros_like(x)
+    lib().or_dense_matvec(kernel, M.ptr, q_ss, _p(x), nrhs, _p(y), int(transpose))
+    return y
+
+
+def dense_rows(kernel: int, mesh, rows, x: np.ndarray, q_ss: int = 5) -> np.ndarray:
+    """Rows of the dense product: returns (nrhs, len(rows))."""
+    M = _mesh(mesh)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    x = _f64(x)
+    nrhs = x.shape[0]
+    y = np.zeros((nrhs, rows.size))
+    lib().or_dense_rows(kernel, M.ptr, q_ss, _p(rows), rows.size, _p(x), nrhs, _p(y))
+    return y
+
+
+class H2:
+    """The oracle's H^2 approximation of G (SLP) or K (DLP)."""
+
+    def __init__(self, mesh, kernel: int = SLP, m: int = 4, eta: float = 2.0, leaf: int = 32, q_ss: int = 5):
+        self.mesh = mesh
+        v = _f64(mesh.vertices)
+        t = np.ascontiguousarray(mesh.triangles, dtype=np.int32)
+        self._keep = (v, t)
+        h = lib().or_h2_create(_p(v), v.shape[0], _p(t), t.shape[0], kernel, m, float(eta), leaf, q_ss)
+        if not h:
+            raise ValueError("or_h2_create failed")
+        self.h = ctypes.c_void_p(h)
+        sz = np.zeros(6, dtype=np.int64)
+        lib().or_h2_sizes(self.h, _p(sz))
+        self.nclusters, self.nfar, self.nnear, self.k, self.nleaves, self.qb = (int(a) for a in sz)
+        self.n = mesh.nt
+        self.m = m
+        self.kernel = kernel
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            lib().or_h2_destroy(h)
+            self.h = None
+
+    def tree(self):
+        nc = self.nclusters
+        out = dict(perm=np.zeros(self.n, np.int64), begin=np.zeros(nc, np.int64), end=np.zeros(nc, np.int64),
+                   child0=np.zeros(nc, np.int64), child1=np.zeros(nc, np.int64),
+                   bmin=np.zeros((nc, 3)), bmax=np.zeros((nc, 3)))
+        lib().or_h2_tree(self.h, *(_p(out[k]) for k in ("perm", "begin", "end", "child0", "child1", "bmin", "bmax")))
+        return out
+
+    def blocks(self):
+        ft, fs = np.zeros(self.nfar, np.int64), np.zeros(self.nfar, np.int64)
+        nt, ns = np.zeros(self.nnear, np.int64), np.zeros(self.nnear, np.int64)
+        lib().or_h2_blocks(self.h, _p(ft), _p(fs), _p(nt), _p(ns))
+        return (ft, fs), (nt, ns)
+
+    def leaf_basis(self, c: int):
+        tr = self.tree()
+        sz = int(tr["end"][c] - tr["begin"][c])
+        V = np.zeros((sz, self.k))
+        W = np.zeros((sz, self.k))
+        if lib().or_h2_leaf_basis(self.h, c, _p(V), _p(W)):
+            raise ValueError("not a leaf")
+        return V, W
+
+    def transfer(self, c: int):
+        E = np.zeros((self.k, self.k))
+        if lib().or_h2_transfer(self.h, c, _p(E)):
+            raise ValueError("bad cluster")
+        return E
+
+    def nodes(self):
+        z = np.zeros((self.nclusters, 3, self.m))
+        lib().or_h2_nodes(self.h, _p(z))
+        return z
+
+    def matvec(self, x: np.ndarray, transpose: bool = False, parts: int = PART_ALL) -> np.ndarray:
+        """x: (nrhs, n) -> (nrhs, n)."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        y = np.zeros_like(x)
+        lib().or_h2_matvec(self.h, _p(x), x.shape[0], _p(y), int(transpose), int(parts))
+        return y
+
+    def rows(self, rows, x: np.ndarray) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        x = _f64(x)
+        y = np.zeros((x.shape[0], rows.size))
+        lib().or_h2_rows(self.h, _p(rows), rows.size, _p(x), x.shape[0], _p(y))
+        return y

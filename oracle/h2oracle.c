@@ -1,0 +1,1074 @@
+/*
+ * FP64 CPU oracle for the Galerkin BEM single-layer (G) and double-layer (K)
+ * Laplace operators with piecewise-constant basis functions, and for their
+ * H^2-matrix approximation by tensor Chebyshev interpolation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this code.  It shares no source, no
+ * header, no table and no constant generator with the CUDA library; the two
+ * implement the same written specification independently.
+ *
+ * Plain, slow and direct: every function follows the definition it names, in
+ * the paper's order and notation, in double precision.  OpenMP only spreads
+ * independent rows (or row clusters) over threads.
+ *
+ * Paper: S. Boerm, "Fast large-scale boundary element algorithms".
+ *   - Green's function g and its normal derivative: section 1.
+ *   - Matrix entries g_ij, k_ij: section 1, eq. (slp) and eq. (dlp).
+ *   - Cluster tree, block tree, farfield/nearfield leaves: section 2,
+ *     Definitions "cluster tree" and "block tree".
+ *   - Cluster basis, transfer matrices: section 2, eq. (transfer).
+ *   - H^2-matrix blocks G|_{t x s} = V_t S_ts W_s^*: section 2, eq. (vsw).
+ *   - Bounding boxes, admissibility: section 3, eq. (admissibility).
+ *   - Tensor Chebyshev interpolation g_int, k = m^3: section 3.
+ *   - Singular (Sauter-Schwab-Erichsen) quadrature is cited, not printed, in
+ *     sections 1 and 5; the region maps used here are the standard relative-
+ *     coordinate Duffy decompositions for identical, edge- and vertex-adjacent
+ *     triangles (6, 5 and 2 regions), written out in h2oracle.h.
+ *
+ * Parity status per function is listed in h2oracle.h.
+ */
+#include "h2oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846264338327950288
+#define OR_INV4PI (1.0 / (4.0 * OR_PI))
+
+/* ------------------------------------------------------------------------- */
+/* 1-D Gauss-Legendre rule on [0,1] (Newton iteration on the three-term      */
+/* recurrence of the Legendre polynomials).                                  */
+/* ------------------------------------------------------------------------- */
+int or_gauss_legendre01(int q, double* x, double* w) {
+    if (q < 1 || q > 64) return -1;
+    for (int i = 0; i < q; ++i) {
+        /* node i of P_q on [-1,1], counted from the right end */
+        double z = cos(OR_PI * (i + 0.75) / (q + 0.5));
+        double pk = 1.0, pkm1 = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            /* P_q(z) and P_{q-1}(z) by the three-term recurrence */
+            pkm1 = 1.0;
+            pk = z;
+            for (int k = 2; k <= q; ++k) {
+                double pkp1 = ((2.0 * k - 1.0) * z * pk - (k - 1.0) * pkm1) / k;
+                pkm1 = pk;
+                pk = pkp1;
+            }
+            if (q == 1) pkm1 = 1.0;
+            dp = q * (z * pk - pkm1) / (z * z - 1.0); /* P_q'(z) */
+            double dz = pk / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        pkm1 = 1.0;
+        pk = z;
+        for (int k = 2; k <= q; ++k) {
+            double pkp1 = ((2.0 * k - 1.0) * z * pk - (k - 1.0) * pkm1) / k;
+            pkm1 = pk;
+            pk = pkp1;
+        }
+        dp = q * (z * pk - pkm1) / (z * z - 1.0);
+        /* map [-1,1] -> [0,1]; ascending order */
+        x[q - 1 - i] = 0.5 * (1.0 + z);
+        w[q - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+    return 0;
+}
+
+/* 7-point rule of degree 5 on the unit simplex {u,v >= 0, u+v <= 1} (Radon's
+ * rule).  Points as (u,v), weights normalised to sum 1, so that
+ * int_tau f ~= |tau| sum_p w_p f(x_p) with x_p = V0 + u(V1-V0) + v(V2-V0). */
+void or_radon7(double* uv, double* w) {
+    const double r = sqrt(15.0);
+    const double a = (6.0 - r) / 21.0, b = (6.0 + r) / 21.0;
+    const double wa = (155.0 - r) / 1200.0, wb = (155.0 + r) / 1200.0;
+    const double pts[7][2] = {{1.0 / 3.0, 1.0 / 3.0}, {a, a}, {1.0 - 2.0 * a, a}, {a, 1.0 - 2.0 * a},
+                              {b, b}, {1.0 - 2.0 * b, b}, {b, 1.0 - 2.0 * b}};
+    const double ws[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    for (int p = 0; p < 7; ++p) {
+        uv[2 * p] = pts[p][0];
+        uv[2 * p + 1] = pts[p][1];
+        w[p] = ws[p];
+    }
+}
+
+/* Collapsed (Duffy) tensor Gauss rule on the unit simplex: u = s,
+ * v = (1-s) t with s,t Gauss-Legendre on [0,1]; exact for total degree
+ * <= 2q-2.  Weights normalised to sum 1.  Returns the point count q*q. */
+int or_collapsed_rule(int q, double* uv, double* w) {
+    double x[64], wx[64];
+    if (or_gauss_legendre01(q, x, wx)) return -1;
+    int k = 0;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            uv[2 * k] = x[i];
+            uv[2 * k + 1] = (1.0 - x[i]) * x[j];
+            w[k] = 2.0 * wx[i] * wx[j] * (1.0 - x[i]);
+            ++k;
+        }
+    return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry                                                                  */
+/* ------------------------------------------------------------------------- */
+static void sub3(const double* a, const double* b, double* c) {
+    c[0] = a[0] - b[0];
+    c[1] = a[1] - b[1];
+    c[2] = a[2] - b[2];
+}
+static void cross3(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* area |tau| and outward unit normal of the triangle (a, b, c). */
+void or_tri_geom(const double* a, const double* b, const double* c, double* area, double* normal) {
+    double e1[3], e2[3], cr[3];
+    sub3(b, a, e1);
+    sub3(c, a, e2);
+    cross3(e1, e2, cr);
+    double len = sqrt(dot3(cr, cr));
+    *area = 0.5 * len;
+    normal[0] = cr[0] / len;
+    normal[1] = cr[1] / len;
+    normal[2] = cr[2] / len;
+}
+
+static void tri_vertices(const or_mesh* M, int64_t i, double* V /* 9 */) {
+    for (int k = 0; k < 3; ++k) {
+        int64_t v = M->tri[3 * i + k];
+        V[3 * k + 0] = M->xyz[3 * v + 0];
+        V[3 * k + 1] = M->xyz[3 * v + 1];
+        V[3 * k + 2] = M->xyz[3 * v + 2];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Kernel functions (section 1): g(x,y) = 1/(4 pi |x-y|), g(x,x) = 0;        */
+/* d g / d n_y (x,y) = (x-y).n_y / (4 pi |x-y|^3).                           */
+/* ------------------------------------------------------------------------- */
+static double kernel_slp(const double* x, const double* y) {
+    double d[3];
+    sub3(x, y, d);
+    double r = sqrt(dot3(d, d));
+    return r > 0.0 ? OR_INV4PI / r : 0.0;
+}
+static double kernel_dlp(const double* x, const double* y, const double* ny) {
+    double d[3];
+    sub3(x, y, d);
+    double r2 = dot3(d, d);
+    if (r2 == 0.0) return 0.0;
+    double r = sqrt(r2);
+    return OR_INV4PI * dot3(d, ny) / (r2 * r);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Regular pairs: 7 x 7 point tensor rule on tau x sigma.                    */
+/* ------------------------------------------------------------------------- */
+double or_pair_regular(int kernel, const double* X, const double* Y) {
+    double uv[14], w[7];
+    or_radon7(uv, w);
+    double ax, nx[3], ay, ny[3];
+    or_tri_geom(X, X + 3, X + 6, &ax, nx);
+    or_tri_geom(Y, Y + 3, Y + 6, &ay, ny);
+    double xp[7][3], yq[7][3];
+    for (int p = 0; p < 7; ++p)
+        for (int d = 0; d < 3; ++d) {
+            xp[p][d] = X[d] + uv[2 * p] * (X[3 + d] - X[d]) + uv[2 * p + 1] * (X[6 + d] - X[d]);
+            yq[p][d] = Y[d] + uv[2 * p] * (Y[3 + d] - Y[d]) + uv[2 * p + 1] * (Y[6 + d] - Y[d]);
+        }
+    double s = 0.0;
+    for (int p = 0; p < 7; ++p) {
+        double sq = 0.0;
+        for (int q = 0; q < 7; ++q) {
+            double k = kernel == OR_SLP ? kernel_slp(xp[p], yq[q]) : kernel_dlp(xp[p], yq[q], ny);
+            sq += w[q] * k;
+        }
+        s += w[p] * sq;
+    }
+    return ax * ay * s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sauter-Schwab quadrature (full 4-D tensor Gauss, q points per direction). */
+/*                                                                           */
+/* Reference triangle T = {(x1,x2): 0 <= x2 <= x1 <= 1}, parametrisation     */
+/* chi(x) = P0 + x1 (P1 - P0) + x2 (P2 - P1), |det| = 2 |tau|.               */
+/* int_tau int_sigma k = 4 |tau||sigma| int_T int_T k(chi_t(x), chi_s(y)).   */
+/* The regions and Jacobians are listed in h2oracle.h.                       */
+/*                                                                           */
+/* kernel: OR_SLP -> g;  OR_DLP -> (x-y).nrm/(4 pi |x-y|^3) with a caller-   */
+/* given normal and sign (sgn=+1: (x-y).n, sgn=-1: (y-x).n).                 */
+/* ------------------------------------------------------------------------- */
+static void chi(const double* P, double x1, double x2, double* out) {
+    for (int d = 0; d < 3; ++d) out[d] = P[d] + x1 * (P[3 + d] - P[d]) + x2 * (P[6 + d] - P[3 + d]);
+}
+
+static double ss_kernel(int kernel, const double* x, const double* y, const double* nrm, double sgn) {
+    if (kernel == OR_SLP) return kernel_slp(x, y);
+    return sgn * kernel_dlp(x, y, nrm);
+}
+
+/* regions: fill up to 6 (x1,x2,y1,y2,jac) tuples for one (xi, e1, e2, e3). */
+static int ss_regions(int type, double xi, double a, double b, double c, double out[6][5]) {
+    if (type == OR_IDENTICAL) {
+        double j = xi * xi * xi * a * a * b;
+        double r[3][4] = {{xi, xi * (1.0 - a + a * b), xi * (1.0 - a * b * c), xi * (1.0 - a)},
+                          {xi, xi * a * (1.0 - b + b * c), xi * (1.0 - a * b), xi * a * (1.0 - b)},
+                          {xi * (1.0 - a * b * c), xi * a * (1.0 - b * c), xi, xi * a * (1.0 - b)}};
+        for (int k = 0; k < 3; ++k) {
+            out[2 * k][0] = r[k][0]; out[2 * k][1] = r[k][1];
+            out[2 * k][2] = r[k][2]; out[2 * k][3] = r[k][3]; out[2 * k][4] = j;
+            out[2 * k + 1][0] = r[k][2]; out[2 * k + 1][1] = r[k][3];
+            out[2 * k + 1][2] = r[k][0]; out[2 * k + 1][3] = r[k][1]; out[2 * k + 1][4] = j;
+        }
+        return 6;
+    }
+    if (type == OR_EDGE) {
+        double j1 = xi * xi * xi * a * a, j2 = j1 * b;
+        double r[5][5] = {
+            {xi, xi * a * c, xi * (1.0 - a * b), xi * a * (1.0 - b), j1},
+            {xi, xi * a, xi * (1.0 - a * b * c), xi * a * b * (1.0 - c), j2},
+            {xi * (1.0 - a * b), xi * a * (1.0 - b), xi, xi * a * b * c, j2},
+            {xi * (1.0 - a * b * c), xi * a * b * (1.0 - c), xi, xi * a, j2},
+            {xi * (1.0 - a * b * c), xi * a * (1.0 - b * c), xi, xi * a * b, j2}};
+        memcpy(out, r, sizeof(r));
+        return 5;
+    }
+    /* OR_VERTEX */
+    double j = xi * xi * xi * b;
+    out[0][0] = xi; out[0][1] = xi * a; out[0][2] = xi * b; out[0][3] = xi * b * c; out[0][4] = j;
+    out[1][0] = xi * b; out[1][1] = xi * b * c; out[1][2] = xi; out[1][3] = xi * a; out[1][4] = j;
+    return 2;
+}
+
+double or_ss_pair(int kernel, int type, const double* P, const double* Q, const double* nrm, double sgn,
+                  int q) {
+    double g[64], gw[64];
+    if (or_gauss_legendre01(q, g, gw)) return NAN;
+    double ap, np_[3], aq, nq[3];
+    or_tri_geom(P, P + 3, P + 6, &ap, np_);
+    or_tri_geom(Q, Q + 3, Q + 6, &aq, nq);
+    /* the parametrisation chi uses (P1-P0, P2-P1); |det| = 2|tau| either way */
+    double s = 0.0;
+    for (int i0 = 0; i0 < q; ++i0)
+        for (int i1 = 0; i1 < q; ++i1)
+            for (int i2 = 0; i2 < q; ++i2)
+                for (int i3 = 0; i3 < q; ++i3) {
+                    double wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    double reg[6][5];
+                    int nr = ss_regions(type, g[i0], g[i1], g[i2], g[i3], reg);
+                    for (int r = 0; r < nr; ++r) {
+                        double x[3], y[3];
+                        chi(P, reg[r][0], reg[r][1], x);
+                        chi(Q, reg[r][2], reg[r][3], y);
+                        s += wt * reg[r][4] * ss_kernel(kernel, x, y, nrm, sgn);
+                    }
+                }
+    return 4.0 * ap * aq * s;
+}
+
+/* Moment of x1^a x2^b y1^c y2^d over T x T computed through the same regions
+ * and Jacobians as or_ss_pair (used to pin the region maps). */
+double or_ss_moment(int type, int q, int a, int b, int c, int d) {
+    double g[64], gw[64];
+    if (or_gauss_legendre01(q, g, gw)) return NAN;
+    double s = 0.0;
+    for (int i0 = 0; i0 < q; ++i0)
+        for (int i1 = 0; i1 < q; ++i1)
+            for (int i2 = 0; i2 < q; ++i2)
+                for (int i3 = 0; i3 < q; ++i3) {
+                    double wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    double reg[6][5];
+                    int nr = ss_regions(type, g[i0], g[i1], g[i2], g[i3], reg);
+                    for (int r = 0; r < nr; ++r)
+                        s += wt * reg[r][4] * pow(reg[r][0], a) * pow(reg[r][1], b) * pow(reg[r][2], c) *
+                             pow(reg[r][3], d);
+                }
+    return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pair classification from shared vertex indices and canonical orientation  */
+/* ------------------------------------------------------------------------- */
+int or_shared_vertices(const or_mesh* M, int64_t i, int64_t j) {
+    int c = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (M->tri[3 * i + a] == M->tri[3 * j + b]) ++c;
+    return c;
+}
+
+/* Orient a singular pair (lo, hi) (lo < hi, user numbering): the vertices of
+ * the outer panel P = tau_lo and of the inner panel Q = tau_hi are listed so
+ * that the shared vertices come first and in the same order.  Edge: P is the
+ * cyclic rotation of tau_lo with its unshared vertex last, Q = (P0, P1, the
+ * unshared vertex of tau_hi).  Vertex: both are the cyclic rotations that
+ * start at the shared vertex. */
+void or_orient_pair(const or_mesh* M, int64_t lo, int64_t hi, int* type_out, double* P, double* Q) {
+    const int32_t* tl = M->tri + 3 * lo;
+    const int32_t* th = M->tri + 3 * hi;
+    int ns = or_shared_vertices(M, lo, hi);
+    int32_t pv[3], qv[3];
+    if (ns == 3) {
+        *type_out = OR_IDENTICAL;
+        for (int k = 0; k < 3; ++k) pv[k] = qv[k] = tl[k];
+    } else if (ns == 2) {
+        *type_out = OR_EDGE;
+        int un = -1; /* unshared local vertex of tau_lo */
+        for (int a = 0; a < 3; ++a) {
+            int found = 0;
+            for (int b = 0; b < 3; ++b) found |= (tl[a] == th[b]);
+            if (!found) un = a;
+        }
+        pv[0] = tl[(un + 1) % 3];
+        pv[1] = tl[(un + 2) % 3];
+        pv[2] = tl[un];
+        int32_t other = -1;
+        for (int b = 0; b < 3; ++b)
+            if (th[b] != pv[0] && th[b] != pv[1]) other = th[b];
+        qv[0] = pv[0];
+        qv[1] = pv[1];
+        qv[2] = other;
+    } else {
+        *type_out = OR_VERTEX;
+        int a0 = -1, b0 = -1;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (tl[a] == th[b]) { a0 = a; b0 = b; }
+        for (int k = 0; k < 3; ++k) {
+            pv[k] = tl[(a0 + k) % 3];
+            qv[k] = th[(b0 + k) % 3];
+        }
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) {
+            P[3 * k + d] = M->xyz[3 * (int64_t)pv[k] + d];
+            Q[3 * k + d] = M->xyz[3 * (int64_t)qv[k] + d];
+        }
+}
+
+/* One Galerkin matrix entry a_ij (section 1, eq. (slp) / eq. (dlp)) with
+ * psi_i = 1 on tau_i.  Pairs that share no vertex use the 7 x 7 rule; pairs
+ * that share vertices use the Sauter-Schwab rule in the canonical orientation
+ * (outer panel = lower user index), so that G is exactly symmetric and k_ij,
+ * k_ji come from one point set.  The double-layer entry of a triangle with
+ * itself vanishes (x - y lies in the plane of tau) and is set to 0. */
+double or_entry(int kernel, const or_mesh* M, int64_t i, int64_t j, int q_ss) {
+    int ns = or_shared_vertices(M, i, j);
+    if (ns == 0) {
+        double X[9], Y[9];
+        tri_vertices(M, i, X);
+        tri_vertices(M, j, Y);
+        return or_pair_regular(kernel, X, Y);
+    }
+    if (i == j && kernel == OR_DLP) return 0.0;
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    double P[9], Q[9];
+    int type;
+    or_orient_pair(M, lo, hi, &type, P, Q);
+    if (kernel == OR_SLP) return or_ss_pair(OR_SLP, type, P, Q, NULL, 1.0, q_ss);
+    /* k_ij uses the normal of tau_j; x in tau_i, y in tau_j. */
+    double aj, nj[3], Yj[9];
+    tri_vertices(M, j, Yj);
+    or_tri_geom(Yj, Yj + 3, Yj + 6, &aj, nj);
+    /* outer panel points p in tau_lo, inner q in tau_hi.
+     * i == lo: x = p, y = q -> (p - q).n_j  (sgn +1)
+     * i == hi: x = q, y = p -> (q - p).n_j  (sgn -1) */
+    return or_ss_pair(OR_DLP, type, P, Q, nj, i == lo ? 1.0 : -1.0, q_ss);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dense matrix-vector products (the plain definition)                       */
+/* x, y column-major n x nrhs with leading dimension n.                      */
+/* ------------------------------------------------------------------------- */
+void or_dense_matvec(int kernel, const or_mesh* M, int q_ss, const double* x, int nrhs, double* y,
+                     int transpose) {
+    int64_t n = M->nt;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[64];
+        for (int r = 0; r < nrhs; ++r) acc[r] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double a = transpose ? or_entry(kernel, M, j, i, q_ss) : or_entry(kernel, M, i, j, q_ss);
+            for (int r = 0; r < nrhs; ++r) acc[r] += a * x[j + r * n];
+        }
+        for (int r = 0; r < nrhs; ++r) y[i + r * n] = acc[r];
+    }
+}
+
+void or_dense_rows(int kernel, const or_mesh* M, int q_ss, const int64_t* rows, int64_t nrows,
+                   const double* x, int nrhs, double* y /* nrows x nrhs, col-major ld nrows */) {
+    int64_t n = M->nt;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nrows; ++k) {
+        int64_t i = rows[k];
+        double acc[64];
+        for (int r = 0; r < nrhs; ++r) acc[r] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double a = or_entry(kernel, M, i, j, q_ss);
+            for (int r = 0; r < nrhs; ++r) acc[r] += a * x[j + r * n];
+        }
+        for (int r = 0; r < nrhs; ++r) y[k + r * nrows] = acc[r];
+    }
+}
+
+void or_dense_matrix(int kernel, const or_mesh* M, int q_ss, double* A /* n x n row-major */) {
+    int64_t n = M->nt;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) A[i * n + j] = or_entry(kernel, M, i, j, q_ss);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cluster tree (section 2, Definition "cluster tree"; boxes: section 3)     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n, cap, count;
+    int64_t* perm;
+    int64_t *begin, *end, *child0, *child1, *parent;
+    int32_t* level;
+    double *bmin, *bmax;
+} tree_t;
+
+static void tree_box(const or_mesh* M, const int64_t* idx, int64_t cnt, double* lo, double* hi) {
+    for (int d = 0; d < 3; ++d) { lo[d] = INFINITY; hi[d] = -INFINITY; }
+    for (int64_t a = 0; a < cnt; ++a)
+        for (int k = 0; k < 3; ++k) {
+            const double* v = M->xyz + 3 * (int64_t)M->tri[3 * idx[a] + k];
+            for (int d = 0; d < 3; ++d) {
+                if (v[d] < lo[d]) lo[d] = v[d];
+                if (v[d] > hi[d]) hi[d] = v[d];
+            }
+        }
+}
+
+static double centroid_coord(const or_mesh* M, int64_t t, int d) {
+    const int32_t* tv = M->tri + 3 * t;
+    return ((M->xyz[3 * (int64_t)tv[0] + d] + M->xyz[3 * (int64_t)tv[1] + d]) + M->xyz[3 * (int64_t)tv[2] + d]) /
+           3.0;
+}
+
+typedef struct { double key; int64_t pos; int64_t id; } sort_item;
+static int cmp_item(const void* a, const void* b) {
+    const sort_item* x = a;
+    const sort_item* y = b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+static int64_t tree_new(tree_t* T) {
+    if (T->count == T->cap) {
+        T->cap = T->cap ? 2 * T->cap : 1024;
+        T->begin = realloc(T->begin, T->cap * sizeof(int64_t));
+        T->end = realloc(T->end, T->cap * sizeof(int64_t));
+        T->child0 = realloc(T->child0, T->cap * sizeof(int64_t));
+        T->child1 = realloc(T->child1, T->cap * sizeof(int64_t));
+        T->parent = realloc(T->parent, T->cap * sizeof(int64_t));
+        T->level = realloc(T->level, T->cap * sizeof(int32_t));
+        T->bmin = realloc(T->bmin, 3 * T->cap * sizeof(double));
+        T->bmax = realloc(T->bmax, 3 * T->cap * sizeof(double));
+    }
+    return T->count++;
+}
+
+static int64_t tree_split(const or_mesh* M, tree_t* T, int64_t b, int64_t e, int64_t parent, int level,
+                          int leaf, int64_t* tmp) {
+    int64_t c = tree_new(T);
+    T->begin[c] = b;
+    T->end[c] = e;
+    T->parent[c] = parent;
+    T->level[c] = level;
+    T->child0[c] = T->child1[c] = -1;
+    tree_box(M, T->perm + b, e - b, T->bmin + 3 * c, T->bmax + 3 * c);
+    if (e - b <= leaf) return c;
+    const double* lo = T->bmin + 3 * c;
+    const double* hi = T->bmax + 3 * c;
+    int axis = 0;
+    for (int d = 1; d < 3; ++d)
+        if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
+    double mid = 0.5 * (lo[axis] + hi[axis]);
+    int64_t n0 = 0;
+    for (int64_t a = b; a < e; ++a)
+        if (centroid_coord(M, T->perm[a], axis) < mid) ++n0;
+    int64_t split;
+    if (n0 == 0 || n0 == e - b) {
+        /* stable median split */
+        sort_item* it = malloc((e - b) * sizeof(sort_item));
+        for (int64_t a = b; a < e; ++a) {
+            it[a - b].key = centroid_coord(M, T->perm[a], axis);
+            it[a - b].pos = a;
+            it[a - b].id = T->perm[a];
+        }
+        qsort(it, e - b, sizeof(sort_item), cmp_item);
+        for (int64_t a = b; a < e; ++a) T->perm[a] = it[a - b].id;
+        free(it);
+        split = b + (e - b) / 2;
+    } else {
+        int64_t k0 = 0, k1 = 0;
+        for (int64_t a = b; a < e; ++a) {
+            int64_t t = T->perm[a];
+            if (centroid_coord(M, t, axis) < mid) T->perm[b + k0++] = t;
+            else tmp[k1++] = t;
+        }
+        for (int64_t a = 0; a < k1; ++a) T->perm[b + n0 + a] = tmp[a];
+        split = b + n0;
+    }
+    int64_t c0 = tree_split(M, T, b, split, c, level + 1, leaf, tmp);
+    int64_t c1 = tree_split(M, T, split, e, c, level + 1, leaf, tmp);
+    T->child0[c] = c0;
+    T->child1[c] = c1;
+    return c;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block tree (section 2, Definition "block tree"; eq. (admissibility) with  */
+/* max(diam B_t, diam B_s) <= eta dist(B_t, B_s), dist > 0).                 */
+/* ------------------------------------------------------------------------- */
+typedef struct { int64_t* t; int64_t* s; int64_t n, cap; } blist;
+static void blist_push(blist* L, int64_t t, int64_t s) {
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 1024;
+        L->t = realloc(L->t, L->cap * sizeof(int64_t));
+        L->s = realloc(L->s, L->cap * sizeof(int64_t));
+    }
+    L->t[L->n] = t;
+    L->s[L->n] = s;
+    L->n++;
+}
+
+static double box_diam(const double* lo, const double* hi) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) s += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    return sqrt(s);
+}
+static double box_dist(const double* lo1, const double* hi1, const double* lo2, const double* hi2) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double g = 0.0;
+        if (lo2[d] > hi1[d]) g = lo2[d] - hi1[d];
+        else if (lo1[d] > hi2[d]) g = lo1[d] - hi2[d];
+        s += g * g;
+    }
+    return sqrt(s);
+}
+
+static void block_build(const tree_t* T, double eta, int64_t t, int64_t s, blist* far, blist* near) {
+    const double *lt = T->bmin + 3 * t, *ht = T->bmax + 3 * t, *ls = T->bmin + 3 * s, *hs = T->bmax + 3 * s;
+    double dt = box_diam(lt, ht), ds = box_diam(ls, hs), dist = box_dist(lt, ht, ls, hs);
+    double dm = dt > ds ? dt : ds;
+    if (dist > 0.0 && dm <= eta * dist) {
+        blist_push(far, t, s);
+        return;
+    }
+    int tl = T->child0[t] < 0, sl = T->child0[s] < 0;
+    if (tl && sl) {
+        blist_push(near, t, s);
+        return;
+    }
+    if (tl) {
+        block_build(T, eta, t, T->child0[s], far, near);
+        block_build(T, eta, t, T->child1[s], far, near);
+    } else if (sl) {
+        block_build(T, eta, T->child0[t], s, far, near);
+        block_build(T, eta, T->child1[t], s, far, near);
+    } else {
+        block_build(T, eta, T->child0[t], T->child0[s], far, near);
+        block_build(T, eta, T->child0[t], T->child1[s], far, near);
+        block_build(T, eta, T->child1[t], T->child0[s], far, near);
+        block_build(T, eta, T->child1[t], T->child1[s], far, near);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tensor Chebyshev interpolation (section 3)                                */
+/* ------------------------------------------------------------------------- */
+/* 1-D Lagrange polynomial L_nu on the nodes z[0..m-1], and its derivative. */
+static double lagrange(const double* z, int m, int nu, double x) {
+    double p = 1.0;
+    for (int k = 0; k < m; ++k)
+        if (k != nu) p *= (x - z[k]) / (z[nu] - z[k]);
+    return p;
+}
+static double lagrange_deriv(const double* z, int m, int nu, double x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == nu) continue;
+        double p = 1.0 / (z[nu] - z[k]);
+        for (int l = 0; l < m; ++l)
+            if (l != nu && l != k) p *= (x - z[l]) / (z[nu] - z[l]);
+        s += p;
+    }
+    return s;
+}
+
+struct or_h2 {
+    or_mesh mesh;
+    double* xyz;
+    int32_t* tri;
+    int kernel, m, k, q_ss, qb;
+    double eta;
+    tree_t T;
+    blist far, near;
+    /* per cluster: Chebyshev nodes per axis, m per axis: nodes[c*3*m + d*m + a] */
+    double* nodes;
+    /* per leaf cluster c: V (|c| x k row-major), W (|c| x k) */
+    double** V;
+    double** W;
+    /* per non-root cluster c: E_c (k x k row-major, E[nu' * k + nu]) */
+    double** E;
+    /* CSR of farfield/nearfield blocks by row cluster */
+    int64_t *far_ptr, *far_col, *near_ptr, *near_col;
+    int64_t *far_ptr_t, *far_row_t; /* by column cluster (transpose) */
+    int64_t *near_ptr_t, *near_row_t;
+};
+
+static void cluster_nodes(const double* lo, const double* hi, int m, double* z /* 3*m */) {
+    double c[3], h[3], hmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        c[d] = 0.5 * (lo[d] + hi[d]);
+        h[d] = 0.5 * (hi[d] - lo[d]);
+        if (h[d] > hmax) hmax = h[d];
+    }
+    for (int d = 0; d < 3; ++d) {
+        double hd = h[d] < 1e-2 * hmax ? 1e-2 * hmax : h[d];
+        for (int a = 0; a < m; ++a) z[d * m + a] = c[d] + hd * cos((2.0 * a + 1.0) * OR_PI / (2.0 * m));
+    }
+}
+
+/* L_{t,nu}(x) for the tensor index nu = a + m (b + m c). */
+static double tensor_lagrange(const double* z, int m, int nu, const double* x) {
+    int a = nu % m, b = (nu / m) % m, c = nu / (m * m);
+    return lagrange(z, m, a, x[0]) * lagrange(z + m, m, b, x[1]) * lagrange(z + 2 * m, m, c, x[2]);
+}
+static void tensor_lagrange_grad(const double* z, int m, int nu, const double* x, double* g) {
+    int a = nu % m, b = (nu / m) % m, c = nu / (m * m);
+    double la = lagrange(z, m, a, x[0]), lb = lagrange(z + m, m, b, x[1]), lc = lagrange(z + 2 * m, m, c, x[2]);
+    g[0] = lagrange_deriv(z, m, a, x[0]) * lb * lc;
+    g[1] = la * lagrange_deriv(z + m, m, b, x[1]) * lc;
+    g[2] = la * lb * lagrange_deriv(z + 2 * m, m, c, x[2]);
+}
+
+static int64_t* csr_from(int64_t nrows, const int64_t* key, const int64_t* val, int64_t n, int64_t** col_out) {
+    int64_t* ptr = calloc(nrows + 1, sizeof(int64_t));
+    for (int64_t b = 0; b < n; ++b) ptr[key[b] + 1]++;
+    for (int64_t r = 0; r < nrows; ++r) ptr[r + 1] += ptr[r];
+    int64_t* fill = malloc(nrows * sizeof(int64_t));
+    memcpy(fill, ptr, nrows * sizeof(int64_t));
+    int64_t* col = malloc((n ? n : 1) * sizeof(int64_t));
+    for (int64_t b = 0; b < n; ++b) col[fill[key[b]]++] = val[b];
+    free(fill);
+    *col_out = col;
+    return ptr;
+}
+
+or_h2* or_h2_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int kernel, int m, double eta,
+                    int leaf, int q_ss) {
+    if (m < 1 || m > 10 || leaf < 1 || nt < 1) return NULL;
+    or_h2* H = calloc(1, sizeof(or_h2));
+    H->xyz = malloc(3 * nv * sizeof(double));
+    H->tri = malloc(3 * nt * sizeof(int32_t));
+    memcpy(H->xyz, xyz, 3 * nv * sizeof(double));
+    memcpy(H->tri, tri, 3 * nt * sizeof(int32_t));
+    H->mesh.xyz = H->xyz;
+    H->mesh.tri = H->tri;
+    H->mesh.nv = nv;
+    H->mesh.nt = nt;
+    H->kernel = kernel;
+    H->m = m;
+    H->k = m * m * m;
+    H->eta = eta;
+    H->q_ss = q_ss;
+    /* basis rule exact for total degree 3(m-1): collapsed Gauss, qb points */
+    H->qb = (3 * (m - 1) + 2 + 1) / 2;
+    if (H->qb < 1) H->qb = 1;
+    /* cluster tree */
+    tree_t* T = &H->T;
+    T->n = nt;
+    T->perm = malloc(nt * sizeof(int64_t));
+    for (int64_t i = 0; i < nt; ++i) T->perm[i] = i;
+    int64_t* tmp = malloc(nt * sizeof(int64_t));
+    tree_split(&H->mesh, T, 0, nt, -1, 0, leaf, tmp);
+    free(tmp);
+    /* block tree */
+    block_build(T, eta, 0, 0, &H->far, &H->near);
+    int64_t nc = T->count;
+    H->far_ptr = csr_from(nc, H->far.t, H->far.s, H->far.n, &H->far_col);
+    H->near_ptr = csr_from(nc, H->near.t, H->near.s, H->near.n, &H->near_col);
+    H->far_ptr_t = csr_from(nc, H->far.s, H->far.t, H->far.n, &H->far_row_t);
+    H->near_ptr_t = csr_from(nc, H->near.s, H->near.t, H->near.n, &H->near_row_t);
+    /* interpolation nodes */
+    H->nodes = malloc(nc * 3 * m * sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) cluster_nodes(T->bmin + 3 * c, T->bmax + 3 * c, m, H->nodes + c * 3 * m);
+    /* leaf bases V_t[i,nu] = int_{tau_i} L_{t,nu};  W_s = V_s (SLP) or
+     * W_s[j,mu] = int_{tau_j} n_j . grad L_{s,mu} (DLP) */
+    H->V = calloc(nc, sizeof(double*));
+    H->W = calloc(nc, sizeof(double*));
+    double ruv[2 * 64 * 64], rw[64 * 64];
+    int np = or_collapsed_rule(H->qb, ruv, rw);
+    int k = H->k;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t sz = T->end[c] - T->begin[c];
+        double* V = calloc(sz * k, sizeof(double));
+        double* W = kernel == OR_DLP ? calloc(sz * k, sizeof(double)) : V; /* W_s = V_s */
+        const double* z = H->nodes + c * 3 * m;
+        for (int64_t a = 0; a < sz; ++a) {
+            double X[9], area, nrm[3];
+            tri_vertices(&H->mesh, T->perm[T->begin[c] + a], X);
+            or_tri_geom(X, X + 3, X + 6, &area, nrm);
+            for (int p = 0; p < np; ++p) {
+                double x[3];
+                for (int d = 0; d < 3; ++d)
+                    x[d] = X[d] + ruv[2 * p] * (X[3 + d] - X[d]) + ruv[2 * p + 1] * (X[6 + d] - X[d]);
+                for (int nu = 0; nu < k; ++nu) {
+                    V[a * k + nu] += area * rw[p] * tensor_lagrange(z, m, nu, x);
+                    if (kernel == OR_DLP) {
+                        double g[3];
+                        tensor_lagrange_grad(z, m, nu, x, g);
+                        W[a * k + nu] += area * rw[p] * dot3(nrm, g);
+                    }
+                }
+            }
+        }
+        H->V[c] = V;
+        H->W[c] = W;
+    }
+    /* transfer matrices E_{t'}[nu', nu] = L_{t,nu}(xi_{t',nu'}), t = parent */
+    H->E = calloc(nc, sizeof(double*));
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 1; c < nc; ++c) {
+        int64_t p = T->parent[c];
+        double* E = malloc((size_t)k * k * sizeof(double));
+        const double* zc = H->nodes + c * 3 * m;
+        const double* zp = H->nodes + p * 3 * m;
+        for (int nup = 0; nup < k; ++nup) {
+            double xi[3] = {zc[nup % m], zc[m + (nup / m) % m], zc[2 * m + nup / (m * m)]};
+            for (int nu = 0; nu < k; ++nu) E[nup * k + nu] = tensor_lagrange(zp, m, nu, xi);
+        }
+        H->E[c] = E;
+    }
+    return H;
+}
+
+void or_h2_destroy(or_h2* H) {
+    if (!H) return;
+    tree_t* T = &H->T;
+    for (int64_t c = 0; c < T->count; ++c) {
+        if (H->W && H->W[c] && H->W[c] != H->V[c]) free(H->W[c]);
+        if (H->V) free(H->V[c]);
+        if (H->E) free(H->E[c]);
+    }
+    free(H->V); free(H->W); free(H->E); free(H->nodes);
+    free(H->far_ptr); free(H->far_col); free(H->near_ptr); free(H->near_col);
+    free(H->far_ptr_t); free(H->far_row_t); free(H->near_ptr_t); free(H->near_row_t);
+    free(H->far.t); free(H->far.s); free(H->near.t); free(H->near.s);
+    free(T->perm); free(T->begin); free(T->end); free(T->child0); free(T->child1); free(T->parent);
+    free(T->level); free(T->bmin); free(T->bmax);
+    free(H->xyz); free(H->tri);
+    free(H);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Introspection                                                             */
+/* ------------------------------------------------------------------------- */
+void or_h2_sizes(const or_h2* H, int64_t* out /* 6 */) {
+    out[0] = H->T.count;
+    out[1] = H->far.n;
+    out[2] = H->near.n;
+    out[3] = H->k;
+    int64_t leaves = 0;
+    for (int64_t c = 0; c < H->T.count; ++c) leaves += H->T.child0[c] < 0;
+    out[4] = leaves;
+    out[5] = H->qb;
+}
+void or_h2_tree(const or_h2* H, int64_t* perm, int64_t* begin, int64_t* end, int64_t* child0, int64_t* child1,
+                double* bmin, double* bmax) {
+    const tree_t* T = &H->T;
+    memcpy(perm, T->perm, T->n * sizeof(int64_t));
+    memcpy(begin, T->begin, T->count * sizeof(int64_t));
+    memcpy(end, T->end, T->count * sizeof(int64_t));
+    memcpy(child0, T->child0, T->count * sizeof(int64_t));
+    memcpy(child1, T->child1, T->count * sizeof(int64_t));
+    memcpy(bmin, T->bmin, 3 * T->count * sizeof(double));
+    memcpy(bmax, T->bmax, 3 * T->count * sizeof(double));
+}
+void or_h2_blocks(const or_h2* H, int64_t* far_t, int64_t* far_s, int64_t* near_t, int64_t* near_s) {
+    memcpy(far_t, H->far.t, H->far.n * sizeof(int64_t));
+    memcpy(far_s, H->far.s, H->far.n * sizeof(int64_t));
+    memcpy(near_t, H->near.t, H->near.n * sizeof(int64_t));
+    memcpy(near_s, H->near.s, H->near.n * sizeof(int64_t));
+}
+/* V_t, W_t of a leaf (|t| x k) and E_c (k x k) */
+int or_h2_leaf_basis(const or_h2* H, int64_t c, double* V, double* W) {
+    if (c < 0 || c >= H->T.count || H->T.child0[c] >= 0) return -1;
+    int64_t sz = (H->T.end[c] - H->T.begin[c]) * H->k;
+    memcpy(V, H->V[c], sz * sizeof(double));
+    memcpy(W, H->W[c], sz * sizeof(double));
+    return 0;
+}
+int or_h2_transfer(const or_h2* H, int64_t c, double* E) {
+    if (c <= 0 || c >= H->T.count) return -1;
+    memcpy(E, H->E[c], (size_t)H->k * H->k * sizeof(double));
+    return 0;
+}
+void or_h2_nodes(const or_h2* H, double* nodes) { memcpy(nodes, H->nodes, H->T.count * 3 * H->m * sizeof(double)); }
+
+/* ------------------------------------------------------------------------- */
+/* H^2 matrix-vector product (section 2, eq. (vsw), eq. (transfer))          */
+/*   forward:   xh_s = W_s^T x|_s (leaves),  xh_t = sum_{t'} E_{t'}^T xh_{t'} */
+/*   coupling:  yh_t = sum_{(t,s) farfield} S_ts xh_s,                        */
+/*              S_ts[nu,mu] = g(xi_{t,nu}, xi_{s,mu})                         */
+/*   backward:  yh_{t'} += E_{t'} yh_t,  y|_t += V_t yh_t (leaves)            */
+/*   nearfield: y|_t += A|_{t x s} x|_s                                       */
+/* transpose != 0 computes y = A^T x with the roles of V and W, rows and      */
+/* columns exchanged.                                                         */
+/* x, y column-major n x nrhs (ld n), user triangle order.                   */
+/* ------------------------------------------------------------------------- */
+/* Test kernel P(x) Q(y), degree 3 in each coordinate of x and of y; with
+ * m >= 4 tensor interpolation reproduces it exactly, so the H^2 farfield of
+ * this kernel is exact and pins the tree, blocks, bases and passes. */
+double or_test_poly_P(const double* x) {
+    return (1.0 + x[0] - 2.0 * x[0] * x[0] * x[0]) * (2.0 - x[1] + x[1] * x[1]) * (0.5 + x[2] * x[2] * x[2] - 3.0 * x[2]);
+}
+double or_test_poly_Q(const double* y) {
+    return (y[0] * y[0] * y[0] - y[0] + 0.25) * (1.0 + y[1] * y[1]) * (2.0 + y[2] - y[2] * y[2]);
+}
+static double test_poly_kernel(const double* x, const double* y) { return or_test_poly_P(x) * or_test_poly_Q(y); }
+
+static void coupling_matrix(const or_h2* H, int64_t t, int64_t s, double* S) {
+    int m = H->m, k = H->k;
+    const double* zt = H->nodes + t * 3 * m;
+    const double* zs = H->nodes + s * 3 * m;
+    for (int nu = 0; nu < k; ++nu) {
+        double xt[3] = {zt[nu % m], zt[m + (nu / m) % m], zt[2 * m + nu / (m * m)]};
+        for (int mu = 0; mu < k; ++mu) {
+            double xs[3] = {zs[mu % m], zs[m + (mu / m) % m], zs[2 * m + mu / (m * m)]};
+            S[nu * k + mu] = H->kernel == OR_TEST_POLY ? test_poly_kernel(xt, xs) : kernel_slp(xt, xs);
+        }
+    }
+}
+
+void or_h2_matvec(const or_h2* H, const double* x, int nrhs, double* y, int transpose, int parts) {
+    const tree_t* T = &H->T;
+    int64_t n = T->n, nc = T->count;
+    int k = H->k;
+    double* xh = calloc((size_t)nc * k * nrhs, sizeof(double)); /* xh[c][nu][r] */
+    double* yh = calloc((size_t)nc * k * nrhs, sizeof(double));
+    double** Bin = transpose ? H->V : H->W;   /* basis applied to the input  */
+    double** Bout = transpose ? H->W : H->V;  /* basis applied to the output */
+    /* forward transformation at the leaves */
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int nu = 0; nu < k; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+                double s = 0.0;
+                for (int64_t a = 0; a < sz; ++a) s += Bin[c][a * k + nu] * x[T->perm[b + a] + r * n];
+                xh[(c * k + nu) * nrhs + r] = s;
+            }
+    }
+    /* upward pass: children carry larger DFS numbers than their parents */
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        if (T->child0[c] < 0) continue;
+        int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q) {
+            const double* E = H->E[ch[q]];
+            for (int nu = 0; nu < k; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nup = 0; nup < k; ++nup) s += E[nup * k + nu] * xh[(ch[q] * k + nup) * nrhs + r];
+                    xh[(c * k + nu) * nrhs + r] += s;
+                }
+        }
+    }
+    /* coupling */
+    const int64_t* ptr = transpose ? H->far_ptr_t : H->far_ptr;
+    const int64_t* col = transpose ? H->far_row_t : H->far_col;
+#pragma omp parallel
+    {
+        double* S = malloc((size_t)k * k * sizeof(double));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nc; ++t) {
+            for (int64_t b = ptr[t]; b < ptr[t + 1]; ++b) {
+                int64_t s = col[b];
+                if (!transpose) coupling_matrix(H, t, s, S);  /* S_ts */
+                else coupling_matrix(H, s, t, S);             /* S_st, used transposed */
+                for (int nu = 0; nu < k; ++nu)
+                    for (int r = 0; r < nrhs; ++r) {
+                        double acc = 0.0;
+                        for (int mu = 0; mu < k; ++mu) {
+                            double smu = transpose ? S[mu * k + nu] : S[nu * k + mu];
+                            acc += smu * xh[(s * k + mu) * nrhs + r];
+                        }
+                        yh[(t * k + nu) * nrhs + r] += acc;
+                    }
+            }
+        }
+        free(S);
+    }
+    /* downward pass */
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] < 0) continue;
+        int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q) {
+            const double* E = H->E[ch[q]];
+            for (int nup = 0; nup < k; ++nup)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < k; ++nu) s += E[nup * k + nu] * yh[(c * k + nu) * nrhs + r];
+                    yh[(ch[q] * k + nup) * nrhs + r] += s;
+                }
+        }
+    }
+    for (int64_t i = 0; i < n * nrhs; ++i) y[i] = 0.0;
+    /* backward transformation at the leaves, then the nearfield */
+    const int64_t* nptr = transpose ? H->near_ptr_t : H->near_ptr;
+    const int64_t* ncol = transpose ? H->near_row_t : H->near_col;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int64_t a = 0; a < sz && (parts & OR_PART_FAR); ++a) {
+            int64_t i = T->perm[b + a];
+            for (int r = 0; r < nrhs; ++r) {
+                double s = 0.0;
+                for (int nu = 0; nu < k; ++nu) s += Bout[c][a * k + nu] * yh[(c * k + nu) * nrhs + r];
+                y[i + r * n] += s;
+            }
+        }
+        for (int64_t q = nptr[c]; q < nptr[c + 1] && (parts & OR_PART_NEAR); ++q) {
+            int64_t s = ncol[q];
+            for (int64_t a = 0; a < sz; ++a) {
+                int64_t i = T->perm[b + a];
+                for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                    int64_t j = T->perm[bb];
+                    double e = transpose ? or_entry(H->kernel, &H->mesh, j, i, H->q_ss)
+                                         : or_entry(H->kernel, &H->mesh, i, j, H->q_ss);
+                    for (int r = 0; r < nrhs; ++r) y[i + r * n] += e * x[j + r * n];
+                }
+            }
+        }
+    }
+    free(xh);
+    free(yh);
+}
+
+/* Selected rows of the H^2 product, one by one (forward only).  The forward
+ * transformation and the upward pass run in full; then row i in leaf t sums
+ * v S_as xh_s over the farfield blocks (a, s) of t and its ancestors a, with
+ * the row vector v = V_t[i,:] E_t E_parent(t) ... (eq. (transfer)), plus the
+ * nearfield row.  y: nrows x nrhs col-major (ld nrows). */
+void or_h2_rows(const or_h2* H, const int64_t* rows, int64_t nrows, const double* x, int nrhs, double* y) {
+    const tree_t* T = &H->T;
+    int64_t n = T->n, nc = T->count;
+    int k = H->k;
+    double* xh = calloc((size_t)nc * k * nrhs, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int nu = 0; nu < k; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+                double s = 0.0;
+                for (int64_t a = 0; a < sz; ++a) s += H->W[c][a * k + nu] * x[T->perm[b + a] + r * n];
+                xh[(c * k + nu) * nrhs + r] = s;
+            }
+    }
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        if (T->child0[c] < 0) continue;
+        int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q) {
+            const double* E = H->E[ch[q]];
+            for (int nu = 0; nu < k; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nup = 0; nup < k; ++nup) s += E[nup * k + nu] * xh[(ch[q] * k + nup) * nrhs + r];
+                    xh[(c * k + nu) * nrhs + r] += s;
+                }
+        }
+    }
+    /* inverse permutation and leaf of each position */
+    int64_t* pos = malloc(n * sizeof(int64_t));
+    for (int64_t a = 0; a < n; ++a) pos[T->perm[a]] = a;
+    int64_t* leaf_of = malloc(n * sizeof(int64_t));
+    for (int64_t c = 0; c < nc; ++c)
+        if (T->child0[c] < 0)
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a) leaf_of[a] = c;
+#pragma omp parallel
+    {
+        double* S = malloc((size_t)k * k * sizeof(double));
+        double* v = malloc(k * sizeof(double));
+        double* v2 = malloc(k * sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nrows; ++q) {
+            int64_t i = rows[q], a = pos[i], t = leaf_of[a];
+            double acc[64];
+            for (int r = 0; r < nrhs; ++r) acc[r] = 0.0;
+            for (int nu = 0; nu < k; ++nu) v[nu] = H->V[t][(a - T->begin[t]) * k + nu];
+            int64_t c = t;
+            while (c >= 0) {
+                for (int64_t b = H->far_ptr[c]; b < H->far_ptr[c + 1]; ++b) {
+                    int64_t s = H->far_col[b];
+                    coupling_matrix(H, c, s, S);
+                    for (int nu = 0; nu < k; ++nu)
+                        for (int r = 0; r < nrhs; ++r) {
+                            double sm = 0.0;
+                            for (int mu = 0; mu < k; ++mu) sm += S[nu * k + mu] * xh[(s * k + mu) * nrhs + r];
+                            acc[r] += v[nu] * sm;
+                        }
+                }
+                if (T->parent[c] < 0) break;
+                /* V_parent|_c = V_c E_c */
+                for (int nu = 0; nu < k; ++nu) {
+                    double s = 0.0;
+                    for (int nup = 0; nup < k; ++nup) s += v[nup] * H->E[c][nup * k + nu];
+                    v2[nu] = s;
+                }
+                memcpy(v, v2, k * sizeof(double));
+                c = T->parent[c];
+            }
+            for (int64_t b = H->near_ptr[t]; b < H->near_ptr[t + 1]; ++b) {
+                int64_t s = H->near_col[b];
+                for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                    int64_t j = T->perm[bb];
+                    double e = or_entry(H->kernel, &H->mesh, i, j, H->q_ss);
+                    for (int r = 0; r < nrhs; ++r) acc[r] += e * x[j + r * n];
+                }
+            }
+            for (int r = 0; r < nrhs; ++r) y[q + r * nrows] = acc[r];
+        }
+        free(S);
+        free(v);
+        free(v2);
+    }
+    free(pos);
+    free(leaf_of);
+    free(xh);
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
