@@ -1,0 +1,175 @@
+/*
+ * h2bem — H^2-matrix-vector products for the Galerkin boundary element
+ * discretisation of the 3-D Laplace single-layer (G) and double-layer (K)
+ * operators on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Problem (S. Boerm, "Fast large-scale boundary element algorithms"):
+ *   section 1, eq. (slp):  g_ij = int_{tau_i} int_{tau_j} g(x,y) dy dx,
+ *   section 1, eq. (dlp):  k_ij = int_{tau_i} int_{tau_j} dg/dn_y(x,y) dy dx,
+ *   with g(x,y) = 1/(4 pi |x-y|), piecewise-constant basis functions
+ *   psi_i = 1 on triangle tau_i (the Dirichlet basis of eq. (dlp) is taken
+ *   piecewise constant as well).
+ *   The matrix is approximated by an H^2-matrix (section 2, eq. (vsw)):
+ *   farfield blocks G|_{t x s} ~ V_t S_ts W_s^T with tensor Chebyshev cluster
+ *   bases of order m (k = m^3, section 3), nested through transfer matrices
+ *   (section 2, eq. (transfer)); nearfield blocks are evaluated on the fly by
+ *   a 7 x 7-point Gauss rule (regular pairs) and Sauter-Schwab quadrature
+ *   (pairs sharing a vertex, sections 1 and 5).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status: H2BEM_OK (0) or one of the
+ *     H2BEM_ERR_* codes.  On error nothing is written to the outputs and a
+ *     message is kept for the calling thread (h2bem_last_error).
+ *   - Handles are opaque.  The library copies what it needs from the caller's
+ *     buffers; the caller keeps ownership of every buffer it passes.  The
+ *     library owns (allocates and frees) the device memory of its handles.
+ *   - Triangles are int32 vertex indices, oriented counter-clockwise seen
+ *     from outside, so (b-a)x(c-a) is the outward normal (section 1).
+ *   - Vectors are column-major n x nrhs with a leading dimension >= n, in the
+ *     caller's triangle order.
+ *   - Functions that take a `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) enqueue their GPU work on it; unless stated otherwise they
+ *     return once the work is enqueued.
+ *   - Nothing runs on a CPU fallback: without a usable CUDA device every GPU
+ *     entry point returns H2BEM_ERR_CUDA.
+ */
+#ifndef H2BEM_H
+#define H2BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define H2BEM_OK 0
+#define H2BEM_ERR_ARG 1     /* invalid argument (null pointer, range, size)  */
+#define H2BEM_ERR_MESH 2    /* degenerate triangle or inward orientation     */
+#define H2BEM_ERR_OOM 3     /* host or device allocation failed              */
+#define H2BEM_ERR_CUDA 4    /* CUDA runtime error or no usable device        */
+#define H2BEM_ERR_TIMEOUT 5 /* a bounded device-side wait expired            */
+#define H2BEM_ERR_STATE 6   /* handle used in a state that does not allow it */
+
+/* ---- operator kinds and precision tiers -------------------------------- */
+#define H2BEM_SLP 0 /* single layer G, eq. (slp) */
+#define H2BEM_DLP 1 /* double layer K, eq. (dlp) */
+
+#define H2BEM_FP64 0       /* every step in FP64                                   */
+#define H2BEM_MIXED_FP32 1 /* FP32 farfield and regular-pair evaluation, FP64      */
+                           /* singular quadrature and nearfield accumulation       */
+#define H2BEM_MIXED_TF32 2 /* as MIXED_FP32, coupling contraction on tensor cores  */
+                           /* in TF32 with FP32 accumulation                        */
+#define H2BEM_MIXED_BF16 3 /* as MIXED_TF32 with BF16 operands                      */
+
+typedef struct h2bem_mesh h2bem_mesh;
+typedef struct h2bem_tree h2bem_tree;
+typedef struct h2bem_op h2bem_op;
+
+/* Options of an operator.  Obtain defaults with h2bem_opts_default. */
+typedef struct {
+    int q_ss;           /* Gauss points per direction of the Sauter-Schwab rules (1..16, default 5) */
+    int precision;      /* H2BEM_FP64 (default) or a MIXED tier                                    */
+    int cache_singular; /* 1: evaluate the x-independent singular entries once at set-up and       */
+                        /*    keep them in device memory (about 13 doubles per triangle); 0: on    */
+                        /*    the fly in every apply (default)                                     */
+    int reserved[5];    /* must be zero                                                            */
+} h2bem_opts;
+
+/* Statistics of an operator (counts are exact, from its own block lists). */
+typedef struct {
+    int64_t n;                 /* triangles                                   */
+    int64_t nclusters, nleaves, depth;
+    int64_t nfar, nnear;       /* farfield / nearfield blocks                 */
+    int64_t near_pairs;        /* triangle pairs in nearfield blocks          */
+    int64_t regular_pairs;     /* of which share no vertex (7 x 7 rule)       */
+    int64_t singular_pairs[3]; /* canonical pairs: identical, edge, vertex    */
+    int64_t k;                 /* interpolation points per cluster, m^3       */
+    double last_apply_ms;      /* device time of the last apply (0 if none)   */
+    double stage_ms[8];        /* per stage of the last timed apply, see      */
+                               /* h2bem_apply_timed                            */
+} h2bem_stats;
+
+/* Message of the last failed call on the calling thread (empty if none).
+ * Writes at most len bytes including the terminating zero; returns H2BEM_OK. */
+int h2bem_last_error(char* buf, size_t len);
+
+/* ---- mesh (host only) ---------------------------------------------------- */
+/* Copies a surface mesh (section 1: index set of panels tau_i).
+ *   xyz: nv x 3 doubles (row per vertex); tri: nt x 3 int32 vertex indices.
+ * Errors: H2BEM_ERR_ARG for null pointers, nv < 3, nt < 1 or an index out of
+ * range; H2BEM_ERR_MESH if a triangle has zero area or the signed enclosed
+ * volume sum_i a_i.(b_i x c_i)/6 is not positive (triangles inward). */
+int h2bem_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, h2bem_mesh** out);
+int h2bem_mesh_destroy(h2bem_mesh* mesh);
+
+/* ---- cluster tree (host only; section 2, Definition "cluster tree") ------ */
+/* Builds the cluster tree by bounding-box bisection: box = bounding box of
+ * the vertices of the cluster's triangles (section 3: supp psi_i in B_t);
+ * split while |t| > leaf_size along the longest axis (lowest axis on ties) at
+ * the box midpoint, by triangle centroid (< midpoint to the first child, in
+ * the current order); a stable median split if one side would be empty.
+ * Clusters are numbered in depth-first pre-order.  leaf_size >= 1. */
+int h2bem_tree_build(const h2bem_mesh* mesh, int leaf_size, h2bem_tree** out);
+/* Takes a caller-made cluster tree: perm[n] (tree position -> triangle),
+ * begin/end[nclusters] (ranges of tree positions), child0/child1[nclusters]
+ * (-1 = none; a cluster has no child or two).  Cluster 0 is the root; each
+ * child's range is the matching half of its parent's.  Boxes are recomputed.
+ * Errors: H2BEM_ERR_ARG if the arrays do not describe such a tree. */
+int h2bem_tree_upload(const h2bem_mesh* mesh, int64_t nclusters, const int64_t* perm, const int64_t* begin,
+                      const int64_t* end, const int64_t* child0, const int64_t* child1, h2bem_tree** out);
+/* Counts; any output pointer may be NULL. */
+int h2bem_tree_info(const h2bem_tree* tree, int64_t* nclusters, int64_t* nleaves, int64_t* depth);
+/* Copies the tree out (arrays sized as in h2bem_tree_upload; bmin/bmax are
+ * nclusters x 3).  Any pointer may be NULL. */
+int h2bem_tree_export(const h2bem_tree* tree, int64_t* perm, int64_t* begin, int64_t* end, int64_t* child0,
+                      int64_t* child1, double* bmin, double* bmax);
+int h2bem_tree_destroy(h2bem_tree* tree);
+
+/* ---- block tree (host only; section 2, Definition "block tree") ---------- */
+/* Farfield and nearfield leaves from (root, root): farfield if dist > 0 and
+ * max(diam B_t, diam B_s) <= eta dist(B_t, B_s) (section 3,
+ * eq. (admissibility) with the factor 2 folded into eta); nearfield if both
+ * clusters are leaves; else subdivide per the block-tree definition.
+ * Call with NULL arrays to get the counts, then with arrays of those sizes.
+ * eta >= 0 (eta = 0: everything nearfield). */
+int h2bem_blocks(const h2bem_tree* tree, double eta, int64_t* nfar, int64_t* nnear, int64_t* far_t, int64_t* far_s,
+                 int64_t* near_t, int64_t* near_s);
+
+/* ---- operator -------------------------------------------------------------- */
+int h2bem_opts_default(h2bem_opts* opts);
+/* Selects G (H2BEM_SLP) or K (H2BEM_DLP), interpolation order m (1..8,
+ * k = m^3, section 3) and admissibility eta; builds the block lists and
+ * uploads mesh, tree and lists to the current CUDA device.  opts may be NULL
+ * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts), OOM, CUDA. */
+int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
+                          const h2bem_opts* opts, h2bem_op** out);
+int h2bem_operator_destroy(h2bem_op* op);
+int h2bem_stats_get(const h2bem_op* op, h2bem_stats* stats);
+
+/* y = A x (A = G or K in its H^2 approximation; section 2, eq. (vsw) for the
+ * farfield, eq. (slp)/(dlp) quadrature for the nearfield).
+ *   x: n x nrhs, leading dimension ldx >= n; y: n x nrhs, ldy >= n; both in
+ *   the caller's triangle order; 1 <= nrhs <= 64.  x and y may each be
+ *   device or host memory (detected per pointer); they must not overlap.
+ *   With device buffers the call is asynchronous on `stream`; with a host
+ *   buffer it copies through device scratch and synchronises the stream
+ *   before returning.
+ * Scratch device memory is allocated on the first call and grown when nrhs
+ * grows; concurrent applies of one operator on different streams race on it.
+ * Errors: ARG (null, nrhs, ld), CUDA, OOM. */
+int h2bem_apply(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
+/* y = A^T x, same conventions (transposed blocks, V and W exchanged). */
+int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                          void* stream);
+/* As h2bem_apply with device buffers only, and records CUDA events around
+ * each stage on `stream`; synchronises and fills the stats' stage_ms:
+ * [0] permute in, [1] leaf forward, [2] upward, [3] coupling, [4] downward,
+ * [5] leaf backward, [6] nearfield regular, [7] nearfield singular. */
+int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

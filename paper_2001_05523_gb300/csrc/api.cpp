@@ -1,0 +1,1049 @@
+// libh2bem host side: validation, cluster tree, block tree, singular-pair
+// lists, quadrature tables, device upload and the apply sequence.
+// The C ABI is declared and documented in include/h2bem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/h2bem.h"
+#include "internal.h"
+
+using h2::kMaxLeaf;
+using h2::kMaxM;
+
+// ===========================================================================
+// errors
+// ===========================================================================
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? H2BEM_ERR_OOM : H2BEM_ERR_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                           \
+    } while (0)
+
+extern "C" int h2bem_last_error(char* buf, size_t len) {
+    if (buf && len) {
+        size_t n = std::min(len - 1, g_err.size());
+        memcpy(buf, g_err.data(), n);
+        buf[n] = 0;
+    }
+    return H2BEM_OK;
+}
+
+// ===========================================================================
+// mesh
+// ===========================================================================
+struct h2bem_mesh {
+    std::vector<double> xyz;
+    std::vector<int32_t> tri;
+    int64_t nv = 0, nt = 0;
+};
+
+extern "C" int h2bem_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, h2bem_mesh** out) {
+    if (!out) return fail(H2BEM_ERR_ARG, "mesh_create: out is NULL");
+    *out = nullptr;
+    if (!xyz || !tri) return fail(H2BEM_ERR_ARG, "mesh_create: NULL array");
+    if (nv < 3 || nt < 1) return fail(H2BEM_ERR_ARG, "mesh_create: need nv >= 3 and nt >= 1 (got %lld, %lld)",
+                                      (long long)nv, (long long)nt);
+    if (nt > (int64_t)1 << 30 || nv > (int64_t)1 << 30) return fail(H2BEM_ERR_ARG, "mesh_create: mesh too large");
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (tri[i] < 0 || tri[i] >= nv)
+            return fail(H2BEM_ERR_ARG, "mesh_create: triangle %lld has vertex index %d out of range",
+                        (long long)(i / 3), (int)tri[i]);
+    double vol = 0.0;
+    for (int64_t i = 0; i < nt; ++i) {
+        const double* a = xyz + 3 * (int64_t)tri[3 * i];
+        const double* b = xyz + 3 * (int64_t)tri[3 * i + 1];
+        const double* c = xyz + 3 * (int64_t)tri[3 * i + 2];
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        if (!(len > 0.0)) return fail(H2BEM_ERR_MESH, "mesh_create: triangle %lld is degenerate", (long long)i);
+        vol += a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+    if (!(vol > 0.0))
+        return fail(H2BEM_ERR_MESH, "mesh_create: signed volume %.3e <= 0 (triangles must be counter-clockwise "
+                    "seen from outside)", vol / 6.0);
+    auto* m = new (std::nothrow) h2bem_mesh;
+    if (!m) return fail(H2BEM_ERR_OOM, "mesh_create: out of host memory");
+    m->xyz.assign(xyz, xyz + 3 * nv);
+    m->tri.assign(tri, tri + 3 * nt);
+    m->nv = nv;
+    m->nt = nt;
+    *out = m;
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_mesh_destroy(h2bem_mesh* mesh) {
+    delete mesh;
+    return H2BEM_OK;
+}
+
+// ===========================================================================
+// cluster tree
+// ===========================================================================
+struct h2bem_tree {
+    int64_t n = 0, nc = 0, depth = 0;
+    std::vector<int64_t> perm, begin, end, child0, child1, parent, level;
+    std::vector<double> bmin, bmax;  // nc x 3
+};
+
+namespace {
+
+void cluster_box(const h2bem_mesh& M, const int64_t* idx, int64_t cnt, double* lo, double* hi) {
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = INFINITY;
+        hi[d] = -INFINITY;
+    }
+    for (int64_t a = 0; a < cnt; ++a)
+        for (int c = 0; c < 3; ++c) {
+            const double* p = &M.xyz[3 * (int64_t)M.tri[3 * idx[a] + c]];
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], p[d]);
+                hi[d] = std::max(hi[d], p[d]);
+            }
+        }
+}
+
+double centroid(const h2bem_mesh& M, int64_t t, int d) {
+    const int32_t* v = &M.tri[3 * t];
+    return ((M.xyz[3 * (int64_t)v[0] + d] + M.xyz[3 * (int64_t)v[1] + d]) + M.xyz[3 * (int64_t)v[2] + d]) / 3.0;
+}
+
+struct TreeBuilder {
+    const h2bem_mesh& M;
+    h2bem_tree& T;
+    int leaf;
+    std::vector<int64_t> scratch;
+
+    int64_t add(int64_t b, int64_t e, int64_t parent, int64_t level) {
+        int64_t c = T.nc++;
+        T.begin.push_back(b);
+        T.end.push_back(e);
+        T.parent.push_back(parent);
+        T.level.push_back(level);
+        T.child0.push_back(-1);
+        T.child1.push_back(-1);
+        T.bmin.resize(3 * T.nc);
+        T.bmax.resize(3 * T.nc);
+        cluster_box(M, &T.perm[b], e - b, &T.bmin[3 * c], &T.bmax[3 * c]);
+        T.depth = std::max(T.depth, level);
+        return c;
+    }
+
+    // iterative depth-first pre-order construction
+    void build() {
+        struct Item { int64_t b, e, parent, level; int which; };
+        std::vector<Item> stack;
+        stack.push_back({0, T.n, -1, 0, -1});
+        while (!stack.empty()) {
+            Item it = stack.back();
+            stack.pop_back();
+            int64_t c = add(it.b, it.e, it.parent, it.level);
+            if (it.parent >= 0) (it.which == 0 ? T.child0 : T.child1)[it.parent] = c;
+            if (it.e - it.b <= leaf) continue;
+            const double* lo = &T.bmin[3 * c];
+            const double* hi = &T.bmax[3 * c];
+            int axis = 0;
+            for (int d = 1; d < 3; ++d)
+                if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
+            const double mid = 0.5 * (lo[axis] + hi[axis]);
+            int64_t* p = &T.perm[it.b];
+            const int64_t cnt = it.e - it.b;
+            scratch.resize(cnt);
+            int64_t n0 = 0, n1 = 0;
+            for (int64_t a = 0; a < cnt; ++a) {
+                if (centroid(M, p[a], axis) < mid) p[n0++] = p[a];
+                else scratch[n1++] = p[a];
+            }
+            std::copy(scratch.begin(), scratch.begin() + n1, p + n0);
+            int64_t split = n0;
+            if (n0 == 0 || n1 == 0) {
+                std::vector<std::pair<double, int64_t>> key(cnt);
+                for (int64_t a = 0; a < cnt; ++a) key[a] = {centroid(M, p[a], axis), a};
+                std::stable_sort(key.begin(), key.end(),
+                                 [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
+                                     return x.first < y.first;
+                                 });
+                std::vector<int64_t> tmp(cnt);
+                for (int64_t a = 0; a < cnt; ++a) tmp[a] = p[key[a].second];
+                std::copy(tmp.begin(), tmp.end(), p);
+                split = cnt / 2;
+            }
+            // push the second child first so the first child is numbered next
+            stack.push_back({it.b + split, it.e, c, it.level + 1, 1});
+            stack.push_back({it.b, it.b + split, c, it.level + 1, 0});
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int h2bem_tree_build(const h2bem_mesh* mesh, int leaf_size, h2bem_tree** out) {
+    if (!out) return fail(H2BEM_ERR_ARG, "tree_build: out is NULL");
+    *out = nullptr;
+    if (!mesh) return fail(H2BEM_ERR_ARG, "tree_build: mesh is NULL");
+    if (leaf_size < 1) return fail(H2BEM_ERR_ARG, "tree_build: leaf_size must be >= 1");
+    std::unique_ptr<h2bem_tree> T(new (std::nothrow) h2bem_tree);
+    if (!T) return fail(H2BEM_ERR_OOM, "tree_build: out of host memory");
+    T->n = mesh->nt;
+    T->perm.resize(T->n);
+    for (int64_t i = 0; i < T->n; ++i) T->perm[i] = i;
+    TreeBuilder B{*mesh, *T, leaf_size, {}};
+    B.build();
+    *out = T.release();
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_tree_upload(const h2bem_mesh* mesh, int64_t nclusters, const int64_t* perm, const int64_t* begin,
+                                 const int64_t* end, const int64_t* child0, const int64_t* child1, h2bem_tree** out) {
+    if (!out) return fail(H2BEM_ERR_ARG, "tree_upload: out is NULL");
+    *out = nullptr;
+    if (!mesh || !perm || !begin || !end || !child0 || !child1 || nclusters < 1)
+        return fail(H2BEM_ERR_ARG, "tree_upload: NULL array or nclusters < 1");
+    const int64_t n = mesh->nt;
+    std::vector<char> seen(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (perm[i] < 0 || perm[i] >= n || seen[perm[i]]) return fail(H2BEM_ERR_ARG, "tree_upload: perm is not a permutation");
+        seen[perm[i]] = 1;
+    }
+    if (begin[0] != 0 || end[0] != n) return fail(H2BEM_ERR_ARG, "tree_upload: root must span [0, n)");
+    std::unique_ptr<h2bem_tree> T(new (std::nothrow) h2bem_tree);
+    if (!T) return fail(H2BEM_ERR_OOM, "tree_upload: out of host memory");
+    T->n = n;
+    T->nc = nclusters;
+    T->perm.assign(perm, perm + n);
+    T->begin.assign(begin, begin + nclusters);
+    T->end.assign(end, end + nclusters);
+    T->child0.assign(child0, child0 + nclusters);
+    T->child1.assign(child1, child1 + nclusters);
+    T->parent.assign(nclusters, -1);
+    T->level.assign(nclusters, -1);
+    T->level[0] = 0;
+    int64_t reached = 1;
+    for (int64_t c = 0; c < nclusters; ++c) {
+        if (begin[c] < 0 || end[c] > n || begin[c] >= end[c])
+            return fail(H2BEM_ERR_ARG, "tree_upload: cluster %lld has an empty or invalid range", (long long)c);
+        const int64_t a = child0[c], b = child1[c];
+        if ((a < 0) != (b < 0)) return fail(H2BEM_ERR_ARG, "tree_upload: cluster %lld has one child", (long long)c);
+        if (a < 0) continue;
+        if (a >= nclusters || b >= nclusters || a == 0 || b == 0 || T->parent[a] >= 0 || T->parent[b] >= 0 || a == b)
+            return fail(H2BEM_ERR_ARG, "tree_upload: bad child index at cluster %lld", (long long)c);
+        if (begin[a] != begin[c] || end[a] != begin[b] || end[b] != end[c])
+            return fail(H2BEM_ERR_ARG, "tree_upload: children of %lld do not split its range", (long long)c);
+        T->parent[a] = T->parent[b] = c;
+        reached += 2;
+    }
+    if (reached != nclusters) return fail(H2BEM_ERR_ARG, "tree_upload: clusters unreachable from the root");
+    // levels top-down (parents need not precede children in the numbering)
+    std::vector<int64_t> st{0};
+    while (!st.empty()) {
+        int64_t c = st.back();
+        st.pop_back();
+        if (T->child0[c] >= 0) {
+            T->level[T->child0[c]] = T->level[T->child1[c]] = T->level[c] + 1;
+            st.push_back(T->child0[c]);
+            st.push_back(T->child1[c]);
+        }
+    }
+    T->bmin.resize(3 * nclusters);
+    T->bmax.resize(3 * nclusters);
+    for (int64_t c = 0; c < nclusters; ++c) {
+        T->depth = std::max(T->depth, T->level[c]);
+        cluster_box(*mesh, &T->perm[T->begin[c]], T->end[c] - T->begin[c], &T->bmin[3 * c], &T->bmax[3 * c]);
+    }
+    *out = T.release();
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_tree_info(const h2bem_tree* tree, int64_t* nclusters, int64_t* nleaves, int64_t* depth) {
+    if (!tree) return fail(H2BEM_ERR_ARG, "tree_info: tree is NULL");
+    if (nclusters) *nclusters = tree->nc;
+    if (nleaves) {
+        int64_t l = 0;
+        for (int64_t c = 0; c < tree->nc; ++c) l += tree->child0[c] < 0;
+        *nleaves = l;
+    }
+    if (depth) *depth = tree->depth;
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_tree_export(const h2bem_tree* tree, int64_t* perm, int64_t* begin, int64_t* end, int64_t* child0,
+                                 int64_t* child1, double* bmin, double* bmax) {
+    if (!tree) return fail(H2BEM_ERR_ARG, "tree_export: tree is NULL");
+    if (perm) std::copy(tree->perm.begin(), tree->perm.end(), perm);
+    if (begin) std::copy(tree->begin.begin(), tree->begin.end(), begin);
+    if (end) std::copy(tree->end.begin(), tree->end.end(), end);
+    if (child0) std::copy(tree->child0.begin(), tree->child0.end(), child0);
+    if (child1) std::copy(tree->child1.begin(), tree->child1.end(), child1);
+    if (bmin) std::copy(tree->bmin.begin(), tree->bmin.end(), bmin);
+    if (bmax) std::copy(tree->bmax.begin(), tree->bmax.end(), bmax);
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_tree_destroy(h2bem_tree* tree) {
+    delete tree;
+    return H2BEM_OK;
+}
+
+// ===========================================================================
+// block tree
+// ===========================================================================
+namespace {
+
+struct Blocks {
+    std::vector<int64_t> ft, fs, nt, ns;
+};
+
+double diam(const h2bem_tree& T, int64_t c) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double e = T.bmax[3 * c + d] - T.bmin[3 * c + d];
+        s += e * e;
+    }
+    return std::sqrt(s);
+}
+
+double dist(const h2bem_tree& T, int64_t a, int64_t b) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double g = 0.0;
+        if (T.bmin[3 * b + d] > T.bmax[3 * a + d]) g = T.bmin[3 * b + d] - T.bmax[3 * a + d];
+        else if (T.bmin[3 * a + d] > T.bmax[3 * b + d]) g = T.bmin[3 * a + d] - T.bmax[3 * b + d];
+        s += g * g;
+    }
+    return std::sqrt(s);
+}
+
+void build_blocks(const h2bem_tree& T, double eta, Blocks& B) {
+    std::vector<std::pair<int64_t, int64_t>> st{{0, 0}};
+    while (!st.empty()) {
+        auto [t, s] = st.back();
+        st.pop_back();
+        const double dd = dist(T, t, s);
+        if (dd > 0.0 && std::max(diam(T, t), diam(T, s)) <= eta * dd) {
+            B.ft.push_back(t);
+            B.fs.push_back(s);
+            continue;
+        }
+        const bool tl = T.child0[t] < 0, sl = T.child0[s] < 0;
+        if (tl && sl) {
+            B.nt.push_back(t);
+            B.ns.push_back(s);
+        } else if (tl) {
+            st.push_back({t, T.child1[s]});
+            st.push_back({t, T.child0[s]});
+        } else if (sl) {
+            st.push_back({T.child1[t], s});
+            st.push_back({T.child0[t], s});
+        } else {
+            st.push_back({T.child1[t], T.child1[s]});
+            st.push_back({T.child1[t], T.child0[s]});
+            st.push_back({T.child0[t], T.child1[s]});
+            st.push_back({T.child0[t], T.child0[s]});
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int h2bem_blocks(const h2bem_tree* tree, double eta, int64_t* nfar, int64_t* nnear, int64_t* far_t,
+                            int64_t* far_s, int64_t* near_t, int64_t* near_s) {
+    if (!tree) return fail(H2BEM_ERR_ARG, "blocks: tree is NULL");
+    if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(H2BEM_ERR_ARG, "blocks: eta must be finite and >= 0");
+    Blocks B;
+    build_blocks(*tree, eta, B);
+    if (nfar) *nfar = (int64_t)B.ft.size();
+    if (nnear) *nnear = (int64_t)B.nt.size();
+    if (far_t) std::copy(B.ft.begin(), B.ft.end(), far_t);
+    if (far_s) std::copy(B.fs.begin(), B.fs.end(), far_s);
+    if (near_t) std::copy(B.nt.begin(), B.nt.end(), near_t);
+    if (near_s) std::copy(B.ns.begin(), B.ns.end(), near_s);
+    return H2BEM_OK;
+}
+
+// ===========================================================================
+// quadrature (library's own construction)
+// ===========================================================================
+namespace {
+
+// Gauss-Legendre on [0,1] by the Golub-Welsch method: the nodes are the
+// eigenvalues of the symmetric tridiagonal Jacobi matrix of the Legendre
+// recurrence (off-diagonal k / sqrt(4k^2 - 1)), the weights the squared first
+// components of its normalised eigenvectors.  Eigen-decomposition by cyclic
+// Jacobi rotations (q <= 32).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    std::vector<double> A(q * q, 0.0), V(q * q, 0.0);
+    for (int i = 0; i < q; ++i) V[i * q + i] = 1.0;
+    for (int k = 1; k < q; ++k) {
+        double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[(k - 1) * q + k] = A[k * q + k - 1] = b;
+    }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < q; ++i)
+            for (int j = i + 1; j < q; ++j) off += A[i * q + j] * A[i * q + j];
+        if (off < 1e-40) break;
+        for (int p = 0; p < q; ++p)
+            for (int r = p + 1; r < q; ++r) {
+                double apr = A[p * q + r];
+                if (apr == 0.0) continue;
+                double theta = (A[r * q + r] - A[p * q + p]) / (2.0 * apr);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < q; ++k) {  // A <- A J
+                    double akp = A[k * q + p], akr = A[k * q + r];
+                    A[k * q + p] = c * akp - s * akr;
+                    A[k * q + r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < q; ++k) {  // A <- J^T A
+                    double apk = A[p * q + k], ark = A[r * q + k];
+                    A[p * q + k] = c * apk - s * ark;
+                    A[r * q + k] = s * apk + c * ark;
+                }
+                for (int k = 0; k < q; ++k) {  // V <- V J
+                    double vkp = V[k * q + p], vkr = V[k * q + r];
+                    V[k * q + p] = c * vkp - s * vkr;
+                    V[k * q + r] = s * vkp + c * vkr;
+                }
+            }
+    }
+    std::vector<std::pair<double, double>> nw(q);
+    for (int i = 0; i < q; ++i) nw[i] = {0.5 * (1.0 + A[i * q + i]), V[0 * q + i] * V[0 * q + i]};
+    std::sort(nw.begin(), nw.end());
+    x.resize(q);
+    w.resize(q);
+    for (int i = 0; i < q; ++i) {
+        x[i] = nw[i].first;
+        w[i] = nw[i].second;
+    }
+}
+
+// Sauter-Schwab point tables after the exact integration of the monomial
+// factors (see k_sing.cu).  Rows: identical [aa, 2ab, bb, W]; edge [6 Gram
+// monomials, alpha, beta, gamma, W_g, W_dg]; vertex [10 Gram monomials,
+// alpha..delta, W_g, W_dg].
+void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vector<double>& tv) {
+    std::vector<double> x, w;
+    gauss_legendre(q, x, w);
+    ti.clear();
+    te.clear();
+    tv.clear();
+    // identical: regions R1, R3, R5 (R2, R4, R6 mirror them); int xi^2 a = 1/6, times 2 mirrors
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < q; ++k) {
+            const double e = x[k];
+            double al, be;
+            if (r == 0) { al = e; be = 1.0; }
+            else if (r == 1) { al = 1.0; be = e; }
+            else { al = -e; be = 1.0 - e; }
+            ti.insert(ti.end(), {al * al, 2.0 * al * be, be * be, w[k] / 3.0});
+        }
+    // edge: (alpha, beta, gamma) for vectors (P1-P0, P2-P1, Q2-Q1)
+    for (int r = 0; r < 5; ++r)
+        for (int k = 0; k < q; ++k)
+            for (int l = 0; l < q; ++l) {
+                const double e2 = x[k], e3 = x[l], ww = w[k] * w[l];
+                double al, be, ga, f;
+                switch (r) {
+                    case 0: al = e2; be = e3; ga = -(1.0 - e2); f = 1.0; break;
+                    case 1: al = e2 * e3; be = 1.0; ga = -e2 * (1.0 - e3); f = e2; break;
+                    case 2: al = -e2; be = 1.0 - e2; ga = -e2 * e3; f = e2; break;
+                    case 3: al = -e2 * e3; be = e2 * (1.0 - e3); ga = -1.0; f = e2; break;
+                    default: al = -e2 * e3; be = 1.0 - e2 * e3; ga = -e2; f = e2; break;
+                }
+                te.insert(te.end(), {al * al, be * be, ga * ga, 2 * al * be, 2 * al * ga, 2 * be * ga, al, be, ga,
+                                     ww * f / 6.0, ww * f / 2.0});
+            }
+    // vertex: (alpha, beta, gamma, delta) for vectors (P1-P0, P2-P1, Q1-Q0, Q2-Q1)
+    for (int r = 0; r < 2; ++r)
+        for (int i = 0; i < q; ++i)
+            for (int k = 0; k < q; ++k)
+                for (int l = 0; l < q; ++l) {
+                    const double e1 = x[i], e2 = x[k], e3 = x[l], ww = w[i] * w[k] * w[l];
+                    double al, be, ga, de;
+                    if (r == 0) { al = 1.0; be = e1; ga = -e2; de = -e2 * e3; }
+                    else { al = e2; be = e2 * e3; ga = -1.0; de = -e1; }
+                    tv.insert(tv.end(), {al * al, be * be, ga * ga, de * de, 2 * al * be, 2 * al * ga, 2 * al * de,
+                                         2 * be * ga, 2 * be * de, 2 * ga * de, al, be, ga, de, ww * e2 / 3.0,
+                                         ww * e2 / 2.0});
+                }
+}
+
+}  // namespace
+
+// ===========================================================================
+// operator
+// ===========================================================================
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t b) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (b == 0) return H2BEM_OK;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? H2BEM_ERR_OOM : H2BEM_ERR_CUDA, "cudaMalloc(%zu): %s", b,
+                        cudaGetErrorString(e));
+        }
+        bytes = b;
+        return H2BEM_OK;
+    }
+    template <typename T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <typename T>
+static int upload(DevBuf& d, const std::vector<T>& h) {
+    int rc = d.alloc(h.size() * sizeof(T));
+    if (rc) return rc;
+    if (!h.empty()) CU(cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return H2BEM_OK;
+}
+
+struct Csr {
+    std::vector<int> rows, ptr, col;  // compacted rows with >= 1 entry
+    DevBuf drows, dptr, dcol;
+    int upload_all() {
+        int rc;
+        if ((rc = upload(drows, rows)) || (rc = upload(dptr, ptr)) || (rc = upload(dcol, col))) return rc;
+        return H2BEM_OK;
+    }
+    int nrows() const { return (int)rows.size(); }
+};
+
+static void make_csr(int64_t nkeys, const std::vector<int64_t>& key, const std::vector<int64_t>& val, Csr& C,
+                     const std::vector<int>* remap_rows = nullptr) {
+    std::vector<int64_t> cnt(nkeys + 1, 0);
+    for (int64_t k : key) cnt[k + 1]++;
+    for (int64_t r = 0; r < nkeys; ++r) cnt[r + 1] += cnt[r];
+    std::vector<int> colall(key.size());
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t b = 0; b < key.size(); ++b) colall[fill[key[b]]++] = (int)val[b];
+    C.rows.clear();
+    C.ptr.assign(1, 0);
+    C.col.clear();
+    for (int64_t r = 0; r < nkeys; ++r) {
+        if (cnt[r + 1] == cnt[r]) continue;
+        C.rows.push_back(remap_rows ? (*remap_rows)[r] : (int)r);
+        // columns of a row in increasing cluster order
+        std::vector<int> cs(colall.begin() + cnt[r], colall.begin() + cnt[r + 1]);
+        std::sort(cs.begin(), cs.end());
+        C.col.insert(C.col.end(), cs.begin(), cs.end());
+        C.ptr.push_back((int)C.col.size());
+    }
+}
+
+struct h2bem_op {
+    int kernel = 0, m = 0, k = 0, precision = 0, q_ss = 5, cache_singular = 0;
+    double eta = 0;
+    int64_t n = 0, nc = 0, nleaves = 0, depth = 0;
+    int64_t nfar = 0, nnear = 0, near_pairs = 0, sing[3] = {0, 0, 0};
+    h2::Consts consts{};
+    // device geometry and tree
+    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid;
+    DevBuf cbegin, cend, cchild0, cchild1, cbox, leaves, basis_rule;
+    std::vector<int> leaves_h;
+    std::vector<std::vector<int>> level_parents;  // non-leaf clusters per level
+    std::vector<DevBuf> dlevel;
+    Csr far, far_t, near, near_t;
+    // singular pairs by type (index 0: identical, 1: edge, 2: vertex)
+    DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3];
+    int sp_npts[3] = {0, 0, 0};
+    int64_t sp_count[3] = {0, 0, 0};
+    // workspace
+    int ws_NR = 0;
+    DevBuf xp, yp, xh, yh, xstage, ystage;
+    size_t stage_elems = 0;
+    cudaEvent_t ev[10] = {};
+    double last_ms = 0.0, stage_ms[8] = {0};
+
+    h2::Geom geom() const {
+        return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
+                        ctr.as<const double>(), vid.as<const int>()};
+    }
+    h2::Tree tree() const {
+        return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
+                        cchild1.as<const int>(), cbox.as<const double>()};
+    }
+    ~h2bem_op() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+extern "C" int h2bem_opts_default(h2bem_opts* opts) {
+    if (!opts) return fail(H2BEM_ERR_ARG, "opts_default: NULL");
+    memset(opts, 0, sizeof *opts);
+    opts->q_ss = 5;
+    opts->precision = H2BEM_FP64;
+    opts->cache_singular = 0;
+    return H2BEM_OK;
+}
+
+namespace {
+
+// Singular pairs in the canonical orientation: outer panel = lower user index.
+// code bits: [1:0] rotation of the outer panel, [3:2],[5:4],[7:6] corners of
+// the inner panel listed as Q0, Q1, Q2.
+void singular_pairs(const h2bem_mesh& M, std::vector<int64_t> lo[3], std::vector<int64_t> hi[3],
+                    std::vector<int> code[3]) {
+    const int64_t nt = M.nt, nv = M.nv;
+    std::vector<int64_t> vptr(nv + 1, 0);
+    for (int64_t i = 0; i < 3 * nt; ++i) vptr[M.tri[i] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    std::vector<int64_t> vtri(3 * nt), fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int c = 0; c < 3; ++c) vtri[fill[M.tri[3 * t + c]]++] = t;
+    std::vector<int64_t> nb;
+    for (int64_t i = 0; i < nt; ++i) {
+        const int32_t* ti = &M.tri[3 * i];
+        nb.clear();
+        for (int c = 0; c < 3; ++c)
+            for (int64_t e = vptr[ti[c]]; e < vptr[ti[c] + 1]; ++e)
+                if (vtri[e] >= i) nb.push_back(vtri[e]);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        for (int64_t j : nb) {
+            const int32_t* tj = &M.tri[3 * j];
+            int shared = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) shared += ti[a] == tj[b];
+            int cd = 0, slot;
+            if (j == i) {
+                slot = 0;
+                cd = 0 | (0 << 2) | (1 << 4) | (2 << 6);
+            } else if (shared == 2) {
+                slot = 1;
+                int un = 0;
+                for (int a = 0; a < 3; ++a) {
+                    bool f = false;
+                    for (int b = 0; b < 3; ++b) f |= ti[a] == tj[b];
+                    if (!f) un = a;
+                }
+                const int rP = (un + 1) % 3;
+                const int32_t p0 = ti[rP], p1 = ti[(rP + 1) % 3];
+                int q0 = 0, q1 = 0, q2 = 0;
+                for (int b = 0; b < 3; ++b) {
+                    if (tj[b] == p0) q0 = b;
+                    else if (tj[b] == p1) q1 = b;
+                    else q2 = b;
+                }
+                cd = rP | (q0 << 2) | (q1 << 4) | (q2 << 6);
+            } else if (shared == 1) {
+                slot = 2;
+                int a0 = 0, b0 = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        if (ti[a] == tj[b]) { a0 = a; b0 = b; }
+                cd = a0 | (b0 << 2) | (((b0 + 1) % 3) << 4) | (((b0 + 2) % 3) << 6);
+            } else {
+                continue;  // duplicate triangles sharing three vertices are not supported
+            }
+            lo[slot].push_back(i);
+            hi[slot].push_back(j);
+            code[slot].push_back(cd);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
+                                     const h2bem_opts* opts_in, h2bem_op** out) {
+    if (!out) return fail(H2BEM_ERR_ARG, "operator_create: out is NULL");
+    *out = nullptr;
+    if (!mesh || !tree) return fail(H2BEM_ERR_ARG, "operator_create: NULL mesh or tree");
+    if (tree->n != mesh->nt) return fail(H2BEM_ERR_ARG, "operator_create: tree is for %lld triangles, mesh has %lld",
+                                         (long long)tree->n, (long long)mesh->nt);
+    if (kernel != H2BEM_SLP && kernel != H2BEM_DLP) return fail(H2BEM_ERR_ARG, "operator_create: kernel must be SLP or DLP");
+    if (m < 1 || m > kMaxM) return fail(H2BEM_ERR_ARG, "operator_create: m must be in 1..%d", kMaxM);
+    if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(H2BEM_ERR_ARG, "operator_create: eta must be finite and >= 0");
+    h2bem_opts opts;
+    h2bem_opts_default(&opts);
+    if (opts_in) opts = *opts_in;
+    if (opts.q_ss < 1 || opts.q_ss > h2::kMaxQss) return fail(H2BEM_ERR_ARG, "operator_create: q_ss must be in 1..%d", h2::kMaxQss);
+    if (opts.precision != H2BEM_FP64 && opts.precision != H2BEM_MIXED_FP32)
+        return fail(H2BEM_ERR_ARG, "operator_create: precision tier %d is not available", opts.precision);
+    for (int r : opts.reserved)
+        if (r) return fail(H2BEM_ERR_ARG, "operator_create: reserved option fields must be zero");
+    for (int64_t c = 0; c < tree->nc; ++c)
+        if (tree->child0[c] < 0 && tree->end[c] - tree->begin[c] > kMaxLeaf)
+            return fail(H2BEM_ERR_ARG, "operator_create: leaf clusters may hold at most %d triangles", kMaxLeaf);
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
+        return fail(H2BEM_ERR_CUDA, "operator_create: no CUDA device");
+
+    std::unique_ptr<h2bem_op> op(new (std::nothrow) h2bem_op);
+    if (!op) return fail(H2BEM_ERR_OOM, "operator_create: out of host memory");
+    op->kernel = kernel;
+    op->m = m;
+    op->k = m * m * m;
+    op->eta = eta;
+    op->precision = opts.precision;
+    op->q_ss = opts.q_ss;
+    op->cache_singular = opts.cache_singular ? 1 : 0;
+    op->n = mesh->nt;
+    op->nc = tree->nc;
+    op->depth = tree->depth;
+    const int64_t n = op->n, nc = op->nc;
+
+    // constants
+    h2::Consts& C = op->consts;
+    C.m = m;
+    C.k = m * m * m;
+    for (int a = 0; a < m; ++a) C.cheb[a] = std::cos((2.0 * a + 1.0) * M_PI / (2.0 * m));
+    {
+        const double r = std::sqrt(15.0);
+        const double a = (6.0 - r) / 21.0, b = (6.0 + r) / 21.0;
+        const double wa = (155.0 - r) / 1200.0, wb = (155.0 + r) / 1200.0;
+        const double u[7] = {1.0 / 3.0, a, 1.0 - 2.0 * a, a, b, 1.0 - 2.0 * b, b};
+        const double v[7] = {1.0 / 3.0, a, a, 1.0 - 2.0 * a, b, b, 1.0 - 2.0 * b};
+        const double w[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+        for (int p = 0; p < 7; ++p) {
+            C.ru[p] = u[p];
+            C.rv[p] = v[p];
+            C.rw[p] = w[p];
+        }
+    }
+    // leaf-basis rule: collapsed Gauss, exact for total degree 3(m-1)
+    {
+        const int qb = (3 * (m - 1) + 3) / 2;
+        std::vector<double> x, w, rule;
+        gauss_legendre(std::max(qb, 1), x, w);
+        for (size_t i = 0; i < x.size(); ++i)
+            for (size_t j = 0; j < x.size(); ++j) rule.insert(rule.end(), {x[i], (1.0 - x[i]) * x[j], 2.0 * w[i] * w[j] * (1.0 - x[i])});
+        C.nb = (int)(rule.size() / 3);
+        if (C.nb > h2::kMaxBasisPts) return fail(H2BEM_ERR_ARG, "operator_create: basis rule too large");
+        int rc = upload(op->basis_rule, rule);
+        if (rc) return rc;
+    }
+
+    // tree arrays, interpolation boxes (half-widths floored at 1e-2 of the largest)
+    std::vector<int> iperm(n), permv(n), cb(nc), ce(nc), c0(nc), c1(nc);
+    std::vector<double> box(6 * nc);
+    for (int64_t i = 0; i < n; ++i) {
+        permv[i] = (int)tree->perm[i];
+        iperm[tree->perm[i]] = (int)i;
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        cb[c] = (int)tree->begin[c];
+        ce[c] = (int)tree->end[c];
+        c0[c] = (int)tree->child0[c];
+        c1[c] = (int)tree->child1[c];
+        double h[3], hmax = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            box[d * nc + c] = 0.5 * (tree->bmin[3 * c + d] + tree->bmax[3 * c + d]);
+            h[d] = 0.5 * (tree->bmax[3 * c + d] - tree->bmin[3 * c + d]);
+            hmax = std::max(hmax, h[d]);
+        }
+        for (int d = 0; d < 3; ++d) box[(3 + d) * nc + c] = std::max(h[d], 1e-2 * hmax);
+        if (c0[c] < 0) op->leaves_h.push_back((int)c);
+        else {
+            if ((int64_t)op->level_parents.size() <= tree->level[c]) op->level_parents.resize(tree->level[c] + 1);
+            op->level_parents[tree->level[c]].push_back((int)c);
+        }
+    }
+    op->nleaves = (int64_t)op->leaves_h.size();
+    std::vector<int> leaf_index(nc, -1);
+    for (size_t l = 0; l < op->leaves_h.size(); ++l) leaf_index[op->leaves_h[l]] = (int)l;
+
+    // block lists
+    Blocks B;
+    build_blocks(*tree, eta, B);
+    op->nfar = (int64_t)B.ft.size();
+    op->nnear = (int64_t)B.nt.size();
+    op->near_pairs = 0;
+    for (size_t b = 0; b < B.nt.size(); ++b)
+        op->near_pairs += (tree->end[B.nt[b]] - tree->begin[B.nt[b]]) * (tree->end[B.ns[b]] - tree->begin[B.ns[b]]);
+    make_csr(nc, B.ft, B.fs, op->far);
+    make_csr(nc, B.fs, B.ft, op->far_t);
+    make_csr(nc, B.nt, B.ns, op->near);
+    make_csr(nc, B.ns, B.nt, op->near_t);
+
+    // singular pairs (tree positions), sorted by outer position
+    std::vector<int64_t> slo[3], shi[3];
+    std::vector<int> scode[3];
+    singular_pairs(*mesh, slo, shi, scode);
+    std::vector<double> tabs[3];
+    ss_tables(op->q_ss, tabs[0], tabs[1], tabs[2]);
+    const int widths[3] = {4, 11, 16};
+
+    int rc;
+    if ((rc = upload(op->xyz, mesh->xyz)) || (rc = upload(op->tri, std::vector<int>(mesh->tri.begin(), mesh->tri.end()))) ||
+        (rc = upload(op->perm, permv)) || (rc = upload(op->iperm, iperm)) || (rc = upload(op->cbegin, cb)) ||
+        (rc = upload(op->cend, ce)) || (rc = upload(op->cchild0, c0)) || (rc = upload(op->cchild1, c1)) ||
+        (rc = upload(op->cbox, box)) || (rc = upload(op->leaves, op->leaves_h)))
+        return rc;
+    if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
+        (rc = op->near_t.upload_all()))
+        return rc;
+    op->dlevel.resize(op->level_parents.size());
+    for (size_t L = 0; L < op->level_parents.size(); ++L)
+        if ((rc = upload(op->dlevel[L], op->level_parents[L]))) return rc;
+    for (int t = 0; t < 3; ++t) {
+        const size_t np = slo[t].size();
+        op->sing[t] = (int64_t)np;
+        op->sp_count[t] = (int64_t)np;
+        std::vector<int> lo(np), hi(np);
+        for (size_t p = 0; p < np; ++p) {
+            lo[p] = iperm[slo[t][p]];
+            hi[p] = iperm[shi[t][p]];
+        }
+        op->sp_npts[t] = (int)(tabs[t].size() / widths[t]);
+        if ((rc = upload(op->sp_lo[t], lo)) || (rc = upload(op->sp_hi[t], hi)) || (rc = upload(op->sp_code[t], scode[t])) ||
+            (rc = upload(op->sp_tab[t], tabs[t])))
+            return rc;
+    }
+    // geometry in tree order
+    if ((rc = op->v.alloc(9 * n * sizeof(double))) || (rc = op->area.alloc(n * sizeof(double))) ||
+        (rc = op->nrm.alloc(3 * n * sizeof(double))) || (rc = op->ctr.alloc(3 * n * sizeof(double))) ||
+        (rc = op->vid.alloc(3 * n * sizeof(int))))
+        return rc;
+    h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->v.as<double>(),
+                    op->area.as<double>(), op->nrm.as<double>(), op->ctr.as<double>(), op->vid.as<int>(), 0);
+    CU(cudaGetLastError());
+    // x-independent singular entries, evaluated once if requested
+    if (op->cache_singular) {
+        for (int t = 0; t < 3; ++t) {
+            const int np = (int)op->sp_count[t];
+            if ((rc = op->sp_v0[t].alloc(np * sizeof(double))) || (rc = op->sp_v1[t].alloc(np * sizeof(double)))) return rc;
+            if (t == 0 && kernel == H2BEM_DLP) {
+                if (np) {
+                    CU(cudaMemset(op->sp_v0[t].p, 0, np * sizeof(double)));
+                    CU(cudaMemset(op->sp_v1[t].p, 0, np * sizeof(double)));
+                }
+                continue;
+            }
+            h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, np, op->sp_lo[t].as<int>(), op->sp_hi[t].as<int>(),
+                                op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(), op->sp_npts[t], 1, false, 1,
+                                nullptr, nullptr, op->sp_v0[t].as<double>(), op->sp_v1[t].as<double>(), 0);
+            CU(cudaGetLastError());
+        }
+    }
+    CU(cudaDeviceSynchronize());
+    for (auto& e : op->ev) CU(cudaEventCreate(&e));
+    *out = op.release();
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_operator_destroy(h2bem_op* op) {
+    if (op) cudaDeviceSynchronize();
+    delete op;
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
+    if (!op || !st) return fail(H2BEM_ERR_ARG, "stats_get: NULL argument");
+    memset(st, 0, sizeof *st);
+    st->n = op->n;
+    st->nclusters = op->nc;
+    st->nleaves = op->nleaves;
+    st->depth = op->depth;
+    st->nfar = op->nfar;
+    st->nnear = op->nnear;
+    st->near_pairs = op->near_pairs;
+    st->singular_pairs[0] = op->sing[0];
+    st->singular_pairs[1] = op->sing[1];
+    st->singular_pairs[2] = op->sing[2];
+    st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
+    st->k = op->k;
+    st->last_apply_ms = op->last_ms;
+    for (int i = 0; i < 8; ++i) st->stage_ms[i] = op->stage_ms[i];
+    return H2BEM_OK;
+}
+
+// ===========================================================================
+// apply
+// ===========================================================================
+static int pad_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+
+static int ensure_workspace(h2bem_op* op, int NR) {
+    if (op->ws_NR >= NR) return H2BEM_OK;
+    const size_t fsz = op->precision == H2BEM_FP64 ? sizeof(double) : sizeof(float);
+    int rc;
+    if ((rc = op->xp.alloc(op->n * NR * sizeof(double))) || (rc = op->yp.alloc(op->n * NR * sizeof(double))) ||
+        (rc = op->xh.alloc((size_t)op->nc * op->k * NR * fsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * fsz)))
+        return rc;
+    op->ws_NR = NR;
+    return H2BEM_OK;
+}
+
+// One chunk of at most 16 right-hand sides, device buffers, tree order work.
+static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
+                       bool transpose, bool timed) {
+    const int NR = pad_nr(nrhs);
+    int rc = ensure_workspace(op, NR);
+    if (rc) return rc;
+    const bool fp32 = op->precision != H2BEM_FP64;
+    const size_t fsz = fp32 ? sizeof(float) : sizeof(double);
+    const h2::Geom g = op->geom();
+    const h2::Tree t = op->tree();
+    const h2::Consts& c = op->consts;
+    const int n = (int)op->n;
+    // forward basis and kernel variants: A = V S W^T + N;  A^T = W S^T V^T + N^T
+    const bool dlp = op->kernel == H2BEM_DLP;
+    const bool in_dlp = dlp && !transpose;   // W_s on the input side
+    const bool out_dlp = dlp && transpose;   // W_s on the output side
+    const int near_ker = !dlp ? h2::SLP : transpose ? h2::DLP_T : h2::DLP;
+    const Csr& far = transpose ? op->far_t : op->far;
+    const Csr& near = transpose ? op->near_t : op->near;
+    auto mark = [&](int i) {
+        if (timed) cudaEventRecord(op->ev[i], s);
+    };
+    mark(0);
+    h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
+    CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    mark(1);
+    if (op->nfar > 0) {
+        CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * fsz, s));
+        h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), in_dlp, fp32,
+                                NR, op->xp.as<double>(), op->xh.p, s);
+        mark(2);
+        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
+            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), fp32, NR, op->xh.p, s);
+        mark(3);
+        h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
+                            op->precision, NR, op->xh.p, op->yh.p, s);
+        mark(4);
+        for (size_t L = 0; L < op->level_parents.size(); ++L)
+            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), fp32, NR, op->yh.p, s);
+        mark(5);
+        h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), out_dlp,
+                                 fp32, NR, op->yh.p, op->yp.as<double>(), s);
+    } else {
+        for (int i = 2; i <= 5; ++i) mark(i);
+    }
+    mark(6);
+    // nearfield rows are row leaves (transposed: column leaves)
+    h2::launch_near_regular(g, t, c, near.nrows(), near.drows.as<int>(), near.dptr.as<int>(), near.dcol.as<int>(),
+                            near_ker, fp32, NR, op->xp.as<double>(), op->yp.as<double>(), s);
+    mark(7);
+    for (int ty = 0; ty < 3; ++ty) {
+        if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
+        const int np = (int)op->sp_count[ty];
+        if (op->cache_singular)
+            h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
+                                nullptr, nullptr, 0, 2, transpose, NR, op->xp.as<double>(), op->yp.as<double>(),
+                                op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
+        else
+            h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
+                                op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, transpose,
+                                NR, op->xp.as<double>(), op->yp.as<double>(), nullptr, nullptr, s);
+    }
+    mark(8);
+    h2::launch_permute_out(op->yp.as<double>(), NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+    mark(9);
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream,
+                      bool transpose, bool timed) {
+    if (!op) return fail(H2BEM_ERR_ARG, "apply: op is NULL");
+    if (!x || !y) return fail(H2BEM_ERR_ARG, "apply: NULL vector");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "apply: nrhs must be in 1..64");
+    if (ldx < op->n || ldy < op->n) return fail(H2BEM_ERR_ARG, "apply: leading dimensions must be >= n");
+    {
+        const char* xb = (const char*)x;
+        const char* xe = (const char*)(x + (nrhs - 1) * ldx + op->n);
+        const char* yb = (const char*)y;
+        const char* ye = (const char*)(y + (nrhs - 1) * ldy + op->n);
+        if (xb < ye && yb < xe) return fail(H2BEM_ERR_ARG, "apply: x and y overlap");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    if (timed && (!xdev || !ydev)) return fail(H2BEM_ERR_ARG, "apply_timed: x and y must be device memory");
+    const double* xd = x;
+    double* yd = y;
+    int64_t lx = ldx, ly = ldy;
+    if (!xdev || !ydev) {
+        const size_t need = (size_t)op->n * nrhs;
+        if (op->stage_elems < need) {
+            int rc;
+            if ((rc = op->xstage.alloc(need * sizeof(double))) || (rc = op->ystage.alloc(need * sizeof(double)))) return rc;
+            op->stage_elems = need;
+        }
+        if (!xdev) {
+            CU(cudaMemcpy2DAsync(op->xstage.p, op->n * sizeof(double), x, ldx * sizeof(double), op->n * sizeof(double),
+                                 nrhs, cudaMemcpyHostToDevice, s));
+            xd = op->xstage.as<double>();
+            lx = op->n;
+        }
+        if (!ydev) {
+            yd = op->ystage.as<double>();
+            ly = op->n;
+        }
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+        const int nr = std::min(16, nrhs - c0);
+        int rc = apply_chunk(op, xd + c0 * lx, lx, nr, yd + c0 * ly, ly, s, transpose, timed);
+        if (rc) return rc;
+    }
+    if (!ydev) {
+        CU(cudaMemcpy2DAsync(y, ldy * sizeof(double), yd, ly * sizeof(double), op->n * sizeof(double), nrhs,
+                             cudaMemcpyDeviceToHost, s));
+    }
+    if (!xdev || !ydev) CU(cudaStreamSynchronize(s));
+    if (timed) {
+        CU(cudaEventSynchronize(op->ev[9]));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, op->ev[0], op->ev[9]);
+        op->last_ms = ms;
+        const int map[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}};
+        for (int i = 0; i < 8; ++i) {
+            cudaEventElapsedTime(&ms, op->ev[map[i][0]], op->ev[map[i][1]]);
+            op->stage_ms[i] = ms;
+        }
+    }
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_apply(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream) {
+    return apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, false);
+}
+
+extern "C" int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                                     void* stream) {
+    return apply_impl(op, x, ldx, nrhs, y, ldy, stream, true, false);
+}
+
+extern "C" int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                                 void* stream) {
+    return apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, true);
+}

@@ -1,0 +1,82 @@
+// Internal declarations shared by the host set-up (api.cpp) and the CUDA
+// kernels of libh2bem.  Not part of the public C ABI (include/h2bem.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace h2 {
+
+constexpr int kMaxM = 6;             // interpolation order (k = m^3 <= 216)
+constexpr int kMaxK = kMaxM * kMaxM * kMaxM;
+constexpr int kMaxLeaf = 64;         // largest leaf cluster the kernels stage
+constexpr int kMaxBasisPts = 128;    // points of the leaf-basis triangle rule
+constexpr int kMaxQss = 8;           // Gauss points per singular direction
+
+enum Kernel { SLP = 0, DLP = 1, DLP_T = 2 };  // DLP_T: rows of K^T (normal at the row triangle)
+enum SingType { IDENTICAL = 3, EDGE = 2, VERTEX = 1 };
+
+// Triangles in tree order, structure of arrays.
+struct Geom {
+    int n;
+    const double* v;     // [9][n]: coordinate d of corner c at v[(3c+d)*n + i]
+    const double* area;  // [n]
+    const double* nrm;   // [3][n] outward unit normal
+    const double* ctr;   // [3][n] centroid
+    const int* vid;      // [3][n] vertex indices (singular-pair test)
+};
+
+// Cluster tree on the device.
+struct Tree {
+    int nc;
+    const int* begin;    // [nc] first tree position
+    const int* end;      // [nc] one past the last
+    const int* child0;   // [nc] -1 for leaves
+    const int* child1;
+    const double* box;   // [6][nc]: centre x,y,z then (floored) half-width x,y,z
+};
+
+// Quadrature and interpolation constants passed by value.
+struct Consts {
+    int m, k;
+    double cheb[kMaxM];          // cos((2a+1) pi / (2m)), a = 0..m-1
+    double ru[7], rv[7], rw[7];  // Radon 7-point rule on the unit simplex, weights sum to 1
+    int nb;                      // points of the leaf-basis rule
+};
+
+// ---- launchers (stream-ordered; no synchronisation) -----------------------
+void launch_geom(const double* xyz, const int* tri, const int* perm, int n, double* v, double* area, double* nrm,
+                 double* ctr, int* vid, cudaStream_t s);
+void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
+                       cudaStream_t s);
+void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,
+                        cudaStream_t s);
+
+// nearfield, regular pairs: one CTA per row leaf in `rows`, columns from CSR
+void launch_near_regular(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows,
+                         const int* ptr, const int* col, int ker, bool fp32, int NR, const double* xp, double* yp,
+                         cudaStream_t s);
+
+// nearfield, singular pairs of one type (canonical orientation, see api.cpp)
+//   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the
+//   values (val0 = a_{lo,hi}, val1 = a_{hi,lo});  mode 2: scatter stored values.
+void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
+                     const double* tab, int npts, int mode, bool transpose, int NR, const double* xp, double* yp,
+                     double* val0, double* val1, cudaStream_t s);
+
+// farfield
+void launch_leaf_forward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
+                         const int* leaves, bool dlp_basis, bool fp32, int NR, const double* xp, void* xh,
+                         cudaStream_t s);
+void launch_leaf_backward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
+                          const int* leaves, bool dlp_basis, bool fp32, int NR, const void* yh, double* yp,
+                          cudaStream_t s);
+void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* xh,
+                   cudaStream_t s);
+void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* yh,
+                     cudaStream_t s);
+// precision: 0 FP64, 1 FP32 SIMT, 2 TF32 tensor cores, 3 BF16 tensor cores
+void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                     int precision, int NR, const void* xh, void* yh, cudaStream_t s);
+
+}  // namespace h2

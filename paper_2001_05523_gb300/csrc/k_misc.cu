@@ -1,0 +1,72 @@
+// Gather/scatter between the caller's column-major vectors (user triangle
+// order, leading dimension ld) and the library's tree-ordered, RHS-interleaved
+// work vectors xp[pos * NR + r] (NR >= nrhs, padded columns are zero).
+#include "internal.h"
+
+namespace h2 {
+
+__global__ void k_permute_in(const double* __restrict__ x, int64_t ldx, int nrhs, int NR,
+                             const int* __restrict__ perm, int n, double* __restrict__ xp) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * NR) return;
+    int pos = (int)(idx / NR), r = (int)(idx % NR);
+    xp[idx] = r < nrhs ? x[perm[pos] + r * ldx] : 0.0;
+}
+
+// iperm: user index -> tree position; writes of y are coalesced.
+__global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, const int* __restrict__ iperm,
+                              int n, double* __restrict__ y, int64_t ldy) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * nrhs) return;
+    int r = (int)(idx / n), i = (int)(idx % n);
+    y[i + r * ldy] = yp[(int64_t)iperm[i] * NR + r];
+}
+
+// Geometry preparation: gathers the triangles into tree order and computes
+// area |tau| = |(b-a) x (c-a)| / 2, the unit normal (b-a) x (c-a) / |...| and
+// the centroid ((a+b)+c)/3 (section 1; the normal is outward for triangles
+// oriented counter-clockwise seen from outside).
+__global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ tri, const int* __restrict__ perm,
+                       int n, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
+                       double* __restrict__ ctr, int* __restrict__ vid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = perm[i];
+    double P[3][3];
+    for (int c = 0; c < 3; ++c) {
+        const int w = tri[3 * t + c];
+        vid[c * n + i] = w;
+        for (int d = 0; d < 3; ++d) {
+            P[c][d] = xyz[3 * (int64_t)w + d];
+            v[(3 * c + d) * n + i] = P[c][d];
+        }
+    }
+    const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    const double e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    area[i] = 0.5 * len;
+    for (int d = 0; d < 3; ++d) {
+        nrm[d * n + i] = cr[d] / len;
+        ctr[d * n + i] = ((P[0][d] + P[1][d]) + P[2][d]) / 3.0;
+    }
+}
+
+void launch_geom(const double* xyz, const int* tri, const int* perm, int n, double* v, double* area, double* nrm,
+                 double* ctr, int* vid, cudaStream_t s) {
+    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, v, area, nrm, ctr, vid);
+}
+
+void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
+                       cudaStream_t s) {
+    int64_t tot = (int64_t)n * NR;
+    k_permute_in<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, ldx, nrhs, NR, perm, n, xp);
+}
+
+void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,
+                        cudaStream_t s) {
+    int64_t tot = (int64_t)n * nrhs;
+    k_permute_out<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(yp, NR, nrhs, iperm, n, y, ldy);
+}
+
+}  // namespace h2

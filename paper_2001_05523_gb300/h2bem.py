@@ -1,0 +1,269 @@
+"""Thin Python binding of libh2bem (the C ABI in include/h2bem.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  There is no CPU fallback; if the compiled library is missing the
+import of a function raises.  Functions keep the C names; torch tensors (CUDA
+or CPU) and numpy arrays are accepted for vectors.  A vector block of nrhs
+right-hand sides is a (nrhs, n) row-major array, i.e. the column-major n x nrhs
+layout with leading dimension n.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libh2bem.so")
+
+H2BEM_OK, H2BEM_ERR_ARG, H2BEM_ERR_MESH, H2BEM_ERR_OOM, H2BEM_ERR_CUDA, H2BEM_ERR_TIMEOUT, H2BEM_ERR_STATE = range(7)
+H2BEM_SLP, H2BEM_DLP = 0, 1
+H2BEM_FP64, H2BEM_MIXED_FP32, H2BEM_MIXED_TF32, H2BEM_MIXED_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": H2BEM_FP64, "mixed_fp32": H2BEM_MIXED_FP32, "mixed_tf32": H2BEM_MIXED_TF32,
+              "mixed_bf16": H2BEM_MIXED_BF16}
+
+EXPORTED = [
+    "h2bem_last_error", "h2bem_mesh_create", "h2bem_mesh_destroy", "h2bem_tree_build", "h2bem_tree_upload",
+    "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
+    "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
+    "h2bem_apply_timed",
+]
+
+
+class H2bemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"h2bem error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nclusters", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("depth", ctypes.c_int64), ("nfar", ctypes.c_int64), ("nnear", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("regular_pairs", ctypes.c_int64),
+                ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("last_apply_ms", ctypes.c_double),
+                ("stage_ms", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["singular_pairs"] = list(self.singular_pairs)
+        d["stage_ms"] = list(self.stage_ms)
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load libh2bem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libh2bem.so not built ({LIB_PATH}); run paper_2001_05523_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "h2bem_last_error": [ctypes.c_char_p, sz],
+            "h2bem_mesh_create": [vp, i64, vp, i64, pp],
+            "h2bem_mesh_destroy": [vp],
+            "h2bem_tree_build": [vp, i32, pp],
+            "h2bem_tree_upload": [vp, i64, vp, vp, vp, vp, vp, pp],
+            "h2bem_tree_info": [vp, vp, vp, vp],
+            "h2bem_tree_export": [vp] * 8,
+            "h2bem_tree_destroy": [vp],
+            "h2bem_blocks": [vp, d, vp, vp, vp, vp, vp, vp],
+            "h2bem_opts_default": [vp],
+            "h2bem_operator_create": [vp, vp, i32, i32, d, vp, pp],
+            "h2bem_operator_destroy": [vp],
+            "h2bem_stats_get": [vp, vp],
+            "h2bem_apply": [vp, vp, i64, i32, vp, i64, vp],
+            "h2bem_apply_transpose": [vp, vp, i64, i32, vp, i64, vp],
+            "h2bem_apply_timed": [vp, vp, i64, i32, vp, i64, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != H2BEM_OK:
+        buf = ctypes.create_string_buffer(512)
+        lib().h2bem_last_error(buf, 512)
+        raise H2bemError(rc, buf.value.decode())
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- C names
+def h2bem_mesh_create(vertices, triangles):
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(triangles, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().h2bem_mesh_create(_np_ptr(v), v.shape[0], _np_ptr(t), t.shape[0], ctypes.byref(h)))
+    return h
+
+
+def h2bem_mesh_destroy(h):
+    _check(lib().h2bem_mesh_destroy(h))
+
+
+def h2bem_tree_build(mesh, leaf_size: int = 32):
+    h = ctypes.c_void_p()
+    _check(lib().h2bem_tree_build(mesh, int(leaf_size), ctypes.byref(h)))
+    return h
+
+
+def h2bem_tree_upload(mesh, perm, begin, end, child0, child1):
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in (perm, begin, end, child0, child1)]
+    h = ctypes.c_void_p()
+    _check(lib().h2bem_tree_upload(mesh, arrs[1].size, *(_np_ptr(a) for a in arrs), ctypes.byref(h)))
+    return h
+
+
+def h2bem_tree_info(tree):
+    nc, nl, dp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().h2bem_tree_info(tree, ctypes.byref(nc), ctypes.byref(nl), ctypes.byref(dp)))
+    return nc.value, nl.value, dp.value
+
+
+def h2bem_tree_export(tree, n: int):
+    nc, _, _ = h2bem_tree_info(tree)
+    out = dict(perm=np.zeros(n, np.int64), begin=np.zeros(nc, np.int64), end=np.zeros(nc, np.int64),
+               child0=np.zeros(nc, np.int64), child1=np.zeros(nc, np.int64), bmin=np.zeros((nc, 3)),
+               bmax=np.zeros((nc, 3)))
+    _check(lib().h2bem_tree_export(tree, *(_np_ptr(out[k]) for k in ("perm", "begin", "end", "child0", "child1",
+                                                                      "bmin", "bmax"))))
+    return out
+
+
+def h2bem_tree_destroy(h):
+    _check(lib().h2bem_tree_destroy(h))
+
+
+def h2bem_blocks(tree, eta: float):
+    nf, nn = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().h2bem_blocks(tree, float(eta), ctypes.byref(nf), ctypes.byref(nn), None, None, None, None))
+    ft, fs = np.zeros(nf.value, np.int64), np.zeros(nf.value, np.int64)
+    nt, ns = np.zeros(nn.value, np.int64), np.zeros(nn.value, np.int64)
+    _check(lib().h2bem_blocks(tree, float(eta), None, None, _np_ptr(ft), _np_ptr(fs), _np_ptr(nt), _np_ptr(ns)))
+    return (ft, fs), (nt, ns)
+
+
+def h2bem_opts_default() -> Opts:
+    o = Opts()
+    _check(lib().h2bem_opts_default(ctypes.byref(o)))
+    return o
+
+
+def h2bem_operator_create(mesh, tree, kernel: int, m: int, eta: float, opts: Opts | None = None):
+    h = ctypes.c_void_p()
+    _check(lib().h2bem_operator_create(mesh, tree, int(kernel), int(m), float(eta),
+                                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)))
+    return h
+
+
+def h2bem_operator_destroy(h):
+    _check(lib().h2bem_operator_destroy(h))
+
+
+def h2bem_stats_get(op) -> dict:
+    s = Stats()
+    _check(lib().h2bem_stats_get(op, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def _vec_args(x, y):
+    """(pointer, ld, nrhs) for (nrhs, n) row-major torch tensors or numpy arrays."""
+    def one(a):
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.ndim != 2:
+                raise ValueError("vectors must be C-contiguous float64 arrays of shape (nrhs, n)")
+            return ctypes.c_void_p(a.ctypes.data), a.shape[1], a.shape[0]
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.dim() != 2:
+            raise ValueError("vectors must be contiguous float64 tensors of shape (nrhs, n)")
+        return ctypes.c_void_p(a.data_ptr()), a.shape[1], a.shape[0]
+    px, lx, rx = one(x)
+    py, ly, ry = one(y)
+    if rx != ry:
+        raise ValueError("x and y must have the same number of right-hand sides")
+    return px, lx, rx, py, ly
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def h2bem_apply(op, x, y, stream=None):
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply(op, px, lx, nr, py, ly, _stream(stream)))
+
+
+def h2bem_apply_transpose(op, x, y, stream=None):
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply_transpose(op, px, lx, nr, py, ly, _stream(stream)))
+
+
+def h2bem_apply_timed(op, x, y, stream=None):
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply_timed(op, px, lx, nr, py, ly, _stream(stream)))
+
+
+# ---------------------------------------------------------------- convenience
+class Operator:
+    """Owns mesh, tree and operator handles for one surface mesh."""
+
+    def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
+                 leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False):
+        self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
+        self.n = int(np.asarray(triangles).shape[0])
+        self.mesh = h2bem_mesh_create(vertices, triangles)
+        self.tree = h2bem_tree_build(self.mesh, leaf_size)
+        o = h2bem_opts_default()
+        o.q_ss = q_ss
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.cache_singular = int(cache_singular)
+        self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
+
+    def close(self):
+        for name, fn in (("op", h2bem_operator_destroy), ("tree", h2bem_tree_destroy), ("mesh", h2bem_mesh_destroy)):
+            h = getattr(self, name, None)
+            if h is not None and h.value:
+                fn(h)
+                setattr(self, name, None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y=None, stream=None, transpose: bool = False):
+        if y is None:
+            y = x.new_empty(x.shape) if not isinstance(x, np.ndarray) else np.empty_like(x)
+        (h2bem_apply_transpose if transpose else h2bem_apply)(self.op, x, y, stream)
+        return y
+
+    def stats(self) -> dict:
+        return h2bem_stats_get(self.op)
