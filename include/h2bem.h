@@ -86,7 +86,8 @@ typedef struct {
     int64_t regular_pairs;     /* of which share no vertex (7 x 7 rule)       */
     int64_t singular_pairs[3]; /* canonical pairs: identical, edge, vertex    */
     int64_t k;                 /* interpolation points per cluster, m^3       */
-    double last_apply_ms;      /* device time of the last apply (0 if none)   */
+    int64_t launches;          /* kernels launched by the last apply          */
+    double last_apply_ms;      /* device time of the last timed apply         */
     double stage_ms[8];        /* per stage of the last timed apply, see      */
                                /* h2bem_apply_timed                            */
 } h2bem_stats;

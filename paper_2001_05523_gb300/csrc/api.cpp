@@ -583,6 +583,7 @@ struct h2bem_op {
     size_t stage_elems = 0;
     cudaEvent_t ev[10] = {};
     double last_ms = 0.0, stage_ms[8] = {0};
+    int64_t launches = 0;
 
     h2::Geom geom() const {
         return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
@@ -719,6 +720,12 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     C.m = m;
     C.k = m * m * m;
     for (int a = 0; a < m; ++a) C.cheb[a] = std::cos((2.0 * a + 1.0) * M_PI / (2.0 * m));
+    for (int a = 0; a < m; ++a) {
+        double pr = 1.0;
+        for (int b = 0; b < m; ++b)
+            if (b != a) pr *= C.cheb[a] - C.cheb[b];
+        C.bary[a] = 1.0 / pr;
+    }
     {
         const double r = std::sqrt(15.0);
         const double a = (6.0 - r) / 21.0, b = (6.0 + r) / 21.0;
@@ -747,7 +754,7 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
 
     // tree arrays, interpolation boxes (half-widths floored at 1e-2 of the largest)
     std::vector<int> iperm(n), permv(n), cb(nc), ce(nc), c0(nc), c1(nc);
-    std::vector<double> box(6 * nc);
+    std::vector<double> box(9 * nc);
     for (int64_t i = 0; i < n; ++i) {
         permv[i] = (int)tree->perm[i];
         iperm[tree->perm[i]] = (int)i;
@@ -763,7 +770,10 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
             h[d] = 0.5 * (tree->bmax[3 * c + d] - tree->bmin[3 * c + d]);
             hmax = std::max(hmax, h[d]);
         }
-        for (int d = 0; d < 3; ++d) box[(3 + d) * nc + c] = std::max(h[d], 1e-2 * hmax);
+        for (int d = 0; d < 3; ++d) {
+            box[(3 + d) * nc + c] = std::max(h[d], 1e-2 * hmax);
+            box[(6 + d) * nc + c] = 1.0 / box[(3 + d) * nc + c];
+        }
         if (c0[c] < 0) op->leaves_h.push_back((int)c);
         else {
             if ((int64_t)op->level_parents.size() <= tree->level[c]) op->level_parents.resize(tree->level[c] + 1);
@@ -874,6 +884,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->singular_pairs[2] = op->sing[2];
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
     st->k = op->k;
+    st->launches = op->launches;
     st->last_apply_ms = op->last_ms;
     for (int i = 0; i < 8; ++i) st->stage_ms[i] = op->stage_ms[i];
     return H2BEM_OK;
@@ -884,12 +895,26 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
 // ===========================================================================
 static int pad_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
 
+// Precision of the farfield vectors: FP64 tier everything double; mixed
+// tier float, except on the side of the double layer's differentiated
+// Lagrange basis W (input side of K, output side of K^T): W has large entries
+// on thin boxes, and an FP32 x-hat (or y-hat) there loses ~1e-6, so that side
+// keeps its basis, transfers and accumulations in double.
+static bool xh_is64(const h2bem_op* op, bool tr) {
+    return op->precision == H2BEM_FP64 || (op->kernel == H2BEM_DLP && !tr);
+}
+static bool yh_is64(const h2bem_op* op, bool tr) {
+    return op->precision == H2BEM_FP64 || (op->kernel == H2BEM_DLP && tr);
+}
+
 static int ensure_workspace(h2bem_op* op, int NR) {
     if (op->ws_NR >= NR) return H2BEM_OK;
-    const size_t fsz = op->precision == H2BEM_FP64 ? sizeof(double) : sizeof(float);
+    const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;  // either direction
+    const size_t xsz = wide ? sizeof(double) : sizeof(float);
+    const size_t ysz = xsz;
     int rc;
     if ((rc = op->xp.alloc(op->n * NR * sizeof(double))) || (rc = op->yp.alloc(op->n * NR * sizeof(double))) ||
-        (rc = op->xh.alloc((size_t)op->nc * op->k * NR * fsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * fsz)))
+        (rc = op->xh.alloc((size_t)op->nc * op->k * NR * xsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * ysz)))
         return rc;
     op->ws_NR = NR;
     return H2BEM_OK;
@@ -902,7 +927,8 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     int rc = ensure_workspace(op, NR);
     if (rc) return rc;
     const bool fp32 = op->precision != H2BEM_FP64;
-    const size_t fsz = fp32 ? sizeof(float) : sizeof(double);
+    const bool xh64 = xh_is64(op, transpose), yh64 = yh_is64(op, transpose);
+    const size_t ysz = yh64 ? sizeof(double) : sizeof(float);
     const h2::Geom g = op->geom();
     const h2::Tree t = op->tree();
     const h2::Consts& c = op->consts;
@@ -917,26 +943,30 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     auto mark = [&](int i) {
         if (timed) cudaEventRecord(op->ev[i], s);
     };
+    int64_t nl = 0;  // kernels launched by this chunk
     mark(0);
     h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
     CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    nl += 1;
     mark(1);
     if (op->nfar > 0) {
-        CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * fsz, s));
-        h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), in_dlp, fp32,
-                                NR, op->xp.as<double>(), op->xh.p, s);
+        CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
+        // the double layer's differentiated basis is evaluated in FP64 in every tier
+        h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), in_dlp,
+                                fp32 && !in_dlp, xh64, NR, op->xp.as<double>(), op->xh.p, s);
+        nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), fp32, NR, op->xh.p, s);
+            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p, s);
         mark(3);
         h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
-                            op->precision, NR, op->xh.p, op->yh.p, s);
+                            op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, op->xh.p, op->yh.p, s);
         mark(4);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
-            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), fp32, NR, op->yh.p, s);
+            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
         mark(5);
         h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), out_dlp,
-                                 fp32, NR, op->yh.p, op->yp.as<double>(), s);
+                                 fp32 && !out_dlp, yh64, NR, op->yh.p, op->yp.as<double>(), s);
     } else {
         for (int i = 2; i <= 5; ++i) mark(i);
     }
@@ -944,10 +974,12 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     // nearfield rows are row leaves (transposed: column leaves)
     h2::launch_near_regular(g, t, c, near.nrows(), near.drows.as<int>(), near.dptr.as<int>(), near.dcol.as<int>(),
                             near_ker, fp32, NR, op->xp.as<double>(), op->yp.as<double>(), s);
+    nl += near.nrows() > 0 ? 1 : 0;
     mark(7);
     for (int ty = 0; ty < 3; ++ty) {
         if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
         const int np = (int)op->sp_count[ty];
+        nl += np > 0 ? 1 : 0;
         if (op->cache_singular)
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
                                 nullptr, nullptr, 0, 2, transpose, NR, op->xp.as<double>(), op->yp.as<double>(),
@@ -959,6 +991,8 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     mark(8);
     h2::launch_permute_out(op->yp.as<double>(), NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+    nl += 1;
+    op->launches += nl;
     mark(9);
     CU(cudaGetLastError());
     return H2BEM_OK;
@@ -987,6 +1021,7 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
         if (xb < ye && yb < xe) return fail(H2BEM_ERR_ARG, "apply: x and y overlap");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    op->launches = 0;
     const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
     if (timed && (!xdev || !ydev)) return fail(H2BEM_ERR_ARG, "apply_timed: x and y must be device memory");
     const double* xd = x;

@@ -33,13 +33,14 @@ struct Tree {
     const int* end;      // [nc] one past the last
     const int* child0;   // [nc] -1 for leaves
     const int* child1;
-    const double* box;   // [6][nc]: centre x,y,z then (floored) half-width x,y,z
+    const double* box;   // [9][nc]: centre x,y,z, (floored) half-width x,y,z, 1/half-width x,y,z
 };
 
 // Quadrature and interpolation constants passed by value.
 struct Consts {
     int m, k;
     double cheb[kMaxM];          // cos((2a+1) pi / (2m)), a = 0..m-1
+    double bary[kMaxM];          // 1 / prod_{b != a} (cheb[a] - cheb[b]) (reference-interval Lagrange weights)
     double ru[7], rv[7], rw[7];  // Radon 7-point rule on the unit simplex, weights sum to 1
     int nb;                      // points of the leaf-basis rule
 };
@@ -64,19 +65,21 @@ void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo
                      const double* tab, int npts, int mode, bool transpose, int NR, const double* xp, double* yp,
                      double* val0, double* val1, cudaStream_t s);
 
-// farfield
+// farfield.  basis32: basis values in FP32 (else FP64); xh64 / yh64: the
+// cluster vectors xh / yh are double (else float).
 void launch_leaf_forward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
-                         const int* leaves, bool dlp_basis, bool fp32, int NR, const double* xp, void* xh,
-                         cudaStream_t s);
+                         const int* leaves, bool dlp_basis, bool basis32, bool xh64, int NR, const double* xp,
+                         void* xh, cudaStream_t s);
 void launch_leaf_backward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
-                          const int* leaves, bool dlp_basis, bool fp32, int NR, const void* yh, double* yp,
-                          cudaStream_t s);
-void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* xh,
+                          const int* leaves, bool dlp_basis, bool basis32, bool yh64, int NR, const void* yh,
+                          double* yp, cudaStream_t s);
+void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,
                    cudaStream_t s);
-void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* yh,
+void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,
                      cudaStream_t s);
-// precision: 0 FP64, 1 FP32 SIMT, 2 TF32 tensor cores, 3 BF16 tensor cores
+// precision: 0 FP64 (xh, yh double), 1 FP32 SIMT arithmetic (xh / yh double
+// if xh64 / yh64, else float)
 void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                     int precision, int NR, const void* xh, void* yh, cudaStream_t s);
+                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s);
 
 }  // namespace h2

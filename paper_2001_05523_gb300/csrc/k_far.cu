@@ -43,82 +43,126 @@ __device__ __forceinline__ double lagrange(const double* z, int m, int a, double
         if (k != a) p *= (y - z[k]) / (z[a] - z[k]);
     return p;
 }
-__device__ __forceinline__ double lagrange_d(const double* z, int m, int a, double y) {
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) {
-        if (k == a) continue;
-        double p = 1.0 / (z[a] - z[k]);
-        for (int l = 0; l < m; ++l)
-            if (l != a && l != k) p *= (y - z[l]) / (z[a] - z[l]);
-        s += p;
-    }
-    return s;
-}
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Leaf transforms.  rule: nb points (u, v, w) on the unit simplex, exact for
-// total degree 3(m-1), weights summing to 1.  One CTA per leaf.
-// Shared: L[p][d][a] (and dL) for the current triangle's points.
+// total degree 3(m-1), weights summing to 1.  One CTA per leaf; the leaf's
+// triangles are processed in chunks of CT.  For every point of a chunk the
+// scaled node differences d_b = (y - z_b) / half of each axis (in FP64, then
+// rounded to TB) and the m Lagrange values L_a = bary[a] prod_{b != a} d_b
+// (and, for the double layer, dL_a/dy = bary[a] sum_{b != a} prod_{c != a,b} d_c / half)
+// are tabulated in shared memory in the basis precision TB; thread nu then
+// forms B[j,nu] = |tau_j| sum_p w_p L_a L_b L_c (or n_j . grad) and accumulates
+// in TA.  No divisions on the device.
+// Shared layout (TB unless noted): LT[CT*nb][3][m], dLT (double layer),
+// wq[CT*nb] = |tau_j| w_p, nr[CT][3]; then TA xs[CT][NR] (forward) or
+// TB prod[CT][k] (backward).
 // ---------------------------------------------------------------------------
-template <typename T, int NR, bool DLPB>
+template <typename TB, bool DLPB>
+__device__ void tabulate_chunk(const Geom& g, const Tree& t, const Consts& c, const double* rule, int cl, int j0,
+                               int cnt, TB* LT, TB* dLT, TB* wq, TB* nr) {
+    const int m = c.m, nb = c.nb, n = g.n;
+    for (int e = threadIdx.x; e < cnt * nb * 3; e += blockDim.x) {
+        const int jp = e / 3, d = e % 3, jl = jp / nb, p = jp % nb;
+        const int j = j0 + jl;
+        const double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
+        const double y = v0 + rule[3 * p] * (v1 - v0) + rule[3 * p + 1] * (v2 - v0);
+        const double ctr = t.box[d * t.nc + cl], half = t.box[(3 + d) * t.nc + cl];
+        const double ihalf = t.box[(6 + d) * t.nc + cl];
+        // (y - z_b) / half with the node z_b = ctr + half * cheb[b]; the
+        // difference is formed in FP64 so each factor keeps full relative accuracy
+        TB diff[kMaxM];
+        for (int b = 0; b < m; ++b) diff[b] = (TB)((y - (ctr + half * c.cheb[b])) * ihalf);
+        for (int a = 0; a < m; ++a) {
+            TB pr = (TB)c.bary[a];
+            for (int b = 0; b < m; ++b)
+                if (b != a) pr *= diff[b];
+            LT[(jp * 3 + d) * m + a] = pr;
+            if (DLPB) {
+                TB sd = 0;
+                for (int b = 0; b < m; ++b) {
+                    if (b == a) continue;
+                    TB q = 1;
+                    for (int cc = 0; cc < m; ++cc)
+                        if (cc != a && cc != b) q *= diff[cc];
+                    sd += q;
+                }
+                dLT[(jp * 3 + d) * m + a] = sd * (TB)c.bary[a] * (TB)ihalf;
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < cnt * nb; e += blockDim.x)
+        wq[e] = (TB)(g.area[j0 + e / nb] * rule[3 * (e % nb) + 2]);
+    if (DLPB)
+        for (int e = threadIdx.x; e < cnt * 3; e += blockDim.x) nr[e] = (TB)g.nrm[(e % 3) * n + j0 + e / 3];
+}
+
+// B[j, nu] for one triangle of the chunk from the tabulated values
+template <typename TB, bool DLPB>
+__device__ __forceinline__ TB basis_value(const TB* LT, const TB* dLT, const TB* wq, const TB* nr, int jl, int nb,
+                                          int m, int ia, int ib, int ic) {
+    TB sum = 0;
+    const TB* Lj = LT + jl * nb * 3 * m;
+    const TB* wj = wq + jl * nb;
+    if (DLPB) {
+        const TB* dLj = dLT + jl * nb * 3 * m;
+        const TB nx = nr[3 * jl], ny = nr[3 * jl + 1], nz = nr[3 * jl + 2];
+        for (int p = 0; p < nb; ++p) {
+            const TB* L = Lj + p * 3 * m;
+            const TB* dL = dLj + p * 3 * m;
+            const TB lx = L[ia], ly = L[m + ib], lz = L[2 * m + ic];
+            sum += wj[p] * (nx * dL[ia] * ly * lz + ny * lx * dL[m + ib] * lz + nz * lx * ly * dL[2 * m + ic]);
+        }
+    } else {
+        for (int p = 0; p < nb; ++p) {
+            const TB* L = Lj + p * 3 * m;
+            sum += wj[p] * (L[ia] * L[m + ib] * L[2 * m + ic]);
+        }
+    }
+    return sum;
+}
+
+template <typename TB>
+__host__ __device__ constexpr size_t chunk_tab_elems(int ct, int nb, int m, bool dlp) {
+    return (size_t)ct * nb * 3 * m * (dlp ? 2 : 1) + (size_t)ct * nb + (size_t)ct * 3;
+}
+
+template <typename TB, typename TA, int NR, bool DLPB>
 __global__ void __launch_bounds__(256) k_leaf_forward(Geom g, Tree t, Consts c, const double* __restrict__ rule,
-                                                      const int* __restrict__ leaves, const double* __restrict__ xp,
-                                                      T* __restrict__ xh) {
-    __shared__ double z[3 * kMaxM];
-    __shared__ T L[kMaxBasisPts * 3 * kMaxM];
-    __shared__ T dL[DLPB ? kMaxBasisPts * 3 * kMaxM : 1];
+                                                      const int* __restrict__ leaves, int CT,
+                                                      const double* __restrict__ xp, TA* __restrict__ xh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = c.m, k = c.k, nb = c.nb;
+    TB* LT = reinterpret_cast<TB*>(smem_raw);
+    TB* dLT = LT + (size_t)CT * nb * 3 * m;
+    TB* wq = dLT + (DLPB ? (size_t)CT * nb * 3 * m : 0);
+    TB* nr = wq + (size_t)CT * nb;
+    TA* xs = reinterpret_cast<TA*>(smem_raw + ((chunk_tab_elems<TB>(CT, nb, m, DLPB) * sizeof(TB) + 15) / 16) * 16);
     const int s = leaves[blockIdx.x];
     const int b = t.begin[s], R = t.end[s] - b;
-    const int m = c.m, k = c.k, nb = c.nb, n = g.n;
-    cluster_nodes(t, c, s, z);
-    constexpr int kPer = (kMaxK + 63) / 64;  // nu per thread at blockDim >= 64
-    T acc[kPer][NR];
+    constexpr int kPer = (kMaxK + 63) / 64;
+    TA acc[kPer][NR];
 #pragma unroll
     for (int q = 0; q < kPer; ++q)
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[q][r] = 0;
-    for (int jl = 0; jl < R; ++jl) {
-        const int j = b + jl;
+    for (int j0 = 0; j0 < R; j0 += CT) {
+        const int cnt = min(CT, R - j0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nb * 3 * m; e += blockDim.x) {
-            const int p = e / (3 * m), d = (e / m) % 3, a = e % m;
-            const double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
-            const double y = v0 + rule[3 * p] * (v1 - v0) + rule[3 * p + 1] * (v2 - v0);
-            L[e] = (T)lagrange(z + d * m, m, a, y);
-            if (DLPB) dL[e] = (T)lagrange_d(z + d * m, m, a, y);
-        }
+        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr);
+        for (int e = threadIdx.x; e < cnt * NR; e += blockDim.x) xs[e] = (TA)xp[(int64_t)(b + j0) * NR + e];
         __syncthreads();
-        const double aj = g.area[j];
-        T nx = 0, ny = 0, nz = 0;
-        if (DLPB) {
-            nx = (T)g.nrm[j];
-            ny = (T)g.nrm[n + j];
-            nz = (T)g.nrm[2 * n + j];
-        }
-        T xj[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) xj[r] = (T)xp[(int64_t)j * NR + r];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int nu = threadIdx.x + q * blockDim.x;
             if (nu >= k) break;
             const int ia = nu % m, ib = (nu / m) % m, ic = nu / (m * m);
-            T sum = 0;
-            for (int p = 0; p < nb; ++p) {
-                const T* Lp = L + p * 3 * m;
-                const T w = (T)rule[3 * p + 2];
-                if (DLPB) {
-                    const T* dLp = dL + p * 3 * m;
-                    const T lx = Lp[ia], ly = Lp[m + ib], lz = Lp[2 * m + ic];
-                    sum += w * (nx * dLp[ia] * ly * lz + ny * lx * dLp[m + ib] * lz + nz * lx * ly * dLp[2 * m + ic]);
-                } else {
-                    sum += w * Lp[ia] * Lp[m + ib] * Lp[2 * m + ic];
-                }
-            }
-            sum *= (T)aj;
+            for (int jl = 0; jl < cnt; ++jl) {
+                const TA w = (TA)basis_value<TB, DLPB>(LT, dLT, wq, nr, jl, nb, m, ia, ib, ic);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[q][r] += sum * xj[r];
+                for (int r = 0; r < NR; ++r) acc[q][r] += w * xs[jl * NR + r];
+            }
         }
     }
 #pragma unroll
@@ -130,79 +174,36 @@ __global__ void __launch_bounds__(256) k_leaf_forward(Geom g, Tree t, Consts c, 
     }
 }
 
-template <typename T, int NR, bool DLPB>
+template <typename TB, typename TA, int NR, bool DLPB>
 __global__ void __launch_bounds__(256) k_leaf_backward(Geom g, Tree t, Consts c, const double* __restrict__ rule,
-                                                       const int* __restrict__ leaves, const T* __restrict__ yh,
-                                                       double* __restrict__ yp) {
-    __shared__ double z[3 * kMaxM];
-    __shared__ T L[kMaxBasisPts * 3 * kMaxM];
-    __shared__ T dL[DLPB ? kMaxBasisPts * 3 * kMaxM : 1];
-    __shared__ T red[8][NR];
+                                                       const int* __restrict__ leaves, int CT,
+                                                       const TA* __restrict__ yh, double* __restrict__ yp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = c.m, k = c.k, nb = c.nb;
+    TB* LT = reinterpret_cast<TB*>(smem_raw);
+    TB* dLT = LT + (size_t)CT * nb * 3 * m;
+    TB* wq = dLT + (DLPB ? (size_t)CT * nb * 3 * m : 0);
+    TB* nr = wq + (size_t)CT * nb;
+    TB* prod = reinterpret_cast<TB*>(smem_raw + ((chunk_tab_elems<TB>(CT, nb, m, DLPB) * sizeof(TB) + 15) / 16) * 16);
+    TA* ys = reinterpret_cast<TA*>(prod + (((size_t)CT * k * sizeof(TB) + 15) / 16) * 16 / sizeof(TB));
     const int s = leaves[blockIdx.x];
     const int b = t.begin[s], R = t.end[s] - b;
-    const int m = c.m, k = c.k, nb = c.nb, n = g.n;
-    cluster_nodes(t, c, s, z);
-    constexpr int kPer = (kMaxK + 63) / 64;
-    T yv[kPer][NR];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const int nu = threadIdx.x + q * blockDim.x;
-#pragma unroll
-        for (int r = 0; r < NR; ++r) yv[q][r] = nu < k ? yh[((int64_t)s * k + nu) * NR + r] : (T)0;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int il = 0; il < R; ++il) {
-        const int i = b + il;
+    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) ys[e] = yh[(int64_t)s * k * NR + e];
+    for (int j0 = 0; j0 < R; j0 += CT) {
+        const int cnt = min(CT, R - j0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nb * 3 * m; e += blockDim.x) {
-            const int p = e / (3 * m), d = (e / m) % 3, a = e % m;
-            const double v0 = g.v[d * n + i], v1 = g.v[(3 + d) * n + i], v2 = g.v[(6 + d) * n + i];
-            const double y = v0 + rule[3 * p] * (v1 - v0) + rule[3 * p + 1] * (v2 - v0);
-            L[e] = (T)lagrange(z + d * m, m, a, y);
-            if (DLPB) dL[e] = (T)lagrange_d(z + d * m, m, a, y);
+        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt * k; e += blockDim.x) {
+            const int jl = e / k, nu = e % k;
+            prod[e] = basis_value<TB, DLPB>(LT, dLT, wq, nr, jl, nb, m, nu % m, (nu / m) % m, nu / (m * m));
         }
         __syncthreads();
-        T nx = 0, ny = 0, nz = 0;
-        if (DLPB) {
-            nx = (T)g.nrm[i];
-            ny = (T)g.nrm[n + i];
-            nz = (T)g.nrm[2 * n + i];
-        }
-        T part[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) part[r] = 0;
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int nu = threadIdx.x + q * blockDim.x;
-            if (nu >= k) break;
-            const int ia = nu % m, ib = (nu / m) % m, ic = nu / (m * m);
-            T sum = 0;
-            for (int p = 0; p < nb; ++p) {
-                const T* Lp = L + p * 3 * m;
-                const T w = (T)rule[3 * p + 2];
-                if (DLPB) {
-                    const T* dLp = dL + p * 3 * m;
-                    const T lx = Lp[ia], ly = Lp[m + ib], lz = Lp[2 * m + ic];
-                    sum += w * (nx * dLp[ia] * ly * lz + ny * lx * dLp[m + ib] * lz + nz * lx * ly * dLp[2 * m + ic]);
-                } else {
-                    sum += w * Lp[ia] * Lp[m + ib] * Lp[2 * m + ic];
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < NR; ++r) part[r] += sum * yv[q][r];
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            T v = part[r];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][r] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < NR) {
-            T v = 0;
-            for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
-            yp[(int64_t)i * NR + threadIdx.x] += g.area[i] * (double)v;
+        for (int e = threadIdx.x; e < cnt * NR; e += blockDim.x) {
+            const int jl = e / NR, r = e % NR;
+            TA v = 0;
+            for (int nu = 0; nu < k; ++nu) v += (TA)prod[jl * k + nu] * ys[nu * NR + r];
+            yp[(int64_t)(b + j0 + jl) * NR + r] += (double)v;
         }
     }
 }
@@ -309,15 +310,17 @@ __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* _
 // Coupling, SIMT: one CTA per row cluster, S_ts generated on the fly from
 // per-axis squared node differences.  Thread (nu, slice) sums over the mu of
 // its slice; slices are reduced in shared memory at the end.
+// TS: precision of the S entries; TA: accumulation (and staged x-hat);
+// TX / TY: storage of x-hat / y-hat.
 // ---------------------------------------------------------------------------
-template <typename T, int NR>
+template <typename TS, typename TA, typename TX, typename TY, int NR>
 __global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const int* __restrict__ rows,
                                                        const int* __restrict__ ptr, const int* __restrict__ col,
-                                                       const T* __restrict__ xh, T* __restrict__ yh) {
-    extern __shared__ unsigned char smem_raw[];
-    T* xs = reinterpret_cast<T*>(smem_raw);  // [k][NR], reused for the reduction [256][NR]
+                                                       const TX* __restrict__ xh, TY* __restrict__ yh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* xs = reinterpret_cast<TA*>(smem_raw);  // [k][NR], reused for the reduction [256][NR]
     __shared__ double zt[3 * kMaxM], zs[3 * kMaxM];
-    __shared__ T D2[3 * kMaxM * kMaxM];
+    __shared__ TS D2[3 * kMaxM * kMaxM];
     const int row = rows[blockIdx.x];
     const int m = c.m, k = c.k;
     const int nslice = blockDim.x / k;
@@ -325,28 +328,28 @@ __global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const i
     const bool active = sl < nslice;
     const int ia = nu % m, ib = (nu / m) % m, ic = nu / (m * m);
     cluster_nodes(t, c, row, zt);
-    T acc[NR];
+    TA acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0;
     for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
         const int s = col[b];
         __syncthreads();
         cluster_nodes(t, c, s, zs);
-        for (int e = threadIdx.x; e < k * NR; e += blockDim.x) xs[e] = xh[(int64_t)s * k * NR + e];
+        for (int e = threadIdx.x; e < k * NR; e += blockDim.x) xs[e] = (TA)xh[(int64_t)s * k * NR + e];
         __syncthreads();
         for (int e = threadIdx.x; e < 3 * m * m; e += blockDim.x) {
             const int d = e / (m * m), a = (e / m) % m, a2 = e % m;
             const double df = zt[d * m + a] - zs[d * m + a2];
-            D2[e] = (T)(df * df);
+            D2[e] = (TS)(df * df);
         }
         __syncthreads();
         if (active) {
-            const T* Dx = D2 + ia * m;
-            const T* Dy = D2 + m * m + ib * m;
-            const T* Dz = D2 + 2 * m * m + ic * m;
+            const TS* Dx = D2 + ia * m;
+            const TS* Dy = D2 + m * m + ib * m;
+            const TS* Dz = D2 + 2 * m * m + ic * m;
             for (int mu = sl; mu < k; mu += nslice) {
                 const int ja = mu % m, jb = (mu / m) % m, jc = mu / (m * m);
-                const T sv = rsq<T>(Dx[ja] + Dy[jb] + Dz[jc]);
+                const TA sv = (TA)rsq<TS>(Dx[ja] + Dy[jb] + Dz[jc]);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[r] += sv * xs[mu * NR + r];
             }
@@ -354,13 +357,13 @@ __global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const i
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) xs[threadIdx.x * NR + r] = active ? acc[r] : (T)0;
+    for (int r = 0; r < NR; ++r) xs[threadIdx.x * NR + r] = active ? acc[r] : (TA)0;
     __syncthreads();
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
         const int v = e / NR, r = e % NR;
-        T s = 0;
+        TA s = 0;
         for (int q = 0; q < nslice; ++q) s += xs[(q * k + v) * NR + r];
-        yh[(int64_t)row * k * NR + e] = s * (T)kInv4Pi;
+        yh[(int64_t)row * k * NR + e] = (TY)(s * (TA)kInv4Pi);
     }
 }
 
@@ -374,19 +377,6 @@ static int far_threads(int k) {
     return th;
 }
 
-template <typename T, int NR>
-static void leaf_fwd(bool dlpb, const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl,
-                     const int* leaves, const double* xp, void* xh, cudaStream_t s) {
-    if (dlpb) k_leaf_forward<T, NR, true><<<nl, far_threads(c.k), 0, s>>>(g, t, c, rule, leaves, xp, (T*)xh);
-    else k_leaf_forward<T, NR, false><<<nl, far_threads(c.k), 0, s>>>(g, t, c, rule, leaves, xp, (T*)xh);
-}
-template <typename T, int NR>
-static void leaf_bwd(bool dlpb, const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl,
-                     const int* leaves, const void* yh, double* yp, cudaStream_t s) {
-    if (dlpb) k_leaf_backward<T, NR, true><<<nl, far_threads(c.k), 0, s>>>(g, t, c, rule, leaves, (const T*)yh, yp);
-    else k_leaf_backward<T, NR, false><<<nl, far_threads(c.k), 0, s>>>(g, t, c, rule, leaves, (const T*)yh, yp);
-}
-
 #define H2_NR_SWITCH(NR, CALL)          \
     switch (NR) {                       \
         case 1: { constexpr int R_ = 1; CALL; } break;  \
@@ -395,20 +385,66 @@ static void leaf_bwd(bool dlpb, const Geom& g, const Tree& t, const Consts& c, c
         default: { constexpr int R_ = 16; CALL; } break; \
     }
 
+// chunk size: tabulated values of one chunk within about 40 KB of shared memory
+static int leaf_chunk(const Consts& c, size_t tb, bool dlp) {
+    const size_t per = ((size_t)c.nb * 3 * c.m * (dlp ? 2 : 1) + c.nb + 3) * tb;
+    int ct = (int)(40960 / per);
+    return ct < 1 ? 1 : ct > kMaxLeaf ? kMaxLeaf : ct;
+}
+
+template <typename TB, typename TA, int NR, bool DLPB>
+static void leaf_fwd(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl, const int* leaves,
+                     const double* xp, void* xh, cudaStream_t s) {
+    const int ct = leaf_chunk(c, sizeof(TB), DLPB);
+    const size_t smem = ((chunk_tab_elems<TB>(ct, c.nb, c.m, DLPB) * sizeof(TB) + 15) / 16) * 16 + (size_t)ct * NR * sizeof(TA);
+    cudaFuncSetAttribute(k_leaf_forward<TB, TA, NR, DLPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_leaf_forward<TB, TA, NR, DLPB><<<nl, far_threads(c.k), smem, s>>>(g, t, c, rule, leaves, ct, xp, (TA*)xh);
+}
+
+template <typename TB, typename TA, int NR, bool DLPB>
+static void leaf_bwd(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl, const int* leaves,
+                     const void* yh, double* yp, cudaStream_t s) {
+    const int ct = leaf_chunk(c, sizeof(TB), DLPB);
+    const size_t smem = ((chunk_tab_elems<TB>(ct, c.nb, c.m, DLPB) * sizeof(TB) + 15) / 16) * 16 +
+                        (((size_t)ct * c.k * sizeof(TB) + 15) / 16) * 16 + (size_t)c.k * NR * sizeof(TA);
+    cudaFuncSetAttribute(k_leaf_backward<TB, TA, NR, DLPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_leaf_backward<TB, TA, NR, DLPB><<<nl, far_threads(c.k), smem, s>>>(g, t, c, rule, leaves, ct, (const TA*)yh, yp);
+}
+
+template <int NR, bool DLPB>
+static void leaf_fwd_prec(bool basis32, bool xh64, const Geom& g, const Tree& t, const Consts& c, const double* rule,
+                          int nl, const int* leaves, const double* xp, void* xh, cudaStream_t s) {
+    // TB = basis precision, TA = precision of the accumulation and of xh
+    if (!basis32 && xh64) leaf_fwd<double, double, NR, DLPB>(g, t, c, rule, nl, leaves, xp, xh, s);
+    else if (!basis32) leaf_fwd<double, float, NR, DLPB>(g, t, c, rule, nl, leaves, xp, xh, s);
+    else if (xh64) leaf_fwd<float, double, NR, DLPB>(g, t, c, rule, nl, leaves, xp, xh, s);
+    else leaf_fwd<float, float, NR, DLPB>(g, t, c, rule, nl, leaves, xp, xh, s);
+}
+
+template <int NR, bool DLPB>
+static void leaf_bwd_prec(bool basis32, bool yh64, const Geom& g, const Tree& t, const Consts& c, const double* rule,
+                          int nl, const int* leaves, const void* yh, double* yp, cudaStream_t s) {
+    // TB = basis precision, TA = precision of yh and of the accumulation
+    if (!basis32 && yh64) leaf_bwd<double, double, NR, DLPB>(g, t, c, rule, nl, leaves, yh, yp, s);
+    else if (!basis32) leaf_bwd<double, float, NR, DLPB>(g, t, c, rule, nl, leaves, yh, yp, s);
+    else if (yh64) leaf_bwd<float, double, NR, DLPB>(g, t, c, rule, nl, leaves, yh, yp, s);
+    else leaf_bwd<float, float, NR, DLPB>(g, t, c, rule, nl, leaves, yh, yp, s);
+}
+
 void launch_leaf_forward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
-                         const int* leaves, bool dlp_basis, bool fp32, int NR, const double* xp, void* xh,
-                         cudaStream_t s) {
+                         const int* leaves, bool dlp_basis, bool basis32, bool xh64, int NR, const double* xp,
+                         void* xh, cudaStream_t s) {
     if (nleaves <= 0) return;
-    if (fp32) { H2_NR_SWITCH(NR, (leaf_fwd<float, R_>(dlp_basis, g, t, c, rule, nleaves, leaves, xp, xh, s))) }
-    else { H2_NR_SWITCH(NR, (leaf_fwd<double, R_>(dlp_basis, g, t, c, rule, nleaves, leaves, xp, xh, s))) }
+    if (dlp_basis) { H2_NR_SWITCH(NR, (leaf_fwd_prec<R_, true>(basis32, xh64, g, t, c, rule, nleaves, leaves, xp, xh, s))) }
+    else { H2_NR_SWITCH(NR, (leaf_fwd_prec<R_, false>(basis32, xh64, g, t, c, rule, nleaves, leaves, xp, xh, s))) }
 }
 
 void launch_leaf_backward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
-                          const int* leaves, bool dlp_basis, bool fp32, int NR, const void* yh, double* yp,
-                          cudaStream_t s) {
+                          const int* leaves, bool dlp_basis, bool basis32, bool yh64, int NR, const void* yh,
+                          double* yp, cudaStream_t s) {
     if (nleaves <= 0) return;
-    if (fp32) { H2_NR_SWITCH(NR, (leaf_bwd<float, R_>(dlp_basis, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
-    else { H2_NR_SWITCH(NR, (leaf_bwd<double, R_>(dlp_basis, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
+    if (dlp_basis) { H2_NR_SWITCH(NR, (leaf_bwd_prec<R_, true>(basis32, yh64, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
+    else { H2_NR_SWITCH(NR, (leaf_bwd_prec<R_, false>(basis32, yh64, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
 }
 
 template <typename T, int NR, bool UP>
@@ -423,33 +459,40 @@ static void updown(const Tree& t, const Consts& c, int np, const int* parents, v
     }
 }
 
-void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* xh,
+void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,
                    cudaStream_t s) {
     if (nparents <= 0) return;
-    if (fp32) { H2_NR_SWITCH(NR, (updown<float, R_, true>(t, c, nparents, parents, xh, s))) }
+    if (!xh64) { H2_NR_SWITCH(NR, (updown<float, R_, true>(t, c, nparents, parents, xh, s))) }
     else { H2_NR_SWITCH(NR, (updown<double, R_, true>(t, c, nparents, parents, xh, s))) }
 }
 
-void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool fp32, int NR, void* yh,
+void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,
                      cudaStream_t s) {
     if (nparents <= 0) return;
-    if (fp32) { H2_NR_SWITCH(NR, (updown<float, R_, false>(t, c, nparents, parents, yh, s))) }
+    if (!yh64) { H2_NR_SWITCH(NR, (updown<float, R_, false>(t, c, nparents, parents, yh, s))) }
     else { H2_NR_SWITCH(NR, (updown<double, R_, false>(t, c, nparents, parents, yh, s))) }
 }
 
-template <typename T, int NR>
+template <typename TS, typename TA, typename TX, typename TY, int NR>
 static void coupling_simt(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
                           const void* xh, void* yh, cudaStream_t s) {
-    const size_t smem = sizeof(T) * (size_t)(256 > c.k ? 256 : c.k) * NR;
-    cudaFuncSetAttribute(k_coupling_simt<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coupling_simt<T, NR><<<nrows, 256, smem, s>>>(t, c, rows, ptr, col, (const T*)xh, (T*)yh);
+    const size_t smem = sizeof(TA) * (size_t)(256 > c.k ? 256 : c.k) * NR;
+    cudaFuncSetAttribute(k_coupling_simt<TS, TA, TX, TY, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coupling_simt<TS, TA, TX, TY, NR><<<nrows, 256, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh, (TY*)yh);
 }
 
 void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                     int precision, int NR, const void* xh, void* yh, cudaStream_t s) {
+                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s) {
     if (nrows <= 0) return;
-    if (precision == 0) { H2_NR_SWITCH(NR, (coupling_simt<double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s))) }
-    else { H2_NR_SWITCH(NR, (coupling_simt<float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s))) }
+    if (precision == 0) {
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else if (xh64) {  // input side in double: FP32 entries and sums
+        H2_NR_SWITCH(NR, (coupling_simt<float, float, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else if (yh64) {  // output side in double: FP32 entries, FP64 sums
+        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else {
+        H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    }
 }
 
 }  // namespace h2

@@ -11,6 +11,13 @@
 // and each pair's centroid difference is formed in FP64 before rounding, so
 // x_p - y_q keeps ~1e-7 relative accuracy even for touching neighbours; the
 // 49-point sum runs in FP32, the entry times x is accumulated in FP64.
+//
+// Double layer: y_q lies in the plane of tau_j, so (x_p - y_q).n_j equals the
+// height (x_p - c_j).n_j of x_p above that plane, which depends on p only.  It
+// is formed once per point and pair, with the centroid part in FP64; this
+// avoids the cancellation of (x_p - y_q).n_j for nearly coplanar neighbours.
+// The transposed double layer uses the height (y_q - c_i).n_i of y_q above the
+// plane of the row triangle in the same way.
 #include <type_traits>
 
 #include "internal.h"
@@ -129,21 +136,36 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
                 Dy = (T)(ci[1] - sctr[kMaxLeaf + jl]);
                 Dz = (T)(ci[2] - sctr[2 * kMaxLeaf + jl]);
             }
-            T nx = 0, ny = 0, nz = 0;
+            // double layer: heights above the plane carrying the normal
+            T hp[7];
             if (KER == DLP) {
-                nx = (T)snrm[jl];
-                ny = (T)snrm[kMaxLeaf + jl];
-                nz = (T)snrm[2 * kMaxLeaf + jl];
-            } else if (KER == DLP_T) {
-                nx = (T)-rn[0];
-                ny = (T)-rn[1];
-                nz = (T)-rn[2];
+                const double nx = snrm[jl], ny = snrm[kMaxLeaf + jl], nz = snrm[2 * kMaxLeaf + jl];
+                const double cx = sctr[jl], cy = sctr[kMaxLeaf + jl], cz = sctr[2 * kMaxLeaf + jl];
+                if (F32) {
+                    const T H0 = (T)((ci[0] - cx) * nx + (ci[1] - cy) * ny + (ci[2] - cz) * nz);
+#pragma unroll
+                    for (int p = 0; p < 7; ++p) hp[p] = H0 + (px[p] * (T)nx + py[p] * (T)ny + pz[p] * (T)nz);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 7; ++p)
+                        hp[p] = ((double)px[p] - cx) * nx + ((double)py[p] - cy) * ny + ((double)pz[p] - cz) * nz;
+                }
             }
             T sum = 0;
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
                 const T ex = sq[jl * 7 + q], ey = sq[kMaxLeaf * 7 + jl * 7 + q], ez = sq[2 * kMaxLeaf * 7 + jl * 7 + q];
                 const T yx = F32 ? Dx - ex : ex, yy = F32 ? Dy - ey : ey, yz = F32 ? Dz - ez : ez;
+                T hq = 0;
+                if (KER == DLP_T) {
+                    if (F32) {
+                        const T H0 = (T)((sctr[jl] - ci[0]) * rn[0] + (sctr[kMaxLeaf + jl] - ci[1]) * rn[1] +
+                                         (sctr[2 * kMaxLeaf + jl] - ci[2]) * rn[2]);
+                        hq = H0 + (ex * (T)rn[0] + ey * (T)rn[1] + ez * (T)rn[2]);
+                    } else {
+                        hq = ((double)ex - ci[0]) * rn[0] + ((double)ey - ci[1]) * rn[1] + ((double)ez - ci[2]) * rn[2];
+                    }
+                }
                 T sp = 0;
 #pragma unroll
                 for (int p = 0; p < 7; ++p) {
@@ -156,8 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
                     if (KER == SLP) {
                         sp += (T)c.rw[p] * ri;
                     } else {
-                        const T dn = dx * nx + dy * ny + dz * nz;
-                        sp += (T)c.rw[p] * dn * (ri * ri * ri);
+                        const T h = KER == DLP ? hp[p] : hq;
+                        sp += (T)c.rw[p] * h * (ri * ri * ri);
                     }
                 }
                 sum += (T)c.rw[q] * sp;

@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nclusters", ctypes.c_int64), ("nleaves", ctypes.c_int64),
                 ("depth", ctypes.c_int64), ("nfar", ctypes.c_int64), ("nnear", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("regular_pairs", ctypes.c_int64),
-                ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("last_apply_ms", ctypes.c_double),
+                ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("last_apply_ms", ctypes.c_double),
                 ("stage_ms", ctypes.c_double * 8)]
 
     def as_dict(self):

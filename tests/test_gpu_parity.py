@@ -183,3 +183,21 @@ def test_sphere32k_fp64_vs_oracle_h2_and_dense_rows(H, orc, kernel):
     rows = np.random.default_rng(1).choice(mesh.nt, 48, replace=False)
     d = orc.dense_rows(kernel, mesh, rows, x)
     assert rel(y[:, rows], d) < (1e-3 if kernel == 0 else 1e-2)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_mixed_fp32_transpose_matches_oracle(H, orc, kernel):
+    mesh = I.jitter(I.ellipsoid(12), 0.01, 6)
+    x = I.rhs(mesh.nt, 3, seed=12)
+    y = gpu_apply(H, mesh, x, kernel=kernel, precision="mixed_fp32", transpose=True)
+    ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=True)
+    assert rel(y, ref) < TOL["mixed_fp32"]
+
+
+def test_mixed_fp32_m5_ellipsoid_16rhs(H, orc):
+    """Ellipsoid (1, 0.5, 0.25), m = 5 (k = 125), 16 right-hand sides."""
+    mesh = I.ellipsoid(20)
+    x = I.rhs(mesh.nt, 16, seed=13)
+    y = gpu_apply(H, mesh, x, kernel=0, m=5, precision="mixed_fp32")
+    ref = orc.H2(mesh, 0, m=5).matvec(x)
+    assert rel(y, ref) < TOL["mixed_fp32"]
