@@ -170,6 +170,31 @@ int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, 
  * [5] leaf backward, [6] nearfield regular, [7] nearfield singular. */
 int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
 
+/* Allocation-free y = A x (the paper has no counterpart: this is a service
+ * for callers of this library).  Same arguments and result as h2bem_apply,
+ * for callers that cannot let the library allocate device memory when they
+ * apply the operator: h2bem_apply allocates its work vectors with cudaMalloc
+ * on its first call, which fails or stalls for a caller whose device memory
+ * is all held by its own pool allocator, or who must not trigger the device
+ * synchronisation a cudaMalloc/cudaFree may imply.  This call allocates
+ * nothing: its work vectors live in a fixed 64 MiB array inside the library,
+ * present on every GPU that loads the library until the process exits.
+ *   - x and y must be device memory (no host staging); they must not overlap.
+ *   - The work space needed is 2 n NRp 8 + 2 nclusters k NRp e bytes, NRp
+ *     being min(nrhs,16) rounded up to 1, 4, 8 or 16 and e = 8 for the FP64
+ *     tier or the double layer, else 4; an operator that needs more than
+ *     64 MiB is rejected with H2BEM_ERR_ARG (use h2bem_apply).
+ *   - The first call on a device looks up the array's device address (once,
+ *     with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array and the work vectors it holds are
+ *     overwritten by every call: calls that may overlap on the GPU (on
+ *     different streams, or from different threads without ordering) race
+ *     and give wrong results.  Calls on one stream are ordered and safe.
+ *   - Enqueued on `stream`; returns once the work is enqueued.
+ * Errors: ARG (null, nrhs, ld, host pointers, work space too large), CUDA. */
+int h2bem_apply_noalloc(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

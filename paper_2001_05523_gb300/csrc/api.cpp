@@ -1082,3 +1082,76 @@ extern "C" int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int
                                  void* stream) {
     return apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, true);
 }
+
+// ===========================================================================
+// apply into caller-provided work vectors (used by the allocation-free entry
+// point in noalloc.cu; the sequence of kernels is the one of apply_chunk)
+// ===========================================================================
+namespace h2 {
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int64_t op_size(const h2bem_op* op) { return op->n; }
+
+// Bytes of work vectors one chunk of NR (padded) right-hand sides needs: the
+// tree-ordered x and y, and the cluster vectors x-hat and y-hat.
+size_t work_bytes(const h2bem_op* op, int NR) {
+    const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;
+    const size_t e = wide ? sizeof(double) : sizeof(float);
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    return 2 * up((size_t)op->n * NR * sizeof(double)) + 2 * up((size_t)op->nc * op->k * NR * e);
+}
+
+int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
+                    unsigned char* work) {
+    const int NR = pad_nr(nrhs);
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;
+    const size_t vb = up((size_t)op->n * NR * sizeof(double));
+    const size_t hb = up((size_t)op->nc * op->k * NR * (wide ? sizeof(double) : sizeof(float)));
+    double* xp = reinterpret_cast<double*>(work);
+    double* yp = reinterpret_cast<double*>(work + vb);
+    void* xh = work + 2 * vb;
+    void* yh = work + 2 * vb + hb;
+    const bool fp32 = op->precision != H2BEM_FP64;
+    const bool xh64 = xh_is64(op, false), yh64 = yh_is64(op, false);
+    const h2::Geom g = op->geom();
+    const h2::Tree t = op->tree();
+    const h2::Consts& c = op->consts;
+    const int n = (int)op->n;
+    const bool dlp = op->kernel == H2BEM_DLP;
+    const int near_ker = dlp ? h2::DLP : h2::SLP;
+    launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, xp, s);
+    CU(cudaMemsetAsync(yp, 0, vb, s));
+    if (op->nfar > 0) {
+        CU(cudaMemsetAsync(yh, 0, hb, s));
+        launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), dlp,
+                            fp32 && !dlp, xh64, NR, xp, xh, s);
+        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
+            launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
+        launch_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(), op->far.dcol.as<int>(),
+                        op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, s);
+        for (size_t L = 0; L < op->level_parents.size(); ++L)
+            launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
+        launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
+                             fp32, yh64, NR, yh, yp, s);
+    }
+    launch_near_regular(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+                        op->near.dcol.as<int>(), near_ker, fp32, NR, xp, yp, s);
+    for (int ty = 0; ty < 3; ++ty) {
+        if (ty == 0 && dlp) continue;
+        const int np = (int)op->sp_count[ty];
+        if (op->cache_singular)
+            launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(), nullptr,
+                            nullptr, 0, 2, false, NR, xp, yp, op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
+        else
+            launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
+                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, false, NR, xp,
+                            yp, nullptr, nullptr, s);
+    }
+    launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+}  // namespace h2

@@ -83,3 +83,13 @@ void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows,
                      int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s);
 
 }  // namespace h2
+
+struct h2bem_op;
+namespace h2 {
+// Used by the allocation-free entry point (noalloc.cu).
+int set_error(int code, const char* msg);
+int64_t op_size(const h2bem_op* op);
+size_t work_bytes(const h2bem_op* op, int NR);
+int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
+                    unsigned char* work);
+}  // namespace h2

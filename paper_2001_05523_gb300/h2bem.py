@@ -27,7 +27,7 @@ EXPORTED = [
     "h2bem_last_error", "h2bem_mesh_create", "h2bem_mesh_destroy", "h2bem_tree_build", "h2bem_tree_upload",
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
-    "h2bem_apply_timed",
+    "h2bem_apply_timed", "h2bem_apply_noalloc",
 ]
 
 
@@ -86,6 +86,7 @@ def lib():
             "h2bem_apply": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_apply_transpose": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_apply_timed": [vp, vp, i64, i32, vp, i64, vp],
+            "h2bem_apply_noalloc": [vp, vp, i64, i32, vp, i64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -224,6 +225,12 @@ def h2bem_apply(op, x, y, stream=None):
 def h2bem_apply_transpose(op, x, y, stream=None):
     px, lx, nr, py, ly = _vec_args(x, y)
     _check(lib().h2bem_apply_transpose(op, px, lx, nr, py, ly, _stream(stream)))
+
+
+def h2bem_apply_noalloc(op, x, y, stream=None):
+    """y = A x without any allocation by the library (device buffers only)."""
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply_noalloc(op, px, lx, nr, py, ly, _stream(stream)))
 
 
 def h2bem_apply_timed(op, x, y, stream=None):
