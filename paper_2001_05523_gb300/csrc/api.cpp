@@ -443,8 +443,8 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
 
 // Sauter-Schwab point tables after the exact integration of the monomial
 // factors (see k_sing.cu).  Rows: identical [aa, 2ab, bb, W]; edge [6 Gram
-// monomials, alpha, beta, gamma, W_g, W_dg]; vertex [10 Gram monomials,
-// alpha..delta, W_g, W_dg].
+// monomials, alpha, beta, gamma, W_g, W_dg]; vertex: the 1-D Gauss rule
+// [x_k, w_k] (the kernel forms the factorised triple sum).
 void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vector<double>& tv) {
     std::vector<double> x, w;
     gauss_legendre(q, x, w);
@@ -477,19 +477,8 @@ void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vec
                 te.insert(te.end(), {al * al, be * be, ga * ga, 2 * al * be, 2 * al * ga, 2 * be * ga, al, be, ga,
                                      ww * f / 6.0, ww * f / 2.0});
             }
-    // vertex: (alpha, beta, gamma, delta) for vectors (P1-P0, P2-P1, Q1-Q0, Q2-Q1)
-    for (int r = 0; r < 2; ++r)
-        for (int i = 0; i < q; ++i)
-            for (int k = 0; k < q; ++k)
-                for (int l = 0; l < q; ++l) {
-                    const double e1 = x[i], e2 = x[k], e3 = x[l], ww = w[i] * w[k] * w[l];
-                    double al, be, ga, de;
-                    if (r == 0) { al = 1.0; be = e1; ga = -e2; de = -e2 * e3; }
-                    else { al = e2; be = e2 * e3; ga = -1.0; de = -e1; }
-                    tv.insert(tv.end(), {al * al, be * be, ga * ga, de * de, 2 * al * be, 2 * al * ga, 2 * al * de,
-                                         2 * be * ga, 2 * be * de, 2 * ga * de, al, be, ga, de, ww * e2 / 3.0,
-                                         ww * e2 / 2.0});
-                }
+    // vertex: the 1-D rule itself (x_k, w_k); the kernel forms the factorised sums
+    for (int k = 0; k < q; ++k) tv.insert(tv.end(), {x[k], w[k]});
 }
 
 }  // namespace
@@ -721,6 +710,10 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     C.k = m * m * m;
     for (int a = 0; a < m; ++a) C.cheb[a] = std::cos((2.0 * a + 1.0) * M_PI / (2.0 * m));
     for (int a = 0; a < m; ++a) {
+        C.cheb_hi[a] = (float)C.cheb[a];
+        C.cheb_lo[a] = (float)(C.cheb[a] - (double)C.cheb_hi[a]);
+    }
+    for (int a = 0; a < m; ++a) {
         double pr = 1.0;
         for (int b = 0; b < m; ++b)
             if (b != a) pr *= C.cheb[a] - C.cheb[b];
@@ -803,7 +796,7 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     singular_pairs(*mesh, slo, shi, scode);
     std::vector<double> tabs[3];
     ss_tables(op->q_ss, tabs[0], tabs[1], tabs[2]);
-    const int widths[3] = {4, 11, 16};
+    const int widths[3] = {4, 11, 2};
 
     int rc;
     if ((rc = upload(op->xyz, mesh->xyz)) || (rc = upload(op->tri, std::vector<int>(mesh->tri.begin(), mesh->tri.end()))) ||
@@ -899,7 +892,8 @@ static int pad_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 4 ? 4 : nrhs <= 8 ?
 // tier float, except on the side of the double layer's differentiated
 // Lagrange basis W (input side of K, output side of K^T): W has large entries
 // on thin boxes, and an FP32 x-hat (or y-hat) there loses ~1e-6, so that side
-// keeps its basis, transfers and accumulations in double.
+// keeps its basis, transfers and accumulations in double (for K x also the
+// coupling entries, whose rounding the cancelling x-hat amplifies).
 static bool xh_is64(const h2bem_op* op, bool tr) {
     return op->precision == H2BEM_FP64 || (op->kernel == H2BEM_DLP && !tr);
 }

@@ -41,6 +41,8 @@ struct Consts {
     int m, k;
     double cheb[kMaxM];          // cos((2a+1) pi / (2m)), a = 0..m-1
     double bary[kMaxM];          // 1 / prod_{b != a} (cheb[a] - cheb[b]) (reference-interval Lagrange weights)
+    float cheb_hi[kMaxM];        // float split of cheb: cheb = hi + lo
+    float cheb_lo[kMaxM];
     double ru[7], rv[7], rw[7];  // Radon 7-point rule on the unit simplex, weights sum to 1
     int nb;                      // points of the leaf-basis rule
 };

@@ -1,0 +1,142 @@
+// Coupling stage of the H^2 product (section 2, eq. (vsw); section 3,
+// S_ts[nu,mu] = g(xi_{t,nu}, xi_{s,mu}) of the tensor Chebyshev interpolant):
+//   yh_t[nu] = sum_{(t,s) farfield} sum_mu S_ts[nu,mu] xh_s[mu],
+// with S_ts generated on the fly; SIMT kernels in FP64 or FP32.
+#include "dmath.cuh"
+#include "internal.h"
+
+namespace h2 {
+
+namespace {
+constexpr double kInv4Pi = 0.07957747154594766788;
+
+template <typename T>
+__device__ __forceinline__ T rsq(T x);
+template <>
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt_nr(x); }
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+
+// nodes of cluster cl along every axis: z[d*m + a]
+__device__ __forceinline__ void cluster_nodes(const Tree& t, const Consts& c, int cl, double* z) {
+    for (int e = threadIdx.x; e < 3 * c.m; e += blockDim.x) {
+        const int d = e / c.m, a = e % c.m;
+        z[e] = t.box[d * t.nc + cl] + t.box[(3 + d) * t.nc + cl] * c.cheb[a];
+    }
+}
+}  // namespace
+
+#define H2_NR_SWITCH(NR, CALL)                         \
+    switch (NR) {                                      \
+        case 1: { constexpr int R_ = 1; CALL; } break;  \
+        case 4: { constexpr int R_ = 4; CALL; } break;  \
+        case 8: { constexpr int R_ = 8; CALL; } break;  \
+        default: { constexpr int R_ = 16; CALL; } break; \
+    }
+
+// ---------------------------------------------------------------------------
+// Coupling, SIMT: one CTA per row cluster, S_ts generated on the fly from
+// per-axis squared node differences.  Thread (nu, slice) sums over the mu of
+// its slice; slices are reduced in shared memory at the end.
+// TS: precision of the S entries; TA: accumulation (and staged x-hat);
+// TX / TY: storage of x-hat / y-hat.
+// ---------------------------------------------------------------------------
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
+__global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const int* __restrict__ rows,
+                                                       const int* __restrict__ ptr, const int* __restrict__ col,
+                                                       const TX* __restrict__ xh, TY* __restrict__ yh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* xs = reinterpret_cast<TA*>(smem_raw);  // [k][NR], reused for the reduction [256][NR]
+    __shared__ double zt[3 * kMaxM], zs[3 * kMaxM];
+    __shared__ TS D2[3 * kMaxM * kMaxM];       // D2[d][a][a2] = (z_t,d[a] - z_s,d[a2])^2
+    const int row = rows[blockIdx.x];
+    const int m = M > 0 ? M : c.m, k = m * m * m;
+    const int nslice = blockDim.x / k;
+    const int nu = threadIdx.x % k, sl = threadIdx.x / k;
+    const bool active = sl < nslice;
+    const int ia = nu % m, ib = (nu / m) % m, ic = nu / (m * m);
+    cluster_nodes(t, c, row, zt);
+    TA acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0;
+    for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
+        const int s = col[b];
+        __syncthreads();
+        cluster_nodes(t, c, s, zs);
+        for (int e = threadIdx.x; e < k * NR; e += blockDim.x) xs[e] = (TA)xh[(int64_t)s * k * NR + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < 3 * m * m; e += blockDim.x) {
+            const int d = e / (m * m), a = (e / m) % m, a2 = e % m;
+            const double df = zt[d * m + a] - zs[d * m + a2];
+            D2[e] = (TS)(df * df);
+        }
+        __syncthreads();
+        if (active) {
+            const TS* Dx = D2 + ia * m;
+            const TS* Dy = D2 + m * m + ib * m;
+            const TS* Dz = D2 + 2 * m * m + ic * m;
+            TS dxr[M > 0 ? M : kMaxM];
+#pragma unroll
+            for (int ja = 0; ja < (M > 0 ? M : kMaxM); ++ja) dxr[ja] = (M > 0 || ja < m) ? Dx[ja] : (TS)0;
+            for (int jc = sl; jc < m; jc += nslice) {
+                const TS szc = Dz[jc];
+#pragma unroll(M > 0 ? M : 1)
+                for (int jb = 0; jb < m; ++jb) {
+                    const TS sbc = Dy[jb] + szc;
+                    const TA* xrow = xs + ((jc * m + jb) * m) * NR;
+#pragma unroll
+                    for (int ja = 0; ja < (M > 0 ? M : kMaxM); ++ja) {
+                        if (M == 0 && ja >= m) break;
+                        const TA sv = (TA)rsq<TS>(dxr[ja] + sbc);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) acc[r] += sv * xrow[ja * NR + r];
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) xs[threadIdx.x * NR + r] = active ? acc[r] : (TA)0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
+        const int v = e / NR, r = e % NR;
+        TA s = 0;
+        for (int q = 0; q < nslice; ++q) s += xs[(q * k + v) * NR + r];
+        yh[(int64_t)row * k * NR + e] = (TY)(s * (TA)kInv4Pi);
+    }
+}
+
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
+static void coupling_m(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                       const void* xh, void* yh, cudaStream_t s) {
+    const size_t smem = sizeof(TA) * (size_t)(256 > c.k ? 256 : c.k) * NR;
+    cudaFuncSetAttribute(k_coupling_simt<TS, TA, TX, TY, NR, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coupling_simt<TS, TA, TX, TY, NR, M><<<nrows, 256, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh, (TY*)yh);
+}
+
+template <typename TS, typename TA, typename TX, typename TY, int NR>
+static void coupling_simt(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                          const void* xh, void* yh, cudaStream_t s) {
+    if (c.m == 4) coupling_m<TS, TA, TX, TY, NR, 4>(t, c, nrows, rows, ptr, col, xh, yh, s);
+    else if (c.m == 5) coupling_m<TS, TA, TX, TY, NR, 5>(t, c, nrows, rows, ptr, col, xh, yh, s);
+    else coupling_m<TS, TA, TX, TY, NR, 0>(t, c, nrows, rows, ptr, col, xh, yh, s);
+}
+
+void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s) {
+    if (nrows <= 0) return;
+    if (precision == 0) {
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else if (xh64) {
+        // input side in double (double layer, K x): the differentiated basis makes
+        // S x-hat cancel strongly, so S and its sums are FP64; y-hat is stored float
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else if (yh64) {  // output side in double (double layer, K^T x): FP32 entries, FP64 sums
+        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    } else {
+        H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+    }
+}
+
+}  // namespace h2

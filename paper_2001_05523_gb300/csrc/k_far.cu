@@ -15,6 +15,7 @@
 // three m x m matrices.  Vectors xh, yh: [cluster][nu][r] with NR columns.
 #include <type_traits>
 
+#include "dmath.cuh"
 #include "internal.h"
 
 namespace h2 {
@@ -25,7 +26,7 @@ constexpr double kInv4Pi = 0.07957747154594766788;
 template <typename T>
 __device__ __forceinline__ T rsq(T x);
 template <>
-__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt_nr(x); }
 template <>
 __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 
@@ -49,8 +50,8 @@ __device__ __forceinline__ double lagrange(const double* z, int m, int a, double
 // Leaf transforms.  rule: nb points (u, v, w) on the unit simplex, exact for
 // total degree 3(m-1), weights summing to 1.  One CTA per leaf; the leaf's
 // triangles are processed in chunks of CT.  For every point of a chunk the
-// scaled node differences d_b = (y - z_b) / half of each axis (in FP64, then
-// rounded to TB) and the m Lagrange values L_a = bary[a] prod_{b != a} d_b
+// scaled node differences d_b = (y - z_b) / half of each axis (exact form
+// described in tabulate_chunk) and the m Lagrange values L_a = bary[a] prod_{b != a} d_b
 // (and, for the double layer, dL_a/dy = bary[a] sum_{b != a} prod_{c != a,b} d_c / half)
 // are tabulated in shared memory in the basis precision TB; thread nu then
 // forms B[j,nu] = |tau_j| sum_p w_p L_a L_b L_c (or n_j . grad) and accumulates
@@ -61,19 +62,33 @@ __device__ __forceinline__ double lagrange(const double* z, int m, int a, double
 // ---------------------------------------------------------------------------
 template <typename TB, bool DLPB>
 __device__ void tabulate_chunk(const Geom& g, const Tree& t, const Consts& c, const double* rule, int cl, int j0,
-                               int cnt, TB* LT, TB* dLT, TB* wq, TB* nr) {
+                               int cnt, TB* LT, TB* dLT, TB* wq, TB* nr, double* sABC) {
     const int m = c.m, nb = c.nb, n = g.n;
+    // per triangle and axis, in reference units of the cluster box:
+    // A = (v0 - ctr) / half, B = (v1 - v0) / half, C = (v2 - v0) / half
+    for (int e = threadIdx.x; e < cnt * 3; e += blockDim.x) {
+        const int jl = e / 3, d = e % 3, j = j0 + jl;
+        const double ih = t.box[(6 + d) * t.nc + cl];
+        const double v0 = g.v[d * n + j];
+        sABC[3 * e] = (v0 - t.box[d * t.nc + cl]) * ih;
+        sABC[3 * e + 1] = (g.v[(3 + d) * n + j] - v0) * ih;
+        sABC[3 * e + 2] = (g.v[(6 + d) * n + j] - v0) * ih;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < cnt * nb * 3; e += blockDim.x) {
         const int jp = e / 3, d = e % 3, jl = jp / nb, p = jp % nb;
-        const int j = j0 + jl;
-        const double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
-        const double y = v0 + rule[3 * p] * (v1 - v0) + rule[3 * p + 1] * (v2 - v0);
-        const double ctr = t.box[d * t.nc + cl], half = t.box[(3 + d) * t.nc + cl];
-        const double ihalf = t.box[(6 + d) * t.nc + cl];
-        // (y - z_b) / half with the node z_b = ctr + half * cheb[b]; the
-        // difference is formed in FP64 so each factor keeps full relative accuracy
+        const double* abc = sABC + 3 * (jl * 3 + d);
+        const double tr = fma(rule[3 * p + 1], abc[2], fma(rule[3 * p], abc[1], abc[0]));
+        // node differences d_b = t - cheb[b]: FP64 tier directly; FP32 tier as
+        // (t_hi - cheb_hi) + (t_lo - cheb_lo) with float splits of both terms,
+        // the first difference exact near the node (Sterbenz)
         TB diff[kMaxM];
-        for (int b = 0; b < m; ++b) diff[b] = (TB)((y - (ctr + half * c.cheb[b])) * ihalf);
+        if (sizeof(TB) == sizeof(double)) {
+            for (int b = 0; b < m; ++b) diff[b] = (TB)(tr - c.cheb[b]);
+        } else {
+            const float th = (float)tr, tl = (float)(tr - (double)th);
+            for (int b = 0; b < m; ++b) diff[b] = (TB)((th - c.cheb_hi[b]) + (tl - c.cheb_lo[b]));
+        }
         for (int a = 0; a < m; ++a) {
             TB pr = (TB)c.bary[a];
             for (int b = 0; b < m; ++b)
@@ -83,12 +98,12 @@ __device__ void tabulate_chunk(const Geom& g, const Tree& t, const Consts& c, co
                 TB sd = 0;
                 for (int b = 0; b < m; ++b) {
                     if (b == a) continue;
-                    TB q = 1;
+                    TB qv = 1;
                     for (int cc = 0; cc < m; ++cc)
-                        if (cc != a && cc != b) q *= diff[cc];
-                    sd += q;
+                        if (cc != a && cc != b) qv *= diff[cc];
+                    sd += qv;
                 }
-                dLT[(jp * 3 + d) * m + a] = sd * (TB)c.bary[a] * (TB)ihalf;
+                dLT[(jp * 3 + d) * m + a] = sd * (TB)c.bary[a] * (TB)t.box[(6 + d) * t.nc + cl];
             }
         }
     }
@@ -139,6 +154,7 @@ __global__ void __launch_bounds__(256) k_leaf_forward(Geom g, Tree t, Consts c, 
     TB* wq = dLT + (DLPB ? (size_t)CT * nb * 3 * m : 0);
     TB* nr = wq + (size_t)CT * nb;
     TA* xs = reinterpret_cast<TA*>(smem_raw + ((chunk_tab_elems<TB>(CT, nb, m, DLPB) * sizeof(TB) + 15) / 16) * 16);
+    __shared__ double sABC[kMaxLeaf * 9];
     const int s = leaves[blockIdx.x];
     const int b = t.begin[s], R = t.end[s] - b;
     constexpr int kPer = (kMaxK + 63) / 64;
@@ -150,7 +166,7 @@ __global__ void __launch_bounds__(256) k_leaf_forward(Geom g, Tree t, Consts c, 
     for (int j0 = 0; j0 < R; j0 += CT) {
         const int cnt = min(CT, R - j0);
         __syncthreads();
-        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr);
+        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr, sABC);
         for (int e = threadIdx.x; e < cnt * NR; e += blockDim.x) xs[e] = (TA)xp[(int64_t)(b + j0) * NR + e];
         __syncthreads();
 #pragma unroll
@@ -186,13 +202,14 @@ __global__ void __launch_bounds__(256) k_leaf_backward(Geom g, Tree t, Consts c,
     TB* nr = wq + (size_t)CT * nb;
     TB* prod = reinterpret_cast<TB*>(smem_raw + ((chunk_tab_elems<TB>(CT, nb, m, DLPB) * sizeof(TB) + 15) / 16) * 16);
     TA* ys = reinterpret_cast<TA*>(prod + (((size_t)CT * k * sizeof(TB) + 15) / 16) * 16 / sizeof(TB));
+    __shared__ double sABC[kMaxLeaf * 9];
     const int s = leaves[blockIdx.x];
     const int b = t.begin[s], R = t.end[s] - b;
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) ys[e] = yh[(int64_t)s * k * NR + e];
     for (int j0 = 0; j0 < R; j0 += CT) {
         const int cnt = min(CT, R - j0);
         __syncthreads();
-        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr);
+        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr, sABC);
         __syncthreads();
         for (int e = threadIdx.x; e < cnt * k; e += blockDim.x) {
             const int jl = e / k, nu = e % k;
@@ -307,67 +324,6 @@ __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* _
 }
 
 // ---------------------------------------------------------------------------
-// Coupling, SIMT: one CTA per row cluster, S_ts generated on the fly from
-// per-axis squared node differences.  Thread (nu, slice) sums over the mu of
-// its slice; slices are reduced in shared memory at the end.
-// TS: precision of the S entries; TA: accumulation (and staged x-hat);
-// TX / TY: storage of x-hat / y-hat.
-// ---------------------------------------------------------------------------
-template <typename TS, typename TA, typename TX, typename TY, int NR>
-__global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const int* __restrict__ rows,
-                                                       const int* __restrict__ ptr, const int* __restrict__ col,
-                                                       const TX* __restrict__ xh, TY* __restrict__ yh) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* xs = reinterpret_cast<TA*>(smem_raw);  // [k][NR], reused for the reduction [256][NR]
-    __shared__ double zt[3 * kMaxM], zs[3 * kMaxM];
-    __shared__ TS D2[3 * kMaxM * kMaxM];
-    const int row = rows[blockIdx.x];
-    const int m = c.m, k = c.k;
-    const int nslice = blockDim.x / k;
-    const int nu = threadIdx.x % k, sl = threadIdx.x / k;
-    const bool active = sl < nslice;
-    const int ia = nu % m, ib = (nu / m) % m, ic = nu / (m * m);
-    cluster_nodes(t, c, row, zt);
-    TA acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0;
-    for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
-        const int s = col[b];
-        __syncthreads();
-        cluster_nodes(t, c, s, zs);
-        for (int e = threadIdx.x; e < k * NR; e += blockDim.x) xs[e] = (TA)xh[(int64_t)s * k * NR + e];
-        __syncthreads();
-        for (int e = threadIdx.x; e < 3 * m * m; e += blockDim.x) {
-            const int d = e / (m * m), a = (e / m) % m, a2 = e % m;
-            const double df = zt[d * m + a] - zs[d * m + a2];
-            D2[e] = (TS)(df * df);
-        }
-        __syncthreads();
-        if (active) {
-            const TS* Dx = D2 + ia * m;
-            const TS* Dy = D2 + m * m + ib * m;
-            const TS* Dz = D2 + 2 * m * m + ic * m;
-            for (int mu = sl; mu < k; mu += nslice) {
-                const int ja = mu % m, jb = (mu / m) % m, jc = mu / (m * m);
-                const TA sv = (TA)rsq<TS>(Dx[ja] + Dy[jb] + Dz[jc]);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] += sv * xs[mu * NR + r];
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < NR; ++r) xs[threadIdx.x * NR + r] = active ? acc[r] : (TA)0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
-        const int v = e / NR, r = e % NR;
-        TA s = 0;
-        for (int q = 0; q < nslice; ++q) s += xs[(q * k + v) * NR + r];
-        yh[(int64_t)row * k * NR + e] = (TY)(s * (TA)kInv4Pi);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static int far_threads(int k) {
@@ -471,28 +427,6 @@ void launch_downward(const Tree& t, const Consts& c, int nparents, const int* pa
     if (nparents <= 0) return;
     if (!yh64) { H2_NR_SWITCH(NR, (updown<float, R_, false>(t, c, nparents, parents, yh, s))) }
     else { H2_NR_SWITCH(NR, (updown<double, R_, false>(t, c, nparents, parents, yh, s))) }
-}
-
-template <typename TS, typename TA, typename TX, typename TY, int NR>
-static void coupling_simt(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                          const void* xh, void* yh, cudaStream_t s) {
-    const size_t smem = sizeof(TA) * (size_t)(256 > c.k ? 256 : c.k) * NR;
-    cudaFuncSetAttribute(k_coupling_simt<TS, TA, TX, TY, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coupling_simt<TS, TA, TX, TY, NR><<<nrows, 256, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh, (TY*)yh);
-}
-
-void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s) {
-    if (nrows <= 0) return;
-    if (precision == 0) {
-        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
-    } else if (xh64) {  // input side in double: FP32 entries and sums
-        H2_NR_SWITCH(NR, (coupling_simt<float, float, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
-    } else if (yh64) {  // output side in double: FP32 entries, FP64 sums
-        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
-    } else {
-        H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
-    }
 }
 
 }  // namespace h2

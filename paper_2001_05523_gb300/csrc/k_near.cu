@@ -10,7 +10,8 @@
 // FP32 variant: points are stored as offsets from their triangle's centroid
 // and each pair's centroid difference is formed in FP64 before rounding, so
 // x_p - y_q keeps ~1e-7 relative accuracy even for touching neighbours; the
-// 49-point sum runs in FP32, the entry times x is accumulated in FP64.
+// 49-point sum, the entry and the thread's row sums run in FP32; the
+// partial row sums of a CTA are combined in FP64.
 //
 // Double layer: y_q lies in the plane of tau_j, so (x_p - y_q).n_j equals the
 // height (x_p - c_j).n_j of x_p above that plane, which depends on p only.  It
@@ -20,6 +21,7 @@
 // plane of the row triangle in the same way.
 #include <type_traits>
 
+#include "dmath.cuh"
 #include "internal.h"
 
 namespace h2 {
@@ -32,11 +34,26 @@ constexpr int kSbuf = 4096;  // doubles: >= staging area and >= kThreads * 16
 template <typename T>
 __device__ __forceinline__ T rsq(T x);
 template <>
-__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt_nr(x); }
 template <>
 __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 }  // namespace
 
+// FP32 tier: no FP64 work per single-layer pair.  Centroids are kept as
+// float pairs hi + lo (hi = fl(c), lo = fl(c - hi)); c_i - c_j is formed as
+// (hi_i - hi_j) + (lo_i - lo_j), where the first difference is exact for
+// nearby points (Sterbenz) and the result keeps ~1e-7 relative accuracy.
+// Entries and row sums run in FP32 per thread; the slices of a row are
+// reduced in FP64.  The double layer forms the plane height of the row
+// centroid and the edge projections in FP64 once per pair (see below).
+//
+// Double-layer heights: with x_p = c_i + (u_p - 1/3) E1 + (v_p - 1/3) E2
+// (E1, E2 the edge vectors of tau_i from its first corner),
+//   (x_p - y_q) . n_j = (c_i - c_j) . n_j + (u_p - 1/3) E1 . n_j + (v_p - 1/3) E2 . n_j.
+// For nearly coplanar neighbours every term is small against |E|, so the
+// three dot products are formed in FP64 (a rounded FP32 normal alone would
+// tilt the plane by 6e-8 and spoil heights of size |c_i - c_j|^2 curvature);
+// only their combination per point runs in FP32.
 template <int NR, int KER, bool F32>
 __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Consts c, const int* __restrict__ rows,
                                                            const int* __restrict__ ptr, const int* __restrict__ col,
@@ -44,12 +61,15 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
     using T = typename std::conditional<F32, float, double>::type;
     __shared__ double sbuf[kSbuf];
     __shared__ int svid[3 * kMaxLeaf];
-    T* sq = reinterpret_cast<T*>(sbuf);                      // [3][kMaxLeaf * 7]
-    constexpr int kQ = 3 * kMaxLeaf * 7 * sizeof(T) / sizeof(double);
-    double* sctr = sbuf + kQ;                                // [3][kMaxLeaf]
-    double* sarea = sctr + 3 * kMaxLeaf;                     // [kMaxLeaf]
-    double* snrm = sarea + kMaxLeaf;                         // [3][kMaxLeaf]
-    double* sx = snrm + 3 * kMaxLeaf;                        // [kMaxLeaf][NR]
+    __shared__ double splane[kMaxLeaf];                    // c_j . n_j (double layer)
+    __shared__ double sn64[KER == SLP ? 1 : 3 * kMaxLeaf];   // n_j in FP64 (double layer)
+    __shared__ double sedge[KER == DLP_T ? 6 * kMaxLeaf : 1];  // E1_j, E2_j in FP64 (transposed double layer)
+    T* sq = reinterpret_cast<T*>(sbuf);                    // [3][kMaxLeaf*7]: F32 y_q - c_j, F64 y_q
+    T* sch = sq + 3 * kMaxLeaf * 7;                        // [3][kMaxLeaf] centroid hi (F32) or centroid (F64)
+    T* scl = sch + 3 * kMaxLeaf;                           // [3][kMaxLeaf] centroid lo (F32)
+    T* sarea = scl + 3 * kMaxLeaf;                         // [kMaxLeaf]
+    T* snrm = sarea + kMaxLeaf;                            // [3][kMaxLeaf]
+    T* sx = snrm + 3 * kMaxLeaf;                           // [kMaxLeaf][NR]
 
     const int row = rows[blockIdx.x];
     const int rb = t.begin[row], R = t.end[row] - rb;
@@ -61,7 +81,8 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
 
     // row triangle i = rb + il: quadrature points (absolute or centroid offsets)
     T px[7], py[7], pz[7];
-    double ci[3] = {0, 0, 0}, rn[3] = {0, 0, 0}, ai = 0;
+    double ci[3] = {0, 0, 0}, rn[3] = {0, 0, 0}, rplane = 0.0, E1[3] = {0, 0, 0}, E2[3] = {0, 0, 0};
+    T chi[3] = {0, 0, 0}, clo[3] = {0, 0, 0}, ai = 0;
     int vi[3] = {-1, -1, -1};
     if (active) {
         const int i = rb + il;
@@ -73,27 +94,29 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
             ci[d] = g.ctr[d * n + i];
             rn[d] = g.nrm[d * n + i];
             vi[d] = g.vid[d * n + i];
+            chi[d] = (T)ci[d];
+            clo[d] = (T)(ci[d] - (double)chi[d]);
         }
-        ai = g.area[i];
+        rplane = ci[0] * rn[0] + ci[1] * rn[1] + ci[2] * rn[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            E1[d] = V[3 + d] - V[d];
+            E2[d] = V[6 + d] - V[d];
+        }
+        ai = (T)g.area[i];
 #pragma unroll
         for (int p = 0; p < 7; ++p) {
-            double x0 = V[0] + c.ru[p] * (V[3] - V[0]) + c.rv[p] * (V[6] - V[0]);
-            double x1 = V[1] + c.ru[p] * (V[4] - V[1]) + c.rv[p] * (V[7] - V[1]);
-            double x2 = V[2] + c.ru[p] * (V[5] - V[2]) + c.rv[p] * (V[8] - V[2]);
-            if (F32) {
-                px[p] = (T)(x0 - ci[0]);
-                py[p] = (T)(x1 - ci[1]);
-                pz[p] = (T)(x2 - ci[2]);
-            } else {
-                px[p] = (T)x0;
-                py[p] = (T)x1;
-                pz[p] = (T)x2;
-            }
+            const double x0 = V[0] + c.ru[p] * (V[3] - V[0]) + c.rv[p] * (V[6] - V[0]);
+            const double x1 = V[1] + c.ru[p] * (V[4] - V[1]) + c.rv[p] * (V[7] - V[1]);
+            const double x2 = V[2] + c.ru[p] * (V[5] - V[2]) + c.rv[p] * (V[8] - V[2]);
+            px[p] = (T)(F32 ? x0 - ci[0] : x0);
+            py[p] = (T)(F32 ? x1 - ci[1] : x1);
+            pz[p] = (T)(F32 ? x2 - ci[2] : x2);
         }
     }
-    double acc[NR];
+    T acc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    for (int r = 0; r < NR; ++r) acc[r] = 0;
 
     for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
         const int s = col[b];
@@ -101,26 +124,37 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
         __syncthreads();
         for (int e = tid; e < C * 7; e += kThreads) {
             const int j = cb + e / 7, q = e % 7;
-            double y[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
-                y[d] = v0 + c.ru[q] * (v1 - v0) + c.rv[q] * (v2 - v0);
-                if (F32) y[d] -= g.ctr[d * n + j];
-                sq[d * (kMaxLeaf * 7) + e] = (T)y[d];
+                const double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
+                double y = v0 + c.ru[q] * (v1 - v0) + c.rv[q] * (v2 - v0);
+                if (F32) y -= g.ctr[d * n + j];
+                sq[d * (kMaxLeaf * 7) + e] = (T)y;
             }
         }
         for (int e = tid; e < C; e += kThreads) {
             const int j = cb + e;
-            sarea[e] = g.area[j];
+            sarea[e] = (T)g.area[j];
+            double pl = 0.0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                sctr[d * kMaxLeaf + e] = g.ctr[d * n + j];
-                snrm[d * kMaxLeaf + e] = g.nrm[d * n + j];
+                const double cd = g.ctr[d * n + j], nd = g.nrm[d * n + j];
+                const T h = (T)cd;
+                sch[d * kMaxLeaf + e] = h;
+                scl[d * kMaxLeaf + e] = (T)(cd - (double)h);
+                snrm[d * kMaxLeaf + e] = (T)nd;
                 svid[d * kMaxLeaf + e] = g.vid[d * n + j];
+                if (KER != SLP) sn64[d * kMaxLeaf + e] = nd;
+                if (KER == DLP_T) {
+                    const double w0 = g.v[d * n + j];
+                    sedge[d * kMaxLeaf + e] = g.v[(3 + d) * n + j] - w0;
+                    sedge[(3 + d) * kMaxLeaf + e] = g.v[(6 + d) * n + j] - w0;
+                }
+                pl += cd * nd;
             }
+            splane[e] = pl;
         }
-        for (int e = tid; e < C * NR; e += kThreads) sx[e] = xp[(int64_t)cb * NR + e];
+        for (int e = tid; e < C * NR; e += kThreads) sx[e] = (T)xp[(int64_t)cb * NR + e];
         __syncthreads();
         if (!active) continue;
         for (int jl = kk; jl < C; jl += K) {
@@ -130,26 +164,39 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
 #pragma unroll
                 for (int bb = 0; bb < 3; ++bb) sing |= (vi[a] == svid[bb * kMaxLeaf + jl]);
             if (sing) continue;
+            // F32: D = c_i - c_j from the hi/lo splits
             T Dx = 0, Dy = 0, Dz = 0;
             if (F32) {
-                Dx = (T)(ci[0] - sctr[jl]);
-                Dy = (T)(ci[1] - sctr[kMaxLeaf + jl]);
-                Dz = (T)(ci[2] - sctr[2 * kMaxLeaf + jl]);
+                Dx = (chi[0] - sch[jl]) + (clo[0] - scl[jl]);
+                Dy = (chi[1] - sch[kMaxLeaf + jl]) + (clo[1] - scl[kMaxLeaf + jl]);
+                Dz = (chi[2] - sch[2 * kMaxLeaf + jl]) + (clo[2] - scl[2 * kMaxLeaf + jl]);
             }
-            // double layer: heights above the plane carrying the normal
+            // double layer: heights above the plane that carries the normal
             T hp[7];
             if (KER == DLP) {
-                const double nx = snrm[jl], ny = snrm[kMaxLeaf + jl], nz = snrm[2 * kMaxLeaf + jl];
-                const double cx = sctr[jl], cy = sctr[kMaxLeaf + jl], cz = sctr[2 * kMaxLeaf + jl];
+                const double nx = sn64[jl], ny = sn64[kMaxLeaf + jl], nz = sn64[2 * kMaxLeaf + jl];
                 if (F32) {
-                    const T H0 = (T)((ci[0] - cx) * nx + (ci[1] - cy) * ny + (ci[2] - cz) * nz);
-#pragma unroll
-                    for (int p = 0; p < 7; ++p) hp[p] = H0 + (px[p] * (T)nx + py[p] * (T)ny + pz[p] * (T)nz);
-                } else {
+                    const T H0 = (T)(ci[0] * nx + ci[1] * ny + ci[2] * nz - splane[jl]);
+                    const T e1 = (T)(E1[0] * nx + E1[1] * ny + E1[2] * nz);
+                    const T e2 = (T)(E2[0] * nx + E2[1] * ny + E2[2] * nz);
 #pragma unroll
                     for (int p = 0; p < 7; ++p)
-                        hp[p] = ((double)px[p] - cx) * nx + ((double)py[p] - cy) * ny + ((double)pz[p] - cz) * nz;
+                        hp[p] = H0 + (T)(c.ru[p] - 1.0 / 3.0) * e1 + (T)(c.rv[p] - 1.0 / 3.0) * e2;
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 7; ++p) hp[p] = (T)(px[p] * nx + py[p] * ny + pz[p] * nz - splane[jl]);
                 }
+            }
+            T H0t = 0, f1 = 0, f2 = 0;
+            if (KER == DLP_T && F32) {
+                // (y_q - c_i) . n_i = (c_j . n_i - c_i . n_i) + (u_q - 1/3) F1 . n_i + (v_q - 1/3) F2 . n_i
+                double cj[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) cj[d] = (double)sch[d * kMaxLeaf + jl] + (double)scl[d * kMaxLeaf + jl];
+                H0t = (T)(cj[0] * rn[0] + cj[1] * rn[1] + cj[2] * rn[2] - rplane);
+                f1 = (T)(sedge[jl] * rn[0] + sedge[kMaxLeaf + jl] * rn[1] + sedge[2 * kMaxLeaf + jl] * rn[2]);
+                f2 = (T)(sedge[3 * kMaxLeaf + jl] * rn[0] + sedge[4 * kMaxLeaf + jl] * rn[1] +
+                         sedge[5 * kMaxLeaf + jl] * rn[2]);
             }
             T sum = 0;
 #pragma unroll
@@ -158,13 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
                 const T yx = F32 ? Dx - ex : ex, yy = F32 ? Dy - ey : ey, yz = F32 ? Dz - ez : ez;
                 T hq = 0;
                 if (KER == DLP_T) {
-                    if (F32) {
-                        const T H0 = (T)((sctr[jl] - ci[0]) * rn[0] + (sctr[kMaxLeaf + jl] - ci[1]) * rn[1] +
-                                         (sctr[2 * kMaxLeaf + jl] - ci[2]) * rn[2]);
-                        hq = H0 + (ex * (T)rn[0] + ey * (T)rn[1] + ez * (T)rn[2]);
-                    } else {
-                        hq = ((double)ex - ci[0]) * rn[0] + ((double)ey - ci[1]) * rn[1] + ((double)ez - ci[2]) * rn[2];
-                    }
+                    if (F32) hq = H0t + (T)(c.ru[q] - 1.0 / 3.0) * f1 + (T)(c.rv[q] - 1.0 / 3.0) * f2;
+                    else hq = (T)(ex * rn[0] + ey * rn[1] + ez * rn[2] - rplane);
                 }
                 T sp = 0;
 #pragma unroll
@@ -184,20 +226,20 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
                 }
                 sum += (T)c.rw[q] * sp;
             }
-            const double a = ai * sarea[jl] * (double)sum * kInv4Pi;
+            const T a = ai * sarea[jl] * sum;
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[r] += a * sx[jl * NR + r];
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NR; ++r) sbuf[tid * NR + r] = active ? acc[r] : 0.0;
+    for (int r = 0; r < NR; ++r) sbuf[tid * NR + r] = active ? (double)acc[r] : 0.0;
     __syncthreads();
     for (int e = tid; e < R * NR; e += kThreads) {
         const int i = e / NR, r = e % NR;
         double s = 0.0;
         for (int q = 0; q < K; ++q) s += sbuf[(q * R + i) * NR + r];
-        yp[(int64_t)(rb + i) * NR + r] += s;
+        yp[(int64_t)(rb + i) * NR + r] += s * kInv4Pi;
     }
 }
 

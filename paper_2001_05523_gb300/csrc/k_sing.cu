@@ -16,9 +16,18 @@
 // with |w|^2 from the Gram matrix of the edge vectors.  The result equals the
 // full 4-D tensor rule up to rounding.
 //
+// Vertex pairs (the bulk of the work): on both regions w = U(e1) - e2 V(e3)
+// with U, V affine in one variable each, so
+//   |w|^2 = A_i - 2 e2_k B_il + e2_k^2 C_l,   A_i = |U(e1_i)|^2, C_l = |V(e3_l)|^2,
+//   B_il = U(e1_i) . V(e3_l),
+// precomputed per pair from the Gram matrix of (a, b, c, d) (O(q^2) work);
+// each of the q^3 points then costs two FMAs, a reciprocal square root and
+// one accumulation.
+//
 // Single layer: a = 4 |P||Q| / (4 pi) sum_p W_p / |w_p|; g_ij = g_ji = a.
 // Double layer: V = sum_p W_p w_p / |w_p|^3 (a vector), then
 //   k_{lo,hi} = 4 |P||Q| / (4 pi)  V . n_hi,   k_{hi,lo} = -4 |P||Q| / (4 pi) V . n_lo.
+#include "dmath.cuh"
 #include "internal.h"
 
 namespace h2 {
@@ -41,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                                                        const double* __restrict__ tab, int npts, bool transpose,
                                                        const double* __restrict__ xp, double* __restrict__ yp,
                                                        double* __restrict__ val0, double* __restrict__ val1) {
-    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 16;  // doubles per table point
+    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 2;  // doubles per table point
     extern __shared__ double stab[];
     if (MODE != 2) {
         for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
@@ -78,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
             for (int p = 0; p < npts; ++p) {
                 const double* T = stab + p * W;
                 const double r2 = T[0] * aa + T[1] * ab + T[2] * bb;
-                s += T[3] * rsqrt(r2);
+                s += T[3] * rsqrt_nr(r2);
             }
             a01 = a10 = sc * s;
         } else if (TYPE == EDGE) {
@@ -90,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 for (int p = 0; p < npts; ++p) {
                     const double* T = stab + p * W;
                     const double r2 = T[0] * G0 + T[1] * G1 + T[2] * G2 + T[3] * G3 + T[4] * G4 + T[5] * G5;
-                    s += T[9] * rsqrt(r2);
+                    s += T[9] * rsqrt_nr(r2);
                 }
                 a01 = a10 = sc * s;
             } else {
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 for (int p = 0; p < npts; ++p) {
                     const double* T = stab + p * W;
                     const double r2 = T[0] * G0 + T[1] * G1 + T[2] * G2 + T[3] * G3 + T[4] * G4 + T[5] * G5;
-                    const double ri = rsqrt(r2);
+                    const double ri = rsqrt_nr(r2);
                     const double f = T[10] * ri * ri * ri;
                     sa += f * T[6];
                     sb += f * T[7];
@@ -114,35 +123,64 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 a01 = sc * dot(V, nhi);
                 a10 = -sc * dot(V, nlo);
             }
-        } else {  // VERTEX: vectors (a, b, c, d)
-            const double G[10] = {dot(ea, ea), dot(eb, eb), dot(ec, ec), dot(ed, ed), dot(ea, eb),
-                                  dot(ea, ec), dot(ea, ed), dot(eb, ec), dot(eb, ed), dot(ec, ed)};
+        } else {  // VERTEX: vectors (a, b, c, d); stab holds the 1-D Gauss rule (x_k, w_k), npts = q
+            const double aa = dot(ea, ea), bb = dot(eb, eb), cc = dot(ec, ec), dd = dot(ed, ed);
+            const double ab = dot(ea, eb), ac = dot(ea, ec), ad = dot(ea, ed), bc = dot(eb, ec), bd = dot(eb, ed),
+                         cd = dot(ec, ed);
+            const int q = npts;
+            double s = 0.0, sa = 0.0, sb = 0.0, sc2 = 0.0, sd = 0.0;
+            for (int reg = 0; reg < 2; ++reg) {
+                // R1: U = a + e1 b, V = c + e3 d;  R2: U = c + e1 d, V = a + e3 b
+                const double uu = reg == 0 ? aa : cc, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : dd;
+                const double pp = reg == 0 ? cc : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? dd : bb;
+                const double b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
+                for (int i = 0; i < q; ++i) {
+                    const double e1 = stab[2 * i], w1 = stab[2 * i + 1];
+                    const double A = fma(e1, fma(e1, vv2, 2.0 * uv2), uu);
+                    const double Bi0 = fma(e1, b2, b0), Bi1 = fma(e1, bd, b1);
+                    for (int l = 0; l < q; ++l) {
+                        const double e3 = stab[2 * l], w3 = stab[2 * l + 1];
+                        const double Cc = fma(e3, fma(e3, qq2, 2.0 * pq2), pp);
+                        const double m2B = -2.0 * fma(e3, Bi1, Bi0);
+                        double f0 = 0.0, f1 = 0.0;
+                        for (int k = 0; k < q; ++k) {
+                            const double e2 = stab[2 * k], we2 = stab[2 * k + 1] * e2;
+                            const double r2 = fma(e2, fma(e2, Cc, m2B), A);
+                            const double ri = rsqrt_nr(r2);
+                            if (KER == SLP) {
+                                f0 = fma(we2, ri, f0);
+                            } else {
+                                const double f = we2 * (ri * ri * ri);
+                                f0 += f;
+                                f1 = fma(f, e2, f1);
+                            }
+                        }
+                        const double ww = w1 * w3;
+                        if (KER == SLP) {
+                            s = fma(ww, f0, s);
+                        } else {
+                            f0 *= ww;
+                            f1 *= ww;
+                            if (reg == 0) {  // w = a + e1 b - e2 c - e2 e3 d
+                                sa += f0;
+                                sb = fma(e1, f0, sb);
+                                sc2 -= f1;
+                                sd = fma(-e3, f1, sd);
+                            } else {         // w = e2 a + e2 e3 b - c - e1 d
+                                sa += f1;
+                                sb = fma(e3, f1, sb);
+                                sc2 -= f0;
+                                sd = fma(-e1, f0, sd);
+                            }
+                        }
+                    }
+                }
+            }
             if (KER == SLP) {
-                double s = 0.0;
-                for (int p = 0; p < npts; ++p) {
-                    const double* T = stab + p * W;
-                    double r2 = 0.0;
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) r2 += T[q] * G[q];
-                    s += T[14] * rsqrt(r2);
-                }
-                a01 = a10 = sc * s;
+                a01 = a10 = sc * s / 3.0;
             } else {
-                double sa = 0.0, sb = 0.0, sc2 = 0.0, sd = 0.0;
-                for (int p = 0; p < npts; ++p) {
-                    const double* T = stab + p * W;
-                    double r2 = 0.0;
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) r2 += T[q] * G[q];
-                    const double ri = rsqrt(r2);
-                    const double f = T[15] * ri * ri * ri;
-                    sa += f * T[10];
-                    sb += f * T[11];
-                    sc2 += f * T[12];
-                    sd += f * T[13];
-                }
                 double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = sa * ea[d] + sb * eb[d] + sc2 * ec[d] + sd * ed[d];
+                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sc2 * ec[d] + sd * ed[d]);
                 double nlo[3], nhi[3];
                 for (int d = 0; d < 3; ++d) {
                     nlo[d] = g.nrm[d * g.n + lo];
@@ -179,7 +217,7 @@ template <int NR, int TYPE, int KER>
 static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
                       const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
                       double* v0, double* v1) {
-    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 16;
+    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 2;
     const size_t smem = mode == 2 ? 0 : (size_t)npts * W * sizeof(double);
     dim3 grid((npairs + kThreads - 1) / kThreads);
     if (mode == 0) {
