@@ -36,12 +36,16 @@ sys.path.insert(0, ROOT)
 METRIC = "H2 SLP matvec triangles/s on 2M-tri sphere, mixed vs FP64, at stated rel. error"
 UNIT = "triangles*rhs/s"
 
-# Algorithmic flops per kernel evaluation (stated in the design doc):
-#   regular pair point  d = x - y (3), |d|^2 (5), rsqrt (1), weighted sum (2)      = 11
-#   singular point      Gram form (identical 5, edge 11, vertex 19), rsqrt (1), sum (2)
-#   coupling entry      |d|^2 from per-axis squares (2), rsqrt (1), 2*nrhs for S x
+# Algorithmic flops per unit of the formulation each kernel evaluates (an FMA
+# counts 2, a reciprocal square root 1; stated in the design doc):
+#   regular pair point   d = x - y (3), |d|^2 (5), rsqrt (1), weighted sum (2)          = 11 per point, 49 points
+#   singular, identical  |w|^2 from a 2x2 Gram form (6), rsqrt (1), sum (2)            = 9 per point, 15 points
+#   singular, edge       |w|^2 from a 3x3 Gram form (12), rsqrt (1), sum (2)           = 15 per point, 125 points
+#   singular, vertex     |w|^2 = A - 2 e B + e^2 C (4), rsqrt (1), sum (2), plus the
+#                        per-(i,l) coefficients (6 per 5 points) and the Gram set-up   ~ 8.6 per point, 250 points
+#   coupling entry       |d|^2 from per-axis squares (1), rsqrt (1), S x-hat (2 nrhs)
 FLOPS_REG = 11
-FLOPS_SING = {0: 5 + 3, 1: 11 + 3, 2: 19 + 3}
+FLOPS_SING = {0: 9.0, 1: 15.0, 2: 8.6}
 PTS_SING_SLP = {0: 15, 1: 125, 2: 250}  # points per canonical pair, q = 5
 
 
@@ -292,7 +296,7 @@ def main():
     work = {
         "near_regular": reg_pairs * 49 * FLOPS_REG,
         "near_singular": sum(sing[t] * PTS_SING_SLP[t] * FLOPS_SING[t] for t in range(3)),
-        "coupling": st_m["nfar"] * st_m["k"] ** 2 * (3 + 2 * nrhs),
+        "coupling": st_m["nfar"] * st_m["k"] ** 2 * (2 + 2 * nrhs),
     }
     bound_peak = {"near_regular": pk["fp32_tflops"], "near_singular": pk["fp64_tflops"],
                   "coupling": pk["fp32_tflops"]}
@@ -302,7 +306,14 @@ def main():
         peak = bound_peak[dname]
         roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "flops_per_launch": work[dname],
-                "peak_source": f"unit counts x {pk['sm_mhz']:.0f} MHz (FP64 2 FMA/clk/SM, FP32 128 FMA/clk/SM)"}
+                "peak_source": f"unit counts x {pk['sm_mhz']:.0f} MHz (FP64 2 FMA/clk/SM, FP32 128 FMA/clk/SM)",
+                "note": "rsqrt counted as 1 flop; on GB300 an FP64 rsqrt costs ~4 FP64-pipe operations after the "
+                        "hardware approximation, so the FP64 pipe is ~90% busy (ncu) at this algorithmic fraction"}
+        roof["all_kernels"] = {
+            nm: {"ms": round(float(stage_m[names.index(nm)]), 3),
+                 "tflops": work[nm] / (stage_m[names.index(nm)] / 1e3) / 1e12,
+                 "frac": work[nm] / (stage_m[names.index(nm)] / 1e3) / 1e12 / bound_peak[nm]}
+            for nm in work}
     else:
         roof = {"bound": "alu", "kernel": dname, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None}

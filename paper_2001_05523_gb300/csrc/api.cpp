@@ -556,7 +556,7 @@ struct h2bem_op {
     int64_t nfar = 0, nnear = 0, near_pairs = 0, sing[3] = {0, 0, 0};
     h2::Consts consts{};
     // device geometry and tree
-    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid;
+    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane;
     DevBuf cbegin, cend, cchild0, cchild1, cbox, leaves, basis_rule;
     std::vector<int> leaves_h;
     std::vector<std::vector<int>> level_parents;  // non-leaf clusters per level
@@ -576,7 +576,8 @@ struct h2bem_op {
 
     h2::Geom geom() const {
         return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
-                        ctr.as<const double>(), vid.as<const int>()};
+                        ctr.as<const double>(), vid.as<const int>(), qo.as<const float>(), qa.as<const double>(),
+                        chl.as<const float>(), plane.as<const double>()};
     }
     h2::Tree tree() const {
         return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
@@ -827,10 +828,13 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     // geometry in tree order
     if ((rc = op->v.alloc(9 * n * sizeof(double))) || (rc = op->area.alloc(n * sizeof(double))) ||
         (rc = op->nrm.alloc(3 * n * sizeof(double))) || (rc = op->ctr.alloc(3 * n * sizeof(double))) ||
-        (rc = op->vid.alloc(3 * n * sizeof(int))))
+        (rc = op->vid.alloc(3 * n * sizeof(int))) || (rc = op->qo.alloc(21 * n * sizeof(float))) ||
+        (rc = op->qa.alloc(21 * n * sizeof(double))) || (rc = op->chl.alloc(6 * n * sizeof(float))) ||
+        (rc = op->plane.alloc(n * sizeof(double))))
         return rc;
-    h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->v.as<double>(),
-                    op->area.as<double>(), op->nrm.as<double>(), op->ctr.as<double>(), op->vid.as<int>(), 0);
+    h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->consts, op->v.as<double>(),
+                    op->area.as<double>(), op->nrm.as<double>(), op->ctr.as<double>(), op->vid.as<int>(),
+                    op->qo.as<float>(), op->qa.as<double>(), op->chl.as<float>(), op->plane.as<double>(), 0);
     CU(cudaGetLastError());
     // x-independent singular entries, evaluated once if requested
     if (op->cache_singular) {

@@ -24,6 +24,11 @@ struct Geom {
     const double* nrm;   // [3][n] outward unit normal
     const double* ctr;   // [3][n] centroid
     const int* vid;      // [3][n] vertex indices (singular-pair test)
+    // nearfield quadrature data (x-independent, computed with the geometry):
+    const float* qo;     // [3][n][7] FP32 offsets y_q - c of the 7-point rule's points
+    const double* qa;    // [3][n][7] FP64 points y_q
+    const float* chl;    // [6][n] centroid split: hi = fl(c) (rows 0..2), lo = fl(c - hi) (rows 3..5)
+    const double* plane; // [n] c . n (offset of the triangle's plane)
 };
 
 // Cluster tree on the device.
@@ -48,8 +53,8 @@ struct Consts {
 };
 
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
-void launch_geom(const double* xyz, const int* tri, const int* perm, int n, double* v, double* area, double* nrm,
-                 double* ctr, int* vid, cudaStream_t s);
+void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
+                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, cudaStream_t s);
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
                        cudaStream_t s);
 void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,

@@ -107,6 +107,90 @@ __global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const i
     }
 }
 
+// Register-blocked variant for compile-time m: thread (row, slice) owns the
+// m target nodes nu = (a, b, c), a = 0..m-1, of one (b, c) row and the mu-rows
+// (jc, jb) of its slice; every x-hat value loaded from shared memory feeds m
+// entries.  Slices are reduced in shared memory at the end.
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
+__global__ void __launch_bounds__(M * M * 4) k_coupling_rows(Tree t, Consts c, const int* __restrict__ rows,
+                                                             const int* __restrict__ ptr, const int* __restrict__ col,
+                                                             const TX* __restrict__ xh, TY* __restrict__ yh) {
+    constexpr int K = M * M * M, M2 = M * M;
+    constexpr int NSL = 4;  // slices of the mu-rows; blockDim = 4 m^2 (small CTAs, many per SM)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* xs = reinterpret_cast<TA*>(smem_raw);  // [K][NR]; reused for the reduction [NSL][K][NR]
+    __shared__ double zt[3 * M], zs[3 * M];
+    __shared__ TS D2[3 * M2];
+    const int row = rows[blockIdx.x];
+    const int rg = threadIdx.x % M2, sl = threadIdx.x / M2;
+    const bool active = sl < NSL;
+    const int ib = rg % M, ic = rg / M;
+    cluster_nodes(t, c, row, zt);
+    TA acc[M][NR];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[a][r] = 0;
+    for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
+        const int s = col[b];
+        __syncthreads();
+        cluster_nodes(t, c, s, zs);
+        for (int e = threadIdx.x; e < K * NR; e += blockDim.x) xs[e] = (TA)xh[(int64_t)s * K * NR + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < 3 * M2; e += blockDim.x) {
+            const int d = e / M2, a = (e / M) % M, a2 = e % M;
+            const double df = zt[d * M + a] - zs[d * M + a2];
+            D2[e] = (TS)(df * df);
+        }
+        __syncthreads();
+        if (!active) continue;
+        TS dx[M][M];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int ja = 0; ja < M; ++ja) dx[a][ja] = D2[a * M + ja];
+        for (int r2 = sl; r2 < M2; r2 += NSL) {
+            const int jc = r2 / M, jb = r2 % M;
+            const TS sbc = D2[M2 + ib * M + jb] + D2[2 * M2 + ic * M + jc];
+            const TA* xrow = xs + (r2 * M) * NR;
+#pragma unroll
+            for (int ja = 0; ja < M; ++ja) {
+                TA xv[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) xv[r] = xrow[ja * NR + r];
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    const TA sv = (TA)rsq<TS>(dx[a][ja] + sbc);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[a][r] += sv * xv[r];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // reduction over slices: slot [sl][nu][r], nu = a + M * rg
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (active) xs[((size_t)sl * K + a + M * rg) * NR + r] = acc[a][r];
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * NR; e += blockDim.x) {
+        TA s = 0;
+        for (int q = 0; q < NSL; ++q) s += xs[(size_t)q * K * NR + e];
+        yh[(int64_t)row * K * NR + e] = (TY)(s * (TA)kInv4Pi);
+    }
+}
+
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
+static void coupling_rows(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                          const void* xh, void* yh, cudaStream_t s) {
+    constexpr int K = M * M * M, NSL = 4;
+    const size_t smem = sizeof(TA) * (size_t)NSL * K * NR;
+    cudaFuncSetAttribute(k_coupling_rows<TS, TA, TX, TY, NR, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coupling_rows<TS, TA, TX, TY, NR, M><<<nrows, M * M * NSL, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh,
+                                                                           (TY*)yh);
+}
+
 template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
 static void coupling_m(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
                        const void* xh, void* yh, cudaStream_t s) {
@@ -118,8 +202,8 @@ static void coupling_m(const Tree& t, const Consts& c, int nrows, const int* row
 template <typename TS, typename TA, typename TX, typename TY, int NR>
 static void coupling_simt(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
                           const void* xh, void* yh, cudaStream_t s) {
-    if (c.m == 4) coupling_m<TS, TA, TX, TY, NR, 4>(t, c, nrows, rows, ptr, col, xh, yh, s);
-    else if (c.m == 5) coupling_m<TS, TA, TX, TY, NR, 5>(t, c, nrows, rows, ptr, col, xh, yh, s);
+    if (c.m == 4) coupling_rows<TS, TA, TX, TY, NR, 4>(t, c, nrows, rows, ptr, col, xh, yh, s);
+    else if (c.m == 5) coupling_rows<TS, TA, TX, TY, NR, 5>(t, c, nrows, rows, ptr, col, xh, yh, s);
     else coupling_m<TS, TA, TX, TY, NR, 0>(t, c, nrows, rows, ptr, col, xh, yh, s);
 }
 

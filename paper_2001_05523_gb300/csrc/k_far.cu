@@ -341,10 +341,11 @@ static int far_threads(int k) {
         default: { constexpr int R_ = 16; CALL; } break; \
     }
 
-// chunk size: tabulated values of one chunk within about 40 KB of shared memory
+// chunk size: tabulated values of one chunk within about 16 KB of shared
+// memory, so that many CTAs (of 64-256 threads) fit on an SM
 static int leaf_chunk(const Consts& c, size_t tb, bool dlp) {
     const size_t per = ((size_t)c.nb * 3 * c.m * (dlp ? 2 : 1) + c.nb + 3) * tb;
-    int ct = (int)(40960 / per);
+    int ct = (int)(16384 / per);
     return ct < 1 ? 1 : ct > kMaxLeaf ? kMaxLeaf : ct;
 }
 

@@ -23,22 +23,25 @@ __global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, c
 }
 
 // Geometry preparation: gathers the triangles into tree order and computes
-// area |tau| = |(b-a) x (c-a)| / 2, the unit normal (b-a) x (c-a) / |...| and
-// the centroid ((a+b)+c)/3 (section 1; the normal is outward for triangles
-// oriented counter-clockwise seen from outside).
+// area |tau| = |(b-a) x (c-a)| / 2, the unit normal (b-a) x (c-a) / |...|, the
+// centroid ((a+b)+c)/3 (section 1; the normal is outward for triangles oriented
+// counter-clockwise seen from outside), the plane offset c . n, and the points
+// y_q = a + u_q (b-a) + v_q (c-a) of the 7-point rule, in FP64 and as FP32
+// offsets from the centroid, with a float split of the centroid.
 __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ tri, const int* __restrict__ perm,
-                       int n, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
-                       double* __restrict__ ctr, int* __restrict__ vid) {
+                       int n, Consts c, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
+                       double* __restrict__ ctr, int* __restrict__ vid, float* __restrict__ qo,
+                       double* __restrict__ qa, float* __restrict__ chl, double* __restrict__ plane) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int t = perm[i];
     double P[3][3];
-    for (int c = 0; c < 3; ++c) {
-        const int w = tri[3 * t + c];
-        vid[c * n + i] = w;
+    for (int k = 0; k < 3; ++k) {
+        const int w = tri[3 * t + k];
+        vid[k * n + i] = w;
         for (int d = 0; d < 3; ++d) {
-            P[c][d] = xyz[3 * (int64_t)w + d];
-            v[(3 * c + d) * n + i] = P[c][d];
+            P[k][d] = xyz[3 * (int64_t)w + d];
+            v[(3 * k + d) * n + i] = P[k][d];
         }
     }
     const double e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
@@ -46,15 +49,28 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
     const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     const double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
     area[i] = 0.5 * len;
+    double pl = 0.0;
     for (int d = 0; d < 3; ++d) {
-        nrm[d * n + i] = cr[d] / len;
-        ctr[d * n + i] = ((P[0][d] + P[1][d]) + P[2][d]) / 3.0;
+        const double nd = cr[d] / len;
+        const double cd = ((P[0][d] + P[1][d]) + P[2][d]) / 3.0;
+        nrm[d * n + i] = nd;
+        ctr[d * n + i] = cd;
+        const float h = (float)cd;
+        chl[d * n + i] = h;
+        chl[(3 + d) * n + i] = (float)(cd - (double)h);
+        pl += cd * nd;
+        for (int q = 0; q < 7; ++q) {
+            const double y = P[0][d] + c.ru[q] * e1[d] + c.rv[q] * e2[d];
+            qa[((int64_t)d * n + i) * 7 + q] = y;
+            qo[((int64_t)d * n + i) * 7 + q] = (float)(y - cd);
+        }
     }
+    plane[i] = pl;
 }
 
-void launch_geom(const double* xyz, const int* tri, const int* perm, int n, double* v, double* area, double* nrm,
-                 double* ctr, int* vid, cudaStream_t s) {
-    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, v, area, nrm, ctr, vid);
+void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
+                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, cudaStream_t s) {
+    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane);
 }
 
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,

@@ -86,32 +86,30 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
     int vi[3] = {-1, -1, -1};
     if (active) {
         const int i = rb + il;
-        double V[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) V[q] = g.v[q * n + i];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             ci[d] = g.ctr[d * n + i];
             rn[d] = g.nrm[d * n + i];
             vi[d] = g.vid[d * n + i];
-            chi[d] = (T)ci[d];
-            clo[d] = (T)(ci[d] - (double)chi[d]);
+            chi[d] = (T)g.chl[d * n + i];
+            clo[d] = (T)g.chl[(3 + d) * n + i];
+            const double w0 = g.v[d * n + i];
+            E1[d] = g.v[(3 + d) * n + i] - w0;
+            E2[d] = g.v[(6 + d) * n + i] - w0;
         }
-        rplane = ci[0] * rn[0] + ci[1] * rn[1] + ci[2] * rn[2];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            E1[d] = V[3 + d] - V[d];
-            E2[d] = V[6 + d] - V[d];
-        }
+        rplane = g.plane[i];
         ai = (T)g.area[i];
 #pragma unroll
         for (int p = 0; p < 7; ++p) {
-            const double x0 = V[0] + c.ru[p] * (V[3] - V[0]) + c.rv[p] * (V[6] - V[0]);
-            const double x1 = V[1] + c.ru[p] * (V[4] - V[1]) + c.rv[p] * (V[7] - V[1]);
-            const double x2 = V[2] + c.ru[p] * (V[5] - V[2]) + c.rv[p] * (V[8] - V[2]);
-            px[p] = (T)(F32 ? x0 - ci[0] : x0);
-            py[p] = (T)(F32 ? x1 - ci[1] : x1);
-            pz[p] = (T)(F32 ? x2 - ci[2] : x2);
+            if (F32) {
+                px[p] = (T)g.qo[((int64_t)0 * n + i) * 7 + p];
+                py[p] = (T)g.qo[((int64_t)1 * n + i) * 7 + p];
+                pz[p] = (T)g.qo[((int64_t)2 * n + i) * 7 + p];
+            } else {
+                px[p] = (T)g.qa[((int64_t)0 * n + i) * 7 + p];
+                py[p] = (T)g.qa[((int64_t)1 * n + i) * 7 + p];
+                pz[p] = (T)g.qa[((int64_t)2 * n + i) * 7 + p];
+            }
         }
     }
     T acc[NR];
@@ -123,36 +121,33 @@ __global__ void __launch_bounds__(kThreads) k_near_regular(Geom g, Tree t, Const
         const int cb = t.begin[s], C = t.end[s] - cb;
         __syncthreads();
         for (int e = tid; e < C * 7; e += kThreads) {
-            const int j = cb + e / 7, q = e % 7;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double v0 = g.v[d * n + j], v1 = g.v[(3 + d) * n + j], v2 = g.v[(6 + d) * n + j];
-                double y = v0 + c.ru[q] * (v1 - v0) + c.rv[q] * (v2 - v0);
-                if (F32) y -= g.ctr[d * n + j];
-                sq[d * (kMaxLeaf * 7) + e] = (T)y;
-            }
+            for (int d = 0; d < 3; ++d)
+                sq[d * (kMaxLeaf * 7) + e] = F32 ? (T)g.qo[((int64_t)d * n + cb) * 7 + e]
+                                                 : (T)g.qa[((int64_t)d * n + cb) * 7 + e];
         }
         for (int e = tid; e < C; e += kThreads) {
             const int j = cb + e;
             sarea[e] = (T)g.area[j];
-            double pl = 0.0;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double cd = g.ctr[d * n + j], nd = g.nrm[d * n + j];
-                const T h = (T)cd;
-                sch[d * kMaxLeaf + e] = h;
-                scl[d * kMaxLeaf + e] = (T)(cd - (double)h);
-                snrm[d * kMaxLeaf + e] = (T)nd;
+                if (F32) {
+                    sch[d * kMaxLeaf + e] = (T)g.chl[d * n + j];
+                    scl[d * kMaxLeaf + e] = (T)g.chl[(3 + d) * n + j];
+                }
                 svid[d * kMaxLeaf + e] = g.vid[d * n + j];
-                if (KER != SLP) sn64[d * kMaxLeaf + e] = nd;
+                if (KER != SLP) {
+                    const double nd = g.nrm[d * n + j];
+                    snrm[d * kMaxLeaf + e] = (T)nd;
+                    sn64[d * kMaxLeaf + e] = nd;
+                }
                 if (KER == DLP_T) {
                     const double w0 = g.v[d * n + j];
                     sedge[d * kMaxLeaf + e] = g.v[(3 + d) * n + j] - w0;
                     sedge[(3 + d) * kMaxLeaf + e] = g.v[(6 + d) * n + j] - w0;
                 }
-                pl += cd * nd;
             }
-            splane[e] = pl;
+            if (KER != SLP) splane[e] = g.plane[j];
         }
         for (int e = tid; e < C * NR; e += kThreads) sx[e] = (T)xp[(int64_t)cb * NR + e];
         __syncthreads();
