@@ -74,7 +74,11 @@ typedef struct {
     int cache_singular; /* 1: evaluate the x-independent singular entries once at set-up and       */
                         /*    keep them in device memory (about 13 doubles per triangle); 0: on    */
                         /*    the fly in every apply (default)                                     */
-    int reserved[5];    /* must be zero                                                            */
+    int use_graph;      /* 1: h2bem_apply / h2bem_apply_transpose with device buffers on a         */
+                        /*    non-default stream replay a captured CUDA graph of their launch      */
+                        /*    sequence when called again with the same buffers, sizes and          */
+                        /*    direction (the second such call captures it); 0: plain launches     */
+    int reserved[4];    /* must be zero                                                            */
 } h2bem_opts;
 
 /* Statistics of an operator (counts are exact, from its own block lists). */
@@ -146,6 +150,18 @@ int h2bem_opts_default(h2bem_opts* opts);
  * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts), OOM, CUDA. */
 int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
                           const h2bem_opts* opts, h2bem_op** out);
+/* Many meshes as one operator (batching).  Builds the block-diagonal operator
+ * diag(A_1, ..., A_B) over the concatenation of the meshes, in the order given:
+ * triangle i of mesh b is index off_b + i with off_b = sum of the earlier
+ * meshes' triangle counts.  Each mesh gets its own cluster tree (as
+ * h2bem_tree_build with leaf_size) and its own block tree from its own root
+ * (section 2, Definitions "cluster tree" and "block tree"; no block couples two
+ * meshes), so A_b equals the operator h2bem_operator_create builds for mesh b
+ * alone.  Every stage of h2bem_apply on the result is then a single launch
+ * over all meshes.  The meshes are copied; the caller keeps ownership.
+ * Errors: as h2bem_operator_create; ARG if nmeshes < 1 or a mesh is NULL. */
+int h2bem_batch_create(int nmeshes, const h2bem_mesh* const* meshes, int leaf_size, int kernel, int m, double eta,
+                       const h2bem_opts* opts, h2bem_op** out);
 int h2bem_operator_destroy(h2bem_op* op);
 int h2bem_stats_get(const h2bem_op* op, h2bem_stats* stats);
 

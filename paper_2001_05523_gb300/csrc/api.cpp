@@ -573,6 +573,22 @@ struct h2bem_op {
     cudaEvent_t ev[10] = {};
     double last_ms = 0.0, stage_ms[8] = {0};
     int64_t launches = 0;
+    // CUDA graph of the launch sequence (use_graph)
+    int use_graph = 0;
+    int64_t ws_gen = 0;
+    cudaGraphExec_t gexec = nullptr;
+    struct GKey {
+        const void* x = nullptr;
+        void* y = nullptr;
+        int64_t ldx = 0, ldy = 0, ws_gen = -1, launches = 0;
+        int nrhs = 0;
+        bool tr = false;
+        cudaStream_t s = nullptr;
+        bool operator==(const GKey& o) const {
+            return x == o.x && y == o.y && ldx == o.ldx && ldy == o.ldy && ws_gen == o.ws_gen && nrhs == o.nrhs &&
+                   tr == o.tr && s == o.s;
+        }
+    } gkey_seen, gkey_graph;
 
     h2::Geom geom() const {
         return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
@@ -586,6 +602,7 @@ struct h2bem_op {
     ~h2bem_op() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        if (gexec) cudaGraphExecDestroy(gexec);
     }
 };
 
@@ -666,8 +683,8 @@ void singular_pairs(const h2bem_mesh& M, std::vector<int64_t> lo[3], std::vector
 
 }  // namespace
 
-extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
-                                     const h2bem_opts* opts_in, h2bem_op** out) {
+static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blocks* prebuilt, int kernel, int m,
+                       double eta, const h2bem_opts* opts_in, h2bem_op** out) {
     if (!out) return fail(H2BEM_ERR_ARG, "operator_create: out is NULL");
     *out = nullptr;
     if (!mesh || !tree) return fail(H2BEM_ERR_ARG, "operator_create: NULL mesh or tree");
@@ -700,6 +717,7 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     op->precision = opts.precision;
     op->q_ss = opts.q_ss;
     op->cache_singular = opts.cache_singular ? 1 : 0;
+    op->use_graph = opts.use_graph ? 1 : 0;
     op->n = mesh->nt;
     op->nc = tree->nc;
     op->depth = tree->depth;
@@ -780,7 +798,8 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
 
     // block lists
     Blocks B;
-    build_blocks(*tree, eta, B);
+    if (prebuilt) B = *prebuilt;
+    else build_blocks(*tree, eta, B);
     op->nfar = (int64_t)B.ft.size();
     op->nnear = (int64_t)B.nt.size();
     op->near_pairs = 0;
@@ -860,6 +879,69 @@ extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* t
     return H2BEM_OK;
 }
 
+extern "C" int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
+                                     const h2bem_opts* opts, h2bem_op** out) {
+    return create_impl(mesh, tree, nullptr, kernel, m, eta, opts, out);
+}
+
+// Block-diagonal operator over several meshes: the meshes are concatenated
+// (vertex and triangle indices offset), their cluster trees form a forest
+// (each built as by h2bem_tree_build), and block lists are built per mesh
+// from its own root, so no block couples two meshes.
+extern "C" int h2bem_batch_create(int nmeshes, const h2bem_mesh* const* meshes, int leaf_size, int kernel, int m,
+                                  double eta, const h2bem_opts* opts, h2bem_op** out) {
+    if (!out) return fail(H2BEM_ERR_ARG, "batch_create: out is NULL");
+    *out = nullptr;
+    if (nmeshes < 1 || !meshes) return fail(H2BEM_ERR_ARG, "batch_create: need at least one mesh");
+    if (leaf_size < 1) return fail(H2BEM_ERR_ARG, "batch_create: leaf_size must be >= 1");
+    if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(H2BEM_ERR_ARG, "batch_create: eta must be finite and >= 0");
+    h2bem_mesh U;
+    h2bem_tree F;
+    Blocks B;
+    int64_t voff = 0, toff = 0, coff = 0;
+    for (int b = 0; b < nmeshes; ++b) {
+        const h2bem_mesh* M = meshes[b];
+        if (!M) return fail(H2BEM_ERR_ARG, "batch_create: mesh %d is NULL", b);
+        if (toff + M->nt > ((int64_t)1 << 30)) return fail(H2BEM_ERR_ARG, "batch_create: batch too large");
+        h2bem_tree* T = nullptr;
+        int rc = h2bem_tree_build(M, leaf_size, &T);
+        if (rc) return rc;
+        std::unique_ptr<h2bem_tree> Tp(T);
+        U.xyz.insert(U.xyz.end(), M->xyz.begin(), M->xyz.end());
+        for (int32_t v : M->tri) U.tri.push_back((int32_t)(v + voff));
+        for (int64_t i = 0; i < T->n; ++i) F.perm.push_back(T->perm[i] + toff);
+        for (int64_t c = 0; c < T->nc; ++c) {
+            F.begin.push_back(T->begin[c] + toff);
+            F.end.push_back(T->end[c] + toff);
+            F.child0.push_back(T->child0[c] < 0 ? -1 : T->child0[c] + coff);
+            F.child1.push_back(T->child1[c] < 0 ? -1 : T->child1[c] + coff);
+            F.parent.push_back(T->parent[c] < 0 ? -1 : T->parent[c] + coff);
+            F.level.push_back(T->level[c]);
+        }
+        F.bmin.insert(F.bmin.end(), T->bmin.begin(), T->bmin.end());
+        F.bmax.insert(F.bmax.end(), T->bmax.begin(), T->bmax.end());
+        F.depth = std::max(F.depth, T->depth);
+        Blocks Bm;
+        build_blocks(*T, eta, Bm);
+        for (size_t q = 0; q < Bm.ft.size(); ++q) {
+            B.ft.push_back(Bm.ft[q] + coff);
+            B.fs.push_back(Bm.fs[q] + coff);
+        }
+        for (size_t q = 0; q < Bm.nt.size(); ++q) {
+            B.nt.push_back(Bm.nt[q] + coff);
+            B.ns.push_back(Bm.ns[q] + coff);
+        }
+        voff += M->nv;
+        toff += M->nt;
+        coff += T->nc;
+    }
+    U.nv = voff;
+    U.nt = toff;
+    F.n = toff;
+    F.nc = coff;
+    return create_impl(&U, &F, &B, kernel, m, eta, opts, out);
+}
+
 extern "C" int h2bem_operator_destroy(h2bem_op* op) {
     if (op) cudaDeviceSynchronize();
     delete op;
@@ -915,6 +997,7 @@ static int ensure_workspace(h2bem_op* op, int NR) {
         (rc = op->xh.alloc((size_t)op->nc * op->k * NR * xsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * ysz)))
         return rc;
     op->ws_NR = NR;
+    op->ws_gen++;
     return H2BEM_OK;
 }
 
@@ -1042,6 +1125,50 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
             yd = op->ystage.as<double>();
             ly = op->n;
         }
+    }
+    // CUDA graph replay: device buffers, a non-default stream, same arguments as
+    // the previous call (the first repeat captures, later repeats replay)
+    const bool graphable = op->use_graph && xdev && ydev && !timed && s != nullptr;
+    if (graphable) {
+        int rc = ensure_workspace(op, pad_nr(std::min(nrhs, 16)));
+        if (rc) return rc;
+        h2bem_op::GKey key;
+        key.x = x;
+        key.y = y;
+        key.ldx = ldx;
+        key.ldy = ldy;
+        key.nrhs = nrhs;
+        key.tr = transpose;
+        key.s = s;
+        key.ws_gen = op->ws_gen;
+        if (op->gexec && key == op->gkey_graph) {
+            CU(cudaGraphLaunch(op->gexec, s));
+            op->launches = op->gkey_graph.launches;
+            return H2BEM_OK;
+        }
+        if (key == op->gkey_seen) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            op->launches = 0;
+            for (int c0 = 0; c0 < nrhs && rc == 0; c0 += 16)
+                rc = apply_chunk(op, xd + c0 * lx, lx, std::min(16, nrhs - c0), yd + c0 * ly, ly, s, transpose, false);
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ce != cudaSuccess) return fail(H2BEM_ERR_CUDA, "apply: graph capture failed: %s", cudaGetErrorString(ce));
+            if (op->gexec) cudaGraphExecDestroy(op->gexec);
+            op->gexec = nullptr;
+            ce = cudaGraphInstantiate(&op->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(H2BEM_ERR_CUDA, "apply: graph instantiation failed: %s", cudaGetErrorString(ce));
+            key.launches = op->launches;
+            op->gkey_graph = key;
+            CU(cudaGraphLaunch(op->gexec, s));
+            return H2BEM_OK;
+        }
+        op->gkey_seen = key;
     }
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);

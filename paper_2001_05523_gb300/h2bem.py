@@ -27,7 +27,7 @@ EXPORTED = [
     "h2bem_last_error", "h2bem_mesh_create", "h2bem_mesh_destroy", "h2bem_tree_build", "h2bem_tree_upload",
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
-    "h2bem_apply_timed", "h2bem_apply_noalloc",
+    "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create",
 ]
 
 
@@ -39,7 +39,7 @@ class H2bemError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +87,7 @@ def lib():
             "h2bem_apply_transpose": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_apply_timed": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_apply_noalloc": [vp, vp, i64, i32, vp, i64, vp],
+            "h2bem_batch_create": [i32, vp, i32, i32, i32, d, vp, pp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -175,6 +176,15 @@ def h2bem_operator_create(mesh, tree, kernel: int, m: int, eta: float, opts: Opt
     return h
 
 
+def h2bem_batch_create(meshes, leaf_size: int, kernel: int, m: int, eta: float, opts: Opts | None = None):
+    arr = (ctypes.c_void_p * len(meshes))(*[mh.value for mh in meshes])
+    h = ctypes.c_void_p()
+    _check(lib().h2bem_batch_create(len(meshes), ctypes.cast(arr, ctypes.c_void_p), int(leaf_size), int(kernel),
+                                    int(m), float(eta), ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(h)))
+    return h
+
+
 def h2bem_operator_destroy(h):
     _check(lib().h2bem_operator_destroy(h))
 
@@ -239,11 +249,55 @@ def h2bem_apply_timed(op, x, y, stream=None):
 
 
 # ---------------------------------------------------------------- convenience
+class BatchOperator:
+    """Block-diagonal operator over many meshes (vectors concatenated in mesh order)."""
+
+    def __init__(self, meshes, kernel: str | int = "slp", m: int = 4, eta: float = 2.0, leaf_size: int = 32,
+                 precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
+                 use_graph: bool = False):
+        kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
+        self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
+        self.sizes = [int(mh.nt) for mh in meshes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        o = h2bem_opts_default()
+        o.q_ss = q_ss
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.cache_singular = int(cache_singular)
+        o.use_graph = int(use_graph)
+        self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
+
+    def close(self):
+        if getattr(self, "op", None) is not None and self.op.value:
+            h2bem_operator_destroy(self.op)
+            self.op = None
+        for mh in getattr(self, "meshes", []):
+            if mh.value:
+                h2bem_mesh_destroy(mh)
+        self.meshes = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, y=None, stream=None, transpose: bool = False):
+        if y is None:
+            y = x.new_empty(x.shape) if not isinstance(x, np.ndarray) else np.empty_like(x)
+        (h2bem_apply_transpose if transpose else h2bem_apply)(self.op, x, y, stream)
+        return y
+
+    def stats(self) -> dict:
+        return h2bem_stats_get(self.op)
+
+
 class Operator:
     """Owns mesh, tree and operator handles for one surface mesh."""
 
     def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
-                 leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False):
+                 leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
+                 use_graph: bool = False):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -252,6 +306,7 @@ class Operator:
         o.q_ss = q_ss
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.cache_singular = int(cache_singular)
+        o.use_graph = int(use_graph)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):
