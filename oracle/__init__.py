@@ -86,6 +86,9 @@ def lib():
             L.or_test_poly_Q.argtypes = [vp]
             L.or_test_poly_Q.restype = d
             L.or_h2_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.or_h2_update_geometry.argtypes = [vp, vp]
+            L.or_h2_grad.argtypes = [vp, vp, vp, i32, vp, i32]
+            L.or_h2_grad.restype = i32
             L.or_num_threads.restype = i32
             L.or_set_threads.argtypes = [i32]
             _lib = L
@@ -296,6 +299,20 @@ class H2:
         y = np.zeros_like(x)
         lib().or_h2_matvec(self.h, _p(x), x.shape[0], _p(y), int(transpose), int(parts))
         return y
+
+    def update_geometry(self, vertices) -> None:
+        """New vertex positions with the cluster tree and block lists unchanged."""
+        v = _f64(vertices)
+        self._keep = (v, self._keep[1])
+        lib().or_h2_update_geometry(self.h, _p(v))
+
+    def grad_vertices(self, w: np.ndarray, x: np.ndarray, parts: int = PART_ALL) -> np.ndarray:
+        """d/dX of sum_r <w_r, A x_r> (single layer), shape (nv, 3)."""
+        w, x = _f64(w), _f64(x)
+        g = np.zeros((self.mesh.nv, 3))
+        if lib().or_h2_grad(self.h, _p(w), _p(x), x.shape[0], _p(g), int(parts)):
+            raise ValueError("gradient is available for the single layer only")
+        return g
 
     def rows(self, rows, x: np.ndarray) -> np.ndarray:
         rows = np.ascontiguousarray(rows, dtype=np.int64)

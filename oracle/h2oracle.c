@@ -671,41 +671,27 @@ static int64_t* csr_from(int64_t nrows, const int64_t* key, const int64_t* val, 
     return ptr;
 }
 
-or_h2* or_h2_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int kernel, int m, double eta,
-                    int leaf, int q_ss) {
-    if (m < 1 || m > 10 || leaf < 1 || nt < 1) return NULL;
-    or_h2* H = calloc(1, sizeof(or_h2));
-    H->xyz = malloc(3 * nv * sizeof(double));
-    H->tri = malloc(3 * nt * sizeof(int32_t));
-    memcpy(H->xyz, xyz, 3 * nv * sizeof(double));
-    memcpy(H->tri, tri, 3 * nt * sizeof(int32_t));
-    H->mesh.xyz = H->xyz;
-    H->mesh.tri = H->tri;
-    H->mesh.nv = nv;
-    H->mesh.nt = nt;
-    H->kernel = kernel;
-    H->m = m;
-    H->k = m * m * m;
-    H->eta = eta;
-    H->q_ss = q_ss;
-    /* basis rule exact for total degree 3(m-1): collapsed Gauss, qb points */
-    H->qb = (3 * (m - 1) + 2 + 1) / 2;
-    if (H->qb < 1) H->qb = 1;
-    /* cluster tree */
+/* Geometry-dependent parts of the H^2 approximation for the current vertex
+ * positions, with the cluster tree and the block lists unchanged: cluster
+ * boxes, interpolation nodes, leaf bases and transfer matrices. */
+static void h2_geometry(or_h2* H) {
     tree_t* T = &H->T;
-    T->n = nt;
-    T->perm = malloc(nt * sizeof(int64_t));
-    for (int64_t i = 0; i < nt; ++i) T->perm[i] = i;
-    int64_t* tmp = malloc(nt * sizeof(int64_t));
-    tree_split(&H->mesh, T, 0, nt, -1, 0, leaf, tmp);
-    free(tmp);
-    /* block tree */
-    block_build(T, eta, 0, 0, &H->far, &H->near);
     int64_t nc = T->count;
-    H->far_ptr = csr_from(nc, H->far.t, H->far.s, H->far.n, &H->far_col);
-    H->near_ptr = csr_from(nc, H->near.t, H->near.s, H->near.n, &H->near_col);
-    H->far_ptr_t = csr_from(nc, H->far.s, H->far.t, H->far.n, &H->far_row_t);
-    H->near_ptr_t = csr_from(nc, H->near.s, H->near.t, H->near.n, &H->near_row_t);
+    int m = H->m;
+    int kernel = H->kernel;
+    for (int64_t c = 0; c < nc; ++c)
+        tree_box(&H->mesh, T->perm + T->begin[c], T->end[c] - T->begin[c], T->bmin + 3 * c, T->bmax + 3 * c);
+    free(H->nodes);
+    if (H->V)
+        for (int64_t c = 0; c < nc; ++c) {
+            if (H->W[c] && H->W[c] != H->V[c]) free(H->W[c]);
+            free(H->V[c]);
+        }
+    if (H->E)
+        for (int64_t c = 0; c < nc; ++c) free(H->E[c]);
+    free(H->V);
+    free(H->W);
+    free(H->E);
     /* interpolation nodes */
     H->nodes = malloc(nc * 3 * m * sizeof(double));
     for (int64_t c = 0; c < nc; ++c) cluster_nodes(T->bmin + 3 * c, T->bmax + 3 * c, m, H->nodes + c * 3 * m);
@@ -758,6 +744,44 @@ or_h2* or_h2_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t n
         }
         H->E[c] = E;
     }
+}
+
+or_h2* or_h2_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int kernel, int m, double eta,
+                    int leaf, int q_ss) {
+    if (m < 1 || m > 10 || leaf < 1 || nt < 1) return NULL;
+    or_h2* H = calloc(1, sizeof(or_h2));
+    H->xyz = malloc(3 * nv * sizeof(double));
+    H->tri = malloc(3 * nt * sizeof(int32_t));
+    memcpy(H->xyz, xyz, 3 * nv * sizeof(double));
+    memcpy(H->tri, tri, 3 * nt * sizeof(int32_t));
+    H->mesh.xyz = H->xyz;
+    H->mesh.tri = H->tri;
+    H->mesh.nv = nv;
+    H->mesh.nt = nt;
+    H->kernel = kernel;
+    H->m = m;
+    H->k = m * m * m;
+    H->eta = eta;
+    H->q_ss = q_ss;
+    /* basis rule exact for total degree 3(m-1): collapsed Gauss, qb points */
+    H->qb = (3 * (m - 1) + 2 + 1) / 2;
+    if (H->qb < 1) H->qb = 1;
+    /* cluster tree */
+    tree_t* T = &H->T;
+    T->n = nt;
+    T->perm = malloc(nt * sizeof(int64_t));
+    for (int64_t i = 0; i < nt; ++i) T->perm[i] = i;
+    int64_t* tmp = malloc(nt * sizeof(int64_t));
+    tree_split(&H->mesh, T, 0, nt, -1, 0, leaf, tmp);
+    free(tmp);
+    /* block tree */
+    block_build(T, eta, 0, 0, &H->far, &H->near);
+    int64_t nc = T->count;
+    H->far_ptr = csr_from(nc, H->far.t, H->far.s, H->far.n, &H->far_col);
+    H->near_ptr = csr_from(nc, H->near.t, H->near.s, H->near.n, &H->near_col);
+    H->far_ptr_t = csr_from(nc, H->far.s, H->far.t, H->far.n, &H->far_row_t);
+    H->near_ptr_t = csr_from(nc, H->near.s, H->near.t, H->near.n, &H->near_row_t);
+    h2_geometry(H);
     return H;
 }
 
@@ -1071,4 +1095,393 @@ void or_set_threads(int n) {
 #else
     (void)n;
 #endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Shape gradient of L = sum_r <w_r, A x_r> for the single layer, with the    */
+/* cluster tree and the block lists frozen: derivative with respect to every  */
+/* vertex coordinate, through the nearfield entries (7 x 7 rule and the full  */
+/* Sauter-Schwab rule, areas included), the leaf bases, the transfer and      */
+/* coupling matrices and, through their interpolation nodes, the cluster      */
+/* boxes (centre and floored half-width) and the extreme vertices that define */
+/* them.                                                                      */
+/* ------------------------------------------------------------------------- */
+void or_h2_update_geometry(or_h2* H, const double* xyz) {
+    memcpy(H->xyz, xyz, 3 * H->mesh.nv * sizeof(double));
+    h2_geometry(H);
+}
+
+/* grad_x g(x, y) = -(x - y) / (4 pi |x - y|^3) */
+static void grad_g(const double* x, const double* y, double* out) {
+    double d[3];
+    sub3(x, y, d);
+    double r2 = dot3(d, d);
+    double c = -OR_INV4PI / (r2 * sqrt(r2));
+    out[0] = c * d[0];
+    out[1] = c * d[1];
+    out[2] = c * d[2];
+}
+
+/* d|tau|/dX_k = 1/2 n x (X_{k+2} - X_{k+1}) (indices mod 3) */
+static void area_grad(const double* X, double* dA) {
+    double area, n[3];
+    or_tri_geom(X, X + 3, X + 6, &area, n);
+    for (int k = 0; k < 3; ++k) {
+        double e[3];
+        sub3(X + 3 * ((k + 2) % 3), X + 3 * ((k + 1) % 3), e);
+        double c[3];
+        cross3(n, e, c);
+        for (int d = 0; d < 3; ++d) dA[3 * k + d] = 0.5 * c[d];
+    }
+}
+
+static void add_vertex(double* gX, int32_t v, const double* g, double s) {
+    for (int d = 0; d < 3; ++d) gX[3 * (int64_t)v + d] += s * g[d];
+}
+
+/* coef * d a_ij / d(vertices), single layer, accumulated into gX */
+static void entry_grad_slp(const or_mesh* M, int64_t i, int64_t j, int q_ss, double coef, double* gX) {
+    int ns = or_shared_vertices(M, i, j);
+    if (ns == 0) {
+        double X[9], Y[9], ax, ay, nx[3], ny[3], uv[14], w[7];
+        tri_vertices(M, i, X);
+        tri_vertices(M, j, Y);
+        or_tri_geom(X, X + 3, X + 6, &ax, nx);
+        or_tri_geom(Y, Y + 3, Y + 6, &ay, ny);
+        or_radon7(uv, w);
+        double xp[7][3], yq[7][3];
+        for (int p = 0; p < 7; ++p)
+            for (int d = 0; d < 3; ++d) {
+                xp[p][d] = X[d] + uv[2 * p] * (X[3 + d] - X[d]) + uv[2 * p + 1] * (X[6 + d] - X[d]);
+                yq[p][d] = Y[d] + uv[2 * p] * (Y[3 + d] - Y[d]) + uv[2 * p + 1] * (Y[6 + d] - Y[d]);
+            }
+        double S = 0.0, gx[3][3] = {{0}}, gy[3][3] = {{0}};
+        for (int p = 0; p < 7; ++p)
+            for (int q = 0; q < 7; ++q) {
+                double wpq = w[p] * w[q], g[3];
+                S += wpq * kernel_slp(xp[p], yq[q]);
+                grad_g(xp[p], yq[q], g);
+                double lx[3] = {1.0 - uv[2 * p] - uv[2 * p + 1], uv[2 * p], uv[2 * p + 1]};
+                double ly[3] = {1.0 - uv[2 * q] - uv[2 * q + 1], uv[2 * q], uv[2 * q + 1]};
+                for (int k = 0; k < 3; ++k)
+                    for (int d = 0; d < 3; ++d) {
+                        gx[k][d] += wpq * lx[k] * g[d];
+                        gy[k][d] -= wpq * ly[k] * g[d];
+                    }
+            }
+        double dAx[9], dAy[9];
+        area_grad(X, dAx);
+        area_grad(Y, dAy);
+        for (int k = 0; k < 3; ++k) {
+            double vx[3], vy[3];
+            for (int d = 0; d < 3; ++d) {
+                vx[d] = dAx[3 * k + d] * ay * S + ax * ay * gx[k][d];
+                vy[d] = dAy[3 * k + d] * ax * S + ax * ay * gy[k][d];
+            }
+            add_vertex(gX, M->tri[3 * i + k], vx, coef);
+            add_vertex(gX, M->tri[3 * j + k], vy, coef);
+        }
+        return;
+    }
+    /* singular: canonical orientation, full tensor rule */
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    double P[9], Q[9];
+    int type;
+    or_orient_pair(M, lo, hi, &type, P, Q);
+    /* vertex ids of P and Q in their listed order */
+    int32_t pv[3], qv[3];
+    for (int k = 0; k < 3; ++k) {
+        pv[k] = qv[k] = -1;
+        for (int a = 0; a < 3; ++a) {
+            const double* va = M->xyz + 3 * (int64_t)M->tri[3 * lo + a];
+            const double* vb = M->xyz + 3 * (int64_t)M->tri[3 * hi + a];
+            if (va[0] == P[3 * k] && va[1] == P[3 * k + 1] && va[2] == P[3 * k + 2]) pv[k] = M->tri[3 * lo + a];
+            if (vb[0] == Q[3 * k] && vb[1] == Q[3 * k + 1] && vb[2] == Q[3 * k + 2]) qv[k] = M->tri[3 * hi + a];
+        }
+    }
+    double g[64], gw[64];
+    or_gauss_legendre01(q_ss, g, gw);
+    double ap, np_[3], aq, nq[3];
+    or_tri_geom(P, P + 3, P + 6, &ap, np_);
+    or_tri_geom(Q, Q + 3, Q + 6, &aq, nq);
+    double S = 0.0, gp[3][3] = {{0}}, gq[3][3] = {{0}};
+    for (int i0 = 0; i0 < q_ss; ++i0)
+        for (int i1 = 0; i1 < q_ss; ++i1)
+            for (int i2 = 0; i2 < q_ss; ++i2)
+                for (int i3 = 0; i3 < q_ss; ++i3) {
+                    double wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    double reg[6][5];
+                    int nr = ss_regions(type, g[i0], g[i1], g[i2], g[i3], reg);
+                    for (int r = 0; r < nr; ++r) {
+                        double x[3], y[3], gg[3];
+                        chi(P, reg[r][0], reg[r][1], x);
+                        chi(Q, reg[r][2], reg[r][3], y);
+                        double c = wt * reg[r][4];
+                        S += c * kernel_slp(x, y);
+                        grad_g(x, y, gg);
+                        /* d chi / d corner: (1 - x1, x1 - x2, x2) */
+                        double lx[3] = {1.0 - reg[r][0], reg[r][0] - reg[r][1], reg[r][1]};
+                        double ly[3] = {1.0 - reg[r][2], reg[r][2] - reg[r][3], reg[r][3]};
+                        for (int k = 0; k < 3; ++k)
+                            for (int d = 0; d < 3; ++d) {
+                                gp[k][d] += c * lx[k] * gg[d];
+                                gq[k][d] -= c * ly[k] * gg[d];
+                            }
+                    }
+                }
+    double dAp[9], dAq[9];
+    area_grad(P, dAp);
+    area_grad(Q, dAq);
+    for (int k = 0; k < 3; ++k) {
+        double vp[3], vq[3];
+        for (int d = 0; d < 3; ++d) {
+            vp[d] = 4.0 * (dAp[3 * k + d] * aq * S + ap * aq * gp[k][d]);
+            vq[d] = 4.0 * (dAq[3 * k + d] * ap * S + ap * aq * gq[k][d]);
+        }
+        add_vertex(gX, pv[k], vp, coef);
+        add_vertex(gX, qv[k], vq, coef);
+    }
+}
+
+/* nodes of cluster c along axis e, centre, floored half-width */
+static void box_ch(const tree_t* T, int64_t c, double* ctr, double* half, int* floored, int* amax) {
+    double h[3], hmax = 0.0;
+    int am = 0;
+    for (int d = 0; d < 3; ++d) {
+        ctr[d] = 0.5 * (T->bmin[3 * c + d] + T->bmax[3 * c + d]);
+        h[d] = 0.5 * (T->bmax[3 * c + d] - T->bmin[3 * c + d]);
+        if (h[d] > hmax) {
+            hmax = h[d];
+            am = d;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        floored[d] = h[d] < 1e-2 * hmax;
+        half[d] = floored[d] ? 1e-2 * hmax : h[d];
+    }
+    *amax = am;
+}
+
+int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, double* gX, int parts) {
+    if (H->kernel != OR_SLP) return -1;
+    const tree_t* T = &H->T;
+    int64_t n = T->n, nc = T->count, nv = H->mesh.nv;
+    int k = H->k, m = H->m;
+    for (int64_t a = 0; a < 3 * nv; ++a) gX[a] = 0.0;
+    if (parts & OR_PART_NEAR) {
+        /* nearfield entries, coefficient c_ij = sum_r w_ir x_jr */
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t b = H->near_ptr[t]; b < H->near_ptr[t + 1]; ++b) {
+                int64_t s = H->near_col[b];
+                for (int64_t a = T->begin[t]; a < T->end[t]; ++a)
+                    for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                        int64_t i = T->perm[a], j = T->perm[bb];
+                        double c = 0.0;
+                        for (int r = 0; r < nrhs; ++r) c += w[i + r * n] * x[j + r * n];
+                        entry_grad_slp(&H->mesh, i, j, H->q_ss, c, gX);
+                    }
+            }
+    }
+    if (!(parts & OR_PART_FAR) || H->far.n == 0) return 0;
+    /* forward quantities: xh = V^T x, wh = V^T w (upward), yh = S xh, zh = S^T wh, then downward */
+    size_t vs = (size_t)nc * k * nrhs;
+    double* xh = calloc(vs, sizeof(double));
+    double* wh = calloc(vs, sizeof(double));
+    double* yh = calloc(vs, sizeof(double));
+    double* zh = calloc(vs, sizeof(double));
+    double* S = malloc((size_t)k * k * sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int nu = 0; nu < k; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+                double sx = 0.0, sw = 0.0;
+                for (int64_t a = 0; a < sz; ++a) {
+                    sx += H->V[c][a * k + nu] * x[T->perm[b + a] + r * n];
+                    sw += H->V[c][a * k + nu] * w[T->perm[b + a] + r * n];
+                }
+                xh[(c * k + nu) * nrhs + r] = sx;
+                wh[(c * k + nu) * nrhs + r] = sw;
+            }
+    }
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        if (T->child0[c] < 0) continue;
+        int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q)
+            for (int nu = 0; nu < k; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double sx = 0.0, sw = 0.0;
+                    for (int nup = 0; nup < k; ++nup) {
+                        sx += H->E[ch[q]][nup * k + nu] * xh[(ch[q] * k + nup) * nrhs + r];
+                        sw += H->E[ch[q]][nup * k + nu] * wh[(ch[q] * k + nup) * nrhs + r];
+                    }
+                    xh[(c * k + nu) * nrhs + r] += sx;
+                    wh[(c * k + nu) * nrhs + r] += sw;
+                }
+    }
+    for (int b = 0; b < H->far.n; ++b) {
+        int64_t t = H->far.t[b], s = H->far.s[b];
+        coupling_matrix(H, t, s, S);
+        for (int nu = 0; nu < k; ++nu)
+            for (int mu = 0; mu < k; ++mu)
+                for (int r = 0; r < nrhs; ++r) {
+                    yh[(t * k + nu) * nrhs + r] += S[nu * k + mu] * xh[(s * k + mu) * nrhs + r];
+                    zh[(s * k + mu) * nrhs + r] += S[nu * k + mu] * wh[(t * k + nu) * nrhs + r];
+                }
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] < 0) continue;
+        int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q)
+            for (int nup = 0; nup < k; ++nup)
+                for (int r = 0; r < nrhs; ++r) {
+                    double sy = 0.0, sz = 0.0;
+                    for (int nu = 0; nu < k; ++nu) {
+                        sy += H->E[ch[q]][nup * k + nu] * yh[(c * k + nu) * nrhs + r];
+                        sz += H->E[ch[q]][nup * k + nu] * zh[(c * k + nu) * nrhs + r];
+                    }
+                    yh[(ch[q] * k + nup) * nrhs + r] += sy;
+                    zh[(ch[q] * k + nup) * nrhs + r] += sz;
+                }
+    }
+    /* dL/d(centre), dL/d(half-width) of every cluster's interpolation box */
+    double* gc = calloc(3 * nc, sizeof(double));
+    double* gh = calloc(3 * nc, sizeof(double));
+    /* coupling: L contains wh_t^T S_ts xh_s */
+    for (int b = 0; b < H->far.n; ++b) {
+        int64_t t = H->far.t[b], s = H->far.s[b];
+        const double* zt = H->nodes + t * 3 * m;
+        const double* zs = H->nodes + s * 3 * m;
+        double ct[3], htt[3], cs[3], hs[3];
+        int fl[3], am;
+        box_ch(T, t, ct, htt, fl, &am);
+        box_ch(T, s, cs, hs, fl, &am);
+        for (int nu = 0; nu < k; ++nu) {
+            int ia[3] = {nu % m, (nu / m) % m, nu / (m * m)};
+            double xt[3] = {zt[ia[0]], zt[m + ia[1]], zt[2 * m + ia[2]]};
+            for (int mu = 0; mu < k; ++mu) {
+                int ja[3] = {mu % m, (mu / m) % m, mu / (m * m)};
+                double xs[3] = {zs[ja[0]], zs[m + ja[1]], zs[2 * m + ja[2]]};
+                double c = 0.0;
+                for (int r = 0; r < nrhs; ++r) c += wh[(t * k + nu) * nrhs + r] * xh[(s * k + mu) * nrhs + r];
+                double gg[3];
+                grad_g(xt, xs, gg);
+                for (int d = 0; d < 3; ++d) {
+                    /* xi = centre + half * cos-node: d xi / d centre = 1, d xi / d half = (xi - centre) / half */
+                    gc[3 * t + d] += c * gg[d];
+                    gh[3 * t + d] += c * gg[d] * (xt[d] - ct[d]) / htt[d];
+                    gc[3 * s + d] -= c * gg[d];
+                    gh[3 * s + d] -= c * gg[d] * (xs[d] - cs[d]) / hs[d];
+                }
+            }
+        }
+    }
+    /* transfers: L contains sum E_c'[nu',nu] (xh_c'[nu'] zh_p[nu] + wh_c'[nu'] yh_p[nu]) */
+    for (int64_t c = 1; c < nc; ++c) {
+        int64_t p = T->parent[c];
+        const double* zc = H->nodes + c * 3 * m;
+        const double* zp = H->nodes + p * 3 * m;
+        double cc[3], hc[3], cp[3], hp[3];
+        int fl[3], am;
+        box_ch(T, c, cc, hc, fl, &am);
+        box_ch(T, p, cp, hp, fl, &am);
+        for (int nup = 0; nup < k; ++nup) {
+            double xi[3] = {zc[nup % m], zc[m + (nup / m) % m], zc[2 * m + nup / (m * m)]};
+            for (int nu = 0; nu < k; ++nu) {
+                double M = 0.0;
+                for (int r = 0; r < nrhs; ++r)
+                    M += xh[(c * k + nup) * nrhs + r] * zh[(p * k + nu) * nrhs + r] +
+                         wh[(c * k + nup) * nrhs + r] * yh[(p * k + nu) * nrhs + r];
+                double gl[3];
+                tensor_lagrange_grad(zp, m, nu, xi, gl);
+                for (int d = 0; d < 3; ++d) {
+                    gc[3 * c + d] += M * gl[d];
+                    gh[3 * c + d] += M * gl[d] * (xi[d] - cc[d]) / hc[d];
+                    gc[3 * p + d] -= M * gl[d];
+                    gh[3 * p + d] -= M * gl[d] * (xi[d] - cp[d]) / hp[d];
+                }
+            }
+        }
+    }
+    /* leaf bases: L contains sum_i sum_nu V_c[i,nu] (x_i zh_c[nu] + w_i yh_c[nu]) */
+    double ruv[2 * 64 * 64], rw[64 * 64];
+    int np = or_collapsed_rule(H->qb, ruv, rw);
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        const double* z = H->nodes + c * 3 * m;
+        double cc[3], hc[3];
+        int fl[3], am;
+        box_ch(T, c, cc, hc, fl, &am);
+        for (int64_t a = T->begin[c]; a < T->end[c]; ++a) {
+            int64_t i = T->perm[a];
+            double beta[512];
+            for (int nu = 0; nu < k; ++nu) {
+                double bsum = 0.0;
+                for (int r = 0; r < nrhs; ++r)
+                    bsum += x[i + r * n] * zh[(c * k + nu) * nrhs + r] + w[i + r * n] * yh[(c * k + nu) * nrhs + r];
+                beta[nu] = bsum;
+            }
+            double X[9], area, nrm[3], dA[9];
+            tri_vertices(&H->mesh, i, X);
+            or_tri_geom(X, X + 3, X + 6, &area, nrm);
+            area_grad(X, dA);
+            double Psum = 0.0, gv[3][3] = {{0}};
+            for (int pp = 0; pp < np; ++pp) {
+                double y[3];
+                for (int d = 0; d < 3; ++d)
+                    y[d] = X[d] + ruv[2 * pp] * (X[3 + d] - X[d]) + ruv[2 * pp + 1] * (X[6 + d] - X[d]);
+                double P = 0.0, gP[3] = {0, 0, 0};
+                for (int nu = 0; nu < k; ++nu) {
+                    double gl[3];
+                    P += beta[nu] * tensor_lagrange(z, m, nu, y);
+                    tensor_lagrange_grad(z, m, nu, y, gl);
+                    for (int d = 0; d < 3; ++d) gP[d] += beta[nu] * gl[d];
+                }
+                Psum += rw[pp] * P;
+                double lam[3] = {1.0 - ruv[2 * pp] - ruv[2 * pp + 1], ruv[2 * pp], ruv[2 * pp + 1]};
+                for (int kk = 0; kk < 3; ++kk)
+                    for (int d = 0; d < 3; ++d) gv[kk][d] += rw[pp] * lam[kk] * gP[d];
+                for (int d = 0; d < 3; ++d) {
+                    gc[3 * c + d] -= area * rw[pp] * gP[d];
+                    gh[3 * c + d] -= area * rw[pp] * gP[d] * (y[d] - cc[d]) / hc[d];
+                }
+            }
+            for (int kk = 0; kk < 3; ++kk) {
+                double v[3];
+                for (int d = 0; d < 3; ++d) v[d] = dA[3 * kk + d] * Psum + area * gv[kk][d];
+                add_vertex(gX, H->tri[3 * i + kk], v, 1.0);
+            }
+        }
+    }
+    /* boxes -> bounding-box extremes -> vertices */
+    for (int64_t c = 0; c < nc; ++c) {
+        double cc[3], hc[3];
+        int fl[3], am;
+        box_ch(T, c, cc, hc, fl, &am);
+        double glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+            glo[d] += 0.5 * gc[3 * c + d];
+            ghi[d] += 0.5 * gc[3 * c + d];
+            int e = fl[d] ? am : d;
+            double f = fl[d] ? 1e-2 : 1.0;
+            glo[e] -= 0.5 * f * gh[3 * c + d];
+            ghi[e] += 0.5 * f * gh[3 * c + d];
+        }
+        /* the vertex realising each extreme: first in traversal order (as tree_box) */
+        for (int d = 0; d < 3; ++d) {
+            double lo = INFINITY, hi = -INFINITY;
+            int32_t vlo = -1, vhi = -1;
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a)
+                for (int q = 0; q < 3; ++q) {
+                    int32_t v = H->tri[3 * T->perm[a] + q];
+                    double val = H->xyz[3 * (int64_t)v + d];
+                    if (val < lo) { lo = val; vlo = v; }
+                    if (val > hi) { hi = val; vhi = v; }
+                }
+            gX[3 * (int64_t)vlo + d] += glo[d];
+            gX[3 * (int64_t)vhi + d] += ghi[d];
+        }
+    }
+    free(gc); free(gh); free(S); free(xh); free(wh); free(yh); free(zh);
+    return 0;
 }
