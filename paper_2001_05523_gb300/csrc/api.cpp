@@ -445,7 +445,8 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
 // factors (see k_sing.cu).  Rows: identical [aa, 2ab, bb, W]; edge [6 Gram
 // monomials, alpha, beta, gamma, W_g, W_dg]; vertex: the 1-D Gauss rule
 // [x_k, w_k] (the kernel forms the factorised triple sum).
-void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vector<double>& tv) {
+void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vector<double>& tv,
+               std::vector<double>& tvg) {
     std::vector<double> x, w;
     gauss_legendre(q, x, w);
     ti.clear();
@@ -479,6 +480,20 @@ void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vec
             }
     // vertex: the 1-D rule itself (x_k, w_k); the kernel forms the factorised sums
     for (int k = 0; k < q; ++k) tv.insert(tv.end(), {x[k], w[k]});
+    // vertex, Gram form for the shape gradient: (alpha, beta, gamma, delta) for
+    // vectors (P1-P0, P2-P1, Q1-Q0, Q2-Q1); rows [10 Gram monomials, W_g]
+    tvg.clear();
+    for (int r = 0; r < 2; ++r)
+        for (int i = 0; i < q; ++i)
+            for (int k = 0; k < q; ++k)
+                for (int l = 0; l < q; ++l) {
+                    const double e1 = x[i], e2 = x[k], e3 = x[l], ww = w[i] * w[k] * w[l];
+                    double al, be, ga, de;
+                    if (r == 0) { al = 1.0; be = e1; ga = -e2; de = -e2 * e3; }
+                    else { al = e2; be = e2 * e3; ga = -1.0; de = -e1; }
+                    tvg.insert(tvg.end(), {al * al, be * be, ga * ga, de * de, 2 * al * be, 2 * al * ga, 2 * al * de,
+                                           2 * be * ga, 2 * be * de, 2 * ga * de, ww * e2 / 3.0});
+                }
 }
 
 }  // namespace
@@ -552,7 +567,7 @@ static void make_csr(int64_t nkeys, const std::vector<int64_t>& key, const std::
 struct h2bem_op {
     int kernel = 0, m = 0, k = 0, precision = 0, q_ss = 5, cache_singular = 0;
     double eta = 0;
-    int64_t n = 0, nc = 0, nleaves = 0, depth = 0;
+    int64_t n = 0, nv = 0, nc = 0, nleaves = 0, depth = 0;
     int64_t nfar = 0, nnear = 0, near_pairs = 0, sing[3] = {0, 0, 0};
     h2::Consts consts{};
     // device geometry and tree
@@ -563,7 +578,13 @@ struct h2bem_op {
     std::vector<DevBuf> dlevel;
     Csr far, far_t, near, near_t;
     // singular pairs by type (index 0: identical, 1: edge, 2: vertex)
-    DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3];
+    DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3], sp_gtab;
+    int sp_gnpts = 0;
+    // shape gradient: per-cluster extreme vertices and floor flags, child list
+    DevBuf cext, cflag, children, parent;
+    int nchildren = 0;
+    DevBuf g_xp, g_wp, g_xh, g_wh, g_yh, g_zh, g_dbox;
+    int g_NR = 0;
     int sp_npts[3] = {0, 0, 0};
     int64_t sp_count[3] = {0, 0, 0};
     // workspace
@@ -719,6 +740,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->cache_singular = opts.cache_singular ? 1 : 0;
     op->use_graph = opts.use_graph ? 1 : 0;
     op->n = mesh->nt;
+    op->nv = mesh->nv;
     op->nc = tree->nc;
     op->depth = tree->depth;
     const int64_t n = op->n, nc = op->nc;
@@ -814,8 +836,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     std::vector<int64_t> slo[3], shi[3];
     std::vector<int> scode[3];
     singular_pairs(*mesh, slo, shi, scode);
-    std::vector<double> tabs[3];
-    ss_tables(op->q_ss, tabs[0], tabs[1], tabs[2]);
+    std::vector<double> tabs[3], tvg;
+    ss_tables(op->q_ss, tabs[0], tabs[1], tabs[2], tvg);
     const int widths[3] = {4, 11, 2};
 
     int rc;
@@ -843,6 +865,48 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         if ((rc = upload(op->sp_lo[t], lo)) || (rc = upload(op->sp_hi[t], hi)) || (rc = upload(op->sp_code[t], scode[t])) ||
             (rc = upload(op->sp_tab[t], tabs[t])))
             return rc;
+    }
+    // shape-gradient data: vertex realising each bounding-box extreme (first in
+    // the cluster's triangle order, corners in order), floored axes, the axis
+    // of the largest half-width, children and parents
+    {
+        std::vector<int> cext(6 * nc), cflag(nc), ch, par(nc, -1);
+        for (int64_t c = 0; c < nc; ++c) {
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            int vlo[3] = {0, 0, 0}, vhi[3] = {0, 0, 0};
+            for (int64_t a = tree->begin[c]; a < tree->end[c]; ++a)
+                for (int q = 0; q < 3; ++q) {
+                    const int32_t v = mesh->tri[3 * tree->perm[a] + q];
+                    for (int d = 0; d < 3; ++d) {
+                        const double val = mesh->xyz[3 * (int64_t)v + d];
+                        if (val < lo[d]) { lo[d] = val; vlo[d] = v; }
+                        if (val > hi[d]) { hi[d] = val; vhi[d] = v; }
+                    }
+                }
+            double h[3], hmax = 0.0;
+            int am = 0;
+            for (int d = 0; d < 3; ++d) {
+                cext[d * nc + c] = vlo[d];
+                cext[(3 + d) * nc + c] = vhi[d];
+                h[d] = 0.5 * (tree->bmax[3 * c + d] - tree->bmin[3 * c + d]);
+                if (h[d] > hmax) { hmax = h[d]; am = d; }
+            }
+            int fl = am << 3;
+            for (int d = 0; d < 3; ++d)
+                if (h[d] < 1e-2 * hmax) fl |= 1 << d;
+            cflag[c] = fl;
+            if (tree->child0[c] >= 0) {
+                ch.push_back((int)tree->child0[c]);
+                ch.push_back((int)tree->child1[c]);
+                par[tree->child0[c]] = par[tree->child1[c]] = (int)c;
+            }
+        }
+        op->nchildren = (int)ch.size();
+        int rc2;
+        if ((rc2 = upload(op->cext, cext)) || (rc2 = upload(op->cflag, cflag)) || (rc2 = upload(op->children, ch)) ||
+            (rc2 = upload(op->parent, par)) || (rc2 = upload(op->sp_gtab, tvg)))
+            return rc2;
+        op->sp_gnpts = (int)(tvg.size() / 11);
     }
     // geometry in tree order
     if ((rc = op->v.alloc(9 * n * sizeof(double))) || (rc = op->area.alloc(n * sizeof(double))) ||
@@ -1206,6 +1270,87 @@ extern "C" int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx,
 extern "C" int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
                                  void* stream) {
     return apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, true);
+}
+
+// ===========================================================================
+// shape gradient (single layer, FP64)
+// ===========================================================================
+extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz,
+                          double* dx, void* stream) {
+    if (!op || !w || !x || !dxyz) return fail(H2BEM_ERR_ARG, "grad: NULL argument");
+    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "grad: the shape gradient is available for the single layer");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "grad: nrhs must be in 1..64");
+    if (ld < op->n) return fail(H2BEM_ERR_ARG, "grad: leading dimension must be >= n");
+    if (!is_device_ptr(w) || !is_device_ptr(x) || !is_device_ptr(dxyz) || (dx && !is_device_ptr(dx)))
+        return fail(H2BEM_ERR_ARG, "grad: all vectors must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)op->n, nc = (int)op->nc, k = op->k;
+    const int NRmax = pad_nr(std::min(nrhs, 16));
+    if (op->g_NR < NRmax) {
+        int rc;
+        const size_t hv = (size_t)nc * k * NRmax * sizeof(double);
+        if ((rc = op->g_xp.alloc((size_t)n * NRmax * sizeof(double))) ||
+            (rc = op->g_wp.alloc((size_t)n * NRmax * sizeof(double))) || (rc = op->g_xh.alloc(hv)) ||
+            (rc = op->g_wh.alloc(hv)) || (rc = op->g_yh.alloc(hv)) || (rc = op->g_zh.alloc(hv)) ||
+            (rc = op->g_dbox.alloc((size_t)6 * nc * sizeof(double))))
+            return rc;
+        op->g_NR = NRmax;
+    }
+    CU(cudaMemsetAsync(dxyz, 0, op->nv * 3 * sizeof(double), s));
+    const h2::Geom g = op->geom();
+    const h2::Tree t = op->tree();
+    const h2::Consts& c = op->consts;
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+        const int nr = std::min(16, nrhs - c0), NR = pad_nr(nr);
+        double *xp = op->g_xp.as<double>(), *wp = op->g_wp.as<double>();
+        double *xh = op->g_xh.as<double>(), *wh = op->g_wh.as<double>();
+        double *yh = op->g_yh.as<double>(), *zh = op->g_zh.as<double>(), *dbox = op->g_dbox.as<double>();
+        h2::launch_permute_in(x + c0 * ld, ld, nr, NR, op->perm.as<int>(), n, xp, s);
+        h2::launch_permute_in(w + c0 * ld, ld, nr, NR, op->perm.as<int>(), n, wp, s);
+        if (op->nfar > 0) {
+            const size_t hv = (size_t)nc * k * NR * sizeof(double);
+            h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
+                                    false, true, NR, xp, xh, s);
+            h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
+                                    false, true, NR, wp, wh, s);
+            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L) {
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, xh, s);
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, wh, s);
+            }
+            CU(cudaMemsetAsync(yh, 0, hv, s));
+            CU(cudaMemsetAsync(zh, 0, hv, s));
+            h2::launch_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(),
+                                op->far.dcol.as<int>(), 0, true, true, NR, xh, yh, s);
+            h2::launch_coupling(t, c, op->far_t.nrows(), op->far_t.drows.as<int>(), op->far_t.dptr.as<int>(),
+                                op->far_t.dcol.as<int>(), 0, true, true, NR, wh, zh, s);
+            for (size_t L = 0; L < op->level_parents.size(); ++L) {
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, yh, s);
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, zh, s);
+            }
+            CU(cudaMemsetAsync(dbox, 0, (size_t)6 * nc * sizeof(double), s));
+            h2::launch_grad_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(),
+                                     op->far.dcol.as<int>(), NR, wh, xh, dbox, s);
+            h2::launch_grad_transfer(t, c, op->nchildren, op->children.as<int>(), op->parent.as<int>(), NR, xh, wh, yh,
+                                     zh, dbox, s);
+            h2::launch_grad_leaf(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), NR, xp,
+                                 wp, yh, zh, dbox, dxyz, s);
+            h2::launch_grad_box(nc, op->cext.as<int>(), op->cflag.as<int>(), dbox, dxyz, s);
+        }
+        h2::launch_grad_near(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+                             op->near.dcol.as<int>(), NR, xp, wp, dxyz, s);
+        for (int ty = 0; ty < 3; ++ty) {
+            const double* tab = ty == 2 ? op->sp_gtab.as<double>() : op->sp_tab[ty].as<double>();
+            const int npts = ty == 2 ? op->sp_gnpts : op->sp_npts[ty];
+            h2::launch_grad_singular(g, h2::IDENTICAL - ty, (int)op->sp_count[ty], op->sp_lo[ty].as<int>(),
+                                     op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), tab, npts, NR, xp, wp, dxyz, s);
+        }
+        CU(cudaGetLastError());
+    }
+    if (dx) {
+        int rc = apply_impl(op, w, ld, nrhs, dx, ld, stream, true, false);
+        if (rc) return rc;
+    }
+    return H2BEM_OK;
 }
 
 // ===========================================================================

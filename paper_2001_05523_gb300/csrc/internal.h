@@ -91,6 +91,25 @@ void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows,
 
 }  // namespace h2
 
+namespace h2 {
+// shape gradient (single layer, FP64), k_grad.cu
+void launch_grad_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                          int NR, const double* wh, const double* xh, double* dbox, cudaStream_t s);
+void launch_grad_transfer(const Tree& t, const Consts& c, int nch, const int* children, const int* parent, int NR,
+                          const double* xh, const double* wh, const double* yh, const double* zh, double* dbox,
+                          cudaStream_t s);
+void launch_grad_leaf(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl, const int* leaves,
+                      int NR, const double* xp, const double* wp, const double* yh, const double* zh, double* dbox,
+                      double* dX, cudaStream_t s);
+void launch_grad_near(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                      const int* col, int NR, const double* xp, const double* wp, double* dX, cudaStream_t s);
+void launch_grad_singular(const Geom& g, int type, int npairs, const int* lo, const int* hi, const int* code,
+                          const double* tab, int npts, int NR, const double* xp, const double* wp, double* dX,
+                          cudaStream_t s);
+void launch_grad_box(int nc, const int* cext, const int* cflag, const double* dbox, double* dX, cudaStream_t s);
+
+}  // namespace h2
+
 struct h2bem_op;
 namespace h2 {
 // Used by the allocation-free entry point (noalloc.cu).

@@ -27,7 +27,7 @@ EXPORTED = [
     "h2bem_last_error", "h2bem_mesh_create", "h2bem_mesh_destroy", "h2bem_tree_build", "h2bem_tree_upload",
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
-    "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create",
+    "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad",
 ]
 
 
@@ -88,6 +88,7 @@ def lib():
             "h2bem_apply_timed": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_apply_noalloc": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_batch_create": [i32, vp, i32, i32, i32, d, vp, pp],
+            "h2bem_grad": [vp, vp, vp, i64, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -235,6 +236,16 @@ def h2bem_apply(op, x, y, stream=None):
 def h2bem_apply_transpose(op, x, y, stream=None):
     px, lx, nr, py, ly = _vec_args(x, y)
     _check(lib().h2bem_apply_transpose(op, px, lx, nr, py, ly, _stream(stream)))
+
+
+def h2bem_grad(op, w, x, dxyz, dx=None, stream=None):
+    """dxyz (nv, 3) = d/dX sum_r <w_r, G x_r>; optional dx = G^T w.  Device tensors."""
+    pw, lw, nw, px, lx = _vec_args(w, x)
+    if lw != lx:
+        raise ValueError("w and x must have the same shape")
+    pd = ctypes.c_void_p(dxyz.data_ptr())
+    pdx = ctypes.c_void_p(dx.data_ptr()) if dx is not None else None
+    _check(lib().h2bem_grad(op, pw, px, lx, nw, pd, pdx, _stream(stream)))
 
 
 def h2bem_apply_noalloc(op, x, y, stream=None):
