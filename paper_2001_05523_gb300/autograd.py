@@ -31,6 +31,39 @@ class H2Apply(torch.autograd.Function):
         return gx, None
 
 
+class H2ApplyShape(torch.autograd.Function):
+    """y = G(X) x, differentiable in x and in the vertex coordinates X (single
+    layer; the operator's cluster tree and block lists stay fixed).  The
+    backward pass returns G^T g for x and, for X, the shape gradient
+    d<g, G(X) x>/dX from h2bem_grad."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, vertices: torch.Tensor, op) -> torch.Tensor:
+        xc = x.contiguous()
+        y = torch.empty_like(xc)
+        H.h2bem_apply(op.op, xc, y)
+        ctx.op = op
+        ctx.save_for_backward(xc, vertices)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy: torch.Tensor):
+        xc, vertices = ctx.saved_tensors
+        g = gy.contiguous()
+        gx = torch.empty_like(g)
+        gX = torch.empty((vertices.shape[0], 3), dtype=torch.float64, device=g.device)
+        H.h2bem_grad(ctx.op.op, g, xc, gX, gx)
+        return gx, gX.to(vertices.dtype), None
+
+
+def h2_apply_shape(x: torch.Tensor, vertices: torch.Tensor, op) -> torch.Tensor:
+    """Differentiable y = G(X) x in x and X; `op` must have been built from the
+    values of `vertices` (shape (nv, 3))."""
+    if x.dim() == 1:
+        return H2ApplyShape.apply(x[None, :], vertices, op)[0]
+    return H2ApplyShape.apply(x, vertices, op)
+
+
 def h2_apply(x: torch.Tensor, op: "H.Operator") -> torch.Tensor:
     """Differentiable y = A x; x of shape (nrhs, n) or (n,)."""
     if x.dim() == 1:

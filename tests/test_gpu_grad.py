@@ -62,3 +62,32 @@ def test_shape_gradient_rejects_double_layer(H):
     with pytest.raises(H.H2bemError):
         H.h2bem_grad(op.op, z, z, g)
     op.close()
+
+
+def test_autograd_shape_and_batch(H, orc):
+    """The autograd wrapper returns G^T g and the shape gradient; on a batch of
+    meshes (one block-diagonal operator) the gradient equals the per-mesh
+    gradients."""
+    import torch
+
+    from paper_2001_05523_gb300 import autograd as A
+
+    meshes = [I.jitter(I.sphere(6), 0.02, 41), I.jitter(I.cube(5), 0.02, 42), I.jitter(I.ellipsoid(7), 0.02, 43)]
+    B = H.BatchOperator(meshes, kernel=0, m=3, leaf_size=8)
+    V = torch.from_numpy(np.concatenate([mm.vertices for mm in meshes])).cuda().requires_grad_(True)
+    x = torch.from_numpy(I.rhs(B.n, 2, seed=5)).cuda().requires_grad_(True)
+    w = torch.from_numpy(I.rhs(B.n, 2, seed=6)).cuda()
+    loss = (w * A.h2_apply_shape(x, V, B)).sum()
+    loss.backward()
+    gV = V.grad.cpu().numpy()
+    gx = x.grad.cpu().numpy()
+    voff = 0
+    for b, mesh in enumerate(meshes):
+        lo, hi = int(B.offsets[b]), int(B.offsets[b + 1])
+        Ho = orc.H2(mesh, 0, m=3, leaf=8)
+        ref = Ho.grad_vertices(w[:, lo:hi].cpu().numpy(), x[:, lo:hi].detach().cpu().numpy())
+        assert np.abs(gV[voff:voff + mesh.nv] - ref).max() <= 1e-10 * np.abs(ref).max()
+        refx = Ho.matvec(w[:, lo:hi].cpu().numpy(), transpose=True)
+        assert np.linalg.norm(gx[:, lo:hi] - refx) / np.linalg.norm(refx) < 1e-10
+        voff += mesh.nv
+    B.close()
