@@ -286,6 +286,54 @@ def main():
                                          "stage_ms": [round(v, 3) for v in stage_dc]}
         extra["speedup_mixed_vs_fp64_cached"] = ms_dc / ms_c
 
+    # other workloads of the benchmark family (reported beside the headline)
+    if not args.no_fp64:
+        # 64 uneven jittered meshes (sphere / ellipsoid / cube, 2k-65k triangles) as one
+        # block-diagonal operator: forward SLP apply and gradients in x and the vertices
+        fam = I.batch_meshes(64)
+        Bop = H.BatchOperator(fam, kernel="slp", m=4, eta=2.0, leaf_size=32, precision="fp64")
+        xb = torch.from_numpy(I.rhs(Bop.n, 1, seed=3)).to(dev)
+        wb = torch.from_numpy(I.rhs(Bop.n, 1, seed=4)).to(dev)
+        yb = torch.empty_like(xb)
+        gX = torch.empty((sum(mm.nv for mm in fam), 3), dtype=torch.float64, device=dev)
+        gx = torch.empty_like(xb)
+        for _ in range(2):
+            H.h2bem_apply(Bop.op, xb, yb, stream)
+            H.h2bem_grad(Bop.op, wb, xb, gX, gx, stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        H.h2bem_apply(Bop.op, xb, yb, stream)
+        ev[1].record(stream)
+        H.h2bem_grad(Bop.op, wb, xb, gX, gx, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        extra["batch64_fp64"] = {"meshes": len(fam), "triangles": Bop.n,
+                                 "apply_ms": ev[0].elapsed_time(ev[1]), "grad_x_and_vertices_ms": ev[1].elapsed_time(ev[2]),
+                                 "apply_triangles_per_s": Bop.n / (ev[0].elapsed_time(ev[1]) / 1e3)}
+        Bop.close()
+        # ellipsoid (1, 0.5, 0.25), 131,072 triangles, m = 5, 16 right-hand sides
+        me = I.ellipsoid(128)
+        xe = torch.from_numpy(I.rhs(me.nt, 16, seed=5)).to(dev)
+        out_e = {}
+        for prec in ("mixed_fp32", "fp64"):
+            oe = H.Operator(me.vertices, me.triangles, kernel="slp", m=5, eta=2.0, precision=prec)
+            ye = torch.empty_like(xe)
+            for _ in range(2):
+                H.h2bem_apply(oe.op, xe, ye, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            H.h2bem_apply(oe.op, xe, ye, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out_e[prec] = (e0.elapsed_time(e1), ye.clone())
+            oe.close()
+        out = {p_: {"ms": v[0], "triangles_rhs_per_s": me.nt * 16 / (v[0] / 1e3)} for p_, v in out_e.items()}
+        out["rel_err_mixed_vs_fp64"] = float(torch.linalg.norm(out_e["mixed_fp32"][1] - out_e["fp64"][1]) /
+                                             torch.linalg.norm(out_e["fp64"][1]))
+        extra["ellipsoid131k_m5_16rhs"] = out
+
     # roofline of the dominant kernel of the headline tier
     pk = peaks()
     names = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_backward", "near_regular",

@@ -446,7 +446,7 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
 // monomials, alpha, beta, gamma, W_g, W_dg]; vertex: the 1-D Gauss rule
 // [x_k, w_k] (the kernel forms the factorised triple sum).
 void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vector<double>& tv,
-               std::vector<double>& tvg) {
+               std::vector<double>& tvg, std::vector<double>& te1) {
     std::vector<double> x, w;
     gauss_legendre(q, x, w);
     ti.clear();
@@ -478,8 +478,11 @@ void ss_tables(int q, std::vector<double>& ti, std::vector<double>& te, std::vec
                 te.insert(te.end(), {al * al, be * be, ga * ga, 2 * al * be, 2 * al * ga, 2 * be * ga, al, be, ga,
                                      ww * f / 6.0, ww * f / 2.0});
             }
-    // vertex: the 1-D rule itself (x_k, w_k); the kernel forms the factorised sums
-    for (int k = 0; k < q; ++k) tv.insert(tv.end(), {x[k], w[k]});
+    // vertex: the 1-D rule (x_k, w_k, w_k x_k / 2); the kernel forms the factorised sums
+    for (int k = 0; k < q; ++k) tv.insert(tv.end(), {x[k], w[k], 0.5 * w[k] * x[k]});
+    // edge: the 1-D rule (x_k, w_k, w_k / 2, w_k x_k / 2) for the factorised sums
+    te1.clear();
+    for (int k = 0; k < q; ++k) te1.insert(te1.end(), {x[k], w[k], 0.5 * w[k], 0.5 * w[k] * x[k]});
     // vertex, Gram form for the shape gradient: (alpha, beta, gamma, delta) for
     // vectors (P1-P0, P2-P1, Q1-Q0, Q2-Q1); rows [10 Gram monomials, W_g]
     tvg.clear();
@@ -578,8 +581,8 @@ struct h2bem_op {
     std::vector<DevBuf> dlevel;
     Csr far, far_t, near, near_t;
     // singular pairs by type (index 0: identical, 1: edge, 2: vertex)
-    DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3], sp_gtab;
-    int sp_gnpts = 0;
+    DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3], sp_gtab, sp_gtab_edge;
+    int sp_gnpts = 0, sp_gnpts_edge = 0;
     // shape gradient: per-cluster extreme vertices and floor flags, child list
     DevBuf cext, cflag, children, parent;
     int nchildren = 0;
@@ -836,9 +839,10 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     std::vector<int64_t> slo[3], shi[3];
     std::vector<int> scode[3];
     singular_pairs(*mesh, slo, shi, scode);
-    std::vector<double> tabs[3], tvg;
-    ss_tables(op->q_ss, tabs[0], tabs[1], tabs[2], tvg);
-    const int widths[3] = {4, 11, 2};
+    std::vector<double> tabs[3], tvg, tgram_edge, te1;
+    ss_tables(op->q_ss, tabs[0], tgram_edge, tabs[2], tvg, te1);
+    tabs[1] = te1;
+    const int widths[3] = {4, 4, 3};
 
     int rc;
     if ((rc = upload(op->xyz, mesh->xyz)) || (rc = upload(op->tri, std::vector<int>(mesh->tri.begin(), mesh->tri.end()))) ||
@@ -904,9 +908,11 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         op->nchildren = (int)ch.size();
         int rc2;
         if ((rc2 = upload(op->cext, cext)) || (rc2 = upload(op->cflag, cflag)) || (rc2 = upload(op->children, ch)) ||
-            (rc2 = upload(op->parent, par)) || (rc2 = upload(op->sp_gtab, tvg)))
+            (rc2 = upload(op->parent, par)) || (rc2 = upload(op->sp_gtab, tvg)) ||
+            (rc2 = upload(op->sp_gtab_edge, tgram_edge)))
             return rc2;
         op->sp_gnpts = (int)(tvg.size() / 11);
+        op->sp_gnpts_edge = (int)(tgram_edge.size() / 11);
     }
     // geometry in tree order
     if ((rc = op->v.alloc(9 * n * sizeof(double))) || (rc = op->area.alloc(n * sizeof(double))) ||
@@ -1339,8 +1345,9 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
         h2::launch_grad_near(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
                              op->near.dcol.as<int>(), NR, xp, wp, dxyz, s);
         for (int ty = 0; ty < 3; ++ty) {
-            const double* tab = ty == 2 ? op->sp_gtab.as<double>() : op->sp_tab[ty].as<double>();
-            const int npts = ty == 2 ? op->sp_gnpts : op->sp_npts[ty];
+            const double* tab = ty == 2 ? op->sp_gtab.as<double>()
+                                : ty == 1 ? op->sp_gtab_edge.as<double>() : op->sp_tab[ty].as<double>();
+            const int npts = ty == 2 ? op->sp_gnpts : ty == 1 ? op->sp_gnpts_edge : op->sp_npts[ty];
             h2::launch_grad_singular(g, h2::IDENTICAL - ty, (int)op->sp_count[ty], op->sp_lo[ty].as<int>(),
                                      op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), tab, npts, NR, xp, wp, dxyz, s);
         }

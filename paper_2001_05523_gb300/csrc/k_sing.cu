@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                                                        const double* __restrict__ tab, int npts, bool transpose,
                                                        const double* __restrict__ xp, double* __restrict__ yp,
                                                        double* __restrict__ val0, double* __restrict__ val1) {
-    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 2;  // doubles per table point
+    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;  // doubles per table point
     extern __shared__ double stab[];
     if (MODE != 2) {
         for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
@@ -91,30 +91,72 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
             }
             a01 = a10 = sc * s;
         } else if (TYPE == EDGE) {
-            // vectors (a, b, d) for coefficients (alpha, beta, gamma)
-            const double G0 = dot(ea, ea), G1 = dot(eb, eb), G2 = dot(ed, ed);
-            const double G3 = dot(ea, eb), G4 = dot(ea, ed), G5 = dot(eb, ed);
+            // vectors (a, b, d); stab holds (x_k, w_k, w_k / 2, w_k x_k / 2), npts = q.
+            // Region r: w = F(o) + t G(o) with the outer variable o and the inner t;
+            // coefficient triples over (a, b, d):
+            //   R1 (o = e2, t = e3, weight w_t):     F = (o, 0, o - 1),  G = (0, 1, 0)
+            //   R2 (o = e3, t = e2, weight w_t t):   F = (0, 1, 0),      G = (o, 0, o - 1)
+            //   R3:                                  F = (0, 1, 0),      G = (-1, -1, -o)
+            //   R4:                                  F = (0, 0, -1),     G = (-o, 1 - o, 0)
+            //   R5:                                  F = (0, 1, 0),      G = (-o, -o, -1)
+            const double Gm[3][3] = {{dot(ea, ea), dot(ea, eb), dot(ea, ed)},
+                                     {dot(ea, eb), dot(eb, eb), dot(eb, ed)},
+                                     {dot(ea, ed), dot(eb, ed), dot(ed, ed)}};
+            const int q = npts;
+            double s = 0.0, sa = 0.0, sb = 0.0, sd = 0.0;
+            for (int reg = 0; reg < 5; ++reg) {
+                for (int oi = 0; oi < q; ++oi) {
+                    const double o = stab[4 * oi], wo = stab[4 * oi + 1];
+                    double F[3], Gv[3];
+                    switch (reg) {
+                        case 0: F[0] = o; F[1] = 0.0; F[2] = o - 1.0; Gv[0] = 0.0; Gv[1] = 1.0; Gv[2] = 0.0; break;
+                        case 1: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = o; Gv[1] = 0.0; Gv[2] = o - 1.0; break;
+                        case 2: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = -1.0; Gv[1] = -1.0; Gv[2] = -o; break;
+                        case 3: F[0] = 0.0; F[1] = 0.0; F[2] = -1.0; Gv[0] = -o; Gv[1] = 1.0 - o; Gv[2] = 0.0; break;
+                        default: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = -o; Gv[1] = -o; Gv[2] = -1.0; break;
+                    }
+                    double A = 0.0, B2 = 0.0, Cc = 0.0;
+                    for (int u = 0; u < 3; ++u)
+                        for (int v = 0; v < 3; ++v) {
+                            A += F[u] * Gm[u][v] * F[v];
+                            B2 += F[u] * Gm[u][v] * Gv[v];
+                            Cc += Gv[u] * Gm[u][v] * Gv[v];
+                        }
+                    B2 *= 2.0;
+                    double f0 = 0.0, f1 = 0.0;
+                    for (int k = 0; k < q; ++k) {
+                        const double tt = stab[4 * k];
+                        const double r2 = fma(tt, fma(tt, Cc, B2), A);
+                        if (KER == SLP) {
+                            // w_t / 2 (R1) or w_t t / 2 (R2-R5) times y (3 - r2 y^2): one Newton step folded in
+                            const double hw = reg == 0 ? stab[4 * k + 2] : stab[4 * k + 3];
+                            double y;
+                            asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
+                            const double tq = r2 * y;
+                            f0 = fma(hw * y, fma(-tq, y, 3.0), f0);
+                        } else {
+                            const double wt = reg == 0 ? stab[4 * k + 1] : 2.0 * stab[4 * k + 3];
+                            const double ri = rsqrt_nr(r2);
+                            const double f = wt * (ri * ri * ri);
+                            f0 += f;
+                            f1 = fma(f, tt, f1);
+                        }
+                    }
+                    if (KER == SLP) {
+                        s = fma(wo, f0, s);
+                    } else {
+                        // sum f w = f0 F + f1 G over (a, b, d)
+                        sa += wo * (f0 * F[0] + f1 * Gv[0]);
+                        sb += wo * (f0 * F[1] + f1 * Gv[1]);
+                        sd += wo * (f0 * F[2] + f1 * Gv[2]);
+                    }
+                }
+            }
             if (KER == SLP) {
-                double s = 0.0;
-                for (int p = 0; p < npts; ++p) {
-                    const double* T = stab + p * W;
-                    const double r2 = T[0] * G0 + T[1] * G1 + T[2] * G2 + T[3] * G3 + T[4] * G4 + T[5] * G5;
-                    s += T[9] * rsqrt_nr(r2);
-                }
-                a01 = a10 = sc * s;
+                a01 = a10 = sc * s / 6.0;
             } else {
-                double sa = 0.0, sb = 0.0, sd = 0.0;
-                for (int p = 0; p < npts; ++p) {
-                    const double* T = stab + p * W;
-                    const double r2 = T[0] * G0 + T[1] * G1 + T[2] * G2 + T[3] * G3 + T[4] * G4 + T[5] * G5;
-                    const double ri = rsqrt_nr(r2);
-                    const double f = T[10] * ri * ri * ri;
-                    sa += f * T[6];
-                    sb += f * T[7];
-                    sd += f * T[8];
-                }
                 double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = sa * ea[d] + sb * eb[d] + sd * ed[d];
+                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
                 double nlo[3], nhi[3];
                 for (int d = 0; d < 3; ++d) {
                     nlo[d] = g.nrm[d * g.n + lo];
@@ -123,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 a01 = sc * dot(V, nhi);
                 a10 = -sc * dot(V, nlo);
             }
-        } else {  // VERTEX: vectors (a, b, c, d); stab holds the 1-D Gauss rule (x_k, w_k), npts = q
+        } else {  // VERTEX: vectors (a, b, c, d); stab holds (x_k, w_k, w_k x_k / 2), npts = q
             const double aa = dot(ea, ea), bb = dot(eb, eb), cc = dot(ec, ec), dd = dot(ed, ed);
             const double ab = dot(ea, eb), ac = dot(ea, ec), ad = dot(ea, ed), bc = dot(eb, ec), bd = dot(eb, ed),
                          cd = dot(ec, ed);
@@ -135,22 +177,26 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 const double pp = reg == 0 ? cc : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? dd : bb;
                 const double b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
                 for (int i = 0; i < q; ++i) {
-                    const double e1 = stab[2 * i], w1 = stab[2 * i + 1];
+                    const double e1 = stab[3 * i], w1 = stab[3 * i + 1];
                     const double A = fma(e1, fma(e1, vv2, 2.0 * uv2), uu);
                     const double Bi0 = fma(e1, b2, b0), Bi1 = fma(e1, bd, b1);
                     for (int l = 0; l < q; ++l) {
-                        const double e3 = stab[2 * l], w3 = stab[2 * l + 1];
+                        const double e3 = stab[3 * l], w3 = stab[3 * l + 1];
                         const double Cc = fma(e3, fma(e3, qq2, 2.0 * pq2), pp);
                         const double m2B = -2.0 * fma(e3, Bi1, Bi0);
                         double f0 = 0.0, f1 = 0.0;
                         for (int k = 0; k < q; ++k) {
-                            const double e2 = stab[2 * k], we2 = stab[2 * k + 1] * e2;
+                            const double e2 = stab[3 * k], hw = stab[3 * k + 2];
                             const double r2 = fma(e2, fma(e2, Cc, m2B), A);
-                            const double ri = rsqrt_nr(r2);
                             if (KER == SLP) {
-                                f0 = fma(we2, ri, f0);
+                                // (w e2 / 2) y (3 - r2 y^2): one Newton step for 1/sqrt(r2) folded in
+                                double y;
+                            asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
+                                const double tq = r2 * y;
+                                f0 = fma(hw * y, fma(-tq, y, 3.0), f0);
                             } else {
-                                const double f = we2 * (ri * ri * ri);
+                                const double ri = rsqrt_nr(r2);
+                                const double f = 2.0 * hw * (ri * ri * ri);
                                 f0 += f;
                                 f1 = fma(f, e2, f1);
                             }
@@ -217,7 +263,7 @@ template <int NR, int TYPE, int KER>
 static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
                       const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
                       double* v0, double* v1) {
-    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 11 : 2;
+    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;
     const size_t smem = mode == 2 ? 0 : (size_t)npts * W * sizeof(double);
     dim3 grid((npairs + kThreads - 1) / kThreads);
     if (mode == 0) {
