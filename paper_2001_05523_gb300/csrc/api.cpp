@@ -938,7 +938,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
                 continue;
             }
             h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, np, op->sp_lo[t].as<int>(), op->sp_hi[t].as<int>(),
-                                op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(), op->sp_npts[t], 1, false, 1,
+                                op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(), op->sp_npts[t], 1,
+                                op->precision != H2BEM_FP64, false, 1,
                                 nullptr, nullptr, op->sp_v0[t].as<double>(), op->sp_v1[t].as<double>(), 0);
             CU(cudaGetLastError());
         }
@@ -1133,11 +1134,11 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         nl += np > 0 ? 1 : 0;
         if (op->cache_singular)
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                                nullptr, nullptr, 0, 2, transpose, NR, op->xp.as<double>(), op->yp.as<double>(),
+                                nullptr, nullptr, 0, 2, false, transpose, NR, op->xp.as<double>(), op->yp.as<double>(),
                                 op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
         else
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                                op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, transpose,
+                                op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, fp32, transpose,
                                 NR, op->xp.as<double>(), op->yp.as<double>(), nullptr, nullptr, s);
     }
     mark(8);
@@ -1420,10 +1421,10 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         const int np = (int)op->sp_count[ty];
         if (op->cache_singular)
             launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(), nullptr,
-                            nullptr, 0, 2, false, NR, xp, yp, op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
+                            nullptr, 0, 2, false, false, NR, xp, yp, op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
         else
             launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, false, NR, xp,
+                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, fp32, false, NR, xp,
                             yp, nullptr, nullptr, s);
     }
     launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);

@@ -69,8 +69,8 @@ void launch_near_regular(const Geom& g, const Tree& t, const Consts& c, int nrow
 //   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the
 //   values (val0 = a_{lo,hi}, val1 = a_{hi,lo});  mode 2: scatter stored values.
 void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
-                     const double* tab, int npts, int mode, bool transpose, int NR, const double* xp, double* yp,
-                     double* val0, double* val1, cudaStream_t s);
+                     const double* tab, int npts, int mode, bool fp32, bool transpose, int NR, const double* xp,
+                     double* yp, double* val0, double* val1, cudaStream_t s);
 
 // farfield.  basis32: basis values in FP32 (else FP64); xh64 / yh64: the
 // cluster vectors xh / yh are double (else float).

@@ -1,5 +1,9 @@
 // Nearfield blocks, singular pairs (triangles sharing a vertex): Sauter-Schwab
-// quadrature (cited in sections 1 and 5), FP64 always.
+// quadrature (cited in sections 1 and 5).  FP64 tier: FP64 throughout.  Mixed
+// tier (F32): the Gram entries of the edge vectors are formed in FP64 and
+// rounded once; the quadrature points of edge and vertex pairs are evaluated
+// in FP32 (hardware reciprocal square root, relative error below 2^-22) and
+// summed in FP32 over at most q^2 points, the partial sums in FP64.
 //
 // Each canonical pair {lo, hi} (outer panel P = triangle of lower user index,
 // shared vertices first and in the same order in P and Q) is evaluated once.
@@ -44,7 +48,13 @@ __device__ __forceinline__ void load_corner(const Geom& g, int i, int corner, do
 __device__ __forceinline__ double dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 }  // namespace
 
-template <int NR, int TYPE, int KER, int MODE>
+__device__ __forceinline__ float rsqrt_f32(float a) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
+template <int NR, int TYPE, int KER, int MODE, bool F32>
 __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const int* __restrict__ plo,
                                                        const int* __restrict__ phi, const int* __restrict__ pcode,
                                                        const double* __restrict__ tab, int npts, bool transpose,
@@ -52,8 +62,18 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                                                        double* __restrict__ val0, double* __restrict__ val1) {
     constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;  // doubles per table point
     extern __shared__ double stab[];
+    float* stf = reinterpret_cast<float*>(stab);  // F32: (x_k, w_k x_k, w_k, 0) per point
     if (MODE != 2) {
-        for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
+        if (F32 && TYPE != IDENTICAL) {
+            for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+                stf[4 * p] = (float)tab[p * W];
+                stf[4 * p + 1] = (float)(2.0 * tab[p * W + W - 1]);
+                stf[4 * p + 2] = (float)tab[p * W + 1];
+                stf[4 * p + 3] = 0.0f;
+            }
+        } else {
+            for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
+        }
         __syncthreads();
     }
     const int pid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,6 +110,72 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 s += T[3] * rsqrt_nr(r2);
             }
             a01 = a10 = sc * s;
+        } else if (TYPE == EDGE && F32) {
+            // as the FP64 branch below, with (x_k, w_k x_k, w_k) from stf
+            const float Gm[3][3] = {{(float)dot(ea, ea), (float)dot(ea, eb), (float)dot(ea, ed)},
+                                    {(float)dot(ea, eb), (float)dot(eb, eb), (float)dot(eb, ed)},
+                                    {(float)dot(ea, ed), (float)dot(eb, ed), (float)dot(ed, ed)}};
+            const int q = npts;
+            double s = 0.0, sa = 0.0, sb = 0.0, sd = 0.0;
+            for (int reg = 0; reg < 5; ++reg) {
+                float rs = 0.0f, ra = 0.0f, rb = 0.0f, rd = 0.0f;
+                for (int oi = 0; oi < q; ++oi) {
+                    const float o = stf[4 * oi], wo = stf[4 * oi + 2];
+                    float F[3], Gv[3];
+                    switch (reg) {
+                        case 0: F[0] = o; F[1] = 0.0f; F[2] = o - 1.0f; Gv[0] = 0.0f; Gv[1] = 1.0f; Gv[2] = 0.0f; break;
+                        case 1: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = o; Gv[1] = 0.0f; Gv[2] = o - 1.0f; break;
+                        case 2: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -1.0f; Gv[1] = -1.0f; Gv[2] = -o; break;
+                        case 3: F[0] = 0.0f; F[1] = 0.0f; F[2] = -1.0f; Gv[0] = -o; Gv[1] = 1.0f - o; Gv[2] = 0.0f; break;
+                        default: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -o; Gv[1] = -o; Gv[2] = -1.0f; break;
+                    }
+                    float A = 0.0f, B2 = 0.0f, Cc = 0.0f;
+                    for (int u = 0; u < 3; ++u)
+                        for (int v = 0; v < 3; ++v) {
+                            A += F[u] * Gm[u][v] * F[v];
+                            B2 += F[u] * Gm[u][v] * Gv[v];
+                            Cc += Gv[u] * Gm[u][v] * Gv[v];
+                        }
+                    B2 *= 2.0f;
+                    float f0 = 0.0f, f1 = 0.0f;
+                    for (int k = 0; k < q; ++k) {
+                        const float tt = stf[4 * k];
+                        const float wt = reg == 0 ? stf[4 * k + 2] : stf[4 * k + 1];  // w_t (R1) or w_t t
+                        const float y = rsqrt_f32(fmaf(tt, fmaf(tt, Cc, B2), A));
+                        if (KER == SLP) {
+                            f0 = fmaf(wt, y, f0);
+                        } else {
+                            const float f = wt * (y * y * y);
+                            f0 += f;
+                            f1 = fmaf(f, tt, f1);
+                        }
+                    }
+                    if (KER == SLP) {
+                        rs = fmaf(wo, f0, rs);
+                    } else {
+                        ra = fmaf(wo, f0 * F[0] + f1 * Gv[0], ra);
+                        rb = fmaf(wo, f0 * F[1] + f1 * Gv[1], rb);
+                        rd = fmaf(wo, f0 * F[2] + f1 * Gv[2], rd);
+                    }
+                }
+                s += rs;
+                sa += ra;
+                sb += rb;
+                sd += rd;
+            }
+            if (KER == SLP) {
+                a01 = a10 = sc * s / 6.0;
+            } else {
+                double V[3];
+                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
+                double nlo[3], nhi[3];
+                for (int d = 0; d < 3; ++d) {
+                    nlo[d] = g.nrm[d * g.n + lo];
+                    nhi[d] = g.nrm[d * g.n + hi];
+                }
+                a01 = sc * dot(V, nhi);
+                a10 = -sc * dot(V, nlo);
+            }
         } else if (TYPE == EDGE) {
             // vectors (a, b, d); stab holds (x_k, w_k, w_k / 2, w_k x_k / 2), npts = q.
             // Region r: w = F(o) + t G(o) with the outer variable o and the inner t;
@@ -157,6 +243,74 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
             } else {
                 double V[3];
                 for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
+                double nlo[3], nhi[3];
+                for (int d = 0; d < 3; ++d) {
+                    nlo[d] = g.nrm[d * g.n + lo];
+                    nhi[d] = g.nrm[d * g.n + hi];
+                }
+                a01 = sc * dot(V, nhi);
+                a10 = -sc * dot(V, nlo);
+            }
+        } else if (F32) {  // VERTEX as the FP64 branch below, with (x_k, w_k x_k, w_k) from stf
+            const float aa = (float)dot(ea, ea), bb = (float)dot(eb, eb), cc = (float)dot(ec, ec),
+                        dd = (float)dot(ed, ed);
+            const float ab = (float)dot(ea, eb), ac = (float)dot(ea, ec), ad = (float)dot(ea, ed),
+                        bc = (float)dot(eb, ec), bd = (float)dot(eb, ed), cd = (float)dot(ec, ed);
+            const int q = npts;
+            double s = 0.0, sa = 0.0, sb = 0.0, sc2 = 0.0, sd = 0.0;
+            for (int reg = 0; reg < 2; ++reg) {
+                const float uu = reg == 0 ? aa : cc, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : dd;
+                const float pp = reg == 0 ? cc : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? dd : bb;
+                const float b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
+                for (int i = 0; i < q; ++i) {
+                    const float e1 = stf[4 * i], w1 = stf[4 * i + 2];
+                    const float A = fmaf(e1, fmaf(e1, vv2, 2.0f * uv2), uu);
+                    const float Bi0 = fmaf(e1, b2, b0), Bi1 = fmaf(e1, bd, b1);
+                    // over l: t0 = sum w3 f0, t1 = sum w3 f1, t2 = sum w3 e3 f1
+                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+                    for (int l = 0; l < q; ++l) {
+                        const float e3 = stf[4 * l], w3 = stf[4 * l + 2];
+                        const float Cc = fmaf(e3, fmaf(e3, qq2, 2.0f * pq2), pp);
+                        const float m2B = -2.0f * fmaf(e3, Bi1, Bi0);
+                        float f0 = 0.0f, f1 = 0.0f;
+                        for (int k = 0; k < q; ++k) {
+                            const float2 T = *reinterpret_cast<const float2*>(stf + 4 * k);  // (e2, w e2)
+                            const float y = rsqrt_f32(fmaf(T.x, fmaf(T.x, Cc, m2B), A));
+                            if (KER == SLP) {
+                                f0 = fmaf(T.y, y, f0);
+                            } else {
+                                const float f = T.y * (y * y * y);
+                                f0 += f;
+                                f1 = fmaf(f, T.x, f1);
+                            }
+                        }
+                        t0 = fmaf(w3, f0, t0);
+                        if (KER != SLP) {
+                            t1 = fmaf(w3, f1, t1);
+                            t2 = fmaf(w3 * e3, f1, t2);
+                        }
+                    }
+                    const double W1 = w1, T0 = (double)w1 * t0;
+                    if (KER == SLP) {
+                        s += T0;
+                    } else if (reg == 0) {  // w = a + e1 b - e2 c - e2 e3 d
+                        sa += T0;
+                        sb = fma((double)e1, T0, sb);
+                        sc2 -= W1 * t1;
+                        sd -= W1 * t2;
+                    } else {                // w = e2 a + e2 e3 b - c - e1 d
+                        sa += W1 * t1;
+                        sb += W1 * t2;
+                        sc2 -= T0;
+                        sd = fma(-(double)e1, T0, sd);
+                    }
+                }
+            }
+            if (KER == SLP) {
+                a01 = a10 = sc * s / 3.0;
+            } else {
+                double V[3];
+                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sc2 * ec[d] + sd * ed[d]);
                 double nlo[3], nhi[3];
                 for (int d = 0; d < 3; ++d) {
                     nlo[d] = g.nrm[d * g.n + lo];
@@ -259,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
     }
 }
 
-template <int NR, int TYPE, int KER>
+template <int NR, int TYPE, int KER, bool F32>
 static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
                       const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
                       double* v0, double* v1) {
@@ -267,43 +421,49 @@ static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const
     const size_t smem = mode == 2 ? 0 : (size_t)npts * W * sizeof(double);
     dim3 grid((npairs + kThreads - 1) / kThreads);
     if (mode == 0) {
-        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_singular<NR, TYPE, KER, 0><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 0, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_singular<NR, TYPE, KER, 0, F32><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     } else if (mode == 1) {
-        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_singular<NR, TYPE, KER, 1><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 1, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_singular<NR, TYPE, KER, 1, F32><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     } else {
-        k_singular<NR, TYPE, KER, 2><<<grid, kThreads, 0, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        k_singular<NR, TYPE, KER, 2, false><<<grid, kThreads, 0, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     }
 }
 
 template <int NR, int TYPE>
-static void sing_ker(int ker, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
-                     const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp, double* v0,
-                     double* v1) {
-    if (ker == SLP) sing_mode<NR, TYPE, SLP>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    else sing_mode<NR, TYPE, DLP>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+static void sing_ker(int ker, bool f32, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo,
+                     const int* hi, const int* code, const double* tab, int npts, bool tr, const double* xp,
+                     double* yp, double* v0, double* v1) {
+    // identical pairs (3q points) stay in FP64 in both tiers; mode 2 only reads cached values
+    if (f32 && TYPE != IDENTICAL && mode != 2) {
+        if (ker == SLP) sing_mode<NR, TYPE, SLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        else sing_mode<NR, TYPE, DLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    } else {
+        if (ker == SLP) sing_mode<NR, TYPE, SLP, false>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        else sing_mode<NR, TYPE, DLP, false>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    }
 }
 
 template <int NR>
-static void sing_type(int type, int ker, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo,
-                      const int* hi, const int* code, const double* tab, int npts, bool tr, const double* xp,
-                      double* yp, double* v0, double* v1) {
-    if (type == IDENTICAL) sing_ker<NR, IDENTICAL>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    else if (type == EDGE) sing_ker<NR, EDGE>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    else sing_ker<NR, VERTEX>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+static void sing_type(int type, int ker, bool f32, int mode, int npairs, cudaStream_t s, const Geom& g,
+                      const int* lo, const int* hi, const int* code, const double* tab, int npts, bool tr,
+                      const double* xp, double* yp, double* v0, double* v1) {
+    if (type == IDENTICAL) sing_ker<NR, IDENTICAL>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    else if (type == EDGE) sing_ker<NR, EDGE>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    else sing_ker<NR, VERTEX>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
 }
 
 void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
-                     const double* tab, int npts, int mode, bool transpose, int NR, const double* xp, double* yp,
-                     double* val0, double* val1, cudaStream_t s) {
+                     const double* tab, int npts, int mode, bool fp32, bool transpose, int NR, const double* xp,
+                     double* yp, double* val0, double* val1, cudaStream_t s) {
     if (npairs <= 0) return;
     if (ker == DLP_T) ker = DLP;  // the transposed double layer swaps the two values
     switch (NR) {
-        case 1: sing_type<1>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        case 4: sing_type<4>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        case 8: sing_type<8>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        default: sing_type<16>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 1: sing_type<1>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 4: sing_type<4>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 8: sing_type<8>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        default: sing_type<16>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
     }
 }
 
