@@ -574,12 +574,12 @@ struct h2bem_op {
     int64_t nfar = 0, nnear = 0, near_pairs = 0, sing[3] = {0, 0, 0};
     h2::Consts consts{};
     // device geometry and tree
-    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane;
+    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
     DevBuf cbegin, cend, cchild0, cchild1, cbox, leaves, basis_rule;
     std::vector<int> leaves_h;
     std::vector<std::vector<int>> level_parents;  // non-leaf clusters per level
     std::vector<DevBuf> dlevel;
-    Csr far, far_t, near, near_t;
+    Csr far, far_t, near, near_u;  // near_u: the blocks (t, s) of near with s >= t
     // singular pairs by type (index 0: identical, 1: edge, 2: vertex)
     DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3], sp_gtab, sp_gtab_edge;
     int sp_gnpts = 0, sp_gnpts_edge = 0;
@@ -617,7 +617,7 @@ struct h2bem_op {
     h2::Geom geom() const {
         return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
                         ctr.as<const double>(), vid.as<const int>(), qo.as<const float>(), qa.as<const double>(),
-                        chl.as<const float>(), plane.as<const double>()};
+                        chl.as<const float>(), plane.as<const double>(), nef.as<const float>()};
     }
     h2::Tree tree() const {
         return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
@@ -774,6 +774,9 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             C.ru[p] = u[p];
             C.rv[p] = v[p];
             C.rw[p] = w[p];
+            C.rwf[p] = (float)w[p];
+            C.ruf[p] = (float)(u[p] - 1.0 / 3.0);
+            C.rvf[p] = (float)(v[p] - 1.0 / 3.0);
         }
     }
     // leaf-basis rule: collapsed Gauss, exact for total degree 3(m-1)
@@ -833,7 +836,25 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     make_csr(nc, B.ft, B.fs, op->far);
     make_csr(nc, B.fs, B.ft, op->far_t);
     make_csr(nc, B.nt, B.ns, op->near);
-    make_csr(nc, B.ns, B.nt, op->near_t);
+    {
+        // The nearfield is applied by unordered pairs of leaves; the block
+        // tree of one cluster tree with a symmetric admissibility condition
+        // contains (s, t) with every (t, s).
+        std::vector<std::pair<int64_t, int64_t>> fwd(B.nt.size()), bwd(B.nt.size());
+        std::vector<int64_t> ut, us;
+        for (size_t b = 0; b < B.nt.size(); ++b) {
+            fwd[b] = {B.nt[b], B.ns[b]};
+            bwd[b] = {B.ns[b], B.nt[b]};
+            if (B.ns[b] >= B.nt[b]) {
+                ut.push_back(B.nt[b]);
+                us.push_back(B.ns[b]);
+            }
+        }
+        std::sort(fwd.begin(), fwd.end());
+        std::sort(bwd.begin(), bwd.end());
+        if (fwd != bwd) return fail(H2BEM_ERR_ARG, "operator_create: nearfield block list is not symmetric");
+        make_csr(nc, ut, us, op->near_u);
+    }
 
     // singular pairs (tree positions), sorted by outer position
     std::vector<int64_t> slo[3], shi[3];
@@ -851,7 +872,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         (rc = upload(op->cbox, box)) || (rc = upload(op->leaves, op->leaves_h)))
         return rc;
     if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
-        (rc = op->near_t.upload_all()))
+        (rc = op->near_u.upload_all()))
         return rc;
     op->dlevel.resize(op->level_parents.size());
     for (size_t L = 0; L < op->level_parents.size(); ++L)
@@ -919,11 +940,12 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         (rc = op->nrm.alloc(3 * n * sizeof(double))) || (rc = op->ctr.alloc(3 * n * sizeof(double))) ||
         (rc = op->vid.alloc(3 * n * sizeof(int))) || (rc = op->qo.alloc(21 * n * sizeof(float))) ||
         (rc = op->qa.alloc(21 * n * sizeof(double))) || (rc = op->chl.alloc(6 * n * sizeof(float))) ||
-        (rc = op->plane.alloc(n * sizeof(double))))
+        (rc = op->plane.alloc(n * sizeof(double))) || (rc = op->nef.alloc(12 * n * sizeof(float))))
         return rc;
     h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->consts, op->v.as<double>(),
                     op->area.as<double>(), op->nrm.as<double>(), op->ctr.as<double>(), op->vid.as<int>(),
-                    op->qo.as<float>(), op->qa.as<double>(), op->chl.as<float>(), op->plane.as<double>(), 0);
+                    op->qo.as<float>(), op->qa.as<double>(), op->chl.as<float>(), op->plane.as<double>(),
+                    op->nef.as<float>(), 0);
     CU(cudaGetLastError());
     // x-independent singular entries, evaluated once if requested
     if (op->cache_singular) {
@@ -1091,7 +1113,6 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     const bool out_dlp = dlp && transpose;   // W_s on the output side
     const int near_ker = !dlp ? h2::SLP : transpose ? h2::DLP_T : h2::DLP;
     const Csr& far = transpose ? op->far_t : op->far;
-    const Csr& near = transpose ? op->near_t : op->near;
     auto mark = [&](int i) {
         if (timed) cudaEventRecord(op->ev[i], s);
     };
@@ -1123,10 +1144,11 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         for (int i = 2; i <= 5; ++i) mark(i);
     }
     mark(6);
-    // nearfield rows are row leaves (transposed: column leaves)
-    h2::launch_near_regular(g, t, c, near.nrows(), near.drows.as<int>(), near.dptr.as<int>(), near.dcol.as<int>(),
-                            near_ker, fp32, NR, op->xp.as<double>(), op->yp.as<double>(), s);
-    nl += near.nrows() > 0 ? 1 : 0;
+    // nearfield, regular pairs: each unordered pair of leaves once, both directions
+    h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
+                        op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR, op->xp.as<double>(),
+                        op->yp.as<double>(), s);
+    nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
     for (int ty = 0; ty < 3; ++ty) {
         if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
@@ -1414,8 +1436,8 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
                              fp32, yh64, NR, yh, yp, s);
     }
-    launch_near_regular(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
-                        op->near.dcol.as<int>(), near_ker, fp32, NR, xp, yp, s);
+    launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
+                    op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, s);
     for (int ty = 0; ty < 3; ++ty) {
         if (ty == 0 && dlp) continue;
         const int np = (int)op->sp_count[ty];

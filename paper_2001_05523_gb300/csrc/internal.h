@@ -29,6 +29,8 @@ struct Geom {
     const double* qa;    // [3][n][7] FP64 points y_q
     const float* chl;    // [6][n] centroid split: hi = fl(c) (rows 0..2), lo = fl(c - hi) (rows 3..5)
     const double* plane; // [n] c . n (offset of the triangle's plane)
+    const float* nef;    // [12][n] FP32: normal hi (0..2) and lo = fl(n - hi) (3..5), edges E1 = b - a (6..8),
+                         // E2 = c - a (9..11), each rounded from FP64
 };
 
 // Cluster tree on the device.
@@ -49,21 +51,25 @@ struct Consts {
     float cheb_hi[kMaxM];        // float split of cheb: cheb = hi + lo
     float cheb_lo[kMaxM];
     double ru[7], rv[7], rw[7];  // Radon 7-point rule on the unit simplex, weights sum to 1
+    float rwf[7], ruf[7], rvf[7];  // the same in FP32: weights, u - 1/3, v - 1/3
     int nb;                      // points of the leaf-basis rule
 };
 
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
-                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, cudaStream_t s);
+                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
+                 cudaStream_t s);
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
                        cudaStream_t s);
 void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,
                         cudaStream_t s);
 
-// nearfield, regular pairs: one CTA per row leaf in `rows`, columns from CSR
-void launch_near_regular(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows,
-                         const int* ptr, const int* col, int ker, bool fp32, int NR, const double* xp, double* yp,
-                         cudaStream_t s);
+// nearfield, regular pairs, each unordered pair of leaves {t, s} once: one
+// CTA per row leaf t in `rows`, columns s >= t from CSR (the first column of
+// a row is t itself).  ker: SLP or DLP; transpose applies K^T (double layer).
+void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                     const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
+                     cudaStream_t s);
 
 // nearfield, singular pairs of one type (canonical orientation, see api.cpp)
 //   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the

@@ -27,11 +27,13 @@ __global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, c
 // centroid ((a+b)+c)/3 (section 1; the normal is outward for triangles oriented
 // counter-clockwise seen from outside), the plane offset c . n, and the points
 // y_q = a + u_q (b-a) + v_q (c-a) of the 7-point rule, in FP64 and as FP32
-// offsets from the centroid, with a float split of the centroid.
+// offsets from the centroid, with a float split of the centroid; in FP32
+// also the normal as hi + lo and the edge vectors b - a, c - a.
 __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ tri, const int* __restrict__ perm,
                        int n, Consts c, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
                        double* __restrict__ ctr, int* __restrict__ vid, float* __restrict__ qo,
-                       double* __restrict__ qa, float* __restrict__ chl, double* __restrict__ plane) {
+                       double* __restrict__ qa, float* __restrict__ chl, double* __restrict__ plane,
+                       float* __restrict__ nef) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int t = perm[i];
@@ -55,6 +57,11 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
         const double cd = ((P[0][d] + P[1][d]) + P[2][d]) / 3.0;
         nrm[d * n + i] = nd;
         ctr[d * n + i] = cd;
+        const float nh = (float)nd;
+        nef[d * n + i] = nh;
+        nef[(3 + d) * n + i] = (float)(nd - (double)nh);
+        nef[(6 + d) * n + i] = (float)e1[d];
+        nef[(9 + d) * n + i] = (float)e2[d];
         const float h = (float)cd;
         chl[d * n + i] = h;
         chl[(3 + d) * n + i] = (float)(cd - (double)h);
@@ -69,8 +76,9 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
 }
 
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
-                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, cudaStream_t s) {
-    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane);
+                 double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
+                 cudaStream_t s) {
+    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef);
 }
 
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
