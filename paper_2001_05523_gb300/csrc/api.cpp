@@ -577,6 +577,8 @@ struct h2bem_op {
     DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
     DevBuf cbegin, cend, cchild0, cchild1, cbox, leaves, basis_rule;
     std::vector<int> leaves_h;
+    int max_leaf = 0;               // largest leaf cluster
+    DevBuf basisV, basisW;          // stored leaf bases [pos][nu]: V (FP32 in the mixed tier), W (double layer, FP64)
     std::vector<std::vector<int>> level_parents;  // non-leaf clusters per level
     std::vector<DevBuf> dlevel;
     Csr far, far_t, near, near_u;  // near_u: the blocks (t, s) of near with s >= t
@@ -947,6 +949,21 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
                     op->qo.as<float>(), op->qa.as<double>(), op->chl.as<float>(), op->plane.as<double>(),
                     op->nef.as<float>(), 0);
     CU(cudaGetLastError());
+    // leaf bases: V_t[i, nu] = int L_nu; for the double layer also W_s[j, nu] = int n_j . grad L_nu
+    for (int l : op->leaves_h) op->max_leaf = std::max(op->max_leaf, (int)(tree->end[l] - tree->begin[l]));
+    {
+        const bool v32 = op->precision != H2BEM_FP64;
+        if ((rc = op->basisV.alloc((size_t)n * op->k * (v32 ? sizeof(float) : sizeof(double))))) return rc;
+        h2::launch_leaf_basis(op->geom(), op->tree(), op->consts, op->basis_rule.as<double>(), (int)op->nleaves,
+                              op->leaves.as<int>(), false, v32, op->basisV.p, 0);
+        CU(cudaGetLastError());
+        if (kernel == H2BEM_DLP) {
+            if ((rc = op->basisW.alloc((size_t)n * op->k * sizeof(double)))) return rc;
+            h2::launch_leaf_basis(op->geom(), op->tree(), op->consts, op->basis_rule.as<double>(), (int)op->nleaves,
+                                  op->leaves.as<int>(), true, false, op->basisW.p, 0);
+            CU(cudaGetLastError());
+        }
+    }
     // x-independent singular entries, evaluated once if requested
     if (op->cache_singular) {
         for (int t = 0; t < 3; ++t) {
@@ -1125,8 +1142,9 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
         // the double layer's differentiated basis is evaluated in FP64 in every tier
-        h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), in_dlp,
-                                fp32 && !in_dlp, xh64, NR, op->xp.as<double>(), op->xh.p, s);
+        h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                       fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
+                                       op->xp.as<double>(), op->xh.p, s);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
@@ -1138,8 +1156,9 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
         mark(5);
-        h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), out_dlp,
-                                 fp32 && !out_dlp, yh64, NR, op->yh.p, op->yp.as<double>(), s);
+        h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                        fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p, op->yh.p,
+                                        op->yp.as<double>(), s);
     } else {
         for (int i = 2; i <= 5; ++i) mark(i);
     }
@@ -1425,16 +1444,16 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
     CU(cudaMemsetAsync(yp, 0, vb, s));
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(yh, 0, hb, s));
-        launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), dlp,
-                            fp32 && !dlp, xh64, NR, xp, xh, s);
+        launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32 && !dlp,
+                                   xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
         launch_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(), op->far.dcol.as<int>(),
                         op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, s);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
-        launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
-                             fp32, yh64, NR, yh, yp, s);
+        launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32, yh64,
+                                    NR, op->basisV.p, yh, yp, s);
     }
     launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
                     op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, s);

@@ -86,6 +86,14 @@ void launch_leaf_forward(const Geom& g, const Tree& t, const Consts& c, const do
 void launch_leaf_backward(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
                           const int* leaves, bool dlp_basis, bool basis32, bool yh64, int NR, const void* yh,
                           double* yp, cudaStream_t s);
+// stored leaf bases B[pos * k + nu] (FP32 if basis32, else FP64), evaluated
+// once; the transforms of an apply read them (max_leaf: largest leaf)
+void launch_leaf_basis(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
+                       const int* leaves, bool dlp_basis, bool basis32, void* B, cudaStream_t s);
+void launch_leaf_forward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,
+                                bool xh64, int NR, const void* B, const double* xp, void* xh, cudaStream_t s);
+void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,
+                                 bool yh64, int NR, const void* B, const void* yh, double* yp, cudaStream_t s);
 void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,
                    cudaStream_t s);
 void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,

@@ -14,6 +14,7 @@
 // with E_{t'}[nu',nu] = L_{t,nu}(xi_{t',nu'}) applied as a Kronecker product of
 // three m x m matrices.  Vectors xh, yh: [cluster][nu][r] with NR columns.
 #include <type_traits>
+#include <utility>
 
 #include "dmath.cuh"
 #include "internal.h"
@@ -226,6 +227,82 @@ __global__ void __launch_bounds__(256) k_leaf_backward(Geom g, Tree t, Consts c,
 }
 
 // ---------------------------------------------------------------------------
+// Stored leaf bases.  The basis B_s[j, nu] of a leaf does not depend on x, so
+// it is evaluated once (k_leaf_basis, the same tabulation as above) and kept
+// in tree order, B[pos * k + nu]: the rows of one leaf are contiguous.  The
+// leaf transforms of an apply are then small products over staged tiles:
+//   forward   xh_s[nu][r] = sum_{j in s} B[j, nu] x_j[r]
+//   backward  y_j[r]     += sum_nu B[j, nu] yh_t[nu][r]
+// ---------------------------------------------------------------------------
+template <typename TB, bool DLPB>
+__global__ void __launch_bounds__(256) k_leaf_basis(Geom g, Tree t, Consts c, const double* __restrict__ rule,
+                                                    const int* __restrict__ leaves, int CT, TB* __restrict__ B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = c.m, k = c.k, nb = c.nb;
+    TB* LT = reinterpret_cast<TB*>(smem_raw);
+    TB* dLT = LT + (size_t)CT * nb * 3 * m;
+    TB* wq = dLT + (DLPB ? (size_t)CT * nb * 3 * m : 0);
+    TB* nr = wq + (size_t)CT * nb;
+    __shared__ double sABC[kMaxLeaf * 9];
+    const int s = leaves[blockIdx.x];
+    const int b = t.begin[s], R = t.end[s] - b;
+    for (int j0 = 0; j0 < R; j0 += CT) {
+        const int cnt = min(CT, R - j0);
+        __syncthreads();
+        tabulate_chunk<TB, DLPB>(g, t, c, rule, s, b + j0, cnt, LT, dLT, wq, nr, sABC);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt * k; e += blockDim.x) {
+            const int jl = e / k, nu = e % k;
+            B[(int64_t)(b + j0) * k + e] =
+                basis_value<TB, DLPB>(LT, dLT, wq, nr, jl, nb, m, nu % m, (nu / m) % m, nu / (m * m));
+        }
+    }
+}
+
+template <typename TB, typename TA, int NR>
+__global__ void __launch_bounds__(128) k_leaf_fwd_st(Tree t, int k, const int* __restrict__ leaves,
+                                                     const TB* __restrict__ B, const double* __restrict__ xp,
+                                                     TA* __restrict__ xh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int s = leaves[blockIdx.x];
+    const int b = t.begin[s], R = t.end[s] - b;
+    TB* sB = reinterpret_cast<TB*>(smem_raw);                                        // [R][k]
+    TA* sx = reinterpret_cast<TA*>(smem_raw + (((size_t)R * k * sizeof(TB) + 15) & ~size_t(15)));  // [R][NR]
+    const TB* Bs = B + (int64_t)b * k;
+    for (int e = threadIdx.x; e < R * k; e += blockDim.x) sB[e] = Bs[e];
+    for (int e = threadIdx.x; e < R * NR; e += blockDim.x) sx[e] = (TA)xp[(int64_t)b * NR + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
+        const int nu = e / NR, r = e % NR;
+        TA acc = 0;
+        for (int j = 0; j < R; ++j) acc += (TA)sB[j * k + nu] * sx[j * NR + r];
+        xh[((int64_t)s * k + nu) * NR + r] = acc;
+    }
+}
+
+template <typename TB, typename TA, int NR>
+__global__ void __launch_bounds__(128) k_leaf_bwd_st(Tree t, int k, const int* __restrict__ leaves,
+                                                     const TB* __restrict__ B, const TA* __restrict__ yh,
+                                                     double* __restrict__ yp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int s = leaves[blockIdx.x];
+    const int b = t.begin[s], R = t.end[s] - b;
+    const int kp = k + 1;  // padded row stride: rows of one warp fall in different banks
+    TB* sB = reinterpret_cast<TB*>(smem_raw);                                         // [R][kp]
+    TA* sy = reinterpret_cast<TA*>(smem_raw + (((size_t)R * kp * sizeof(TB) + 15) & ~size_t(15)));  // [k][NR]
+    const TB* Bs = B + (int64_t)b * k;
+    for (int e = threadIdx.x; e < R * k; e += blockDim.x) sB[(e / k) * kp + e % k] = Bs[e];
+    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) sy[e] = yh[(int64_t)s * k * NR + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * NR; e += blockDim.x) {
+        const int j = e / NR, r = e % NR;
+        TA acc = 0;
+        for (int nu = 0; nu < k; ++nu) acc += (TA)sB[j * kp + nu] * sy[nu * NR + r];
+        yp[(int64_t)(b + j) * NR + r] += (double)acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Transfers between a parent t and its children (Kronecker form).
 // E1[ch][d][a'][a] = L_{t,a}^{(d)}(z_{ch,d}[a']).
 // ---------------------------------------------------------------------------
@@ -402,6 +479,71 @@ void launch_leaf_backward(const Geom& g, const Tree& t, const Consts& c, const d
     if (nleaves <= 0) return;
     if (dlp_basis) { H2_NR_SWITCH(NR, (leaf_bwd_prec<R_, true>(basis32, yh64, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
     else { H2_NR_SWITCH(NR, (leaf_bwd_prec<R_, false>(basis32, yh64, g, t, c, rule, nleaves, leaves, yh, yp, s))) }
+}
+
+void launch_leaf_basis(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nleaves,
+                       const int* leaves, bool dlp_basis, bool basis32, void* B, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    auto go = [&](auto kern, size_t tb) {
+        const int ct = leaf_chunk(c, tb, dlp_basis);
+        const size_t smem = ((chunk_tab_elems<double>(ct, c.nb, c.m, dlp_basis) * tb + 15) / 16) * 16;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return std::make_pair(ct, smem);
+    };
+    if (basis32) {
+        if (dlp_basis) {
+            auto [ct, sm] = go(k_leaf_basis<float, true>, sizeof(float));
+            k_leaf_basis<float, true><<<nleaves, far_threads(c.k), sm, s>>>(g, t, c, rule, leaves, ct, (float*)B);
+        } else {
+            auto [ct, sm] = go(k_leaf_basis<float, false>, sizeof(float));
+            k_leaf_basis<float, false><<<nleaves, far_threads(c.k), sm, s>>>(g, t, c, rule, leaves, ct, (float*)B);
+        }
+    } else {
+        if (dlp_basis) {
+            auto [ct, sm] = go(k_leaf_basis<double, true>, sizeof(double));
+            k_leaf_basis<double, true><<<nleaves, far_threads(c.k), sm, s>>>(g, t, c, rule, leaves, ct, (double*)B);
+        } else {
+            auto [ct, sm] = go(k_leaf_basis<double, false>, sizeof(double));
+            k_leaf_basis<double, false><<<nleaves, far_threads(c.k), sm, s>>>(g, t, c, rule, leaves, ct, (double*)B);
+        }
+    }
+}
+
+template <typename TB, typename TA, int NR>
+static void leaf_st(bool fwd, const Tree& t, int k, int maxR, int nl, const int* leaves, const void* B,
+                    const double* xp, void* xh, const void* yh, double* yp, cudaStream_t s) {
+    if (fwd) {
+        const size_t smem = (((size_t)maxR * k * sizeof(TB) + 15) & ~size_t(15)) + (size_t)maxR * NR * sizeof(TA);
+        cudaFuncSetAttribute(k_leaf_fwd_st<TB, TA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_leaf_fwd_st<TB, TA, NR><<<nl, 128, smem, s>>>(t, k, leaves, (const TB*)B, xp, (TA*)xh);
+    } else {
+        const size_t smem = (((size_t)maxR * (k + 1) * sizeof(TB) + 15) & ~size_t(15)) + (size_t)k * NR * sizeof(TA);
+        cudaFuncSetAttribute(k_leaf_bwd_st<TB, TA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_leaf_bwd_st<TB, TA, NR><<<nl, 128, smem, s>>>(t, k, leaves, (const TB*)B, (const TA*)yh, yp);
+    }
+}
+
+template <int NR>
+static void leaf_st_prec(bool fwd, bool basis32, bool v64, const Tree& t, int k, int maxR, int nl, const int* leaves,
+                         const void* B, const double* xp, void* xh, const void* yh, double* yp, cudaStream_t s) {
+    if (!basis32 && v64) leaf_st<double, double, NR>(fwd, t, k, maxR, nl, leaves, B, xp, xh, yh, yp, s);
+    else if (!basis32) leaf_st<double, float, NR>(fwd, t, k, maxR, nl, leaves, B, xp, xh, yh, yp, s);
+    else if (v64) leaf_st<float, double, NR>(fwd, t, k, maxR, nl, leaves, B, xp, xh, yh, yp, s);
+    else leaf_st<float, float, NR>(fwd, t, k, maxR, nl, leaves, B, xp, xh, yh, yp, s);
+}
+
+void launch_leaf_forward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,
+                                bool xh64, int NR, const void* B, const double* xp, void* xh, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    H2_NR_SWITCH(NR, (leaf_st_prec<R_>(true, basis32, xh64, t, k, max_leaf, nleaves, leaves, B, xp, xh, nullptr,
+                                       nullptr, s)))
+}
+
+void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,
+                                 bool yh64, int NR, const void* B, const void* yh, double* yp, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    H2_NR_SWITCH(NR, (leaf_st_prec<R_>(false, basis32, yh64, t, k, max_leaf, nleaves, leaves, B, nullptr, nullptr,
+                                       yh, yp, s)))
 }
 
 template <typename T, int NR, bool UP>
