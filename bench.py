@@ -8,9 +8,10 @@ eta = 2.  Metric: triangles x right-hand sides per second.
 
 Arms
   ours (default)      CUDA path through the C ABI; headline = MIXED_FP32 tier
-                      (FP32 farfield and regular-pair evaluation, FP64 singular
-                      quadrature and accumulation), with the all-FP64 tier, the
-                      cached-singular variants and the relative errors reported.
+                      (FP32 farfield, regular-pair and edge/vertex Sauter-Schwab
+                      point evaluation; FP64 pair set-up, partial sums and
+                      accumulation), with the all-FP64 tier, the cached-singular
+                      variants and the relative errors reported.
   --impl reference    the FP64 CPU oracle as it stands on the host cores (the
                       same H^2 product on the 32,768-triangle member of the
                       sphere family, bounded so the run takes a few minutes).
@@ -36,23 +37,29 @@ sys.path.insert(0, ROOT)
 METRIC = "H2 SLP matvec triangles/s on 2M-tri sphere, mixed vs FP64, at stated rel. error"
 UNIT = "triangles*rhs/s"
 
-# Algorithmic flops per unit of the formulation each kernel evaluates (an FMA
-# counts 2, a reciprocal square root 1; stated in the design doc):
-#   regular pair point   d = x - y (3), |d|^2 (5), rsqrt (1), weighted sum (2)          = 11 per point, 49 points
-#   singular, identical  |w|^2 from a 2x2 Gram form (6), rsqrt (1), sum (2)            = 9 per point, 15 points
-#   singular, edge       |w|^2 from a 3x3 Gram form (12), rsqrt (1), sum (2)           = 15 per point, 125 points
-#   singular, vertex     |w|^2 = A - 2 e B + e^2 C (4), rsqrt (1), sum (2), plus the
-#                        per-(i,l) coefficients (6 per 5 points) and the Gram set-up   ~ 8.6 per point, 250 points
-#   coupling entry       |d|^2 from per-axis squares (1), rsqrt (1), S x-hat (2 nrhs)
-FLOPS_REG = 11
-FLOPS_SING = {0: 9.0, 1: 15.0, 2: 8.6}
-PTS_SING_SLP = {0: 15, 1: 125, 2: 250}  # points per canonical pair, q = 5
+# Work units of the kernels (stated in the design doc).  Every kernel evaluation
+# costs one hardware reciprocal square root (the MUFU unit, 16 per clock per
+# SM), and the nearfield and coupling kernels are bound by that unit together
+# with the FP32 issue slots around it, so their achieved rate is reported as
+# kernel evaluations per second against the measured MUFU rate:
+#   regular nearfield  49 evaluations per pair the kernel evaluates (regular_evals:
+#                      every unordered regular pair once, both orders in diagonal blocks)
+#   singular           points per canonical pair: identical 3q (FP64 in every tier),
+#                      edge-adjacent 5q^2, vertex-adjacent 2q^3 (FP32 in the mixed tier)
+#   coupling           k^2 entries of S_ts per farfield block, plus 2 k^2 nrhs FP32 flops
+PTS_SING = {0: 15, 1: 125, 2: 250}  # q = 5
+# DRAM bytes (read + write) per launch of the regular nearfield kernel on this
+# workload, from one ncu capture of the same kernel on the 524,288-triangle
+# sphere, scaled by the 4x units (profiles/kernels_mixed_slp_sphere524k.md)
+TRAFFIC = {"near_regular": 4 * (136.10e6 + 19.85e6)}
 
 
 def peaks():
-    """ALU peaks from unit counts and the maximum SM clock (152 SMs, 2070 MHz):
-    FP32 128 FMA/clk/SM; FP64 2 FMA/clk/SM (1.25 TFLOP/s nominal).  HBM and
-    bf16 from MEASURED_PEAKS.json when present."""
+    """Arithmetic peaks measured live by the microbenchmark csrc/peaks.cu
+    (built with the library): FP32/FP64 FMA, FP32 MUFU rsqrt, FP64 MMA.  If it
+    cannot run, unit counts x the maximum SM clock (152 SMs, 2070 MHz; FP32 128
+    FMA, FP64 2 FMA, MUFU 16 per clock per SM).  HBM and bf16 from
+    MEASURED_PEAKS.json when present."""
     p = {"sm": 152, "sm_mhz": 2070.0, "hbm_gbs": 6800.0, "src": "fallback"}
     try:
         mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -64,6 +71,21 @@ def peaks():
     clk = p["sm_mhz"] * 1e6
     p["fp32_tflops"] = p["sm"] * 128 * 2 * clk / 1e12
     p["fp64_tflops"] = p["sm"] * 2 * 2 * clk / 1e12
+    p["rsqrt_tops"] = p["sm"] * 16 * clk / 1e12
+    p["alu_src"] = "unit counts x max SM clock"
+    exe = os.path.join(ROOT, "paper_2001_05523_gb300", "_build", "peaks")
+    try:
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+        m = json.loads(r.stdout.strip().splitlines()[-1])
+        if r.returncode == 0 and m.get("status") == "no error":
+            p["fp32_tflops"] = m["fp32_fma_tflops"]
+            p["fp64_tflops"] = m["fp64_fma_tflops"]
+            p["rsqrt_tops"] = m["rsqrt_f32_tops"]
+            p["fp64_mma_tflops"] = m["fp64_mma_tflops"]
+            p["rsqrt_f64_tops"] = m["rsqrt_f64_approx_tops"]
+            p["alu_src"] = "measured (csrc/peaks.cu)"
+    except Exception:
+        pass
     return p
 
 
@@ -339,32 +361,30 @@ def main():
     names = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_backward", "near_regular",
              "near_singular"]
     dom = int(np.argmax(stage_m))
-    reg_pairs = st_m["regular_pairs"]
     sing = st_m["singular_pairs"]
-    work = {
-        "near_regular": reg_pairs * 49 * FLOPS_REG,
-        "near_singular": sum(sing[t] * PTS_SING_SLP[t] * FLOPS_SING[t] for t in range(3)),
-        "coupling": st_m["nfar"] * st_m["k"] ** 2 * (2 + 2 * nrhs),
+    evals = {
+        "near_regular": st_m["regular_evals"] * 49,
+        "near_singular": sum(sing[t] * PTS_SING[t] for t in range(3)),
+        "coupling": st_m["nfar"] * st_m["k"] ** 2,
     }
-    bound_peak = {"near_regular": pk["fp32_tflops"], "near_singular": pk["fp64_tflops"],
-                  "coupling": pk["fp32_tflops"]}
+    kern = {}
+    for nm, ev in evals.items():
+        ms = float(stage_m[names.index(nm)])
+        rate = ev / (ms / 1e3) / 1e9  # Geval/s
+        kern[nm] = {"ms": round(ms, 3), "evals": int(ev), "geval_s": rate,
+                    "frac_of_rsqrt_peak": rate / (pk["rsqrt_tops"] * 1e3)}
+    kern["coupling"]["fp32_tflops"] = st_m["nfar"] * st_m["k"] ** 2 * 2 * nrhs / (kern["coupling"]["ms"] / 1e3) / 1e12
+    kern["coupling"]["frac_of_fp32_peak"] = kern["coupling"]["fp32_tflops"] / pk["fp32_tflops"]
     dname = names[dom]
-    if dname in work:
-        achieved = work[dname] / (stage_m[dom] / 1e3) / 1e12
-        peak = bound_peak[dname]
-        roof = {"bound": "alu", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "flops_per_launch": work[dname],
-                "peak_source": f"unit counts x {pk['sm_mhz']:.0f} MHz (FP64 2 FMA/clk/SM, FP32 128 FMA/clk/SM)",
-                "note": "rsqrt counted as 1 flop; on GB300 an FP64 rsqrt costs ~4 FP64-pipe operations after the "
-                        "hardware approximation, so the FP64 pipe is ~90% busy (ncu) at this algorithmic fraction"}
-        roof["all_kernels"] = {
-            nm: {"ms": round(float(stage_m[names.index(nm)]), 3),
-                 "tflops": work[nm] / (stage_m[names.index(nm)] / 1e3) / 1e12,
-                 "frac": work[nm] / (stage_m[names.index(nm)] / 1e3) / 1e12 / bound_peak[nm]}
-            for nm in work}
+    if dname in kern:
+        roof = {"bound": "alu", "kernel": dname, "achieved": kern[dname]["geval_s"],
+                "peak": pk["rsqrt_tops"] * 1e3, "unit": "Geval/s", "frac": kern[dname]["frac_of_rsqrt_peak"],
+                "traffic": TRAFFIC.get(dname),
+                "peak_source": f"FP32 reciprocal square root rate, {pk['alu_src']} (one per kernel evaluation)",
+                "all_kernels": kern, "peaks": {k_: v for k_, v in pk.items() if k_ != "src"}}
     else:
-        roof = {"bound": "alu", "kernel": dname, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                "traffic": None}
+        roof = {"bound": "alu", "kernel": dname, "achieved": None, "peak": None, "unit": "Geval/s", "frac": None,
+                "traffic": None, "all_kernels": kern}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -377,7 +397,8 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64 (mixed: FP32 farfield/regular pairs, FP64 singular quadrature and accumulation)",
+        "dtype": "f32+f64 (mixed tier: FP32 farfield, regular pairs and edge/vertex Sauter-Schwab points; "
+                 "FP64 identical-pair quadrature, pair set-up, partial sums and accumulation)",
         "data": "synthetic",
         "config": {"workload": "sphere_2097152_slp_m4_eta2_leaf32_nrhs8", "n": n, "nrhs": nrhs, "m": 4,
                    "eta": 2.0, "leaf": 32, "tier": "mixed_fp32", "nearfield": "on the fly",

@@ -94,6 +94,11 @@ typedef struct {
     double last_apply_ms;      /* device time of the last timed apply         */
     double stage_ms[8];        /* per stage of the last timed apply, see      */
                                /* h2bem_apply_timed                            */
+    int64_t regular_evals;     /* pairs the regular nearfield kernel          */
+                               /* evaluates per apply (49 kernel evaluations   */
+                               /* each): every pair of the blocks (t, s >= t)  */
+                               /* sharing no vertex, both orders when s = t;   */
+                               /* its result serves (t, s) and (s, t)          */
 } h2bem_stats;
 
 /* Message of the last failed call on the calling thread (empty if none).

@@ -14,6 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libh2bem.so")
+PEAKS = os.path.join(OUT_DIR, "peaks")  # arithmetic-peak microbenchmark (csrc/peaks.cu)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "k_misc.cu", "k_nearsym.cu", "k_sing.cu", "k_far.cu", "k_coupling.cu", "k_grad.cu", "noalloc.cu"]
 
@@ -51,6 +52,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc, *_flags(s), "-c", src, "-o", obj])
+    psrc = os.path.join(CSRC, "peaks.cu")
+    if force or _stale(PEAKS, [psrc]):
+        jobs.append([nvcc, "-O3", *ARCH, psrc, "-o", PEAKS])
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,7 +63,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             sys.stderr.write(r.stdout + r.stderr)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
+    if any(j[-1] != PEAKS for j in jobs) or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "--cudart", "shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)

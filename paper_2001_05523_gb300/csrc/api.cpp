@@ -572,6 +572,7 @@ struct h2bem_op {
     double eta = 0;
     int64_t n = 0, nv = 0, nc = 0, nleaves = 0, depth = 0;
     int64_t nfar = 0, nnear = 0, near_pairs = 0, sing[3] = {0, 0, 0};
+    int64_t regular_evals = 0;  // pairs evaluated by the regular nearfield kernel
     h2::Consts consts{};
     // device geometry and tree
     DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
@@ -879,6 +880,25 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->dlevel.resize(op->level_parents.size());
     for (size_t L = 0; L < op->level_parents.size(); ++L)
         if ((rc = upload(op->dlevel[L], op->level_parents[L]))) return rc;
+    {
+        // pairs the regular nearfield kernel evaluates: all pairs of the
+        // blocks (t, s >= t) that share no vertex, both orders in s = t
+        std::vector<int> leaf_of(n);
+        for (int l : op->leaves_h)
+            for (int64_t p = tree->begin[l]; p < tree->end[l]; ++p) leaf_of[p] = l;
+        int64_t ev = 0;
+        for (size_t r = 0; r < op->near_u.rows.size(); ++r) {
+            const int t0 = op->near_u.rows[r];
+            for (int b = op->near_u.ptr[r]; b < op->near_u.ptr[r + 1]; ++b) {
+                const int s0 = op->near_u.col[b];
+                ev += (tree->end[t0] - tree->begin[t0]) * (tree->end[s0] - tree->begin[s0]);
+            }
+        }
+        for (int t = 0; t < 3; ++t)
+            for (size_t p = 0; p < slo[t].size(); ++p)
+                ev -= t == 0 ? 1 : leaf_of[iperm[slo[t][p]]] == leaf_of[iperm[shi[t][p]]] ? 2 : 1;
+        op->regular_evals = ev;
+    }
     for (int t = 0; t < 3; ++t) {
         const size_t np = slo[t].size();
         op->sing[t] = (int64_t)np;
@@ -1072,6 +1092,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->singular_pairs[1] = op->sing[1];
     st->singular_pairs[2] = op->sing[2];
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
+    st->regular_evals = op->regular_evals;
     st->k = op->k;
     st->launches = op->launches;
     st->last_apply_ms = op->last_ms;

@@ -21,32 +21,6 @@
 
 namespace h2 {
 
-namespace {
-constexpr double kInv4Pi = 0.07957747154594766788;
-
-template <typename T>
-__device__ __forceinline__ T rsq(T x);
-template <>
-__device__ __forceinline__ double rsq<double>(double x) { return rsqrt_nr(x); }
-template <>
-__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
-
-// nodes of cluster c along every axis: z[d*m + a]
-__device__ __forceinline__ void cluster_nodes(const Tree& t, const Consts& c, int cl, double* z) {
-    for (int e = threadIdx.x; e < 3 * c.m; e += blockDim.x) {
-        const int d = e / c.m, a = e % c.m;
-        z[e] = t.box[d * t.nc + cl] + t.box[(3 + d) * t.nc + cl] * c.cheb[a];
-    }
-}
-
-__device__ __forceinline__ double lagrange(const double* z, int m, int a, double y) {
-    double p = 1.0;
-    for (int k = 0; k < m; ++k)
-        if (k != a) p *= (y - z[k]) / (z[a] - z[k]);
-    return p;
-}
-}  // namespace
-
 // ---------------------------------------------------------------------------
 // Leaf transforms.  rule: nb points (u, v, w) on the unit simplex, exact for
 // total degree 3(m-1), weights summing to 1.  One CTA per leaf; the leaf's
@@ -307,15 +281,19 @@ __global__ void __launch_bounds__(128) k_leaf_bwd_st(Tree t, int k, const int* _
 // E1[ch][d][a'][a] = L_{t,a}^{(d)}(z_{ch,d}[a']).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void transfer_1d(const Tree& t, const Consts& c, int parent, const int* ch, T* E1, double* zp,
-                            double* zc) {
+__device__ void transfer_1d(const Tree& t, const Consts& c, int parent, const int* ch, T* E1) {
+    // child node z = c_ch + h_ch cheb[a'] in reference units of the parent,
+    // yhat = (z - c_p) / h_p, and L_a(yhat) = bary[a] prod_{b != a} (yhat - cheb[b])
     const int m = c.m;
-    cluster_nodes(t, c, parent, zp);
-    for (int q = 0; q < 2; ++q) cluster_nodes(t, c, ch[q], zc + q * 3 * m);
-    __syncthreads();
     for (int e = threadIdx.x; e < 2 * 3 * m * m; e += blockDim.x) {
         const int q = e / (3 * m * m), d = (e / (m * m)) % 3, ap = (e / m) % m, a = e % m;
-        E1[e] = (T)lagrange(zp + d * m, m, a, zc[q * 3 * m + d * m + ap]);
+        const int cl = ch[q];
+        const double yh = (t.box[d * t.nc + cl] - t.box[d * t.nc + parent] + t.box[(3 + d) * t.nc + cl] * c.cheb[ap]) *
+                          t.box[(6 + d) * t.nc + parent];
+        double pr = c.bary[a];
+        for (int b = 0; b < m; ++b)
+            if (b != a) pr *= yh - c.cheb[b];
+        E1[e] = (T)pr;
     }
     __syncthreads();
 }
@@ -364,10 +342,9 @@ __global__ void __launch_bounds__(256) k_upward(Tree t, Consts c, const int* __r
     T* tmp1 = in + k * NR;
     T* tmp2 = tmp1 + k * NR;
     T* out = tmp2 + k * NR;
-    __shared__ double zp[3 * kMaxM], zc[2 * 3 * kMaxM];
     const int p = parents[blockIdx.x];
     const int ch[2] = {t.child0[p], t.child1[p]};
-    transfer_1d<T>(t, c, p, ch, E1, zp, zc);
+    transfer_1d<T>(t, c, p, ch, E1);
     for (int q = 0; q < 2; ++q) {
         for (int e = threadIdx.x; e < k * NR; e += blockDim.x) in[e] = xh[(int64_t)ch[q] * k * NR + e];
         __syncthreads();
@@ -387,10 +364,9 @@ __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* _
     T* tmp1 = in + k * NR;
     T* tmp2 = tmp1 + k * NR;
     T* out = tmp2 + k * NR;
-    __shared__ double zp[3 * kMaxM], zc[2 * 3 * kMaxM];
     const int p = parents[blockIdx.x];
     const int ch[2] = {t.child0[p], t.child1[p]};
-    transfer_1d<T>(t, c, p, ch, E1, zp, zc);
+    transfer_1d<T>(t, c, p, ch, E1);
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) in[e] = yh[(int64_t)p * k * NR + e];
     __syncthreads();
     for (int q = 0; q < 2; ++q) {

@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("regular_pairs", ctypes.c_int64),
                 ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("last_apply_ms", ctypes.c_double),
-                ("stage_ms", ctypes.c_double * 8)]
+                ("stage_ms", ctypes.c_double * 8), ("regular_evals", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

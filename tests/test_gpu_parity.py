@@ -201,3 +201,25 @@ def test_mixed_fp32_m5_ellipsoid_16rhs(H, orc):
     y = gpu_apply(H, mesh, x, kernel=0, m=5, precision="mixed_fp32")
     ref = orc.H2(mesh, 0, m=5).matvec(x)
     assert rel(y, ref) < TOL["mixed_fp32"]
+
+
+def test_regular_evals_count(H, orc):
+    """regular_evals: pairs of the nearfield blocks (t, s >= t) that share no
+    vertex, both orders when s = t, counted by brute force from the oracle's
+    own tree and block lists."""
+    mesh = I.jitter(I.sphere(12), 0.01, 3)
+    ref = orc.H2(mesh, 0, m=4, eta=2.0, leaf=32)
+    tr = ref.tree()
+    _, (nt, ns) = ref.blocks()
+    tri = mesh.triangles[tr["perm"]]  # tree order
+    want = 0
+    for t, s in zip(nt, ns):
+        if s < t:
+            continue
+        a = tri[tr["begin"][t]:tr["end"][t]]
+        b = tri[tr["begin"][s]:tr["end"][s]]
+        share = (a[:, None, :, None] == b[None, :, None, :]).any(axis=(2, 3))
+        want += int((~share).sum())
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=4)
+    assert op.stats()["regular_evals"] == want
+    op.close()
