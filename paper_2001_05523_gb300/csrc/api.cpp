@@ -724,8 +724,11 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     h2bem_opts_default(&opts);
     if (opts_in) opts = *opts_in;
     if (opts.q_ss < 1 || opts.q_ss > h2::kMaxQss) return fail(H2BEM_ERR_ARG, "operator_create: q_ss must be in 1..%d", h2::kMaxQss);
-    if (opts.precision != H2BEM_FP64 && opts.precision != H2BEM_MIXED_FP32)
-        return fail(H2BEM_ERR_ARG, "operator_create: precision tier %d is not available", opts.precision);
+    if (opts.precision < H2BEM_FP64 || opts.precision > H2BEM_MIXED_BF16)
+        return fail(H2BEM_ERR_ARG, "operator_create: unknown precision tier %d", opts.precision);
+    if ((opts.precision == H2BEM_MIXED_TF32 && !h2::coupling_tc_supported(m, 0)) ||
+        (opts.precision == H2BEM_MIXED_BF16 && !h2::coupling_tc_supported(m, 2)))
+        return fail(H2BEM_ERR_ARG, "operator_create: the tensor-core tiers need m <= 5 (k <= 128), got m = %d", m);
     for (int r : opts.reserved)
         if (r) return fail(H2BEM_ERR_ARG, "operator_create: reserved option fields must be zero");
     for (int64_t c = 0; c < tree->nc; ++c)
@@ -1132,6 +1135,26 @@ static int ensure_workspace(h2bem_op* op, int NR) {
     return H2BEM_OK;
 }
 
+// Coupling stage: on the tensor cores in the TF32 / BF16 tiers where both
+// cluster vectors are FP32, else the SIMT kernels.
+static int tc_kind(const h2bem_op* op, bool xh64, bool yh64) {
+    if (xh64 || yh64) return -1;
+    if (op->precision == H2BEM_MIXED_TF32) return 0;
+    if (op->precision == H2BEM_MIXED_BF16) return 2;
+    return -1;
+}
+
+static void run_coupling(const h2bem_op* op, const h2::Tree& t, const h2::Consts& c, const Csr& far, bool xh64,
+                         bool yh64, int NR, void* xh, void* yh, cudaStream_t s) {
+    const int kind = tc_kind(op, xh64, yh64);
+    if (kind >= 0)
+        h2::launch_coupling_tc(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(), kind, NR,
+                               (const float*)xh, (float*)yh, s);
+    else
+        h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
+                            op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, s);
+}
+
 // One chunk of at most 16 right-hand sides, device buffers, tree order work.
 static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
                        bool transpose, bool timed) {
@@ -1171,8 +1194,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p, s);
         mark(3);
-        h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
-                            op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, op->xh.p, op->yh.p, s);
+        run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, s);
         mark(4);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
@@ -1312,7 +1334,11 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
         CU(cudaMemcpy2DAsync(y, ldy * sizeof(double), yd, ly * sizeof(double), op->n * sizeof(double), nrhs,
                              cudaMemcpyDeviceToHost, s));
     }
-    if (!xdev || !ydev) CU(cudaStreamSynchronize(s));
+    if (!xdev || !ydev) {
+        CU(cudaStreamSynchronize(s));
+        if (h2::coupling_tc_status(true))
+            return fail(H2BEM_ERR_TIMEOUT, "apply: a bounded wait of the tensor-core coupling expired");
+    }
     if (timed) {
         CU(cudaEventSynchronize(op->ev[9]));
         float ms = 0.f;
@@ -1323,6 +1349,8 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
             cudaEventElapsedTime(&ms, op->ev[map[i][0]], op->ev[map[i][1]]);
             op->stage_ms[i] = ms;
         }
+        if (h2::coupling_tc_status(true))
+            return fail(H2BEM_ERR_TIMEOUT, "apply_timed: a bounded wait of the tensor-core coupling expired");
     }
     return H2BEM_OK;
 }
@@ -1469,8 +1497,7 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
                                    xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
-        launch_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(), op->far.dcol.as<int>(),
-                        op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, s);
+        run_coupling(op, t, c, op->far, xh64, yh64, NR, xh, yh, s);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
         launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32, yh64,

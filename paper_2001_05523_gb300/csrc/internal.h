@@ -102,6 +102,13 @@ void launch_downward(const Tree& t, const Consts& c, int nparents, const int* pa
 // if xh64 / yh64, else float)
 void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
                      int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s);
+// coupling on the tensor cores (k_coupling_tc.cu), float x-hat / y-hat;
+// kind 0 TF32, 1 TF32x3, 2 BF16.  coupling_tc_status reads (and optionally
+// clears) the device flag an expired wait sets (H2BEM_ERR_TIMEOUT, else 0).
+bool coupling_tc_supported(int m, int kind);
+void launch_coupling_tc(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                        int kind, int NR, const float* xh, float* yh, cudaStream_t s);
+int coupling_tc_status(bool reset);
 
 }  // namespace h2
 

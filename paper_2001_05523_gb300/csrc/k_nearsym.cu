@@ -50,6 +50,31 @@ __device__ __forceinline__ float rsqrt_f32(float a) {
     return y;
 }
 
+// Packed FP32 pairs (f32x2): one instruction for two lanes of work, which
+// halves the issue slots of the point loop (the FP32 pipe rate is unchanged).
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Knuth's TwoSum: s + e = a + b exactly (round to nearest, no contraction).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -153,6 +178,17 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
             }
         }
     }
+    // FP32: the row points as packed pairs (0,1), (2,3), (4,5), and packed weights
+    f2 PX[3], PY[3], PZ[3], W2[3];
+    if constexpr (F32) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            PX[g] = pk(px[2 * g], px[2 * g + 1]);
+            PY[g] = pk(py[2 * g], py[2 * g + 1]);
+            PZ[g] = pk(pz[2 * g], pz[2 * g + 1]);
+            W2[g] = pk(w[2 * g], w[2 * g + 1]);
+        }
+    }
     T acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0;
@@ -234,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
                     // double layer: heights of the row points above plane j (hp)
                     // and of the column points above plane i (hq = H0q + ru_q f1 + rv_q f2)
                     T hp[7];
-                    T H0q = 0, f1 = 0, f2 = 0;
+                    T H0q = 0, f1 = 0, f2v = 0;
                     double cn[3] = {0, 0, 0}, cplane = 0.0;
                     if (DLPK) {
                         if (F32) {
@@ -263,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
                             for (int p = 0; p < 7; ++p) hp[p] = w[p] * fmaf(ru[p], e1, fmaf(rv[p], e2, H0));
                             H0q = (Dx * dl[0] + Dy * dl[1] + Dz * dl[2]) - H0;
                             f1 = -(snf[6 * kCol + jc] * dl[0] + snf[7 * kCol + jc] * dl[1] + snf[8 * kCol + jc] * dl[2]);
-                            f2 = -(snf[9 * kCol + jc] * dl[0] + snf[10 * kCol + jc] * dl[1] + snf[11 * kCol + jc] * dl[2]);
+                            f2v = -(snf[9 * kCol + jc] * dl[0] + snf[10 * kCol + jc] * dl[1] + snf[11 * kCol + jc] * dl[2]);
                         } else {
                             cn[0] = snd[jc];
                             cn[1] = snd[kCol + jc];
@@ -275,32 +311,69 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
                         }
                     }
                     T S1 = 0, S2 = 0;
+                    if constexpr (F32) {
+                        // row points in packed pairs (0,1), (2,3), (4,5) and point 6 alone
+                        f2 HP[3];
+                        if constexpr (DLPK) {
+#pragma unroll
+                            for (int g = 0; g < 3; ++g) HP[g] = pk(hp[2 * g], hp[2 * g + 1]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 7; ++q) {
+                            const float yx = Dx - sq[jc * 7 + q], yy = Dy - sq[kCol * 7 + jc * 7 + q],
+                                        yz = Dz - sq[2 * kCol * 7 + jc * 7 + q];
+                            const f2 YX = pk(yx, yx), YY = pk(yy, yy), YZ = pk(yz, yz);
+                            f2 A1 = 0, A2 = 0;
+#pragma unroll
+                            for (int g = 0; g < 3; ++g) {
+                                const f2 dx = add2(PX[g], YX), dy = add2(PY[g], YY), dz = add2(PZ[g], YZ);
+                                const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                                float r0, r1;
+                                upk(r2, r0, r1);
+                                const f2 ri = pk(rsqrt_f32(r0), rsqrt_f32(r1));
+                                if constexpr (!DLPK) {
+                                    A1 = fma2(W2[g], ri, A1);
+                                } else {
+                                    const f2 ri3 = mul2(mul2(ri, ri), ri);
+                                    A1 = fma2(HP[g], ri3, A1);
+                                    A2 = fma2(W2[g], ri3, A2);
+                                }
+                            }
+                            const float dx6 = px[6] + yx, dy6 = py[6] + yy, dz6 = pz[6] + yz;
+                            const float ri6 = rsqrt_f32(dx6 * dx6 + dy6 * dy6 + dz6 * dz6);
+                            float a0, a1;
+                            upk(A1, a0, a1);
+                            if constexpr (!DLPK) {
+                                S1 = fmaf(w[q], fmaf(w[6], ri6, a0 + a1), S1);
+                            } else {
+                                const float r36 = ri6 * ri6 * ri6;
+                                float b0, b1;
+                                upk(A2, b0, b1);
+                                const float hq = fmaf(ru[q], f1, fmaf(rv[q], f2v, H0q));
+                                S1 = fmaf(w[q], fmaf(hp[6], r36, a0 + a1), S1);
+                                S2 = fmaf(w[q] * hq, fmaf(w[6], r36, b0 + b1), S2);
+                            }
+                        }
+                    } else {
 #pragma unroll
                     for (int q = 0; q < 7; ++q) {
                         const T ex = sq[jc * 7 + q], ey = sq[kCol * 7 + jc * 7 + q], ez = sq[2 * kCol * 7 + jc * 7 + q];
-                        // F32: x_p - y_q = (x_p - c_i) + (D - (y_q - c_j));  F64: x_p - y_q
-                        const T yx = F32 ? Dx - ex : ex, yy = F32 ? Dy - ey : ey, yz = F32 ? Dz - ez : ez;
+                        const T yx = ex, yy = ey, yz = ez;
                         T sp1 = 0, sp2 = 0;
 #pragma unroll
                         for (int p = 0; p < 7; ++p) {
-                            const T dx = F32 ? px[p] + yx : px[p] - yx;
-                            const T dy = F32 ? py[p] + yy : py[p] - yy;
-                            const T dz = F32 ? pz[p] + yz : pz[p] - yz;
+                            const T dx = px[p] - yx;
+                            const T dy = py[p] - yy;
+                            const T dz = pz[p] - yz;
                             const T r2 = dx * dx + dy * dy + dz * dz;
                             if (!DLPK) {
-                                if (F32) {
-                                    sp1 = fmaf(w[p], rsqrt_f32(r2), sp1);
-                                } else {
-                                    // w/2 y (3 - r2 y^2): one Newton step for 1/sqrt(r2) folded in
-                                    double y;
-                                    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"((double)r2));
-                                    const double tq = r2 * y;
-                                    sp1 = fma(w[p] * y, fma(-tq, y, 3.0), sp1);
-                                }
+                                // w/2 y (3 - r2 y^2): one Newton step for 1/sqrt(r2) folded in
+                                double y;
+                                asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"((double)r2));
+                                const double tq = r2 * y;
+                                sp1 = fma(w[p] * y, fma(-tq, y, 3.0), sp1);
                             } else {
-                                T ri;
-                                if (F32) ri = rsqrt_f32(r2);
-                                else ri = (T)rsqrt_nr((double)r2);
+                                const T ri = (T)rsqrt_nr((double)r2);
                                 const T ri3 = ri * ri * ri;
                                 sp1 += hp[p] * ri3;
                                 sp2 += w[p] * ri3;
@@ -309,12 +382,11 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
                         if (!DLPK) {
                             S1 += w[q] * sp1;
                         } else {
-                            T hq;
-                            if (F32) hq = fmaf(ru[q], f1, fmaf(rv[q], f2, H0q));
-                            else hq = (T)(ex * rn[0] + ey * rn[1] + ez * rn[2] - rplane);
+                            const T hq = (T)(ex * rn[0] + ey * rn[1] + ez * rn[2] - rplane);
                             S1 += w[q] * sp1;
                             S2 += (w[q] * hq) * sp2;
                         }
+                    }
                     }
                     const T aa = ai * sarea[jc];
                     if (!DLPK) {
