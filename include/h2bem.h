@@ -78,7 +78,17 @@ typedef struct {
                         /*    non-default stream replay a captured CUDA graph of their launch      */
                         /*    sequence when called again with the same buffers, sizes and          */
                         /*    direction (the second such call captures it); 0: plain launches     */
-    int reserved[4];    /* must be zero                                                            */
+    int autotune;       /* 1: the first apply with a given right-hand-side width and direction    */
+                        /*    times the launch variants of the regular nearfield (one CTA per     */
+                        /*    row leaf, or persistent CTAs taking rows from a work counter) and   */
+                        /*    of the SIMT coupling (2, 4 or 8 slices per CTA, one CTA per row or  */
+                        /*    persistent) on the operator's own data and keeps the fastest; the   */
+                        /*    variants sum in different orders, so results differ by rounding.    */
+                        /*    No tuning while the stream is being captured.  0: defaults (one     */
+                        /*    CTA per row, 4 slices).  2 + v (v = 0..11) fixes a variant:         */
+                        /*    v = nearfield persistent + 2 coupling persistent + 4 i, where i =   */
+                        /*    0, 1, 2 selects 2, 4, 8 slices                                       */
+    int reserved[3];    /* must be zero                                                            */
 } h2bem_opts;
 
 /* Statistics of an operator (counts are exact, from its own block lists). */
@@ -94,6 +104,10 @@ typedef struct {
     double last_apply_ms;      /* device time of the last timed apply         */
     double stage_ms[8];        /* per stage of the last timed apply, see      */
                                /* h2bem_apply_timed                            */
+    int64_t launch_variant[4]; /* of the last apply: regular nearfield         */
+                               /* persistent (0/1), SIMT coupling slices per   */
+                               /* CTA, SIMT coupling persistent (0/1), 1 if    */
+                               /* chosen by the autotuner                      */
     int64_t regular_evals;     /* pairs the regular nearfield kernel          */
                                /* evaluates per apply (49 kernel evaluations   */
                                /* each): every pair of the blocks (t, s >= t)  */

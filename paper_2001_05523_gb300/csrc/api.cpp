@@ -600,6 +600,15 @@ struct h2bem_op {
     cudaEvent_t ev[10] = {};
     double last_ms = 0.0, stage_ms[8] = {0};
     int64_t launches = 0;
+    // launch variants (autotune): per right-hand-side width slot and direction
+    int autotune = 0;
+    struct Tuned {
+        bool done = false;
+        h2::LaunchCfg near, coup;  // work pointers filled in at launch
+        bool near_persist = false, coup_persist = false;
+    } tuned[4][2];
+    int64_t last_variant[4] = {0, 4, 0, 0};
+    DevBuf work;  // row counters of persistent launches (2 ints)
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
     int64_t ws_gen = 0;
@@ -748,6 +757,19 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->q_ss = opts.q_ss;
     op->cache_singular = opts.cache_singular ? 1 : 0;
     op->use_graph = opts.use_graph ? 1 : 0;
+    if (opts.autotune < 0 || opts.autotune > 13)
+        return fail(H2BEM_ERR_ARG, "operator_create: autotune must be 0, 1 or 2..13, got %d", opts.autotune);
+    op->autotune = opts.autotune == 1 ? 1 : 0;
+    if (opts.autotune >= 2) {  // a fixed launch variant for every width and direction
+        const int v = opts.autotune - 2;
+        for (auto& slot : op->tuned)
+            for (auto& tu : slot) {
+                tu.done = true;
+                tu.near_persist = (v & 1) != 0;
+                tu.coup_persist = (v & 2) != 0;
+                tu.coup.nsl = v / 4 == 0 ? 2 : v / 4 == 1 ? 4 : 8;
+            }
+    }
     op->n = mesh->nt;
     op->nv = mesh->nv;
     op->nc = tree->nc;
@@ -878,7 +900,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         (rc = upload(op->cbox, box)) || (rc = upload(op->leaves, op->leaves_h)))
         return rc;
     if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
-        (rc = op->near_u.upload_all()))
+        (rc = op->near_u.upload_all()) || (rc = op->work.alloc(4 * sizeof(int))))
         return rc;
     op->dlevel.resize(op->level_parents.size());
     for (size_t L = 0; L < op->level_parents.size(); ++L)
@@ -1096,6 +1118,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->singular_pairs[2] = op->sing[2];
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
     st->regular_evals = op->regular_evals;
+    for (int i = 0; i < 4; ++i) st->launch_variant[i] = op->last_variant[i];
     st->k = op->k;
     st->launches = op->launches;
     st->last_apply_ms = op->last_ms;
@@ -1145,14 +1168,55 @@ static int tc_kind(const h2bem_op* op, bool xh64, bool yh64) {
 }
 
 static void run_coupling(const h2bem_op* op, const h2::Tree& t, const h2::Consts& c, const Csr& far, bool xh64,
-                         bool yh64, int NR, void* xh, void* yh, cudaStream_t s) {
+                         bool yh64, int NR, void* xh, void* yh, const h2::LaunchCfg& cfg, cudaStream_t s) {
     const int kind = tc_kind(op, xh64, yh64);
     if (kind >= 0)
         h2::launch_coupling_tc(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(), kind, NR,
                                (const float*)xh, (float*)yh, s);
     else
         h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
-                            op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, s);
+                            op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, cfg, s);
+}
+
+static int nr_slot(int NR) { return NR == 1 ? 0 : NR == 4 ? 1 : NR == 8 ? 2 : 3; }
+
+// device time of f() on stream s: best of two after one warm-up (synchronises)
+template <typename F>
+static float time_on(cudaStream_t s, F f) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    f();
+    float best = 1e30f;
+    for (int r = 0; r < 2; ++r) {
+        cudaEventRecord(a, s);
+        f();
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// the launch variants an apply uses (tuned ones once the autotuner has run)
+static void launch_cfgs(h2bem_op* op, int NR, bool transpose, h2::LaunchCfg& near, h2::LaunchCfg& coup) {
+    const auto& tu = op->tuned[nr_slot(NR)][transpose ? 1 : 0];
+    int* w = op->work.as<int>();
+    near = h2::LaunchCfg{};
+    coup = h2::LaunchCfg{};
+    if (tu.done) {
+        near.work = tu.near_persist ? w : nullptr;
+        coup.nsl = tu.coup.nsl;
+        coup.work = tu.coup_persist ? w + 1 : nullptr;
+    }
+    op->last_variant[0] = near.work != nullptr;
+    op->last_variant[1] = coup.nsl;
+    op->last_variant[2] = coup.work != nullptr;
+    op->last_variant[3] = tu.done ? 1 : 0;
 }
 
 // One chunk of at most 16 right-hand sides, device buffers, tree order work.
@@ -1178,9 +1242,30 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         if (timed) cudaEventRecord(op->ev[i], s);
     };
     int64_t nl = 0;  // kernels launched by this chunk
+    // autotuning on the first apply of this width and direction (not under capture)
+    auto& tu = op->tuned[nr_slot(NR)][transpose ? 1 : 0];
+    bool tune_now = false;
+    if (op->autotune && !tu.done) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        tune_now = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    }
+    auto near_launch = [&](int* work) {
+        h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
+                            op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR,
+                            op->xp.as<double>(), op->yp.as<double>(), work, s);
+    };
     mark(0);
     h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
     CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    if (tune_now && op->near_u.nrows() > 0) {
+        const float t_plain = time_on(s, [&] { near_launch(nullptr); });
+        const float t_pers = time_on(s, [&] { near_launch(op->work.as<int>()); });
+        tu.near_persist = t_pers < t_plain;
+        CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    }
+    if (tune_now && op->nfar > 0 && tc_kind(op, xh64, yh64) < 0 && (op->m == 4 || op->m == 5)) {
+        tu.coup.nsl = -1;  // tuned below, once x-hat is ready
+    }
     nl += 1;
     mark(1);
     if (op->nfar > 0) {
@@ -1194,7 +1279,28 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p, s);
         mark(3);
-        run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, s);
+        if (tune_now && tu.coup.nsl == -1) {
+            float best = 1e30f;
+            for (int nsl : {2, 4, 8})
+                for (int pers = 0; pers < 2; ++pers) {
+                    h2::LaunchCfg cf;
+                    cf.nsl = nsl;
+                    cf.work = pers ? op->work.as<int>() + 1 : nullptr;
+                    const float ms = time_on(s, [&] { run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, cf, s); });
+                    if (ms < best) {
+                        best = ms;
+                        tu.coup.nsl = nsl;
+                        tu.coup_persist = pers != 0;
+                    }
+                }
+        }
+        if (tune_now) {
+            if (tu.coup.nsl < 0) tu.coup.nsl = 4;
+            tu.done = true;
+        }
+        h2::LaunchCfg cfg_near, cfg_coup;
+        launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
+        run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
         mark(4);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
@@ -1207,9 +1313,12 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     mark(6);
     // nearfield, regular pairs: each unordered pair of leaves once, both directions
-    h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
-                        op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR, op->xp.as<double>(),
-                        op->yp.as<double>(), s);
+    if (tune_now) tu.done = true;  // operators without farfield
+    {
+        h2::LaunchCfg cfg_near, cfg_coup;
+        launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
+        near_launch(cfg_near.work);
+    }
     nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
     for (int ty = 0; ty < 3; ++ty) {
@@ -1417,9 +1526,9 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
             CU(cudaMemsetAsync(yh, 0, hv, s));
             CU(cudaMemsetAsync(zh, 0, hv, s));
             h2::launch_coupling(t, c, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(),
-                                op->far.dcol.as<int>(), 0, true, true, NR, xh, yh, s);
+                                op->far.dcol.as<int>(), 0, true, true, NR, xh, yh, h2::LaunchCfg{}, s);
             h2::launch_coupling(t, c, op->far_t.nrows(), op->far_t.drows.as<int>(), op->far_t.dptr.as<int>(),
-                                op->far_t.dcol.as<int>(), 0, true, true, NR, wh, zh, s);
+                                op->far_t.dcol.as<int>(), 0, true, true, NR, wh, zh, h2::LaunchCfg{}, s);
             for (size_t L = 0; L < op->level_parents.size(); ++L) {
                 h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, yh, s);
                 h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), true, NR, zh, s);
@@ -1497,14 +1606,20 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
                                    xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
-        run_coupling(op, t, c, op->far, xh64, yh64, NR, xh, yh, s);
+        h2::LaunchCfg cfg_near, cfg_coup;
+        launch_cfgs(op, NR, false, cfg_near, cfg_coup);
+        run_coupling(op, t, c, op->far, xh64, yh64, NR, xh, yh, cfg_coup, s);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
         launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32, yh64,
                                     NR, op->basisV.p, yh, yp, s);
     }
-    launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
-                    op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, s);
+    {
+        h2::LaunchCfg cfg_near, cfg_coup;
+        launch_cfgs(op, NR, false, cfg_near, cfg_coup);
+        launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
+                        op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, cfg_near.work, s);
+    }
     for (int ty = 0; ty < 3; ++ty) {
         if (ty == 0 && dlp) continue;
         const int np = (int)op->sp_count[ty];

@@ -69,7 +69,7 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 // a row is t itself).  ker: SLP or DLP; transpose applies K^T (double layer).
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     cudaStream_t s);
+                     int* work, cudaStream_t s);
 
 // nearfield, singular pairs of one type (canonical orientation, see api.cpp)
 //   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the
@@ -98,10 +98,21 @@ void launch_upward(const Tree& t, const Consts& c, int nparents, const int* pare
                    cudaStream_t s);
 void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,
                      cudaStream_t s);
+// Launch variant of a row-parallel kernel: work != nullptr runs persistent
+// CTAs (as many as fit on the GPU) that take rows from the counter *work
+// (reset by the launcher); nsl = slices of the SIMT coupling (2, 4 or 8).
+struct LaunchCfg {
+    int nsl = 4;
+    int* work = nullptr;
+};
+// CTAs of `func` resident on the whole GPU at once (occupancy x SMs)
+int resident_ctas(const void* func, int threads, size_t smem);
+
 // precision: 0 FP64 (xh, yh double), 1 FP32 SIMT arithmetic (xh / yh double
 // if xh64 / yh64, else float)
 void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s);
+                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, const LaunchCfg& cfg,
+                     cudaStream_t s);
 // coupling on the tensor cores (k_coupling_tc.cu), float x-hat / y-hat;
 // kind 0 TF32, 1 TF32x3, 2 BF16.  coupling_tc_status reads (and optionally
 // clears) the device flag an expired wait sets (H2BEM_ERR_TIMEOUT, else 0).

@@ -2,6 +2,8 @@
 // S_ts[nu,mu] = g(xi_{t,nu}, xi_{s,mu}) of the tensor Chebyshev interpolant):
 //   yh_t[nu] = sum_{(t,s) farfield} sum_mu S_ts[nu,mu] xh_s[mu],
 // with S_ts generated on the fly; SIMT kernels in FP64 or FP32.
+#include <algorithm>
+
 #include "dmath.cuh"
 #include "internal.h"
 
@@ -110,18 +112,18 @@ __global__ void __launch_bounds__(256) k_coupling_simt(Tree t, Consts c, const i
 // Register-blocked variant for compile-time m: thread (row, slice) owns the
 // m target nodes nu = (a, b, c), a = 0..m-1, of one (b, c) row and the mu-rows
 // (jc, jb) of its slice; every x-hat value loaded from shared memory feeds m
-// entries.  Slices are reduced in shared memory at the end.
-template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
-__global__ void __launch_bounds__(M * M * 4) k_coupling_rows(Tree t, Consts c, const int* __restrict__ rows,
-                                                             const int* __restrict__ ptr, const int* __restrict__ col,
-                                                             const TX* __restrict__ xh, TY* __restrict__ yh) {
+// entries.  Slices are reduced in shared memory at the end.  NSL slices per
+// CTA (blockDim = NSL m^2): a tile shape the autotuner chooses.
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M, int NSL>
+__device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, const int* __restrict__ rows,
+                                             const int* __restrict__ ptr, const int* __restrict__ col,
+                                             const TX* __restrict__ xh, TY* __restrict__ yh, int bi) {
     constexpr int K = M * M * M, M2 = M * M;
-    constexpr int NSL = 4;  // slices of the mu-rows; blockDim = 4 m^2 (small CTAs, many per SM)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* xs = reinterpret_cast<TA*>(smem_raw);  // [K][NR]; reused for the reduction [NSL][K][NR]
     __shared__ double zt[3 * M], zs[3 * M];
     __shared__ TS D2[3 * M2];
-    const int row = rows[blockIdx.x];
+    const int row = rows[bi];
     const int rg = threadIdx.x % M2, sl = threadIdx.x / M2;
     const bool active = sl < NSL;
     const int ib = rg % M, ic = rg / M;
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(M * M * 4) k_coupling_rows(Tree t, Consts c, c
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[a][r] = 0;
-    for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
+    for (int b = ptr[bi]; b < ptr[bi + 1]; ++b) {
         const int s = col[b];
         __syncthreads();
         cluster_nodes(t, c, s, zs);
@@ -181,14 +183,51 @@ __global__ void __launch_bounds__(M * M * 4) k_coupling_rows(Tree t, Consts c, c
     }
 }
 
+// One CTA per row cluster (work == nullptr), or persistent CTAs that take the
+// next row from the counter *work (zero before the launch) until none is left.
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M, int NSL, bool PERSIST>
+__global__ void __launch_bounds__(M * M * NSL)
+    k_coupling_rows(Tree t, Consts c, int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
+                    const int* __restrict__ col, const TX* __restrict__ xh, TY* __restrict__ yh, int* __restrict__ work) {
+    if constexpr (!PERSIST) {
+        coupling_row<TS, TA, TX, TY, NR, M, NSL>(t, c, rows, ptr, col, xh, yh, blockIdx.x);
+        return;
+    }
+    __shared__ int s_bi;
+    while (true) {
+        __syncthreads();  // the previous row is done with shared memory and s_bi
+        if (threadIdx.x == 0) s_bi = atomicAdd(work, 1);
+        __syncthreads();
+        const int bi = s_bi;
+        if (bi >= nrows) break;
+        coupling_row<TS, TA, TX, TY, NR, M, NSL>(t, c, rows, ptr, col, xh, yh, bi);
+    }
+}
+
+template <typename TS, typename TA, typename TX, typename TY, int NR, int M, int NSL>
+static void coupling_rows_nsl(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                              const int* col, const void* xh, void* yh, int* work, cudaStream_t s) {
+    constexpr int K = M * M * M;
+    const size_t smem = sizeof(TA) * (size_t)NSL * K * NR;
+    if (!work) {
+        auto kern = k_coupling_rows<TS, TA, TX, TY, NR, M, NSL, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<nrows, M * M * NSL, smem, s>>>(t, c, nrows, rows, ptr, col, (const TX*)xh, (TY*)yh, nullptr);
+        return;
+    }
+    auto kern = k_coupling_rows<TS, TA, TX, TY, NR, M, NSL, true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::min(nrows, resident_ctas((const void*)kern, M * M * NSL, smem));
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    kern<<<grid, M * M * NSL, smem, s>>>(t, c, nrows, rows, ptr, col, (const TX*)xh, (TY*)yh, work);
+}
+
 template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
 static void coupling_rows(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                          const void* xh, void* yh, cudaStream_t s) {
-    constexpr int K = M * M * M, NSL = 4;
-    const size_t smem = sizeof(TA) * (size_t)NSL * K * NR;
-    cudaFuncSetAttribute(k_coupling_rows<TS, TA, TX, TY, NR, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coupling_rows<TS, TA, TX, TY, NR, M><<<nrows, M * M * NSL, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh,
-                                                                           (TY*)yh);
+                          const void* xh, void* yh, const LaunchCfg& cfg, cudaStream_t s) {
+    if (cfg.nsl == 2) coupling_rows_nsl<TS, TA, TX, TY, NR, M, 2>(t, c, nrows, rows, ptr, col, xh, yh, cfg.work, s);
+    else if (cfg.nsl == 8) coupling_rows_nsl<TS, TA, TX, TY, NR, M, 8>(t, c, nrows, rows, ptr, col, xh, yh, cfg.work, s);
+    else coupling_rows_nsl<TS, TA, TX, TY, NR, M, 4>(t, c, nrows, rows, ptr, col, xh, yh, cfg.work, s);
 }
 
 template <typename TS, typename TA, typename TX, typename TY, int NR, int M>
@@ -201,25 +240,26 @@ static void coupling_m(const Tree& t, const Consts& c, int nrows, const int* row
 
 template <typename TS, typename TA, typename TX, typename TY, int NR>
 static void coupling_simt(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                          const void* xh, void* yh, cudaStream_t s) {
-    if (c.m == 4) coupling_rows<TS, TA, TX, TY, NR, 4>(t, c, nrows, rows, ptr, col, xh, yh, s);
-    else if (c.m == 5) coupling_rows<TS, TA, TX, TY, NR, 5>(t, c, nrows, rows, ptr, col, xh, yh, s);
+                          const void* xh, void* yh, const LaunchCfg& cfg, cudaStream_t s) {
+    if (c.m == 4) coupling_rows<TS, TA, TX, TY, NR, 4>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s);
+    else if (c.m == 5) coupling_rows<TS, TA, TX, TY, NR, 5>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s);
     else coupling_m<TS, TA, TX, TY, NR, 0>(t, c, nrows, rows, ptr, col, xh, yh, s);
 }
 
 void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, cudaStream_t s) {
+                     int precision, bool xh64, bool yh64, int NR, const void* xh, void* yh, const LaunchCfg& cfg,
+                     cudaStream_t s) {
     if (nrows <= 0) return;
     if (precision == 0) {
-        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     } else if (xh64) {
         // input side in double (double layer, K x): the differentiated basis makes
         // S x-hat cancel strongly, so S and its sums are FP64; y-hat is stored float
-        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     } else if (yh64) {  // output side in double (double layer, K^T x): FP32 entries, FP64 sums
-        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     } else {
-        H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, s)))
+        H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     }
 }
 

@@ -1,6 +1,8 @@
 // Gather/scatter between the caller's column-major vectors (user triangle
 // order, leading dimension ld) and the library's tree-ordered, RHS-interleaved
 // work vectors xp[pos * NR + r] (NR >= nrhs, padded columns are zero).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace h2 {
@@ -79,6 +81,14 @@ void launch_geom(const double* xyz, const int* tri, const int* perm, int n, cons
                  double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
                  cudaStream_t s) {
     k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef);
+}
+
+int resident_ctas(const void* func, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem);
+    return std::max(1, per_sm) * std::max(1, sms);
 }
 
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,

@@ -31,6 +31,7 @@
 // of tau_j; E . n_i = 0 on the plane of tau_i) and D . n_j as an exact
 // double-float dot product: Dekker's product (the FMA residual of each
 // product) and Knuth's TwoSum for the cancelling sum.
+#include <algorithm>
 #include <type_traits>
 
 #include "dmath.cuh"
@@ -103,11 +104,12 @@ struct Smem {
 };
 }  // namespace
 
+// the work of one row leaf (index bi of the row list)
 template <int NR, bool DLPK, bool F32>
-__global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(Geom g, Tree t, Consts c, const int* __restrict__ rows,
-                                                       const int* __restrict__ ptr, const int* __restrict__ col,
-                                                       bool transpose, const double* __restrict__ xp,
-                                                       double* __restrict__ yp) {
+__device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const Consts& c,
+                                             const int* __restrict__ rows, const int* __restrict__ ptr,
+                                             const int* __restrict__ col, bool transpose,
+                                             const double* __restrict__ xp, double* __restrict__ yp, int bi) {
     using T = typename std::conditional<F32, float, double>::type;
     using L = Smem<T, NR, DLPK>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
     float* snf = reinterpret_cast<float*>(smem + L::NRM);
     double* snd = reinterpret_cast<double*>(smem + L::NRM);
 
-    const int row = rows[blockIdx.x];
+    const int row = rows[bi];
     const int rb = t.begin[row], R = t.end[row] - rb;
     const int K = kThreads / R;
     const int tid = threadIdx.x;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0;
 
-    const int bbeg = ptr[blockIdx.x], bend = ptr[blockIdx.x + 1];
+    const int bbeg = ptr[bi], bend = ptr[bi + 1];
     for (int b = bbeg; b < bend;) {
         // chunk: column leaves b .. b2-1 (the same decision in every thread)
         int ctot = 0, b2 = b;
@@ -427,37 +429,69 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2) k_near_sym(G
     }
 }
 
+// One CTA per row leaf (work == nullptr), or persistent CTAs that take the
+// next row from the counter *work (zero before the launch) until none is left.
+template <int NR, bool DLPK, bool F32, bool PERSIST>
+__global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2)
+    k_near_sym(Geom g, Tree t, Consts c, int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
+               const int* __restrict__ col, bool transpose, const double* __restrict__ xp, double* __restrict__ yp,
+               int* __restrict__ work) {
+    if constexpr (!PERSIST) {
+        near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, blockIdx.x);
+        return;
+    }
+    __shared__ int s_bi;
+    while (true) {
+        __syncthreads();  // the previous row is done with shared memory and s_bi
+        if (threadIdx.x == 0) s_bi = atomicAdd(work, 1);
+        __syncthreads();
+        const int bi = s_bi;
+        if (bi >= nrows) break;
+        near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, bi);
+    }
+}
+
 template <int NR, bool DLPK, bool F32>
 static void near_sym_go(int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c, const int* rows,
-                        const int* ptr, const int* col, bool tr, const double* xp, double* yp) {
+                        const int* ptr, const int* col, bool tr, const double* xp, double* yp, int* work) {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr size_t smem = Smem<T, NR, DLPK>::BYTES;
-    cudaFuncSetAttribute(k_near_sym<NR, DLPK, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_near_sym<NR, DLPK, F32><<<nrows, kThreads, smem, s>>>(g, t, c, rows, ptr, col, tr, xp, yp);
+    if (!work) {
+        cudaFuncSetAttribute(k_near_sym<NR, DLPK, F32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_near_sym<NR, DLPK, F32, false><<<nrows, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp,
+                                                                      nullptr);
+        return;
+    }
+    auto kern = k_near_sym<NR, DLPK, F32, true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::min(nrows, resident_ctas((const void*)kern, kThreads, smem));
+    cudaMemsetAsync(work, 0, sizeof(int), s);
+    kern<<<grid, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, work);
 }
 
 template <int NR>
 static void near_sym_nr(int ker, bool fp32, int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c,
-                        const int* rows, const int* ptr, const int* col, bool tr, const double* xp, double* yp) {
+                        const int* rows, const int* ptr, const int* col, bool tr, const double* xp, double* yp,
+                        int* work) {
     const bool dlp = ker != SLP;
     if (fp32) {
-        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp);
-        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp);
+        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
+        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
     } else {
-        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp);
-        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp);
+        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
+        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
     }
 }
 
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     cudaStream_t s) {
+                     int* work, cudaStream_t s) {
     if (nrows <= 0) return;
     switch (NR) {
-        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp); break;
-        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp); break;
-        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp); break;
-        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp); break;
+        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
+        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
+        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
+        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
     }
 }
 

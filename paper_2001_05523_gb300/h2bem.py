@@ -39,7 +39,7 @@ class H2bemError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -48,12 +48,14 @@ class Stats(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("regular_pairs", ctypes.c_int64),
                 ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("last_apply_ms", ctypes.c_double),
-                ("stage_ms", ctypes.c_double * 8), ("regular_evals", ctypes.c_int64)]
+                ("stage_ms", ctypes.c_double * 8), ("launch_variant", ctypes.c_int64 * 4),
+                ("regular_evals", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["singular_pairs"] = list(self.singular_pairs)
         d["stage_ms"] = list(self.stage_ms)
+        d["launch_variant"] = list(self.launch_variant)
         return d
 
 
@@ -265,7 +267,7 @@ class BatchOperator:
 
     def __init__(self, meshes, kernel: str | int = "slp", m: int = 4, eta: float = 2.0, leaf_size: int = 32,
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
-                 use_graph: bool = False):
+                 use_graph: bool = False, autotune: int = 0):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -276,6 +278,7 @@ class BatchOperator:
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.cache_singular = int(cache_singular)
         o.use_graph = int(use_graph)
+        o.autotune = int(autotune)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
     def close(self):
@@ -308,7 +311,7 @@ class Operator:
 
     def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
-                 use_graph: bool = False):
+                 use_graph: bool = False, autotune: int = 0):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -318,6 +321,7 @@ class Operator:
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         o.cache_singular = int(cache_singular)
         o.use_graph = int(use_graph)
+        o.autotune = int(autotune)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):
