@@ -204,6 +204,8 @@ def main():
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 tier")
+    ap.add_argument("--tier", default="mixed_fp32", choices=["mixed_fp32", "mixed_tf32", "mixed_bf16"],
+                    help="precision tier of the timed step (default mixed_fp32)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -247,8 +249,9 @@ def main():
 
     def timed_tier(precision: str, cache: bool, steps: int):
         t0 = time.perf_counter()
+        # autotune: the first warm-up apply times the launch variants and keeps the fastest
         op = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, eta=2.0, leaf_size=32,
-                        precision=precision, cache_singular=cache)
+                        precision=precision, cache_singular=cache, autotune=1)
         setup_s = time.perf_counter() - t0
         y = torch.empty_like(x)
         for _ in range(args.warmup):
@@ -271,7 +274,7 @@ def main():
 
     results = {}
     with ClockSampler(local) as clk:
-        op_m, y_m, ms_m, stage_m, st_m, setup_m = timed_tier("mixed_fp32", False, args.steps)
+        op_m, y_m, ms_m, stage_m, st_m, setup_m = timed_tier(args.tier, False, args.steps)
     clocks = clk.summary()
     results["mixed_fp32"] = (ms_m, stage_m)
     # e2e through the public API with pinned host buffers (copies inside the timed region)
@@ -308,6 +311,17 @@ def main():
                                          "stage_ms": [round(v, 3) for v in stage_dc]}
         extra["speedup_mixed_vs_fp64_cached"] = ms_dc / ms_c
 
+    # tensor-core tiers of the coupling (tcgen05): same workload, error against the FP64 tier
+    if not args.no_fp64:
+        tiers = {}
+        for prec in ("mixed_tf32", "mixed_bf16"):
+            opt, y_t, ms_t, stage_t, _, _ = timed_tier(prec, False, args.steps)
+            opt.close()
+            tiers[prec] = {"value": world * n * nrhs / (ms_t / 1e3), "ms_per_step": ms_t,
+                           "stage_ms": [round(v, 3) for v in stage_t],
+                           "rel_err_vs_fp64": float(torch.linalg.norm(y_t - y_d) / torch.linalg.norm(y_d))}
+        extra["tensor_core_tiers"] = tiers
+
     # other workloads of the benchmark family (reported beside the headline)
     if not args.no_fp64:
         # 64 uneven jittered meshes (sphere / ellipsoid / cube, 2k-65k triangles) as one
@@ -338,8 +352,8 @@ def main():
         me = I.ellipsoid(128)
         xe = torch.from_numpy(I.rhs(me.nt, 16, seed=5)).to(dev)
         out_e = {}
-        for prec in ("mixed_fp32", "fp64"):
-            oe = H.Operator(me.vertices, me.triangles, kernel="slp", m=5, eta=2.0, precision=prec)
+        for prec in ("mixed_fp32", "mixed_tf32", "mixed_bf16", "fp64"):
+            oe = H.Operator(me.vertices, me.triangles, kernel="slp", m=5, eta=2.0, precision=prec, autotune=1)
             ye = torch.empty_like(xe)
             for _ in range(2):
                 H.h2bem_apply(oe.op, xe, ye, stream)
@@ -352,8 +366,9 @@ def main():
             out_e[prec] = (e0.elapsed_time(e1), ye.clone())
             oe.close()
         out = {p_: {"ms": v[0], "triangles_rhs_per_s": me.nt * 16 / (v[0] / 1e3)} for p_, v in out_e.items()}
-        out["rel_err_mixed_vs_fp64"] = float(torch.linalg.norm(out_e["mixed_fp32"][1] - out_e["fp64"][1]) /
-                                             torch.linalg.norm(out_e["fp64"][1]))
+        for p_ in ("mixed_fp32", "mixed_tf32", "mixed_bf16"):
+            out[p_]["rel_err_vs_fp64"] = float(torch.linalg.norm(out_e[p_][1] - out_e["fp64"][1]) /
+                                               torch.linalg.norm(out_e["fp64"][1]))
         extra["ellipsoid131k_m5_16rhs"] = out
 
     # roofline of the dominant kernel of the headline tier
@@ -400,8 +415,8 @@ def main():
         "dtype": "f32+f64 (mixed tier: FP32 farfield, regular pairs and edge/vertex Sauter-Schwab points; "
                  "FP64 identical-pair quadrature, pair set-up, partial sums and accumulation)",
         "data": "synthetic",
-        "config": {"workload": "sphere_2097152_slp_m4_eta2_leaf32_nrhs8", "n": n, "nrhs": nrhs, "m": 4,
-                   "eta": 2.0, "leaf": 32, "tier": "mixed_fp32", "nearfield": "on the fly",
+        "config": {"workload": f"sphere_{n}_slp_m4_eta2_leaf32_nrhs{nrhs}", "n": n, "nrhs": nrhs, "m": 4,
+                   "eta": 2.0, "leaf": 32, "tier": args.tier, "nearfield": "on the fly",
                    "l2": "inputs exceed L2 (geometry 151 MB, x/y 134 MB, cluster vectors >400 MB per step)",
                    "parallelism": f"replicas{world}"},
         "stage_ms": {nm: round(float(v), 3) for nm, v in zip(names, stage_m)},
@@ -413,6 +428,8 @@ def main():
         "e2e": {"value": world * n * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * nrhs * 8,
                 "d2h_bytes_per_step": n * nrhs * 8},
         "gpu_launches": int(st_m["launches"]) * args.steps,
+        "launch_variant": {"near_persistent": st_m["launch_variant"][0], "coupling_slices": st_m["launch_variant"][1],
+                           "coupling_persistent": st_m["launch_variant"][2], "autotuned": st_m["launch_variant"][3]},
         "clocks": clocks,
     }
     out.update(extra)

@@ -133,11 +133,35 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[a][r] = 0;
-    for (int b = ptr[bi]; b < ptr[bi + 1]; ++b) {
+    // register prefetch of the next block's x-hat values and column nodes, so
+    // that their global-memory latency overlaps the current block's work
+    constexpr int NT = M2 * NSL, PF = (K * NR + NT - 1) / NT;
+    static_assert(3 * M <= NT, "one column node per thread");
+    TX xpre[PF];
+    double zpre = 0.0;
+    auto prefetch = [&](int b) {
         const int s = col[b];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int e = threadIdx.x + j * NT;
+            xpre[j] = e < K * NR ? xh[(int64_t)s * K * NR + e] : (TX)0;
+        }
+        if (threadIdx.x < 3 * M) {
+            const int d = threadIdx.x / M, a = threadIdx.x % M;
+            zpre = t.box[d * t.nc + s] + t.box[(3 + d) * t.nc + s] * c.cheb[a];
+        }
+    };
+    const int bbeg = ptr[bi], bend = ptr[bi + 1];
+    if (bbeg < bend) prefetch(bbeg);
+    for (int b = bbeg; b < bend; ++b) {
         __syncthreads();
-        cluster_nodes(t, c, s, zs);
-        for (int e = threadIdx.x; e < K * NR; e += blockDim.x) xs[e] = (TA)xh[(int64_t)s * K * NR + e];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int e = threadIdx.x + j * NT;
+            if (e < K * NR) xs[e] = (TA)xpre[j];
+        }
+        if (threadIdx.x < 3 * M) zs[threadIdx.x] = zpre;
+        if (b + 1 < bend) prefetch(b + 1);
         __syncthreads();
         for (int e = threadIdx.x; e < 3 * M2; e += blockDim.x) {
             const int d = e / M2, a = (e / M) % M, a2 = e % M;

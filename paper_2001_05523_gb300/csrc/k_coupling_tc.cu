@@ -214,6 +214,25 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
     const int ia = nu % M, ib = (nu / M) % M, ic = nu / (M * M);
     bool ok = true;
     int issued = 0;  // commits issued (by thread 0)
+    // register prefetch of the next block's x-hat values and box (centre, half-width)
+    constexpr int PF = (S::K * NR + kThreads - 1) / kThreads;
+    float xpre[PF];
+    double bcen = 0.0, bhalf = 0.0;
+    static_assert(3 * M * M <= kThreads, "one D2 entry per thread");
+    auto prefetch = [&](int b) {
+        const int s = col[b0 + b];
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int e = tid + j * kThreads;
+            xpre[j] = e < S::K * NR ? xh[(int64_t)s * S::K * NR + e] : 0.0f;
+        }
+        if (tid < 3 * M * M) {
+            const int d = tid / (M * M);
+            bcen = t.box[d * t.nc + s];
+            bhalf = t.box[(3 + d) * t.nc + s];
+        }
+    };
+    if (nb > 0) prefetch(0);
     for (int b = 0; b < nb; ++b) {
         const int st = b & 1;
         unsigned char* stage = base + st * S::STAGE;
@@ -222,17 +241,18 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
             ok = __syncthreads_and(w) != 0;
             if (!ok) break;
         }
-        const int s = col[b0 + b];
-        for (int e = tid; e < 3 * M * M; e += kThreads) {
-            const int d = e / (M * M), a = (e / M) % M, a2 = e % M;
-            const double zs = t.box[d * t.nc + s] + t.box[(3 + d) * t.nc + s] * c.cheb[a2];
-            const double df = zt[d * M + a] - zs;
-            D2[e] = (float)(df * df);
+        if (tid < 3 * M * M) {
+            const int d = tid / (M * M), a = (tid / M) % M, a2 = tid % M;
+            const double df = zt[d * M + a] - (bcen + bhalf * c.cheb[a2]);
+            D2[tid] = (float)(df * df);
         }
         // x-hat_s staged transposed: row r, column mu
-        for (int e = tid; e < S::K * NR; e += kThreads) {
+#pragma unroll
+        for (int j = 0; j < PF; ++j) {
+            const int e = tid + j * kThreads;
+            if (e >= S::K * NR) break;
             const int mu = e / NR, r = e % NR;
-            const float v = xh[((int64_t)s * S::K + mu) * NR + r];
+            const float v = xpre[j];
             unsigned char* bt = stage + S::ATILE;
             const int off = sw_off<S::EB>(r, mu, (S::N / 8) * 1024);
             if (KIND == 2) {
@@ -246,6 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
                     *reinterpret_cast<uint32_t*>(bt + S::ATILE + S::BTILE + off) = to_tf32(v - __uint_as_float(hb));
             }
         }
+        if (b + 1 < nb) prefetch(b + 1);  // in flight while block b is generated
         __syncthreads();
         if (gen) {
             float X[M], Y[M], Z[M];
