@@ -247,11 +247,11 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    def timed_tier(precision: str, cache: bool, steps: int):
+    def timed_tier(precision: str, cache: bool, steps: int, **kw):
         t0 = time.perf_counter()
         # autotune: the first warm-up apply times the launch variants and keeps the fastest
         op = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, eta=2.0, leaf_size=32,
-                        precision=precision, cache_singular=cache, autotune=1)
+                        precision=precision, cache_singular=cache, autotune=1, **kw)
         setup_s = time.perf_counter() - t0
         y = torch.empty_like(x)
         for _ in range(args.warmup):
@@ -321,6 +321,15 @@ def main():
                            "stage_ms": [round(v, 3) for v in stage_t],
                            "rel_err_vs_fp64": float(torch.linalg.norm(y_t - y_d) / torch.linalg.norm(y_d))}
         extra["tensor_core_tiers"] = tiers
+        # mixed tier variants: FP64 Sauter-Schwab points; leaf bases re-evaluated in every apply
+        variants = {}
+        for name, kw in (("singular_fp64", {"singular_fp64": True}), ("recompute_basis", {"recompute_basis": True})):
+            opv, y_v, ms_v, stage_v, _, _ = timed_tier("mixed_fp32", False, max(1, min(args.steps, 3)), **kw)
+            opv.close()
+            variants[name] = {"value": world * n * nrhs / (ms_v / 1e3), "ms_per_step": ms_v,
+                              "stage_ms": [round(v, 3) for v in stage_v],
+                              "rel_err_vs_fp64": float(torch.linalg.norm(y_v - y_d) / torch.linalg.norm(y_d))}
+        extra["mixed_fp32_variants"] = variants
 
     # other workloads of the benchmark family (reported beside the headline)
     if not args.no_fp64:

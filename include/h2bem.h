@@ -88,7 +88,13 @@ typedef struct {
                         /*    CTA per row, 4 slices).  2 + v (v = 0..11) fixes a variant:         */
                         /*    v = nearfield persistent + 2 coupling persistent + 4 i, where i =   */
                         /*    0, 1, 2 selects 2, 4, 8 slices                                       */
-    int reserved[3];    /* must be zero                                                            */
+    int singular_fp64;  /* 1: Sauter-Schwab quadrature points of edge- and vertex-adjacent pairs   */
+                        /*    in FP64 in every tier; 0 (default): FP32 points in the MIXED tiers  */
+                        /*    (Gram set-up, partial sums and accumulation stay FP64)              */
+    int recompute_basis; /* 1: no stored leaf bases; every apply re-evaluates the cluster-basis   */
+                        /*    values by quadrature (saves n k values of device memory); 0         */
+                        /*    (default): V (and W) evaluated once at set-up and stored             */
+    int reserved[1];    /* must be zero                                                            */
 } h2bem_opts;
 
 /* Statistics of an operator (counts are exact, from its own block lists). */

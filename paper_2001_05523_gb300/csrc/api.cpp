@@ -602,6 +602,7 @@ struct h2bem_op {
     int64_t launches = 0;
     // launch variants (autotune): per right-hand-side width slot and direction
     int autotune = 0;
+    int singular_fp64 = 0, recompute_basis = 0;
     struct Tuned {
         bool done = false;
         h2::LaunchCfg near, coup;  // work pointers filled in at launch
@@ -760,6 +761,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if (opts.autotune < 0 || opts.autotune > 13)
         return fail(H2BEM_ERR_ARG, "operator_create: autotune must be 0, 1 or 2..13, got %d", opts.autotune);
     op->autotune = opts.autotune == 1 ? 1 : 0;
+    op->singular_fp64 = opts.singular_fp64 ? 1 : 0;
+    op->recompute_basis = opts.recompute_basis ? 1 : 0;
     if (opts.autotune >= 2) {  // a fixed launch variant for every width and direction
         const int v = opts.autotune - 2;
         for (auto& slot : op->tuned)
@@ -996,7 +999,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     CU(cudaGetLastError());
     // leaf bases: V_t[i, nu] = int L_nu; for the double layer also W_s[j, nu] = int n_j . grad L_nu
     for (int l : op->leaves_h) op->max_leaf = std::max(op->max_leaf, (int)(tree->end[l] - tree->begin[l]));
-    {
+    if (!op->recompute_basis) {
         const bool v32 = op->precision != H2BEM_FP64;
         if ((rc = op->basisV.alloc((size_t)n * op->k * (v32 ? sizeof(float) : sizeof(double))))) return rc;
         h2::launch_leaf_basis(op->geom(), op->tree(), op->consts, op->basis_rule.as<double>(), (int)op->nleaves,
@@ -1023,7 +1026,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             }
             h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, np, op->sp_lo[t].as<int>(), op->sp_hi[t].as<int>(),
                                 op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(), op->sp_npts[t], 1,
-                                op->precision != H2BEM_FP64, false, 1,
+                                op->precision != H2BEM_FP64 && !op->singular_fp64, false, 1,
                                 nullptr, nullptr, op->sp_v0[t].as<double>(), op->sp_v1[t].as<double>(), 0);
             CU(cudaGetLastError());
         }
@@ -1271,9 +1274,13 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
         // the double layer's differentiated basis is evaluated in FP64 in every tier
-        h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
-                                       fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
-                                       op->xp.as<double>(), op->xh.p, s);
+        if (op->recompute_basis)
+            h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
+                                    in_dlp, fp32 && !in_dlp, xh64, NR, op->xp.as<double>(), op->xh.p, s);
+        else
+            h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                           fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
+                                           op->xp.as<double>(), op->xh.p, s);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
@@ -1305,9 +1312,13 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
         mark(5);
-        h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
-                                        fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p, op->yh.p,
-                                        op->yp.as<double>(), s);
+        if (op->recompute_basis)
+            h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
+                                     out_dlp, fp32 && !out_dlp, yh64, NR, op->yh.p, op->yp.as<double>(), s);
+        else
+            h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                            fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p,
+                                            op->yh.p, op->yp.as<double>(), s);
     } else {
         for (int i = 2; i <= 5; ++i) mark(i);
     }
@@ -1331,7 +1342,8 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                                 op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
         else
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                                op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, fp32, transpose,
+                                op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0,
+                                fp32 && !op->singular_fp64, transpose,
                                 NR, op->xp.as<double>(), op->yp.as<double>(), nullptr, nullptr, s);
     }
     mark(8);
@@ -1602,8 +1614,12 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
     CU(cudaMemsetAsync(yp, 0, vb, s));
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(yh, 0, hb, s));
-        launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32 && !dlp,
-                                   xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
+        if (op->recompute_basis)
+            launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), dlp,
+                                fp32 && !dlp, xh64, NR, xp, xh, s);
+        else
+            launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                       fp32 && !dlp, xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
         h2::LaunchCfg cfg_near, cfg_coup;
@@ -1611,8 +1627,12 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         run_coupling(op, t, c, op->far, xh64, yh64, NR, xh, yh, cfg_coup, s);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
-        launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32, yh64,
-                                    NR, op->basisV.p, yh, yp, s);
+        if (op->recompute_basis)
+            launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
+                                 fp32, yh64, NR, yh, yp, s);
+        else
+            launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
+                                        yh64, NR, op->basisV.p, yh, yp, s);
     }
     {
         h2::LaunchCfg cfg_near, cfg_coup;
@@ -1628,7 +1648,8 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
                             nullptr, 0, 2, false, false, NR, xp, yp, op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
         else
             launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0, fp32, false, NR, xp,
+                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0,
+                            fp32 && !op->singular_fp64, false, NR, xp,
                             yp, nullptr, nullptr, s);
     }
     launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);

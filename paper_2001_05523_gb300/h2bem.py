@@ -39,7 +39,8 @@ class H2bemError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -267,7 +268,8 @@ class BatchOperator:
 
     def __init__(self, meshes, kernel: str | int = "slp", m: int = 4, eta: float = 2.0, leaf_size: int = 32,
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
-                 use_graph: bool = False, autotune: int = 0):
+                 use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
+                 recompute_basis: bool = False):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -279,6 +281,8 @@ class BatchOperator:
         o.cache_singular = int(cache_singular)
         o.use_graph = int(use_graph)
         o.autotune = int(autotune)
+        o.singular_fp64 = int(singular_fp64)
+        o.recompute_basis = int(recompute_basis)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
     def close(self):
@@ -311,7 +315,8 @@ class Operator:
 
     def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
-                 use_graph: bool = False, autotune: int = 0):
+                 use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
+                 recompute_basis: bool = False):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -322,6 +327,8 @@ class Operator:
         o.cache_singular = int(cache_singular)
         o.use_graph = int(use_graph)
         o.autotune = int(autotune)
+        o.singular_fp64 = int(singular_fp64)
+        o.recompute_basis = int(recompute_basis)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):

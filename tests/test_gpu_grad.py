@@ -91,3 +91,57 @@ def test_autograd_shape_and_batch(H, orc):
         assert np.linalg.norm(gx[:, lo:hi] - refx) / np.linalg.norm(refx) < 1e-10
         voff += mesh.nv
     B.close()
+
+
+def test_shape_gradient_matches_gpu_central_differences(H):
+    """32 sampled vertex coordinates: the gradient of sum_r <w_r, G(X) x_r>
+    against central differences (step 1e-6) of the GPU FP64 apply with the
+    cluster tree held fixed (uploaded unchanged; boxes and blocks follow the
+    moved vertices, and a coordinate whose move changes the block counts is
+    skipped).  Relative to the largest gradient entry: 1e-5."""
+    import torch
+
+    mesh = I.jitter(I.sphere(6), 0.03, 41)
+    m, leaf, h = 3, 8, 1e-6
+    base = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=m, leaf_size=leaf)
+    tr = H.h2bem_tree_export(base.tree, mesh.nt)
+    counts = (base.stats()["nfar"], base.stats()["nnear"])
+    w = I.rhs(mesh.nt, 2, seed=51)
+    x = I.rhs(mesh.nt, 2, seed=52)
+    wd, xd = torch.from_numpy(w).cuda(), torch.from_numpy(x).cuda()
+    g = torch.zeros((mesh.nv, 3), dtype=torch.float64, device="cuda")
+    H.h2bem_grad(base.op, wd, xd, g)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    base.close()
+
+    def f(X):
+        ms = H.h2bem_mesh_create(X, mesh.triangles)
+        ts = H.h2bem_tree_upload(ms, tr["perm"], tr["begin"], tr["end"], tr["child0"], tr["child1"])
+        o = H.h2bem_opts_default()
+        op = H.h2bem_operator_create(ms, ts, 0, m, 2.0, o)
+        st = H.h2bem_stats_get(op)
+        y = torch.empty_like(xd)
+        H.h2bem_apply(op, xd, y)
+        torch.cuda.synchronize()
+        val = float((wd * y).sum())
+        for hd, fn in ((op, H.h2bem_operator_destroy), (ts, H.h2bem_tree_destroy), (ms, H.h2bem_mesh_destroy)):
+            fn(hd)
+        return val, (st["nfar"], st["nnear"])
+
+    rng = np.random.default_rng(7)
+    picks = [(int(v), int(d)) for v, d in zip(rng.choice(mesh.nv, 32, replace=False), rng.integers(0, 3, 32))]
+    scale = np.abs(g).max()
+    checked = 0
+    for v, d in picks:
+        Xp, Xm = mesh.vertices.copy(), mesh.vertices.copy()
+        Xp[v, d] += h
+        Xm[v, d] -= h
+        fp, cp = f(Xp)
+        fm, cm = f(Xm)
+        if cp != counts or cm != counts:
+            continue
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g[v, d]) <= 1e-5 * scale, (v, d, fd, g[v, d])
+        checked += 1
+    assert checked >= 24

@@ -223,3 +223,36 @@ def test_regular_evals_count(H, orc):
     op = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=4)
     assert op.stats()["regular_evals"] == want
     op.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+@pytest.mark.parametrize("kernel,transpose", [(0, False), (1, False), (1, True)])
+def test_recomputed_bases_equal_stored(H, orc, precision, kernel, transpose):
+    """recompute_basis: the leaf bases are re-evaluated in every apply instead of stored."""
+    import torch
+
+    mesh = I.jitter(I.ellipsoid(12), 0.01, 8)
+    x = I.rhs(mesh.nt, 3, seed=14)
+    ys = []
+    for rb in (False, True):
+        op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, precision=precision, recompute_basis=rb)
+        xd = torch.from_numpy(x).cuda()
+        ys.append(op.apply(xd, transpose=transpose).cpu().numpy())
+        op.close()
+    ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)
+    assert rel(ys[1], ref) < TOL[precision]
+    assert rel(ys[0], ys[1]) < (1e-13 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_mixed_with_fp64_singular_points(H, orc, kernel):
+    """singular_fp64: the mixed tier with FP64 Sauter-Schwab points."""
+    mesh = I.jitter(I.sphere(14), 0.01, 4)
+    x = I.rhs(mesh.nt, 2, seed=6)
+    import torch
+
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, precision="mixed_fp32", singular_fp64=True)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    op.close()
+    ref = orc.H2(mesh, kernel, m=4).matvec(x)
+    assert rel(y, ref) < TOL["mixed_fp32"]
