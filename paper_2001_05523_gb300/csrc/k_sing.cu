@@ -1,9 +1,14 @@
 // Nearfield blocks, singular pairs (triangles sharing a vertex): Sauter-Schwab
-// quadrature (cited in sections 1 and 5).  FP64 tier: FP64 throughout.  Mixed
-// tier (F32): the Gram entries of the edge vectors are formed in FP64 and
-// rounded once; the quadrature points of edge and vertex pairs are evaluated
-// in FP32 (hardware reciprocal square root, relative error below 2^-22) and
-// summed in FP32 over at most q^2 points, the partial sums in FP64.
+// quadrature (cited in sections 1 and 5).  k_singular: FP64 throughout (FP64
+// tier, or on request in every tier).  k_singular32 (mixed tiers): every pair
+// in FP32 - edge vectors as differences of the triangles' FP32 edge vectors
+// (quantities of size h, no cancellation), Gram entries, quadrature points
+// (hardware reciprocal square root, relative error below 2^-22) and sums; the
+// area scale and the accumulation into y are FP64.  The double-layer
+// projections use the difference of the split normals delta = n_hi - n_lo:
+// an edge of one panel is orthogonal to its own normal (and the shared edge
+// of an edge pair to both), so e . n_other = e . (+-delta), of size h^2 kappa
+// and computed without cancellation.
 //
 // Each canonical pair {lo, hi} (outer panel P = triangle of lower user index,
 // shared vertices first and in the same order in P and Q) is evaluated once.
@@ -54,7 +59,7 @@ __device__ __forceinline__ float rsqrt_f32(float a) {
     return y;
 }
 
-template <int NR, int TYPE, int KER, int MODE, bool F32>
+template <int NR, int TYPE, int KER, int MODE>
 __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const int* __restrict__ plo,
                                                        const int* __restrict__ phi, const int* __restrict__ pcode,
                                                        const double* __restrict__ tab, int npts, bool transpose,
@@ -62,18 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                                                        double* __restrict__ val0, double* __restrict__ val1) {
     constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;  // doubles per table point
     extern __shared__ double stab[];
-    float* stf = reinterpret_cast<float*>(stab);  // F32: (x_k, w_k x_k, w_k, 0) per point
     if (MODE != 2) {
-        if (F32 && TYPE != IDENTICAL) {
-            for (int p = threadIdx.x; p < npts; p += blockDim.x) {
-                stf[4 * p] = (float)tab[p * W];
-                stf[4 * p + 1] = (float)(2.0 * tab[p * W + W - 1]);
-                stf[4 * p + 2] = (float)tab[p * W + 1];
-                stf[4 * p + 3] = 0.0f;
-            }
-        } else {
-            for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
-        }
+        for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
         __syncthreads();
     }
     const int pid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,72 +105,6 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
                 s += T[3] * rsqrt_nr(r2);
             }
             a01 = a10 = sc * s;
-        } else if (TYPE == EDGE && F32) {
-            // as the FP64 branch below, with (x_k, w_k x_k, w_k) from stf
-            const float Gm[3][3] = {{(float)dot(ea, ea), (float)dot(ea, eb), (float)dot(ea, ed)},
-                                    {(float)dot(ea, eb), (float)dot(eb, eb), (float)dot(eb, ed)},
-                                    {(float)dot(ea, ed), (float)dot(eb, ed), (float)dot(ed, ed)}};
-            const int q = npts;
-            double s = 0.0, sa = 0.0, sb = 0.0, sd = 0.0;
-            for (int reg = 0; reg < 5; ++reg) {
-                float rs = 0.0f, ra = 0.0f, rb = 0.0f, rd = 0.0f;
-                for (int oi = 0; oi < q; ++oi) {
-                    const float o = stf[4 * oi], wo = stf[4 * oi + 2];
-                    float F[3], Gv[3];
-                    switch (reg) {
-                        case 0: F[0] = o; F[1] = 0.0f; F[2] = o - 1.0f; Gv[0] = 0.0f; Gv[1] = 1.0f; Gv[2] = 0.0f; break;
-                        case 1: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = o; Gv[1] = 0.0f; Gv[2] = o - 1.0f; break;
-                        case 2: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -1.0f; Gv[1] = -1.0f; Gv[2] = -o; break;
-                        case 3: F[0] = 0.0f; F[1] = 0.0f; F[2] = -1.0f; Gv[0] = -o; Gv[1] = 1.0f - o; Gv[2] = 0.0f; break;
-                        default: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -o; Gv[1] = -o; Gv[2] = -1.0f; break;
-                    }
-                    float A = 0.0f, B2 = 0.0f, Cc = 0.0f;
-                    for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v) {
-                            A += F[u] * Gm[u][v] * F[v];
-                            B2 += F[u] * Gm[u][v] * Gv[v];
-                            Cc += Gv[u] * Gm[u][v] * Gv[v];
-                        }
-                    B2 *= 2.0f;
-                    float f0 = 0.0f, f1 = 0.0f;
-                    for (int k = 0; k < q; ++k) {
-                        const float tt = stf[4 * k];
-                        const float wt = reg == 0 ? stf[4 * k + 2] : stf[4 * k + 1];  // w_t (R1) or w_t t
-                        const float y = rsqrt_f32(fmaf(tt, fmaf(tt, Cc, B2), A));
-                        if (KER == SLP) {
-                            f0 = fmaf(wt, y, f0);
-                        } else {
-                            const float f = wt * (y * y * y);
-                            f0 += f;
-                            f1 = fmaf(f, tt, f1);
-                        }
-                    }
-                    if (KER == SLP) {
-                        rs = fmaf(wo, f0, rs);
-                    } else {
-                        ra = fmaf(wo, f0 * F[0] + f1 * Gv[0], ra);
-                        rb = fmaf(wo, f0 * F[1] + f1 * Gv[1], rb);
-                        rd = fmaf(wo, f0 * F[2] + f1 * Gv[2], rd);
-                    }
-                }
-                s += rs;
-                sa += ra;
-                sb += rb;
-                sd += rd;
-            }
-            if (KER == SLP) {
-                a01 = a10 = sc * s / 6.0;
-            } else {
-                double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
-                double nlo[3], nhi[3];
-                for (int d = 0; d < 3; ++d) {
-                    nlo[d] = g.nrm[d * g.n + lo];
-                    nhi[d] = g.nrm[d * g.n + hi];
-                }
-                a01 = sc * dot(V, nhi);
-                a10 = -sc * dot(V, nlo);
-            }
         } else if (TYPE == EDGE) {
             // vectors (a, b, d); stab holds (x_k, w_k, w_k / 2, w_k x_k / 2), npts = q.
             // Region r: w = F(o) + t G(o) with the outer variable o and the inner t;
@@ -243,74 +172,6 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
             } else {
                 double V[3];
                 for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
-                double nlo[3], nhi[3];
-                for (int d = 0; d < 3; ++d) {
-                    nlo[d] = g.nrm[d * g.n + lo];
-                    nhi[d] = g.nrm[d * g.n + hi];
-                }
-                a01 = sc * dot(V, nhi);
-                a10 = -sc * dot(V, nlo);
-            }
-        } else if (F32) {  // VERTEX as the FP64 branch below, with (x_k, w_k x_k, w_k) from stf
-            const float aa = (float)dot(ea, ea), bb = (float)dot(eb, eb), cc = (float)dot(ec, ec),
-                        dd = (float)dot(ed, ed);
-            const float ab = (float)dot(ea, eb), ac = (float)dot(ea, ec), ad = (float)dot(ea, ed),
-                        bc = (float)dot(eb, ec), bd = (float)dot(eb, ed), cd = (float)dot(ec, ed);
-            const int q = npts;
-            double s = 0.0, sa = 0.0, sb = 0.0, sc2 = 0.0, sd = 0.0;
-            for (int reg = 0; reg < 2; ++reg) {
-                const float uu = reg == 0 ? aa : cc, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : dd;
-                const float pp = reg == 0 ? cc : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? dd : bb;
-                const float b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
-                for (int i = 0; i < q; ++i) {
-                    const float e1 = stf[4 * i], w1 = stf[4 * i + 2];
-                    const float A = fmaf(e1, fmaf(e1, vv2, 2.0f * uv2), uu);
-                    const float Bi0 = fmaf(e1, b2, b0), Bi1 = fmaf(e1, bd, b1);
-                    // over l: t0 = sum w3 f0, t1 = sum w3 f1, t2 = sum w3 e3 f1
-                    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
-                    for (int l = 0; l < q; ++l) {
-                        const float e3 = stf[4 * l], w3 = stf[4 * l + 2];
-                        const float Cc = fmaf(e3, fmaf(e3, qq2, 2.0f * pq2), pp);
-                        const float m2B = -2.0f * fmaf(e3, Bi1, Bi0);
-                        float f0 = 0.0f, f1 = 0.0f;
-                        for (int k = 0; k < q; ++k) {
-                            const float2 T = *reinterpret_cast<const float2*>(stf + 4 * k);  // (e2, w e2)
-                            const float y = rsqrt_f32(fmaf(T.x, fmaf(T.x, Cc, m2B), A));
-                            if (KER == SLP) {
-                                f0 = fmaf(T.y, y, f0);
-                            } else {
-                                const float f = T.y * (y * y * y);
-                                f0 += f;
-                                f1 = fmaf(f, T.x, f1);
-                            }
-                        }
-                        t0 = fmaf(w3, f0, t0);
-                        if (KER != SLP) {
-                            t1 = fmaf(w3, f1, t1);
-                            t2 = fmaf(w3 * e3, f1, t2);
-                        }
-                    }
-                    const double W1 = w1, T0 = (double)w1 * t0;
-                    if (KER == SLP) {
-                        s += T0;
-                    } else if (reg == 0) {  // w = a + e1 b - e2 c - e2 e3 d
-                        sa += T0;
-                        sb = fma((double)e1, T0, sb);
-                        sc2 -= W1 * t1;
-                        sd -= W1 * t2;
-                    } else {                // w = e2 a + e2 e3 b - c - e1 d
-                        sa += W1 * t1;
-                        sb += W1 * t2;
-                        sc2 -= T0;
-                        sd = fma(-(double)e1, T0, sd);
-                    }
-                }
-            }
-            if (KER == SLP) {
-                a01 = a10 = sc * s / 3.0;
-            } else {
-                double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sc2 * ec[d] + sd * ed[d]);
                 double nlo[3], nhi[3];
                 for (int d = 0; d < 3; ++d) {
                     nlo[d] = g.nrm[d * g.n + lo];
@@ -413,6 +274,214 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
     }
 }
 
+// FP32 evaluation (mixed tiers).  Table per point: identical (T0, T1, T2, T3)
+// as the FP64 table; edge and vertex (x_k, w_k x_k, w_k, 0).
+template <int NR, int TYPE, int KER, int MODE>
+__global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, const int* __restrict__ plo,
+                                                         const int* __restrict__ phi, const int* __restrict__ pcode,
+                                                         const double* __restrict__ tab, int npts, bool transpose,
+                                                         const double* __restrict__ xp, double* __restrict__ yp,
+                                                         double* __restrict__ val0, double* __restrict__ val1) {
+    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;  // doubles per point of the FP64 table
+    extern __shared__ double stab[];
+    float* stf = reinterpret_cast<float*>(stab);
+    for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+        if (TYPE == IDENTICAL) {
+            for (int j = 0; j < 4; ++j) stf[4 * p + j] = (float)tab[p * 4 + j];
+        } else {
+            stf[4 * p] = (float)tab[p * W];
+            stf[4 * p + 1] = (float)(2.0 * tab[p * W + W - 1]);
+            stf[4 * p + 2] = (float)tab[p * W + 1];
+            stf[4 * p + 3] = 0.0f;
+        }
+    }
+    __syncthreads();
+    const int pid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pid >= npairs) return;
+    const int lo = plo[pid], hi = phi[pid], n = g.n;
+    const int code = pcode[pid];
+    const int rP = code & 3, q0 = (code >> 2) & 3, q1 = (code >> 4) & 3, q2 = (code >> 6) & 3;
+    // corner k minus corner 0 of each panel, from the FP32 edge vectors (corner 0: zero)
+    float EL[3][3], EH[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        EL[0][d] = 0.0f;
+        EL[1][d] = g.nef[(6 + d) * n + lo];
+        EL[2][d] = g.nef[(9 + d) * n + lo];
+        EH[0][d] = 0.0f;
+        EH[1][d] = g.nef[(6 + d) * n + hi];
+        EH[2][d] = g.nef[(9 + d) * n + hi];
+    }
+    const int p0 = rP, p1 = (rP + 1) % 3, p2 = (rP + 2) % 3;
+    float a[3], b[3], cc[3], dd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a[d] = EL[p1][d] - EL[p0][d];
+        b[d] = EL[p2][d] - EL[p1][d];
+        cc[d] = EH[q1][d] - EH[q0][d];
+        dd[d] = EH[q2][d] - EH[q1][d];
+    }
+    auto dot3 = [](const float* u, const float* v) { return fmaf(u[2], v[2], fmaf(u[1], v[1], u[0] * v[0])); };
+    // delta = n_hi - n_lo from the split normals (double layer)
+    float del[3] = {0, 0, 0};
+    if (KER != SLP) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            del[d] = (g.nef[d * n + hi] - g.nef[d * n + lo]) + (g.nef[(3 + d) * n + hi] - g.nef[(3 + d) * n + lo]);
+    }
+    const double sc = 4.0 * g.area[lo] * g.area[hi] * kInv4Pi;
+    double a01, a10;
+    if (TYPE == IDENTICAL) {
+        const float aa = dot3(a, a), ab = dot3(a, b), bb = dot3(b, b);
+        float sum = 0.0f;
+        for (int p = 0; p < npts; ++p) {
+            const float* T = stf + 4 * p;
+            sum = fmaf(T[3], rsqrt_f32(fmaf(T[2], bb, fmaf(T[1], ab, T[0] * aa))), sum);
+        }
+        a01 = a10 = sc * (double)sum;
+    } else if (TYPE == EDGE) {
+        // vectors (a, b, d); regions and coefficient triples as in k_singular
+        const float Gm[3][3] = {{dot3(a, a), dot3(a, b), dot3(a, dd)},
+                                {dot3(a, b), dot3(b, b), dot3(b, dd)},
+                                {dot3(a, dd), dot3(b, dd), dot3(dd, dd)}};
+        const int q = npts;
+        float ssum = 0.0f, sb = 0.0f, sd = 0.0f;
+        for (int reg = 0; reg < 5; ++reg) {
+            float rs = 0.0f, rb = 0.0f, rd = 0.0f;
+            for (int oi = 0; oi < q; ++oi) {
+                const float o = stf[4 * oi], wo = stf[4 * oi + 2];
+                float F[3], Gv[3];
+                switch (reg) {
+                    case 0: F[0] = o; F[1] = 0.0f; F[2] = o - 1.0f; Gv[0] = 0.0f; Gv[1] = 1.0f; Gv[2] = 0.0f; break;
+                    case 1: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = o; Gv[1] = 0.0f; Gv[2] = o - 1.0f; break;
+                    case 2: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -1.0f; Gv[1] = -1.0f; Gv[2] = -o; break;
+                    case 3: F[0] = 0.0f; F[1] = 0.0f; F[2] = -1.0f; Gv[0] = -o; Gv[1] = 1.0f - o; Gv[2] = 0.0f; break;
+                    default: F[0] = 0.0f; F[1] = 1.0f; F[2] = 0.0f; Gv[0] = -o; Gv[1] = -o; Gv[2] = -1.0f; break;
+                }
+                float A = 0.0f, B2 = 0.0f, Cc = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        A += F[u] * Gm[u][v] * F[v];
+                        B2 += F[u] * Gm[u][v] * Gv[v];
+                        Cc += Gv[u] * Gm[u][v] * Gv[v];
+                    }
+                B2 *= 2.0f;
+                float f0 = 0.0f, f1 = 0.0f;
+                for (int k = 0; k < q; ++k) {
+                    const float tt = stf[4 * k];
+                    const float wt = reg == 0 ? stf[4 * k + 2] : stf[4 * k + 1];  // w_t (R1) or w_t t
+                    const float y = rsqrt_f32(fmaf(tt, fmaf(tt, Cc, B2), A));
+                    if (KER == SLP) {
+                        f0 = fmaf(wt, y, f0);
+                    } else {
+                        const float f = wt * (y * y * y);
+                        f0 += f;
+                        f1 = fmaf(f, tt, f1);
+                    }
+                }
+                if (KER == SLP) {
+                    rs = fmaf(wo, f0, rs);
+                } else {
+                    rb = fmaf(wo, f0 * F[1] + f1 * Gv[1], rb);
+                    rd = fmaf(wo, f0 * F[2] + f1 * Gv[2], rd);
+                }
+            }
+            ssum += rs;
+            sb += rb;
+            sd += rd;
+        }
+        if (KER == SLP) {
+            a01 = a10 = sc * (double)ssum / 6.0;
+        } else {
+            // V = (sa a + sb b + sd d) / 2; a is in both planes, b in lo's, d in hi's
+            a01 = 0.5 * sc * (double)(sb * dot3(b, del));
+            a10 = 0.5 * sc * (double)(sd * dot3(dd, del));
+        }
+    } else {  // VERTEX: vectors (a, b, c, d)
+        const float aa = dot3(a, a), bb = dot3(b, b), c2 = dot3(cc, cc), d2 = dot3(dd, dd);
+        const float ab = dot3(a, b), ac = dot3(a, cc), ad = dot3(a, dd), bc = dot3(b, cc), bd = dot3(b, dd),
+                    cd = dot3(cc, dd);
+        const int q = npts;
+        float ssum = 0.0f, sa = 0.0f, sb = 0.0f, sc2 = 0.0f, sd = 0.0f;
+        for (int reg = 0; reg < 2; ++reg) {
+            const float uu = reg == 0 ? aa : c2, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : d2;
+            const float pp = reg == 0 ? c2 : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? d2 : bb;
+            const float b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
+            for (int i = 0; i < q; ++i) {
+                const float e1 = stf[4 * i], w1 = stf[4 * i + 2];
+                const float A = fmaf(e1, fmaf(e1, vv2, 2.0f * uv2), uu);
+                const float Bi0 = fmaf(e1, b2, b0), Bi1 = fmaf(e1, bd, b1);
+                float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+                for (int l = 0; l < q; ++l) {
+                    const float e3 = stf[4 * l], w3 = stf[4 * l + 2];
+                    const float Cq = fmaf(e3, fmaf(e3, qq2, 2.0f * pq2), pp);
+                    const float m2B = -2.0f * fmaf(e3, Bi1, Bi0);
+                    float f0 = 0.0f, f1 = 0.0f;
+                    for (int k = 0; k < q; ++k) {
+                        const float2 T = *reinterpret_cast<const float2*>(stf + 4 * k);  // (e2, w e2)
+                        const float y = rsqrt_f32(fmaf(T.x, fmaf(T.x, Cq, m2B), A));
+                        if (KER == SLP) {
+                            f0 = fmaf(T.y, y, f0);
+                        } else {
+                            const float f = T.y * (y * y * y);
+                            f0 += f;
+                            f1 = fmaf(f, T.x, f1);
+                        }
+                    }
+                    t0 = fmaf(w3, f0, t0);
+                    if (KER != SLP) {
+                        t1 = fmaf(w3, f1, t1);
+                        t2 = fmaf(w3 * e3, f1, t2);
+                    }
+                }
+                const float T0 = w1 * t0;
+                if (KER == SLP) {
+                    ssum += T0;
+                } else if (reg == 0) {  // w = a + e1 b - e2 c - e2 e3 d
+                    sa += T0;
+                    sb = fmaf(e1, T0, sb);
+                    sc2 = fmaf(-w1, t1, sc2);
+                    sd = fmaf(-w1, t2, sd);
+                } else {                // w = e2 a + e2 e3 b - c - e1 d
+                    sa = fmaf(w1, t1, sa);
+                    sb = fmaf(w1, t2, sb);
+                    sc2 -= T0;
+                    sd = fmaf(-e1, T0, sd);
+                }
+            }
+        }
+        if (KER == SLP) {
+            a01 = a10 = sc * (double)ssum / 3.0;
+        } else {
+            // V = (sa a + sb b + sc c + sd d) / 2; a, b in lo's plane, c, d in hi's
+            a01 = 0.5 * sc * (double)fmaf(sa, dot3(a, del), sb * dot3(b, del));
+            a10 = 0.5 * sc * (double)fmaf(sc2, dot3(cc, del), sd * dot3(dd, del));
+        }
+    }
+    if (MODE == 1) {
+        val0[pid] = a01;
+        val1[pid] = a10;
+        return;
+    }
+    if (transpose) {
+        const double tmp = a01;
+        a01 = a10;
+        a10 = tmp;
+    }
+    if (lo == hi) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) atomicAdd(&yp[(int64_t)lo * NR + r], a01 * xp[(int64_t)lo * NR + r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            atomicAdd(&yp[(int64_t)lo * NR + r], a01 * xp[(int64_t)hi * NR + r]);
+            atomicAdd(&yp[(int64_t)hi * NR + r], a10 * xp[(int64_t)lo * NR + r]);
+        }
+    }
+}
+
 template <int NR, int TYPE, int KER, bool F32>
 static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
                       const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
@@ -420,14 +489,22 @@ static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const
     constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;
     const size_t smem = mode == 2 ? 0 : (size_t)npts * W * sizeof(double);
     dim3 grid((npairs + kThreads - 1) / kThreads);
-    if (mode == 0) {
-        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 0, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_singular<NR, TYPE, KER, 0, F32><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    } else if (mode == 1) {
-        cudaFuncSetAttribute(k_singular<NR, TYPE, KER, 1, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_singular<NR, TYPE, KER, 1, F32><<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    if (mode == 2) {
+        k_singular<NR, TYPE, KER, 2><<<grid, kThreads, 0, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        return;
+    }
+    if constexpr (F32) {
+        auto k0 = k_singular32<NR, TYPE, KER, 0>;
+        auto k1 = k_singular32<NR, TYPE, KER, 1>;
+        auto kern = mode == 0 ? k0 : k1;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     } else {
-        k_singular<NR, TYPE, KER, 2, false><<<grid, kThreads, 0, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+        auto k0 = k_singular<NR, TYPE, KER, 0>;
+        auto k1 = k_singular<NR, TYPE, KER, 1>;
+        auto kern = mode == 0 ? k0 : k1;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     }
 }
 
@@ -435,8 +512,8 @@ template <int NR, int TYPE>
 static void sing_ker(int ker, bool f32, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo,
                      const int* hi, const int* code, const double* tab, int npts, bool tr, const double* xp,
                      double* yp, double* v0, double* v1) {
-    // identical pairs (3q points) stay in FP64 in both tiers; mode 2 only reads cached values
-    if (f32 && TYPE != IDENTICAL && mode != 2) {
+    // mode 2 only reads cached values
+    if (f32 && mode != 2) {
         if (ker == SLP) sing_mode<NR, TYPE, SLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
         else sing_mode<NR, TYPE, DLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     } else {
