@@ -576,7 +576,7 @@ struct h2bem_op {
     h2::Consts consts{};
     // device geometry and tree
     DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
-    DevBuf cbegin, cend, cchild0, cchild1, cbox, leaves, basis_rule;
+    DevBuf cbegin, cend, cchild0, cchild1, cbox, czhl, leaves, basis_rule;
     std::vector<int> leaves_h;
     int max_leaf = 0;               // largest leaf cluster
     DevBuf basisV, basisW;          // stored leaf bases [pos][nu]: V (FP32 in the mixed tier), W (double layer, FP64)
@@ -634,7 +634,7 @@ struct h2bem_op {
     }
     h2::Tree tree() const {
         return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
-                        cchild1.as<const int>(), cbox.as<const double>()};
+                        cchild1.as<const int>(), cbox.as<const double>(), czhl.as<const float2>()};
     }
     ~h2bem_op() {
         for (auto& e : ev)
@@ -851,6 +851,17 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             op->level_parents[tree->level[c]].push_back((int)c);
         }
     }
+    // interpolation nodes z = c + h cheb[a] of every cluster and axis as FP32 (hi, lo)
+    std::vector<float> zhl((size_t)nc * 3 * m * 2);
+    for (int64_t c = 0; c < nc; ++c)
+        for (int d = 0; d < 3; ++d)
+            for (int a = 0; a < m; ++a) {
+                const double z = box[d * nc + c] + box[(3 + d) * nc + c] * op->consts.cheb[a];
+                const float hi = (float)z;
+                const size_t e = (((size_t)c * 3 + d) * m + a) * 2;
+                zhl[e] = hi;
+                zhl[e + 1] = (float)(z - (double)hi);
+            }
     op->nleaves = (int64_t)op->leaves_h.size();
     std::vector<int> leaf_index(nc, -1);
     for (size_t l = 0; l < op->leaves_h.size(); ++l) leaf_index[op->leaves_h[l]] = (int)l;
@@ -900,7 +911,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if ((rc = upload(op->xyz, mesh->xyz)) || (rc = upload(op->tri, std::vector<int>(mesh->tri.begin(), mesh->tri.end()))) ||
         (rc = upload(op->perm, permv)) || (rc = upload(op->iperm, iperm)) || (rc = upload(op->cbegin, cb)) ||
         (rc = upload(op->cend, ce)) || (rc = upload(op->cchild0, c0)) || (rc = upload(op->cchild1, c1)) ||
-        (rc = upload(op->cbox, box)) || (rc = upload(op->leaves, op->leaves_h)))
+        (rc = upload(op->cbox, box)) || (rc = upload(op->czhl, zhl)) || (rc = upload(op->leaves, op->leaves_h)))
         return rc;
     if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
         (rc = op->near_u.upload_all()) || (rc = op->work.alloc(4 * sizeof(int))))

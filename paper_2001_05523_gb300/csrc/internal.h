@@ -41,6 +41,8 @@ struct Tree {
     const int* child0;   // [nc] -1 for leaves
     const int* child1;
     const double* box;   // [9][nc]: centre x,y,z, (floored) half-width x,y,z, 1/half-width x,y,z
+    const float2* zhl;   // [nc][3][m] interpolation node coordinates c_d + h_d cheb[a] as FP32 (hi, lo):
+                         // hi = fl(z), lo = fl(z - hi)
 };
 
 // Quadrature and interpolation constants passed by value.

@@ -3,6 +3,7 @@
 //   yh_t[nu] = sum_{(t,s) farfield} sum_mu S_ts[nu,mu] xh_s[mu],
 // with S_ts generated on the fly; SIMT kernels in FP64 or FP32.
 #include <algorithm>
+#include <type_traits>
 
 #include "dmath.cuh"
 #include "internal.h"
@@ -121,13 +122,21 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
     constexpr int K = M * M * M, M2 = M * M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* xs = reinterpret_cast<TA*>(smem_raw);  // [K][NR]; reused for the reduction [NSL][K][NR]
+    // node coordinates: FP64, or for FP32 entries (hi, lo) splits whose
+    // differences keep ~1e-7 relative accuracy without the FP64 pipe
+    constexpr bool F32N = std::is_same<TS, float>::value;
     __shared__ double zt[3 * M], zs[3 * M];
+    __shared__ float2 zt2[3 * M], zs2[3 * M];
     __shared__ TS D2[3 * M2];
     const int row = rows[bi];
     const int rg = threadIdx.x % M2, sl = threadIdx.x / M2;
     const bool active = sl < NSL;
     const int ib = rg % M, ic = rg / M;
-    cluster_nodes(t, c, row, zt);
+    if constexpr (F32N) {
+        for (int e = threadIdx.x; e < 3 * M; e += blockDim.x) zt2[e] = t.zhl[(int64_t)row * 3 * M + e];
+    } else {
+        cluster_nodes(t, c, row, zt);
+    }
     TA acc[M][NR];
 #pragma unroll
     for (int a = 0; a < M; ++a)
@@ -139,6 +148,7 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
     static_assert(3 * M <= NT, "one column node per thread");
     TX xpre[PF];
     double zpre = 0.0;
+    float2 zpre2 = make_float2(0.0f, 0.0f);
     auto prefetch = [&](int b) {
         const int s = col[b];
 #pragma unroll
@@ -147,8 +157,12 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
             xpre[j] = e < K * NR ? xh[(int64_t)s * K * NR + e] : (TX)0;
         }
         if (threadIdx.x < 3 * M) {
-            const int d = threadIdx.x / M, a = threadIdx.x % M;
-            zpre = t.box[d * t.nc + s] + t.box[(3 + d) * t.nc + s] * c.cheb[a];
+            if constexpr (F32N) {
+                zpre2 = t.zhl[(int64_t)s * 3 * M + threadIdx.x];
+            } else {
+                const int d = threadIdx.x / M, a = threadIdx.x % M;
+                zpre = t.box[d * t.nc + s] + t.box[(3 + d) * t.nc + s] * c.cheb[a];
+            }
         }
     };
     const int bbeg = ptr[bi], bend = ptr[bi + 1];
@@ -160,13 +174,22 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
             const int e = threadIdx.x + j * NT;
             if (e < K * NR) xs[e] = (TA)xpre[j];
         }
-        if (threadIdx.x < 3 * M) zs[threadIdx.x] = zpre;
+        if (threadIdx.x < 3 * M) {
+            if constexpr (F32N) zs2[threadIdx.x] = zpre2;
+            else zs[threadIdx.x] = zpre;
+        }
         if (b + 1 < bend) prefetch(b + 1);
         __syncthreads();
         for (int e = threadIdx.x; e < 3 * M2; e += blockDim.x) {
             const int d = e / M2, a = (e / M) % M, a2 = e % M;
-            const double df = zt[d * M + a] - zs[d * M + a2];
-            D2[e] = (TS)(df * df);
+            if constexpr (F32N) {
+                const float2 u = zt2[d * M + a], v = zs2[d * M + a2];
+                const float df = (u.x - v.x) + (u.y - v.y);
+                D2[e] = df * df;
+            } else {
+                const double df = zt[d * M + a] - zs[d * M + a2];
+                D2[e] = (TS)(df * df);
+            }
         }
         __syncthreads();
         if (!active) continue;

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
     using S = TcShape<M, NR, KIND>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    __shared__ double zt[3 * M];
+    __shared__ float2 zt[3 * M];  // nodes of t as FP32 (hi, lo)
     __shared__ float D2[3 * M * M];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tslot;
@@ -185,10 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
 
     // zero both stages (padding rows and columns stay zero), nodes of t
     for (int e = tid; e < 2 * S::STAGE / 16; e += kThreads) reinterpret_cast<uint4*>(base)[e] = make_uint4(0, 0, 0, 0);
-    for (int e = tid; e < 3 * M; e += kThreads) {
-        const int d = e / M, a = e % M;
-        zt[e] = t.box[d * t.nc + row] + t.box[(3 + d) * t.nc + row] * c.cheb[a];
-    }
+    for (int e = tid; e < 3 * M; e += kThreads) zt[e] = t.zhl[(int64_t)row * 3 * M + e];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                      "r"(S::TMEM_COLS));
@@ -217,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
     // register prefetch of the next block's x-hat values and box (centre, half-width)
     constexpr int PF = (S::K * NR + kThreads - 1) / kThreads;
     float xpre[PF];
-    double bcen = 0.0, bhalf = 0.0;
+    float2 zpre = make_float2(0.0f, 0.0f);  // node (d, a2) of the column cluster, (hi, lo)
     static_assert(3 * M * M <= kThreads, "one D2 entry per thread");
     auto prefetch = [&](int b) {
         const int s = col[b0 + b];
@@ -227,9 +224,8 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
             xpre[j] = e < S::K * NR ? xh[(int64_t)s * S::K * NR + e] : 0.0f;
         }
         if (tid < 3 * M * M) {
-            const int d = tid / (M * M);
-            bcen = t.box[d * t.nc + s];
-            bhalf = t.box[(3 + d) * t.nc + s];
+            const int d = tid / (M * M), a2 = tid % M;
+            zpre = t.zhl[(int64_t)s * 3 * M + d * M + a2];
         }
     };
     if (nb > 0) prefetch(0);
@@ -242,9 +238,10 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
             if (!ok) break;
         }
         if (tid < 3 * M * M) {
-            const int d = tid / (M * M), a = (tid / M) % M, a2 = tid % M;
-            const double df = zt[d * M + a] - (bcen + bhalf * c.cheb[a2]);
-            D2[tid] = (float)(df * df);
+            const int d = tid / (M * M), a = (tid / M) % M;
+            const float2 u = zt[d * M + a];
+            const float df = (u.x - zpre.x) + (u.y - zpre.y);
+            D2[tid] = df * df;
         }
         // x-hat_s staged transposed: row r, column mu
 #pragma unroll
@@ -334,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
         for (int mt = 0; mt < S::MT; ++mt) {
 #pragma unroll
             for (int c0 = 0; c0 < S::N; c0 += 8) {
-                double sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                float sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
                 for (int a = 0; a < S::NACC; ++a) {
                     uint32_t v[8];
@@ -345,13 +342,13 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
                                  : "r"(ta));
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) sum[q] += (double)__uint_as_float(v[q]);
+                    for (int q = 0; q < 8; ++q) sum[q] += __uint_as_float(v[q]);
                 }
                 const int nu_out = mt * 64 + warp * 16 + lane;
                 if (lane < 16 && nu_out < S::K) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (c0 + q < NR) yh[((int64_t)row * S::K + nu_out) * NR + c0 + q] = (float)(sum[q] * kInv4Pi);
+                        if (c0 + q < NR) yh[((int64_t)row * S::K + nu_out) * NR + c0 + q] = (float)sum[q] * (float)kInv4Pi;
                 }
             }
         }
