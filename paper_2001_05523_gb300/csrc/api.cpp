@@ -576,7 +576,7 @@ struct h2bem_op {
     h2::Consts consts{};
     // device geometry and tree
     DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
-    DevBuf cbegin, cend, cchild0, cchild1, cbox, czhl, leaves, basis_rule;
+    DevBuf cbegin, cend, cchild0, cchild1, cbox, czhl, cetr, leaves, basis_rule;
     std::vector<int> leaves_h;
     int max_leaf = 0;               // largest leaf cluster
     DevBuf basisV, basisW;          // stored leaf bases [pos][nu]: V (FP32 in the mixed tier), W (double layer, FP64)
@@ -634,7 +634,8 @@ struct h2bem_op {
     }
     h2::Tree tree() const {
         return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
-                        cchild1.as<const int>(), cbox.as<const double>(), czhl.as<const float2>()};
+                        cchild1.as<const int>(), cbox.as<const double>(), czhl.as<const float2>(),
+                        cetr.as<const float>()};
     }
     ~h2bem_op() {
         for (auto& e : ev)
@@ -862,6 +863,24 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
                 zhl[e] = hi;
                 zhl[e + 1] = (float)(z - (double)hi);
             }
+    // FP32 transfer factors of every child to its parent: L_{p,a}(z_{c}[a']) with
+    // yhat = (z - c_p) / h_p, by barycentric products in FP64, rounded once
+    std::vector<float> etr((size_t)nc * 3 * m * m, 0.0f);
+    for (int64_t p = 0; p < nc; ++p) {
+        if (c0[p] < 0) continue;
+        for (int ch : {c0[p], c1[p]})
+            for (int d = 0; d < 3; ++d)
+                for (int ap = 0; ap < m; ++ap) {
+                    const double z = box[d * nc + ch] + box[(3 + d) * nc + ch] * op->consts.cheb[ap];
+                    const double yh = (z - box[d * nc + p]) * box[(6 + d) * nc + p];
+                    for (int a = 0; a < m; ++a) {
+                        double pr = op->consts.bary[a];
+                        for (int b = 0; b < m; ++b)
+                            if (b != a) pr *= yh - op->consts.cheb[b];
+                        etr[(((size_t)ch * 3 + d) * m + ap) * m + a] = (float)pr;
+                    }
+                }
+    }
     op->nleaves = (int64_t)op->leaves_h.size();
     std::vector<int> leaf_index(nc, -1);
     for (size_t l = 0; l < op->leaves_h.size(); ++l) leaf_index[op->leaves_h[l]] = (int)l;
@@ -911,7 +930,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if ((rc = upload(op->xyz, mesh->xyz)) || (rc = upload(op->tri, std::vector<int>(mesh->tri.begin(), mesh->tri.end()))) ||
         (rc = upload(op->perm, permv)) || (rc = upload(op->iperm, iperm)) || (rc = upload(op->cbegin, cb)) ||
         (rc = upload(op->cend, ce)) || (rc = upload(op->cchild0, c0)) || (rc = upload(op->cchild1, c1)) ||
-        (rc = upload(op->cbox, box)) || (rc = upload(op->czhl, zhl)) || (rc = upload(op->leaves, op->leaves_h)))
+        (rc = upload(op->cbox, box)) || (rc = upload(op->czhl, zhl)) || (rc = upload(op->cetr, etr)) || (rc = upload(op->leaves, op->leaves_h)))
         return rc;
     if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
         (rc = op->near_u.upload_all()) || (rc = op->work.alloc(4 * sizeof(int))))

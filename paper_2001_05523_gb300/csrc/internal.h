@@ -43,6 +43,8 @@ struct Tree {
     const double* box;   // [9][nc]: centre x,y,z, (floored) half-width x,y,z, 1/half-width x,y,z
     const float2* zhl;   // [nc][3][m] interpolation node coordinates c_d + h_d cheb[a] as FP32 (hi, lo):
                          // hi = fl(z), lo = fl(z - hi)
+    const float* etr;    // [nc][3][m][m] FP32 transfer factors of each non-root cluster c to its parent p:
+                         // E[d][a'][a] = L_{p,a}^{(d)}(z_{c,d}[a']), evaluated in FP64 and rounded once
 };
 
 // Quadrature and interpolation constants passed by value.

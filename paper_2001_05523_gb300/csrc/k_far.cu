@@ -233,6 +233,21 @@ __global__ void __launch_bounds__(256) k_leaf_basis(Geom g, Tree t, Consts c, co
     }
 }
 
+// copy `bytes` bytes of a contiguous tile from global to shared memory:
+// 16-byte loads where source and size allow, else 4-byte loads
+template <typename T>
+__device__ __forceinline__ void stage_tile(T* dst, const T* src, size_t bytes) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (bytes & 15) == 0) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        for (size_t e = threadIdx.x; e < bytes / 16; e += blockDim.x) d4[e] = s4[e];
+    } else {
+        const unsigned* s1 = reinterpret_cast<const unsigned*>(src);
+        unsigned* d1 = reinterpret_cast<unsigned*>(dst);
+        for (size_t e = threadIdx.x; e < bytes / 4; e += blockDim.x) d1[e] = s1[e];
+    }
+}
+
 template <typename TB, typename TA, int NR>
 __global__ void __launch_bounds__(128) k_leaf_fwd_st(Tree t, int k, const int* __restrict__ leaves,
                                                      const TB* __restrict__ B, const double* __restrict__ xp,
@@ -243,8 +258,17 @@ __global__ void __launch_bounds__(128) k_leaf_fwd_st(Tree t, int k, const int* _
     TB* sB = reinterpret_cast<TB*>(smem_raw);                                        // [R][k]
     TA* sx = reinterpret_cast<TA*>(smem_raw + (((size_t)R * k * sizeof(TB) + 15) & ~size_t(15)));  // [R][NR]
     const TB* Bs = B + (int64_t)b * k;
-    for (int e = threadIdx.x; e < R * k; e += blockDim.x) sB[e] = Bs[e];
-    for (int e = threadIdx.x; e < R * NR; e += blockDim.x) sx[e] = (TA)xp[(int64_t)b * NR + e];
+    stage_tile(sB, Bs, (size_t)R * k * sizeof(TB));
+    if (NR % 2 == 0) {  // x rows of the leaf: 16-byte loads of two doubles
+        const double2* x2 = reinterpret_cast<const double2*>(xp + (int64_t)b * NR);
+        for (int e = threadIdx.x; e < R * NR / 2; e += blockDim.x) {
+            const double2 v = x2[e];
+            sx[2 * e] = (TA)v.x;
+            sx[2 * e + 1] = (TA)v.y;
+        }
+    } else {
+        for (int e = threadIdx.x; e < R * NR; e += blockDim.x) sx[e] = (TA)xp[(int64_t)b * NR + e];
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
         const int nu = e / NR, r = e % NR;
@@ -265,8 +289,21 @@ __global__ void __launch_bounds__(128) k_leaf_bwd_st(Tree t, int k, const int* _
     TB* sB = reinterpret_cast<TB*>(smem_raw);                                         // [R][kp]
     TA* sy = reinterpret_cast<TA*>(smem_raw + (((size_t)R * kp * sizeof(TB) + 15) & ~size_t(15)));  // [k][NR]
     const TB* Bs = B + (int64_t)b * k;
-    for (int e = threadIdx.x; e < R * k; e += blockDim.x) sB[(e / k) * kp + e % k] = Bs[e];
-    for (int e = threadIdx.x; e < k * NR; e += blockDim.x) sy[e] = yh[(int64_t)s * k * NR + e];
+    if (sizeof(TB) == 4 && (k % 4) == 0) {  // 16-byte loads of four basis values, spread to the padded rows
+        const uint4* b4 = reinterpret_cast<const uint4*>(Bs);
+        for (int e = threadIdx.x; e < R * k / 4; e += blockDim.x) {
+            const uint4 v = b4[e];
+            const int j = (4 * e) / k, nu = (4 * e) % k;
+            TB* dst = sB + j * kp + nu;
+            dst[0] = __uint_as_float(v.x);
+            dst[1] = __uint_as_float(v.y);
+            dst[2] = __uint_as_float(v.z);
+            dst[3] = __uint_as_float(v.w);
+        }
+    } else {
+        for (int e = threadIdx.x; e < R * k; e += blockDim.x) sB[(e / k) * kp + e % k] = Bs[e];
+    }
+    stage_tile(sy, yh + (int64_t)s * k * NR, (size_t)k * NR * sizeof(TA));
     __syncthreads();
     for (int e = threadIdx.x; e < R * NR; e += blockDim.x) {
         const int j = e / NR, r = e % NR;
@@ -280,28 +317,36 @@ __global__ void __launch_bounds__(128) k_leaf_bwd_st(Tree t, int k, const int* _
 // Transfers between a parent t and its children (Kronecker form).
 // E1[ch][d][a'][a] = L_{t,a}^{(d)}(z_{ch,d}[a']).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int MM>
 __device__ void transfer_1d(const Tree& t, const Consts& c, int parent, const int* ch, T* E1) {
-    // child node z = c_ch + h_ch cheb[a'] in reference units of the parent,
-    // yhat = (z - c_p) / h_p, and L_a(yhat) = bary[a] prod_{b != a} (yhat - cheb[b])
-    const int m = c.m;
+    // E1[q][d][a'][a] = L_{p,a}(yhat), yhat = (z_{ch_q}[a'] - c_p) / h_p: FP32
+    // vectors take the factors evaluated at set-up (FP64, rounded once); FP64
+    // vectors evaluate L_a(yhat) = bary[a] prod_{b != a} (yhat - cheb[b]) here
+    const int m = MM > 0 ? MM : c.m;
     for (int e = threadIdx.x; e < 2 * 3 * m * m; e += blockDim.x) {
-        const int q = e / (3 * m * m), d = (e / (m * m)) % 3, ap = (e / m) % m, a = e % m;
-        const int cl = ch[q];
-        const double yh = (t.box[d * t.nc + cl] - t.box[d * t.nc + parent] + t.box[(3 + d) * t.nc + cl] * c.cheb[ap]) *
-                          t.box[(6 + d) * t.nc + parent];
-        double pr = c.bary[a];
-        for (int b = 0; b < m; ++b)
-            if (b != a) pr *= yh - c.cheb[b];
-        E1[e] = (T)pr;
+        const int q = e / (3 * m * m), r = e % (3 * m * m);
+        if constexpr (sizeof(T) == sizeof(float)) {
+            E1[e] = t.etr[(int64_t)ch[q] * 3 * m * m + r];
+        } else {
+            const int d = r / (m * m), ap = (r / m) % m, a = r % m;
+            const int cl = ch[q];
+            const double yd = (t.box[d * t.nc + cl] - t.box[d * t.nc + parent] + t.box[(3 + d) * t.nc + cl] * c.cheb[ap]) *
+                              t.box[(6 + d) * t.nc + parent];
+            double pr = c.bary[a];
+            for (int b = 0; b < m; ++b)
+                if (b != a) pr *= yd - c.cheb[b];
+            E1[e] = (T)pr;
+        }
     }
     __syncthreads();
 }
 
 // up: X[a',b',c'] -> out[a,b,c] = sum E_x[a'][a] E_y[b'][b] E_z[c'][c] X
 // down: Y[a,b,c] -> out[a',b',c'] = sum E_x[a'][a] E_y[b'][b] E_z[c'][c] Y
-template <typename T, int NR, bool UP>
-__device__ void kron_apply(const T* E1, int m, const T* in, T* tmp1, T* tmp2, T* out, bool accumulate) {
+// MM: compile-time m (0: runtime m)
+template <typename T, int NR, bool UP, int MM>
+__device__ void kron_apply(const T* E1, int mrt, const T* in, T* tmp1, T* tmp2, T* out, bool accumulate) {
+    const int m = MM > 0 ? MM : mrt;
     const int k = m * m * m;
     const T* Ex = E1;
     const T* Ey = E1 + m * m;
@@ -310,67 +355,78 @@ __device__ void kron_apply(const T* E1, int m, const T* in, T* tmp1, T* tmp2, T*
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
         const int r = e % NR, nu = e / NR, a = nu % m, rest = nu / m;
         T s = 0;
-        for (int q = 0; q < m; ++q) s += (UP ? Ex[q * m + a] : Ex[a * m + q]) * in[((rest * m) + q) * NR + r];
+#pragma unroll
+        for (int q = 0; q < (MM > 0 ? MM : kMaxM); ++q) {
+            if (MM == 0 && q >= m) break;
+            s += (UP ? Ex[q * m + a] : Ex[a * m + q]) * in[((rest * m) + q) * NR + r];
+        }
         tmp1[e] = s;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
         const int r = e % NR, nu = e / NR, a = nu % m, b = (nu / m) % m, cc = nu / (m * m);
         T s = 0;
-        for (int q = 0; q < m; ++q)
+#pragma unroll
+        for (int q = 0; q < (MM > 0 ? MM : kMaxM); ++q) {
+            if (MM == 0 && q >= m) break;
             s += (UP ? Ey[q * m + b] : Ey[b * m + q]) * tmp1[((cc * m + q) * m + a) * NR + r];
+        }
         tmp2[e] = s;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) {
         const int r = e % NR, nu = e / NR, ab = nu % (m * m), cc = nu / (m * m);
         T s = 0;
-        for (int q = 0; q < m; ++q) s += (UP ? Ez[q * m + cc] : Ez[cc * m + q]) * tmp2[((q * m * m) + ab) * NR + r];
+#pragma unroll
+        for (int q = 0; q < (MM > 0 ? MM : kMaxM); ++q) {
+            if (MM == 0 && q >= m) break;
+            s += (UP ? Ez[q * m + cc] : Ez[cc * m + q]) * tmp2[((q * m * m) + ab) * NR + r];
+        }
         if (accumulate) out[e] += s;
         else out[e] = s;
     }
     __syncthreads();
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int MM>
 __global__ void __launch_bounds__(256) k_upward(Tree t, Consts c, const int* __restrict__ parents, T* __restrict__ xh) {
     extern __shared__ unsigned char smem_raw[];
     T* E1 = reinterpret_cast<T*>(smem_raw);
     T* buf = E1 + 2 * 3 * kMaxM * kMaxM;
-    const int k = c.k;
+    const int m = MM > 0 ? MM : c.m, k = m * m * m;
     T* in = buf;
     T* tmp1 = in + k * NR;
     T* tmp2 = tmp1 + k * NR;
     T* out = tmp2 + k * NR;
     const int p = parents[blockIdx.x];
     const int ch[2] = {t.child0[p], t.child1[p]};
-    transfer_1d<T>(t, c, p, ch, E1);
+    transfer_1d<T, MM>(t, c, p, ch, E1);
     for (int q = 0; q < 2; ++q) {
         for (int e = threadIdx.x; e < k * NR; e += blockDim.x) in[e] = xh[(int64_t)ch[q] * k * NR + e];
         __syncthreads();
-        kron_apply<T, NR, true>(E1 + q * 3 * c.m * c.m, c.m, in, tmp1, tmp2, out, q == 1);
+        kron_apply<T, NR, true, MM>(E1 + q * 3 * m * m, m, in, tmp1, tmp2, out, q == 1);
     }
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) xh[(int64_t)p * k * NR + e] = out[e];
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int MM>
 __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* __restrict__ parents,
                                                   T* __restrict__ yh) {
     extern __shared__ unsigned char smem_raw[];
     T* E1 = reinterpret_cast<T*>(smem_raw);
     T* buf = E1 + 2 * 3 * kMaxM * kMaxM;
-    const int k = c.k;
+    const int m = MM > 0 ? MM : c.m, k = m * m * m;
     T* in = buf;
     T* tmp1 = in + k * NR;
     T* tmp2 = tmp1 + k * NR;
     T* out = tmp2 + k * NR;
     const int p = parents[blockIdx.x];
     const int ch[2] = {t.child0[p], t.child1[p]};
-    transfer_1d<T>(t, c, p, ch, E1);
+    transfer_1d<T, MM>(t, c, p, ch, E1);
     for (int e = threadIdx.x; e < k * NR; e += blockDim.x) in[e] = yh[(int64_t)p * k * NR + e];
     __syncthreads();
     for (int q = 0; q < 2; ++q) {
-        kron_apply<T, NR, false>(E1 + q * 3 * c.m * c.m, c.m, in, tmp1, tmp2, out, false);
+        kron_apply<T, NR, false, MM>(E1 + q * 3 * m * m, m, in, tmp1, tmp2, out, false);
         for (int e = threadIdx.x; e < k * NR; e += blockDim.x) yh[(int64_t)ch[q] * k * NR + e] += out[e];
         __syncthreads();
     }
@@ -522,16 +578,23 @@ void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves
                                        yh, yp, s)))
 }
 
-template <typename T, int NR, bool UP>
-static void updown(const Tree& t, const Consts& c, int np, const int* parents, void* v, cudaStream_t s) {
+template <typename T, int NR, bool UP, int MM>
+static void updown_m(const Tree& t, const Consts& c, int np, const int* parents, void* v, cudaStream_t s) {
     const size_t smem = sizeof(T) * (2 * 3 * kMaxM * kMaxM + 4 * (size_t)c.k * NR);
     if (UP) {
-        cudaFuncSetAttribute(k_upward<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_upward<T, NR><<<np, 256, smem, s>>>(t, c, parents, (T*)v);
+        cudaFuncSetAttribute(k_upward<T, NR, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_upward<T, NR, MM><<<np, 256, smem, s>>>(t, c, parents, (T*)v);
     } else {
-        cudaFuncSetAttribute(k_downward<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_downward<T, NR><<<np, 256, smem, s>>>(t, c, parents, (T*)v);
+        cudaFuncSetAttribute(k_downward<T, NR, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_downward<T, NR, MM><<<np, 256, smem, s>>>(t, c, parents, (T*)v);
     }
+}
+
+template <typename T, int NR, bool UP>
+static void updown(const Tree& t, const Consts& c, int np, const int* parents, void* v, cudaStream_t s) {
+    if (c.m == 4) updown_m<T, NR, UP, 4>(t, c, np, parents, v, s);
+    else if (c.m == 5) updown_m<T, NR, UP, 5>(t, c, np, parents, v, s);
+    else updown_m<T, NR, UP, 0>(t, c, np, parents, v, s);
 }
 
 void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,

@@ -411,21 +411,21 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
             const int jc = cdiag + e / NR, r = e % NR;
             T sum = 0;
             for (int i = 0; i < R; ++i) sum += sA[i * cmax + jc] * sxr[i * NR + r];
-            atomicAdd(&yp[(int64_t)sgid[jc] * NR + r], (double)sum * kInv4Pi);
+            atomicAdd(&yp[(int64_t)sgid[jc] * NR + r], (double)(sum * (T)kInv4Pi));
         }
         b = b2;
     }
     __syncthreads();
-    // row side: reduce the K partial sums of each row
-    double* sred = reinterpret_cast<double*>(smem);
+    // row side: reduce the K partial sums of each row (in the working precision)
+    T* sred = reinterpret_cast<T*>(smem);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) sred[tid * NR + r] = active ? (double)acc[r] : 0.0;
+    for (int r = 0; r < NR; ++r) sred[tid * NR + r] = active ? acc[r] : (T)0;
     __syncthreads();
     for (int e = tid; e < R * NR; e += kThreads) {
         const int i = e / NR, r = e % NR;
-        double s = 0.0;
+        T s = 0;
         for (int q = 0; q < K; ++q) s += sred[(q * R + i) * NR + r];
-        atomicAdd(&yp[(int64_t)(rb + i) * NR + r], s * kInv4Pi);
+        atomicAdd(&yp[(int64_t)(rb + i) * NR + r], (double)(s * (T)kInv4Pi));
     }
 }
 

@@ -256,3 +256,23 @@ def test_mixed_with_fp64_singular_points(H, orc, kernel):
     op.close()
     ref = orc.H2(mesh, kernel, m=4).matvec(x)
     assert rel(y, ref) < TOL["mixed_fp32"]
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_mixed_vs_fp64_on_a_deep_tree(H, kernel):
+    """524,288-triangle sphere (17 tree levels): the mixed tier against the
+    FP64 tier on the same operator and 8 right-hand sides, at the mixed
+    tolerance.  Rounding in per-level quantities (transfer factors, node
+    coordinates) compounds with depth, so small meshes alone do not bound it."""
+    import torch
+
+    mesh = I.sphere(256)
+    x = torch.from_numpy(I.rhs(mesh.nt, 8, seed=21)).cuda()
+    ys = {}
+    for prec in ("fp64", "mixed_fp32"):
+        op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, precision=prec)
+        ys[prec] = op.apply(x)
+        torch.cuda.synchronize()
+        op.close()
+    err = float(torch.linalg.norm(ys["mixed_fp32"] - ys["fp64"]) / torch.linalg.norm(ys["fp64"]))
+    assert err < TOL["mixed_fp32"], err
