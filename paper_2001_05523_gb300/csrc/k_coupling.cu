@@ -144,17 +144,31 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
         for (int r = 0; r < NR; ++r) acc[a][r] = 0;
     // register prefetch of the next block's x-hat values and column nodes, so
     // that their global-memory latency overlaps the current block's work
-    constexpr int NT = M2 * NSL, PF = (K * NR + NT - 1) / NT;
+    constexpr int NT = M2 * NSL;
     static_assert(3 * M <= NT, "one column node per thread");
+    // x-hat of the next block: asynchronous 16-byte copies into the other half
+    // of a double buffer (same type in global and shared memory), else a
+    // register prefetch with conversion
+    constexpr bool ASYNC = std::is_same<TX, TA>::value && (K * NR * sizeof(TA)) % 16 == 0;
+    constexpr int PF = ASYNC ? 1 : (K * NR + NT - 1) / NT;
     TX xpre[PF];
     double zpre = 0.0;
     float2 zpre2 = make_float2(0.0f, 0.0f);
-    auto prefetch = [&](int b) {
+    auto prefetch = [&](int b, TA* dst) {
         const int s = col[b];
+        if constexpr (ASYNC) {
+            const char* src = reinterpret_cast<const char*>(xh + (int64_t)s * K * NR);
+            const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+            for (int e = threadIdx.x; e < (int)(K * NR * sizeof(TA) / 16); e += NT)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16 * e), "l"(src + 16 * e)
+                             : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        } else {
 #pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int e = threadIdx.x + j * NT;
-            xpre[j] = e < K * NR ? xh[(int64_t)s * K * NR + e] : (TX)0;
+            for (int j = 0; j < PF; ++j) {
+                const int e = threadIdx.x + j * NT;
+                xpre[j] = e < K * NR ? xh[(int64_t)s * K * NR + e] : (TX)0;
+            }
         }
         if (threadIdx.x < 3 * M) {
             if constexpr (F32N) {
@@ -166,19 +180,26 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
         }
     };
     const int bbeg = ptr[bi], bend = ptr[bi + 1];
-    if (bbeg < bend) prefetch(bbeg);
+    if (bbeg < bend) prefetch(bbeg, xs);
     for (int b = bbeg; b < bend; ++b) {
-        __syncthreads();
+        TA* xcur = xs + (ASYNC ? ((b - bbeg) & 1) * K * NR : 0);
+        __syncthreads();  // the previous block is done with shared memory
+        if constexpr (!ASYNC) {
 #pragma unroll
-        for (int j = 0; j < PF; ++j) {
-            const int e = threadIdx.x + j * NT;
-            if (e < K * NR) xs[e] = (TA)xpre[j];
+            for (int j = 0; j < PF; ++j) {
+                const int e = threadIdx.x + j * NT;
+                if (e < K * NR) xcur[e] = (TA)xpre[j];
+            }
         }
         if (threadIdx.x < 3 * M) {
             if constexpr (F32N) zs2[threadIdx.x] = zpre2;
             else zs[threadIdx.x] = zpre;
         }
-        if (b + 1 < bend) prefetch(b + 1);
+        if (b + 1 < bend) prefetch(b + 1, xs + (ASYNC ? ((b + 1 - bbeg) & 1) * K * NR : 0));
+        if constexpr (ASYNC) {
+            if (b + 1 < bend) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
         __syncthreads();
         for (int e = threadIdx.x; e < 3 * M2; e += blockDim.x) {
             const int d = e / M2, a = (e / M) % M, a2 = e % M;
@@ -201,7 +222,7 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
         for (int r2 = sl; r2 < M2; r2 += NSL) {
             const int jc = r2 / M, jb = r2 % M;
             const TS sbc = D2[M2 + ib * M + jb] + D2[2 * M2 + ic * M + jc];
-            const TA* xrow = xs + (r2 * M) * NR;
+            const TA* xrow = xcur + (r2 * M) * NR;
 #pragma unroll
             for (int ja = 0; ja < M; ++ja) {
                 TA xv[NR];
@@ -255,7 +276,7 @@ template <typename TS, typename TA, typename TX, typename TY, int NR, int M, int
 static void coupling_rows_nsl(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                               const int* col, const void* xh, void* yh, int* work, cudaStream_t s) {
     constexpr int K = M * M * M;
-    const size_t smem = sizeof(TA) * (size_t)NSL * K * NR;
+    const size_t smem = sizeof(TA) * (size_t)(NSL > 2 ? NSL : 2) * K * NR;  // reduction area, or two x-hat tiles
     if (!work) {
         auto kern = k_coupling_rows<TS, TA, TX, TY, NR, M, NSL, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
