@@ -437,8 +437,9 @@ def main():
         "e2e": {"value": world * n * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * nrhs * 8,
                 "d2h_bytes_per_step": n * nrhs * 8},
         "gpu_launches": int(st_m["launches"]) * args.steps,
-        "launch_variant": {"near_persistent": st_m["launch_variant"][0], "coupling_slices": st_m["launch_variant"][1],
-                           "coupling_persistent": st_m["launch_variant"][2], "autotuned": st_m["launch_variant"][3]},
+        "launch_variant": {"near_persistent": st_m["launch_variant"][0], "near_ctas_per_sm": st_m["launch_variant"][1],
+                           "coupling_slices": st_m["launch_variant"][2],
+                           "coupling_persistent": st_m["launch_variant"][3], "autotuned": st_m["launch_variant"][4]},
         "clocks": clocks,
     }
     out.update(extra)

@@ -80,14 +80,17 @@ typedef struct {
                         /*    direction (the second such call captures it); 0: plain launches     */
     int autotune;       /* 1: the first apply with a given right-hand-side width and direction    */
                         /*    times the launch variants of the regular nearfield (one CTA per     */
-                        /*    row leaf, or persistent CTAs taking rows from a work counter) and   */
+                        /*    row leaf, or persistent CTAs taking rows from a work counter; the  */
+                        /*    register budget) and                                                 */
                         /*    of the SIMT coupling (2, 4 or 8 slices per CTA, one CTA per row or  */
                         /*    persistent) on the operator's own data and keeps the fastest; the   */
                         /*    variants sum in different orders, so results differ by rounding.    */
                         /*    No tuning while the stream is being captured.  0: defaults (one     */
-                        /*    CTA per row, 4 slices).  2 + v (v = 0..11) fixes a variant:         */
-                        /*    v = nearfield persistent + 2 coupling persistent + 4 i, where i =   */
-                        /*    0, 1, 2 selects 2, 4, 8 slices                                       */
+                        /*    CTA per row, 4 slices).  2 + v (v = 0..35) fixes a variant:         */
+                        /*    v = nearfield persistent + 2 coupling persistent + 4 i + 12 j,     */
+                        /*    where i = 0, 1, 2 selects 2, 4, 8 slices and j = 0, 1, 2 a          */
+                        /*    nearfield register budget for 4, 3, 2 CTAs per SM (FP32 single     */
+                        /*    layer)                                                               */
     int singular_fp64;  /* 1: Sauter-Schwab quadrature points of edge- and vertex-adjacent pairs   */
                         /*    in FP64 in every tier; 0 (default): FP32 points in the MIXED tiers  */
                         /*    (Gram set-up, partial sums and accumulation stay FP64)              */
@@ -110,10 +113,12 @@ typedef struct {
     double last_apply_ms;      /* device time of the last timed apply         */
     double stage_ms[8];        /* per stage of the last timed apply, see      */
                                /* h2bem_apply_timed                            */
-    int64_t launch_variant[4]; /* of the last apply: regular nearfield         */
-                               /* persistent (0/1), SIMT coupling slices per   */
-                               /* CTA, SIMT coupling persistent (0/1), 1 if    */
-                               /* chosen by the autotuner                      */
+    int64_t launch_variant[5]; /* of the last apply: regular nearfield         */
+                               /* persistent (0/1), regular nearfield CTAs per */
+                               /* SM of its register budget (4, 3, 2), SIMT    */
+                               /* coupling slices per CTA, SIMT coupling       */
+                               /* persistent (0/1), 1 if chosen by the         */
+                               /* autotuner or fixed through opts.autotune     */
     int64_t regular_evals;     /* pairs the regular nearfield kernel          */
                                /* evaluates per apply (49 kernel evaluations   */
                                /* each): every pair of the blocks (t, s >= t)  */

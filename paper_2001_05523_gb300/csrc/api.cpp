@@ -607,8 +607,9 @@ struct h2bem_op {
         bool done = false;
         h2::LaunchCfg near, coup;  // work pointers filled in at launch
         bool near_persist = false, coup_persist = false;
+        int near_nb = 0;
     } tuned[4][2];
-    int64_t last_variant[4] = {0, 4, 0, 0};
+    int64_t last_variant[5] = {0, 4, 4, 0, 0};
     DevBuf work;  // row counters of persistent launches (2 ints)
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
@@ -759,8 +760,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->q_ss = opts.q_ss;
     op->cache_singular = opts.cache_singular ? 1 : 0;
     op->use_graph = opts.use_graph ? 1 : 0;
-    if (opts.autotune < 0 || opts.autotune > 13)
-        return fail(H2BEM_ERR_ARG, "operator_create: autotune must be 0, 1 or 2..13, got %d", opts.autotune);
+    if (opts.autotune < 0 || opts.autotune > 37)
+        return fail(H2BEM_ERR_ARG, "operator_create: autotune must be 0, 1 or 2..37, got %d", opts.autotune);
     op->autotune = opts.autotune == 1 ? 1 : 0;
     op->singular_fp64 = opts.singular_fp64 ? 1 : 0;
     op->recompute_basis = opts.recompute_basis ? 1 : 0;
@@ -771,7 +772,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
                 tu.done = true;
                 tu.near_persist = (v & 1) != 0;
                 tu.coup_persist = (v & 2) != 0;
-                tu.coup.nsl = v / 4 == 0 ? 2 : v / 4 == 1 ? 4 : 8;
+                tu.coup.nsl = (v / 4) % 3 == 0 ? 2 : (v / 4) % 3 == 1 ? 4 : 8;
+                tu.near_nb = v / 12 == 0 ? 0 : v / 12 == 1 ? 3 : 2;
             }
     }
     op->n = mesh->nt;
@@ -1151,7 +1153,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->singular_pairs[2] = op->sing[2];
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
     st->regular_evals = op->regular_evals;
-    for (int i = 0; i < 4; ++i) st->launch_variant[i] = op->last_variant[i];
+    for (int i = 0; i < 5; ++i) st->launch_variant[i] = op->last_variant[i];
     st->k = op->k;
     st->launches = op->launches;
     st->last_apply_ms = op->last_ms;
@@ -1243,13 +1245,17 @@ static void launch_cfgs(h2bem_op* op, int NR, bool transpose, h2::LaunchCfg& nea
     coup = h2::LaunchCfg{};
     if (tu.done) {
         near.work = tu.near_persist ? w : nullptr;
+        near.nb = tu.near_nb;
         coup.nsl = tu.coup.nsl;
         coup.work = tu.coup_persist ? w + 1 : nullptr;
     }
     op->last_variant[0] = near.work != nullptr;
-    op->last_variant[1] = coup.nsl;
-    op->last_variant[2] = coup.work != nullptr;
-    op->last_variant[3] = tu.done ? 1 : 0;
+    // register budget in effect: variants exist for the FP32 single layer, the others use 2 CTAs per SM
+    const bool budgets = op->precision != H2BEM_FP64 && op->kernel == H2BEM_SLP;
+    op->last_variant[1] = budgets ? (near.nb == 0 ? 4 : near.nb) : 2;
+    op->last_variant[2] = coup.nsl;
+    op->last_variant[3] = coup.work != nullptr;
+    op->last_variant[4] = tu.done ? 1 : 0;
 }
 
 // One chunk of at most 16 right-hand sides, device buffers, tree order work.
@@ -1282,18 +1288,31 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         tune_now = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
     }
-    auto near_launch = [&](int* work) {
+    auto near_launch = [&](const h2::LaunchCfg& cf) {
         h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
                             op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR,
-                            op->xp.as<double>(), op->yp.as<double>(), work, s);
+                            op->xp.as<double>(), op->yp.as<double>(), cf, s);
     };
     mark(0);
     h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
     CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
     if (tune_now && op->near_u.nrows() > 0) {
-        const float t_plain = time_on(s, [&] { near_launch(nullptr); });
-        const float t_pers = time_on(s, [&] { near_launch(op->work.as<int>()); });
-        tu.near_persist = t_pers < t_plain;
+        float best = 1e30f;
+        const bool budgets = fp32 && !dlp;  // register-budget variants exist for the FP32 single layer
+        for (int nb : {0, 3, 2}) {
+            if (nb && !budgets) continue;
+            for (int pers = 0; pers < 2; ++pers) {
+                h2::LaunchCfg cf;
+                cf.nb = nb;
+                cf.work = pers ? op->work.as<int>() : nullptr;
+                const float ms = time_on(s, [&] { near_launch(cf); });
+                if (ms < best) {
+                    best = ms;
+                    tu.near_persist = pers != 0;
+                    tu.near_nb = nb;
+                }
+            }
+        }
         CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
     }
     if (tune_now && op->nfar > 0 && tc_kind(op, xh64, yh64) < 0 && (op->m == 4 || op->m == 5)) {
@@ -1358,7 +1377,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     {
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
-        near_launch(cfg_near.work);
+        near_launch(cfg_near);
     }
     nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
@@ -1668,7 +1687,7 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, false, cfg_near, cfg_coup);
         launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
-                        op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, cfg_near.work, s);
+                        op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, cfg_near, s);
     }
     for (int ty = 0; ty < 3; ++ty) {
         if (ty == 0 && dlp) continue;

@@ -59,6 +59,17 @@ struct Consts {
     int nb;                      // points of the leaf-basis rule
 };
 
+// Launch variant of a row-parallel kernel: work != nullptr runs persistent
+// CTAs (as many as fit on the GPU) that take rows from the counter *work
+// (reset by the launcher); nsl = slices of the SIMT coupling (2, 4 or 8).
+struct LaunchCfg {
+    int nsl = 4;
+    int* work = nullptr;
+    int nb = 0;  // regular nearfield (FP32 single layer): CTAs per SM of the register budget (0: 4)
+};
+// CTAs of `func` resident on the whole GPU at once (occupancy x SMs)
+int resident_ctas(const void* func, int threads, size_t smem);
+
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
                  double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
@@ -73,7 +84,7 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 // a row is t itself).  ker: SLP or DLP; transpose applies K^T (double layer).
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     int* work, cudaStream_t s);
+                     const LaunchCfg& cfg, cudaStream_t s);
 
 // nearfield, singular pairs of one type (canonical orientation, see api.cpp)
 //   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the
@@ -102,15 +113,7 @@ void launch_upward(const Tree& t, const Consts& c, int nparents, const int* pare
                    cudaStream_t s);
 void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,
                      cudaStream_t s);
-// Launch variant of a row-parallel kernel: work != nullptr runs persistent
-// CTAs (as many as fit on the GPU) that take rows from the counter *work
-// (reset by the launcher); nsl = slices of the SIMT coupling (2, 4 or 8).
-struct LaunchCfg {
-    int nsl = 4;
-    int* work = nullptr;
-};
-// CTAs of `func` resident on the whole GPU at once (occupancy x SMs)
-int resident_ctas(const void* func, int threads, size_t smem);
+
 
 // precision: 0 FP64 (xh, yh double), 1 FP32 SIMT arithmetic (xh / yh double
 // if xh64 / yh64, else float)

@@ -431,8 +431,10 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
 
 // One CTA per row leaf (work == nullptr), or persistent CTAs that take the
 // next row from the counter *work (zero before the launch) until none is left.
-template <int NR, bool DLPK, bool F32, bool PERSIST>
-__global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2)
+// NB: CTAs per SM the register budget is sized for (0: 4 for the FP32 single
+// layer, else 2); a launch shape the autotuner chooses.
+template <int NR, bool DLPK, bool F32, bool PERSIST, int NB>
+__global__ void __launch_bounds__(kThreads, NB > 0 ? NB : ((F32 && !DLPK) ? 4 : 2))
     k_near_sym(Geom g, Tree t, Consts c, int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
                const int* __restrict__ col, bool transpose, const double* __restrict__ xp, double* __restrict__ yp,
                int* __restrict__ work) {
@@ -453,45 +455,54 @@ __global__ void __launch_bounds__(kThreads, (F32 && !DLPK) ? 4 : 2)
 
 template <int NR, bool DLPK, bool F32>
 static void near_sym_go(int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c, const int* rows,
-                        const int* ptr, const int* col, bool tr, const double* xp, double* yp, int* work) {
+                        const int* ptr, const int* col, bool tr, const double* xp, double* yp, int* work, int nb) {
     using T = typename std::conditional<F32, float, double>::type;
     constexpr size_t smem = Smem<T, NR, DLPK>::BYTES;
-    if (!work) {
-        cudaFuncSetAttribute(k_near_sym<NR, DLPK, F32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_near_sym<NR, DLPK, F32, false><<<nrows, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp,
-                                                                      nullptr);
-        return;
+    auto go = [&](auto kplain, auto kpers) {
+        if (!work) {
+            cudaFuncSetAttribute(kplain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kplain<<<nrows, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, nullptr);
+            return;
+        }
+        cudaFuncSetAttribute(kpers, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = std::min(nrows, resident_ctas((const void*)kpers, kThreads, smem));
+        cudaMemsetAsync(work, 0, sizeof(int), s);
+        kpers<<<grid, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, work);
+    };
+    if constexpr (F32 && !DLPK) {
+        if (nb == 3) go(k_near_sym<NR, DLPK, F32, false, 3>, k_near_sym<NR, DLPK, F32, true, 3>);
+        else if (nb == 2) go(k_near_sym<NR, DLPK, F32, false, 2>, k_near_sym<NR, DLPK, F32, true, 2>);
+        else go(k_near_sym<NR, DLPK, F32, false, 0>, k_near_sym<NR, DLPK, F32, true, 0>);
+    } else {
+        go(k_near_sym<NR, DLPK, F32, false, 0>, k_near_sym<NR, DLPK, F32, true, 0>);
     }
-    auto kern = k_near_sym<NR, DLPK, F32, true>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = std::min(nrows, resident_ctas((const void*)kern, kThreads, smem));
-    cudaMemsetAsync(work, 0, sizeof(int), s);
-    kern<<<grid, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, work);
 }
 
 template <int NR>
 static void near_sym_nr(int ker, bool fp32, int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c,
                         const int* rows, const int* ptr, const int* col, bool tr, const double* xp, double* yp,
-                        int* work) {
+                        int* work, int nb) {
     const bool dlp = ker != SLP;
     if (fp32) {
-        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
-        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
+        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
+        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
     } else {
-        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
-        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work);
+        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
+        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
     }
 }
 
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     int* work, cudaStream_t s) {
+                     const LaunchCfg& cfg, cudaStream_t s) {
+    int* work = cfg.work;
+    const int nb = cfg.nb;
     if (nrows <= 0) return;
     switch (NR) {
-        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
-        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
-        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
-        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work); break;
+        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
+        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
+        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
+        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
     }
 }
 

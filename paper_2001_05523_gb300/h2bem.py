@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("regular_pairs", ctypes.c_int64),
                 ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("last_apply_ms", ctypes.c_double),
-                ("stage_ms", ctypes.c_double * 8), ("launch_variant", ctypes.c_int64 * 4),
+                ("stage_ms", ctypes.c_double * 8), ("launch_variant", ctypes.c_int64 * 5),
                 ("regular_evals", ctypes.c_int64)]
 
     def as_dict(self):

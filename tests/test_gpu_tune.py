@@ -46,7 +46,7 @@ def apply(H, mesh, x, tune, precision="fp64", kernel=0, transpose=False):
     return ys, st
 
 
-@pytest.mark.parametrize("v", list(range(12)))
+@pytest.mark.parametrize("v", list(range(36)))
 def test_fixed_variants_match_oracle(H, orc, v):
     mesh = I.jitter(I.sphere(14), 0.01, 21)
     x = I.rhs(mesh.nt, 8, seed=v)
@@ -54,8 +54,9 @@ def test_fixed_variants_match_oracle(H, orc, v):
     for prec in ("fp64", "mixed_fp32"):
         (y1, y2), st = apply(H, mesh, x, 2 + v, precision=prec)
         assert rel(y1, ref) < TOL[prec] and rel(y2, ref) < TOL[prec]
-        near_p, nsl, coup_p, tuned = st["launch_variant"]
-        assert (near_p, coup_p, nsl, tuned) == (v & 1, (v >> 1) & 1, (2, 4, 8)[v // 4], 1)
+        near_p, near_nb, nsl, coup_p, tuned = st["launch_variant"]
+        assert (near_p, coup_p, nsl, tuned) == (v & 1, (v >> 1) & 1, (2, 4, 8)[(v // 4) % 3], 1)
+        assert near_nb == ((4, 3, 2)[v // 12] if prec == "mixed_fp32" else 2)
 
 
 @pytest.mark.parametrize("kernel,transpose", [(0, False), (1, False), (1, True)])
@@ -65,8 +66,8 @@ def test_autotuner_choice_is_valid_and_correct(H, orc, kernel, transpose):
     ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)
     (y_first, y_second), st = apply(H, mesh, x, 1, kernel=kernel, transpose=transpose)
     assert rel(y_first, ref) < TOL["fp64"] and rel(y_second, ref) < TOL["fp64"]
-    near_p, nsl, coup_p, tuned = st["launch_variant"]
-    assert tuned == 1 and near_p in (0, 1) and coup_p in (0, 1) and nsl in (2, 4, 8)
+    near_p, near_nb, nsl, coup_p, tuned = st["launch_variant"]
+    assert tuned == 1 and near_p in (0, 1) and coup_p in (0, 1) and nsl in (2, 4, 8) and near_nb in (2, 3, 4)
     (d1, _), _ = apply(H, mesh, x, 0, kernel=kernel, transpose=transpose)
     assert rel(y_second, d1) < 1e-13
 
@@ -74,5 +75,5 @@ def test_autotuner_choice_is_valid_and_correct(H, orc, kernel, transpose):
 def test_autotune_rejects_bad_values(H):
     mesh = I.sphere(4)
     with pytest.raises(H.H2bemError) as e:
-        H.Operator(mesh.vertices, mesh.triangles, autotune=14)
+        H.Operator(mesh.vertices, mesh.triangles, autotune=38)
     assert e.value.code == H.H2BEM_ERR_ARG
