@@ -206,6 +206,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 tier")
     ap.add_argument("--tier", default="mixed_fp32", choices=["mixed_fp32", "mixed_tf32", "mixed_bf16"],
                     help="precision tier of the timed step (default mixed_fp32)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="opts.autotune of the timed operators: 1 tunes at the first apply (default), "
+                         "0 defaults, 2..37 a fixed launch variant (reproducible profiles)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -251,7 +254,7 @@ def main():
         t0 = time.perf_counter()
         # autotune: the first warm-up apply times the launch variants and keeps the fastest
         op = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, eta=2.0, leaf_size=32,
-                        precision=precision, cache_singular=cache, autotune=1, **kw)
+                        precision=precision, cache_singular=cache, autotune=args.autotune, **kw)
         setup_s = time.perf_counter() - t0
         y = torch.empty_like(x)
         for _ in range(args.warmup):
@@ -421,8 +424,8 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64 (mixed tier: FP32 farfield, regular pairs and edge/vertex Sauter-Schwab points; "
-                 "FP64 identical-pair quadrature, pair set-up, partial sums and accumulation)",
+        "dtype": "f32+f64 (mixed tier: FP32 farfield, regular pairs and Sauter-Schwab pairs; "
+                 "FP64 area scaling and accumulation of y)",
         "data": "synthetic",
         "config": {"workload": f"sphere_{n}_slp_m4_eta2_leaf32_nrhs{nrhs}", "n": n, "nrhs": nrhs, "m": 4,
                    "eta": 2.0, "leaf": 32, "tier": args.tier, "nearfield": "on the fly",

@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
             sd += rd;
         }
         if (KER == SLP) {
-            a01 = a10 = sc * (double)ssum / 6.0;
+            a01 = a10 = sc * (double)ssum * (1.0 / 6.0);
         } else {
             // V = (sa a + sb b + sd d) / 2; a is in both planes, b in lo's, d in hi's
             a01 = 0.5 * sc * (double)(sb * dot3(b, del));
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
             }
         }
         if (KER == SLP) {
-            a01 = a10 = sc * (double)ssum / 3.0;
+            a01 = a10 = sc * (double)ssum * (1.0 / 3.0);
         } else {
             // V = (sa a + sb b + sc c + sd d) / 2; a, b in lo's plane, c, d in hi's
             a01 = 0.5 * sc * (double)fmaf(sa, dot3(a, del), sb * dot3(b, del));
