@@ -383,6 +383,55 @@ def main():
                                                torch.linalg.norm(out_e["fp64"][1]))
         extra["ellipsoid131k_m5_16rhs"] = out
 
+    # Dirichlet-to-Neumann solve on the same sphere (section 1, eq. (matrix_dtn)):
+    # G x = (M/2 + K) b by the library's conjugate gradients, mixed tier, for the
+    # harmonic test functions u1 = x1^2 - x3^2, u2 = g(., (1.2, 1.2, 1.2)),
+    # u3 = g(., (1, 0.25, 1)); b = L2 projection onto the triangles
+    if not args.no_fp64:
+        v = mesh.vertices
+        ta, tb, tc = (v[mesh.triangles[:, q]] for q in range(3))
+        # edge-midpoint rule (exact for degree 2) for the projection and the error
+        ru = np.array([0.5, 0.5, 0.0])
+        rv = np.array([0.0, 0.5, 0.5])
+        rw = np.array([1 / 3, 1 / 3, 1 / 3])
+        pts = ta[:, None] + ru[None, :, None] * (tb - ta)[:, None] + rv[None, :, None] * (tc - ta)[:, None]
+        area = 0.5 * np.linalg.norm(np.cross(tb - ta, tc - ta), axis=1)
+        proj = pts / np.linalg.norm(pts, axis=-1, keepdims=True)
+
+        def u_dn(k, p_):
+            if k == 0:
+                return p_[..., 0] ** 2 - p_[..., 2] ** 2, 2 * p_[..., 0] ** 2 - 2 * p_[..., 2] ** 2
+            yv = np.array([1.2, 1.2, 1.2]) if k == 1 else np.array([1.0, 0.25, 1.0])
+            dd = p_ - yv
+            r = np.linalg.norm(dd, axis=-1)
+            return 1 / (4 * np.pi * r), -(dd * p_).sum(-1) / (4 * np.pi * r ** 3)
+
+        bvec = np.stack([(u_dn(k, pts)[0] * rw[None, :]).sum(1) for k in range(3)])
+        opG = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, precision="mixed_fp32", autotune=1)
+        opK = H.Operator(mesh.vertices, mesh.triangles, kernel="dlp", m=4, precision="mixed_fp32", autotune=1)
+        bd = torch.from_numpy(np.ascontiguousarray(bvec)).to(dev)
+        rhs_d = torch.empty_like(bd)
+        xd_ = torch.empty_like(bd)
+        H.h2bem_apply_mass(opK.op, 0.5, bd, rhs_d, stream)
+        H.h2bem_cg(opG.op, rhs_d, xd_, rtol=1e-3, maxit=5, stream=stream)  # warm-up (tuning)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        H.h2bem_apply_mass(opK.op, 0.5, bd, rhs_d, stream)
+        its, rel = H.h2bem_cg(opG.op, rhs_d, xd_, rtol=1e-6, maxit=2000, stream=stream)
+        torch.cuda.synchronize(dev)
+        t_solve = time.perf_counter() - t0
+        xs = xd_.cpu().numpy()
+        l2 = {}
+        for k, nm in enumerate(("u1", "u2", "u3")):
+            dn = u_dn(k, proj)[1]
+            l2[nm] = float(np.sqrt((area[:, None] * rw[None, :] * (xs[k][:, None] - dn) ** 2).sum() /
+                                   (area[:, None] * rw[None, :] * dn ** 2).sum()))
+        extra["dtn_cg_mixed"] = {"triangles": n, "rhs": 3, "iterations": its, "rtol": 1e-6, "relres": rel,
+                                 "solve_s": t_solve, "ms_per_iteration": 1e3 * t_solve / max(its, 1),
+                                 "neumann_l2_rel_err": l2}
+        opG.close()
+        opK.close()
+
     # roofline of the dominant kernel of the headline tier
     pk = peaks()
     names = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_backward", "near_regular",

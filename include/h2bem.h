@@ -227,6 +227,28 @@ int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, 
  * nrhs, ld, host pointers), CUDA, OOM. */
 int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz, double* dx,
                void* stream);
+/* y = A x + alpha M x with the P0 mass matrix M = diag(|tau_i|) (section 1,
+ * the mass matrix m_ij of eq. (matrix_dtn) with piecewise-constant columns).
+ * With A = K and alpha = 1/2 this is the right-hand side (M/2 + K) b of the
+ * Dirichlet-to-Neumann system G x = (M/2 + K) b.  x, y: device, n x nrhs,
+ * leading dimensions ldx, ldy >= n, caller's triangle order; asynchronous on
+ * `stream`.  Errors: as h2bem_apply; ARG for host pointers. */
+int h2bem_apply_mass(h2bem_op* op, double alpha, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                     void* stream);
+/* Conjugate gradients for G x = b (G the single layer, symmetric positive
+ * definite; section 1, eq. (matrix_dtn) for the Dirichlet-to-Neumann
+ * problem), every column an independent system: x0 = 0, stop when
+ * |b - G x| <= rtol |b| for every column or after maxit iterations.  G is
+ * applied in the operator's tier; the iteration runs in FP64.
+ *   b: device n x nrhs (ldb >= n); x: device n x nrhs output (ldx >= n);
+ *   iters (host, may be NULL): iterations done; relres (host, may be NULL,
+ *   nrhs values): final |r| / |b| per column (the recurrence residual).
+ * Synchronises `stream` in every iteration (the step lengths are host
+ * scalars).  Work vectors are allocated on the first call.
+ * Errors: ARG (NULL, double-layer operator, nrhs, ld, rtol <= 0, maxit < 0,
+ * host pointers), CUDA, OOM. */
+int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol, int maxit,
+             int* iters, double* relres, void* stream);
 /* As h2bem_apply with device buffers only, and records CUDA events around
  * each stage on `stream`; synchronises and fills the stats' stage_ms:
  * [0] permute in, [1] leaf forward, [2] upward, [3] coupling, [4] downward,

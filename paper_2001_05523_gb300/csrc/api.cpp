@@ -611,6 +611,9 @@ struct h2bem_op {
     } tuned[4][2];
     int64_t last_variant[5] = {0, 4, 4, 0, 0};
     DevBuf work;  // row counters of persistent launches (2 ints)
+    DevBuf area_user;              // |tau_i| in the caller's order (mass term), made on first use
+    DevBuf cg_r, cg_p, cg_q, cg_s; // conjugate-gradient vectors and scalars
+    int64_t cg_cap = 0;
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
     int64_t ws_gen = 0;
@@ -1537,6 +1540,94 @@ extern "C" int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx,
 extern "C" int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
                                  void* stream) {
     return apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, true);
+}
+
+// ===========================================================================
+// mass term and conjugate gradients (section 1, eq. (matrix_dtn))
+// ===========================================================================
+static int ensure_area_user(h2bem_op* op, cudaStream_t s) {
+    if (op->area_user.p) return H2BEM_OK;
+    int rc = op->area_user.alloc(op->n * sizeof(double));
+    if (rc) return rc;
+    h2::launch_area_user((int)op->n, op->perm.as<int>(), op->area.as<double>(), op->area_user.as<double>(), s);
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_apply_mass(h2bem_op* op, double alpha, const double* x, int64_t ldx, int nrhs, double* y,
+                                int64_t ldy, void* stream) {
+    if (!op || !x || !y) return fail(H2BEM_ERR_ARG, "apply_mass: NULL argument");
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(H2BEM_ERR_ARG, "apply_mass: x and y must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = apply_impl(op, x, ldx, nrhs, y, ldy, stream, false, false);
+    if (rc) return rc;
+    if ((rc = ensure_area_user(op, s))) return rc;
+    h2::launch_mass_add((int)op->n, nrhs, alpha, op->area_user.as<double>(), x, ldx, y, ldy, s);
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol,
+                        int maxit, int* iters, double* relres, void* stream) {
+    if (!op || !b || !x) return fail(H2BEM_ERR_ARG, "cg: NULL argument");
+    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "cg: needs the (symmetric positive definite) single layer");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "cg: nrhs must be in 1..64");
+    if (ldb < op->n || ldx < op->n) return fail(H2BEM_ERR_ARG, "cg: leading dimensions must be >= n");
+    if (!(rtol > 0.0) || maxit < 0) return fail(H2BEM_ERR_ARG, "cg: rtol must be > 0 and maxit >= 0");
+    if (!is_device_ptr(b) || !is_device_ptr(x)) return fail(H2BEM_ERR_ARG, "cg: b and x must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)op->n;
+    const int64_t need = (int64_t)n * nrhs;
+    int rc;
+    if (op->cg_cap < need) {
+        if ((rc = op->cg_r.alloc(need * sizeof(double))) || (rc = op->cg_p.alloc(need * sizeof(double))) ||
+            (rc = op->cg_q.alloc(need * sizeof(double))) || (rc = op->cg_s.alloc(6 * 64 * sizeof(double))))
+            return rc;
+        op->cg_cap = need;
+    }
+    double *r = op->cg_r.as<double>(), *p = op->cg_p.as<double>(), *q = op->cg_q.as<double>();
+    double* sc = op->cg_s.as<double>();  // [0..63] dots, [64..127] alpha, [128..191] beta
+    // x0 = 0, r = p = b
+    for (int c = 0; c < nrhs; ++c) CU(cudaMemsetAsync(x + c * ldx, 0, n * sizeof(double), s));
+    CU(cudaMemcpy2DAsync(r, n * sizeof(double), b, ldb * sizeof(double), n * sizeof(double), nrhs,
+                         cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(p, r, need * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    std::vector<double> bb(nrhs), rr(nrhs), pq(nrhs), al(nrhs), be(nrhs);
+    h2::launch_dots(n, nrhs, b, ldb, b, ldb, sc, s);
+    CU(cudaMemcpyAsync(bb.data(), sc, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    rr = bb;
+    std::vector<char> done(nrhs);
+    int it = 0;
+    auto converged = [&](int c) { return bb[c] == 0.0 || rr[c] <= rtol * rtol * bb[c]; };
+    for (int c = 0; c < nrhs; ++c) done[c] = converged(c);
+    while (it < maxit && std::find(done.begin(), done.end(), 0) != done.end()) {
+        if ((rc = apply_impl(op, p, n, nrhs, q, n, stream, false, false))) return rc;
+        h2::launch_dots(n, nrhs, p, n, q, n, sc, s);
+        CU(cudaMemcpyAsync(pq.data(), sc, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int c = 0; c < nrhs; ++c) al[c] = (done[c] || pq[c] <= 0.0) ? 0.0 : rr[c] / pq[c];
+        CU(cudaMemcpyAsync(sc + 64, al.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        h2::launch_cg_step(n, nrhs, sc + 64, p, n, q, n, x, ldx, r, n, s);
+        h2::launch_dots(n, nrhs, r, n, r, n, sc, s);
+        std::vector<double> rn(nrhs);
+        CU(cudaMemcpyAsync(rn.data(), sc, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ++it;
+        for (int c = 0; c < nrhs; ++c) {
+            be[c] = (done[c] || rr[c] == 0.0) ? 0.0 : rn[c] / rr[c];
+            if (!done[c]) rr[c] = rn[c];
+            done[c] = done[c] || converged(c);
+        }
+        CU(cudaMemcpyAsync(sc + 128, be.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        h2::launch_cg_dir(n, nrhs, sc + 128, r, n, p, n, s);
+        CU(cudaGetLastError());
+    }
+    CU(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres)
+        for (int c = 0; c < nrhs; ++c) relres[c] = bb[c] > 0.0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
+    return H2BEM_OK;
 }
 
 // ===========================================================================

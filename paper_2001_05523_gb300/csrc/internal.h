@@ -149,6 +149,19 @@ void launch_grad_box(int nc, const int* cext, const int* cflag, const double* db
 
 }  // namespace h2
 
+namespace h2 {
+// conjugate gradients and mass term (k_cg.cu); vectors column-major n x nrhs
+void launch_dots(int n, int nrhs, const double* a, int64_t lda, const double* b, int64_t ldb, double* out,
+                 cudaStream_t s);
+void launch_cg_step(int n, int nrhs, const double* alpha, const double* p, int64_t ldp, const double* q, int64_t ldq,
+                    double* x, int64_t ldx, double* res, int64_t ldr, cudaStream_t s);
+void launch_cg_dir(int n, int nrhs, const double* beta, const double* res, int64_t ldr, double* p, int64_t ldp,
+                   cudaStream_t s);
+void launch_mass_add(int n, int nrhs, double alpha, const double* area_user, const double* x, int64_t ldx, double* y,
+                     int64_t ldy, cudaStream_t s);
+void launch_area_user(int n, const int* perm, const double* area, double* out, cudaStream_t s);
+}  // namespace h2
+
 struct h2bem_op;
 namespace h2 {
 // Used by the allocation-free entry point (noalloc.cu).
