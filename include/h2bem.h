@@ -174,7 +174,7 @@ int h2bem_blocks(const h2bem_tree* tree, double eta, int64_t* nfar, int64_t* nne
 
 /* ---- operator -------------------------------------------------------------- */
 int h2bem_opts_default(h2bem_opts* opts);
-/* Selects G (H2BEM_SLP) or K (H2BEM_DLP), interpolation order m (1..8,
+/* Selects G (H2BEM_SLP) or K (H2BEM_DLP), interpolation order m (1..6,
  * k = m^3, section 3) and admissibility eta; builds the block lists and
  * uploads mesh, tree and lists to the current CUDA device.  opts may be NULL
  * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts), OOM, CUDA. */

@@ -12,9 +12,9 @@
 // thread issues tcgen05.mma with M = 64 rows of nu per tile, N = 8 or 16
 // right-hand sides and K = 8 (TF32) or 16 (BF16) values of mu per
 // instruction; the accumulator D (FP32) stays in tensor memory over all blocks
-// of the row, spread over up to 8 independent accumulators (consecutive MMAs
-// rotate over them, so none waits for the previous one) that the epilogue
-// sums in FP64.  Two stages of shared memory let the CTA generate block b+1
+// of the row (one accumulator per row tile: rotating consecutive MMAs over
+// several accumulators measured slower) and the epilogue adds it to y-hat in
+// FP64.  Two stages of shared memory let the CTA generate block b+1
 // while the tensor core consumes block b (an mbarrier per stage, signalled by
 // tcgen05.commit).  Accumulator layout for M = 64: row i of a tile is tensor
 // memory lane 32 (i / 16) + i % 16, so warp w reads rows 16w .. 16w+15.
