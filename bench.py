@@ -313,6 +313,26 @@ def main():
         extra["fp64_cached_singular"] = {"value": world * n * nrhs / (ms_dc / 1e3), "ms_per_step": ms_dc,
                                          "stage_ms": [round(v, 3) for v in stage_dc]}
         extra["speedup_mixed_vs_fp64_cached"] = ms_dc / ms_c
+        # stored nearfield: every nearfield entry evaluated once at set-up (FP32 in the mixed
+        # tier, FP64 in the FP64 tier) and streamed from HBM in every apply
+        pk_h = peaks()["hbm_gbs"]
+        stored = {}
+        for prec, st_steps in (("mixed_fp32", args.steps), ("fp64", max(1, min(args.steps, 3)))):
+            ops, y_s, ms_s, stage_s, st_s, setup_s = timed_tier(prec, False, st_steps, store_near=True)
+            ops.close()
+            es = 4 if prec == "mixed_fp32" else 8
+            # algorithmic bytes of the nearfield stage: every entry once, x in the stored
+            # precision, y written in FP64
+            alg = st_s["near_pairs"] * es + n * nrhs * (es + 8)
+            near_ms = float(stage_s[6])
+            stored[prec] = {"value": world * n * nrhs / (ms_s / 1e3), "ms_per_step": ms_s,
+                            "stage_ms": [round(v, 3) for v in stage_s], "setup_s": round(setup_s, 2),
+                            "near_stored_bytes": st_s["near_stored_bytes"],
+                            "near_stage_algorithmic_bytes": alg,
+                            "near_stage_gbs": alg / (near_ms / 1e3) / 1e9,
+                            "near_stage_frac_of_hbm_peak": alg / (near_ms / 1e3) / 1e9 / pk_h,
+                            "rel_err_vs_fp64": float(torch.linalg.norm(y_s - y_d) / torch.linalg.norm(y_d))}
+        extra["stored_nearfield"] = stored
 
     # tensor-core tiers of the coupling (tcgen05): same workload, error against the FP64 tier
     if not args.no_fp64:
@@ -412,8 +432,13 @@ def main():
             area = 0.5 * np.linalg.norm(np.cross(tb - ta, tc - ta), axis=1)
             proj = pts / np.linalg.norm(pts, axis=-1, keepdims=True)
             bvec = np.stack([(u_dn(k, pts)[0] * rw[None, :]).sum(1) for k in range(3)])
-            opG = H.Operator(v, md.triangles, kernel="slp", m=m_dtn, eta=eta_dtn, precision="mixed_fp32", autotune=1)
+            t_set = time.perf_counter()
+            # a solve applies G hundreds of times: nearfield entries stored once
+            opG = H.Operator(v, md.triangles, kernel="slp", m=m_dtn, eta=eta_dtn, precision="mixed_fp32", autotune=1,
+                             store_near=True)
             opK = H.Operator(v, md.triangles, kernel="dlp", m=m_dtn, eta=eta_dtn, precision="mixed_fp32", autotune=1)
+            torch.cuda.synchronize(dev)
+            t_set = time.perf_counter() - t_set
             bd = torch.from_numpy(np.ascontiguousarray(bvec)).to(dev)
             rhs_d = torch.empty_like(bd)
             xd_ = torch.empty_like(bd)
@@ -434,7 +459,8 @@ def main():
             opG.close()
             opK.close()
             return {"triangles": md.nt, "m": m_dtn, "eta": eta_dtn, "rhs": 3, "iterations": its, "rtol": rtol,
-                    "relres": rel, "solve_s": t_solve, "ms_per_iteration": 1e3 * t_solve / max(its, 1),
+                    "relres": rel, "setup_s": t_set, "solve_s": t_solve, "ms_per_iteration": 1e3 * t_solve / max(its, 1),
+                    "store_near": True,
                     "neumann_l2_rel_err": l2}
 
         coarse = dtn_case(128, 6, 1.0, 1e-8)

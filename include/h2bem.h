@@ -97,6 +97,13 @@ typedef struct {
     int recompute_basis; /* 1: no stored leaf bases; every apply re-evaluates the cluster-basis   */
                         /*    values by quadrature (saves n k values of device memory); 0         */
                         /*    (default): V (and W) evaluated once at set-up and stored             */
+    int store_near;     /* 1: evaluate every nearfield entry once at set-up (regular pairs and     */
+                        /*    Sauter-Schwab pairs, in the tier's working precision: FP32 in the    */
+                        /*    MIXED tiers, FP64 in H2BEM_FP64) and keep the nearfield blocks in    */
+                        /*    device memory (stats.near_stored_bytes, about near_pairs values);    */
+                        /*    every apply then streams them instead of evaluating the quadrature. */
+                        /*    The nearfield sum of each row is formed by one CTA without atomics. */
+                        /*    0 (default): nearfield on the fly in every apply                     */
     int reserved[1];    /* must be zero                                                            */
 } h2bem_opts;
 
@@ -124,6 +131,8 @@ typedef struct {
                                /* each): every pair of the blocks (t, s >= t)  */
                                /* sharing no vertex, both orders when s = t;   */
                                /* its result serves (t, s) and (s, t)          */
+    int64_t near_stored_bytes; /* device bytes of the stored nearfield blocks */
+                               /* (opts.store_near), else 0                    */
 } h2bem_stats;
 
 /* Message of the last failed call on the calling thread (empty if none).

@@ -614,6 +614,12 @@ struct h2bem_op {
     DevBuf area_user;              // |tau_i| in the caller's order (mass term), made on first use
     DevBuf cg_r, cg_p, cg_q, cg_s; // conjugate-gradient vectors and scalars
     int64_t cg_cap = 0;
+    // stored nearfield (store_near): the blocks of `near` and their offsets
+    // (boff: block (t, s); boff_t: block (s, t) of the same list entry)
+    int store_near = 0;
+    DevBuf nst, nrow, nblk, nblk_t, xs;  // values, NearRow per row, NearBlock per block (and for A^T)
+    int64_t nst_bytes = 0;
+    int stage_order = 0;  // 1: the last apply ran the stored nearfield first
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
     int64_t ws_gen = 0;
@@ -725,6 +731,115 @@ void singular_pairs(const h2bem_mesh& M, std::vector<int64_t> lo[3], std::vector
 
 }  // namespace
 
+// Stored nearfield (opts.store_near): offsets of the ordered blocks (t, s)
+// of `near` (|s| columns of |t| | 1 values, each block on a 16-byte
+// boundary), the regular entries written by the storing variant of the
+// nearfield kernel, then the Sauter-Schwab entries of the canonical pairs
+// scattered to (lo, hi) and (hi, lo).
+static int build_near_store(h2bem_op* op, const h2bem_tree& tree, const std::vector<int>& iperm,
+                            const std::vector<int64_t> (&slo)[3], const std::vector<int64_t> (&shi)[3]) {
+    const bool f32 = op->precision != H2BEM_FP64;
+    const int es = f32 ? (int)sizeof(float) : (int)sizeof(double), vec = 16 / es;
+    const Csr& N = op->near;
+    const int64_t nc = op->nc;
+    auto size_of = [&](int64_t c) { return (int)(tree.end[c] - tree.begin[c]); };
+    std::vector<int> rowpos(nc, -1);
+    for (int r = 0; r < N.nrows(); ++r) rowpos[N.rows[r]] = r;
+    // index of block (t, s) in the ordered list (columns of a row are sorted)
+    auto find = [&](int t, int s) -> int64_t {
+        const int r = rowpos[t];
+        if (r < 0) return -1;
+        const auto b = std::lower_bound(N.col.begin() + N.ptr[r], N.col.begin() + N.ptr[r + 1], s);
+        if (b == N.col.begin() + N.ptr[r + 1] || *b != s) return -1;
+        return b - N.col.begin();
+    };
+    std::vector<int64_t> boff(N.col.size()), boff_t(N.col.size());
+    int64_t tot = 0;
+    for (int r = 0; r < N.nrows(); ++r) {
+        const int ld = size_of(N.rows[r]) | 1;
+        for (int b = N.ptr[r]; b < N.ptr[r + 1]; ++b) {
+            boff[b] = tot;
+            tot += ((int64_t)size_of(N.col[b]) * ld + vec - 1) / vec * vec;
+        }
+    }
+    for (int r = 0; r < N.nrows(); ++r)
+        for (int b = N.ptr[r]; b < N.ptr[r + 1]; ++b) {
+            const int64_t bt = find(N.col[b], N.rows[r]);
+            if (bt < 0) return fail(H2BEM_ERR_ARG, "operator_create: nearfield block list is not symmetric");
+            boff_t[b] = boff[bt];
+        }
+    const Csr& U = op->near_u;
+    std::vector<int64_t> ots(U.col.size()), ost(U.col.size());
+    for (int r = 0; r < U.nrows(); ++r)
+        for (int b = U.ptr[r]; b < U.ptr[r + 1]; ++b) {
+            const int64_t b1 = find(U.rows[r], U.col[b]), b2 = find(U.col[b], U.rows[r]);
+            if (b1 < 0 || b2 < 0) return fail(H2BEM_ERR_ARG, "operator_create: nearfield block list is not symmetric");
+            ots[b] = boff[b1];
+            ost[b] = boff[b2];
+        }
+    std::vector<int> leaf_of(op->n, -1);
+    for (int l : op->leaves_h)
+        for (int64_t p = tree.begin[l]; p < tree.end[l]; ++p) leaf_of[p] = l;
+    int rc;
+    op->nst_bytes = tot * es;
+    std::vector<h2::NearRow> nrow(N.nrows());
+    std::vector<h2::NearBlock> nblk(N.col.size()), nblk_t(N.col.size());
+    for (int r = 0; r < N.nrows(); ++r) {
+        nrow[r] = h2::NearRow{(int)tree.begin[N.rows[r]], size_of(N.rows[r]), N.ptr[r], N.ptr[r + 1]};
+        for (int b = N.ptr[r]; b < N.ptr[r + 1]; ++b) {
+            nblk[b] = h2::NearBlock{(long long)boff[b], (int)tree.begin[N.col[b]], size_of(N.col[b])};
+            nblk_t[b] = h2::NearBlock{(long long)boff_t[b], (int)tree.begin[N.col[b]], size_of(N.col[b])};
+        }
+    }
+    if ((rc = op->nst.alloc((size_t)op->nst_bytes)) || (rc = upload(op->nrow, nrow)) || (rc = upload(op->nblk, nblk)) ||
+        (rc = upload(op->nblk_t, nblk_t)))
+        return rc;
+    CU(cudaMemset(op->nst.p, 0, (size_t)op->nst_bytes));
+    {
+        DevBuf dts, dst;
+        if ((rc = upload(dts, ots)) || (rc = upload(dst, ost))) return rc;
+        h2::NearStore ns;
+        ns.N = op->nst.p;
+        ns.off_ts = dts.as<int64_t>();
+        ns.off_st = dst.as<int64_t>();
+        h2::launch_near_sym_store(op->geom(), op->tree(), op->consts, U.nrows(), U.drows.as<int>(), U.dptr.as<int>(),
+                                  U.dcol.as<int>(), op->kernel == H2BEM_DLP ? h2::DLP : h2::SLP, f32, ns, 0);
+        CU(cudaGetLastError());
+        CU(cudaDeviceSynchronize());
+    }
+    for (int ty = 0; ty < 3; ++ty) {
+        if (ty == 0 && op->kernel == H2BEM_DLP) continue;  // k_ii = 0, written by the regular pass
+        const int np = (int)op->sp_count[ty];
+        if (np == 0) continue;
+        std::vector<int64_t> p0(np), p1(np);
+        for (int p = 0; p < np; ++p) {
+            const int lo = iperm[slo[ty][p]], hi = iperm[shi[ty][p]];
+            const int lt = leaf_of[lo], ls = leaf_of[hi];
+            const int il = lo - (int)tree.begin[lt], jl = hi - (int)tree.begin[ls];
+            const int64_t b1 = find(lt, ls), b2 = find(ls, lt);
+            if (b1 < 0 || b2 < 0) return fail(H2BEM_ERR_ARG, "operator_create: a singular pair outside the nearfield");
+            p0[p] = boff[b1] + (int64_t)jl * (size_of(lt) | 1) + il;
+            p1[p] = boff[b2] + (int64_t)il * (size_of(ls) | 1) + jl;
+        }
+        DevBuf dp0, dp1, v0, v1;
+        if ((rc = upload(dp0, p0)) || (rc = upload(dp1, p1))) return rc;
+        const double *pv0 = op->sp_v0[ty].as<double>(), *pv1 = op->sp_v1[ty].as<double>();
+        if (!op->cache_singular) {
+            if ((rc = v0.alloc(np * sizeof(double))) || (rc = v1.alloc(np * sizeof(double)))) return rc;
+            h2::launch_singular(op->geom(), h2::IDENTICAL - ty, op->kernel, np, op->sp_lo[ty].as<int>(),
+                                op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(),
+                                op->sp_npts[ty], 1, f32 && !op->singular_fp64, false, 1, nullptr, nullptr,
+                                v0.as<double>(), v1.as<double>(), 0);
+            pv0 = v0.as<double>();
+            pv1 = v1.as<double>();
+        }
+        h2::launch_sing_scatter(f32, np, dp0.as<int64_t>(), dp1.as<int64_t>(), pv0, pv1, op->nst.p, 0);
+        CU(cudaGetLastError());
+        CU(cudaDeviceSynchronize());
+    }
+    return H2BEM_OK;
+}
+
 static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blocks* prebuilt, int kernel, int m,
                        double eta, const h2bem_opts* opts_in, h2bem_op** out) {
     if (!out) return fail(H2BEM_ERR_ARG, "operator_create: out is NULL");
@@ -768,6 +883,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->autotune = opts.autotune == 1 ? 1 : 0;
     op->singular_fp64 = opts.singular_fp64 ? 1 : 0;
     op->recompute_basis = opts.recompute_basis ? 1 : 0;
+    op->store_near = opts.store_near ? 1 : 0;
     if (opts.autotune >= 2) {  // a fixed launch variant for every width and direction
         const int v = opts.autotune - 2;
         for (auto& slot : op->tuned)
@@ -1066,6 +1182,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             CU(cudaGetLastError());
         }
     }
+    if (op->store_near && (rc = build_near_store(op.get(), *tree, iperm, slo, shi))) return rc;
     CU(cudaDeviceSynchronize());
     for (auto& e : op->ev) CU(cudaEventCreate(&e));
     *out = op.release();
@@ -1156,6 +1273,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->singular_pairs[2] = op->sing[2];
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
     st->regular_evals = op->regular_evals;
+    st->near_stored_bytes = op->nst_bytes;
     for (int i = 0; i < 5; ++i) st->launch_variant[i] = op->last_variant[i];
     st->k = op->k;
     st->launches = op->launches;
@@ -1182,6 +1300,33 @@ static bool yh_is64(const h2bem_op* op, bool tr) {
     return op->precision == H2BEM_FP64 || (op->kernel == H2BEM_DLP && tr);
 }
 
+// x in the stored nearfield's precision (FP32 tiers, or a single FP64 column
+// padded to 16 bytes); 0 where the stored apply reads x directly
+static size_t store_x_bytes(const h2bem_op* op, int NR) {
+    if (!op->store_near) return 0;
+    const bool f32 = op->precision != H2BEM_FP64;
+    if (!f32 && NR > 1) return 0;
+    return (size_t)op->n * h2::near_store_nx(f32, NR) * (f32 ? sizeof(float) : sizeof(double));
+}
+
+// Nearfield of an apply from the stored blocks (x converted first where
+// needed): writes every row of yp; returns the number of launches.
+static int64_t near_stored_apply(const h2bem_op* op, int NR, bool transpose, const double* xp, double* yp, void* xs,
+                                 cudaStream_t s) {
+    const bool f32 = op->precision != H2BEM_FP64;
+    const bool tr = transpose && op->kernel == H2BEM_DLP;  // the stored single layer is symmetric
+    int64_t nl = 0;
+    const void* xsrc = xp;
+    if (store_x_bytes(op, NR)) {
+        h2::launch_store_x(f32, (int)op->n, NR, xp, xs, s);
+        xsrc = xs;
+        ++nl;
+    }
+    h2::launch_near_stored(f32, tr, NR, op->near.nrows(), op->nrow.as<h2::NearRow>(),
+                           (tr ? op->nblk_t : op->nblk).as<h2::NearBlock>(), op->nst.p, xsrc, op->max_leaf, yp, s);
+    return nl + (op->near.nrows() > 0 ? 1 : 0);
+}
+
 static int ensure_workspace(h2bem_op* op, int NR) {
     if (op->ws_NR >= NR) return H2BEM_OK;
     const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;  // either direction
@@ -1189,7 +1334,8 @@ static int ensure_workspace(h2bem_op* op, int NR) {
     const size_t ysz = xsz;
     int rc;
     if ((rc = op->xp.alloc(op->n * NR * sizeof(double))) || (rc = op->yp.alloc(op->n * NR * sizeof(double))) ||
-        (rc = op->xh.alloc((size_t)op->nc * op->k * NR * xsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * ysz)))
+        (rc = op->xh.alloc((size_t)op->nc * op->k * NR * xsz)) || (rc = op->yh.alloc((size_t)op->nc * op->k * NR * ysz)) ||
+        (rc = op->xs.alloc(store_x_bytes(op, NR))))
         return rc;
     op->ws_NR = NR;
     op->ws_gen++;
@@ -1298,8 +1444,9 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     };
     mark(0);
     h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
-    CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
-    if (tune_now && op->near_u.nrows() > 0) {
+    // the stored nearfield writes every row of y first; otherwise the stages add to zero
+    if (!op->store_near) CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    if (tune_now && op->near_u.nrows() > 0 && !op->store_near) {
         float best = 1e30f;
         const bool budgets = fp32 && !dlp;  // register-budget variants exist for the FP32 single layer
         for (int nb : {0, 3, 2}) {
@@ -1323,6 +1470,13 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     nl += 1;
     mark(1);
+    // stored nearfield first (stage times are then mapped by the order of the events)
+    const int fo = op->store_near ? 1 : 0;
+    op->stage_order = fo;
+    if (op->store_near) {
+        nl += near_stored_apply(op, NR, transpose, op->xp.as<double>(), op->yp.as<double>(), op->xs.p, s);
+        mark(2);
+    }
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
         // the double layer's differentiated basis is evaluated in FP64 in every tier
@@ -1334,10 +1488,10 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                                            fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
                                            op->xp.as<double>(), op->xh.p, s);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
-        mark(2);
+        mark(2 + fo);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
             h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p, s);
-        mark(3);
+        mark(3 + fo);
         if (tune_now && tu.coup.nsl == -1) {
             float best = 1e30f;
             for (int nsl : {2, 4, 8})
@@ -1360,10 +1514,10 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
         run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
-        mark(4);
+        mark(4 + fo);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
             h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
-        mark(5);
+        mark(5 + fo);
         if (op->recompute_basis)
             h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
                                      out_dlp, fp32 && !out_dlp, yh64, NR, op->yh.p, op->yp.as<double>(), s);
@@ -1372,11 +1526,21 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                                             fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p,
                                             op->yh.p, op->yp.as<double>(), s);
     } else {
-        for (int i = 2; i <= 5; ++i) mark(i);
+        for (int i = 2 + fo; i <= 5 + fo; ++i) mark(i);
+    }
+    if (tune_now) tu.done = true;  // operators without farfield
+    if (op->store_near) {
+        mark(7);
+        mark(8);
+        h2::launch_permute_out(op->yp.as<double>(), NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+        nl += 1;
+        op->launches += nl;
+        mark(9);
+        CU(cudaGetLastError());
+        return H2BEM_OK;
     }
     mark(6);
     // nearfield, regular pairs: each unordered pair of leaves once, both directions
-    if (tune_now) tu.done = true;  // operators without farfield
     {
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
@@ -1517,9 +1681,11 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
         float ms = 0.f;
         cudaEventElapsedTime(&ms, op->ev[0], op->ev[9]);
         op->last_ms = ms;
-        const int map[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}};
+        // events in launch order; the stored nearfield runs right after permute_in
+        const int map[2][8][2] = {{{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}},
+                                  {{0, 1}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {1, 2}, {7, 8}}};
         for (int i = 0; i < 8; ++i) {
-            cudaEventElapsedTime(&ms, op->ev[map[i][0]], op->ev[map[i][1]]);
+            cudaEventElapsedTime(&ms, op->ev[map[op->stage_order][i][0]], op->ev[map[op->stage_order][i][1]]);
             op->stage_ms[i] = ms;
         }
         if (h2::coupling_tc_status(true))
@@ -1728,7 +1894,8 @@ size_t work_bytes(const h2bem_op* op, int NR) {
     const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;
     const size_t e = wide ? sizeof(double) : sizeof(float);
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    return 2 * up((size_t)op->n * NR * sizeof(double)) + 2 * up((size_t)op->nc * op->k * NR * e);
+    return 2 * up((size_t)op->n * NR * sizeof(double)) + 2 * up((size_t)op->nc * op->k * NR * e) +
+           up(store_x_bytes(op, NR));
 }
 
 int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
@@ -1742,6 +1909,7 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
     double* yp = reinterpret_cast<double*>(work + vb);
     void* xh = work + 2 * vb;
     void* yh = work + 2 * vb + hb;
+    void* xs = work + 2 * vb + 2 * hb;
     const bool fp32 = op->precision != H2BEM_FP64;
     const bool xh64 = xh_is64(op, false), yh64 = yh_is64(op, false);
     const h2::Geom g = op->geom();
@@ -1751,7 +1919,8 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
     const bool dlp = op->kernel == H2BEM_DLP;
     const int near_ker = dlp ? h2::DLP : h2::SLP;
     launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, xp, s);
-    CU(cudaMemsetAsync(yp, 0, vb, s));
+    if (op->store_near) near_stored_apply(op, NR, false, xp, yp, xs, s);  // writes every row of yp
+    else CU(cudaMemsetAsync(yp, 0, vb, s));
     if (op->nfar > 0) {
         CU(cudaMemsetAsync(yh, 0, hb, s));
         if (op->recompute_basis)
@@ -1773,6 +1942,11 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         else
             launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
                                         yh64, NR, op->basisV.p, yh, yp, s);
+    }
+    if (op->store_near) {
+        launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+        CU(cudaGetLastError());
+        return H2BEM_OK;
     }
     {
         h2::LaunchCfg cfg_near, cfg_coup;

@@ -85,6 +85,38 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
                      const LaunchCfg& cfg, cudaStream_t s);
+// Stored nearfield (k_nearstore.cu).  Block (t, s) of the ordered list at
+// element offset off[b], column by column with leading dimension |t| | 1
+// (FP32 if f32, else FP64).  NearStore: destination of the storing variant of
+// the regular kernel (entries a / (4 pi); off_ts / off_st: offsets of (t, s)
+// and (s, t) for block b of the unordered list).
+struct NearStore {
+    void* N = nullptr;
+    const int64_t* off_ts = nullptr;
+    const int64_t* off_st = nullptr;
+};
+void launch_near_sym_store(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                           const int* col, int ker, bool fp32, const NearStore& ns, cudaStream_t s);
+// x in the stored precision, rows of near_store_nx(f32, NR) values
+int near_store_nx(bool f32, int NR);
+void launch_store_x(bool f32, int n, int NR, const double* xp, void* xs, cudaStream_t s);
+// One row leaf t of the ordered list: positions [rb, rb + R), blocks [b0, b1).
+struct alignas(16) NearRow {
+    int rb, R, b0, b1;
+};
+// One block (t, s): element offset of its stored values (of block (s, t) for
+// the transposed apply), first position and size of s.
+struct alignas(16) NearBlock {
+    long long off;
+    int cb, C;
+};
+// y|_t = sum N_ts x|_s over the ordered list (transpose: block (s, t) read
+// transposed); writes every row of y (the farfield adds afterwards)
+int near_stored_warps(bool f32, int max_leaf, int NR);
+void launch_near_stored(bool f32, bool transpose, int NR, int nrows, const NearRow* rows, const NearBlock* blocks,
+                        const void* nst, const void* xs, int max_leaf, double* yp, cudaStream_t s);
+void launch_sing_scatter(bool f32, int np, const int64_t* pos0, const int64_t* pos1, const double* v0,
+                         const double* v1, void* nst, cudaStream_t s);
 
 // nearfield, singular pairs of one type (canonical orientation, see api.cpp)
 //   mode 0: evaluate and scatter into yp;  mode 1: evaluate and store the

@@ -84,7 +84,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // Byte offsets into the dynamic shared memory of one CTA.
-template <typename T, int NR, bool DLPK>
+template <typename T, int NR, bool DLPK, bool STORE = false>
 struct Smem {
     static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
     static constexpr bool F32 = std::is_same<T, float>::value;
@@ -98,20 +98,26 @@ struct Smem {
     static constexpr size_t XR = al(XC + sizeof(T) * kCol * NR);     // T [kMaxLeaf][NR] x of the row leaf
     // double layer: F32 float [12][kCol] (n hi, n lo, F1, F2); F64 double [4][kCol] (n, plane offset)
     static constexpr size_t NRM = al(XR + sizeof(T) * kMaxLeaf * NR);
-    static constexpr size_t END = al(NRM + (DLPK ? (F32 ? 4 * 12 * kCol : 8 * 4 * kCol) : 0));
+    static constexpr size_t SB = al(NRM + (DLPK ? (F32 ? 4 * 12 * kCol : 8 * 4 * kCol) : 0));
+    static constexpr size_t END = al(SB + (STORE ? 4 * kCol : 0));  // int [kCol] block of each column (storing)
     static constexpr size_t RED = sizeof(double) * kThreads * NR;  // final row reduction (reuses the front)
     static constexpr size_t BYTES = END > RED ? END : RED;
 };
 }  // namespace
 
-// the work of one row leaf (index bi of the row list)
-template <int NR, bool DLPK, bool F32>
+// the work of one row leaf (index bi of the row list).  STORE: instead of
+// applying the entries, write a_ij / (4 pi) of block (t, s) at
+// ns.off_ts[b] + j' (|t| | 1) + i' and a_ji / (4 pi) of block (s, t) at
+// ns.off_st[b] + i' (|s| | 1) + j' (i', j' positions within the leaves; the
+// stored layout of the apply in k_nearstore.cu); pairs sharing a vertex get 0.
+template <int NR, bool DLPK, bool F32, bool STORE = false>
 __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const Consts& c,
                                              const int* __restrict__ rows, const int* __restrict__ ptr,
                                              const int* __restrict__ col, bool transpose,
-                                             const double* __restrict__ xp, double* __restrict__ yp, int bi) {
+                                             const double* __restrict__ xp, double* __restrict__ yp, int bi,
+                                             const NearStore& ns = NearStore{}) {
     using T = typename std::conditional<F32, float, double>::type;
-    using L = Smem<T, NR, DLPK>;
+    using L = Smem<T, NR, DLPK, STORE>;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sA = reinterpret_cast<T*>(smem + L::A);
     T* sq = reinterpret_cast<T*>(smem + L::Q);
@@ -123,6 +129,7 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
     T* sxr = reinterpret_cast<T*>(smem + L::XR);
     float* snf = reinterpret_cast<float*>(smem + L::NRM);
     double* snd = reinterpret_cast<double*>(smem + L::NRM);
+    int* sblk = reinterpret_cast<int*>(smem + L::SB);
 
     const int row = rows[bi];
     const int rb = t.begin[row], R = t.end[row] - rb;
@@ -138,7 +145,8 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
     const float* ru = c.ruf;
     const float* rv = c.rvf;
 
-    for (int e = tid; e < R * NR; e += kThreads) sxr[e] = (T)xp[(int64_t)rb * NR + e];
+    if (!STORE)
+        for (int e = tid; e < R * NR; e += kThreads) sxr[e] = (T)xp[(int64_t)rb * NR + e];
 
     // row triangle i = rb + il
     T px[7], py[7], pz[7];
@@ -212,7 +220,10 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
         for (int bl = b, off = 0; bl < b2; ++bl) {
             const int s = col[bl];
             const int cb = t.begin[s], C = t.end[s] - cb;
-            for (int e = tid; e < C; e += kThreads) sgid[off + e] = cb + e;
+            for (int e = tid; e < C; e += kThreads) {
+                sgid[off + e] = cb + e;
+                if (STORE) sblk[off + e] = bl;
+            }
             off += C;
         }
         __syncthreads();
@@ -244,7 +255,8 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
                 }
             }
         }
-        for (int e = tid; e < ctot * NR; e += kThreads) sxc[e] = (T)xp[(int64_t)sgid[e / NR] * NR + e % NR];
+        if (!STORE)
+            for (int e = tid; e < ctot * NR; e += kThreads) sxc[e] = (T)xp[(int64_t)sgid[e / NR] * NR + e % NR];
         __syncthreads();
 
         // phase 1: entries (row side into registers, column side into sA)
@@ -399,12 +411,26 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
                         acol = aa * (transpose ? S1 : S2);
                     }
                 }
+                if constexpr (STORE) {
+                    T* nout = reinterpret_cast<T*>(ns.N);
+                    const int bl = sblk[jc];
+                    const int s = col[bl];
+                    const int jl = sgid[jc] - t.begin[s];
+                    nout[ns.off_ts[bl] + (int64_t)jl * (R | 1) + il] = arow * (T)kInv4Pi;
+                    if (jc >= cdiag)  // the diagonal block is written whole on the row side
+                        nout[ns.off_st[bl] + (int64_t)il * ((t.end[s] - t.begin[s]) | 1) + jl] = acol * (T)kInv4Pi;
+                } else {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] += arow * sxc[jc * NR + r];
-                sA[il * cmax + jc] = acol;
+                    for (int r = 0; r < NR; ++r) acc[r] += arow * sxc[jc * NR + r];
+                    sA[il * cmax + jc] = acol;
+                }
             }
         }
         __syncthreads();
+        if (STORE) {
+            b = b2;
+            continue;
+        }
 
         // phase 2: column side of the off-diagonal leaves, y_j += sum_i a_ji x_i
         for (int e = tid; e < (ctot - cdiag) * NR; e += kThreads) {
@@ -415,6 +441,7 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
         }
         b = b2;
     }
+    if (STORE) return;
     __syncthreads();
     // row side: reduce the K partial sums of each row (in the working precision)
     T* sred = reinterpret_cast<T*>(smem);
@@ -450,6 +477,31 @@ __global__ void __launch_bounds__(kThreads, NB > 0 ? NB : ((F32 && !DLPK) ? 4 : 
         const int bi = s_bi;
         if (bi >= nrows) break;
         near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, bi);
+    }
+}
+
+// Storing variant: one CTA per row of the unordered list, writes the entries.
+template <bool DLPK, bool F32>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_near_sym_store(Geom g, Tree t, Consts c, const int* __restrict__ rows, const int* __restrict__ ptr,
+                     const int* __restrict__ col, NearStore ns) {
+    near_sym_row<1, DLPK, F32, true>(g, t, c, rows, ptr, col, false, nullptr, nullptr, blockIdx.x, ns);
+}
+
+void launch_near_sym_store(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                           const int* col, int ker, bool fp32, const NearStore& ns, cudaStream_t s) {
+    if (nrows <= 0) return;
+    auto go = [&](auto kern, size_t smem) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<nrows, kThreads, smem, s>>>(g, t, c, rows, ptr, col, ns);
+    };
+    const bool dlp = ker != SLP;
+    if (fp32) {
+        if (dlp) go(k_near_sym_store<true, true>, Smem<float, 1, true, true>::BYTES);
+        else go(k_near_sym_store<false, true>, Smem<float, 1, false, true>::BYTES);
+    } else {
+        if (dlp) go(k_near_sym_store<true, false>, Smem<double, 1, true, true>::BYTES);
+        else go(k_near_sym_store<false, false>, Smem<double, 1, false, true>::BYTES);
     }
 }
 

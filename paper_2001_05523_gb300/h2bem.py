@@ -41,7 +41,8 @@ class H2bemError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("store_near", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -51,7 +52,7 @@ class Stats(ctypes.Structure):
                 ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("last_apply_ms", ctypes.c_double),
                 ("stage_ms", ctypes.c_double * 8), ("launch_variant", ctypes.c_int64 * 5),
-                ("regular_evals", ctypes.c_int64)]
+                ("regular_evals", ctypes.c_int64), ("near_stored_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -288,7 +289,7 @@ class BatchOperator:
     def __init__(self, meshes, kernel: str | int = "slp", m: int = 4, eta: float = 2.0, leaf_size: int = 32,
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
-                 recompute_basis: bool = False):
+                 recompute_basis: bool = False, store_near: bool = False):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -302,6 +303,7 @@ class BatchOperator:
         o.autotune = int(autotune)
         o.singular_fp64 = int(singular_fp64)
         o.recompute_basis = int(recompute_basis)
+        o.store_near = int(store_near)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
     def close(self):
@@ -335,7 +337,7 @@ class Operator:
     def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
-                 recompute_basis: bool = False):
+                 recompute_basis: bool = False, store_near: bool = False):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -348,6 +350,7 @@ class Operator:
         o.autotune = int(autotune)
         o.singular_fp64 = int(singular_fp64)
         o.recompute_basis = int(recompute_basis)
+        o.store_near = int(store_near)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):
