@@ -324,8 +324,12 @@ void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows,
         // input side in double (double layer, K x): the differentiated basis makes
         // S x-hat cancel strongly, so S and its sums are FP64; y-hat is stored float
         H2_NR_SWITCH(NR, (coupling_simt<double, double, double, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
-    } else if (yh64) {  // output side in double (double layer, K^T x): FP32 entries, FP64 sums
-        H2_NR_SWITCH(NR, (coupling_simt<float, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
+    } else if (yh64) {
+        // output side in double (double layer, K^T x): W_t y-hat_t is the normal
+        // derivative of a potential that varies along the surface, so on flat
+        // faces it cancels to a small fraction of its terms and amplifies the
+        // ~1e-7 error of FP32 entries; S and its sums are FP64 as for K x
+        H2_NR_SWITCH(NR, (coupling_simt<double, double, float, double, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     } else {
         H2_NR_SWITCH(NR, (coupling_simt<float, float, float, float, R_>(t, c, nrows, rows, ptr, col, xh, yh, cfg, s)))
     }

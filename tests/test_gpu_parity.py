@@ -185,6 +185,16 @@ def test_sphere32k_fp64_vs_oracle_h2_and_dense_rows(H, orc, kernel):
     assert rel(y[:, rows], d) < (1e-3 if kernel == 0 else 1e-2)
 
 
+def test_mixed_fp32_dlp_transpose_on_flat_faces(H, orc):
+    """K^T on the jittered cube: W_t y-hat_t is a normal derivative that nearly
+    cancels on flat faces (FP32 coupling entries gave 1.3e-6 here)."""
+    mesh = I.jitter(I.cube(9), 0.01, 3)
+    x = I.rhs(mesh.nt, 2, seed=9)
+    y = gpu_apply(H, mesh, x, kernel=1, precision="mixed_fp32", transpose=True)
+    ref = orc.H2(mesh, 1, m=4).matvec(x, transpose=True)
+    assert rel(y, ref) < TOL["mixed_fp32"]
+
+
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_mixed_fp32_transpose_matches_oracle(H, orc, kernel):
     mesh = I.jitter(I.ellipsoid(12), 0.01, 6)

@@ -93,9 +93,9 @@ def test_stored_transpose(H, orc, kernel, precision):
 @pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_stored_equals_on_the_fly_on_cube(H, orc, kernel, transpose):
-    """Jittered cube, both directions: FP64 against the oracle; the mixed tier's
-    stored nearfield against its on-the-fly one (the two differ by the FP32
-    rounding of the stored entries and the order of the sums)."""
+    """Jittered cube, both directions: both tiers against the oracle, and the
+    mixed tier's stored nearfield against its on-the-fly one (the two differ
+    by the FP32 rounding of the stored entries and the order of the sums)."""
     mesh = I.jitter(I.cube(9), 0.01, 3)
     x = I.rhs(mesh.nt, 2, seed=9)
     y, _ = stored_apply(H, mesh, x, kernel=kernel, transpose=transpose)
@@ -105,6 +105,7 @@ def test_stored_equals_on_the_fly_on_cube(H, orc, kernel, transpose):
     yf = apply_np(a, x, transpose)
     a.close()
     assert rel(ys, yf) < 3e-7
+    assert rel(ys, orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)) < TOL["mixed_fp32"]
 
 
 @pytest.mark.parametrize("nrhs", [1, 4, 5, 8, 16, 21])
