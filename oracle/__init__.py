@@ -5,9 +5,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``paper_2001_05523_gb300`` never does: it has no CPU fallback.
 
 The arithmetic lives in ``h2oracle.c`` (plain C, FP64, OpenMP over rows);
-this module only compiles it with gcc and marshals numpy arrays through
-ctypes.  The specification each function follows is written out in
-``h2oracle.h``.
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+The specification each function follows is written out in ``h2oracle.h``.
+The hypersingular operator at the end of this module is plain numpy on top
+of those functions (its curls and the sum over the three components).
 """
 from __future__ import annotations
 
@@ -320,3 +321,63 @@ class H2:
         y = np.zeros((x.shape[0], rows.size))
         lib().or_h2_rows(self.h, _p(rows), rows.size, _p(x), x.shape[0], _p(y))
         return y
+
+
+# ---------------------------------------------------------------------------
+# Hypersingular operator W on continuous piecewise-linear functions (section 1,
+# eq. (slp) ff.: w_ij = -int phi_i d/dn_x int dg/dn_y phi_j).  Section 1 sets
+# it up through its representation by the single-layer operator (the
+# integration-by-parts identity it cites from Sauter and Schwab): for the
+# Laplace kernel on a closed surface
+#     w_ij = int int g(x, y) curl phi_i(x) . curl phi_j(y) dy dx,
+# with the surface curl curl phi = n x grad phi.  A hat function is linear on
+# each triangle, so its curl is a constant vector there, and
+#     W = sum_{d=1..3} C_d^T G C_d,   (C_d)_{tau j} = (curl phi_j |_tau)_d,
+# G the piecewise-constant single-layer matrix of eq. (slp).  Plain numpy;
+# the Galerkin matrix G (or its H^2 product) comes from the functions above.
+# ---------------------------------------------------------------------------
+def curl_p1(mesh):
+    """Surface curls of the hat functions, constant per triangle.
+
+    For tau = (a, b, c) with n = (b - a) x (c - a) / (2 |tau|):
+        grad phi_a = n x (c - b) / (2 |tau|),  curl phi_a = n x grad phi_a = (b - c) / (2 |tau|),
+    and cyclically curl phi_b = (c - a) / (2 |tau|), curl phi_c = (a - b) / (2 |tau|).
+    Returns (rows, cols, vals): vals[d] are the entries of C_d at (tau, j)."""
+    v = np.asarray(mesh.vertices, float)
+    t = np.asarray(mesh.triangles, np.int64)
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    two_area = np.linalg.norm(np.cross(b - a, c - a), axis=1)[:, None]
+    curls = [(b - c) / two_area, (c - a) / two_area, (a - b) / two_area]  # corner k of each triangle
+    rows = np.repeat(np.arange(len(t)), 3)
+    cols = t.reshape(-1)
+    vals = np.stack([np.stack([curls[k][:, d] for k in range(3)], axis=1).reshape(-1) for d in range(3)])
+    return rows, cols, vals
+
+
+def curl_matrices(mesh):
+    """C_d as scipy.sparse matrices (nt x nv), d = 0, 1, 2."""
+    import scipy.sparse as sp
+
+    rows, cols, vals = curl_p1(mesh)
+    shape = (mesh.nt, mesh.vertices.shape[0])
+    return [sp.csr_matrix((vals[d], (rows, cols)), shape=shape) for d in range(3)]
+
+
+def hypersingular_matvec(mesh, x: np.ndarray, slp_matvec=None, q_ss: int = 5) -> np.ndarray:
+    """W x = sum_d C_d^T G (C_d x); x: (nrhs, nv) -> (nrhs, nv).  slp_matvec
+    applies G to (k, nt) arrays (default: the dense Galerkin product)."""
+    x = _f64(x)
+    if slp_matvec is None:
+        slp_matvec = lambda z: dense_matvec(SLP, mesh, z, q_ss)  # noqa: E731
+    C = curl_matrices(mesh)
+    z = np.concatenate([(C[d] @ x.T).T for d in range(3)])  # (3 nrhs, nt)
+    w = slp_matvec(z)
+    nr = x.shape[0]
+    return sum((C[d].T @ w[d * nr:(d + 1) * nr].T).T for d in range(3))
+
+
+def hypersingular_dense(mesh, q_ss: int = 5) -> np.ndarray:
+    """The matrix W (nv x nv) from the dense Galerkin matrix G."""
+    G = dense_matrix(SLP, mesh, q_ss)
+    C = curl_matrices(mesh)
+    return sum((C[d].T @ (C[d].T @ G.T).T) for d in range(3))
