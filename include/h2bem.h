@@ -236,6 +236,22 @@ int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, 
  * nrhs, ld, host pointers), CUDA, OOM. */
 int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz, double* dx,
                void* stream);
+/* y = W x, the hypersingular operator on continuous piecewise-linear
+ * functions (section 1: w_ij = -int phi_i d/dn_x int dg/dn_y phi_j, hat
+ * functions phi_j of the mesh vertices), through its single-layer
+ * representation, which section 1 uses to set W up:
+ *   W = sum_{d=1..3} C_d^T G C_d,  (C_d)_{tau j} = (curl phi_j |_tau)_d,
+ * curl phi = n x grad phi, constant on each triangle tau = (a, b, c):
+ * curl phi_a = (b - c) / (2 |tau|) and cyclically.  G is this operator, which
+ * must be a single layer (H2BEM_SLP); one call applies it to 3 nrhs columns
+ * in its own tier.  x, y: device, nv x nrhs, leading dimensions ldx, ldy >= nv,
+ * the caller's vertex order (the vertices of h2bem_mesh_create; for a batch
+ * operator the concatenated vertices).  W annihilates constants.
+ * Asynchronous on `stream`; work vectors (2 x 3 n nrhs doubles) are kept by
+ * the operator.  Errors: ARG (NULL, double-layer operator, nrhs < 0, ld, host
+ * pointers), CUDA, OOM. */
+int h2bem_apply_hypersingular(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                              void* stream);
 /* y = A x + alpha M x with the P0 mass matrix M = diag(|tau_i|) (section 1,
  * the mass matrix m_ij of eq. (matrix_dtn) with piecewise-constant columns).
  * With A = K and alpha = 1/2 this is the right-hand side (M/2 + K) b of the

@@ -620,6 +620,9 @@ struct h2bem_op {
     DevBuf nst, nrow, nblk, nblk_t, xs;  // values, NearRow per row, NearBlock per block (and for A^T)
     int64_t nst_bytes = 0;
     int stage_order = 0;  // 1: the last apply ran the stored nearfield first
+    // hypersingular operator: triangles at each vertex (3 tau + corner), work vectors
+    DevBuf vptr, vinc, hyp_z, hyp_w;
+    int64_t hyp_cap = 0;
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
     int64_t ws_gen = 0;
@@ -1056,6 +1059,15 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if ((rc = op->far.upload_all()) || (rc = op->far_t.upload_all()) || (rc = op->near.upload_all()) ||
         (rc = op->near_u.upload_all()) || (rc = op->work.alloc(4 * sizeof(int))))
         return rc;
+    {
+        // triangles at each vertex (caller's order), for the hypersingular operator
+        std::vector<int> vp(op->nv + 1, 0), vi(3 * n);
+        for (int64_t e = 0; e < 3 * n; ++e) vp[mesh->tri[e] + 1]++;
+        for (int64_t v = 0; v < op->nv; ++v) vp[v + 1] += vp[v];
+        std::vector<int> fill(vp.begin(), vp.end() - 1);
+        for (int64_t e = 0; e < 3 * n; ++e) vi[fill[mesh->tri[e]]++] = (int)e;
+        if ((rc = upload(op->vptr, vp)) || (rc = upload(op->vinc, vi))) return rc;
+    }
     op->dlevel.resize(op->level_parents.size());
     for (size_t L = 0; L < op->level_parents.size(); ++L)
         if ((rc = upload(op->dlevel[L], op->level_parents[L]))) return rc;
@@ -1729,6 +1741,33 @@ extern "C" int h2bem_apply_mass(h2bem_op* op, double alpha, const double* x, int
     if (rc) return rc;
     if ((rc = ensure_area_user(op, s))) return rc;
     h2::launch_mass_add((int)op->n, nrhs, alpha, op->area_user.as<double>(), x, ldx, y, ldy, s);
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_apply_hypersingular(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y,
+                                         int64_t ldy, void* stream) {
+    if (!op || !x || !y) return fail(H2BEM_ERR_ARG, "apply_hypersingular: NULL argument");
+    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "apply_hypersingular: needs a single-layer operator");
+    if (nrhs < 0) return fail(H2BEM_ERR_ARG, "apply_hypersingular: nrhs must be >= 0");
+    if (ldx < op->nv || ldy < op->nv) return fail(H2BEM_ERR_ARG, "apply_hypersingular: leading dimensions must be >= nv");
+    if (!is_device_ptr(x) || !is_device_ptr(y))
+        return fail(H2BEM_ERR_ARG, "apply_hypersingular: x and y must be device memory");
+    if (nrhs == 0) return H2BEM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)op->n;
+    const int64_t need = 3 * (int64_t)n * nrhs;
+    int rc;
+    if (op->hyp_cap < need) {
+        if ((rc = op->hyp_z.alloc(need * sizeof(double))) || (rc = op->hyp_w.alloc(need * sizeof(double)))) return rc;
+        op->hyp_cap = need;
+    }
+    double *z = op->hyp_z.as<double>(), *w = op->hyp_w.as<double>();
+    h2::launch_curl_fwd(n, nrhs, op->xyz.as<double>(), op->tri.as<int>(), x, ldx, z, s);
+    CU(cudaGetLastError());
+    if ((rc = apply_impl(op, z, n, 3 * nrhs, w, n, stream, false, false))) return rc;
+    h2::launch_curl_bwd((int)op->nv, n, nrhs, op->vptr.as<int>(), op->vinc.as<int>(), op->xyz.as<double>(),
+                        op->tri.as<int>(), w, y, ldy, s);
     CU(cudaGetLastError());
     return H2BEM_OK;
 }

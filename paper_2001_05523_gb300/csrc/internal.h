@@ -192,6 +192,12 @@ void launch_cg_dir(int n, int nrhs, const double* beta, const double* res, int64
 void launch_mass_add(int n, int nrhs, double alpha, const double* area_user, const double* x, int64_t ldx, double* y,
                      int64_t ldy, cudaStream_t s);
 void launch_area_user(int n, const int* perm, const double* area, double* out, cudaStream_t s);
+// hypersingular operator through the single layer (k_hyper.cu): z = C_d x
+// (n x 3 nrhs, column d nrhs + r) and y = sum_d C_d^T w
+void launch_curl_fwd(int n, int nrhs, const double* xyz, const int* tri, const double* x, int64_t ldx, double* z,
+                     cudaStream_t s);
+void launch_curl_bwd(int nv, int n, int nrhs, const int* vptr, const int* inc, const double* xyz, const int* tri,
+                     const double* w, double* y, int64_t ldy, cudaStream_t s);
 }  // namespace h2
 
 struct h2bem_op;

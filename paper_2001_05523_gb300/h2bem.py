@@ -27,7 +27,7 @@ EXPORTED = [
     "h2bem_last_error", "h2bem_mesh_create", "h2bem_mesh_destroy", "h2bem_tree_build", "h2bem_tree_upload",
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
-    "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad", "h2bem_apply_mass",
+    "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad", "h2bem_apply_mass", "h2bem_apply_hypersingular",
     "h2bem_cg",
 ]
 
@@ -95,6 +95,7 @@ def lib():
             "h2bem_batch_create": [i32, vp, i32, i32, i32, d, vp, pp],
             "h2bem_grad": [vp, vp, vp, i64, i32, vp, vp, vp],
             "h2bem_apply_mass": [vp, d, vp, i64, i32, vp, i64, vp],
+            "h2bem_apply_hypersingular": [vp, vp, i64, i32, vp, i64, vp],
             "h2bem_cg": [vp, vp, i64, i32, vp, i64, d, i32, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -270,6 +271,13 @@ def h2bem_apply_mass(op, alpha, x, y, stream=None):
     """y = A x + alpha M x, M = diag(|tau_i|) (device buffers)."""
     px, lx, nr, py, ly = _vec_args(x, y)
     _check(lib().h2bem_apply_mass(op, ctypes.c_double(alpha), px, lx, nr, py, ly, _stream(stream)))
+
+
+def h2bem_apply_hypersingular(op, x, y, stream=None):
+    """y = W x, the hypersingular operator on piecewise-linear functions through
+    the single layer `op` (device buffers, (nrhs, nv))."""
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply_hypersingular(op, px, lx, nr, py, ly, _stream(stream)))
 
 
 def h2bem_cg(op, b, x, rtol=1e-8, maxit=1000, stream=None):
