@@ -262,21 +262,21 @@ def main():
         y = torch.empty_like(x)
         for _ in range(args.warmup):
             H.h2bem_apply(op.op, x, y, stream)
-        stage = np.zeros(8)
         barrier()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            H.h2bem_apply_timed(op.op, x, y, stream)  # records per-stage events on `stream`
-            stage += np.array(op.stats()["stage_ms"])
+            # back to back: the timed apply only records stage events on `stream`
+            # (no host wait), so the steps run without gaps
+            H.h2bem_apply_timed(op.op, x, y, stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1) / steps)
-        st = op.stats()
-        return op, y.clone(), ms, stage / steps, st, setup_s
+        st = op.stats()  # stage times (CUDA events) of the last timed step
+        return op, y.clone(), ms, np.array(st["stage_ms"]), st, setup_s
 
     results = {}
     with ClockSampler(local) as clk:
@@ -474,6 +474,45 @@ def main():
             "observed_order": {nm: float(np.log2(coarse["neumann_l2_rel_err"][nm] / fine["neumann_l2_rel_err"][nm]))
                                for nm in ("u1", "u2", "u3")},
             "expected_order": 1.0}
+
+    # hypersingular operator W on piecewise-linear functions (section 1) through its
+    # single-layer representation W = sum_d C_d^T G C_d, on the same sphere: one
+    # apply with nrhs vertex vectors (3 nrhs single-layer columns), the Rayleigh
+    # quotient of the interpolated harmonic Y_2 (exact value 6/5 on the unit sphere)
+    # and W 1 (zero: W annihilates constants)
+    if not args.no_fp64:
+        opw = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, eta=2.0, leaf_size=32,
+                         precision=args.tier, autotune=args.autotune)
+        nv = mesh.vertices.shape[0]
+        xv = torch.from_numpy(I.rhs(nv, nrhs, seed=11)).to(dev)
+        yv = torch.empty_like(xv)
+        for _ in range(2):
+            H.h2bem_apply_hypersingular(opw.op, xv, yv, stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            H.h2bem_apply_hypersingular(opw.op, xv, yv, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_w = e0.elapsed_time(e1) / 3
+        vv = mesh.vertices
+        u = 3 * vv[:, 2] ** 2 - (vv ** 2).sum(1)
+        tt = mesh.triangles
+        ar = 0.5 * np.linalg.norm(np.cross(vv[tt[:, 1]] - vv[tt[:, 0]], vv[tt[:, 2]] - vv[tt[:, 0]]), axis=1)
+        ut = u[tt]
+        uMu = float((ar / 12 * ((ut ** 2).sum(1) + ut.sum(1) ** 2)).sum())
+        ud = torch.from_numpy(np.ascontiguousarray(np.stack([u, np.ones(nv)]))).to(dev)
+        wu = torch.empty_like(ud)
+        H.h2bem_apply_hypersingular(opw.op, ud, wu, stream)
+        torch.cuda.synchronize(dev)
+        wu = wu.cpu().numpy()
+        opw.close()
+        extra["hypersingular_w"] = {
+            "vertices": nv, "rhs": nrhs, "single_layer_columns": 3 * nrhs, "ms_per_apply": ms_w,
+            "vertex_rhs_per_s": nv * nrhs / (ms_w / 1e3), "tier": args.tier,
+            "rayleigh_Y2": float(u @ wu[0] / uMu), "rayleigh_Y2_exact": 1.2,
+            "W1_rel": float(np.abs(wu[1]).max() / np.abs(wu[0]).max())}
 
     # roofline of the dominant kernel of the headline tier
     pk = peaks()

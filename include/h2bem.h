@@ -202,6 +202,9 @@ int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int ke
 int h2bem_batch_create(int nmeshes, const h2bem_mesh* const* meshes, int leaf_size, int kernel, int m, double eta,
                        const h2bem_opts* opts, h2bem_op** out);
 int h2bem_operator_destroy(h2bem_op* op);
+/* Counts and the launch variants of the last apply; after h2bem_apply_timed
+ * waits for its events and adds their stage times.  Errors: ARG (NULL),
+ * CUDA, TIMEOUT (see h2bem_apply_timed). */
 int h2bem_stats_get(const h2bem_op* op, h2bem_stats* stats);
 
 /* y = A x (A = G or K in its H^2 approximation; section 2, eq. (vsw) for the
@@ -275,9 +278,14 @@ int h2bem_apply_mass(h2bem_op* op, double alpha, const double* x, int64_t ldx, i
 int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol, int maxit,
              int* iters, double* relres, void* stream);
 /* As h2bem_apply with device buffers only, and records CUDA events around
- * each stage on `stream`; synchronises and fills the stats' stage_ms:
+ * each stage on `stream` (asynchronous: no host wait, so timed applies can run
+ * back to back).  The next h2bem_stats_get waits for the last of them and
+ * fills stage_ms and last_apply_ms of that apply:
  * [0] permute in, [1] leaf forward, [2] upward, [3] coupling, [4] downward,
- * [5] leaf backward, [6] nearfield regular, [7] nearfield singular. */
+ * [5] leaf backward, [6] nearfield regular (with opts.store_near: the stored
+ * nearfield, which runs right after [0]), [7] nearfield singular.
+ * h2bem_stats_get then also reports an expired bounded wait of the
+ * tensor-core coupling (TIMEOUT). */
 int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
 
 /* Allocation-free y = A x (the paper has no counterpart: this is a service

@@ -599,6 +599,7 @@ struct h2bem_op {
     size_t stage_elems = 0;
     cudaEvent_t ev[10] = {};
     double last_ms = 0.0, stage_ms[8] = {0};
+    bool timing_pending = false;  // a timed apply recorded events not read yet (h2bem_stats_get reads them)
     int64_t launches = 0;
     // launch variants (autotune): per right-hand-side width slot and direction
     int autotune = 0;
@@ -1270,8 +1271,13 @@ extern "C" int h2bem_operator_destroy(h2bem_op* op) {
     return H2BEM_OK;
 }
 
+static int resolve_timing(h2bem_op* op);
+
 extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     if (!op || !st) return fail(H2BEM_ERR_ARG, "stats_get: NULL argument");
+    // the stage times of a timed apply are read here (the operator's own
+    // event buffer; the counts are unchanged)
+    const int trc = resolve_timing(const_cast<h2bem_op*>(op));
     memset(st, 0, sizeof *st);
     st->n = op->n;
     st->nclusters = op->nc;
@@ -1291,7 +1297,7 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->launches = op->launches;
     st->last_apply_ms = op->last_ms;
     for (int i = 0; i < 8; ++i) st->stage_ms[i] = op->stage_ms[i];
-    return H2BEM_OK;
+    return trc;
 }
 
 // ===========================================================================
@@ -1688,21 +1694,27 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
         if (h2::coupling_tc_status(true))
             return fail(H2BEM_ERR_TIMEOUT, "apply: a bounded wait of the tensor-core coupling expired");
     }
-    if (timed) {
-        CU(cudaEventSynchronize(op->ev[9]));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, op->ev[0], op->ev[9]);
-        op->last_ms = ms;
-        // events in launch order; the stored nearfield runs right after permute_in
-        const int map[2][8][2] = {{{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}},
-                                  {{0, 1}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {1, 2}, {7, 8}}};
-        for (int i = 0; i < 8; ++i) {
-            cudaEventElapsedTime(&ms, op->ev[map[op->stage_order][i][0]], op->ev[map[op->stage_order][i][1]]);
-            op->stage_ms[i] = ms;
-        }
-        if (h2::coupling_tc_status(true))
-            return fail(H2BEM_ERR_TIMEOUT, "apply_timed: a bounded wait of the tensor-core coupling expired");
+    if (timed) op->timing_pending = true;  // read by h2bem_stats_get: no host wait here
+    return H2BEM_OK;
+}
+
+// Stage times of the last timed apply: waits for its last event.
+static int resolve_timing(h2bem_op* op) {
+    if (!op->timing_pending) return H2BEM_OK;
+    op->timing_pending = false;
+    CU(cudaEventSynchronize(op->ev[9]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, op->ev[0], op->ev[9]);
+    op->last_ms = ms;
+    // events in launch order; the stored nearfield runs right after permute_in
+    const int map[2][8][2] = {{{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {7, 8}},
+                              {{0, 1}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {1, 2}, {7, 8}}};
+    for (int i = 0; i < 8; ++i) {
+        cudaEventElapsedTime(&ms, op->ev[map[op->stage_order][i][0]], op->ev[map[op->stage_order][i][1]]);
+        op->stage_ms[i] = ms;
     }
+    if (h2::coupling_tc_status(true))
+        return fail(H2BEM_ERR_TIMEOUT, "apply_timed: a bounded wait of the tensor-core coupling expired");
     return H2BEM_OK;
 }
 
