@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "dmath.cuh"
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace h2 {
@@ -17,8 +18,17 @@ template <typename T>
 __device__ __forceinline__ T rsq(T x);
 template <>
 __device__ __forceinline__ double rsq<double>(double x) { return rsqrt_nr(x); }
+// FP32: the hardware reciprocal square root alone (PTX rsqrt.approx.ftz.f32,
+// ~2^-22.9 relative error); the squared distances between interpolation nodes
+// of admissible clusters are far from the subnormal range, so flushing them
+// changes nothing, and the range handling of a non-flushing rsqrt would add
+// instructions to every entry
 template <>
-__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsq<float>(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // nodes of cluster cl along every axis: z[d*m + a]
 __device__ __forceinline__ void cluster_nodes(const Tree& t, const Consts& c, int cl, double* z) {
@@ -137,11 +147,19 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
     } else {
         cluster_nodes(t, c, row, zt);
     }
-    TA acc[M][NR];
+    // FP32 entries and sums with an even number of right-hand sides: the sums
+    // as packed pairs (one f32x2 multiply-add for two right-hand sides)
+    constexpr bool PK = std::is_same<TA, float>::value && std::is_same<TS, float>::value && NR % 2 == 0;
+    constexpr int NA = PK ? 1 : NR, NP = PK ? NR / 2 : 1;
+    TA acc[M][NA];
+    f2 acc2[M][NP];
 #pragma unroll
-    for (int a = 0; a < M; ++a)
+    for (int a = 0; a < M; ++a) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[a][r] = 0;
+        for (int r = 0; r < NA; ++r) acc[a][r] = 0;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc2[a][q] = 0;
+    }
     // register prefetch of the next block's x-hat values and column nodes, so
     // that their global-memory latency overlaps the current block's work
     constexpr int NT = M2 * NSL;
@@ -225,14 +243,28 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
             const TA* xrow = xcur + (r2 * M) * NR;
 #pragma unroll
             for (int ja = 0; ja < M; ++ja) {
-                TA xv[NR];
+                if constexpr (PK) {
+                    f2 xv2[NP];
+                    const f2* xr2 = reinterpret_cast<const f2*>(xrow + ja * NR);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) xv[r] = xrow[ja * NR + r];
+                    for (int q = 0; q < NP; ++q) xv2[q] = xr2[q];
 #pragma unroll
-                for (int a = 0; a < M; ++a) {
-                    const TA sv = (TA)rsq<TS>(dx[a][ja] + sbc);
+                    for (int a = 0; a < M; ++a) {
+                        const float sv = rsq<float>(dx[a][ja] + sbc);
+                        const f2 s2 = pk(sv, sv);
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[a][r] += sv * xv[r];
+                        for (int q = 0; q < NP; ++q) acc2[a][q] = fma2(s2, xv2[q], acc2[a][q]);
+                    }
+                } else {
+                    TA xv[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) xv[r] = xrow[ja * NR + r];
+#pragma unroll
+                    for (int a = 0; a < M; ++a) {
+                        const TA sv = (TA)rsq<TS>(dx[a][ja] + sbc);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) acc[a][r] += sv * xv[r];
+                    }
                 }
             }
         }
@@ -241,8 +273,17 @@ __device__ __forceinline__ void coupling_row(const Tree& t, const Consts& c, con
     // reduction over slices: slot [sl][nu][r], nu = a + M * rg
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (active) xs[((size_t)sl * K + a + M * rg) * NR + r] = acc[a][r];
+        for (int r = 0; r < NR; ++r) {
+            TA v;
+            if constexpr (PK) {
+                float lo, hi;
+                upk(acc2[a][r / 2], lo, hi);
+                v = (r & 1) ? hi : lo;
+            } else {
+                v = acc[a][r];
+            }
+            if (active) xs[((size_t)sl * K + a + M * rg) * NR + r] = v;
+        }
     __syncthreads();
     for (int e = threadIdx.x; e < K * NR; e += blockDim.x) {
         TA s = 0;
