@@ -621,6 +621,12 @@ struct h2bem_op {
     DevBuf nst, nrow, nblk, nblk_t, xs;  // values, NearRow per row, NearBlock per block (and for A^T)
     int64_t nst_bytes = 0;
     int stage_order = 0;  // 1: the last apply ran the stored nearfield first
+    // singular entries applied by rows (FP32 Sauter-Schwab points): CSR of the
+    // entries of each tree position, values as float pairs per canonical pair
+    // (types in order at sg_off), evaluated per apply or once (cache_singular)
+    int sing_gather = 0;
+    DevBuf sg_ptr, sg_ent, sg_vals;
+    int64_t sg_off[3] = {0, 0, 0};
     // hypersingular operator: triangles at each vertex (3 tau + corner), work vectors
     DevBuf vptr, vinc, hyp_z, hyp_w;
     int64_t hyp_cap = 0;
@@ -828,7 +834,7 @@ static int build_near_store(h2bem_op* op, const h2bem_tree& tree, const std::vec
         DevBuf dp0, dp1, v0, v1;
         if ((rc = upload(dp0, p0)) || (rc = upload(dp1, p1))) return rc;
         const double *pv0 = op->sp_v0[ty].as<double>(), *pv1 = op->sp_v1[ty].as<double>();
-        if (!op->cache_singular) {
+        if (!pv0 || !pv1) {  // no FP64 cache (not requested, or kept as float pairs for the row gather)
             if ((rc = v0.alloc(np * sizeof(double))) || (rc = v1.alloc(np * sizeof(double)))) return rc;
             h2::launch_singular(op->geom(), h2::IDENTICAL - ty, op->kernel, np, op->sp_lo[ty].as<int>(),
                                 op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(),
@@ -1105,6 +1111,36 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             (rc = upload(op->sp_tab[t], tabs[t])))
             return rc;
     }
+    op->sing_gather = op->precision != H2BEM_FP64 && !op->singular_fp64;
+    if (op->sing_gather) {
+        // entries by row: (2 pid, other) in row lo, (2 pid + 1, lo) in row hi (once if lo = hi);
+        // the double layer has no identical-pair entries (k_ii = 0)
+        int64_t tot = 0;
+        for (int t = 0; t < 3; ++t) {
+            op->sg_off[t] = tot;
+            tot += (int64_t)slo[t].size();
+        }
+        std::vector<int> ptr(n + 1, 0);
+        for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
+            for (size_t p = 0; p < slo[t].size(); ++p) {
+                const int lo = iperm[slo[t][p]], hi = iperm[shi[t][p]];
+                ptr[lo + 1]++;
+                if (hi != lo) ptr[hi + 1]++;
+            }
+        for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        std::vector<int2> ent(ptr[n]);
+        for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
+            for (size_t p = 0; p < slo[t].size(); ++p) {
+                const int lo = iperm[slo[t][p]], hi = iperm[shi[t][p]];
+                const int v = (int)(2 * (op->sg_off[t] + (int64_t)p));
+                ent[fill[lo]++] = make_int2(v, hi);
+                if (hi != lo) ent[fill[hi]++] = make_int2(v + 1, lo);
+            }
+        if ((rc = upload(op->sg_ptr, ptr)) || (rc = upload(op->sg_ent, ent)) ||
+            (rc = op->sg_vals.alloc((size_t)std::max<int64_t>(2 * tot, 1) * sizeof(float))))
+            return rc;
+    }
     // shape-gradient data: vertex realising each bounding-box extreme (first in
     // the cluster's triangle order, corners in order), floored axes, the axis
     // of the largest half-width, children and parents
@@ -1176,8 +1212,16 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             CU(cudaGetLastError());
         }
     }
-    // x-independent singular entries, evaluated once if requested
-    if (op->cache_singular) {
+    // x-independent singular entries, evaluated once if requested: float pairs
+    // for the row gather (FP32 points), else FP64 values for the scatter
+    if (op->cache_singular && op->sing_gather) {
+        for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
+            h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, (int)op->sp_count[t], op->sp_lo[t].as<int>(),
+                                op->sp_hi[t].as<int>(), op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(),
+                                op->sp_npts[t], 3, true, false, 1, nullptr, nullptr,
+                                reinterpret_cast<double*>(op->sg_vals.as<float>() + 2 * op->sg_off[t]), nullptr, 0);
+        CU(cudaGetLastError());
+    } else if (op->cache_singular) {
         for (int t = 0; t < 3; ++t) {
             const int np = (int)op->sp_count[t];
             if ((rc = op->sp_v0[t].alloc(np * sizeof(double))) || (rc = op->sp_v1[t].alloc(np * sizeof(double)))) return rc;
@@ -1319,12 +1363,37 @@ static bool yh_is64(const h2bem_op* op, bool tr) {
 }
 
 // x in the stored nearfield's precision (FP32 tiers, or a single FP64 column
-// padded to 16 bytes); 0 where the stored apply reads x directly
+// padded to 16 bytes), or in FP32 for the singular row gather; 0 where
+// neither needs it (the stored FP64 apply reads x directly)
 static size_t store_x_bytes(const h2bem_op* op, int NR) {
-    if (!op->store_near) return 0;
     const bool f32 = op->precision != H2BEM_FP64;
+    if (!op->store_near) return op->sing_gather ? (size_t)op->n * h2::near_store_nx(true, NR) * sizeof(float) : 0;
     if (!f32 && NR > 1) return 0;
     return (size_t)op->n * h2::near_store_nx(f32, NR) * (f32 ? sizeof(float) : sizeof(double));
+}
+
+// Singular entries of an apply by rows: the float pairs of every canonical
+// pair (evaluated here unless cached), x in FP32, and one gather launch;
+// returns the number of launches.
+static int64_t sing_gather_apply(const h2bem_op* op, int NR, bool transpose, const double* xp, double* yp, void* xs,
+                                 cudaStream_t s) {
+    const h2::Geom g = op->geom();
+    const bool dlp = op->kernel == H2BEM_DLP;
+    int64_t nl = 0;
+    if (!op->cache_singular)
+        for (int ty = (dlp ? 1 : 0); ty < 3; ++ty) {
+            const int np = (int)op->sp_count[ty];
+            h2::launch_singular(g, h2::IDENTICAL - ty, dlp ? h2::DLP : h2::SLP, np, op->sp_lo[ty].as<int>(),
+                                op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(),
+                                op->sp_npts[ty], 3, true, false, 1, nullptr, nullptr,
+                                reinterpret_cast<double*>(const_cast<float*>(op->sg_vals.as<float>()) + 2 * op->sg_off[ty]),
+                                nullptr, s);
+            nl += np > 0 ? 1 : 0;
+        }
+    h2::launch_store_x(true, (int)op->n, NR, xp, xs, s);
+    h2::launch_sing_gather(NR, transpose && dlp, (int)op->n, op->sg_ptr.as<int>(), op->sg_ent.as<int2>(),
+                           op->sg_vals.as<float>(), (const float*)xs, yp, s);
+    return nl + 2;
 }
 
 // Nearfield of an apply from the stored blocks (x converted first where
@@ -1566,7 +1635,8 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
-    for (int ty = 0; ty < 3; ++ty) {
+    if (op->sing_gather) nl += sing_gather_apply(op, NR, transpose, op->xp.as<double>(), op->yp.as<double>(), op->xs.p, s);
+    for (int ty = 0; ty < 3 && !op->sing_gather; ++ty) {
         if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
         const int np = (int)op->sp_count[ty];
         nl += np > 0 ? 1 : 0;
@@ -2005,7 +2075,8 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
         launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
                         op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, cfg_near, s);
     }
-    for (int ty = 0; ty < 3; ++ty) {
+    if (op->sing_gather) sing_gather_apply(op, NR, false, xp, yp, xs, s);
+    for (int ty = 0; ty < 3 && !op->sing_gather; ++ty) {
         if (ty == 0 && dlp) continue;
         const int np = (int)op->sp_count[ty];
         if (op->cache_singular)

@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const
 }
 
 // FP32 evaluation (mixed tiers).  Table per point: identical (T0, T1, T2, T3)
-// as the FP64 table; edge and vertex (x_k, w_k x_k, w_k, 0).
-template <int NR, int TYPE, int KER, int MODE>
+// as the FP64 table; edge and vertex (x_k, w_k x_k, w_k, 0).  Q: the Gauss
+// points per direction at compile time (edge and vertex pairs; 0: npts at run
+// time), so that the nested point loops unroll.
+template <int NR, int TYPE, int KER, int MODE, int Q = 0>
 __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, const int* __restrict__ plo,
                                                          const int* __restrict__ phi, const int* __restrict__ pcode,
                                                          const double* __restrict__ tab, int npts, bool transpose,
@@ -329,8 +331,11 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
         for (int d = 0; d < 3; ++d)
             del[d] = (g.nef[d * n + hi] - g.nef[d * n + lo]) + (g.nef[(3 + d) * n + hi] - g.nef[(3 + d) * n + lo]);
     }
-    const double sc = 4.0 * g.area[lo] * g.area[hi] * kInv4Pi;
-    double a01, a10;
+    // MODE 3: the two entries as a float pair, scaled in FP32 (no FP64 arithmetic)
+    const double sc = MODE == 3 ? 0.0 : 4.0 * g.area[lo] * g.area[hi] * kInv4Pi;
+    const float scf = MODE == 3 ? (float)(4.0 * kInv4Pi) * (float)g.area[lo] * (float)g.area[hi] : 0.0f;
+    double a01 = 0.0, a10 = 0.0;
+    float v01 = 0.0f, v10 = 0.0f;
     if (TYPE == IDENTICAL) {
         const float aa = dot3(a, a), ab = dot3(a, b), bb = dot3(b, b);
         float sum = 0.0f;
@@ -338,16 +343,18 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
             const float* T = stf + 4 * p;
             sum = fmaf(T[3], rsqrt_f32(fmaf(T[2], bb, fmaf(T[1], ab, T[0] * aa))), sum);
         }
-        a01 = a10 = sc * (double)sum;
+        if (MODE == 3) v01 = v10 = scf * sum;
+        else a01 = a10 = sc * (double)sum;
     } else if (TYPE == EDGE) {
         // vectors (a, b, d); regions and coefficient triples as in k_singular
         const float Gm[3][3] = {{dot3(a, a), dot3(a, b), dot3(a, dd)},
                                 {dot3(a, b), dot3(b, b), dot3(b, dd)},
                                 {dot3(a, dd), dot3(b, dd), dot3(dd, dd)}};
-        const int q = npts;
+        const int q = Q > 0 ? Q : npts;
         float ssum = 0.0f, sb = 0.0f, sd = 0.0f;
         for (int reg = 0; reg < 5; ++reg) {
             float rs = 0.0f, rb = 0.0f, rd = 0.0f;
+#pragma unroll
             for (int oi = 0; oi < q; ++oi) {
                 const float o = stf[4 * oi], wo = stf[4 * oi + 2];
                 float F[3], Gv[3];
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
                     }
                 B2 *= 2.0f;
                 float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
                 for (int k = 0; k < q; ++k) {
                     const float tt = stf[4 * k];
                     const float wt = reg == 0 ? stf[4 * k + 2] : stf[4 * k + 1];  // w_t (R1) or w_t t
@@ -393,7 +401,11 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
             sd += rd;
         }
         if (KER == SLP) {
-            a01 = a10 = sc * (double)ssum * (1.0 / 6.0);
+            if (MODE == 3) v01 = v10 = scf * ssum * (1.0f / 6.0f);
+            else a01 = a10 = sc * (double)ssum * (1.0 / 6.0);
+        } else if (MODE == 3) {
+            v01 = 0.5f * scf * (sb * dot3(b, del));
+            v10 = 0.5f * scf * (sd * dot3(dd, del));
         } else {
             // V = (sa a + sb b + sd d) / 2; a is in both planes, b in lo's, d in hi's
             a01 = 0.5 * sc * (double)(sb * dot3(b, del));
@@ -403,22 +415,25 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
         const float aa = dot3(a, a), bb = dot3(b, b), c2 = dot3(cc, cc), d2 = dot3(dd, dd);
         const float ab = dot3(a, b), ac = dot3(a, cc), ad = dot3(a, dd), bc = dot3(b, cc), bd = dot3(b, dd),
                     cd = dot3(cc, dd);
-        const int q = npts;
+        const int q = Q > 0 ? Q : npts;
         float ssum = 0.0f, sa = 0.0f, sb = 0.0f, sc2 = 0.0f, sd = 0.0f;
         for (int reg = 0; reg < 2; ++reg) {
             const float uu = reg == 0 ? aa : c2, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : d2;
             const float pp = reg == 0 ? c2 : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? d2 : bb;
             const float b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
+#pragma unroll
             for (int i = 0; i < q; ++i) {
                 const float e1 = stf[4 * i], w1 = stf[4 * i + 2];
                 const float A = fmaf(e1, fmaf(e1, vv2, 2.0f * uv2), uu);
                 const float Bi0 = fmaf(e1, b2, b0), Bi1 = fmaf(e1, bd, b1);
                 float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+#pragma unroll
                 for (int l = 0; l < q; ++l) {
                     const float e3 = stf[4 * l], w3 = stf[4 * l + 2];
                     const float Cq = fmaf(e3, fmaf(e3, qq2, 2.0f * pq2), pp);
                     const float m2B = -2.0f * fmaf(e3, Bi1, Bi0);
                     float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
                     for (int k = 0; k < q; ++k) {
                         const float2 T = *reinterpret_cast<const float2*>(stf + 4 * k);  // (e2, w e2)
                         const float y = rsqrt_f32(fmaf(T.x, fmaf(T.x, Cq, m2B), A));
@@ -453,12 +468,20 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
             }
         }
         if (KER == SLP) {
-            a01 = a10 = sc * (double)ssum * (1.0 / 3.0);
+            if (MODE == 3) v01 = v10 = scf * ssum * (1.0f / 3.0f);
+            else a01 = a10 = sc * (double)ssum * (1.0 / 3.0);
+        } else if (MODE == 3) {
+            v01 = 0.5f * scf * fmaf(sa, dot3(a, del), sb * dot3(b, del));
+            v10 = 0.5f * scf * fmaf(sc2, dot3(cc, del), sd * dot3(dd, del));
         } else {
             // V = (sa a + sb b + sc c + sd d) / 2; a, b in lo's plane, c, d in hi's
             a01 = 0.5 * sc * (double)fmaf(sa, dot3(a, del), sb * dot3(b, del));
             a10 = 0.5 * sc * (double)fmaf(sc2, dot3(cc, del), sd * dot3(dd, del));
         }
+    }
+    if (MODE == 3) {
+        reinterpret_cast<float2*>(val0)[pid] = make_float2(v01, v10);
+        return;
     }
     if (MODE == 1) {
         val0[pid] = a01;
@@ -494,9 +517,12 @@ static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const
         return;
     }
     if constexpr (F32) {
-        auto k0 = k_singular32<NR, TYPE, KER, 0>;
-        auto k1 = k_singular32<NR, TYPE, KER, 1>;
-        auto kern = mode == 0 ? k0 : k1;
+        // the default 5 points per direction unrolled (edge and vertex pairs)
+        const bool q5 = TYPE != IDENTICAL && npts == 5;
+        auto k0 = q5 ? k_singular32<NR, TYPE, KER, 0, 5> : k_singular32<NR, TYPE, KER, 0>;
+        auto k1 = q5 ? k_singular32<NR, TYPE, KER, 1, 5> : k_singular32<NR, TYPE, KER, 1>;
+        auto k3 = q5 ? k_singular32<1, TYPE, KER, 3, 5> : k_singular32<1, TYPE, KER, 3>;
+        auto kern = mode == 0 ? k0 : mode == 1 ? k1 : k3;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     } else {
@@ -529,6 +555,47 @@ static void sing_type(int type, int ker, bool f32, int mode, int npairs, cudaStr
     if (type == IDENTICAL) sing_ker<NR, IDENTICAL>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     else if (type == EDGE) sing_ker<NR, EDGE>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
     else sing_ker<NR, VERTEX>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+}
+
+// Singular entries applied by rows: y_i += sum_e v_e x_{o_e} over the entries
+// e of row i (tree position): v_e = vals[ent.x ^ tr] (the pair's two entries
+// sit at 2 pid, 2 pid + 1: a_{lo,hi}, a_{hi,lo}; tr = 1 swaps them for the
+// transposed double layer), o_e = ent.y the other triangle of the pair.  FP32
+// products and row sums over the ~13 singular neighbours of a triangle, one
+// FP64 addition per row and right-hand side; no atomics (one thread per row).
+template <int NR>
+__global__ void __launch_bounds__(kThreads) k_sing_gather(int n, const int* __restrict__ ptr,
+                                                          const int2* __restrict__ ent,
+                                                          const float* __restrict__ vals, int tr,
+                                                          const float* __restrict__ xs, double* __restrict__ yp) {
+    constexpr int NX = NR > 4 ? NR : 4;  // row width of the FP32 copy of x
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0f;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int2 en = ent[e];
+        const float v = vals[en.x ^ tr];
+        const float* xo = xs + (int64_t)en.y * NX;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = fmaf(v, xo[r], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) yp[(int64_t)i * NR + r] += (double)acc[r];
+}
+
+void launch_sing_gather(int NR, bool transpose, int n, const int* ptr, const int2* ent, const float* vals,
+                        const float* xs, double* yp, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
+    const int tr = transpose ? 1 : 0;
+    switch (NR) {
+        case 1: k_sing_gather<1><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
+        case 4: k_sing_gather<4><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
+        case 8: k_sing_gather<8><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
+        default: k_sing_gather<16><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
+    }
 }
 
 void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
