@@ -213,8 +213,10 @@ int h2bem_stats_get(const h2bem_op* op, h2bem_stats* stats);
  *   the caller's triangle order; 1 <= nrhs <= 64.  x and y may each be
  *   device or host memory (detected per pointer); they must not overlap.
  *   With device buffers the call is asynchronous on `stream`; with a host
- *   buffer it copies through device scratch and synchronises the stream
- *   before returning.
+ *   buffer it synchronises the stream before returning.  Page-locked host
+ *   memory that is mapped into the device's address space (cudaHostAlloc,
+ *   cudaHostRegister) is read and written in place by the kernels, in the
+ *   caller's order; other host memory is copied through device scratch.
  * Scratch device memory is allocated on the first call and grown when nrhs
  * grows; concurrent applies of one operator on different streams race on it.
  * Errors: ARG (null, nrhs, ld), CUDA, OOM. */

@@ -1496,7 +1496,7 @@ static void launch_cfgs(h2bem_op* op, int NR, bool transpose, h2::LaunchCfg& nea
 
 // One chunk of at most 16 right-hand sides, device buffers, tree order work.
 static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
-                       bool transpose, bool timed) {
+                       bool transpose, bool timed, bool xmapped = false) {
     const int NR = pad_nr(nrhs);
     int rc = ensure_workspace(op, NR);
     if (rc) return rc;
@@ -1530,7 +1530,10 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                             op->xp.as<double>(), op->yp.as<double>(), cf, s);
     };
     mark(0);
-    h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
+    if (xmapped)  // x in mapped host memory: read in the caller's order
+        h2::launch_permute_in_scatter(x, ldx, nrhs, NR, op->iperm.as<int>(), n, op->xp.as<double>(), s);
+    else
+        h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
     // the stored nearfield writes every row of y first; otherwise the stages add to zero
     if (!op->store_near) CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
     if (tune_now && op->near_u.nrows() > 0 && !op->store_near) {
@@ -1668,6 +1671,19 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory with a device address (UVA maps it; on this
+// platform the device reads and writes it coherently over the host link).
+static bool mapped_host(const void* p, void** dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev = a.devicePointer;
+    return true;
+}
+
 static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream,
                       bool transpose, bool timed) {
     if (!op) return fail(H2BEM_ERR_ARG, "apply: op is NULL");
@@ -1688,20 +1704,27 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
     const double* xd = x;
     double* yd = y;
     int64_t lx = ldx, ly = ldy;
-    if (!xdev || !ydev) {
+    // page-locked host memory mapped into the device's address space: the
+    // permute kernels read x and write y through it (over the host link, in
+    // the caller's order); other host memory goes through staging copies
+    void *xmap = nullptr, *ymap = nullptr;
+    const bool xm = !xdev && mapped_host(x, &xmap), ym = !ydev && mapped_host(y, &ymap);
+    if (xm) xd = (const double*)xmap;
+    if (ym) yd = (double*)ymap;
+    if ((!xdev && !xm) || (!ydev && !ym)) {
         const size_t need = (size_t)op->n * nrhs;
         if (op->stage_elems < need) {
             int rc;
             if ((rc = op->xstage.alloc(need * sizeof(double))) || (rc = op->ystage.alloc(need * sizeof(double)))) return rc;
             op->stage_elems = need;
         }
-        if (!xdev) {
+        if (!xdev && !xm) {
             CU(cudaMemcpy2DAsync(op->xstage.p, op->n * sizeof(double), x, ldx * sizeof(double), op->n * sizeof(double),
                                  nrhs, cudaMemcpyHostToDevice, s));
             xd = op->xstage.as<double>();
             lx = op->n;
         }
-        if (!ydev) {
+        if (!ydev && !ym) {
             yd = op->ystage.as<double>();
             ly = op->n;
         }
@@ -1752,10 +1775,10 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
     }
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nr = std::min(16, nrhs - c0);
-        int rc = apply_chunk(op, xd + c0 * lx, lx, nr, yd + c0 * ly, ly, s, transpose, timed);
+        int rc = apply_chunk(op, xd + c0 * lx, lx, nr, yd + c0 * ly, ly, s, transpose, timed, xm);
         if (rc) return rc;
     }
-    if (!ydev) {
+    if (!ydev && !ym) {
         CU(cudaMemcpy2DAsync(y, ldy * sizeof(double), yd, ly * sizeof(double), op->n * sizeof(double), nrhs,
                              cudaMemcpyDeviceToHost, s));
     }

@@ -76,6 +76,10 @@ void launch_geom(const double* xyz, const int* tri, const int* perm, int n, cons
                  cudaStream_t s);
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
                        cudaStream_t s);
+// the same, reading x in the caller's order and scattering through iperm
+// (for x in mapped host memory: coalesced reads over the host link)
+void launch_permute_in_scatter(const double* x, int64_t ldx, int nrhs, int NR, const int* iperm, int n, double* xp,
+                               cudaStream_t s);
 void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,
                         cudaStream_t s);
 

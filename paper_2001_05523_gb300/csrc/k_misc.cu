@@ -15,6 +15,16 @@ __global__ void k_permute_in(const double* __restrict__ x, int64_t ldx, int nrhs
     xp[idx] = r < nrhs ? x[perm[pos] + r * ldx] : 0.0;
 }
 
+// As k_permute_in, reading x in the caller's order (coalesced) and scattering
+// into xp through iperm: for x in mapped host memory, read over the host link.
+__global__ void k_permute_in_scatter(const double* __restrict__ x, int64_t ldx, int nrhs, int NR,
+                                     const int* __restrict__ iperm, int n, double* __restrict__ xp) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * NR) return;
+    int r = (int)(idx / n), i = (int)(idx % n);
+    xp[(int64_t)iperm[i] * NR + r] = r < nrhs ? x[i + r * ldx] : 0.0;
+}
+
 // iperm: user index -> tree position; writes of y are coalesced.
 __global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, const int* __restrict__ iperm,
                               int n, double* __restrict__ y, int64_t ldy) {
@@ -95,6 +105,12 @@ void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int
                        cudaStream_t s) {
     int64_t tot = (int64_t)n * NR;
     k_permute_in<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, ldx, nrhs, NR, perm, n, xp);
+}
+
+void launch_permute_in_scatter(const double* x, int64_t ldx, int nrhs, int NR, const int* iperm, int n, double* xp,
+                               cudaStream_t s) {
+    int64_t tot = (int64_t)n * NR;
+    k_permute_in_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, ldx, nrhs, NR, iperm, n, xp);
 }
 
 void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, int n, double* y, int64_t ldy,

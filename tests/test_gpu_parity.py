@@ -157,6 +157,32 @@ def test_host_buffers_equal_device_buffers(H):
     op.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_pinned_host_buffers_equal_device_buffers(H, kernel):
+    """Page-locked (mapped) host x and y are read and written in place by the
+    permute kernels: the same kernels and sums as with device buffers (up to
+    the order of the nearfield's FP64 atomic additions); mixed with pageable
+    and device buffers too."""
+    import torch
+
+    mesh = I.jitter(I.sphere(9), 0.01, 2)
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, precision="mixed_fp32")
+    for nrhs, tr in ((3, False), (21, True)):  # 21: chunks of 16 and 5
+        x = I.rhs(mesh.nt, nrhs, seed=nrhs)
+        xd = torch.from_numpy(x).cuda()
+        yd = op.apply(xd, transpose=tr)
+        torch.cuda.synchronize()
+        ref = yd.cpu().numpy()
+        xp = torch.from_numpy(x).pin_memory()
+        for xin, yout in ((xp, torch.zeros_like(xp).pin_memory()), (xp, torch.zeros(x.shape, dtype=torch.float64)),
+                          (torch.from_numpy(x.copy()), torch.zeros_like(xp).pin_memory()),
+                          (xp, torch.zeros_like(xd))):
+            op.apply(xin, yout, transpose=tr)
+            torch.cuda.synchronize()
+            assert rel(yout.cpu().numpy(), ref) < 1e-13
+    op.close()
+
+
 def test_bad_arguments_at_apply(H):
     import torch
 
