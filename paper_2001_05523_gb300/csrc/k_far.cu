@@ -432,6 +432,98 @@ __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* _
     }
 }
 
+// Warp-per-parent transfers for compile-time m: warp w of a CTA takes parent
+// blockIdx.x * W + w; the factors and the three one-dimensional contractions
+// of each child run on warp-private shared memory with warp barriers only
+// (the CTA-per-parent kernels above synchronise the whole CTA around every
+// contraction, ~2 multiply-adds per thread each).  Up: the parent's sums are
+// kept in a fourth warp-private array over both children; down: each child's
+// block is added to its y-hat in place.  Same factors and summation order per
+// element as above.
+template <typename T, int NR, bool UP, int M>
+__global__ void __launch_bounds__(256) k_updown_w(Tree t, Consts c, int np, const int* __restrict__ parents,
+                                                  T* __restrict__ v) {
+    constexpr int K = M * M * M, KN = K * NR, PER = (KN + 31) / 32, F = 3 * M * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* E1 = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (2 * F + 4 * KN);
+    T* in = E1 + 2 * F;
+    T* tmp1 = in + KN;
+    T* tmp2 = tmp1 + KN;
+    T* out = tmp2 + KN;  // parent's sums (up)
+    const int pi = blockIdx.x * W + warp;
+    if (pi >= np) return;  // no CTA-wide barrier in this kernel
+    const int p = parents[pi];
+    const int ch[2] = {t.child0[p], t.child1[p]};
+    // E1[q][d][a'][a] = L_{p,a}(z_{ch_q,d}[a']) as in transfer_1d
+    for (int e = lane; e < 2 * F; e += 32) {
+        const int q = e / F, r = e % F;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            E1[e] = t.etr[(int64_t)ch[q] * F + r];
+        } else {
+            const int d = r / (M * M), ap = (r / M) % M, a = r % M;
+            const int cl = ch[q];
+            const double yd = (t.box[d * t.nc + cl] - t.box[d * t.nc + p] + t.box[(3 + d) * t.nc + cl] * c.cheb[ap]) *
+                              t.box[(6 + d) * t.nc + p];
+            double pr = c.bary[a];
+            for (int b = 0; b < M; ++b)
+                if (b != a) pr *= yd - c.cheb[b];
+            E1[e] = (T)pr;
+        }
+    }
+    if (!UP)
+        for (int e = lane; e < KN; e += 32) in[e] = v[(int64_t)p * KN + e];
+    for (int q = 0; q < 2; ++q) {
+        if (UP)
+            for (int e = lane; e < KN; e += 32) in[e] = v[(int64_t)ch[q] * KN + e];
+        __syncwarp();
+        const T* Ex = E1 + q * F;
+        const T* Ey = Ex + M * M;
+        const T* Ez = Ey + M * M;
+#pragma unroll 4
+        for (int j = 0; j < PER; ++j) {  // contract x
+            const int e = lane + 32 * j;
+            if (e < KN) {
+                const int r = e % NR, nu = e / NR, a = nu % M, rest = nu / M;
+                T sum = 0;
+#pragma unroll
+                for (int w = 0; w < M; ++w) sum += (UP ? Ex[w * M + a] : Ex[a * M + w]) * in[((rest * M) + w) * NR + r];
+                tmp1[e] = sum;
+            }
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int j = 0; j < PER; ++j) {  // contract y
+            const int e = lane + 32 * j;
+            if (e < KN) {
+                const int r = e % NR, nu = e / NR, a = nu % M, b = (nu / M) % M, cc = nu / (M * M);
+                T sum = 0;
+#pragma unroll
+                for (int w = 0; w < M; ++w)
+                    sum += (UP ? Ey[w * M + b] : Ey[b * M + w]) * tmp1[((cc * M + w) * M + a) * NR + r];
+                tmp2[e] = sum;
+            }
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int j = 0; j < PER; ++j) {  // contract z
+            const int e = lane + 32 * j;
+            if (e < KN) {
+                const int r = e % NR, nu = e / NR, ab = nu % (M * M), cc = nu / (M * M);
+                T sum = 0;
+#pragma unroll
+                for (int w = 0; w < M; ++w)
+                    sum += (UP ? Ez[w * M + cc] : Ez[cc * M + w]) * tmp2[((w * M * M) + ab) * NR + r];
+                if (UP) out[e] = q == 0 ? sum : out[e] + sum;
+                else v[(int64_t)ch[q] * KN + e] += sum;
+            }
+        }
+        __syncwarp();  // the next child overwrites in / tmp1 / tmp2
+    }
+    if (UP)
+        for (int e = lane; e < KN; e += 32) v[(int64_t)p * KN + e] = out[e];
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -580,6 +672,16 @@ void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves
 
 template <typename T, int NR, bool UP, int MM>
 static void updown_m(const Tree& t, const Consts& c, int np, const int* parents, void* v, cudaStream_t s) {
+    if constexpr (MM > 0) {
+        // warp per parent; warps per CTA so that a CTA keeps under ~160 KB
+        const size_t per_warp = sizeof(T) * (2 * 3 * MM * MM + 4 * (size_t)MM * MM * MM * NR);
+        int W = 8;
+        while (W > 1 && W * per_warp > 160 * 1024) --W;
+        auto kern = k_updown_w<T, NR, UP, MM>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(W * per_warp));
+        kern<<<(np + W - 1) / W, 32 * W, W * per_warp, s>>>(t, c, np, parents, (T*)v);
+        return;
+    }
     const size_t smem = sizeof(T) * (2 * 3 * kMaxM * kMaxM + 4 * (size_t)c.k * NR);
     if (UP) {
         cudaFuncSetAttribute(k_upward<T, NR, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
