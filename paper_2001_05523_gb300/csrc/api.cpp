@@ -622,10 +622,12 @@ struct h2bem_op {
     int64_t nst_bytes = 0;
     int stage_order = 0;  // 1: the last apply ran the stored nearfield first
     // singular entries applied by rows (FP32 Sauter-Schwab points): CSR of the
-    // entries of each tree position, values as float pairs per canonical pair
-    // (types in order at sg_off), evaluated per apply or once (cache_singular)
+    // entries of each tree position (partner positions sg_other), the values in
+    // that order (sg_vals; sg_vals_t for the cached transposed double layer),
+    // and per canonical pair its two places (types in order at sg_off);
+    // evaluated per apply or once (cache_singular)
     int sing_gather = 0;
-    DevBuf sg_ptr, sg_ent, sg_vals;
+    DevBuf sg_ptr, sg_other, sg_pos, sg_vals, sg_vals_t;
     int64_t sg_off[3] = {0, 0, 0};
     // hypersingular operator: triangles at each vertex (3 tau + corner), work vectors
     DevBuf vptr, vinc, hyp_z, hyp_w;
@@ -1129,17 +1131,24 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
             }
         for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
         std::vector<int> fill(ptr.begin(), ptr.end() - 1);
-        std::vector<int2> ent(ptr[n]);
+        std::vector<int> other(ptr[n]);
+        std::vector<int2> pos(std::max<int64_t>(tot, 1), make_int2(0, -1));
         for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
             for (size_t p = 0; p < slo[t].size(); ++p) {
                 const int lo = iperm[slo[t][p]], hi = iperm[shi[t][p]];
-                const int v = (int)(2 * (op->sg_off[t] + (int64_t)p));
-                ent[fill[lo]++] = make_int2(v, hi);
-                if (hi != lo) ent[fill[hi]++] = make_int2(v + 1, lo);
+                int2& ps = pos[op->sg_off[t] + (int64_t)p];
+                ps.x = fill[lo];
+                other[fill[lo]++] = hi;
+                if (hi != lo) {
+                    ps.y = fill[hi];
+                    other[fill[hi]++] = lo;
+                }
             }
-        if ((rc = upload(op->sg_ptr, ptr)) || (rc = upload(op->sg_ent, ent)) ||
-            (rc = op->sg_vals.alloc((size_t)std::max<int64_t>(2 * tot, 1) * sizeof(float))))
+        const size_t nv = (size_t)std::max<int64_t>(ptr[n], 1);
+        if ((rc = upload(op->sg_ptr, ptr)) || (rc = upload(op->sg_other, other)) || (rc = upload(op->sg_pos, pos)) ||
+            (rc = op->sg_vals.alloc(nv * sizeof(float))))
             return rc;
+        if (op->cache_singular && kernel == H2BEM_DLP && (rc = op->sg_vals_t.alloc(nv * sizeof(float)))) return rc;
     }
     // shape-gradient data: vertex realising each bounding-box extreme (first in
     // the cluster's triangle order, corners in order), floored axes, the axis
@@ -1215,11 +1224,14 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     // x-independent singular entries, evaluated once if requested: float pairs
     // for the row gather (FP32 points), else FP64 values for the scatter
     if (op->cache_singular && op->sing_gather) {
-        for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
-            h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, (int)op->sp_count[t], op->sp_lo[t].as<int>(),
-                                op->sp_hi[t].as<int>(), op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(),
-                                op->sp_npts[t], 3, true, false, 1, nullptr, nullptr,
-                                reinterpret_cast<double*>(op->sg_vals.as<float>() + 2 * op->sg_off[t]), nullptr, 0);
+        // both orders for the double layer (A and A^T); the single layer is symmetric
+        for (int tr = 0; tr < (kernel == H2BEM_DLP ? 2 : 1); ++tr)
+            for (int t = (kernel == H2BEM_DLP ? 1 : 0); t < 3; ++t)
+                h2::launch_singular(op->geom(), h2::IDENTICAL - t, kernel, (int)op->sp_count[t], op->sp_lo[t].as<int>(),
+                                    op->sp_hi[t].as<int>(), op->sp_code[t].as<int>(), op->sp_tab[t].as<double>(),
+                                    op->sp_npts[t], 3, true, tr == 1, 1, nullptr, nullptr,
+                                    reinterpret_cast<double*>((tr ? op->sg_vals_t : op->sg_vals).as<float>()),
+                                    reinterpret_cast<double*>(op->sg_pos.as<int2>() + op->sg_off[t]), 0);
         CU(cudaGetLastError());
     } else if (op->cache_singular) {
         for (int t = 0; t < 3; ++t) {
@@ -1380,19 +1392,20 @@ static int64_t sing_gather_apply(const h2bem_op* op, int NR, bool transpose, con
     const h2::Geom g = op->geom();
     const bool dlp = op->kernel == H2BEM_DLP;
     int64_t nl = 0;
+    const bool tr = transpose && dlp;
     if (!op->cache_singular)
         for (int ty = (dlp ? 1 : 0); ty < 3; ++ty) {
             const int np = (int)op->sp_count[ty];
             h2::launch_singular(g, h2::IDENTICAL - ty, dlp ? h2::DLP : h2::SLP, np, op->sp_lo[ty].as<int>(),
                                 op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(),
-                                op->sp_npts[ty], 3, true, false, 1, nullptr, nullptr,
-                                reinterpret_cast<double*>(const_cast<float*>(op->sg_vals.as<float>()) + 2 * op->sg_off[ty]),
-                                nullptr, s);
+                                op->sp_npts[ty], 3, true, tr, 1, nullptr, nullptr,
+                                reinterpret_cast<double*>(op->sg_vals.as<float>()),
+                                reinterpret_cast<double*>(op->sg_pos.as<int2>() + op->sg_off[ty]), s);
             nl += np > 0 ? 1 : 0;
         }
+    const float* vals = (op->cache_singular && tr) ? op->sg_vals_t.as<float>() : op->sg_vals.as<float>();
     h2::launch_store_x(true, (int)op->n, NR, xp, xs, s);
-    h2::launch_sing_gather(NR, transpose && dlp, (int)op->n, op->sg_ptr.as<int>(), op->sg_ent.as<int2>(),
-                           op->sg_vals.as<float>(), (const float*)xs, yp, s);
+    h2::launch_sing_gather(NR, (int)op->n, op->sg_ptr.as<int>(), op->sg_other.as<int>(), vals, (const float*)xs, yp, s);
     return nl + 2;
 }
 

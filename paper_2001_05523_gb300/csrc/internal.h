@@ -129,12 +129,13 @@ void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo
                      const double* tab, int npts, int mode, bool fp32, bool transpose, int NR, const double* xp,
                      double* yp, double* val0, double* val1, cudaStream_t s);
 // mode 3 of launch_singular (FP32 evaluation only): the pair's entries
-// (a_{lo,hi}, a_{hi,lo}) as a float pair at ((float2*)val0)[pid].
-// launch_sing_gather: y_i += sum over the singular entries of row i (CSR ptr /
-// ent = (value index, other position)) of vals[...] x_other, x in FP32 rows of
-// max(NR, 4) values (launch_store_x); transpose swaps the two entries.
-void launch_sing_gather(int NR, bool transpose, int n, const int* ptr, const int2* ent, const float* vals,
-                        const float* xs, double* yp, cudaStream_t s);
+// a_{lo,hi}, a_{hi,lo} (swapped if transpose) as floats at the places
+// ((int2*)val1)[pid] = (position in row lo, position in row hi or -1) of
+// (float*)val0, the row order of launch_sing_gather.
+// launch_sing_gather: y_i += sum_{e in [ptr[i], ptr[i+1])} vals[e] x_{other[e]},
+// x in FP32 rows of max(NR, 4) values (launch_store_x).
+void launch_sing_gather(int NR, int n, const int* ptr, const int* other, const float* vals, const float* xs,
+                        double* yp, cudaStream_t s);
 
 // farfield.  basis32: basis values in FP32 (else FP64); xh64 / yh64: the
 // cluster vectors xh / yh are double (else float).

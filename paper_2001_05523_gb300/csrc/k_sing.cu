@@ -480,7 +480,12 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
         }
     }
     if (MODE == 3) {
-        reinterpret_cast<float2*>(val0)[pid] = make_float2(v01, v10);
+        // each entry at its place in the row order of the gather: val1 holds
+        // (position in row lo, position in row hi or -1) per pair
+        const int2 ps = reinterpret_cast<const int2*>(val1)[pid];
+        float* vo = reinterpret_cast<float*>(val0);
+        vo[ps.x] = transpose ? v10 : v01;
+        if (ps.y >= 0) vo[ps.y] = transpose ? v01 : v10;
         return;
     }
     if (MODE == 1) {
@@ -557,16 +562,15 @@ static void sing_type(int type, int ker, bool f32, int mode, int npairs, cudaStr
     else sing_ker<NR, VERTEX>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
 }
 
-// Singular entries applied by rows: y_i += sum_e v_e x_{o_e} over the entries
-// e of row i (tree position): v_e = vals[ent.x ^ tr] (the pair's two entries
-// sit at 2 pid, 2 pid + 1: a_{lo,hi}, a_{hi,lo}; tr = 1 swaps them for the
-// transposed double layer), o_e = ent.y the other triangle of the pair.  FP32
-// products and row sums over the ~13 singular neighbours of a triangle, one
-// FP64 addition per row and right-hand side; no atomics (one thread per row).
+// Singular entries applied by rows: y_i += sum_e vals[e] x_{other[e]} over the
+// entries e in [ptr[i], ptr[i+1]) of row i (tree position); the pair kernels
+// write vals in this order.  FP32 products and row sums over the ~13 singular
+// neighbours of a triangle, one FP64 addition per row and right-hand side; no
+// atomics (one thread per row).
 template <int NR>
 __global__ void __launch_bounds__(kThreads) k_sing_gather(int n, const int* __restrict__ ptr,
-                                                          const int2* __restrict__ ent,
-                                                          const float* __restrict__ vals, int tr,
+                                                          const int* __restrict__ other,
+                                                          const float* __restrict__ vals,
                                                           const float* __restrict__ xs, double* __restrict__ yp) {
     constexpr int NX = NR > 4 ? NR : 4;  // row width of the FP32 copy of x
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -575,9 +579,8 @@ __global__ void __launch_bounds__(kThreads) k_sing_gather(int n, const int* __re
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = 0.0f;
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-        const int2 en = ent[e];
-        const float v = vals[en.x ^ tr];
-        const float* xo = xs + (int64_t)en.y * NX;
+        const float v = vals[e];
+        const float* xo = xs + (int64_t)other[e] * NX;
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] = fmaf(v, xo[r], acc[r]);
     }
@@ -585,16 +588,15 @@ __global__ void __launch_bounds__(kThreads) k_sing_gather(int n, const int* __re
     for (int r = 0; r < NR; ++r) yp[(int64_t)i * NR + r] += (double)acc[r];
 }
 
-void launch_sing_gather(int NR, bool transpose, int n, const int* ptr, const int2* ent, const float* vals,
-                        const float* xs, double* yp, cudaStream_t s) {
+void launch_sing_gather(int NR, int n, const int* ptr, const int* other, const float* vals, const float* xs,
+                        double* yp, cudaStream_t s) {
     if (n <= 0) return;
     const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
-    const int tr = transpose ? 1 : 0;
     switch (NR) {
-        case 1: k_sing_gather<1><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
-        case 4: k_sing_gather<4><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
-        case 8: k_sing_gather<8><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
-        default: k_sing_gather<16><<<grid, kThreads, 0, s>>>(n, ptr, ent, vals, tr, xs, yp); break;
+        case 1: k_sing_gather<1><<<grid, kThreads, 0, s>>>(n, ptr, other, vals, xs, yp); break;
+        case 4: k_sing_gather<4><<<grid, kThreads, 0, s>>>(n, ptr, other, vals, xs, yp); break;
+        case 8: k_sing_gather<8><<<grid, kThreads, 0, s>>>(n, ptr, other, vals, xs, yp); break;
+        default: k_sing_gather<16><<<grid, kThreads, 0, s>>>(n, ptr, other, vals, xs, yp); break;
     }
 }
 
