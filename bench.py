@@ -141,6 +141,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(v: float, world: int, device) -> float:
+    """The largest value over the ranks of the process group (the time of the
+    slowest replica); the value itself with one process."""
+    if world == 1:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units, over the slowest replica's time (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -246,13 +264,6 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     def timed_tier(precision: str, cache: bool, steps: int, **kw):
         t0 = time.perf_counter()
         # autotune: the first warm-up apply times the launch variants and keeps the fastest
@@ -274,7 +285,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
         st = op.stats()  # stage times (CUDA events) of the last timed step
         return op, y.clone(), ms, np.array(st["stage_ms"]), st, setup_s
 
@@ -293,7 +304,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         H.h2bem_apply(op_m.op, xpin, ypin, stream)  # synchronises the stream before returning
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
     torch.cuda.synchronize(dev)
     op_m.close()
 
@@ -564,7 +575,7 @@ def main():
                "sample": f"oracle H2 SLP apply (m=4, eta=2, leaf 32, {nrhs} rhs) on the {nt_small}-triangle "
                          f"sphere (s=64); per-triangle cost of this O(n) method is size-independent up to log n"}
 
-    value = world * n * nrhs / (ms_m / 1e3)
+    value = replica_throughput(n * nrhs, ms_m / 1e3, world)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -582,7 +593,7 @@ def main():
                                         "singular_pairs")},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * n * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * nrhs * 8,
+        "e2e": {"value": replica_throughput(n * nrhs, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": n * nrhs * 8,
                 "d2h_bytes_per_step": n * nrhs * 8},
         "gpu_launches": int(st_m["launches"]) * args.steps,
         "launch_variant": {"near_persistent": st_m["launch_variant"][0], "near_ctas_per_sm": st_m["launch_variant"][1],
