@@ -672,11 +672,12 @@ void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves
 
 template <typename T, int NR, bool UP, int MM>
 static void updown_m(const Tree& t, const Consts& c, int np, const int* parents, void* v, cudaStream_t s) {
-    if constexpr (MM > 0) {
-        // warp per parent; warps per CTA so that a CTA keeps under ~160 KB
-        const size_t per_warp = sizeof(T) * (2 * 3 * MM * MM + 4 * (size_t)MM * MM * MM * NR);
-        int W = 8;
-        while (W > 1 && W * per_warp > 160 * 1024) --W;
+    // warp per parent where a warp's arrays are small (8 warps per CTA, at
+    // least 3 CTAs per SM); larger blocks (FP64, m = 5, 16 right-hand sides)
+    // would leave too few warps per SM and keep the CTA per parent
+    constexpr size_t per_warp = sizeof(T) * (2 * 3 * MM * MM + 4 * (size_t)MM * MM * MM * NR);
+    if constexpr (MM > 0 && per_warp <= 9 * 1024) {
+        constexpr int W = 8;
         auto kern = k_updown_w<T, NR, UP, MM>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(W * per_warp));
         kern<<<(np + W - 1) / W, 32 * W, W * per_warp, s>>>(t, c, np, parents, (T*)v);
