@@ -43,6 +43,7 @@ def _stale(obj: str, deps) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "h2bem.h")]
+    headers += sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh"))
     nvcc = _nvcc()
     jobs = []
     objs = []
