@@ -37,15 +37,15 @@ sys.path.insert(0, ROOT)
 METRIC = "H2 SLP matvec triangles/s on 2M-tri sphere, mixed vs FP64, at stated rel. error"
 UNIT = "triangles*rhs/s"
 
-# Work units of the kernels (stated in the design doc).  Every kernel evaluation
+# Work units of the kernels.  Every kernel evaluation
 # costs one hardware reciprocal square root (the MUFU unit, 16 per clock per
 # SM), and the nearfield and coupling kernels are bound by that unit together
 # with the FP32 issue slots around it, so their achieved rate is reported as
 # kernel evaluations per second against the measured MUFU rate:
 #   regular nearfield  49 evaluations per pair the kernel evaluates (regular_evals:
 #                      every unordered regular pair once, both orders in diagonal blocks)
-#   singular           points per canonical pair: identical 3q (FP64 in every tier),
-#                      edge-adjacent 5q^2, vertex-adjacent 2q^3 (FP32 in the mixed tier)
+#   singular           points per canonical pair: identical 3q, edge-adjacent 5q^2,
+#                      vertex-adjacent 2q^3 (FP32 in the mixed tiers, FP64 in the FP64 tier)
 #   coupling           k^2 entries of S_ts per farfield block, plus 2 k^2 nrhs FP32 flops
 PTS_SING = {0: 15, 1: 125, 2: 250}  # q = 5
 # DRAM bytes (read + write) per launch of the regular nearfield kernel on this
