@@ -68,6 +68,9 @@ def lib():
             L.or_dense_matvec.argtypes = [i32, vp, i32, vp, i32, vp, i32]
             L.or_dense_rows.argtypes = [i32, vp, i32, vp, i64, vp, i32, vp]
             L.or_dense_matrix.argtypes = [i32, vp, i32, vp]
+            L.or_ss_pair3.argtypes = [i32, i32, vp, vp, vp, d, i32, i32, vp]
+            L.or_entry_dlp_p1.argtypes = [vp, i64, i64, i32, vp]
+            L.or_dense_dlp_p1.argtypes = [vp, i32, vp]
             L.or_h2_create.argtypes = [vp, i64, vp, i64, i32, i32, d, i32, i32]
             L.or_h2_create.restype = vp
             L.or_h2_destroy.argtypes = [vp]
@@ -210,6 +213,31 @@ def dense_matrix(kernel: int, mesh, q_ss: int = 5) -> np.ndarray:
     A = np.zeros((mesh.nt, mesh.nt))
     lib().or_dense_matrix(kernel, M.ptr, q_ss, _p(A))
     return A
+
+
+def entry_dlp_p1(mesh, i: int, j: int, q_ss: int = 5) -> np.ndarray:
+    """int_{tau_i} int_{tau_j} dg/dn_y lambda_{j,c}(y) for the corners c of tau_j
+    (the double layer with piecewise-linear trial functions, per pair)."""
+    M = _mesh(mesh)
+    out = np.zeros(3)
+    lib().or_entry_dlp_p1(M.ptr, i, j, q_ss, _p(out))
+    return out
+
+
+def dense_dlp_p1(mesh, q_ss: int = 5) -> np.ndarray:
+    """K1 (nt x nv): the double layer with piecewise-linear trial functions."""
+    M = _mesh(mesh)
+    A = np.zeros((mesh.nt, mesh.vertices.shape[0]))
+    lib().or_dense_dlp_p1(M.ptr, q_ss, _p(A))
+    return A
+
+
+def ss_pair3(kernel: int, kind: int, P, Q, q: int, side: int, nrm=None, sgn: float = 1.0) -> np.ndarray:
+    P, Q = _f64(np.asarray(P).reshape(-1)), _f64(np.asarray(Q).reshape(-1))
+    n = _f64(np.zeros(3) if nrm is None else np.asarray(nrm))
+    out = np.zeros(3)
+    lib().or_ss_pair3(kernel, kind, _p(P), _p(Q), _p(n), sgn, q, side, _p(out))
+    return out
 
 
 def dense_matvec(kernel: int, mesh, x: np.ndarray, q_ss: int = 5, transpose: bool = False) -> np.ndarray:

@@ -313,11 +313,11 @@ int or_shared_vertices(const or_mesh* M, int64_t i, int64_t j) {
  * cyclic rotation of tau_lo with its unshared vertex last, Q = (P0, P1, the
  * unshared vertex of tau_hi).  Vertex: both are the cyclic rotations that
  * start at the shared vertex. */
-void or_orient_pair(const or_mesh* M, int64_t lo, int64_t hi, int* type_out, double* P, double* Q) {
+/* canonical vertex order of the pair (lo, hi): pv (outer panel), qv (inner) */
+static void orient_ids(const or_mesh* M, int64_t lo, int64_t hi, int* type_out, int32_t* pv, int32_t* qv) {
     const int32_t* tl = M->tri + 3 * lo;
     const int32_t* th = M->tri + 3 * hi;
     int ns = or_shared_vertices(M, lo, hi);
-    int32_t pv[3], qv[3];
     if (ns == 3) {
         *type_out = OR_IDENTICAL;
         for (int k = 0; k < 3; ++k) pv[k] = qv[k] = tl[k];
@@ -349,6 +349,11 @@ void or_orient_pair(const or_mesh* M, int64_t lo, int64_t hi, int* type_out, dou
             qv[k] = th[(b0 + k) % 3];
         }
     }
+}
+
+void or_orient_pair(const or_mesh* M, int64_t lo, int64_t hi, int* type_out, double* P, double* Q) {
+    int32_t pv[3], qv[3];
+    orient_ids(M, lo, hi, type_out, pv, qv);
     for (int k = 0; k < 3; ++k)
         for (int d = 0; d < 3; ++d) {
             P[3 * k + d] = M->xyz[3 * (int64_t)pv[k] + d];
@@ -384,6 +389,123 @@ double or_entry(int kernel, const or_mesh* M, int64_t i, int64_t j, int q_ss) {
      * i == lo: x = p, y = q -> (p - q).n_j  (sgn +1)
      * i == hi: x = q, y = p -> (q - p).n_j  (sgn -1) */
     return or_ss_pair(OR_DLP, type, P, Q, nj, i == lo ? 1.0 : -1.0, q_ss);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Double layer with continuous piecewise-linear trial functions (section 1,  */
+/* eq. (dlp) with phi_j the hat functions of the vertices): on each pair of   */
+/* triangles the trial function is the barycentric coordinate of one corner   */
+/* of the source panel, so the pair contributes three values                  */
+/*   int_tau int_sigma dg/dn_y(x, y) lambda_c(y) dy dx,  c = corners of sigma, */
+/* with the quadrature of or_pair_regular / or_ss_pair and the factor          */
+/* lambda_c(y) at the source points.                                           */
+/* ------------------------------------------------------------------------- */
+
+/* As or_ss_pair, with the barycentric coordinates of the point on panel
+ * `side` (0: P, 1: Q) as factors: out[k], k = corner k of that panel in its
+ * given order.  chi(x) = P0 + x1 (P1 - P0) + x2 (P2 - P1) gives
+ * lambda = (1 - x1, x1 - x2, x2). */
+void or_ss_pair3(int kernel, int type, const double* P, const double* Q, const double* nrm, double sgn, int q,
+                 int side, double* out) {
+    double g[64], gw[64];
+    out[0] = out[1] = out[2] = 0.0;
+    if (or_gauss_legendre01(q, g, gw)) {
+        out[0] = out[1] = out[2] = NAN;
+        return;
+    }
+    double ap, np_[3], aq, nq[3];
+    or_tri_geom(P, P + 3, P + 6, &ap, np_);
+    or_tri_geom(Q, Q + 3, Q + 6, &aq, nq);
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int i0 = 0; i0 < q; ++i0)
+        for (int i1 = 0; i1 < q; ++i1)
+            for (int i2 = 0; i2 < q; ++i2)
+                for (int i3 = 0; i3 < q; ++i3) {
+                    double wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    double reg[6][5];
+                    int nr = ss_regions(type, g[i0], g[i1], g[i2], g[i3], reg);
+                    for (int r = 0; r < nr; ++r) {
+                        double x[3], y[3];
+                        chi(P, reg[r][0], reg[r][1], x);
+                        chi(Q, reg[r][2], reg[r][3], y);
+                        const double f = wt * reg[r][4] * ss_kernel(kernel, x, y, nrm, sgn);
+                        const double z1 = reg[r][side ? 2 : 0], z2 = reg[r][side ? 3 : 1];
+                        s[0] += f * (1.0 - z1);
+                        s[1] += f * (z1 - z2);
+                        s[2] += f * z2;
+                    }
+                }
+    for (int k = 0; k < 3; ++k) out[k] = 4.0 * ap * aq * s[k];
+}
+
+/* out[c] = int_{tau_i} int_{tau_j} dg/dn_y(x, y) lambda_{j,c}(y) dy dx, c = 0, 1, 2
+ * the corners of tau_j in the caller's order (n_y the normal of tau_j).  Pairs
+ * sharing no vertex: the 7 x 7 rule (lambda = (1 - u - v, u, v) at the rule's
+ * points); pairs sharing vertices: Sauter-Schwab in the canonical orientation
+ * of or_entry; a triangle with itself: 0 (x - y lies in its plane). */
+void or_entry_dlp_p1(const or_mesh* M, int64_t i, int64_t j, int q_ss, double* out) {
+    out[0] = out[1] = out[2] = 0.0;
+    int ns = or_shared_vertices(M, i, j);
+    double Yj[9], aj, nj[3];
+    tri_vertices(M, j, Yj);
+    or_tri_geom(Yj, Yj + 3, Yj + 6, &aj, nj);
+    if (ns == 0) {
+        double X[9], ax, nx[3], uv[14], w[7];
+        tri_vertices(M, i, X);
+        or_tri_geom(X, X + 3, X + 6, &ax, nx);
+        or_radon7(uv, w);
+        double xp[7][3], yq[7][3];
+        for (int p = 0; p < 7; ++p)
+            for (int d = 0; d < 3; ++d) {
+                xp[p][d] = X[d] + uv[2 * p] * (X[3 + d] - X[d]) + uv[2 * p + 1] * (X[6 + d] - X[d]);
+                yq[p][d] = Yj[d] + uv[2 * p] * (Yj[3 + d] - Yj[d]) + uv[2 * p + 1] * (Yj[6 + d] - Yj[d]);
+            }
+        for (int p = 0; p < 7; ++p)
+            for (int qq = 0; qq < 7; ++qq) {
+                const double f = w[p] * w[qq] * kernel_dlp(xp[p], yq[qq], nj);
+                const double u = uv[2 * qq], v = uv[2 * qq + 1];
+                out[0] += f * (1.0 - u - v);
+                out[1] += f * u;
+                out[2] += f * v;
+            }
+        for (int c = 0; c < 3; ++c) out[c] *= ax * aj;
+        return;
+    }
+    if (i == j) return;
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int type;
+    int32_t pv[3], qv[3];
+    orient_ids(M, lo, hi, &type, pv, qv);
+    double P[9], Q[9];
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) {
+            P[3 * k + d] = M->xyz[3 * (int64_t)pv[k] + d];
+            Q[3 * k + d] = M->xyz[3 * (int64_t)qv[k] + d];
+        }
+    /* the source panel is tau_j: Q (side 1) if i == lo, else P (side 0) */
+    const int side = i == lo ? 1 : 0;
+    double can[3];
+    or_ss_pair3(OR_DLP, type, P, Q, nj, i == lo ? 1.0 : -1.0, q_ss, side, can);
+    const int32_t* sv = side ? qv : pv;
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c)
+            if (M->tri[3 * j + c] == sv[k]) out[c] += can[k];
+}
+
+/* The matrix K1 (nt x nv, row-major): K1[i, v] = sum over the triangles j at
+ * vertex v of or_entry_dlp_p1(i, j)[corner of v in j]. */
+void or_dense_dlp_p1(const or_mesh* M, int q_ss, double* A) {
+    const int64_t n = M->nt, nv = M->nv;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        double* row = A + i * nv;
+        for (int64_t v = 0; v < nv; ++v) row[v] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double e[3];
+            or_entry_dlp_p1(M, i, j, q_ss, e);
+            for (int c = 0; c < 3; ++c) row[M->tri[3 * j + c]] += e[c];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -95,6 +95,20 @@ void or_dense_rows(int kernel, const or_mesh* M, int q_ss, const int64_t* rows, 
                    int nrhs, double* y);
 void or_dense_matrix(int kernel, const or_mesh* M, int q_ss, double* A);
 
+/* Double layer with continuous piecewise-linear trial functions (section 1,
+ * eq. (dlp), phi_j the hat functions of the vertices).
+ *   or_ss_pair3: or_ss_pair with the barycentric coordinate of each corner of
+ *     panel `side` (0: P, 1: Q; lambda = (1 - z1, z1 - z2, z2) in chi's
+ *     coordinates) as a factor: out[3].
+ *   or_entry_dlp_p1: out[c] = int_{tau_i} int_{tau_j} dg/dn_y lambda_{j,c}(y),
+ *     c the corners of tau_j in the caller's order.
+ *   or_dense_dlp_p1: K1 (nt x nv, row-major), K1[i, v] = sum over the
+ *     triangles j at vertex v of the corner values. */
+void or_ss_pair3(int kernel, int type, const double* P, const double* Q, const double* nrm, double sgn, int q,
+                 int side, double* out);
+void or_entry_dlp_p1(const or_mesh* M, int64_t i, int64_t j, int q_ss, double* out);
+void or_dense_dlp_p1(const or_mesh* M, int q_ss, double* A);
+
 or_h2* or_h2_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int kernel, int m, double eta,
                     int leaf, int q_ss);
 void or_h2_destroy(or_h2* H);
