@@ -14,7 +14,11 @@
  *   bases of order m (k = m^3, section 3), nested through transfer matrices
  *   (section 2, eq. (transfer)); nearfield blocks are evaluated on the fly by
  *   a 7 x 7-point Gauss rule (regular pairs) and Sauter-Schwab quadrature
- *   (pairs sharing a vertex, sections 1 and 5).
+ *   (pairs sharing a vertex, sections 1 and 5), or once and stored
+ *   (opts.store_near).  The hypersingular operator on continuous piecewise-
+ *   linear functions is applied through its single-layer representation
+ *   (h2bem_apply_hypersingular), and the Dirichlet-to-Neumann system of
+ *   section 1 is solved by conjugate gradients (h2bem_apply_mass, h2bem_cg).
  *
  * Conventions (all entry points):
  *   - Every function returns an int status: H2BEM_OK (0) or one of the
@@ -26,7 +30,8 @@
  *   - Triangles are int32 vertex indices, oriented counter-clockwise seen
  *     from outside, so (b-a)x(c-a) is the outward normal (section 1).
  *   - Vectors are column-major n x nrhs with a leading dimension >= n, in the
- *     caller's triangle order.
+ *     caller's triangle order (vertex order, nv x nrhs, for the hypersingular
+ *     operator).
  *   - Functions that take a `stream` (a cudaStream_t, NULL = legacy default
  *     stream) enqueue their GPU work on it; unless stated otherwise they
  *     return once the work is enqueued.
@@ -57,8 +62,10 @@ extern "C" {
 #define H2BEM_DLP 1 /* double layer K, eq. (dlp) */
 
 #define H2BEM_FP64 0       /* every step in FP64                                   */
-#define H2BEM_MIXED_FP32 1 /* FP32 farfield and regular-pair evaluation, FP64      */
-                           /* singular quadrature and nearfield accumulation       */
+#define H2BEM_MIXED_FP32 1 /* FP32 farfield, regular and Sauter-Schwab pairs (FP64  */
+                           /* points with opts.singular_fp64); the double layer's  */
+                           /* differentiated-basis side and the accumulation into  */
+                           /* y in FP64                                            */
 #define H2BEM_MIXED_TF32 2 /* as MIXED_FP32, coupling contraction on tensor cores  */
                            /* in TF32 with FP32 accumulation                        */
 #define H2BEM_MIXED_BF16 3 /* as MIXED_TF32 with BF16 operands                      */
