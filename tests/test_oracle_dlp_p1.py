@@ -187,3 +187,19 @@ def test_neumann_to_dirichlet_solution_converges_at_order_two(orc):
     for k in range(3):
         assert errs[(k, 16)] / errs[(k, 32)] > 3.0, errs
         assert errs[(k, 32)] < 3e-4, errs
+
+
+def test_h2_form_equals_dense_at_eta_zero_and_converges_in_m(orc):
+    """K1 in the H^2 form of section 2 (per-corner source basis W1, the same
+    transfers, coupling and output basis V as the other operators): with
+    eta = 0 it is the dense K1; with eta = 2 its error decays geometrically in
+    the interpolation order (section 3)."""
+    mesh = I.jitter(I.ellipsoid(8), 0.01, 2)
+    x = I.rhs(mesh.nv, 3, seed=4)
+    ref = x @ orc.dense_dlp_p1(mesh).T
+    y0 = orc.H2(mesh, 1, m=4, eta=0.0).matvec_dlp_p1(x)
+    assert np.linalg.norm(y0 - ref) < 1e-13 * np.linalg.norm(ref)
+    errs = [np.linalg.norm(orc.H2(mesh, 1, m=m, eta=2.0).matvec_dlp_p1(x) - ref) / np.linalg.norm(ref)
+            for m in (2, 3, 4, 5, 6)]
+    assert all(errs[q] / errs[q + 1] > 2.5 for q in range(4)), errs
+    assert errs[-1] < 1e-4, errs
