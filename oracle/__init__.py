@@ -83,7 +83,7 @@ def lib():
             L.or_h2_transfer.restype = i32
             L.or_h2_nodes.argtypes = [vp, vp]
             L.or_h2_matvec.argtypes = [vp, vp, i32, vp, i32, i32]
-            L.or_h2_matvec_dlp_p1.argtypes = [vp, vp, i32, vp, i32]
+            L.or_h2_matvec_dlp_p1.argtypes = [vp, vp, i32, vp, i32, i32]
             L.or_ss_moment.argtypes = [i32, i32, i32, i32, i32, i32]
             L.or_ss_moment.restype = d
             L.or_test_poly_P.argtypes = [vp]
@@ -330,13 +330,15 @@ class H2:
         lib().or_h2_matvec(self.h, _p(x), x.shape[0], _p(y), int(transpose), int(parts))
         return y
 
-    def matvec_dlp_p1(self, x: np.ndarray, parts: int = PART_ALL) -> np.ndarray:
-        """K1 x (piecewise-linear trial functions): x (nrhs, nv) -> (nrhs, nt)."""
+    def matvec_dlp_p1(self, x: np.ndarray, transpose: bool = False, parts: int = PART_ALL) -> np.ndarray:
+        """K1 x: (nrhs, nv) -> (nrhs, nt), or K1^T x: (nrhs, nt) -> (nrhs, nv)
+        (the double layer with piecewise-linear trial functions)."""
         x = _f64(x)
         if x.ndim == 1:
             x = x[None, :]
-        y = np.zeros((x.shape[0], self.n))
-        lib().or_h2_matvec_dlp_p1(self.h, _p(x), x.shape[0], _p(y), int(parts))
+        nv = self.mesh.vertices.shape[0]
+        y = np.zeros((x.shape[0], nv if transpose else self.n))
+        lib().or_h2_matvec_dlp_p1(self.h, _p(x), x.shape[0], _p(y), int(transpose), int(parts))
         return y
 
     def update_geometry(self, vertices) -> None:

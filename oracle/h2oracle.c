@@ -1122,66 +1122,94 @@ void or_h2_matvec(const or_h2* H, const double* x, int nrhs, double* y, int tran
     free(yh);
 }
 
-/* K1 x: the double layer with piecewise-linear trial functions (section 1,
- * eq. (dlp), phi_j the hat functions) in the same H^2 form, forward only.
- * The source side takes the per-corner basis
+/* K1 x and K1^T x: the double layer with piecewise-linear trial functions
+ * (section 1, eq. (dlp), phi_j the hat functions) in the same H^2 form.  The
+ * vertex side takes the per-corner basis
  *   W1_s[a, c, mu] = int_{tau_a} n_a . grad L_{s,mu}(y) lambda_c(y) dy
  * (the collapsed rule of the leaf bases, lambda = (1 - u - v, u, v) at its
- * points; the integrand's degree 3(m-1) is within the rule's exactness), so
- * that x-hat_s = sum_a sum_c W1_s[a, c, :] x[vertex c of tau_a]; the passes
- * and the output side V are those of or_h2_matvec; the nearfield uses
- * or_entry_dlp_p1.  x: nv x nrhs, y: nt x nrhs (column-major). */
-void or_h2_matvec_dlp_p1(const or_h2* H, const double* x, int nrhs, double* y, int parts) {
+ * points; the integrand's degree 3(m-1) is within the rule's exactness); the
+ * triangle side takes V; the passes are those of or_h2_matvec (transposed for
+ * K1^T); the nearfield uses or_entry_dlp_p1.
+ *   forward:   x nv x nrhs, y nt x nrhs;   transpose: x nt x nrhs, y nv x nrhs
+ * (column-major). */
+static void leaf_w1(const or_h2* H, int64_t j, const double* z, double* W1 /* 3 x k */) {
+    int k = H->k, m = H->m;
+    double ruv[2 * 64 * 64], rw[64 * 64];
+    int np = or_collapsed_rule(H->qb, ruv, rw);
+    double X[9], area, nrm[3];
+    tri_vertices(&H->mesh, j, X);
+    or_tri_geom(X, X + 3, X + 6, &area, nrm);
+    for (int e = 0; e < 3 * k; ++e) W1[e] = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const double u = ruv[2 * p], v = ruv[2 * p + 1];
+        const double lam[3] = {1.0 - u - v, u, v};
+        double xq[3], g[3];
+        for (int d = 0; d < 3; ++d) xq[d] = X[d] + u * (X[3 + d] - X[d]) + v * (X[6 + d] - X[d]);
+        for (int mu = 0; mu < k; ++mu) {
+            tensor_lagrange_grad(z, m, mu, xq, g);
+            const double f = area * rw[p] * dot3(nrm, g);
+            for (int cc = 0; cc < 3; ++cc) W1[cc * k + mu] += f * lam[cc];
+        }
+    }
+}
+
+void or_h2_matvec_dlp_p1(const or_h2* H, const double* x, int nrhs, double* y, int transpose, int parts) {
     const tree_t* T = &H->T;
     int64_t n = T->n, nc = T->count, nv = H->mesh.nv;
     int k = H->k, m = H->m;
+    const int64_t nin = transpose ? n : nv, nout = transpose ? nv : n;
     double* xh = calloc((size_t)nc * k * nrhs, sizeof(double));
     double* yh = calloc((size_t)nc * k * nrhs, sizeof(double));
-    double ruv[2 * 64 * 64], rw[64 * 64];
-    int np = or_collapsed_rule(H->qb, ruv, rw);
+    /* input side at the leaves */
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t c = 0; c < nc; ++c) {
         if (T->child0[c] >= 0) continue;
         const double* z = H->nodes + c * 3 * m;
         int64_t b = T->begin[c], sz = T->end[c] - b;
-        double* W1 = calloc((size_t)3 * k, sizeof(double));
+        double* W1 = malloc((size_t)3 * k * sizeof(double));
         for (int64_t a = 0; a < sz; ++a) {
             const int64_t j = T->perm[b + a];
-            double X[9], area, nrm[3];
-            tri_vertices(&H->mesh, j, X);
-            or_tri_geom(X, X + 3, X + 6, &area, nrm);
-            for (int e = 0; e < 3 * k; ++e) W1[e] = 0.0;
-            for (int p = 0; p < np; ++p) {
-                const double u = ruv[2 * p], v = ruv[2 * p + 1];
-                const double lam[3] = {1.0 - u - v, u, v};
-                double xq[3], g[3];
-                for (int d = 0; d < 3; ++d) xq[d] = X[d] + u * (X[3 + d] - X[d]) + v * (X[6 + d] - X[d]);
-                for (int mu = 0; mu < k; ++mu) {
-                    tensor_lagrange_grad(z, m, mu, xq, g);
-                    const double f = area * rw[p] * dot3(nrm, g);
-                    for (int cc = 0; cc < 3; ++cc) W1[cc * k + mu] += f * lam[cc];
-                }
+            if (transpose) {
+                for (int mu = 0; mu < k; ++mu)
+                    for (int r = 0; r < nrhs; ++r) xh[(c * k + mu) * nrhs + r] += H->V[c][a * k + mu] * x[j + r * nin];
+                continue;
             }
+            leaf_w1(H, j, z, W1);
             for (int cc = 0; cc < 3; ++cc) {
                 const int64_t vtx = H->mesh.tri[3 * j + cc];
                 for (int mu = 0; mu < k; ++mu)
-                    for (int r = 0; r < nrhs; ++r) xh[(c * k + mu) * nrhs + r] += W1[cc * k + mu] * x[vtx + r * nv];
+                    for (int r = 0; r < nrhs; ++r) xh[(c * k + mu) * nrhs + r] += W1[cc * k + mu] * x[vtx + r * nin];
             }
         }
         free(W1);
     }
-    h2_far_passes(H, xh, yh, nrhs, 0);
-    for (int64_t i = 0; i < n * nrhs; ++i) y[i] = 0.0;
-#pragma omp parallel for schedule(dynamic, 4)
+    h2_far_passes(H, xh, yh, nrhs, transpose);
+    for (int64_t i = 0; i < nout * nrhs; ++i) y[i] = 0.0;
+    /* output side and nearfield, one leaf at a time (vertex rows of different
+     * leaves may coincide, so the transpose runs serially) */
     for (int64_t c = 0; c < nc; ++c) {
         if (T->child0[c] >= 0) continue;
+        const double* z = H->nodes + c * 3 * m;
         int64_t b = T->begin[c], sz = T->end[c] - b;
+        double W1[3 * 216];
         for (int64_t a = 0; a < sz && (parts & OR_PART_FAR); ++a) {
             int64_t i = T->perm[b + a];
-            for (int r = 0; r < nrhs; ++r) {
-                double s = 0.0;
-                for (int nu = 0; nu < k; ++nu) s += H->V[c][a * k + nu] * yh[(c * k + nu) * nrhs + r];
-                y[i + r * n] += s;
+            if (!transpose) {
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < k; ++nu) s += H->V[c][a * k + nu] * yh[(c * k + nu) * nrhs + r];
+                    y[i + r * nout] += s;
+                }
+            } else {
+                leaf_w1(H, i, z, W1);
+                for (int cc = 0; cc < 3; ++cc) {
+                    const int64_t vtx = H->mesh.tri[3 * i + cc];
+                    for (int r = 0; r < nrhs; ++r) {
+                        double s = 0.0;
+                        for (int nu = 0; nu < k; ++nu) s += W1[cc * k + nu] * yh[(c * k + nu) * nrhs + r];
+                        y[vtx + r * nout] += s;
+                    }
+                }
             }
         }
         for (int64_t q = H->near_ptr[c]; q < H->near_ptr[c + 1] && (parts & OR_PART_NEAR); ++q) {
@@ -1194,7 +1222,10 @@ void or_h2_matvec_dlp_p1(const or_h2* H, const double* x, int nrhs, double* y, i
                     or_entry_dlp_p1(&H->mesh, i, j, H->q_ss, e);
                     for (int cc = 0; cc < 3; ++cc) {
                         const int64_t vtx = H->mesh.tri[3 * j + cc];
-                        for (int r = 0; r < nrhs; ++r) y[i + r * n] += e[cc] * x[vtx + r * nv];
+                        for (int r = 0; r < nrhs; ++r) {
+                            if (!transpose) y[i + r * nout] += e[cc] * x[vtx + r * nin];
+                            else y[vtx + r * nout] += e[cc] * x[i + r * nin];
+                        }
                     }
                 }
             }

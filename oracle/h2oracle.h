@@ -120,10 +120,12 @@ int or_h2_leaf_basis(const or_h2* H, int64_t c, double* V, double* W);
 int or_h2_transfer(const or_h2* H, int64_t c, double* E);
 void or_h2_nodes(const or_h2* H, double* nodes);
 void or_h2_matvec(const or_h2* H, const double* x, int nrhs, double* y, int transpose, int parts);
-/* K1 x, the double layer with piecewise-linear trial functions in the same H^2
- * form (per-corner source basis W1, the passes and V of or_h2_matvec, the
- * nearfield by or_entry_dlp_p1); x: nv x nrhs, y: nt x nrhs. */
-void or_h2_matvec_dlp_p1(const or_h2* H, const double* x, int nrhs, double* y, int parts);
+/* K1 x (transpose = 0: x nv x nrhs, y nt x nrhs) or K1^T x (transpose = 1:
+ * x nt x nrhs, y nv x nrhs), the double layer with piecewise-linear trial
+ * functions in the same H^2 form (per-corner basis W1 on the vertex side, V on
+ * the triangle side, the passes of or_h2_matvec, the nearfield by
+ * or_entry_dlp_p1). */
+void or_h2_matvec_dlp_p1(const or_h2* H, const double* x, int nrhs, double* y, int transpose, int parts);
 double or_ss_moment(int type, int q, int a, int b, int c, int d);
 double or_test_poly_P(const double* x);
 double or_test_poly_Q(const double* y);

@@ -203,3 +203,20 @@ def test_h2_form_equals_dense_at_eta_zero_and_converges_in_m(orc):
             for m in (2, 3, 4, 5, 6)]
     assert all(errs[q] / errs[q + 1] > 2.5 for q in range(4)), errs
     assert errs[-1] < 1e-4, errs
+
+
+def test_h2_transpose_equals_dense_and_is_the_adjoint(orc):
+    """K1^T in the H^2 form (V on the triangle side, the transposed passes,
+    W1 gathered to the vertices): the dense K1^T at eta = 0, and the adjoint
+    of the forward H^2 product at eta = 2 to rounding."""
+    mesh = I.jitter(I.ellipsoid(8), 0.01, 2)
+    K1 = orc.dense_dlp_p1(mesh)
+    xt = I.rhs(mesh.nt, 3, seed=5)
+    xv = I.rhs(mesh.nv, 3, seed=4)
+    y0 = orc.H2(mesh, 1, m=4, eta=0.0).matvec_dlp_p1(xt, transpose=True)
+    assert np.linalg.norm(y0 - xt @ K1) < 1e-13 * np.linalg.norm(xt @ K1)
+    H = orc.H2(mesh, 1, m=4, eta=2.0)
+    yt = H.matvec_dlp_p1(xt, transpose=True)
+    y = H.matvec_dlp_p1(xv)
+    assert abs((xt * y).sum() - (yt * xv).sum()) < 1e-13 * np.linalg.norm(xt) * np.linalg.norm(y) * 10
+    assert np.linalg.norm(yt - xt @ K1) < 3e-3 * np.linalg.norm(xt @ K1)
