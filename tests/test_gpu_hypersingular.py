@@ -28,8 +28,7 @@ def H():
     return h2bem
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from tests._parity import close, rel  # noqa: E402
 
 
 def apply_w(H, op, x):
@@ -50,7 +49,7 @@ def test_dense_equals_oracle_matrix(H, orc, precision):
     y = apply_w(H, op, x)
     op.close()
     W = orc.hypersingular_dense(mesh)
-    assert rel(y, x @ W.T) < TOL[precision]
+    close(y, x @ W.T, TOL[precision])
 
 
 @pytest.mark.parametrize("name", ["sphere", "cube", "ellipsoid"])
@@ -64,7 +63,7 @@ def test_h2_matches_oracle(H, orc, name, precision, nrhs):
     y = apply_w(H, op, x)
     op.close()
     ref = orc.hypersingular_matvec(mesh, x, slp_matvec=orc.H2(mesh, 0, m=4).matvec)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 def test_constants_and_symmetry(H):
@@ -106,7 +105,7 @@ def test_batch_is_block_diagonal(H, orc):
     for mh, nv in zip(meshes, nvs):
         ref = orc.hypersingular_matvec(mh, np.ascontiguousarray(x[:, off:off + nv]),
                                        slp_matvec=orc.H2(mh, 0, m=4).matvec)
-        assert rel(y[:, off:off + nv], ref) < 1e-10
+        close(y[:, off:off + nv], ref, 1e-10)
         off += nv
 
 

@@ -29,8 +29,7 @@ def H():
     return h2bem
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from tests._parity import close, rel  # noqa: E402
 
 
 def gpu_apply(H, mesh, x, kernel=0, m=4, eta=2.0, leaf=32, precision="fp64", transpose=False, cache=False,
@@ -63,7 +62,7 @@ def test_fp64_matches_oracle_h2(H, orc, name, kernel):
     x = I.rhs(mesh.nt, 3, seed=3)
     y = gpu_apply(H, mesh, x, kernel=kernel)
     ref = orc.H2(mesh, kernel, m=4, eta=2.0, leaf=32).matvec(x)
-    assert rel(y, ref) < TOL["fp64"]
+    close(y, ref, TOL["fp64"])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -72,7 +71,7 @@ def test_fp64_transpose_matches_oracle(H, orc, kernel):
     x = I.rhs(mesh.nt, 2, seed=4)
     y = gpu_apply(H, mesh, x, kernel=kernel, transpose=True)
     ref = orc.H2(mesh, kernel, m=4, eta=2.0, leaf=32).matvec(x, transpose=True)
-    assert rel(y, ref) < TOL["fp64"]
+    close(y, ref, TOL["fp64"])
 
 
 @pytest.mark.parametrize("nrhs", [1, 2, 5, 8, 16, 19])
@@ -81,7 +80,7 @@ def test_nrhs_padding_and_chunks(H, orc, nrhs):
     x = I.rhs(mesh.nt, nrhs, seed=nrhs)
     y = gpu_apply(H, mesh, x, kernel=0)
     ref = orc.H2(mesh, 0, m=4).matvec(x)
-    assert rel(y, ref) < TOL["fp64"]
+    close(y, ref, TOL["fp64"])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -93,7 +92,7 @@ def test_dense_512_sphere(H, orc, kernel):
     x = I.rhs(mesh.nt, 1)
     y = gpu_apply(H, mesh, x, kernel=kernel, eta=0.0)
     ref = orc.dense_matvec(kernel, mesh, x)
-    assert rel(y, ref) < 1e-12
+    close(y, ref, 1e-12)
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 5, 6])
@@ -102,7 +101,7 @@ def test_interpolation_orders(H, orc, m):
     x = I.rhs(mesh.nt, 2, seed=m)
     y = gpu_apply(H, mesh, x, kernel=1 if m % 2 else 0, m=m)
     ref = orc.H2(mesh, 1 if m % 2 else 0, m=m).matvec(x)
-    assert rel(y, ref) < TOL["fp64"]
+    close(y, ref, TOL["fp64"])
 
 
 @pytest.mark.parametrize("leaf", [1, 5, 64])
@@ -111,7 +110,7 @@ def test_leaf_sizes_and_tiny_meshes(H, orc, leaf):
         x = I.rhs(mesh.nt, 2, seed=leaf)
         y = gpu_apply(H, mesh, x, kernel=0, leaf=leaf, m=2)
         ref = orc.H2(mesh, 0, m=2, leaf=leaf).matvec(x)
-        assert rel(y, ref) < TOL["fp64"]
+        close(y, ref, TOL["fp64"])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -120,7 +119,7 @@ def test_cache_singular_equals_on_the_fly(H, kernel):
     x = I.rhs(mesh.nt, 4)
     a = gpu_apply(H, mesh, x, kernel=kernel, cache=False)
     b = gpu_apply(H, mesh, x, kernel=kernel, cache=True)
-    assert rel(a, b) < 1e-13
+    close(a, b, 1e-13)
 
 
 @pytest.mark.parametrize("q", [2, 7, 8])
@@ -130,7 +129,7 @@ def test_singular_orders(H, orc, q):
     for kernel in (0, 1):
         y = gpu_apply(H, mesh, x, kernel=kernel, eta=0.0, q_ss=q)
         ref = orc.dense_matvec(kernel, mesh, x, q_ss=q)
-        assert rel(y, ref) < 1e-12
+        close(y, ref, 1e-12)
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -139,7 +138,7 @@ def test_mixed_fp32_matches_oracle(H, orc, kernel):
     x = I.rhs(mesh.nt, 4, seed=8)
     y = gpu_apply(H, mesh, x, kernel=kernel, precision="mixed_fp32")
     ref = orc.H2(mesh, kernel, m=4).matvec(x)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 def test_host_buffers_equal_device_buffers(H):
@@ -153,7 +152,7 @@ def test_host_buffers_equal_device_buffers(H):
     xd = torch.from_numpy(x).cuda()
     yd = op.apply(xd)
     torch.cuda.synchronize()
-    assert rel(yh, yd.cpu().numpy()) < 1e-13
+    close(yh, yd.cpu().numpy(), 1e-13)
     op.close()
 
 
@@ -179,7 +178,7 @@ def test_pinned_host_buffers_equal_device_buffers(H, kernel):
                           (xp, torch.zeros_like(xd))):
             op.apply(xin, yout, transpose=tr)
             torch.cuda.synchronize()
-            assert rel(yout.cpu().numpy(), ref) < 1e-13
+            close(yout.cpu().numpy(), ref, 1e-13)
     op.close()
 
 
@@ -205,7 +204,7 @@ def test_sphere32k_fp64_vs_oracle_h2_and_dense_rows(H, orc, kernel):
     x = I.rhs(mesh.nt, 2)
     y = gpu_apply(H, mesh, x, kernel=kernel)
     ref = orc.H2(mesh, kernel, m=4).matvec(x)
-    assert rel(y, ref) < TOL["fp64"]
+    close(y, ref, TOL["fp64"])
     rows = np.random.default_rng(1).choice(mesh.nt, 48, replace=False)
     d = orc.dense_rows(kernel, mesh, rows, x)
     assert rel(y[:, rows], d) < (1e-3 if kernel == 0 else 1e-2)
@@ -216,16 +215,20 @@ def test_sphere32k_fp64_vs_oracle_h2_and_dense_rows(H, orc, kernel):
 def test_sphere2M_in_the_benchmark_configuration(H, orc, kernel):
     """The benchmark's workload and launch configuration: 2,097,152-triangle
     sphere, m 4, leaf 32, eta 2, 8 right-hand sides, autotuned launches.
-    FP64 tier: 24 sampled rows against the dense definition, which the oracle
-    computes row by row, at the stated H^2 error.  The oracle's own H^2 product
-    (equal to the FP64 tier to 1e-10) measures 2.7e-4 (G) and 3.3e-2 (K) on
-    exactly these rows and right-hand sides; K's error at fixed m grows with n
-    (4.4e-3 at 32k, 1.6e-2 at 524k).  Mixed tier: all rows against the FP64
-    tier at the mixed tolerance."""
+      - Both tiers against the oracle's H^2 product (section 2, eq. (vsw)) on
+        64 seeded rows, which the oracle computes one by one after its own
+        upward pass: FP64 at 1e-10, mixed at 1e-6, in the 2-norm and per row.
+      - The mixed tier against the FP64 tier on all rows.
+      - The FP64 tier against 24 rows of the dense definition (eq. (slp) /
+        eq. (dlp)) at the stated H^2 error: measured 2.7e-4 (G) and 3.3e-2
+        (K); K's error at fixed m grows with n (4.4e-3 at 32k, 1.6e-2 at
+        524k)."""
     import torch
 
     mesh = I.sphere(512)
     xn = I.rhs(mesh.nt, 8, seed=3)
+    rows = np.sort(np.random.default_rng(20010552).choice(mesh.nt, 64, replace=False))
+    ref = orc.H2(mesh, kernel, m=4, eta=2.0, leaf=32).rows(rows, xn)
     x = torch.from_numpy(xn).cuda()
     ys = {}
     for prec in ("fp64", "mixed_fp32"):
@@ -235,13 +238,34 @@ def test_sphere2M_in_the_benchmark_configuration(H, orc, kernel):
         for _ in range(2):  # the first apply tunes the launch variants
             op.apply(x, y)
         torch.cuda.synchronize()
-        ys[prec] = y.clone()
+        ys[prec] = y.cpu().numpy()
         op.close()
-    err = float(torch.linalg.norm(ys["mixed_fp32"] - ys["fp64"]) / torch.linalg.norm(ys["fp64"]))
-    assert err < TOL["mixed_fp32"], err
-    rows = np.random.default_rng(1).choice(mesh.nt, 24, replace=False)
-    d = orc.dense_rows(kernel, mesh, rows, xn)
-    assert rel(ys["fp64"].cpu().numpy()[:, rows], d) < (1e-3 if kernel == 0 else 6e-2)
+        close(ys[prec][:, rows], ref, TOL[prec], f"2M {prec} kernel {kernel} vs oracle H2 rows")
+    close(ys["mixed_fp32"], ys["fp64"], TOL["mixed_fp32"], f"2M mixed vs fp64 kernel {kernel}")
+    drows = np.random.default_rng(1).choice(mesh.nt, 24, replace=False)
+    d = orc.dense_rows(kernel, mesh, drows, xn)
+    assert rel(ys["fp64"][:, drows], d) < (1e-3 if kernel == 0 else 6e-2)
+
+
+@pytest.mark.slow
+def test_ellipsoid131k_m5_16rhs_full_size(H, orc):
+    """Ellipsoid (1, 0.5, 0.25) with 131,072 triangles, m 5 (k = 125), 16
+    right-hand sides, single layer: every tier against the oracle's full H^2
+    product at the tier's tolerance (tensor-core tiers: the operand-rounding
+    bounds of tests/test_gpu_tc.py)."""
+    import torch
+
+    mesh = I.ellipsoid(128)
+    xn = I.rhs(mesh.nt, 16, seed=13)
+    ref = orc.H2(mesh, 0, m=5, eta=2.0, leaf=32).matvec(xn)
+    x = torch.from_numpy(xn).cuda()
+    tol = dict(TOL, mixed_tf32=1e-3, mixed_bf16=1e-2)
+    for prec in ("fp64", "mixed_fp32", "mixed_tf32", "mixed_bf16"):
+        op = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=5, eta=2.0, leaf_size=32, precision=prec)
+        y = op.apply(x)
+        torch.cuda.synchronize()
+        close(y.cpu().numpy(), ref, tol[prec], f"131k ellipsoid m5 {prec}")
+        op.close()
 
 
 def test_mixed_fp32_dlp_transpose_on_flat_faces(H, orc):
@@ -251,7 +275,7 @@ def test_mixed_fp32_dlp_transpose_on_flat_faces(H, orc):
     x = I.rhs(mesh.nt, 2, seed=9)
     y = gpu_apply(H, mesh, x, kernel=1, precision="mixed_fp32", transpose=True)
     ref = orc.H2(mesh, 1, m=4).matvec(x, transpose=True)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -260,7 +284,7 @@ def test_mixed_fp32_transpose_matches_oracle(H, orc, kernel):
     x = I.rhs(mesh.nt, 3, seed=12)
     y = gpu_apply(H, mesh, x, kernel=kernel, precision="mixed_fp32", transpose=True)
     ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=True)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 def test_mixed_fp32_m5_ellipsoid_16rhs(H, orc):
@@ -269,7 +293,7 @@ def test_mixed_fp32_m5_ellipsoid_16rhs(H, orc):
     x = I.rhs(mesh.nt, 16, seed=13)
     y = gpu_apply(H, mesh, x, kernel=0, m=5, precision="mixed_fp32")
     ref = orc.H2(mesh, 0, m=5).matvec(x)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 def test_regular_evals_count(H, orc):
@@ -309,7 +333,7 @@ def test_recomputed_bases_equal_stored(H, orc, precision, kernel, transpose):
         ys.append(op.apply(xd, transpose=transpose).cpu().numpy())
         op.close()
     ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)
-    assert rel(ys[1], ref) < TOL[precision]
+    close(ys[1], ref, TOL[precision])
     assert rel(ys[0], ys[1]) < (1e-13 if precision == "fp64" else 1e-6)
 
 
@@ -324,7 +348,7 @@ def test_mixed_with_fp64_singular_points(H, orc, kernel):
     y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
     op.close()
     ref = orc.H2(mesh, kernel, m=4).matvec(x)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])

@@ -36,8 +36,7 @@ def H():
     return h2bem
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from tests._parity import close, rel  # noqa: E402
 
 
 def apply_np(op, x, transpose=False):
@@ -74,7 +73,7 @@ def test_stored_matches_oracle(H, orc, name, kernel, precision):
     x = I.rhs(mesh.nt, 3, seed=11)
     y, st = stored_apply(H, mesh, x, kernel=kernel, precision=precision)
     ref = orc.H2(mesh, kernel, m=4).matvec(x)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
     es = 8 if precision == "fp64" else 4
     # every ordered nearfield pair once, plus the odd leading dimension and 16-byte padding
     assert st["near_pairs"] * es <= st["near_stored_bytes"] <= 1.3 * st["near_pairs"] * es
@@ -87,7 +86,7 @@ def test_stored_transpose(H, orc, kernel, precision):
     x = I.rhs(mesh.nt, 2, seed=9)
     y, _ = stored_apply(H, mesh, x, kernel=kernel, precision=precision, transpose=True)
     ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=True)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -99,13 +98,13 @@ def test_stored_equals_on_the_fly_on_cube(H, orc, kernel, transpose):
     mesh = I.jitter(I.cube(9), 0.01, 3)
     x = I.rhs(mesh.nt, 2, seed=9)
     y, _ = stored_apply(H, mesh, x, kernel=kernel, transpose=transpose)
-    assert rel(y, orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)) < TOL["fp64"]
+    close(y, orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose), TOL["fp64"])
     ys, _ = stored_apply(H, mesh, x, kernel=kernel, precision="mixed_fp32", transpose=transpose)
     a = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, precision="mixed_fp32")
     yf = apply_np(a, x, transpose)
     a.close()
-    assert rel(ys, yf) < 3e-7
-    assert rel(ys, orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)) < TOL["mixed_fp32"]
+    close(ys, yf, 3e-7)
+    close(ys, orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose), TOL["mixed_fp32"])
 
 
 @pytest.mark.parametrize("nrhs", [1, 4, 5, 8, 16, 21])
@@ -116,7 +115,7 @@ def test_stored_rhs_widths(H, orc, nrhs, precision):
     x = I.rhs(mesh.nt, nrhs, seed=nrhs)
     y, _ = stored_apply(H, mesh, x, kernel=1, precision=precision)
     ref = orc.H2(mesh, 1, m=4).matvec(x)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 @pytest.mark.parametrize("leaf", [1, 7, 33, 64])
@@ -129,7 +128,7 @@ def test_stored_leaf_sizes(H, orc, leaf, kernel):
     for tr in (False, True):
         y, _ = stored_apply(H, mesh, x, kernel=kernel, leaf=leaf, transpose=tr)
         ref = orc.H2(mesh, kernel, m=4, leaf=leaf).matvec(x, transpose=tr)
-        assert rel(y, ref) < 1e-10, (leaf, tr)
+        close(y, ref, 1e-10)
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -143,8 +142,8 @@ def test_stored_dense_equals_oracle_matrix_and_repeats_bitwise(H, orc, kernel, p
     yt = apply_np(op, x, transpose=True)
     op.close()
     A = orc.dense_matrix(kernel, mesh)
-    assert rel(y1, x @ A.T) < TOL[precision]
-    assert rel(yt, x @ A) < TOL[precision]
+    close(y1, x @ A.T, TOL[precision])
+    close(yt, x @ A, TOL[precision])
     assert np.array_equal(y1, y2)
 
 
@@ -159,7 +158,7 @@ def test_stored_equals_on_the_fly_with_cache_and_fp64_singular(H):
             ya = apply_np(a, x)
             a.close()
             yb, _ = stored_apply(H, mesh, x, kernel=kernel, precision="mixed_fp32", **kw)
-            assert rel(yb, ya) < 5e-7, (kw, kernel)
+            close(yb, ya, 5e-7)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
@@ -172,7 +171,7 @@ def test_stored_batch(H, orc, precision):
     for k, mh in enumerate(meshes):
         a, b = int(np.sum([m.nt for m in meshes[:k]])), int(np.sum([m.nt for m in meshes[:k + 1]]))
         ref = orc.H2(mh, 0, m=4).matvec(np.ascontiguousarray(x[:, a:b]))
-        assert rel(y[:, a:b], ref) < TOL[precision]
+        close(y[:, a:b], ref, TOL[precision])
 
 
 def test_stored_graph_replay_and_noalloc(H, orc):
@@ -192,13 +191,13 @@ def test_stored_graph_replay_and_noalloc(H, orc):
         with torch.cuda.stream(s):
             H.h2bem_apply(op.op, xd, yd, s)
         s.synchronize()
-        assert rel(yd.cpu().numpy(), ref) < 1e-6
+        close(yd.cpu().numpy(), ref, 1e-6)
     y2 = torch.full_like(xd, float("nan"))
     rc = H.lib().h2bem_apply_noalloc(op.op, ctypes.c_void_p(xd.data_ptr()), xd.shape[1], xd.shape[0],
                                      ctypes.c_void_p(y2.data_ptr()), y2.shape[1], None)
     torch.cuda.synchronize()
     assert rc == H.H2BEM_OK
-    assert rel(y2.cpu().numpy(), ref) < 1e-6
+    close(y2.cpu().numpy(), ref, 1e-6)
     op.close()
 
 
@@ -222,4 +221,4 @@ def test_stored_dtn_solve_matches_on_the_fly(H):
         out.append(xd.cpu().numpy())
         G.close()
         K.close()
-    assert rel(out[1], out[0]) < 1e-5
+    close(out[1], out[0], 1e-5)

@@ -34,8 +34,7 @@ def H():
     return h2bem
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from tests._parity import close, rel  # noqa: E402
 
 
 def run(H, mesh, x, kernel=0, m=4, precision="mixed_tf32", transpose=False, leaf=32):
@@ -58,7 +57,7 @@ def test_slp_tiers_match_oracle(H, orc, precision, nrhs):
     x = I.rhs(mesh.nt, nrhs, seed=40 + nrhs)
     y = run(H, mesh, x, precision=precision)
     ref = orc.H2(mesh, 0, m=4).matvec(x)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 @pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_bf16"])
@@ -69,7 +68,7 @@ def test_tc_orders(H, orc, precision, m):
     x = I.rhs(mesh.nt, 3, seed=m)
     y = run(H, mesh, x, m=m, precision=precision)
     ref = orc.H2(mesh, 0, m=m).matvec(x)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 @pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_bf16", "mixed_fp32"])
@@ -78,7 +77,7 @@ def test_slp_transpose(H, orc, precision):
     x = I.rhs(mesh.nt, 2, seed=9)
     y = run(H, mesh, x, precision=precision, transpose=True)
     ref = orc.H2(mesh, 0, m=4).matvec(x, transpose=True)
-    assert rel(y, ref) < TOL[precision]
+    close(y, ref, TOL[precision])
 
 
 @pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_bf16"])
@@ -88,7 +87,7 @@ def test_dlp_keeps_simt_coupling(H, orc, precision, transpose):
     x = I.rhs(mesh.nt, 2, seed=5)
     y = run(H, mesh, x, kernel=1, precision=precision, transpose=transpose)
     ref = orc.H2(mesh, 1, m=4).matvec(x, transpose=transpose)
-    assert rel(y, ref) < TOL["mixed_fp32"]
+    close(y, ref, TOL["mixed_fp32"])
 
 
 def test_tiers_ordered_by_operand_precision(H):

@@ -26,8 +26,7 @@ def H():
     return h2bem
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from tests._parity import close, rel  # noqa: E402
 
 
 def apply(H, mesh, x, tune, precision="fp64", kernel=0, transpose=False):
@@ -53,7 +52,8 @@ def test_fixed_variants_match_oracle(H, orc, v):
     ref = orc.H2(mesh, 0, m=4).matvec(x)
     for prec in ("fp64", "mixed_fp32"):
         (y1, y2), st = apply(H, mesh, x, 2 + v, precision=prec)
-        assert rel(y1, ref) < TOL[prec] and rel(y2, ref) < TOL[prec]
+        close(y1, ref, TOL[prec])
+        close(y2, ref, TOL[prec])
         near_p, near_nb, nsl, coup_p, tuned = st["launch_variant"]
         assert (near_p, coup_p, nsl, tuned) == (v & 1, (v >> 1) & 1, (2, 4, 8)[(v // 4) % 3], 1)
         assert near_nb == ((4, 3, 2)[v // 12] if prec == "mixed_fp32" else 2)
@@ -65,11 +65,12 @@ def test_autotuner_choice_is_valid_and_correct(H, orc, kernel, transpose):
     x = I.rhs(mesh.nt, 4, seed=3)
     ref = orc.H2(mesh, kernel, m=4).matvec(x, transpose=transpose)
     (y_first, y_second), st = apply(H, mesh, x, 1, kernel=kernel, transpose=transpose)
-    assert rel(y_first, ref) < TOL["fp64"] and rel(y_second, ref) < TOL["fp64"]
+    close(y_first, ref, TOL["fp64"])
+    close(y_second, ref, TOL["fp64"])
     near_p, near_nb, nsl, coup_p, tuned = st["launch_variant"]
     assert tuned == 1 and near_p in (0, 1) and coup_p in (0, 1) and nsl in (2, 4, 8) and near_nb in (2, 3, 4)
     (d1, _), _ = apply(H, mesh, x, 0, kernel=kernel, transpose=transpose)
-    assert rel(y_second, d1) < 1e-13
+    close(y_second, d1, 1e-13)
 
 
 def test_autotune_rejects_bad_values(H):
