@@ -306,11 +306,18 @@ int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
  * synchronisation a cudaMalloc/cudaFree may imply.  This call allocates
  * nothing: its work vectors live in a fixed 64 MiB array inside the library,
  * present on every GPU that loads the library until the process exits.
- *   - x and y must be device memory (no host staging); they must not overlap.
- *   - The work space needed is 2 n NRp 8 + 2 nclusters k NRp e bytes, NRp
- *     being min(nrhs,16) rounded up to 1, 4, 8 or 16 and e = 8 for the FP64
- *     tier or the double layer, else 4; an operator that needs more than
- *     64 MiB is rejected with H2BEM_ERR_ARG (use h2bem_apply).
+ *   - x and y must be device memory of the current device (no host
+ *     staging); they must not overlap.  The operator must have been created
+ *     with that device current.
+ *   - The work space needed is 2 n NRp 8 + 2 nclusters k NRp e + n nx b
+ *     bytes, every term rounded up to a multiple of 256.  NRp is min(nrhs,16)
+ *     rounded up to 1, 4, 8 or 16; e = 8 for the FP64 tier or the double
+ *     layer, else 4.  The last term is x in the stored nearfield's precision
+ *     or in FP32 for the singular row gather: b = 4, nx = max(NRp, 4) in the
+ *     MIXED tiers unless opts.singular_fp64 is set without opts.store_near;
+ *     b = 8, nx = 2 in the FP64 tier with opts.store_near and NRp = 1; else
+ *     0.  An operator that needs more than 64 MiB is rejected with
+ *     H2BEM_ERR_ARG (use h2bem_apply).
  *   - The first call on a device looks up the array's device address (once,
  *     with that device current); make that first call before any stream
  *     capture.
@@ -318,8 +325,13 @@ int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
  *     overwritten by every call: calls that may overlap on the GPU (on
  *     different streams, or from different threads without ordering) race
  *     and give wrong results.  Calls on one stream are ordered and safe.
- *   - Enqueued on `stream`; returns once the work is enqueued.
- * Errors: ARG (null, nrhs, ld, host pointers, work space too large), CUDA. */
+ *   - Enqueued on `stream`; returns once the work is enqueued.  The launch
+ *     sequence is h2bem_apply's (without autotuning: the launch variants are
+ *     those an earlier h2bem_apply tuned, else the defaults).  An expired
+ *     bounded wait of the tensor-core coupling is reported, as for
+ *     h2bem_apply_timed, by the next h2bem_stats_get (H2BEM_ERR_TIMEOUT).
+ * Errors: ARG (null, nrhs, ld, host pointers or another device's memory,
+ * work space too large), CUDA. */
 int h2bem_apply_noalloc(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
 
 #ifdef __cplusplus

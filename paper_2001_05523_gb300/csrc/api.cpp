@@ -1507,12 +1507,31 @@ static void launch_cfgs(h2bem_op* op, int NR, bool transpose, h2::LaunchCfg& nea
     op->last_variant[4] = tu.done ? 1 : 0;
 }
 
+// Work vectors of one chunk: tree-ordered x and y (FP64, RHS-interleaved),
+// the cluster vectors x-hat and y-hat, and x in FP32 for the singular row
+// gather / the stored nearfield (store_x_bytes).
+struct Work {
+    double* xp;
+    double* yp;
+    void* xh;
+    void* yh;
+    void* xs;
+};
+
 // One chunk of at most 16 right-hand sides, device buffers, tree order work.
+// ext = NULL: the operator's own work vectors (allocated or grown here);
+// otherwise caller-provided ones of work_bytes() (no allocation, no tuning).
 static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, cudaStream_t s,
-                       bool transpose, bool timed, bool xmapped = false) {
+                       bool transpose, bool timed, bool xmapped = false, const Work* ext = nullptr) {
     const int NR = pad_nr(nrhs);
-    int rc = ensure_workspace(op, NR);
-    if (rc) return rc;
+    Work w;
+    if (ext) {
+        w = *ext;
+    } else {
+        int rc = ensure_workspace(op, NR);
+        if (rc) return rc;
+        w = Work{op->xp.as<double>(), op->yp.as<double>(), op->xh.p, op->yh.p, op->xs.p};
+    }
     const bool fp32 = op->precision != H2BEM_FP64;
     const bool xh64 = xh_is64(op, transpose), yh64 = yh_is64(op, transpose);
     const size_t ysz = yh64 ? sizeof(double) : sizeof(float);
@@ -1533,22 +1552,22 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     // autotuning on the first apply of this width and direction (not under capture)
     auto& tu = op->tuned[nr_slot(NR)][transpose ? 1 : 0];
     bool tune_now = false;
-    if (op->autotune && !tu.done) {
+    if (op->autotune && !tu.done && !ext) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         tune_now = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
     }
     auto near_launch = [&](const h2::LaunchCfg& cf) {
         h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
                             op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR,
-                            op->xp.as<double>(), op->yp.as<double>(), cf, s);
+                            w.xp, w.yp, cf, s);
     };
     mark(0);
     if (xmapped)  // x in mapped host memory: read in the caller's order
-        h2::launch_permute_in_scatter(x, ldx, nrhs, NR, op->iperm.as<int>(), n, op->xp.as<double>(), s);
+        h2::launch_permute_in_scatter(x, ldx, nrhs, NR, op->iperm.as<int>(), n, w.xp, s);
     else
-        h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, op->xp.as<double>(), s);
+        h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, w.xp, s);
     // the stored nearfield writes every row of y first; otherwise the stages add to zero
-    if (!op->store_near) CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+    if (!op->store_near) CU(cudaMemsetAsync(w.yp, 0, op->n * NR * sizeof(double), s));
     if (tune_now && op->near_u.nrows() > 0 && !op->store_near) {
         float best = 1e30f;
         const bool budgets = fp32 && !dlp;  // register-budget variants exist for the FP32 single layer
@@ -1566,7 +1585,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                 }
             }
         }
-        CU(cudaMemsetAsync(op->yp.p, 0, op->n * NR * sizeof(double), s));
+        CU(cudaMemsetAsync(w.yp, 0, op->n * NR * sizeof(double), s));
     }
     if (tune_now && op->nfar > 0 && tc_kind(op, xh64, yh64) < 0 && (op->m == 4 || op->m == 5)) {
         tu.coup.nsl = -1;  // tuned below, once x-hat is ready
@@ -1577,23 +1596,23 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     const int fo = op->store_near ? 1 : 0;
     op->stage_order = fo;
     if (op->store_near) {
-        nl += near_stored_apply(op, NR, transpose, op->xp.as<double>(), op->yp.as<double>(), op->xs.p, s);
+        nl += near_stored_apply(op, NR, transpose, w.xp, w.yp, w.xs, s);
         mark(2);
     }
     if (op->nfar > 0) {
-        CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
+        CU(cudaMemsetAsync(w.yh, 0, (size_t)op->nc * op->k * NR * ysz, s));
         // the double layer's differentiated basis is evaluated in FP64 in every tier
         if (op->recompute_basis)
             h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
-                                    in_dlp, fp32 && !in_dlp, xh64, NR, op->xp.as<double>(), op->xh.p, s);
+                                    in_dlp, fp32 && !in_dlp, xh64, NR, w.xp, w.xh, s);
         else
             h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                            fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
-                                           op->xp.as<double>(), op->xh.p, s);
+                                           w.xp, w.xh, s);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2 + fo);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p, s);
+            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, s);
         mark(3 + fo);
         if (tune_now && tu.coup.nsl == -1) {
             float best = 1e30f;
@@ -1602,7 +1621,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                     h2::LaunchCfg cf;
                     cf.nsl = nsl;
                     cf.work = pers ? op->work.as<int>() + 1 : nullptr;
-                    const float ms = time_on(s, [&] { run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, cf, s); });
+                    const float ms = time_on(s, [&] { run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cf, s); });
                     if (ms < best) {
                         best = ms;
                         tu.coup.nsl = nsl;
@@ -1616,18 +1635,18 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         }
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
-        run_coupling(op, t, c, far, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
+        run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, s);
         mark(4 + fo);
         for (size_t L = 0; L < op->level_parents.size(); ++L)
-            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, op->yh.p, s);
+            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, s);
         mark(5 + fo);
         if (op->recompute_basis)
             h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
-                                     out_dlp, fp32 && !out_dlp, yh64, NR, op->yh.p, op->yp.as<double>(), s);
+                                     out_dlp, fp32 && !out_dlp, yh64, NR, w.yh, w.yp, s);
         else
             h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                             fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p,
-                                            op->yh.p, op->yp.as<double>(), s);
+                                            w.yh, w.yp, s);
     } else {
         for (int i = 2 + fo; i <= 5 + fo; ++i) mark(i);
     }
@@ -1635,7 +1654,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     if (op->store_near) {
         mark(7);
         mark(8);
-        h2::launch_permute_out(op->yp.as<double>(), NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+        h2::launch_permute_out(w.yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
         nl += 1;
         op->launches += nl;
         mark(9);
@@ -1651,23 +1670,23 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
-    if (op->sing_gather) nl += sing_gather_apply(op, NR, transpose, op->xp.as<double>(), op->yp.as<double>(), op->xs.p, s);
+    if (op->sing_gather) nl += sing_gather_apply(op, NR, transpose, w.xp, w.yp, w.xs, s);
     for (int ty = 0; ty < 3 && !op->sing_gather; ++ty) {
         if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
         const int np = (int)op->sp_count[ty];
         nl += np > 0 ? 1 : 0;
         if (op->cache_singular)
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                                nullptr, nullptr, 0, 2, false, transpose, NR, op->xp.as<double>(), op->yp.as<double>(),
+                                nullptr, nullptr, 0, 2, false, transpose, NR, w.xp, w.yp,
                                 op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
         else
             h2::launch_singular(g, h2::IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
                                 op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0,
                                 fp32 && !op->singular_fp64, transpose,
-                                NR, op->xp.as<double>(), op->yp.as<double>(), nullptr, nullptr, s);
+                                NR, w.xp, w.yp, nullptr, nullptr, s);
     }
     mark(8);
-    h2::launch_permute_out(op->yp.as<double>(), NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+    h2::launch_permute_out(w.yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
     nl += 1;
     op->launches += nl;
     mark(9);
@@ -2037,7 +2056,7 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
 
 // ===========================================================================
 // apply into caller-provided work vectors (used by the allocation-free entry
-// point in noalloc.cu; the sequence of kernels is the one of apply_chunk)
+// point in noalloc.cu): apply_chunk's launch sequence on those vectors
 // ===========================================================================
 namespace h2 {
 
@@ -2062,71 +2081,9 @@ int apply_with_work(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double
     const bool wide = op->precision == H2BEM_FP64 || op->kernel == H2BEM_DLP;
     const size_t vb = up((size_t)op->n * NR * sizeof(double));
     const size_t hb = up((size_t)op->nc * op->k * NR * (wide ? sizeof(double) : sizeof(float)));
-    double* xp = reinterpret_cast<double*>(work);
-    double* yp = reinterpret_cast<double*>(work + vb);
-    void* xh = work + 2 * vb;
-    void* yh = work + 2 * vb + hb;
-    void* xs = work + 2 * vb + 2 * hb;
-    const bool fp32 = op->precision != H2BEM_FP64;
-    const bool xh64 = xh_is64(op, false), yh64 = yh_is64(op, false);
-    const h2::Geom g = op->geom();
-    const h2::Tree t = op->tree();
-    const h2::Consts& c = op->consts;
-    const int n = (int)op->n;
-    const bool dlp = op->kernel == H2BEM_DLP;
-    const int near_ker = dlp ? h2::DLP : h2::SLP;
-    launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, xp, s);
-    if (op->store_near) near_stored_apply(op, NR, false, xp, yp, xs, s);  // writes every row of yp
-    else CU(cudaMemsetAsync(yp, 0, vb, s));
-    if (op->nfar > 0) {
-        CU(cudaMemsetAsync(yh, 0, hb, s));
-        if (op->recompute_basis)
-            launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), dlp,
-                                fp32 && !dlp, xh64, NR, xp, xh, s);
-        else
-            launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
-                                       fp32 && !dlp, xh64, NR, dlp ? op->basisW.p : op->basisV.p, xp, xh, s);
-        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-            launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
-        h2::LaunchCfg cfg_near, cfg_coup;
-        launch_cfgs(op, NR, false, cfg_near, cfg_coup);
-        run_coupling(op, t, c, op->far, xh64, yh64, NR, xh, yh, cfg_coup, s);
-        for (size_t L = 0; L < op->level_parents.size(); ++L)
-            launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
-        if (op->recompute_basis)
-            launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
-                                 fp32, yh64, NR, yh, yp, s);
-        else
-            launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
-                                        yh64, NR, op->basisV.p, yh, yp, s);
-    }
-    if (op->store_near) {
-        launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
-        CU(cudaGetLastError());
-        return H2BEM_OK;
-    }
-    {
-        h2::LaunchCfg cfg_near, cfg_coup;
-        launch_cfgs(op, NR, false, cfg_near, cfg_coup);
-        launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
-                        op->near_u.dcol.as<int>(), near_ker, false, fp32, NR, xp, yp, cfg_near, s);
-    }
-    if (op->sing_gather) sing_gather_apply(op, NR, false, xp, yp, xs, s);
-    for (int ty = 0; ty < 3 && !op->sing_gather; ++ty) {
-        if (ty == 0 && dlp) continue;
-        const int np = (int)op->sp_count[ty];
-        if (op->cache_singular)
-            launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(), nullptr,
-                            nullptr, 0, 2, false, false, NR, xp, yp, op->sp_v0[ty].as<double>(), op->sp_v1[ty].as<double>(), s);
-        else
-            launch_singular(g, IDENTICAL - ty, near_ker, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
-                            op->sp_code[ty].as<int>(), op->sp_tab[ty].as<double>(), op->sp_npts[ty], 0,
-                            fp32 && !op->singular_fp64, false, NR, xp,
-                            yp, nullptr, nullptr, s);
-    }
-    launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
-    CU(cudaGetLastError());
-    return H2BEM_OK;
+    const Work w{reinterpret_cast<double*>(work), reinterpret_cast<double*>(work + vb), work + 2 * vb,
+                 work + 2 * vb + hb, store_x_bytes(op, NR) ? work + 2 * vb + 2 * hb : nullptr};
+    return apply_chunk(op, x, ldx, nrhs, y, ldy, s, false, false, false, &w);
 }
 
 }  // namespace h2

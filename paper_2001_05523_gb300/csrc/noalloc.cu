@@ -52,13 +52,20 @@ int scratch_address(unsigned char** out) {
     return H2BEM_OK;
 }
 
+// Device (or managed) memory of the current device: the scratch array used is
+// the current device's, so buffers of another GPU are refused.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -77,7 +84,7 @@ extern "C" int h2bem_apply_noalloc(h2bem_op* op, const double* x, int64_t ldx, i
         if (xb < ye && yb < xe) return h2::set_error(H2BEM_ERR_ARG, "apply_noalloc: x and y overlap");
     }
     if (!on_device(x) || !on_device(y))
-        return h2::set_error(H2BEM_ERR_ARG, "apply_noalloc: x and y must be device memory");
+        return h2::set_error(H2BEM_ERR_ARG, "apply_noalloc: x and y must be device memory of the current device");
     const int chunk = nrhs < 16 ? nrhs : 16;
     const int NR = chunk <= 1 ? 1 : chunk <= 4 ? 4 : chunk <= 8 ? 8 : 16;
     const size_t need = h2::work_bytes(op, NR);

@@ -17,7 +17,7 @@ from paper_2001_05523_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed_fp32": 1e-6}
+TOL = {"fp64": 1e-10, "mixed_fp32": 1e-6, "mixed_tf32": 1e-6, "mixed_bf16": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -42,12 +42,22 @@ def _noalloc(H, op, x, y):
     return rc
 
 
-@pytest.mark.parametrize("kernel,precision", [(0, "fp64"), (1, "fp64"), (0, "mixed_fp32"), (1, "mixed_fp32")])
-def test_noalloc_matches_apply_twice(H, kernel, precision):
+# Every tier, and the options that change the launch sequence (recomputed
+# bases, cached singular entries, FP64 singular points, stored nearfield).
+# The tensor-core tiers run the same kernels in both calls, so they are held to
+# the FP32 tier's tolerance against each other.
+CASES = [(0, "fp64", {}), (1, "fp64", {}), (0, "mixed_fp32", {}), (1, "mixed_fp32", {}), (0, "mixed_tf32", {}),
+         (0, "mixed_bf16", {}), (0, "mixed_fp32", {"recompute_basis": True}), (1, "fp64", {"recompute_basis": True}),
+         (0, "mixed_fp32", {"cache_singular": True}), (1, "mixed_fp32", {"singular_fp64": True}),
+         (0, "mixed_bf16", {"store_near": True}), (1, "fp64", {"store_near": True})]
+
+
+@pytest.mark.parametrize("kernel,precision,opts", CASES)
+def test_noalloc_matches_apply_twice(H, kernel, precision, opts):
     import torch
 
     mesh = I.jitter(I.sphere(18), 0.01, 21)
-    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, eta=2.0, precision=precision)
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, eta=2.0, precision=precision, **opts)
     x = torch.from_numpy(I.rhs(mesh.nt, 5, seed=31)).cuda()
     ref = torch.empty_like(x)
     H.h2bem_apply(op.op, x, ref)
