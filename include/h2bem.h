@@ -313,8 +313,9 @@ int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
  *     bytes, every term rounded up to a multiple of 256.  NRp is min(nrhs,16)
  *     rounded up to 1, 4, 8 or 16; e = 8 for the FP64 tier or the double
  *     layer, else 4.  The last term is x in the stored nearfield's precision
- *     or in FP32 for the singular row gather: b = 4, nx = max(NRp, 4) in the
- *     MIXED tiers unless opts.singular_fp64 is set without opts.store_near;
+ *     or in FP32 for the regular nearfield and the singular row gather:
+ *     b = 4, nx = max(NRp, 4) in the MIXED tiers (for the double layer
+ *     without opts.store_near only unless opts.singular_fp64 is set);
  *     b = 8, nx = 2 in the FP64 tier with opts.store_near and NRp = 1; else
  *     0.  An operator that needs more than 64 MiB is rejected with
  *     H2BEM_ERR_ARG (use h2bem_apply).

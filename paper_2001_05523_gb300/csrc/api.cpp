@@ -575,7 +575,7 @@ struct h2bem_op {
     int64_t regular_evals = 0;  // pairs evaluated by the regular nearfield kernel
     h2::Consts consts{};
     // device geometry and tree
-    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef;
+    DevBuf xyz, tri, perm, iperm, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef, areaf;
     DevBuf cbegin, cend, cchild0, cchild1, cbox, czhl, cetr, leaves, basis_rule;
     std::vector<int> leaves_h;
     int max_leaf = 0;               // largest leaf cluster
@@ -652,7 +652,8 @@ struct h2bem_op {
     h2::Geom geom() const {
         return h2::Geom{(int)n, v.as<const double>(), area.as<const double>(), nrm.as<const double>(),
                         ctr.as<const double>(), vid.as<const int>(), qo.as<const float>(), qa.as<const double>(),
-                        chl.as<const float>(), plane.as<const double>(), nef.as<const float>()};
+                        chl.as<const float>(), plane.as<const double>(), nef.as<const float>(),
+                        areaf.as<const float>()};
     }
     h2::Tree tree() const {
         return h2::Tree{(int)nc, cbegin.as<const int>(), cend.as<const int>(), cchild0.as<const int>(),
@@ -1199,12 +1200,13 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         (rc = op->nrm.alloc(3 * n * sizeof(double))) || (rc = op->ctr.alloc(3 * n * sizeof(double))) ||
         (rc = op->vid.alloc(3 * n * sizeof(int))) || (rc = op->qo.alloc(21 * n * sizeof(float))) ||
         (rc = op->qa.alloc(21 * n * sizeof(double))) || (rc = op->chl.alloc(6 * n * sizeof(float))) ||
-        (rc = op->plane.alloc(n * sizeof(double))) || (rc = op->nef.alloc(12 * n * sizeof(float))))
+        (rc = op->plane.alloc(n * sizeof(double))) || (rc = op->nef.alloc(12 * n * sizeof(float))) ||
+        (rc = op->areaf.alloc(n * sizeof(float))))
         return rc;
     h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->consts, op->v.as<double>(),
                     op->area.as<double>(), op->nrm.as<double>(), op->ctr.as<double>(), op->vid.as<int>(),
                     op->qo.as<float>(), op->qa.as<double>(), op->chl.as<float>(), op->plane.as<double>(),
-                    op->nef.as<float>(), 0);
+                    op->nef.as<float>(), op->areaf.as<float>(), 0);
     CU(cudaGetLastError());
     // leaf bases: V_t[i, nu] = int L_nu; for the double layer also W_s[j, nu] = int n_j . grad L_nu
     for (int l : op->leaves_h) op->max_leaf = std::max(op->max_leaf, (int)(tree->end[l] - tree->begin[l]));
@@ -1374,12 +1376,19 @@ static bool yh_is64(const h2bem_op* op, bool tr) {
     return op->precision == H2BEM_FP64 || (op->kernel == H2BEM_DLP && tr);
 }
 
+// The regular nearfield of the FP32 single layer reads x in FP32 (xs).
+static bool near_reads_xs(const h2bem_op* op) {
+    return !op->store_near && op->precision != H2BEM_FP64 && op->kernel == H2BEM_SLP;
+}
+
 // x in the stored nearfield's precision (FP32 tiers, or a single FP64 column
-// padded to 16 bytes), or in FP32 for the singular row gather; 0 where
-// neither needs it (the stored FP64 apply reads x directly)
+// padded to 16 bytes), or in FP32 for the singular row gather and the FP32
+// single layer's regular nearfield; 0 where none needs it (the stored FP64
+// apply reads x directly)
 static size_t store_x_bytes(const h2bem_op* op, int NR) {
     const bool f32 = op->precision != H2BEM_FP64;
-    if (!op->store_near) return op->sing_gather ? (size_t)op->n * h2::near_store_nx(true, NR) * sizeof(float) : 0;
+    if (!op->store_near)
+        return (op->sing_gather || near_reads_xs(op)) ? (size_t)op->n * h2::near_store_nx(true, NR) * sizeof(float) : 0;
     if (!f32 && NR > 1) return 0;
     return (size_t)op->n * h2::near_store_nx(f32, NR) * (f32 ? sizeof(float) : sizeof(double));
 }
@@ -1388,7 +1397,7 @@ static size_t store_x_bytes(const h2bem_op* op, int NR) {
 // pair (evaluated here unless cached), x in FP32, and one gather launch;
 // returns the number of launches.
 static int64_t sing_gather_apply(const h2bem_op* op, int NR, bool transpose, const double* xp, double* yp, void* xs,
-                                 cudaStream_t s) {
+                                 bool xs_ready, cudaStream_t s) {
     const h2::Geom g = op->geom();
     const bool dlp = op->kernel == H2BEM_DLP;
     int64_t nl = 0;
@@ -1404,9 +1413,9 @@ static int64_t sing_gather_apply(const h2bem_op* op, int NR, bool transpose, con
             nl += np > 0 ? 1 : 0;
         }
     const float* vals = (op->cache_singular && tr) ? op->sg_vals_t.as<float>() : op->sg_vals.as<float>();
-    h2::launch_store_x(true, (int)op->n, NR, xp, xs, s);
+    if (!xs_ready) h2::launch_store_x(true, (int)op->n, NR, xp, xs, s);
     h2::launch_sing_gather(NR, (int)op->n, op->sg_ptr.as<int>(), op->sg_other.as<int>(), vals, (const float*)xs, yp, s);
-    return nl + 2;
+    return nl + (xs_ready ? 1 : 2);
 }
 
 // Nearfield of an apply from the stored blocks (x converted first where
@@ -1559,7 +1568,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     auto near_launch = [&](const h2::LaunchCfg& cf) {
         h2::launch_near_sym(g, t, c, op->near_u.nrows(), op->near_u.drows.as<int>(), op->near_u.dptr.as<int>(),
                             op->near_u.dcol.as<int>(), dlp ? h2::DLP : h2::SLP, transpose, fp32, NR,
-                            w.xp, w.yp, cf, s);
+                            w.xp, (const float*)w.xs, w.yp, cf, s);
     };
     mark(0);
     if (xmapped)  // x in mapped host memory: read in the caller's order
@@ -1568,6 +1577,12 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, w.xp, s);
     // the stored nearfield writes every row of y first; otherwise the stages add to zero
     if (!op->store_near) CU(cudaMemsetAsync(w.yp, 0, op->n * NR * sizeof(double), s));
+    // x in FP32 for the regular nearfield (and then the singular row gather)
+    const bool xs_ready = near_reads_xs(op) && op->near_u.nrows() > 0;
+    if (xs_ready) {
+        h2::launch_store_x(true, n, NR, w.xp, w.xs, s);
+        nl += 1;
+    }
     if (tune_now && op->near_u.nrows() > 0 && !op->store_near) {
         float best = 1e30f;
         const bool budgets = fp32 && !dlp;  // register-budget variants exist for the FP32 single layer
@@ -1670,7 +1685,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     nl += op->near_u.nrows() > 0 ? 1 : 0;
     mark(7);
-    if (op->sing_gather) nl += sing_gather_apply(op, NR, transpose, w.xp, w.yp, w.xs, s);
+    if (op->sing_gather) nl += sing_gather_apply(op, NR, transpose, w.xp, w.yp, w.xs, xs_ready, s);
     for (int ty = 0; ty < 3 && !op->sing_gather; ++ty) {
         if (ty == 0 && dlp) continue;  // the double-layer entry of a triangle with itself vanishes
         const int np = (int)op->sp_count[ty];

@@ -31,6 +31,7 @@ struct Geom {
     const double* plane; // [n] c . n (offset of the triangle's plane)
     const float* nef;    // [12][n] FP32: normal hi (0..2) and lo = fl(n - hi) (3..5), edges E1 = b - a (6..8),
                          // E2 = c - a (9..11), each rounded from FP64
+    const float* areaf;  // [n] area rounded to FP32
 };
 
 // Cluster tree on the device.
@@ -73,7 +74,7 @@ int resident_ctas(const void* func, int threads, size_t smem);
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
                  double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
-                 cudaStream_t s);
+                 float* areaf, cudaStream_t s);
 void launch_permute_in(const double* x, int64_t ldx, int nrhs, int NR, const int* perm, int n, double* xp,
                        cudaStream_t s);
 // the same, reading x in the caller's order and scattering through iperm
@@ -86,9 +87,11 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 // nearfield, regular pairs, each unordered pair of leaves {t, s} once: one
 // CTA per row leaf t in `rows`, columns s >= t from CSR (the first column of
 // a row is t itself).  ker: SLP or DLP; transpose applies K^T (double layer).
+// xs: x in FP32, rows of near_store_nx(true, NR) values (launch_store_x); read
+// by the FP32 single layer, which takes x from it instead of xp.
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
-                     const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     const LaunchCfg& cfg, cudaStream_t s);
+                     const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, const float* xs,
+                     double* yp, const LaunchCfg& cfg, cudaStream_t s);
 // Stored nearfield (k_nearstore.cu).  Block (t, s) of the ordered list at
 // element offset off[b], column by column with leading dimension |t| | 1
 // (FP32 if f32, else FP64).  NearStore: destination of the storing variant of

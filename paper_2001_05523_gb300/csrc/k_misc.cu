@@ -40,12 +40,12 @@ __global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, c
 // counter-clockwise seen from outside), the plane offset c . n, and the points
 // y_q = a + u_q (b-a) + v_q (c-a) of the 7-point rule, in FP64 and as FP32
 // offsets from the centroid, with a float split of the centroid; in FP32
-// also the normal as hi + lo and the edge vectors b - a, c - a.
+// also the normal as hi + lo, the edge vectors b - a, c - a and the area.
 __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ tri, const int* __restrict__ perm,
                        int n, Consts c, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
                        double* __restrict__ ctr, int* __restrict__ vid, float* __restrict__ qo,
                        double* __restrict__ qa, float* __restrict__ chl, double* __restrict__ plane,
-                       float* __restrict__ nef) {
+                       float* __restrict__ nef, float* __restrict__ areaf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int t = perm[i];
@@ -63,6 +63,7 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
     const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     const double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
     area[i] = 0.5 * len;
+    areaf[i] = (float)(0.5 * len);
     double pl = 0.0;
     for (int d = 0; d < 3; ++d) {
         const double nd = cr[d] / len;
@@ -89,8 +90,9 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
 
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
                  double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
-                 cudaStream_t s) {
-    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef);
+                 float* areaf, cudaStream_t s) {
+    k_geom<<<(n + 255) / 256, 256, 0, s>>>(xyz, tri, perm, n, c, v, area, nrm, ctr, vid, qo, qa, chl, plane, nef,
+                                           areaf);
 }
 
 int resident_ctas(const void* func, int threads, size_t smem) {

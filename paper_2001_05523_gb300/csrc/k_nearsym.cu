@@ -432,6 +432,341 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 single layer (the mixed tiers' hot case): packed over column pairs.
+//
+// Thread (il, kk) takes row triangle i = rb + il and the column pairs
+// (2 pj, 2 pj + 1), pj = kk, kk + K, ...  Each f32x2 lane pair evaluates the
+// same row point against the two columns' points, so all 7 x 7 point pairs of
+// both entries are packed with no odd point left over, and the column data
+// (centroid splits, point offsets, areas) arrive as natural pairs from one
+// 64-bit shared-memory load: columns are stored [quantity][jc], adjacent.  The
+// row's quantities are held duplicated (p, p) in registers.
+// With P_p the row point's offset from the row centroid and Y_q = D - Q_q
+// (D the centroid difference, Q_q the column point's offset), the squared
+// distance is expanded as |P_p + Y_q|^2 = (|P_p|^2 + |Y_q|^2) + 2 P_p . Y_q:
+// one add and three fma per evaluation instead of three add, one mul and two
+// fma.  |P_p| is below the triangle's size and the rule's points of regular
+// pairs stay apart, so the rounding of the expanded form is that of the
+// direct one (float emulation over the nearest regular pairs of sphere, flat
+// ellipsoid and jittered cube meshes: 2.3e-8 against 2.2e-8 relative in the
+// product).  Per two kernel evaluations the loop issues 4 packed ops for the
+// distance, 2 reciprocal square roots and 1 packed op for the sum, whose
+// weights take the rule's three values (centre, two orbits).  A column sharing a
+// vertex with the row is moved far away (its distance stays finite) and its
+// entry masked to zero; the singular kernels supply those entries.  An odd
+// column count is padded with one zero-area column far away.
+//
+// Staging: the column leaves of a row are taken in chunks of at most kColA
+// triangles, copied into shared memory by cp.async in two stages, so that the
+// next chunk's copies are in flight while the current one is evaluated.  All
+// inputs are FP32 (x from the FP32 copy xs, areas from areaf): GB300's FP64
+// pipe runs at 1/70 of FP32, and conversions from double would sit on the
+// staging path.  The FP64 additions into y take their FP32 sums converted
+// exactly by integer operations.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kColA = 104;   // staged column triangles of one chunk
+constexpr int kEntA = 4160;  // column-side entries of one chunk, (R | 1) x columns: 65 x 64 for the largest leaves
+constexpr int kSeg = 128;    // column leaves of a row described in shared memory at a time
+static_assert(kColA >= kMaxLeaf && kEntA >= (kMaxLeaf | 1) * kMaxLeaf, "a chunk holds a column leaf of any row leaf");
+
+template <int NR>
+struct Smem32 {
+    static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
+    // one stage of staged columns
+    static constexpr size_t SQ = 0;                          // float [3][7][kColA] point offsets
+    static constexpr size_t SCH = al(SQ + 4 * 21 * kColA);   // float [6][kColA] centroid hi, lo
+    static constexpr size_t SVID = al(SCH + 4 * 6 * kColA);  // int [3][kColA] vertex ids
+    static constexpr size_t SGID = al(SVID + 4 * 3 * kColA); // int [kColA] tree positions
+    static constexpr size_t SAR = al(SGID + 4 * kColA);      // float [kColA] areas
+    static constexpr size_t SX = al(SAR + 4 * kColA);        // float [kColA][NR] x
+    static constexpr size_t STAGE = al(SX + 4 * kColA * NR);
+    // CTA layout
+    static constexpr size_t A = 0;                           // float [kEntA] column-side entries [jc][R | 1]
+    static constexpr size_t ST = al(A + 4 * kEntA);          // two stages
+    static constexpr size_t XR = al(ST + 2 * STAGE);         // float [kMaxLeaf][NR] x of the row leaf
+    static constexpr size_t RC = al(XR + 4 * kMaxLeaf * NR); // f2 [kMaxLeaf][6] row centroid splits (duplicated)
+    static constexpr size_t BL = al(RC + 8 * 6 * kMaxLeaf);  // int2 [kSeg] (first position, size) per block
+    static constexpr size_t END = al(BL + 8 * kSeg);
+    static constexpr size_t RED = 4 * kThreads * NR;         // final row reduction (reuses the front)
+    static constexpr size_t BYTES = END > RED ? END : RED;
+};
+
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void cp4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// float -> double, exact, by integer operations (zero and subnormal inputs give
+// a signed zero; no infinities or NaNs reach it)
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned hi = (u & 0x80000000u) | (e ? (((e + 896u) << 20) | ((u >> 3) & 0xfffffu)) : 0u);
+    const unsigned lo = e ? (u << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// one chunk of a row's column leaves: blocks [b, b2) of the staged list
+struct Chunk {
+    int b, b2, ctot;
+};
+}  // namespace
+
+template <int NR>
+__device__ __forceinline__ void near_slp32_row(const Geom& g, const Tree& t, const Consts& c,
+                                               const int* __restrict__ rows, const int* __restrict__ ptr,
+                                               const int* __restrict__ col, const float* __restrict__ xs,
+                                               double* __restrict__ yp, int bi) {
+    using L = Smem32<NR>;
+    constexpr int NX = NR < 4 ? 4 : NR;  // row stride of xs
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* sA = reinterpret_cast<float*>(smem + L::A);
+    float* sxr = reinterpret_cast<float*>(smem + L::XR);
+    f2* src = reinterpret_cast<f2*>(smem + L::RC);
+    int2* sbl = reinterpret_cast<int2*>(smem + L::BL);
+
+    const int row = rows[bi];
+    const int rb = t.begin[row], R = t.end[row] - rb;
+    const int K = kThreads / R;
+    const int tid = threadIdx.x;
+    const int il = tid % R, kk = tid / R;
+    const bool active = kk < K;
+    const int n = g.n;
+    const int RS = R | 1;                         // odd stride of the entry tile: no bank conflicts
+    const int cmax = min(kColA, kEntA / RS) & ~1;  // even: room for the padding column
+
+    __syncthreads();  // a persistent CTA's previous row is done with shared memory
+    for (int e = tid; e < R * NR; e += kThreads) sxr[e] = xs[(int64_t)(rb + e / NR) * NX + e % NR];
+    for (int e = tid; e < R * 6; e += kThreads) {
+        const float v = g.chl[(e % 6) * n + rb + e / 6];
+        src[e] = pk(v, v);
+    }
+
+    // row triangle, duplicated into both lanes: 2 P_p, |P_p|^2 (centroid splits in shared memory)
+    f2 PX[7], PY[7], PZ[7], CP[7];
+    int vi[3];
+    float ai;
+    {
+        const int i = rb + (active ? il : 0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) vi[d] = g.vid[d * n + i];
+        ai = g.areaf[i];
+#pragma unroll
+        for (int p = 0; p < 7; ++p) {
+            const float x = g.qo[((int64_t)0 * n + i) * 7 + p], y = g.qo[((int64_t)1 * n + i) * 7 + p],
+                        z = g.qo[((int64_t)2 * n + i) * 7 + p];
+            PX[p] = pk(2.0f * x, 2.0f * x);
+            PY[p] = pk(2.0f * y, 2.0f * y);
+            PZ[p] = pk(2.0f * z, 2.0f * z);
+            const float cp = fmaf(z, z, fmaf(y, y, x * x));
+            CP[p] = pk(cp, cp);
+        }
+    }
+    // the rule's weights: centre (point 0), first orbit (1..3), second orbit (4..6)
+    const f2 W0 = pk(c.rwf[0], c.rwf[0]), WA = pk(c.rwf[1], c.rwf[1]), WB = pk(c.rwf[4], c.rwf[4]);
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0f;
+
+    const int bbeg = ptr[bi], bend = ptr[bi + 1];
+    const bool diag = bend > bbeg && col[bbeg] == row;  // the first column leaf is t itself
+    for (int seg = bbeg; seg < bend; seg += kSeg) {
+        const int nbl = min(kSeg, bend - seg);
+        __syncthreads();
+        if (tid < nbl) {
+            const int s = col[seg + tid];
+            sbl[tid] = make_int2(t.begin[s], t.end[s] - t.begin[s]);
+        }
+        __syncthreads();
+        // the next chunk from block b of this segment; jc -> its tree position jpos
+        auto next = [&](int b, int jc, int& jpos) {
+            Chunk ch{b, b, 0};
+            jpos = -1;
+            while (ch.b2 < nbl) {
+                const int2 bl = sbl[ch.b2];
+                if (ch.ctot + bl.y > cmax) break;
+                if (jc >= ch.ctot && jc < ch.ctot + bl.y) jpos = bl.x + (jc - ch.ctot);
+                ch.ctot += bl.y;
+                ++ch.b2;
+            }
+            return ch;
+        };
+        // copies of one chunk into a stage: thread jc (< 128) the point offsets,
+        // thread 128 + jc the rest; the padding column by plain stores
+        const int jc = tid & 127, half = tid >> 7;
+        auto issue = [&](const Chunk& ch, int jpos, unsigned char* st) {
+            float* q = reinterpret_cast<float*>(st + L::SQ);
+            float* chs = reinterpret_cast<float*>(st + L::SCH);
+            int* vid = reinterpret_cast<int*>(st + L::SVID);
+            int* gid = reinterpret_cast<int*>(st + L::SGID);
+            float* ar = reinterpret_cast<float*>(st + L::SAR);
+            float* xc = reinterpret_cast<float*>(st + L::SX);
+            if (jc < ch.ctot) {
+                if (half == 0) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int qq = 0; qq < 7; ++qq) cp4(q + (d * 7 + qq) * kColA + jc, g.qo + ((int64_t)d * n + jpos) * 7 + qq);
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) cp4(chs + d * kColA + jc, g.chl + (int64_t)d * n + jpos);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cp4(vid + d * kColA + jc, g.vid + (int64_t)d * n + jpos);
+                    cp4(ar + jc, g.areaf + jpos);
+                    if constexpr (NR >= 4) {
+#pragma unroll
+                        for (int r = 0; r < NR; r += 4) cp16(xc + jc * NR + r, xs + (int64_t)jpos * NX + r);
+                    } else {
+                        cp4(xc + jc, xs + (int64_t)jpos * NX);
+                    }
+                    gid[jc] = jpos;
+                }
+            } else if (jc == ch.ctot && (ch.ctot & 1)) {  // padding column: zero area, far away, no vertex
+                if (half == 0) {
+#pragma unroll
+                    for (int d = 0; d < 21; ++d) q[d * kColA + jc] = 0.0f;
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        chs[d * kColA + jc] = 1.0e4f;
+                        chs[(3 + d) * kColA + jc] = 0.0f;
+                        vid[d * kColA + jc] = -2;
+                    }
+                    ar[jc] = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) xc[jc * NR + r] = 0.0f;
+                }
+            }
+        };
+
+        int jpos;
+        Chunk cur = next(0, jc, jpos);
+        issue(cur, jpos, smem + L::ST);
+        cp_commit();
+        for (int it = 0; cur.b2 > cur.b; ++it) {
+            unsigned char* st = smem + L::ST + (it & 1) * L::STAGE;
+            int jn;
+            const Chunk nxt = next(cur.b2, jc, jn);
+            if (nxt.b2 > nxt.b) issue(nxt, jn, smem + L::ST + ((it + 1) & 1) * L::STAGE);
+            cp_commit();
+            cp_wait1();  // this thread's copies of the current chunk are done
+            __syncthreads();
+            const float* sq = reinterpret_cast<const float*>(st + L::SQ);
+            const float* sch = reinterpret_cast<const float*>(st + L::SCH);
+            const int* svid = reinterpret_cast<const int*>(st + L::SVID);
+            const int* sgid = reinterpret_cast<const int*>(st + L::SGID);
+            const float* sarea = reinterpret_cast<const float*>(st + L::SAR);
+            const float* sxc = reinterpret_cast<const float*>(st + L::SX);
+            const int ctot = cur.ctot, ctp = (ctot + 1) & ~1;
+            const int cdiag = (diag && seg == bbeg && cur.b == 0) ? R : 0;  // leading columns of the diagonal block
+
+            if (active) {
+                for (int pj = kk; 2 * pj < ctp; pj += K) {
+                    const int ja = 2 * pj;
+                    bool sa = false, sb = false;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int va = svid[d * kColA + ja], vb = svid[d * kColA + ja + 1];
+                        sa |= (va == vi[0]) | (va == vi[1]) | (va == vi[2]);
+                        sb |= (vb == vi[0]) | (vb == vi[1]) | (vb == vi[2]);
+                    }
+                    f2 D[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        D[d] = add2(sub2(src[il * 6 + d], ld2(sch + d * kColA + ja)),
+                                    sub2(src[il * 6 + 3 + d], ld2(sch + (3 + d) * kColA + ja)));
+                    // a column sharing a vertex: far away (finite distances), entry masked below
+                    D[0] = add2(D[0], pk(sa ? 1.0e4f : 0.0f, sb ? 1.0e4f : 0.0f));
+                    f2 S = 0;
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        const f2 YX = sub2(D[0], ld2(sq + (0 * 7 + q) * kColA + ja));
+                        const f2 YY = sub2(D[1], ld2(sq + (1 * 7 + q) * kColA + ja));
+                        const f2 YZ = sub2(D[2], ld2(sq + (2 * 7 + q) * kColA + ja));
+                        const f2 EQ = fma2(YZ, YZ, fma2(YY, YY, mul2(YX, YX)));
+                        f2 ri[7];
+#pragma unroll
+                        for (int p = 0; p < 7; ++p) {
+                            const f2 r2 = fma2(PZ[p], YZ, fma2(PY[p], YY, fma2(PX[p], YX, add2(CP[p], EQ))));
+                            float r0, r1;
+                            upk(r2, r0, r1);
+                            ri[p] = pk(rsqrt_f32(r0), rsqrt_f32(r1));
+                        }
+                        f2 A = mul2(W0, ri[0]);
+                        A = fma2(WA, add2(add2(ri[1], ri[2]), ri[3]), A);
+                        A = fma2(WB, add2(add2(ri[4], ri[5]), ri[6]), A);
+                        S = fma2(q == 0 ? W0 : q <= 3 ? WA : WB, A, S);
+                    }
+                    float a0, a1;
+                    upk(mul2(S, ld2(sarea + ja)), a0, a1);
+                    a0 = sa ? 0.0f : a0 * ai;
+                    a1 = sb ? 0.0f : a1 * ai;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        acc[r] = fmaf(a1, sxc[(ja + 1) * NR + r], fmaf(a0, sxc[ja * NR + r], acc[r]));
+                    sA[ja * RS + il] = a0;
+                    sA[(ja + 1) * RS + il] = a1;
+                }
+            }
+            __syncthreads();
+
+            // column side of the off-diagonal leaves, y_j += sum_i a_ji x_i
+            constexpr int RV = NR >= 4 ? 4 : 1;
+            for (int e = tid; e < (ctot - cdiag) * (NR / RV); e += kThreads) {
+                const int j = cdiag + e / (NR / RV), r0 = (e % (NR / RV)) * RV;
+                float sum[RV];
+#pragma unroll
+                for (int v = 0; v < RV; ++v) sum[v] = 0.0f;
+                for (int i = 0; i < R; ++i) {
+                    const float a = sA[j * RS + i];
+                    if constexpr (RV == 4) {
+                        const float4 xv = *reinterpret_cast<const float4*>(sxr + i * NR + r0);
+                        sum[0] = fmaf(a, xv.x, sum[0]);
+                        sum[1] = fmaf(a, xv.y, sum[1]);
+                        sum[2] = fmaf(a, xv.z, sum[2]);
+                        sum[3] = fmaf(a, xv.w, sum[3]);
+                    } else {
+                        sum[0] = fmaf(a, sxr[i * NR + r0], sum[0]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < RV; ++v)
+                    atomicAdd(&yp[(int64_t)sgid[j] * NR + r0 + v], f2d_exact(sum[v] * (float)kInv4Pi));
+            }
+            __syncthreads();  // the stage and the entry tile are free for the chunk after next
+            cur = nxt;
+            jpos = jn;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    float* sred = reinterpret_cast<float*>(smem);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sred[tid * NR + r] = active ? acc[r] : 0.0f;
+    __syncthreads();
+    for (int e = tid; e < R * NR; e += kThreads) {
+        const int i = e / NR, r = e % NR;
+        float s = 0.0f;
+        for (int q = 0; q < K; ++q) s += sred[(q * R + i) * NR + r];
+        atomicAdd(&yp[(int64_t)(rb + i) * NR + r], f2d_exact(s * (float)kInv4Pi));
+    }
+}
+
 // One CTA per row leaf (work == nullptr), or persistent CTAs that take the
 // next row from the counter *work (zero before the launch) until none is left.
 // NB: CTAs per SM the register budget is sized for (0: 4 for the FP32 single
@@ -439,10 +774,11 @@ __device__ __forceinline__ void near_sym_row(const Geom& g, const Tree& t, const
 template <int NR, bool DLPK, bool F32, bool PERSIST, int NB>
 __global__ void __launch_bounds__(kThreads, NB > 0 ? NB : ((F32 && !DLPK) ? 4 : 2))
     k_near_sym(Geom g, Tree t, Consts c, int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
-               const int* __restrict__ col, bool transpose, const double* __restrict__ xp, double* __restrict__ yp,
-               int* __restrict__ work) {
+               const int* __restrict__ col, bool transpose, const double* __restrict__ xp,
+               const float* __restrict__ xs, double* __restrict__ yp, int* __restrict__ work) {
     if constexpr (!PERSIST) {
-        near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, blockIdx.x);
+        if constexpr (F32 && !DLPK) near_slp32_row<NR>(g, t, c, rows, ptr, col, xs, yp, blockIdx.x);
+        else near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, blockIdx.x);
         return;
     }
     __shared__ int s_bi;
@@ -452,7 +788,8 @@ __global__ void __launch_bounds__(kThreads, NB > 0 ? NB : ((F32 && !DLPK) ? 4 : 
         __syncthreads();
         const int bi = s_bi;
         if (bi >= nrows) break;
-        near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, bi);
+        if constexpr (F32 && !DLPK) near_slp32_row<NR>(g, t, c, rows, ptr, col, xs, yp, bi);
+        else near_sym_row<NR, DLPK, F32>(g, t, c, rows, ptr, col, transpose, xp, yp, bi);
     }
 }
 
@@ -483,19 +820,20 @@ void launch_near_sym_store(const Geom& g, const Tree& t, const Consts& c, int nr
 
 template <int NR, bool DLPK, bool F32>
 static void near_sym_go(int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c, const int* rows,
-                        const int* ptr, const int* col, bool tr, const double* xp, double* yp, int* work, int nb) {
+                        const int* ptr, const int* col, bool tr, const double* xp, const float* xs, double* yp,
+                        int* work, int nb) {
     using T = typename std::conditional<F32, float, double>::type;
-    constexpr size_t smem = Smem<T, NR, DLPK>::BYTES;
+    constexpr size_t smem = (F32 && !DLPK) ? Smem32<NR>::BYTES : Smem<T, NR, DLPK>::BYTES;
     auto go = [&](auto kplain, auto kpers) {
         if (!work) {
             cudaFuncSetAttribute(kplain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            kplain<<<nrows, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, nullptr);
+            kplain<<<nrows, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, xs, yp, nullptr);
             return;
         }
         cudaFuncSetAttribute(kpers, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = std::min(nrows, resident_ctas((const void*)kpers, kThreads, smem));
         cudaMemsetAsync(work, 0, sizeof(int), s);
-        kpers<<<grid, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, yp, work);
+        kpers<<<grid, kThreads, smem, s>>>(g, t, c, nrows, rows, ptr, col, tr, xp, xs, yp, work);
     };
     if constexpr (F32 && !DLPK) {
         if (nb == 3) go(k_near_sym<NR, DLPK, F32, false, 3>, k_near_sym<NR, DLPK, F32, true, 3>);
@@ -508,29 +846,29 @@ static void near_sym_go(int nrows, cudaStream_t s, const Geom& g, const Tree& t,
 
 template <int NR>
 static void near_sym_nr(int ker, bool fp32, int nrows, cudaStream_t s, const Geom& g, const Tree& t, const Consts& c,
-                        const int* rows, const int* ptr, const int* col, bool tr, const double* xp, double* yp,
-                        int* work, int nb) {
+                        const int* rows, const int* ptr, const int* col, bool tr, const double* xp, const float* xs,
+                        double* yp, int* work, int nb) {
     const bool dlp = ker != SLP;
     if (fp32) {
-        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
-        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
+        if (dlp) near_sym_go<NR, true, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, xs, yp, work, nb);
+        else near_sym_go<NR, false, true>(nrows, s, g, t, c, rows, ptr, col, tr, xp, xs, yp, work, nb);
     } else {
-        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
-        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, yp, work, nb);
+        if (dlp) near_sym_go<NR, true, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, xs, yp, work, nb);
+        else near_sym_go<NR, false, false>(nrows, s, g, t, c, rows, ptr, col, tr, xp, xs, yp, work, nb);
     }
 }
 
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
-                     const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, double* yp,
-                     const LaunchCfg& cfg, cudaStream_t s) {
+                     const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, const float* xs,
+                     double* yp, const LaunchCfg& cfg, cudaStream_t s) {
     int* work = cfg.work;
     const int nb = cfg.nb;
     if (nrows <= 0) return;
     switch (NR) {
-        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
-        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
-        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
-        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, yp, work, nb); break;
+        case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
+        case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
+        case 8: near_sym_nr<8>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
+        default: near_sym_nr<16>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
     }
 }
 
