@@ -96,6 +96,27 @@ def lib():
             L.or_h2_grad.restype = i32
             L.or_num_threads.restype = i32
             L.or_set_threads.argtypes = [i32]
+            L.or_gca_boundary_rule.argtypes = [vp, vp, i32, vp, vp, vp]
+            L.or_gca_boundary_rule.restype = i32
+            L.or_gca_green.argtypes = [vp, vp, i32, vp, vp]
+            L.or_gca_green.restype = d
+            L.or_gca_aca.argtypes = [vp, i32, i32, d, i32, vp, vp]
+            L.or_gca_aca.restype = i32
+            L.or_gca_create.argtypes = [vp, i64, vp, i64, i32, d, i32, d, i32, i32]
+            L.or_gca_create.restype = vp
+            L.or_gca_destroy.argtypes = [vp]
+            L.or_gca_sizes.argtypes = [vp, vp]
+            L.or_gca_ranks.argtypes = [vp, vp]
+            L.or_gca_pivots.argtypes = [vp, i64, vp]
+            L.or_gca_basis.argtypes = [vp, i64, vp]
+            L.or_gca_basis.restype = i32
+            L.or_gca_transfer.argtypes = [vp, i64, vp]
+            L.or_gca_transfer.restype = i32
+            L.or_gca_L.argtypes = [vp, i64, vp, vp]
+            L.or_gca_L.restype = i64
+            L.or_gca_rowcount.argtypes = [vp, i64]
+            L.or_gca_rowcount.restype = i64
+            L.or_gca_matvec.argtypes = [vp, vp, i32, vp, i32]
             _lib = L
     return _lib
 
@@ -360,6 +381,101 @@ class H2:
         x = _f64(x)
         y = np.zeros((x.shape[0], rows.size))
         lib().or_h2_rows(self.h, _p(rows), rows.size, _p(x), x.shape[0], _p(y))
+        return y
+
+
+# ---------------------------------------------------------------------------
+# Green cross approximation of the single layer (section 4); the arithmetic is
+# in h2oracle.c (or_gca_*), whose comment block states each step.
+# ---------------------------------------------------------------------------
+def gca_boundary_rule(lo, hi, q: int):
+    """Composite Gauss rule on the boundary of the box [lo, hi]: points (k, 3),
+    weights (k,), outward normals (k, 3), k = 6 q^2."""
+    k = 6 * q * q
+    z, w, nz = np.zeros((k, 3)), np.zeros(k), np.zeros((k, 3))
+    if lib().or_gca_boundary_rule(_p(_f64(lo)), _p(_f64(hi)), q, _p(z), _p(w), _p(nz)) != k:
+        raise ValueError("bad q")
+    return z, w, nz
+
+
+def gca_green(lo, hi, q: int, x, y) -> float:
+    """g~_grn(x, y): Green's representation formula on the box [lo, hi] with the rule above."""
+    return float(lib().or_gca_green(_p(_f64(lo)), _p(_f64(hi)), q, _p(_f64(x)), _p(_f64(y))))
+
+
+def gca_aca(L: np.ndarray, eps: float, kmax: int):
+    """Full-pivot cross approximation of L: (tau, sigma) pivot lists."""
+    L = _f64(L)
+    rows, cols = L.shape
+    tau = np.zeros(kmax + 1, np.int32)
+    sigma = np.zeros(kmax + 1, np.int32)
+    k = lib().or_gca_aca(_p(L), rows, cols, float(eps), int(kmax), _p(tau), _p(sigma))
+    return tau[:k].copy(), sigma[:k].copy()
+
+
+class GCA:
+    """The oracle's GCA approximation of the single layer G: q Gauss points per
+    face axis of d omega_t, ACA tolerance eps (relative to the first pivot),
+    ranks capped at kmax."""
+
+    def __init__(self, mesh, q: int = 4, eta: float = 2.0, leaf: int = 32, eps: float = 1e-6, kmax: int = 64,
+                 q_ss: int = 5):
+        self.mesh = mesh
+        v = _f64(mesh.vertices)
+        t = np.ascontiguousarray(mesh.triangles, dtype=np.int32)
+        self._keep = (v, t)
+        h = lib().or_gca_create(_p(v), v.shape[0], _p(t), t.shape[0], q, float(eta), leaf, float(eps), kmax, q_ss)
+        if not h:
+            raise ValueError("or_gca_create failed")
+        self.h = ctypes.c_void_p(h)
+        sz = np.zeros(5, dtype=np.int64)
+        lib().or_gca_sizes(self.h, _p(sz))
+        self.nclusters, self.nfar, self.nnear, self.maxrank, self.k = (int(a) for a in sz)
+        self.n = mesh.nt
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            lib().or_gca_destroy(h)
+            self.h = None
+
+    def ranks(self) -> np.ndarray:
+        r = np.zeros(self.nclusters, np.int32)
+        lib().or_gca_ranks(self.h, _p(r))
+        return r
+
+    def pivots(self, c: int) -> np.ndarray:
+        p = np.zeros(int(self.ranks()[c]), np.int64)
+        lib().or_gca_pivots(self.h, c, _p(p))
+        return p
+
+    def leaf_basis(self, c: int, size: int) -> np.ndarray:
+        V = np.zeros((size, int(self.ranks()[c])))
+        if lib().or_gca_basis(self.h, c, _p(V)):
+            raise ValueError("not a leaf")
+        return V
+
+    def transfer(self, c: int, parent: int) -> np.ndarray:
+        r = self.ranks()
+        E = np.zeros((int(r[c]), int(r[parent])))
+        if lib().or_gca_transfer(self.h, c, _p(E)):
+            raise ValueError("bad cluster")
+        return E
+
+    def L(self, c: int):
+        nr = int(lib().or_gca_rowcount(self.h, c))
+        rows = np.zeros(nr, np.int64)
+        L = np.zeros((nr, 2 * self.k))
+        lib().or_gca_L(self.h, c, _p(rows), _p(L))
+        return rows, L
+
+    def matvec(self, x: np.ndarray, parts: int = PART_ALL) -> np.ndarray:
+        """x: (nrhs, n) -> (nrhs, n)."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        y = np.zeros_like(x)
+        lib().or_gca_matvec(self.h, _p(x), x.shape[0], _p(y), int(parts))
         return y
 
 

@@ -1731,3 +1731,448 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
     free(gc); free(gh); free(S); free(xh); free(wh); free(yh); free(zh);
     return 0;
 }
+
+/* ========================================================================= */
+/* Green cross approximation, GCA (section 4), single layer G               */
+/* ========================================================================= */
+/* For a cluster t with box B_t = [a, b]:                                     */
+/*  1. The auxiliary box omega_t = [a - delta_t, b + delta_t] on every axis,  */
+/*     delta_t = max_d (b_d - a_d) (the choice of the experiments, section 5, */
+/*     dist(d omega_t, B_t) = delta_t).                                       */
+/*  2. Green's representation formula on omega_t (section 4):                 */
+/*       g(x,y) = int g(x,z) dg/dn_z(z,y) dz - int dg/dn_z(x,z) g(z,y) dz,    */
+/*     discretised by a composite Gauss rule on the six faces of d omega_t:   */
+/*     face f = 2 d + side (side 0: x_d = lo_d, normal -e_d; side 1: x_d =   */
+/*     hi_d, normal +e_d), q x q Gauss-Legendre points over its two other     */
+/*     axes d1 < d2, point nu = (f q + a) q + b, weight w_nu = gw_a gw_b      */
+/*     len_d1 len_d2; k = 6 q^2 points.                                       */
+/*  3. L = (A C), rows = the row set of t, A_i,nu = w_nu^(1/2) int_tau_i      */
+/*     g(x, z_nu) dx, C_i,nu = w_nu^(1/2) int_tau_i dg/dn_z(x, z_nu) dx (the  */
+/*     7-point rule on tau_i; z_nu is at distance >= delta_t from B_t).       */
+/*     The row set is the triangles of t (a leaf, in tree order) or          */
+/*     t^_{t1} followed by t^_{t2} (the children's pivots, nested form).     */
+/*  4. Adaptive cross approximation of L with full pivoting (the pivoted LU  */
+/*     of section 3): residual R = L; while rank < kmax and rank < min(rows, */
+/*     cols): pivot (i*, j*) = the first entry of largest |R| in row-major   */
+/*     order; stop if R_i*j* = 0 or (rank > 0 and |R_i*j*| <= eps |first    */
+/*     pivot|); R_ij -= R_ij* (R_i*j / R_i*j*) for all i, j (the row of the  */
+/*     pivot divided first); tau += i*, sigma += j*.                          */
+/*  5. V^_t = L|_{rows x sigma} (L|_{tau x sigma})^{-1} (eq. gca_onesided);  */
+/*     t^ = rows[tau] in pivot order.  Leaf: V_t = V^_t.  Otherwise          */
+/*     (E_t1; E_t2) = V^_t split by rows (eq. (transfer)).                   */
+/*  6. Coupling S_ts = G|_{t^ x s^} (Galerkin entries of the pivot           */
+/*     triangles, eq. (slp)); the single layer is symmetric, so W_s = V_s.   */
+/* The H^2 product then runs the passes of section 2 with these V, E, S.     */
+
+struct or_gca {
+    or_mesh mesh;
+    double* xyz;
+    int32_t* tri;
+    int q, q_ss, kmax;
+    double eta, eps;
+    tree_t T;
+    blist far, near;
+    int64_t *far_ptr, *far_col, *near_ptr, *near_col;
+    int* rank;      /* k~_t */
+    int64_t** piv;  /* pivot triangles (user indices) of t, pivot order */
+    double** V;     /* leaves: |t| x rank_t, rows in tree order */
+    double** E;     /* non-root clusters: rank_c x rank_parent */
+};
+
+/* The composite Gauss rule on the boundary of the box [lo, hi] (step 2):
+ * z[3 k], w[k], nz[3 k] with k = 6 q^2. */
+int or_gca_boundary_rule(const double* lo, const double* hi, int q, double* z, double* w, double* nz) {
+    double g[64], gw[64];
+    if (or_gauss_legendre01(q, g, gw)) return -1;
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2, side = f % 2;
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        const double l1 = hi[d1] - lo[d1], l2 = hi[d2] - lo[d2];
+        for (int a = 0; a < q; ++a)
+            for (int b = 0; b < q; ++b) {
+                const int nu = (f * q + a) * q + b;
+                z[3 * nu + d] = side ? hi[d] : lo[d];
+                z[3 * nu + d1] = lo[d1] + l1 * g[a];
+                z[3 * nu + d2] = lo[d2] + l2 * g[b];
+                w[nu] = gw[a] * gw[b] * l1 * l2;
+                nz[3 * nu + 0] = nz[3 * nu + 1] = nz[3 * nu + 2] = 0.0;
+                nz[3 * nu + d] = side ? 1.0 : -1.0;
+            }
+    }
+    return 6 * q * q;
+}
+
+/* g~_grn(x, y) of step 2 with the boundary rule of [lo, hi]. */
+double or_gca_green(const double* lo, const double* hi, int q, const double* x, const double* y) {
+    const int k = 6 * q * q;
+    double* z = malloc(3 * k * sizeof(double));
+    double* w = malloc(k * sizeof(double));
+    double* nz = malloc(3 * k * sizeof(double));
+    or_gca_boundary_rule(lo, hi, q, z, w, nz);
+    double s = 0.0;
+    for (int nu = 0; nu < k; ++nu)
+        s += w[nu] * (kernel_slp(x, z + 3 * nu) * kernel_dlp(y, z + 3 * nu, nz + 3 * nu) -
+                      kernel_dlp(x, z + 3 * nu, nz + 3 * nu) * kernel_slp(z + 3 * nu, y));
+    free(z);
+    free(w);
+    free(nz);
+    return s;
+}
+
+/* Row of L for triangle i (step 3): 2k values. */
+static void gca_L_row(const or_mesh* M, int64_t i, int k, const double* z, const double* w, const double* nz,
+                      double* L) {
+    double X[9], area, nrm[3], uv[14], rw[7], xp[7][3];
+    tri_vertices(M, i, X);
+    or_tri_geom(X, X + 3, X + 6, &area, nrm);
+    or_radon7(uv, rw);
+    for (int p = 0; p < 7; ++p)
+        for (int d = 0; d < 3; ++d) xp[p][d] = X[d] + uv[2 * p] * (X[3 + d] - X[d]) + uv[2 * p + 1] * (X[6 + d] - X[d]);
+    for (int nu = 0; nu < k; ++nu) {
+        double a = 0.0, c = 0.0;
+        for (int p = 0; p < 7; ++p) {
+            a += rw[p] * kernel_slp(xp[p], z + 3 * nu);
+            c += rw[p] * kernel_dlp(xp[p], z + 3 * nu, nz + 3 * nu);
+        }
+        const double sw = sqrt(w[nu]);
+        L[nu] = sw * area * a;
+        L[k + nu] = sw * area * c;
+    }
+}
+
+/* omega_t of step 1 */
+static void gca_omega(const tree_t* T, int64_t c, double* lo, double* hi) {
+    const double* a = T->bmin + 3 * c;
+    const double* b = T->bmax + 3 * c;
+    double delta = 0.0;
+    for (int d = 0; d < 3; ++d)
+        if (b[d] - a[d] > delta) delta = b[d] - a[d];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = a[d] - delta;
+        hi[d] = b[d] + delta;
+    }
+}
+
+/* Row set of cluster c (step 3): user triangle indices; returns the count. */
+static int64_t gca_rows(const or_gca* G, int64_t c, int64_t* rows) {
+    const tree_t* T = &G->T;
+    if (T->child0[c] < 0) {
+        for (int64_t a = T->begin[c]; a < T->end[c]; ++a) rows[a - T->begin[c]] = T->perm[a];
+        return T->end[c] - T->begin[c];
+    }
+    int64_t n = 0;
+    const int64_t ch[2] = {T->child0[c], T->child1[c]};
+    for (int h = 0; h < 2; ++h)
+        for (int r = 0; r < G->rank[ch[h]]; ++r) rows[n++] = G->piv[ch[h]][r];
+    return n;
+}
+
+/* L of cluster c (rows x 2k, row-major) for its row set; returns rows. */
+static int64_t gca_L(const or_gca* G, int64_t c, int64_t* rows, double* L) {
+    const int k = 6 * G->q * G->q;
+    double lo[3], hi[3];
+    gca_omega(&G->T, c, lo, hi);
+    double* z = malloc(3 * k * sizeof(double));
+    double* w = malloc(k * sizeof(double));
+    double* nz = malloc(3 * k * sizeof(double));
+    or_gca_boundary_rule(lo, hi, G->q, z, w, nz);
+    const int64_t nr = gca_rows(G, c, rows);
+    for (int64_t r = 0; r < nr; ++r) gca_L_row(&G->mesh, rows[r], k, z, w, nz, L + r * 2 * k);
+    free(z);
+    free(w);
+    free(nz);
+    return nr;
+}
+
+/* Step 4: full-pivot cross approximation; returns the rank. */
+int or_gca_aca(const double* L, int rows, int cols, double eps, int kmax, int* tau, int* sigma) {
+    double* R = malloc((size_t)rows * cols * sizeof(double));
+    double* col = malloc(rows * sizeof(double));
+    double* row = malloc(cols * sizeof(double));
+    memcpy(R, L, (size_t)rows * cols * sizeof(double));
+    int k = 0;
+    double first = 0.0;
+    while (k < kmax && k < rows && k < cols) {
+        int bi = 0, bj = 0;
+        double best = -1.0;
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j)
+                if (fabs(R[(size_t)i * cols + j]) > best) {
+                    best = fabs(R[(size_t)i * cols + j]);
+                    bi = i;
+                    bj = j;
+                }
+        const double p = R[(size_t)bi * cols + bj];
+        if (p == 0.0) break;
+        if (k == 0) first = fabs(p);
+        else if (fabs(p) <= eps * first) break;
+        tau[k] = bi;
+        sigma[k] = bj;
+        ++k;
+        for (int i = 0; i < rows; ++i) col[i] = R[(size_t)i * cols + bj];
+        for (int j = 0; j < cols; ++j) row[j] = R[(size_t)bi * cols + j] / p;
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j) R[(size_t)i * cols + j] -= col[i] * row[j];
+    }
+    free(R);
+    free(col);
+    free(row);
+    return k;
+}
+
+/* Step 5: V = L|_{: x sigma} (L|_{tau x sigma})^{-1} (rows x k), by Gaussian
+ * elimination with partial pivoting on M^T V^T = L|_{: x sigma}^T. */
+static void gca_interp(const double* L, int rows, int cols, int k, const int* tau, const int* sigma, double* V) {
+    double* Mt = malloc((size_t)k * k * sizeof(double));  /* Mt[a][b] = L[tau[b]][sigma[a]] */
+    double* B = malloc((size_t)k * rows * sizeof(double)); /* B[a][r] = L[r][sigma[a]] */
+    for (int a = 0; a < k; ++a) {
+        for (int b = 0; b < k; ++b) Mt[a * k + b] = L[(size_t)tau[b] * cols + sigma[a]];
+        for (int r = 0; r < rows; ++r) B[(size_t)a * rows + r] = L[(size_t)r * cols + sigma[a]];
+    }
+    for (int c = 0; c < k; ++c) {
+        int pr = c;
+        for (int a = c + 1; a < k; ++a)
+            if (fabs(Mt[a * k + c]) > fabs(Mt[pr * k + c])) pr = a;
+        if (pr != c) {
+            for (int b = 0; b < k; ++b) {
+                double t = Mt[c * k + b];
+                Mt[c * k + b] = Mt[pr * k + b];
+                Mt[pr * k + b] = t;
+            }
+            for (int r = 0; r < rows; ++r) {
+                double t = B[(size_t)c * rows + r];
+                B[(size_t)c * rows + r] = B[(size_t)pr * rows + r];
+                B[(size_t)pr * rows + r] = t;
+            }
+        }
+        for (int a = c + 1; a < k; ++a) {
+            const double f = Mt[a * k + c] / Mt[c * k + c];
+            for (int b = c; b < k; ++b) Mt[a * k + b] -= f * Mt[c * k + b];
+            for (int r = 0; r < rows; ++r) B[(size_t)a * rows + r] -= f * B[(size_t)c * rows + r];
+        }
+    }
+    for (int c = k - 1; c >= 0; --c)
+        for (int r = 0; r < rows; ++r) {
+            double s = B[(size_t)c * rows + r];
+            for (int b = c + 1; b < k; ++b) s -= Mt[c * k + b] * V[(size_t)r * k + b];
+            V[(size_t)r * k + c] = s / Mt[c * k + c];
+        }
+    free(Mt);
+    free(B);
+}
+
+or_gca* or_gca_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int q, double eta, int leaf,
+                      double eps, int kmax, int q_ss) {
+    if (q < 1 || q > 16 || leaf < 1 || nt < 1 || kmax < 1) return NULL;
+    or_gca* G = calloc(1, sizeof(or_gca));
+    G->xyz = malloc(3 * nv * sizeof(double));
+    G->tri = malloc(3 * nt * sizeof(int32_t));
+    memcpy(G->xyz, xyz, 3 * nv * sizeof(double));
+    memcpy(G->tri, tri, 3 * nt * sizeof(int32_t));
+    G->mesh.xyz = G->xyz;
+    G->mesh.tri = G->tri;
+    G->mesh.nv = nv;
+    G->mesh.nt = nt;
+    G->q = q;
+    G->eta = eta;
+    G->eps = eps;
+    G->kmax = kmax;
+    G->q_ss = q_ss;
+    tree_t* T = &G->T;
+    T->n = nt;
+    T->perm = malloc(nt * sizeof(int64_t));
+    for (int64_t i = 0; i < nt; ++i) T->perm[i] = i;
+    int64_t* tmp = malloc(nt * sizeof(int64_t));
+    tree_split(&G->mesh, T, 0, nt, -1, 0, leaf, tmp);
+    free(tmp);
+    block_build(T, eta, 0, 0, &G->far, &G->near);
+    const int64_t nc = T->count;
+    G->far_ptr = csr_from(nc, G->far.t, G->far.s, G->far.n, &G->far_col);
+    G->near_ptr = csr_from(nc, G->near.t, G->near.s, G->near.n, &G->near_col);
+    G->rank = calloc(nc, sizeof(int));
+    G->piv = calloc(nc, sizeof(int64_t*));
+    G->V = calloc(nc, sizeof(double*));
+    G->E = calloc(nc, sizeof(double*));
+    const int k = 6 * q * q;
+    /* children before parents: clusters are numbered in pre-order; a level of
+     * the tree at a time, its clusters in parallel */
+    int maxlev = 0;
+    for (int64_t c = 0; c < nc; ++c)
+        if (T->level[c] > maxlev) maxlev = T->level[c];
+    for (int lev = maxlev; lev >= 0; --lev) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T->level[c] != lev) continue;
+            const int64_t cap = (T->end[c] - T->begin[c]) > 2 * kmax ? (T->end[c] - T->begin[c]) : 2 * kmax;
+            int64_t* rows = malloc(cap * sizeof(int64_t));
+            double* L = malloc((size_t)cap * 2 * k * sizeof(double));
+            const int64_t nr = gca_L(G, c, rows, L);
+            int* tau = malloc((kmax + 1) * sizeof(int));
+            int* sigma = malloc((kmax + 1) * sizeof(int));
+            const int rk = or_gca_aca(L, (int)nr, 2 * k, eps, kmax, tau, sigma);
+            double* Vh = malloc(((size_t)nr * rk + 1) * sizeof(double));
+            gca_interp(L, (int)nr, 2 * k, rk, tau, sigma, Vh);
+            G->rank[c] = rk;
+            G->piv[c] = malloc((rk + 1) * sizeof(int64_t));
+            for (int r = 0; r < rk; ++r) G->piv[c][r] = rows[tau[r]];
+            if (T->child0[c] < 0) {
+                G->V[c] = Vh;
+            } else {
+                const int64_t ch[2] = {T->child0[c], T->child1[c]};
+                int off = 0;
+                for (int h = 0; h < 2; ++h) {
+                    const int kc = G->rank[ch[h]];
+                    G->E[ch[h]] = malloc(((size_t)kc * rk + 1) * sizeof(double));
+                    memcpy(G->E[ch[h]], Vh + (size_t)off * rk, (size_t)kc * rk * sizeof(double));
+                    off += kc;
+                }
+                free(Vh);
+            }
+            free(rows);
+            free(L);
+            free(tau);
+            free(sigma);
+        }
+    }
+    return G;
+}
+
+void or_gca_destroy(or_gca* G) {
+    if (!G) return;
+    tree_t* T = &G->T;
+    for (int64_t c = 0; c < T->count; ++c) {
+        free(G->piv[c]);
+        free(G->V[c]);
+        free(G->E[c]);
+    }
+    free(G->piv); free(G->V); free(G->E); free(G->rank);
+    free(G->far_ptr); free(G->far_col); free(G->near_ptr); free(G->near_col);
+    free(G->far.t); free(G->far.s); free(G->near.t); free(G->near.s);
+    free(T->perm); free(T->begin); free(T->end); free(T->child0); free(T->child1); free(T->parent);
+    free(T->level); free(T->bmin); free(T->bmax);
+    free(G->xyz); free(G->tri);
+    free(G);
+}
+
+/* counts: clusters, farfield blocks, nearfield blocks, largest rank, points k */
+void or_gca_sizes(const or_gca* G, int64_t* out) {
+    out[0] = G->T.count;
+    out[1] = G->far.n;
+    out[2] = G->near.n;
+    int mx = 0;
+    for (int64_t c = 0; c < G->T.count; ++c)
+        if (G->rank[c] > mx) mx = G->rank[c];
+    out[3] = mx;
+    out[4] = 6 * G->q * G->q;
+}
+void or_gca_ranks(const or_gca* G, int32_t* rank) {
+    for (int64_t c = 0; c < G->T.count; ++c) rank[c] = G->rank[c];
+}
+void or_gca_pivots(const or_gca* G, int64_t c, int64_t* piv) {
+    memcpy(piv, G->piv[c], G->rank[c] * sizeof(int64_t));
+}
+/* V_t of a leaf (|t| x rank) or E_c (rank_c x rank_parent); -1 otherwise */
+int or_gca_basis(const or_gca* G, int64_t c, double* out) {
+    if (c < 0 || c >= G->T.count) return -1;
+    if (G->T.child0[c] < 0) {
+        memcpy(out, G->V[c], (size_t)(G->T.end[c] - G->T.begin[c]) * G->rank[c] * sizeof(double));
+        return 0;
+    }
+    return -1;
+}
+int or_gca_transfer(const or_gca* G, int64_t c, double* out) {
+    if (c <= 0 || c >= G->T.count) return -1;
+    const int64_t p = G->T.parent[c];
+    memcpy(out, G->E[c], (size_t)G->rank[c] * G->rank[p] * sizeof(double));
+    return 0;
+}
+/* L of cluster c and its row set (user indices); returns the row count. */
+int64_t or_gca_L(const or_gca* G, int64_t c, int64_t* rows, double* L) { return gca_L(G, c, rows, L); }
+int64_t or_gca_rowcount(const or_gca* G, int64_t c) {
+    const tree_t* T = &G->T;
+    if (T->child0[c] < 0) return T->end[c] - T->begin[c];
+    return G->rank[T->child0[c]] + G->rank[T->child1[c]];
+}
+
+/* y = G~ x (x, y column-major n x nrhs, user order): step 6 and the passes of
+ * section 2 with the GCA bases; parts selects farfield / nearfield. */
+void or_gca_matvec(const or_gca* G, const double* x, int nrhs, double* y, int parts) {
+    const tree_t* T = &G->T;
+    const int64_t n = T->n, nc = T->count;
+    const int K = G->kmax;
+    double* xh = calloc((size_t)nc * K * nrhs, sizeof(double));
+    double* yh = calloc((size_t)nc * K * nrhs, sizeof(double));
+    for (int64_t i = 0; i < n * nrhs; ++i) y[i] = 0.0;
+    if (parts & OR_PART_FAR) {
+        /* leaves: xh_t = V_t^T x|_t */
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T->child0[c] >= 0) continue;
+            const int rk = G->rank[c];
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a)
+                for (int nu = 0; nu < rk; ++nu)
+                    for (int r = 0; r < nrhs; ++r)
+                        xh[(c * K + nu) * nrhs + r] += G->V[c][(a - T->begin[c]) * rk + nu] * x[T->perm[a] + r * n];
+        }
+        /* upward, children after their parents in pre-order: reverse order */
+        for (int64_t c = nc - 1; c >= 1; --c) {
+            const int64_t p = T->parent[c];
+            const int kc = G->rank[c], kp = G->rank[p];
+            for (int nu = 0; nu < kp; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int a = 0; a < kc; ++a) s += G->E[c][a * kp + nu] * xh[(c * K + a) * nrhs + r];
+                    xh[(p * K + nu) * nrhs + r] += s;
+                }
+        }
+        /* coupling S_ts = G|_{t^ x s^} */
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t b = G->far_ptr[t]; b < G->far_ptr[t + 1]; ++b) {
+                const int64_t s = G->far_col[b];
+                for (int nu = 0; nu < G->rank[t]; ++nu)
+                    for (int mu = 0; mu < G->rank[s]; ++mu) {
+                        const double e = or_entry(OR_SLP, &G->mesh, G->piv[t][nu], G->piv[s][mu], G->q_ss);
+                        for (int r = 0; r < nrhs; ++r) yh[(t * K + nu) * nrhs + r] += e * xh[(s * K + mu) * nrhs + r];
+                    }
+            }
+        /* downward: parents before children */
+        for (int64_t c = 1; c < nc; ++c) {
+            const int64_t p = T->parent[c];
+            const int kc = G->rank[c], kp = G->rank[p];
+            for (int a = 0; a < kc; ++a)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < kp; ++nu) s += G->E[c][a * kp + nu] * yh[(p * K + nu) * nrhs + r];
+                    yh[(c * K + a) * nrhs + r] += s;
+                }
+        }
+        /* leaves: y|_t += V_t yh_t */
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T->child0[c] >= 0) continue;
+            const int rk = G->rank[c];
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < rk; ++nu) s += G->V[c][(a - T->begin[c]) * rk + nu] * yh[(c * K + nu) * nrhs + r];
+                    y[T->perm[a] + r * n] += s;
+                }
+        }
+    }
+    if (parts & OR_PART_NEAR) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t b = G->near_ptr[t]; b < G->near_ptr[t + 1]; ++b) {
+                const int64_t s = G->near_col[b];
+                for (int64_t a = T->begin[t]; a < T->end[t]; ++a) {
+                    const int64_t i = T->perm[a];
+                    for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                        const int64_t j = T->perm[bb];
+                        const double e = or_entry(OR_SLP, &G->mesh, i, j, G->q_ss);
+                        for (int r = 0; r < nrhs; ++r) y[i + r * n] += e * x[j + r * n];
+                    }
+                }
+            }
+    }
+    free(xh);
+    free(yh);
+}

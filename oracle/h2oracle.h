@@ -135,6 +135,24 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
 int or_num_threads(void);
 void or_set_threads(int n);
 
+/* Green cross approximation of the single layer G (section 4); the
+ * specification is written out before or_gca_create in h2oracle.c. */
+typedef struct or_gca or_gca;
+int or_gca_boundary_rule(const double* lo, const double* hi, int q, double* z, double* w, double* nz);
+double or_gca_green(const double* lo, const double* hi, int q, const double* x, const double* y);
+int or_gca_aca(const double* L, int rows, int cols, double eps, int kmax, int* tau, int* sigma);
+or_gca* or_gca_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int q, double eta, int leaf,
+                      double eps, int kmax, int q_ss);
+void or_gca_destroy(or_gca* G);
+void or_gca_sizes(const or_gca* G, int64_t* out);
+void or_gca_ranks(const or_gca* G, int32_t* rank);
+void or_gca_pivots(const or_gca* G, int64_t c, int64_t* piv);
+int or_gca_basis(const or_gca* G, int64_t c, double* out);
+int or_gca_transfer(const or_gca* G, int64_t c, double* out);
+int64_t or_gca_L(const or_gca* G, int64_t c, int64_t* rows, double* L);
+int64_t or_gca_rowcount(const or_gca* G, int64_t c);
+void or_gca_matvec(const or_gca* G, const double* x, int nrhs, double* y, int parts);
+
 #ifdef __cplusplus
 }
 #endif
