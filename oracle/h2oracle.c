@@ -1753,10 +1753,13 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
 /*     t^_{t1} followed by t^_{t2} (the children's pivots, nested form).     */
 /*  4. Adaptive cross approximation of L with full pivoting (the pivoted LU  */
 /*     of section 3): residual R = L; while rank < kmax and rank < min(rows, */
-/*     cols): pivot (i*, j*) = the first entry of largest |R| in row-major   */
-/*     order; stop if R_i*j* = 0 or (rank > 0 and |R_i*j*| <= eps |first    */
-/*     pivot|); R_ij -= R_ij* (R_i*j / R_i*j*) for all i, j (the row of the  */
-/*     pivot divided first); tau += i*, sigma += j*.                          */
+/*     cols): with M = max |R|, the pivot (i*, j*) is the first entry in     */
+/*     row-major order with |R_ij| >= (1 - 2^-40) M (the paper leaves ties   */
+/*     open; this makes the choice insensitive to rounding far below 2^-40,  */
+/*     so exact ties of symmetric meshes resolve alike everywhere); stop if  */
+/*     M = 0 or (rank > 0 and |R_i*j*| <= eps |first pivot|);                */
+/*     R_ij -= R_ij* (R_i*j / R_i*j*) for all i, j (the row of the pivot      */
+/*     divided first); tau += i*, sigma += j*.                                */
 /*  5. V^_t = L|_{rows x sigma} (L|_{tau x sigma})^{-1} (eq. gca_onesided);  */
 /*     t^ = rows[tau] in pivot order.  Leaf: V_t = V^_t.  Otherwise          */
 /*     (E_t1; E_t2) = V^_t split by rows (eq. (transfer)).                   */
@@ -1893,17 +1896,15 @@ int or_gca_aca(const double* L, int rows, int cols, double eps, int kmax, int* t
     int k = 0;
     double first = 0.0;
     while (k < kmax && k < rows && k < cols) {
-        int bi = 0, bj = 0;
-        double best = -1.0;
-        for (int i = 0; i < rows; ++i)
-            for (int j = 0; j < cols; ++j)
-                if (fabs(R[(size_t)i * cols + j]) > best) {
-                    best = fabs(R[(size_t)i * cols + j]);
-                    bi = i;
-                    bj = j;
-                }
+        double M = 0.0;
+        for (size_t e = 0; e < (size_t)rows * cols; ++e)
+            if (fabs(R[e]) > M) M = fabs(R[e]);
+        if (M == 0.0) break;
+        const double thr = M * (1.0 - ldexp(1.0, -40));
+        size_t e = 0;
+        while (fabs(R[e]) < thr) ++e;
+        const int bi = (int)(e / cols), bj = (int)(e % cols);
         const double p = R[(size_t)bi * cols + bj];
-        if (p == 0.0) break;
         if (k == 0) first = fabs(p);
         else if (fabs(p) <= eps * first) break;
         tau[k] = bi;

@@ -106,11 +106,17 @@ def test_aca_exact_on_low_rank_and_pivots_are_maxima(orc):
         t, s = tau[:r], sigma[:r]
         R = M[:, s] @ np.linalg.solve(M[np.ix_(t, s)], M[t, :])
         assert np.max(np.abs(R - M)) < 1e-10 * np.max(np.abs(M))
-        # brute force: each pivot is the largest entry of the residual of the earlier ones
+        # brute force: each pivot is the first entry (row-major) within 2^-40 of
+        # the largest of the residual of the earlier ones
         Rz = M.copy()
         for i, j in zip(tau[:r], sigma[:r]):
-            assert abs(Rz[i, j]) == np.max(np.abs(Rz))
+            A = np.abs(Rz)
+            first = np.flatnonzero(A.ravel() >= A.max() * (1 - 2.0 ** -40))[0]
+            assert (i, j) == divmod(int(first), Rz.shape[1])
             Rz = Rz - np.outer(Rz[:, j], Rz[i, :] / Rz[i, j])
+    # exact ties resolve to the first entry in row-major order
+    tau, sigma = orc.gca_aca(np.array([[1.0, 2.0], [2.0, -2.0]]), 0.0, 1)
+    assert (tau[0], sigma[0]) == (0, 1)
     # tolerance: stops once the pivot falls below eps times the first
     M = np.diag([1.0, 1e-3, 1e-7, 1e-12])
     tau, _ = orc.gca_aca(M, 1e-6, 10)
