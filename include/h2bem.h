@@ -70,6 +70,10 @@ extern "C" {
                            /* in TF32 with FP32 accumulation                        */
 #define H2BEM_MIXED_BF16 3 /* as MIXED_TF32 with BF16 operands                      */
 
+/* cluster bases of the farfield (h2bem_opts.basis) */
+#define H2BEM_BASIS_CHEBYSHEV 0 /* tensor Chebyshev interpolation of order m (section 3) */
+#define H2BEM_BASIS_GCA 1       /* Green cross approximation (section 4)                 */
+
 typedef struct h2bem_mesh h2bem_mesh;
 typedef struct h2bem_tree h2bem_tree;
 typedef struct h2bem_op h2bem_op;
@@ -111,7 +115,25 @@ typedef struct {
                         /*    every apply then streams them instead of evaluating the quadrature. */
                         /*    The nearfield sum of each row is formed by one CTA without atomics. */
                         /*    0 (default): nearfield on the fly in every apply                     */
+    int basis;          /* H2BEM_BASIS_CHEBYSHEV (default) or H2BEM_BASIS_GCA: cluster bases by   */
+                        /*    Green cross approximation (section 4) for the single layer in the   */
+                        /*    FP64 and MIXED_FP32 tiers.  For every cluster t, Green's             */
+                        /*    representation formula on the box omega_t (B_t grown by its largest  */
+                        /*    side on every side, section 5) is discretised by gca_q x gca_q       */
+                        /*    Gauss points on each face; adaptive cross approximation of the       */
+                        /*    matrix L = (A C) of the potentials of the rows (the triangles of a   */
+                        /*    leaf, the children's pivot triangles otherwise) picks pivot          */
+                        /*    triangles t^ and gives V^_t = L|sigma (L|tau,sigma)^-1: the leaf     */
+                        /*    basis of a leaf, the transfer matrices of the children otherwise     */
+                        /*    (eq. (transfer)).  The coupling matrices are the Galerkin entries    */
+                        /*    G|_{t^ x s^} (7 x 7-point rule), evaluated once at set-up and stored */
+                        /*    in the tier's precision; the interpolation order m is then unused    */
+                        /*    for the farfield.  The construction runs on the host (OpenMP).       */
+    int gca_q;          /* GCA: Gauss points per face axis (1..16, default 4; 6 q^2 points)        */
+    int gca_kmax;       /* GCA: largest rank of a cluster (1..64, default 64)                      */
     int reserved[1];    /* must be zero                                                            */
+    double gca_eps;     /* GCA: ACA stops when a pivot falls to gca_eps times the first            */
+                        /*    (>= 0, default 1e-6)                                                 */
 } h2bem_opts;
 
 /* Statistics of an operator (counts are exact, from its own block lists). */
@@ -140,6 +162,9 @@ typedef struct {
                                /* its result serves (t, s) and (s, t)          */
     int64_t near_stored_bytes; /* device bytes of the stored nearfield blocks */
                                /* (opts.store_near), else 0                    */
+    int64_t far_stored_bytes;  /* device bytes of stored farfield matrices     */
+                               /* (GCA: coupling and transfer matrices)        */
+    double mean_rank;          /* GCA: mean rank over the clusters; else k     */
 } h2bem_stats;
 
 /* Message of the last failed call on the calling thread (empty if none).
@@ -188,12 +213,24 @@ int h2bem_tree_destroy(h2bem_tree* tree);
 int h2bem_blocks(const h2bem_tree* tree, double eta, int64_t* nfar, int64_t* nnear, int64_t* far_t, int64_t* far_s,
                  int64_t* near_t, int64_t* near_s);
 
+/* ---- Green cross approximation (host only; section 4) -------------------- */
+/* The GCA cluster bases that h2bem_operator_create builds with opts->basis =
+ * H2BEM_BASIS_GCA (gca_q, gca_kmax, gca_eps of opts; the other fields are
+ * ignored), for inspection: rank[c] for every cluster (nclusters values) and
+ * the pivot triangles of every cluster as tree positions, cluster by cluster
+ * in pivot order (npiv = the sum of the ranks).  Any output may be NULL; call
+ * with piv = NULL to get npiv first.  Errors: ARG (NULL mesh, tree or opts,
+ * sizes, gca_q, gca_kmax, gca_eps). */
+int h2bem_gca_bases(const h2bem_mesh* mesh, const h2bem_tree* tree, const h2bem_opts* opts, int64_t* rank,
+                    int64_t* npiv, int64_t* piv);
+
 /* ---- operator -------------------------------------------------------------- */
 int h2bem_opts_default(h2bem_opts* opts);
 /* Selects G (H2BEM_SLP) or K (H2BEM_DLP), interpolation order m (1..6,
  * k = m^3, section 3) and admissibility eta; builds the block lists and
  * uploads mesh, tree and lists to the current CUDA device.  opts may be NULL
- * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts), OOM, CUDA. */
+ * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts; GCA bases
+ * with the double layer, a tensor-core tier or recompute_basis), OOM, CUDA. */
 int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
                           const h2bem_opts* opts, h2bem_op** out);
 /* Many meshes as one operator (batching).  Builds the block-diagonal operator
@@ -245,7 +282,7 @@ int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, 
  *   h2bem_apply_transpose in the operator's tier.
  * All buffers device memory; asynchronous on `stream`.  Work vectors are
  * allocated on the first call.  Errors: ARG (NULL, double-layer operator,
- * nrhs, ld, host pointers), CUDA, OOM. */
+ * GCA bases, nrhs, ld, host pointers), CUDA, OOM. */
 int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz, double* dx,
                void* stream);
 /* y = W x, the hypersingular operator on continuous piecewise-linear

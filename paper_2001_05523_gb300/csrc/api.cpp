@@ -632,6 +632,14 @@ struct h2bem_op {
     // hypersingular operator: triangles at each vertex (3 tau + corner), work vectors
     DevBuf vptr, vinc, hyp_z, hyp_w;
     int64_t hyp_cap = 0;
+    // Green cross approximation (opts.basis = GCA): rank and pivot tree
+    // positions per cluster, transfer matrices E_c and coupling matrices S_b
+    // stored compactly at eoff[c] / soff[b] (FP64, or FP32 in MIXED_FP32); the
+    // leaf bases are basisV, zero-padded to k columns
+    int gca = 0;
+    DevBuf g_rank, g_pivoff, g_piv, g_eoff, g_E, g_soff, g_S;
+    int64_t gca_bytes = 0;
+    double gca_mean_rank = 0.0;
     // CUDA graph of the launch sequence (use_graph)
     int use_graph = 0;
     int64_t ws_gen = 0;
@@ -673,6 +681,10 @@ extern "C" int h2bem_opts_default(h2bem_opts* opts) {
     opts->q_ss = 5;
     opts->precision = H2BEM_FP64;
     opts->cache_singular = 0;
+    opts->basis = H2BEM_BASIS_CHEBYSHEV;
+    opts->gca_q = 4;
+    opts->gca_kmax = h2::kGcaMaxRank;
+    opts->gca_eps = 1e-6;
     return H2BEM_OK;
 }
 
@@ -853,6 +865,133 @@ static int build_near_store(h2bem_op* op, const h2bem_tree& tree, const std::vec
     return H2BEM_OK;
 }
 
+// GCA cluster bases (gca.cpp on the host), uploaded compactly; the leaf bases
+// into basisV zero-padded to op->k = the largest rank rounded up to 4; the
+// coupling matrices of the farfield CSR evaluated on the GPU (k_gca.cu).
+static int gca_setup(h2bem_op* op, const h2bem_mesh* mesh, const h2bem_tree* tree, const h2bem_opts& opts) {
+    const int64_t n = op->n, nc = op->nc;
+    std::vector<double> glx, glw;
+    gauss_legendre(opts.gca_q, glx, glw);
+    h2::GcaSetup S{};
+    S.xyz = mesh->xyz.data();
+    S.tri = mesh->tri.data();
+    S.n = n;
+    S.nc = nc;
+    S.perm = tree->perm.data();
+    S.begin = tree->begin.data();
+    S.end = tree->end.data();
+    S.child0 = tree->child0.data();
+    S.child1 = tree->child1.data();
+    S.level = tree->level.data();
+    S.bmin = tree->bmin.data();
+    S.bmax = tree->bmax.data();
+    S.q = opts.gca_q;
+    S.kmax = opts.gca_kmax;
+    S.eps = opts.gca_eps;
+    S.gl_x = glx.data();
+    S.gl_w = glw.data();
+    S.ru = op->consts.ru;
+    S.rv = op->consts.rv;
+    S.rw = op->consts.rw;
+    h2::GcaResult R;
+    h2::gca_build(S, R);
+    int kmax = 1;
+    double rsum = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        kmax = std::max(kmax, R.rank[c]);
+        rsum += R.rank[c];
+    }
+    op->gca = 1;
+    op->gca_mean_rank = nc ? rsum / nc : 0.0;
+    const int K = (kmax + 3) / 4 * 4;
+    op->k = K;
+    const bool f32 = op->precision != H2BEM_FP64;
+    const size_t es = f32 ? sizeof(float) : sizeof(double);
+    // leaf bases [pos][K]
+    std::vector<double> B((size_t)n * K, 0.0);
+    for (int64_t c = 0; c < nc; ++c) {
+        if (tree->child0[c] >= 0) continue;
+        const int rk = R.rank[c];
+        for (int64_t a = tree->begin[c]; a < tree->end[c]; ++a)
+            for (int nu = 0; nu < rk; ++nu)
+                B[(size_t)a * K + nu] = R.V[R.voff[c] + (a - tree->begin[c]) * rk + nu];
+    }
+    std::vector<int64_t> eoff(nc, 0);
+    for (int64_t c = 0; c < nc; ++c) eoff[c] = R.eoff[c] < 0 ? 0 : R.eoff[c];
+    // coupling offsets in the order of the farfield CSR
+    std::vector<int64_t> soff(op->far.col.size() + 1, 0);
+    for (int r = 0; r < op->far.nrows(); ++r) {
+        const int t = op->far.rows[r];
+        for (int b = op->far.ptr[r]; b < op->far.ptr[r + 1]; ++b)
+            soff[b + 1] = soff[b] + (int64_t)R.rank[t] * R.rank[op->far.col[b]];
+    }
+    int rc;
+    if (f32) {
+        std::vector<float> Bf(B.begin(), B.end()), Ef(R.E.begin(), R.E.end());
+        if ((rc = upload(op->basisV, Bf)) || (rc = upload(op->g_E, Ef))) return rc;
+    } else {
+        if ((rc = upload(op->basisV, B)) || (rc = upload(op->g_E, R.E))) return rc;
+    }
+    if ((rc = upload(op->g_rank, R.rank)) || (rc = upload(op->g_pivoff, R.piv_off)) || (rc = upload(op->g_piv, R.piv)) ||
+        (rc = upload(op->g_eoff, eoff)) || (rc = upload(op->g_soff, soff)))
+        return rc;
+    const int64_t ns = soff.back();
+    if ((rc = op->g_S.alloc((size_t)std::max<int64_t>(ns, 1) * es))) return rc;
+    h2::launch_gca_assemble(op->geom(), op->consts, op->far.nrows(), op->far.drows.as<int>(), op->far.dptr.as<int>(),
+                            op->far.dcol.as<int>(), op->g_rank.as<int>(), op->g_pivoff.as<int>(), op->g_piv.as<int>(),
+                            op->g_soff.as<int64_t>(), f32, op->g_S.p, 0);
+    CU(cudaGetLastError());
+    op->gca_bytes = (int64_t)((size_t)ns * es + R.E.size() * es);
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_gca_bases(const h2bem_mesh* mesh, const h2bem_tree* tree, const h2bem_opts* opts_in,
+                               int64_t* rank, int64_t* npiv, int64_t* piv) {
+    if (!mesh || !tree || !opts_in) return fail(H2BEM_ERR_ARG, "gca_bases: NULL argument");
+    if (tree->n != mesh->nt) return fail(H2BEM_ERR_ARG, "gca_bases: tree and mesh differ in size");
+    const h2bem_opts& opts = *opts_in;
+    if (opts.gca_q < 1 || opts.gca_q > 16 || opts.gca_kmax < 1 || opts.gca_kmax > h2::kGcaMaxRank ||
+        !(opts.gca_eps >= 0.0) || !std::isfinite(opts.gca_eps))
+        return fail(H2BEM_ERR_ARG, "gca_bases: gca_q in 1..16, gca_kmax in 1..%d, gca_eps >= 0", h2::kGcaMaxRank);
+    std::vector<double> glx, glw;
+    gauss_legendre(opts.gca_q, glx, glw);
+    const double r15 = std::sqrt(15.0);
+    const double a = (6.0 - r15) / 21.0, b = (6.0 + r15) / 21.0;
+    const double wa = (155.0 - r15) / 1200.0, wb = (155.0 + r15) / 1200.0;
+    const double u[7] = {1.0 / 3.0, a, 1.0 - 2.0 * a, a, b, 1.0 - 2.0 * b, b};
+    const double v[7] = {1.0 / 3.0, a, a, 1.0 - 2.0 * a, b, b, 1.0 - 2.0 * b};
+    const double w[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    h2::GcaSetup S{};
+    S.xyz = mesh->xyz.data();
+    S.tri = mesh->tri.data();
+    S.n = tree->n;
+    S.nc = tree->nc;
+    S.perm = tree->perm.data();
+    S.begin = tree->begin.data();
+    S.end = tree->end.data();
+    S.child0 = tree->child0.data();
+    S.child1 = tree->child1.data();
+    S.level = tree->level.data();
+    S.bmin = tree->bmin.data();
+    S.bmax = tree->bmax.data();
+    S.q = opts.gca_q;
+    S.kmax = opts.gca_kmax;
+    S.eps = opts.gca_eps;
+    S.gl_x = glx.data();
+    S.gl_w = glw.data();
+    S.ru = u;
+    S.rv = v;
+    S.rw = w;
+    h2::GcaResult R;
+    h2::gca_build(S, R);
+    if (rank)
+        for (int64_t c = 0; c < tree->nc; ++c) rank[c] = R.rank[c];
+    if (npiv) *npiv = (int64_t)R.piv.size();
+    if (piv)
+        for (size_t e = 0; e < R.piv.size(); ++e) piv[e] = R.piv[e];
+    return H2BEM_OK;
+}
+
 static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blocks* prebuilt, int kernel, int m,
                        double eta, const h2bem_opts* opts_in, h2bem_op** out) {
     if (!out) return fail(H2BEM_ERR_ARG, "operator_create: out is NULL");
@@ -874,6 +1013,19 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         return fail(H2BEM_ERR_ARG, "operator_create: the tensor-core tiers need m <= 5 (k <= 128), got m = %d", m);
     for (int r : opts.reserved)
         if (r) return fail(H2BEM_ERR_ARG, "operator_create: reserved option fields must be zero");
+    if (opts.basis != H2BEM_BASIS_CHEBYSHEV && opts.basis != H2BEM_BASIS_GCA)
+        return fail(H2BEM_ERR_ARG, "operator_create: unknown basis %d", opts.basis);
+    if (opts.basis == H2BEM_BASIS_GCA) {
+        if (kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "operator_create: GCA bases are built for the single layer");
+        if (opts.precision != H2BEM_FP64 && opts.precision != H2BEM_MIXED_FP32)
+            return fail(H2BEM_ERR_ARG, "operator_create: GCA bases run in the FP64 and MIXED_FP32 tiers");
+        if (opts.recompute_basis) return fail(H2BEM_ERR_ARG, "operator_create: GCA bases are stored (recompute_basis = 0)");
+        if (opts.gca_q < 1 || opts.gca_q > 16) return fail(H2BEM_ERR_ARG, "operator_create: gca_q must be in 1..16");
+        if (opts.gca_kmax < 1 || opts.gca_kmax > h2::kGcaMaxRank)
+            return fail(H2BEM_ERR_ARG, "operator_create: gca_kmax must be in 1..%d", h2::kGcaMaxRank);
+        if (!(opts.gca_eps >= 0.0) || !std::isfinite(opts.gca_eps))
+            return fail(H2BEM_ERR_ARG, "operator_create: gca_eps must be finite and >= 0");
+    }
     for (int64_t c = 0; c < tree->nc; ++c)
         if (tree->child0[c] < 0 && tree->end[c] - tree->begin[c] > kMaxLeaf)
             return fail(H2BEM_ERR_ARG, "operator_create: leaf clusters may hold at most %d triangles", kMaxLeaf);
@@ -1210,7 +1362,9 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     CU(cudaGetLastError());
     // leaf bases: V_t[i, nu] = int L_nu; for the double layer also W_s[j, nu] = int n_j . grad L_nu
     for (int l : op->leaves_h) op->max_leaf = std::max(op->max_leaf, (int)(tree->end[l] - tree->begin[l]));
-    if (!op->recompute_basis) {
+    if (opts.basis == H2BEM_BASIS_GCA) {
+        if ((rc = gca_setup(op.get(), mesh, tree, opts))) return rc;
+    } else if (!op->recompute_basis) {
         const bool v32 = op->precision != H2BEM_FP64;
         if ((rc = op->basisV.alloc((size_t)n * op->k * (v32 ? sizeof(float) : sizeof(double))))) return rc;
         h2::launch_leaf_basis(op->geom(), op->tree(), op->consts, op->basis_rule.as<double>(), (int)op->nleaves,
@@ -1350,6 +1504,8 @@ extern "C" int h2bem_stats_get(const h2bem_op* op, h2bem_stats* st) {
     st->regular_pairs = op->near_pairs - op->sing[0] - 2 * (op->sing[1] + op->sing[2]);
     st->regular_evals = op->regular_evals;
     st->near_stored_bytes = op->nst_bytes;
+    st->far_stored_bytes = op->gca_bytes;
+    st->mean_rank = op->gca ? op->gca_mean_rank : (double)op->k;
     for (int i = 0; i < 5; ++i) st->launch_variant[i] = op->last_variant[i];
     st->k = op->k;
     st->launches = op->launches;
@@ -1553,7 +1709,9 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     const bool in_dlp = dlp && !transpose;   // W_s on the input side
     const bool out_dlp = dlp && transpose;   // W_s on the output side
     const int near_ker = !dlp ? h2::SLP : transpose ? h2::DLP_T : h2::DLP;
-    const Csr& far = transpose ? op->far_t : op->far;
+    // GCA: the single layer is symmetric and its coupling matrices are stored
+    // for the blocks of `far`, so A^T x runs the forward farfield
+    const Csr& far = (transpose && !op->gca) ? op->far_t : op->far;
     auto mark = [&](int i) {
         if (timed) cudaEventRecord(op->ev[i], s);
     };
@@ -1602,7 +1760,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         }
         CU(cudaMemsetAsync(w.yp, 0, op->n * NR * sizeof(double), s));
     }
-    if (tune_now && op->nfar > 0 && tc_kind(op, xh64, yh64) < 0 && (op->m == 4 || op->m == 5)) {
+    if (tune_now && op->nfar > 0 && !op->gca && tc_kind(op, xh64, yh64) < 0 && (op->m == 4 || op->m == 5)) {
         tu.coup.nsl = -1;  // tuned below, once x-hat is ready
     }
     nl += 1;
@@ -1626,8 +1784,14 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                                            w.xp, w.xh, s);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2 + fo);
-        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-            h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, s);
+        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L) {
+            if (op->gca)
+                h2::launch_gca_updown(true, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
+                                      op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
+                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.xh, s);
+            else
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, s);
+        }
         mark(3 + fo);
         if (tune_now && tu.coup.nsl == -1) {
             float best = 1e30f;
@@ -1650,10 +1814,21 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         }
         h2::LaunchCfg cfg_near, cfg_coup;
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
-        run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, s);
+        if (op->gca)
+            h2::launch_gca_coupling(fp32, NR, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
+                                    op->g_rank.as<int>(), op->g_soff.as<int64_t>(), op->g_S.p, (int)op->k, w.xh, w.yh,
+                                    s);
+        else
+            run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, s);
         mark(4 + fo);
-        for (size_t L = 0; L < op->level_parents.size(); ++L)
-            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, s);
+        for (size_t L = 0; L < op->level_parents.size(); ++L) {
+            if (op->gca)
+                h2::launch_gca_updown(false, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
+                                      op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
+                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.yh, s);
+            else
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, s);
+        }
         mark(5 + fo);
         if (op->recompute_basis)
             h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
@@ -1994,6 +2169,7 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
                           double* dx, void* stream) {
     if (!op || !w || !x || !dxyz) return fail(H2BEM_ERR_ARG, "grad: NULL argument");
     if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "grad: the shape gradient is available for the single layer");
+    if (op->gca) return fail(H2BEM_ERR_ARG, "grad: the shape gradient runs through Chebyshev bases, not GCA bases");
     if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "grad: nrhs must be in 1..64");
     if (ld < op->n) return fail(H2BEM_ERR_ARG, "grad: leading dimension must be >= n");
     if (!is_device_ptr(w) || !is_device_ptr(x) || !is_device_ptr(dxyz) || (dx && !is_device_ptr(dx)))

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace h2 {
 
@@ -70,6 +71,46 @@ struct LaunchCfg {
 };
 // CTAs of `func` resident on the whole GPU at once (occupancy x SMs)
 int resident_ctas(const void* func, int threads, size_t smem);
+
+// ---- Green cross approximation (gca.cpp, k_gca.cu) -----------------------
+// Inputs of the host construction of the GCA cluster bases: mesh, cluster
+// tree (tree positions; boxes nc x 3), the Gauss-Legendre rule on [0, 1] with
+// q points for the faces of d omega_t, the 7-point rule (u, v, weight), the
+// ACA tolerance and the largest rank.
+struct GcaSetup {
+    const double* xyz;
+    const int32_t* tri;
+    int64_t n, nc;
+    const int64_t *perm, *begin, *end, *child0, *child1, *level;
+    const double *bmin, *bmax;
+    int q, kmax;
+    double eps;
+    const double *gl_x, *gl_w;
+    const double *ru, *rv, *rw;
+};
+// Result: rank per cluster; pivot tree positions (CSR piv_off / piv, pivot
+// order); leaf bases V (|t| x rank_t row-major, rows in tree order) at voff[t];
+// transfer matrices E_c (rank_c x rank_parent row-major) at eoff[c]; -1 where
+// absent.
+struct GcaResult {
+    std::vector<int> rank, piv_off, piv;
+    std::vector<int64_t> voff, eoff;
+    std::vector<double> V, E;
+};
+int gca_build(const GcaSetup& setup, GcaResult& result);
+constexpr int kGcaMaxRank = 64;  // largest GCA rank the kernels stage
+// coupling matrices S_b = G|_{t^ x s^} of the farfield CSR (rows / ptr / col)
+// at element offsets soff[b], FP64 quadrature stored as FP32 (f32) or FP64
+void launch_gca_assemble(const Geom& g, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                         const int* rank, const int* piv_off, const int* piv, const int64_t* soff, bool f32, void* S,
+                         cudaStream_t s);
+// one tree level: x-hat_p = sum_c E_c^T x-hat_c (up) or y-hat_c += E_c y-hat_p
+void launch_gca_updown(bool up, bool f32, int NR, int np, const int* parents, const int* child0, const int* child1,
+                       const int* rank, const int64_t* eoff, const void* E, int K, void* v, cudaStream_t s);
+// y-hat_t = sum_b S_b x-hat_s over the farfield blocks of every row t
+void launch_gca_coupling(bool f32, int NR, int nrows, const int* rows, const int* ptr, const int* col,
+                         const int* rank, const int64_t* soff, const void* S, int K, const void* xh, void* yh,
+                         cudaStream_t s);
 
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libh2bem.so")
 
 H2BEM_OK, H2BEM_ERR_ARG, H2BEM_ERR_MESH, H2BEM_ERR_OOM, H2BEM_ERR_CUDA, H2BEM_ERR_TIMEOUT, H2BEM_ERR_STATE = range(7)
 H2BEM_SLP, H2BEM_DLP = 0, 1
+H2BEM_BASIS_CHEBYSHEV, H2BEM_BASIS_GCA = 0, 1
 H2BEM_FP64, H2BEM_MIXED_FP32, H2BEM_MIXED_TF32, H2BEM_MIXED_BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": H2BEM_FP64, "mixed_fp32": H2BEM_MIXED_FP32, "mixed_tf32": H2BEM_MIXED_TF32,
               "mixed_bf16": H2BEM_MIXED_BF16}
@@ -28,7 +29,7 @@ EXPORTED = [
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
     "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad", "h2bem_apply_mass", "h2bem_apply_hypersingular",
-    "h2bem_cg",
+    "h2bem_cg", "h2bem_gca_bases",
 ]
 
 
@@ -42,7 +43,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("q_ss", ctypes.c_int), ("precision", ctypes.c_int), ("cache_singular", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("store_near", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("basis", ctypes.c_int), ("gca_q", ctypes.c_int), ("gca_kmax", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1), ("gca_eps", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -52,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("singular_pairs", ctypes.c_int64 * 3), ("k", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("last_apply_ms", ctypes.c_double),
                 ("stage_ms", ctypes.c_double * 8), ("launch_variant", ctypes.c_int64 * 5),
-                ("regular_evals", ctypes.c_int64), ("near_stored_bytes", ctypes.c_int64)]
+                ("regular_evals", ctypes.c_int64), ("near_stored_bytes", ctypes.c_int64),
+                ("far_stored_bytes", ctypes.c_int64), ("mean_rank", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -84,6 +87,7 @@ def lib():
             "h2bem_tree_export": [vp] * 8,
             "h2bem_tree_destroy": [vp],
             "h2bem_blocks": [vp, d, vp, vp, vp, vp, vp, vp],
+            "h2bem_gca_bases": [vp, vp, vp, vp, vp, vp],
             "h2bem_opts_default": [vp],
             "h2bem_operator_create": [vp, vp, i32, i32, d, vp, pp],
             "h2bem_operator_destroy": [vp],
@@ -170,6 +174,19 @@ def h2bem_blocks(tree, eta: float):
     nt, ns = np.zeros(nn.value, np.int64), np.zeros(nn.value, np.int64)
     _check(lib().h2bem_blocks(tree, float(eta), None, None, _np_ptr(ft), _np_ptr(fs), _np_ptr(nt), _np_ptr(ns)))
     return (ft, fs), (nt, ns)
+
+
+def h2bem_gca_bases(mesh, tree, nclusters: int, q: int = 4, kmax: int = 64, eps: float = 1e-6):
+    """Ranks (per cluster) and pivot tree positions (cluster by cluster) of the
+    GCA cluster bases, computed on the host."""
+    o = h2bem_opts_default()
+    o.basis, o.gca_q, o.gca_kmax, o.gca_eps = H2BEM_BASIS_GCA, int(q), int(kmax), float(eps)
+    rank = np.zeros(nclusters, np.int64)
+    npiv = ctypes.c_int64()
+    _check(lib().h2bem_gca_bases(mesh, tree, ctypes.byref(o), _np_ptr(rank), ctypes.byref(npiv), None))
+    piv = np.zeros(npiv.value, np.int64)
+    _check(lib().h2bem_gca_bases(mesh, tree, ctypes.byref(o), None, None, _np_ptr(piv)))
+    return rank, piv
 
 
 def h2bem_opts_default() -> Opts:
@@ -297,7 +314,8 @@ class BatchOperator:
     def __init__(self, meshes, kernel: str | int = "slp", m: int = 4, eta: float = 2.0, leaf_size: int = 32,
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
-                 recompute_basis: bool = False, store_near: bool = False):
+                 recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
+                 gca_kmax: int = 64, gca_eps: float = 1e-6):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -312,6 +330,9 @@ class BatchOperator:
         o.singular_fp64 = int(singular_fp64)
         o.recompute_basis = int(recompute_basis)
         o.store_near = int(store_near)
+        if gca:
+            o.basis = H2BEM_BASIS_GCA
+            o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
     def close(self):
@@ -345,7 +366,8 @@ class Operator:
     def __init__(self, vertices, triangles, kernel: str | int = "slp", m: int = 4, eta: float = 2.0,
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
-                 recompute_basis: bool = False, store_near: bool = False):
+                 recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
+                 gca_kmax: int = 64, gca_eps: float = 1e-6):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -359,6 +381,9 @@ class Operator:
         o.singular_fp64 = int(singular_fp64)
         o.recompute_basis = int(recompute_basis)
         o.store_near = int(store_near)
+        if gca:
+            o.basis = H2BEM_BASIS_GCA
+            o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):

@@ -119,3 +119,26 @@ def test_operator_argument_checks(H):
     with pytest.raises(H.H2bemError) as e:
         H.h2bem_operator_create(mh8, big, 0, 4, 2.0)
     assert e.value.code == H.H2BEM_ERR_ARG
+
+
+@pytest.mark.parametrize("mk,q,kmax,eps", [(lambda: I.sphere(16), 4, 64, 1e-6), (lambda: I.jitter(I.sphere(12), 0.01, 3), 3, 40, 1e-5),
+                                           (lambda: I.cube(9), 4, 64, 1e-7), (lambda: I.ellipsoid(14), 2, 24, 0.0)])
+def test_gca_bases_match_oracle(H, orc, mk, q, kmax, eps):
+    """The library's host construction of the GCA bases (section 4) picks the
+    same ranks and pivot triangles as the oracle's, cluster by cluster: the
+    adaptive cross approximation is a sequence of discrete choices, and the
+    pivot rule (first entry within 2^-40 of the largest) makes them agree
+    although the two compute L with their own Gauss rules and sums."""
+    m = mk()
+    mh = H.h2bem_mesh_create(m.vertices, m.triangles)
+    th = H.h2bem_tree_build(mh, 32)
+    tr = H.h2bem_tree_export(th, m.nt)
+    nc = len(tr["begin"])
+    rank, piv = H.h2bem_gca_bases(mh, th, nc, q=q, kmax=kmax, eps=eps)
+    G = orc.GCA(m, q=q, eps=eps, kmax=kmax)
+    assert np.array_equal(rank, G.ranks().astype(np.int64))
+    off = np.concatenate([[0], np.cumsum(rank)])
+    for c in range(nc):
+        assert np.array_equal(tr["perm"][piv[off[c]:off[c + 1]]], G.pivots(c)), c
+    H.h2bem_tree_destroy(th)
+    H.h2bem_mesh_destroy(mh)
