@@ -918,12 +918,13 @@ static int gca_setup(h2bem_op* op, const h2bem_mesh* mesh, const h2bem_tree* tre
     }
     std::vector<int64_t> eoff(nc, 0);
     for (int64_t c = 0; c < nc; ++c) eoff[c] = R.eoff[c] < 0 ? 0 : R.eoff[c];
-    // coupling offsets in the order of the farfield CSR
+    // coupling offsets in the order of the farfield CSR, every block on a
+    // 16-byte boundary (sizes rounded up to 4 elements) for the asynchronous copies
     std::vector<int64_t> soff(op->far.col.size() + 1, 0);
     for (int r = 0; r < op->far.nrows(); ++r) {
         const int t = op->far.rows[r];
         for (int b = op->far.ptr[r]; b < op->far.ptr[r + 1]; ++b)
-            soff[b + 1] = soff[b] + (int64_t)R.rank[t] * R.rank[op->far.col[b]];
+            soff[b + 1] = soff[b] + ((int64_t)R.rank[t] * R.rank[op->far.col[b]] + 3) / 4 * 4;
     }
     int rc;
     if (f32) {

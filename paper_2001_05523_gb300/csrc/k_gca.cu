@@ -23,7 +23,9 @@ constexpr double kInv4Pi = 0.07957747154594766788;
 // S_b[a][c] = int_{tau_i} int_{tau_j} g for the pivot triangles i = t^[a],
 // j = s^[c] of every farfield block b = (t, s): the 7 x 7-point rule of the
 // nearfield's regular pairs, in FP64 (pivot triangles of admissible clusters
-// are apart, so no pair shares a vertex); stored as T.
+// are apart, so no pair shares a vertex); stored as T, column by column
+// (S_b[a][c] at c rank_t + a), so that the lanes of a warp owning rows a read
+// a column in one coalesced access.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gca_assemble(Geom g, Consts c, const int* __restrict__ rows,
                                                       const int* __restrict__ ptr, const int* __restrict__ col,
@@ -35,8 +37,8 @@ __global__ void __launch_bounds__(256) k_gca_assemble(Geom g, Consts c, const in
     const int n = g.n;
     for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
         const int s = col[b], rs = rank[s];
-        for (int e = threadIdx.x; e < rt * rs; e += blockDim.x) {
-            const int i = piv[piv_off[t] + e / rs], j = piv[piv_off[s] + e % rs];
+        for (int e = threadIdx.x; e < rt * rs; e += blockDim.x) {  // column-major: e = c rt + a
+            const int i = piv[piv_off[t] + e % rt], j = piv[piv_off[s] + e / rt];
             double yq[3][7];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
@@ -118,46 +120,116 @@ __global__ void __launch_bounds__(128) k_gca_updown(const int* __restrict__ pare
 }
 
 // Coupling: y-hat_t = sum_b S_b x-hat_s over the farfield blocks b = (t, s) of
-// row t, one CTA per row; S_b and x-hat_s staged in shared memory, item
-// (nu, r) = e of the rank_t x NR outputs per thread e, e + 256, ...
+// row t, one CTA per row.  The blocks' S_b (stored column-major, each at a
+// 16-byte aligned offset) and x-hat_s stream through a ring of NST shared-
+// memory stages filled by 16-byte cp.async copies, NST - 1 blocks ahead of
+// the one being multiplied, so that the HBM reads of later blocks overlap the
+// products.  Output item (a, r) = e of the rank_t x NR entries per thread
+// e, e + 256, ...
+namespace {
+// NR consecutive values of a cluster vector row, by 16-byte loads
+template <typename T, int NR>
+struct XRow {
+    static __device__ __forceinline__ void load(const T* p, T* v) {
+        constexpr int W = 16 / (int)sizeof(T);
+        if constexpr (NR % W == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; r += W) {
+                if constexpr (W == 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(p + r);
+                    v[r] = q.x, v[r + 1] = q.y, v[r + 2] = q.z, v[r + 3] = q.w;
+                } else {
+                    const double2 q = *reinterpret_cast<const double2*>(p + r);
+                    v[r] = q.x, v[r + 1] = q.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = p[r];
+        }
+    }
+};
+template <typename T>
+struct GcaStages {
+    static constexpr int NST = sizeof(T) == 4 ? 3 : 2;              // ring depth
+    static constexpr int V = 16 / (int)sizeof(T);                   // elements per 16-byte copy
+    static constexpr int SMAX = kGcaMaxRank * kGcaMaxRank;          // S_b
+    template <int NR>
+    static constexpr int xmax() { return (kGcaMaxRank * NR + V - 1) / V * V; }
+    template <int NR>
+    static constexpr size_t bytes() { return sizeof(T) * (size_t)NST * (SMAX + xmax<NR>()); }
+};
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+}  // namespace
+
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_gca_coupling(const int* __restrict__ rows, const int* __restrict__ ptr,
                                                       const int* __restrict__ col, const int* __restrict__ rank,
                                                       const int64_t* __restrict__ soff, const T* __restrict__ S,
                                                       int K, const T* __restrict__ xh, T* __restrict__ yh) {
-    constexpr int J = (kGcaMaxRank * NR + 255) / 256;
+    using G = GcaStages<T>;
+    constexpr int NST = G::NST, V = G::V, SMAX = G::SMAX, XMAX = G::template xmax<NR>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sS = reinterpret_cast<T*>(smem_raw);                                  // [rank_t][rank_s]
-    T* sx = reinterpret_cast<T*>(smem_raw + sizeof(T) * kGcaMaxRank * kGcaMaxRank);  // [rank_s][NR]
+    T* ring = reinterpret_cast<T*>(smem_raw);  // NST x (S_b [SMAX], x-hat_s [XMAX])
     const int t = rows[blockIdx.x];
     const int rt = rank[t];
     const int tid = threadIdx.x;
-    T acc[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) acc[j] = 0;
-    for (int b = ptr[blockIdx.x]; b < ptr[blockIdx.x + 1]; ++b) {
-        const int s = col[b], rs = rank[s];
-        __syncthreads();
+    // thread (a, g): output row a of y-hat_t for every right-hand side, over
+    // the columns mu = g, g + NG, ... of each block
+    const int NG = 256 / max(rt, 1);
+    const int a = tid % max(rt, 1), g = tid / max(rt, 1);
+    const bool active = g < NG && rt > 0;
+    const int b0 = ptr[blockIdx.x], nb = ptr[blockIdx.x + 1] - b0;
+    auto issue = [&](int j) {
+        const int b = b0 + j, s = col[b], rs = rank[s];
+        T* st = ring + (size_t)(j % NST) * (SMAX + XMAX);
         const T* Sb = S + soff[b];
-        for (int e = tid; e < rt * rs; e += blockDim.x) sS[e] = Sb[e];
-        for (int e = tid; e < rs * NR; e += blockDim.x) sx[e] = xh[(int64_t)s * K * NR + e];
-        __syncthreads();
+        const T* xs = xh + (int64_t)s * K * NR;
+        const int nS = (rt * rs + V - 1) / V, nX = (rs * NR + V - 1) / V;
+        for (int e = tid; e < nS; e += 256) cpa16(st + e * V, Sb + e * V);
+        for (int e = tid; e < nX; e += 256) cpa16(st + SMAX + e * V, xs + e * V);
+    };
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int e = tid + 256 * j;
-            if (e < rt * NR) {
-                const int nu = e / NR, r = e % NR;
-                const T* Srow = sS + nu * rs;
-                T sum = 0;
-                for (int mu = 0; mu < rs; ++mu) sum += Srow[mu] * sx[mu * NR + r];
-                acc[j] += sum;
-            }
-        }
+    for (int j = 0; j < NST - 1; ++j) {
+        if (j < nb) issue(j);
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    T acc[NR];
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const int e = tid + 256 * j;
-        if (e < rt * NR) yh[(int64_t)t * K * NR + e] = acc[j];
+    for (int r = 0; r < NR; ++r) acc[r] = 0;
+    for (int j = 0; j < nb; ++j) {
+        if (j + NST - 1 < nb) issue(j + NST - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(NST - 1) : "memory");
+        __syncthreads();
+        const T* sS = ring + (size_t)(j % NST) * (SMAX + XMAX);
+        const T* sx = sS + SMAX;
+        const int rs = rank[col[b0 + j]];
+        if (active)
+            for (int mu = g; mu < rs; mu += NG) {
+                const T sv = sS[mu * rt + a];
+                T xv[NR];
+                XRow<T, NR>::load(sx + mu * NR, xv);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += sv * xv[r];
+            }
+        __syncthreads();  // the stage is refilled NST - 1 blocks later
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // sum over the column slices g (the ring is free now)
+    T* red = ring;  // [NG][rt][NR]
+    if (active)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[((size_t)g * rt + a) * NR + r] = acc[r];
+    __syncthreads();
+    for (int e = tid; e < rt * NR; e += 256) {
+        T sum = 0;
+        for (int q = 0; q < NG; ++q) sum += red[(size_t)q * rt * NR + e];
+        yh[(int64_t)t * K * NR + e] = sum;
     }
 }
 
@@ -201,7 +273,7 @@ void launch_gca_updown(bool up, bool f32, int NR, int np, const int* parents, co
 template <typename T, int NR>
 static void coupling_go(int nrows, const int* rows, const int* ptr, const int* col, const int* rank,
                         const int64_t* soff, const void* S, int K, const void* xh, void* yh, cudaStream_t s) {
-    const size_t smem = sizeof(T) * ((size_t)kGcaMaxRank * kGcaMaxRank + (size_t)kGcaMaxRank * NR);
+    constexpr size_t smem = GcaStages<T>::template bytes<NR>();
     cudaFuncSetAttribute(k_gca_coupling<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gca_coupling<T, NR><<<nrows, 256, smem, s>>>(rows, ptr, col, rank, soff, (const T*)S, K, (const T*)xh, (T*)yh);
 }
