@@ -91,6 +91,7 @@ def lib():
             L.or_test_poly_Q.argtypes = [vp]
             L.or_test_poly_Q.restype = d
             L.or_h2_rows.argtypes = [vp, vp, i64, vp, i32, vp]
+            L.or_h2_matvec_subtree.argtypes = [vp, i64, vp, i32, vp]
             L.or_h2_update_geometry.argtypes = [vp, vp]
             L.or_h2_grad.argtypes = [vp, vp, vp, i32, vp, i32]
             L.or_h2_grad.restype = i32
@@ -375,6 +376,15 @@ class H2:
         if lib().or_h2_grad(self.h, _p(w), _p(x), x.shape[0], _p(g), int(parts)):
             raise ValueError("gradient is available for the single layer only")
         return g
+
+    def matvec_subtree(self, c0: int, x: np.ndarray) -> np.ndarray:
+        """Forward product restricted to the rows of cluster c0: (nrhs, n), other rows 0."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        y = np.zeros_like(x)
+        lib().or_h2_matvec_subtree(self.h, int(c0), _p(x), x.shape[0], _p(y))
+        return y
 
     def rows(self, rows, x: np.ndarray) -> np.ndarray:
         rows = np.ascontiguousarray(rows, dtype=np.int64)

@@ -2177,3 +2177,108 @@ void or_gca_matvec(const or_gca* G, const double* x, int nrhs, double* y, int pa
     free(xh);
     free(yh);
 }
+
+/* The rows of y = A x (forward, A = G or K in its H^2 form) for the triangles
+ * of cluster c0 only: the leaf forward transformation and the upward pass run
+ * in full; the coupling, downward pass, leaf backward transformation and
+ * nearfield only where they reach the rows of c0 (c0's ancestors and
+ * descendants).  The other rows of y are 0.  Used as a bounded sample of the
+ * full product. */
+void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y) {
+    const tree_t* T = &H->T;
+    const int64_t n = T->n, nc = T->count;
+    const int k = H->k;
+    double* xh = calloc((size_t)nc * k * nrhs, sizeof(double));
+    double* yh = calloc((size_t)nc * k * nrhs, sizeof(double));
+    char* act = calloc(nc, 1);
+    for (int64_t c = 0; c < nc; ++c) {
+        const int anc = T->begin[c] <= T->begin[c0] && T->end[c] >= T->end[c0];
+        const int des = T->begin[c] >= T->begin[c0] && T->end[c] <= T->end[c0];
+        act[c] = (char)(anc || des);
+    }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0) continue;
+        int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int nu = 0; nu < k; ++nu)
+            for (int r = 0; r < nrhs; ++r) {
+                double s = 0.0;
+                for (int64_t a = 0; a < sz; ++a) s += H->W[c][a * k + nu] * x[T->perm[b + a] + r * n];
+                xh[(c * k + nu) * nrhs + r] = s;
+            }
+    }
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        if (T->child0[c] < 0) continue;
+        const int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q) {
+            const double* E = H->E[ch[q]];
+            for (int nu = 0; nu < k; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nup = 0; nup < k; ++nup) s += E[nup * k + nu] * xh[(ch[q] * k + nup) * nrhs + r];
+                    xh[(c * k + nu) * nrhs + r] += s;
+                }
+        }
+    }
+#pragma omp parallel
+    {
+        double* S = malloc((size_t)k * k * sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < nc; ++t) {
+            if (!act[t]) continue;
+            for (int64_t b = H->far_ptr[t]; b < H->far_ptr[t + 1]; ++b) {
+                const int64_t s = H->far_col[b];
+                coupling_matrix(H, t, s, S);
+                for (int nu = 0; nu < k; ++nu)
+                    for (int r = 0; r < nrhs; ++r) {
+                        double acc = 0.0;
+                        for (int mu = 0; mu < k; ++mu) acc += S[nu * k + mu] * xh[(s * k + mu) * nrhs + r];
+                        yh[(t * k + nu) * nrhs + r] += acc;
+                    }
+            }
+        }
+        free(S);
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] < 0 || !act[c]) continue;
+        const int64_t ch[2] = {T->child0[c], T->child1[c]};
+        for (int q = 0; q < 2; ++q) {
+            if (!act[ch[q]]) continue;
+            const double* E = H->E[ch[q]];
+            for (int nup = 0; nup < k; ++nup)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < k; ++nu) s += E[nup * k + nu] * yh[(c * k + nu) * nrhs + r];
+                    yh[(ch[q] * k + nup) * nrhs + r] += s;
+                }
+        }
+    }
+    for (int64_t i = 0; i < n * nrhs; ++i) y[i] = 0.0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (T->child0[c] >= 0 || !act[c] || T->begin[c] < T->begin[c0] || T->end[c] > T->end[c0]) continue;
+        const int64_t b = T->begin[c], sz = T->end[c] - b;
+        for (int64_t a = 0; a < sz; ++a) {
+            const int64_t i = T->perm[b + a];
+            for (int r = 0; r < nrhs; ++r) {
+                double s = 0.0;
+                for (int nu = 0; nu < k; ++nu) s += H->V[c][a * k + nu] * yh[(c * k + nu) * nrhs + r];
+                y[i + r * n] += s;
+            }
+        }
+        for (int64_t q = H->near_ptr[c]; q < H->near_ptr[c + 1]; ++q) {
+            const int64_t s = H->near_col[q];
+            for (int64_t a = 0; a < sz; ++a) {
+                const int64_t i = T->perm[b + a];
+                for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                    const int64_t j = T->perm[bb];
+                    const double e = or_entry(H->kernel, &H->mesh, i, j, H->q_ss);
+                    for (int r = 0; r < nrhs; ++r) y[i + r * n] += e * x[j + r * n];
+                }
+            }
+        }
+    }
+    free(act);
+    free(xh);
+    free(yh);
+}

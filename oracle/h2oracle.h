@@ -130,6 +130,8 @@ double or_ss_moment(int type, int q, int a, int b, int c, int d);
 double or_test_poly_P(const double* x);
 double or_test_poly_Q(const double* y);
 void or_h2_rows(const or_h2* H, const int64_t* rows, int64_t nrows, const double* x, int nrhs, double* y);
+/* rows of the forward product for the triangles of cluster c0 only (others 0) */
+void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y);
 void or_h2_update_geometry(or_h2* H, const double* xyz);
 int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, double* gX, int parts);
 int or_num_threads(void);

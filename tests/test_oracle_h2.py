@@ -244,3 +244,21 @@ def test_double_layer_h2_error(orc, m2k):
     e4 = np.linalg.norm(orc.H2(m2k, 1, m=4).matvec(x) - yd) / np.linalg.norm(yd)
     e6 = np.linalg.norm(orc.H2(m2k, 1, m=6).matvec(x) - yd) / np.linalg.norm(yd)
     assert e4 < 5e-3 and e6 < e4 / 10
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_subtree_rows_equal_full_product(orc, kernel):
+    """or_h2_matvec_subtree (the bounded sample the benchmark times on the host)
+    gives exactly the rows of the full product for the triangles of a cluster,
+    and zero elsewhere."""
+    mesh = I.jitter(I.sphere(12), 0.01, 2)
+    H = orc.H2(mesh, kernel, m=3)
+    x = I.rhs(mesh.nt, 2, seed=4)
+    full = H.matvec(x)
+    tr = H.tree()
+    for c0 in (0, 1, 5, int(np.flatnonzero(tr["child0"] < 0)[7])):
+        y = H.matvec_subtree(c0, x)
+        rows = tr["perm"][tr["begin"][c0]:tr["end"][c0]]
+        assert np.allclose(y[:, rows], full[:, rows], rtol=1e-12, atol=1e-14 * np.abs(full).max())
+        others = np.setdiff1d(np.arange(mesh.nt), rows)
+        assert np.all(y[:, others] == 0)
