@@ -131,7 +131,12 @@ typedef struct {
                         /*    for the farfield.  The construction runs on the host (OpenMP).       */
     int gca_q;          /* GCA: Gauss points per face axis (1..16, default 4; 6 q^2 points)        */
     int gca_kmax;       /* GCA: largest rank of a cluster (1..64, default 64)                      */
-    int reserved[1];    /* must be zero                                                            */
+    int tc_wait_test;   /* 0 (default).  1, for tests of the fault path only: in the tensor-core   */
+                        /*    coupling the first pipeline wait of every CTA with three or more     */
+                        /*    blocks waits on a barrier that nothing signals, with a bound of      */
+                        /*    about 50 us, so that it expires; the CTA then drains what it issued */
+                        /*    (normal bound), frees its tensor memory and returns, and the apply   */
+                        /*    reports H2BEM_ERR_TIMEOUT (its result is invalid)                   */
     double gca_eps;     /* GCA: ACA stops when a pivot falls to gca_eps times the first            */
                         /*    (>= 0, default 1e-6)                                                 */
 } h2bem_opts;
@@ -331,7 +336,8 @@ int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, in
  * [5] leaf backward, [6] nearfield regular (with opts.store_near: the stored
  * nearfield, which runs right after [0]), [7] nearfield singular.
  * h2bem_stats_get then also reports an expired bounded wait of the
- * tensor-core coupling (TIMEOUT). */
+ * tensor-core coupling (TIMEOUT); for operators of the tensor-core tiers it
+ * reports one of any completed apply. */
 int h2bem_apply_timed(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
 
 /* Allocation-free y = A x (the paper has no counterpart: this is a service

@@ -637,6 +637,7 @@ struct h2bem_op {
     // stored compactly at eoff[c] / soff[b] (FP64, or FP32 in MIXED_FP32); the
     // leaf bases are basisV, zero-padded to k columns
     int gca = 0;
+    int tc_wait_test = 0;  // opts.tc_wait_test (tests of the tensor-core timeout path)
     DevBuf g_rank, g_pivoff, g_piv, g_eoff, g_E, g_soff, g_S;
     int64_t gca_bytes = 0;
     double gca_mean_rank = 0.0;
@@ -1012,8 +1013,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if ((opts.precision == H2BEM_MIXED_TF32 && !h2::coupling_tc_supported(m, 0)) ||
         (opts.precision == H2BEM_MIXED_BF16 && !h2::coupling_tc_supported(m, 2)))
         return fail(H2BEM_ERR_ARG, "operator_create: the tensor-core tiers need m <= 5 (k <= 128), got m = %d", m);
-    for (int r : opts.reserved)
-        if (r) return fail(H2BEM_ERR_ARG, "operator_create: reserved option fields must be zero");
+    if (opts.tc_wait_test != 0 && opts.tc_wait_test != 1)
+        return fail(H2BEM_ERR_ARG, "operator_create: tc_wait_test must be 0 or 1");
     if (opts.basis != H2BEM_BASIS_CHEBYSHEV && opts.basis != H2BEM_BASIS_GCA)
         return fail(H2BEM_ERR_ARG, "operator_create: unknown basis %d", opts.basis);
     if (opts.basis == H2BEM_BASIS_GCA) {
@@ -1050,6 +1051,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     op->singular_fp64 = opts.singular_fp64 ? 1 : 0;
     op->recompute_basis = opts.recompute_basis ? 1 : 0;
     op->store_near = opts.store_near ? 1 : 0;
+    op->tc_wait_test = opts.tc_wait_test;
     if (opts.autotune >= 2) {  // a fixed launch variant for every width and direction
         const int v = opts.autotune - 2;
         for (auto& slot : op->tuned)
@@ -1622,7 +1624,7 @@ static void run_coupling(const h2bem_op* op, const h2::Tree& t, const h2::Consts
     const int kind = tc_kind(op, xh64, yh64);
     if (kind >= 0)
         h2::launch_coupling_tc(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(), kind, NR,
-                               (const float*)xh, (float*)yh, s);
+                               (const float*)xh, (float*)yh, op->tc_wait_test, s);
     else
         h2::launch_coupling(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
                             op->precision == H2BEM_FP64 ? 0 : 1, xh64, yh64, NR, xh, yh, cfg, s);
@@ -2014,9 +2016,17 @@ static int apply_impl(h2bem_op* op, const double* x, int64_t ldx, int nrhs, doub
     return H2BEM_OK;
 }
 
-// Stage times of the last timed apply: waits for its last event.
+// Stage times of the last timed apply: waits for its last event.  Operators of
+// the tensor-core tiers also read the timeout flag of the coupling kernels
+// (synchronous), so an expired wait of any completed apply is reported here.
 static int resolve_timing(h2bem_op* op) {
-    if (!op->timing_pending) return H2BEM_OK;
+    if (!op->timing_pending) {
+        if (op->precision == H2BEM_MIXED_TF32 || op->precision == H2BEM_MIXED_BF16) {
+            if (h2::coupling_tc_status(true))
+                return fail(H2BEM_ERR_TIMEOUT, "stats_get: a bounded wait of the tensor-core coupling expired");
+        }
+        return H2BEM_OK;
+    }
     op->timing_pending = false;
     CU(cudaEventSynchronize(op->ev[9]));
     float ms = 0.f;

@@ -112,6 +112,24 @@ void launch_gca_coupling(bool f32, int NR, int nrows, const int* rows, const int
                          const int* rank, const int64_t* soff, const void* S, int K, const void* xh, void* yh,
                          cudaStream_t s);
 
+// ---- double layer with piecewise-linear trial functions (k_p1.cu) --------
+// corner gather x3[(c n + pos) NR + r] = x[vid_c(pos) + r ldx]; vertex sum of
+// y3 (same layout) into y; regular nearfield over the ordered blocks (forward:
+// y += K1 x from x3; transposed: y3 += from x in tree order); Sauter-Schwab
+// values (6 per canonical edge / vertex pair) and their application
+void launch_p1_gather(int n, int NR, int nrhs, const int* vid, const double* x, int64_t ldx, double* x3,
+                      cudaStream_t s);
+void launch_p1_scatter(int nv, int n, int NR, int nrhs, const int* vptr, const int* inc, const int* iperm,
+                       const double* y3, double* y, int64_t ldy, cudaStream_t s);
+void launch_p1_near(bool transpose, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
+                    const int* rows, const int* ptr, const int* col, const double* xin, double* yout, cudaStream_t s);
+void launch_p1_sing_eval(const Geom& g, int np, const int* lo, const int* hi, const int* code, const double* tab,
+                         int npts, double* vals, cudaStream_t s);
+void launch_p1_sing_apply(bool transpose, int n, int np, int NR, const int* lo, const int* hi, const int* code,
+                          const double* vals, const double* xin, double* yout, cudaStream_t s);
+void launch_leaf_forward_stored_acc(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool xh64,
+                                    int NR, const double* B, const double* xp, void* xh, cudaStream_t s);
+
 // ---- launchers (stream-ordered; no synchronisation) -----------------------
 void launch_geom(const double* xyz, const int* tri, const int* perm, int n, const Consts& c, double* v, double* area,
                  double* nrm, double* ctr, int* vid, float* qo, double* qa, float* chl, double* plane, float* nef,
@@ -213,7 +231,7 @@ void launch_coupling(const Tree& t, const Consts& c, int nrows, const int* rows,
 // clears) the device flag an expired wait sets (H2BEM_ERR_TIMEOUT, else 0).
 bool coupling_tc_supported(int m, int kind);
 void launch_coupling_tc(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                        int kind, int NR, const float* xh, float* yh, cudaStream_t s);
+                        int kind, int NR, const float* xh, float* yh, int stall_test, cudaStream_t s);
 int coupling_tc_status(bool reset);
 
 }  // namespace h2

@@ -39,6 +39,7 @@ namespace {
 constexpr double kInv4Pi = 0.07957747154594766788;
 constexpr int kThreads = 128;
 constexpr long long kWaitCycles = 2000000000LL;  // about a second at the SM clock
+constexpr long long kTestWaitCycles = 100000LL;   // the test wait on a barrier nothing signals (~50 us)
 
 __device__ int g_tc_status;  // 0, or H2BEM_ERR_TIMEOUT's value after an expired wait
 
@@ -68,7 +69,7 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
            ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -171,13 +172,14 @@ __device__ __forceinline__ void gen_row(unsigned char* stage, int nu, const floa
 template <int M, int NR, int KIND>
 __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, const int* __restrict__ rows,
                                                           const int* __restrict__ ptr, const int* __restrict__ col,
-                                                          const float* __restrict__ xh, float* __restrict__ yh) {
+                                                          const float* __restrict__ xh, float* __restrict__ yh,
+                                                          int stall_test) {
     using S = TcShape<M, NR, KIND>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     __shared__ float2 zt[3 * M];  // nodes of t as FP32 (hi, lo)
     __shared__ float D2[3 * M * M];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];  // two pipeline stages; [2] is never signalled (stall_test)
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = rows[blockIdx.x];
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[2])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -233,7 +236,12 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
         const int st = b & 1;
         unsigned char* stage = base + st * S::STAGE;
         if (b >= 2) {
-            bool w = mbar_wait(smem_u32(&mbar[st]), ((b - 2) >> 1) & 1);
+            // stall_test: the first of these waits is on mbar[2], which nothing
+            // signals, with a short bound, so that it expires (the issued MMAs
+            // are still drained below with the normal bound)
+            const bool stall = stall_test && b == 2;
+            bool w = stall ? mbar_wait(smem_u32(&mbar[2]), 0, kTestWaitCycles)
+                           : mbar_wait(smem_u32(&mbar[st]), ((b - 2) >> 1) & 1);
             ok = __syncthreads_and(w) != 0;
             if (!ok) break;
         }
@@ -361,33 +369,33 @@ __global__ void __launch_bounds__(kThreads) k_coupling_tc(Tree t, Consts c, cons
 
 template <int M, int NR, int KIND>
 static void tc_go(int nrows, const Tree& t, const Consts& c, const int* rows, const int* ptr, const int* col,
-                  const float* xh, float* yh, cudaStream_t s) {
+                  const float* xh, float* yh, int stall_test, cudaStream_t s) {
     constexpr size_t smem = TcShape<M, NR, KIND>::SMEM;
     cudaFuncSetAttribute(k_coupling_tc<M, NR, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coupling_tc<M, NR, KIND><<<nrows, kThreads, smem, s>>>(t, c, rows, ptr, col, xh, yh);
+    k_coupling_tc<M, NR, KIND><<<nrows, kThreads, smem, s>>>(t, c, rows, ptr, col, xh, yh, stall_test);
 }
 
 template <int M, int KIND>
 static void tc_nr(int NR, int nrows, const Tree& t, const Consts& c, const int* rows, const int* ptr, const int* col,
-                  const float* xh, float* yh, cudaStream_t s) {
+                  const float* xh, float* yh, int st, cudaStream_t s) {
     switch (NR) {
-        case 1: tc_go<M, 1, KIND>(nrows, t, c, rows, ptr, col, xh, yh, s); break;
-        case 4: tc_go<M, 4, KIND>(nrows, t, c, rows, ptr, col, xh, yh, s); break;
-        case 8: tc_go<M, 8, KIND>(nrows, t, c, rows, ptr, col, xh, yh, s); break;
-        default: tc_go<M, 16, KIND>(nrows, t, c, rows, ptr, col, xh, yh, s); break;
+        case 1: tc_go<M, 1, KIND>(nrows, t, c, rows, ptr, col, xh, yh, st, s); break;
+        case 4: tc_go<M, 4, KIND>(nrows, t, c, rows, ptr, col, xh, yh, st, s); break;
+        case 8: tc_go<M, 8, KIND>(nrows, t, c, rows, ptr, col, xh, yh, st, s); break;
+        default: tc_go<M, 16, KIND>(nrows, t, c, rows, ptr, col, xh, yh, st, s); break;
     }
 }
 
 bool coupling_tc_supported(int m, int kind) { return m >= 1 && m <= (kind == 1 ? 4 : 5); }
 
 void launch_coupling_tc(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                        int kind, int NR, const float* xh, float* yh, cudaStream_t s) {
+                        int kind, int NR, const float* xh, float* yh, int stall_test, cudaStream_t s) {
     if (nrows <= 0) return;
     auto go = [&](auto mk) {
         constexpr int M = decltype(mk)::value;
-        if (kind == 0) tc_nr<M, 0>(NR, nrows, t, c, rows, ptr, col, xh, yh, s);
-        else if (kind == 1) tc_nr<(M <= 4 ? M : 4), 1>(NR, nrows, t, c, rows, ptr, col, xh, yh, s);
-        else tc_nr<M, 2>(NR, nrows, t, c, rows, ptr, col, xh, yh, s);
+        if (kind == 0) tc_nr<M, 0>(NR, nrows, t, c, rows, ptr, col, xh, yh, stall_test, s);
+        else if (kind == 1) tc_nr<(M <= 4 ? M : 4), 1>(NR, nrows, t, c, rows, ptr, col, xh, yh, stall_test, s);
+        else tc_nr<M, 2>(NR, nrows, t, c, rows, ptr, col, xh, yh, stall_test, s);
     };
     switch (c.m) {
         case 1: go(std::integral_constant<int, 1>{}); break;

@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("store_near", ctypes.c_int),
                 ("basis", ctypes.c_int), ("gca_q", ctypes.c_int), ("gca_kmax", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1), ("gca_eps", ctypes.c_double)]
+                ("tc_wait_test", ctypes.c_int), ("gca_eps", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -315,7 +315,7 @@ class BatchOperator:
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
                  recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
-                 gca_kmax: int = 64, gca_eps: float = 1e-6):
+                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -333,6 +333,7 @@ class BatchOperator:
         if gca:
             o.basis = H2BEM_BASIS_GCA
             o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
+        o.tc_wait_test = int(tc_wait_test)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
     def close(self):
@@ -367,7 +368,7 @@ class Operator:
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
                  recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
-                 gca_kmax: int = 64, gca_eps: float = 1e-6):
+                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
@@ -384,6 +385,7 @@ class Operator:
         if gca:
             o.basis = H2BEM_BASIS_GCA
             o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
+        o.tc_wait_test = int(tc_wait_test)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 
     def close(self):

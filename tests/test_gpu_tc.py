@@ -106,3 +106,34 @@ def test_tc_tiers_reject_m6(H):
         with pytest.raises(H.H2bemError) as err:
             H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=6, precision=p)
         assert err.value.code == H.H2BEM_ERR_ARG
+
+
+def test_tc_timeout_path_reports_and_recovers(H, orc):
+    """The bounded waits of the tensor-core coupling: with opts.tc_wait_test the
+    first pipeline wait of every CTA with three or more blocks waits on a
+    barrier that nothing signals and gives up after about 50 us.  The CTA
+    drains the MMAs it issued (normal bound), frees its tensor memory and
+    returns; h2bem_stats_get reports H2BEM_ERR_TIMEOUT, the next call finds the
+    flag cleared, and an ordinary operator on the same context gives the
+    oracle's result."""
+    import torch
+
+    mesh = I.jitter(I.sphere(16), 0.01, 7)
+    x = I.rhs(mesh.nt, 4, seed=2)
+    xd = torch.from_numpy(x).cuda()
+    bad = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=4, eta=2.0, precision="mixed_tf32", tc_wait_test=True)
+    yd = torch.empty_like(xd)
+    H.h2bem_apply(bad.op, xd, yd)  # device buffers: asynchronous, no status here
+    torch.cuda.synchronize()
+    with pytest.raises(H.H2bemError) as e:
+        bad.stats()
+    assert e.value.code == H.H2BEM_ERR_TIMEOUT
+    bad.stats()  # the flag was read and cleared
+    # host buffers: the synchronous apply reports it itself
+    yh = np.zeros_like(x)
+    with pytest.raises(H.H2bemError) as e:
+        bad.apply(x, yh)
+    assert e.value.code == H.H2BEM_ERR_TIMEOUT
+    bad.close()
+    y = run(H, mesh, x, precision="mixed_tf32")
+    close(y, orc.H2(mesh, 0, m=4).matvec(x), TOL["mixed_tf32"], "after the timeout")
