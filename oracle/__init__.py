@@ -92,6 +92,8 @@ def lib():
             L.or_test_poly_Q.restype = d
             L.or_h2_rows.argtypes = [vp, vp, i64, vp, i32, vp]
             L.or_h2_matvec_subtree.argtypes = [vp, i64, vp, i32, vp]
+            L.or_h2_upward.argtypes = [vp, vp, i32, vp]
+            L.or_h2_matvec_subtree_from.argtypes = [vp, i64, vp, vp, i32, vp]
             L.or_h2_update_geometry.argtypes = [vp, vp]
             L.or_h2_grad.argtypes = [vp, vp, vp, i32, vp, i32]
             L.or_h2_grad.restype = i32
@@ -384,6 +386,24 @@ class H2:
             x = x[None, :]
         y = np.zeros_like(x)
         lib().or_h2_matvec_subtree(self.h, int(c0), _p(x), x.shape[0], _p(y))
+        return y
+
+    def upward(self, x: np.ndarray) -> np.ndarray:
+        """x-hat of every cluster (leaf forward transformation and upward pass)."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        xh = np.zeros((self.nclusters, self.k, x.shape[0]))
+        lib().or_h2_upward(self.h, _p(x), x.shape[0], _p(xh))
+        return xh
+
+    def matvec_subtree_from(self, c0: int, xh: np.ndarray, x: np.ndarray) -> np.ndarray:
+        """As matvec_subtree with x-hat from upward()."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        y = np.zeros_like(x)
+        lib().or_h2_matvec_subtree_from(self.h, int(c0), _p(xh), _p(x), x.shape[0], _p(y))
         return y
 
     def rows(self, rows, x: np.ndarray) -> np.ndarray:

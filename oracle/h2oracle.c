@@ -2184,18 +2184,13 @@ void or_gca_matvec(const or_gca* G, const double* x, int nrhs, double* y, int pa
  * nearfield only where they reach the rows of c0 (c0's ancestors and
  * descendants).  The other rows of y are 0.  Used as a bounded sample of the
  * full product. */
-void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y) {
+/* The leaf forward transformation and the upward pass of the forward product
+ * (x-hat of every cluster, [nc][k][nrhs]). */
+void or_h2_upward(const or_h2* H, const double* x, int nrhs, double* xh) {
     const tree_t* T = &H->T;
     const int64_t n = T->n, nc = T->count;
     const int k = H->k;
-    double* xh = calloc((size_t)nc * k * nrhs, sizeof(double));
-    double* yh = calloc((size_t)nc * k * nrhs, sizeof(double));
-    char* act = calloc(nc, 1);
-    for (int64_t c = 0; c < nc; ++c) {
-        const int anc = T->begin[c] <= T->begin[c0] && T->end[c] >= T->end[c0];
-        const int des = T->begin[c] >= T->begin[c0] && T->end[c] <= T->end[c0];
-        act[c] = (char)(anc || des);
-    }
+    for (size_t e = 0; e < (size_t)nc * k * nrhs; ++e) xh[e] = 0.0;
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t c = 0; c < nc; ++c) {
         if (T->child0[c] >= 0) continue;
@@ -2219,6 +2214,28 @@ void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs,
                     xh[(c * k + nu) * nrhs + r] += s;
                 }
         }
+    }
+}
+
+/* The rows for cluster c0 from x-hat of or_h2_upward (xh != NULL), else
+ * computing x-hat first. */
+void or_h2_matvec_subtree_from(const or_h2* H, int64_t c0, const double* xh_in, const double* x, int nrhs, double* y) {
+    const tree_t* T = &H->T;
+    const int64_t n = T->n, nc = T->count;
+    const int k = H->k;
+    double* xh_own = NULL;
+    if (!xh_in) {
+        xh_own = malloc((size_t)nc * k * nrhs * sizeof(double));
+        or_h2_upward(H, x, nrhs, xh_own);
+        xh_in = xh_own;
+    }
+    const double* xh = xh_in;
+    double* yh = calloc((size_t)nc * k * nrhs, sizeof(double));
+    char* act = calloc(nc, 1);
+    for (int64_t c = 0; c < nc; ++c) {
+        const int anc = T->begin[c] <= T->begin[c0] && T->end[c] >= T->end[c0];
+        const int des = T->begin[c] >= T->begin[c0] && T->end[c] <= T->end[c0];
+        act[c] = (char)(anc || des);
     }
 #pragma omp parallel
     {
@@ -2279,6 +2296,10 @@ void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs,
         }
     }
     free(act);
-    free(xh);
+    free(xh_own);
     free(yh);
+}
+
+void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y) {
+    or_h2_matvec_subtree_from(H, c0, NULL, x, nrhs, y);
 }

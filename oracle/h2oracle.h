@@ -132,6 +132,9 @@ double or_test_poly_Q(const double* y);
 void or_h2_rows(const or_h2* H, const int64_t* rows, int64_t nrows, const double* x, int nrhs, double* y);
 /* rows of the forward product for the triangles of cluster c0 only (others 0) */
 void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y);
+/* its two parts: x-hat of every cluster ([nc][k][nrhs]), and the rows from it */
+void or_h2_upward(const or_h2* H, const double* x, int nrhs, double* xh);
+void or_h2_matvec_subtree_from(const or_h2* H, int64_t c0, const double* xh, const double* x, int nrhs, double* y);
 void or_h2_update_geometry(or_h2* H, const double* xyz);
 int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, double* gX, int parts);
 int or_num_threads(void);

@@ -258,6 +258,7 @@ def test_subtree_rows_equal_full_product(orc, kernel):
     tr = H.tree()
     for c0 in (0, 1, 5, int(np.flatnonzero(tr["child0"] < 0)[7])):
         y = H.matvec_subtree(c0, x)
+        assert np.array_equal(y, H.matvec_subtree_from(c0, H.upward(x), x))
         rows = tr["perm"][tr["begin"][c0]:tr["end"][c0]]
         assert np.allclose(y[:, rows], full[:, rows], rtol=1e-12, atol=1e-14 * np.abs(full).max())
         others = np.setdiff1d(np.arange(mesh.nt), rows)
