@@ -306,6 +306,33 @@ int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int n
  * pointers), CUDA, OOM. */
 int h2bem_apply_hypersingular(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
                               void* stream);
+/* The double layer with continuous piecewise-linear trial functions (section 1,
+ * eq. (dlp) with phi_v the hat functions of the vertices; the Dirichlet basis
+ * of the paper's experiments, section 5):
+ *   (K1)_{i v} = int_{tau_i} int dg/dn_y(x, y) phi_v(y) dy dx,
+ * rows the triangles, columns the vertices.  Per pair of triangles the trial
+ * function is the barycentric coordinate of a corner of the source panel, so
+ * the H^2 form keeps the operator's tree, blocks, transfers, coupling and
+ * output basis V and takes per-corner source bases W1_c = int n . grad L
+ * lambda_c; regular nearfield pairs use the 7 x 7-point rule with lambda_c at
+ * the source points, pairs sharing a vertex the full Sauter-Schwab tensor
+ * rule (q_ss points per direction) with the same factors.  op must be a
+ * double-layer operator (H2BEM_DLP) with stored leaf bases.  The K1-specific
+ * parts (corner bases, nearfield and singular values) are FP64 in every tier;
+ * the passes follow the operator's tier.  The first call evaluates the corner
+ * bases and the singular values (synchronous); later calls are asynchronous.
+ *   transpose = 0: y = K1 x + alpha M1 x, x on the vertices (nv x nrhs,
+ *                  ldx >= nv, the vertex order of h2bem_mesh_create), y on the
+ *                  triangles (n x nrhs, ldy >= n, the caller's triangle order);
+ *   transpose = 1: y = K1^T x + alpha M1^T x, x on the triangles, y on the
+ *                  vertices;
+ * M1 is the P0 x P1 mass matrix, (M1)_{i v} = int_{tau_i} phi_v = |tau_i| / 3
+ * for the corners v of tau_i (alpha = -1/2 with x = -b gives the right-hand
+ * side (M1^T/2 - K1^T) b of the Neumann-to-Dirichlet system of section 1).
+ * 1 <= nrhs <= 64; device buffers.  Errors: ARG (NULL, kernel, recompute_basis,
+ * nrhs, ld, host pointers), CUDA, OOM. */
+int h2bem_apply_dlp_p1(h2bem_op* op, double alpha, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
+                       int transpose, void* stream);
 /* y = A x + alpha M x with the P0 mass matrix M = diag(|tau_i|) (section 1,
  * the mass matrix m_ij of eq. (matrix_dtn) with piecewise-constant columns).
  * With A = K and alpha = 1/2 this is the right-hand side (M/2 + K) b of the
@@ -328,6 +355,24 @@ int h2bem_apply_mass(h2bem_op* op, double alpha, const double* x, int64_t ldx, i
  * host pointers), CUDA, OOM. */
 int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol, int maxit,
              int* iters, double* relres, void* stream);
+/* Conjugate gradients for (W + m m^T) x = b, W the hypersingular operator on
+ * continuous piecewise-linear functions applied through this single layer
+ * (h2bem_apply_hypersingular; section 1), m a vector on the vertices (for
+ * example the integrals of the hat functions) or NULL.  W is symmetric
+ * positive semi-definite and annihilates constants (on a closed surface); the
+ * rank-one term m m^T with m . 1 != 0 makes the system definite.  Summing the
+ * equations gives (m . 1)(m . x) = 1 . b, so for data b = c + mu m with
+ * 1 . c = 0 (the right-hand side of a compatible system plus a multiple of m)
+ * the solution has m . x = mu: the constant that W leaves free (the
+ * Neumann-to-Dirichlet system W x = (M1^T/2 - K1^T) b of section 1 needs such
+ * a condition).  Every column is an independent system; x0 = 0; stop when
+ * |b - A x| <= rtol |b| or after maxit iterations.
+ *   m: device, nv values (or NULL); b, x: device, nv x nrhs (ldb, ldx >= nv);
+ *   iters, relres as for h2bem_cg.
+ * Synchronises `stream` in every iteration.  Errors: ARG (NULL, double-layer
+ * operator, nrhs, ld, rtol, maxit, host pointers), CUDA, OOM. */
+int h2bem_cg_hypersingular(h2bem_op* op, const double* m, const double* b, int64_t ldb, int nrhs, double* x,
+                           int64_t ldx, double rtol, int maxit, int* iters, double* relres, void* stream);
 /* As h2bem_apply with device buffers only, and records CUDA events around
  * each stage on `stream` (asynchronous: no host wait, so timed applies can run
  * back to back).  The next h2bem_stats_get waits for the last of them and

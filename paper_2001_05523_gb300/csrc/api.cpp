@@ -441,6 +441,54 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
+// Collapsed Gauss rule on the unit simplex, (u, v, weight) per point, exact
+// for total degree 3(m - 1): the leaf bases' rule.
+void basis_rule_host(int m, std::vector<double>& rule) {
+    const int qb = (3 * (m - 1) + 3) / 2;
+    std::vector<double> x, w;
+    gauss_legendre(std::max(qb, 1), x, w);
+    rule.clear();
+    for (size_t i = 0; i < x.size(); ++i)
+        for (size_t j = 0; j < x.size(); ++j) rule.insert(rule.end(), {x[i], (1.0 - x[i]) * x[j], 2.0 * w[i] * w[j] * (1.0 - x[i])});
+}
+
+// The full Sauter-Schwab tensor rule for pairs sharing an edge (type 1) or a
+// vertex (type 2), q Gauss points per direction: per point the reference
+// coordinates (x1, x2) on P and (y1, y2) on Q of T = {0 <= x2 <= x1 <= 1} and
+// the weight times the region's Jacobian (relative-coordinate Duffy maps with
+// (xi, a, b, c) in [0, 1]^4; the shared vertices are the first corners):
+//   edge, R1 (xi^3 a^2):   x = (xi, xi a c),             y = (xi (1-ab), xi a (1-b))
+//         R2 (xi^3 a^2 b): x = (xi, xi a),               y = (xi (1-abc), xi a b (1-c))
+//         R3 (xi^3 a^2 b): x = (xi (1-ab), xi a (1-b)),  y = (xi, xi a b c)
+//         R4 (xi^3 a^2 b): x = (xi (1-abc), xi a b (1-c)), y = (xi, xi a)
+//         R5 (xi^3 a^2 b): x = (xi (1-abc), xi a (1-bc)), y = (xi, xi a b)
+//   vertex (xi^3 b):       x = (xi, xi a), y = (xi b, xi b c), and x, y exchanged.
+void ss_full_table(int type, int q, std::vector<double>& tab) {
+    std::vector<double> g, w;
+    gauss_legendre(q, g, w);
+    tab.clear();
+    for (int i0 = 0; i0 < q; ++i0)
+        for (int i1 = 0; i1 < q; ++i1)
+            for (int i2 = 0; i2 < q; ++i2)
+                for (int i3 = 0; i3 < q; ++i3) {
+                    const double xi = g[i0], a = g[i1], b = g[i2], c = g[i3];
+                    const double wt = w[i0] * w[i1] * w[i2] * w[i3];
+                    const double x3 = xi * xi * xi;
+                    if (type == 1) {
+                        const double j1 = x3 * a * a, j2 = j1 * b;
+                        tab.insert(tab.end(), {xi, xi * a * c, xi * (1 - a * b), xi * a * (1 - b), wt * j1});
+                        tab.insert(tab.end(), {xi, xi * a, xi * (1 - a * b * c), xi * a * b * (1 - c), wt * j2});
+                        tab.insert(tab.end(), {xi * (1 - a * b), xi * a * (1 - b), xi, xi * a * b * c, wt * j2});
+                        tab.insert(tab.end(), {xi * (1 - a * b * c), xi * a * b * (1 - c), xi, xi * a, wt * j2});
+                        tab.insert(tab.end(), {xi * (1 - a * b * c), xi * a * (1 - b * c), xi, xi * a * b, wt * j2});
+                    } else {
+                        const double j = x3 * b;
+                        tab.insert(tab.end(), {xi, xi * a, xi * b, xi * b * c, wt * j});
+                        tab.insert(tab.end(), {xi * b, xi * b * c, xi, xi * a, wt * j});
+                    }
+                }
+}
+
 // Sauter-Schwab point tables after the exact integration of the monomial
 // factors (see k_sing.cu).  Rows: identical [aa, 2ab, bb, W]; edge [6 Gram
 // monomials, alpha, beta, gamma, W_g, W_dg]; vertex: the 1-D Gauss rule
@@ -613,7 +661,7 @@ struct h2bem_op {
     int64_t last_variant[5] = {0, 4, 4, 0, 0};
     DevBuf work;  // row counters of persistent launches (2 ints)
     DevBuf area_user;              // |tau_i| in the caller's order (mass term), made on first use
-    DevBuf cg_r, cg_p, cg_q, cg_s; // conjugate-gradient vectors and scalars
+    DevBuf cg_r, cg_p, cg_q, cg_s, cg_d; // conjugate-gradient vectors and scalars
     int64_t cg_cap = 0;
     // stored nearfield (store_near): the blocks of `near` and their offsets
     // (boff: block (t, s); boff_t: block (s, t) of the same list entry)
@@ -632,6 +680,13 @@ struct h2bem_op {
     // hypersingular operator: triangles at each vertex (3 tau + corner), work vectors
     DevBuf vptr, vinc, hyp_z, hyp_w;
     int64_t hyp_cap = 0;
+    // double layer with piecewise-linear trial functions (h2bem_apply_dlp_p1),
+    // made on first use: per-corner leaf bases W1_c [pos][k] (FP64), the
+    // Sauter-Schwab values of the edge / vertex pairs (6 per pair), and corner
+    // work vectors x3 / y3 [3][n][NR]
+    int p1_ready = 0;
+    DevBuf p1_W1[3], p1_vals[2], p1_tab, p1_x3, p1_y3;
+    int64_t p1_cap = 0;
     // Green cross approximation (opts.basis = GCA): rank and pivot tree
     // positions per cluster, transfer matrices E_c and coupling matrices S_b
     // stored compactly at eoff[c] / soff[b] (FP64, or FP32 in MIXED_FP32); the
@@ -1102,11 +1157,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     }
     // leaf-basis rule: collapsed Gauss, exact for total degree 3(m-1)
     {
-        const int qb = (3 * (m - 1) + 3) / 2;
-        std::vector<double> x, w, rule;
-        gauss_legendre(std::max(qb, 1), x, w);
-        for (size_t i = 0; i < x.size(); ++i)
-            for (size_t j = 0; j < x.size(); ++j) rule.insert(rule.end(), {x[i], (1.0 - x[i]) * x[j], 2.0 * w[i] * w[j] * (1.0 - x[i])});
+        std::vector<double> rule;
+        basis_rule_host(m, rule);
         C.nb = (int)(rule.size() / 3);
         if (C.nb > h2::kMaxBasisPts) return fail(H2BEM_ERR_ARG, "operator_create: basis rule too large");
         int rc = upload(op->basis_rule, rule);
@@ -2110,16 +2162,162 @@ extern "C" int h2bem_apply_hypersingular(h2bem_op* op, const double* x, int64_t 
     return H2BEM_OK;
 }
 
-extern "C" int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol,
-                        int maxit, int* iters, double* relres, void* stream) {
-    if (!op || !b || !x) return fail(H2BEM_ERR_ARG, "cg: NULL argument");
-    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "cg: needs the (symmetric positive definite) single layer");
-    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "cg: nrhs must be in 1..64");
-    if (ldb < op->n || ldx < op->n) return fail(H2BEM_ERR_ARG, "cg: leading dimensions must be >= n");
-    if (!(rtol > 0.0) || maxit < 0) return fail(H2BEM_ERR_ARG, "cg: rtol must be > 0 and maxit >= 0");
-    if (!is_device_ptr(b) || !is_device_ptr(x)) return fail(H2BEM_ERR_ARG, "cg: b and x must be device memory");
-    cudaStream_t s = (cudaStream_t)stream;
+// ===========================================================================
+// double layer with piecewise-linear trial functions K1 (h2bem_apply_dlp_p1)
+// ===========================================================================
+// First use: the per-corner leaf bases W1_c[pos][nu] = int_{tau} n . grad
+// L_nu lambda_c (the leaf-basis kernel with the rule's weights scaled by the
+// barycentric coordinate lambda_c = (1 - u - v, u, v) of its points; the
+// integrand's degree stays within the rule's exactness), and the Sauter-Schwab
+// values of the edge- and vertex-adjacent pairs (full tensor rule, q_ss
+// points per direction, FP64).  The double layer's identical pairs vanish.
+static int p1_setup(h2bem_op* op) {
+    if (op->p1_ready) return H2BEM_OK;
+    const int64_t n = op->n;
+    const h2::Geom g = op->geom();
+    const h2::Tree t = op->tree();
+    int rc;
+    std::vector<double> rule;
+    basis_rule_host(op->m, rule);
+    for (int c = 0; c < 3; ++c) {
+        std::vector<double> rc_ = rule;
+        for (size_t p = 0; p < rule.size() / 3; ++p) {
+            const double u = rule[3 * p], v = rule[3 * p + 1];
+            rc_[3 * p + 2] *= c == 0 ? 1.0 - u - v : c == 1 ? u : v;
+        }
+        DevBuf dr;
+        if ((rc = upload(dr, rc_))) return rc;
+        if ((rc = op->p1_W1[c].alloc((size_t)n * op->k * sizeof(double)))) return rc;
+        if (op->nfar > 0)
+            h2::launch_leaf_basis(g, t, op->consts, dr.as<double>(), (int)op->nleaves, op->leaves.as<int>(), true, false,
+                                  op->p1_W1[c].p, 0);
+        CU(cudaDeviceSynchronize());
+    }
+    for (int ty = 1; ty <= 2; ++ty) {
+        std::vector<double> tab;
+        ss_full_table(ty, op->q_ss, tab);
+        if ((rc = upload(op->p1_tab, tab))) return rc;
+        const int np = (int)op->sp_count[ty];
+        if ((rc = op->p1_vals[ty - 1].alloc((size_t)std::max(np, 1) * 6 * sizeof(double)))) return rc;
+        h2::launch_p1_sing_eval(g, np, op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(),
+                                op->p1_tab.as<double>(), (int)(tab.size() / 5), op->p1_vals[ty - 1].as<double>(), 0);
+        CU(cudaDeviceSynchronize());
+    }
+    op->p1_ready = 1;
+    return H2BEM_OK;
+}
+
+// One chunk of at most 16 right-hand sides, device buffers.
+// forward:  x on vertices (ldx), y on triangles (ldy);  transpose: the reverse.
+static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t ldx, int nrhs, double* y,
+                          int64_t ldy, cudaStream_t s, bool transpose) {
+    const int NR = pad_nr(nrhs);
+    int rc;
+    if ((rc = ensure_workspace(op, NR))) return rc;
+    const int64_t need = 3 * op->n * NR;
+    if (op->p1_cap < need) {
+        if ((rc = op->p1_x3.alloc(need * sizeof(double))) || (rc = op->p1_y3.alloc(need * sizeof(double)))) return rc;
+        op->p1_cap = need;
+    }
+    const bool fp32 = op->precision != H2BEM_FP64;
+    const bool xh64 = xh_is64(op, transpose), yh64 = yh_is64(op, transpose);
+    const size_t xsz = xh64 ? sizeof(double) : sizeof(float), ysz = yh64 ? sizeof(double) : sizeof(float);
+    const h2::Geom g = op->geom();
+    const h2::Tree t = op->tree();
+    const h2::Consts& c = op->consts;
     const int n = (int)op->n;
+    double* x3 = op->p1_x3.as<double>();
+    double* y3 = op->p1_y3.as<double>();
+    double* xp = op->xp.as<double>();
+    double* yp = op->yp.as<double>();
+    h2::LaunchCfg cfg_near, cfg_coup;
+    launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
+    if (!transpose) {
+        h2::launch_p1_gather(n, NR, nrhs, op->vid.as<int>(), x, ldx, x3, s);
+        CU(cudaMemsetAsync(yp, 0, (size_t)n * NR * sizeof(double), s));
+        if (op->nfar > 0) {
+            CU(cudaMemsetAsync(op->xh.p, 0, (size_t)op->nc * op->k * NR * xsz, s));
+            CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
+            for (int cc = 0; cc < 3; ++cc)
+                h2::launch_leaf_forward_stored_acc(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                                   xh64, NR, op->p1_W1[cc].as<double>(), x3 + (size_t)cc * n * NR,
+                                                   op->xh.p, s);
+            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p,
+                                  s);
+            run_coupling(op, t, c, op->far, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
+            for (size_t L = 0; L < op->level_parents.size(); ++L)
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR,
+                                    op->yh.p, s);
+            h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
+                                            yh64, NR, op->basisV.p, op->yh.p, yp, s);
+        }
+        h2::launch_p1_near(false, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+                           op->near.dcol.as<int>(), x3, yp, s);
+        for (int ty = 1; ty <= 2; ++ty)
+            h2::launch_p1_sing_apply(false, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),
+                                     op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(),
+                                     op->p1_vals[ty - 1].as<double>(), x3, yp, s);
+        h2::launch_p1_mass(false, n, NR, alpha, op->area.as<double>(), x3, yp, s);
+        h2::launch_permute_out(yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
+    } else {
+        h2::launch_permute_in(x, ldx, nrhs, NR, op->perm.as<int>(), n, xp, s);
+        CU(cudaMemsetAsync(y3, 0, (size_t)need * sizeof(double), s));
+        if (op->nfar > 0) {
+            CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
+            h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
+                                           xh64, NR, op->basisV.p, xp, op->xh.p, s);
+            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p,
+                                  s);
+            run_coupling(op, t, c, op->far_t, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
+            for (size_t L = 0; L < op->level_parents.size(); ++L)
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR,
+                                    op->yh.p, s);
+            for (int cc = 0; cc < 3; ++cc)
+                h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                                false, yh64, NR, op->p1_W1[cc].p, op->yh.p, y3 + (size_t)cc * n * NR,
+                                                s);
+        }
+        h2::launch_p1_near(true, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+                           op->near.dcol.as<int>(), xp, y3, s);
+        for (int ty = 1; ty <= 2; ++ty)
+            h2::launch_p1_sing_apply(true, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),
+                                     op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(),
+                                     op->p1_vals[ty - 1].as<double>(), xp, y3, s);
+        h2::launch_p1_mass(true, n, NR, alpha, op->area.as<double>(), xp, y3, s);
+        h2::launch_p1_scatter((int)op->nv, n, NR, nrhs, op->vptr.as<int>(), op->vinc.as<int>(), op->iperm.as<int>(),
+                              y3, y, ldy, s);
+    }
+    CU(cudaGetLastError());
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_apply_dlp_p1(h2bem_op* op, double alpha, const double* x, int64_t ldx, int nrhs, double* y,
+                                  int64_t ldy, int transpose, void* stream) {
+    if (!op || !x || !y) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: NULL argument");
+    if (op->kernel != H2BEM_DLP) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: needs a double-layer operator");
+    if (op->recompute_basis) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: needs stored leaf bases (recompute_basis = 0)");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: nrhs must be in 1..64");
+    const int64_t nin = transpose ? op->n : op->nv, nout = transpose ? op->nv : op->n;
+    if (ldx < nin || ldy < nout) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: leading dimensions too small");
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(H2BEM_ERR_ARG, "apply_dlp_p1: x and y must be device memory");
+    int rc;
+    if ((rc = p1_setup(op))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+        const int nr = std::min(16, nrhs - c0);
+        if ((rc = apply_p1_chunk(op, alpha, x + c0 * ldx, ldx, nr, y + c0 * ldy, ldy, s, transpose != 0))) return rc;
+    }
+    return H2BEM_OK;
+}
+
+// Conjugate gradients on n-vectors with the operator q = A p (apply(p, q),
+// n x nrhs blocks with leading dimension n), every column its own system;
+// x0 = 0; the step lengths are host scalars.
+template <typename F>
+static int cg_run(h2bem_op* op, int n, F apply, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx,
+                  double rtol, int maxit, int* iters, double* relres, cudaStream_t s) {
     const int64_t need = (int64_t)n * nrhs;
     int rc;
     if (op->cg_cap < need) {
@@ -2145,7 +2343,7 @@ extern "C" int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, do
     auto converged = [&](int c) { return bb[c] == 0.0 || rr[c] <= rtol * rtol * bb[c]; };
     for (int c = 0; c < nrhs; ++c) done[c] = converged(c);
     while (it < maxit && std::find(done.begin(), done.end(), 0) != done.end()) {
-        if ((rc = apply_impl(op, p, n, nrhs, q, n, stream, false, false))) return rc;
+        if ((rc = apply(p, q))) return rc;
         h2::launch_dots(n, nrhs, p, n, q, n, sc, s);
         CU(cudaMemcpyAsync(pq.data(), sc, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
@@ -2171,6 +2369,46 @@ extern "C" int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, do
     if (relres)
         for (int c = 0; c < nrhs; ++c) relres[c] = bb[c] > 0.0 ? std::sqrt(rr[c] / bb[c]) : 0.0;
     return H2BEM_OK;
+}
+
+extern "C" int h2bem_cg(h2bem_op* op, const double* b, int64_t ldb, int nrhs, double* x, int64_t ldx, double rtol,
+                        int maxit, int* iters, double* relres, void* stream) {
+    if (!op || !b || !x) return fail(H2BEM_ERR_ARG, "cg: NULL argument");
+    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "cg: needs the (symmetric positive definite) single layer");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "cg: nrhs must be in 1..64");
+    if (ldb < op->n || ldx < op->n) return fail(H2BEM_ERR_ARG, "cg: leading dimensions must be >= n");
+    if (!(rtol > 0.0) || maxit < 0) return fail(H2BEM_ERR_ARG, "cg: rtol must be > 0 and maxit >= 0");
+    if (!is_device_ptr(b) || !is_device_ptr(x)) return fail(H2BEM_ERR_ARG, "cg: b and x must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)op->n;
+    return cg_run(op, n, [&](const double* p, double* q) { return apply_impl(op, p, n, nrhs, q, n, stream, false, false); },
+                  b, ldb, nrhs, x, ldx, rtol, maxit, iters, relres, s);
+}
+
+extern "C" int h2bem_cg_hypersingular(h2bem_op* op, const double* mvec, const double* b, int64_t ldb, int nrhs,
+                                      double* x, int64_t ldx, double rtol, int maxit, int* iters, double* relres,
+                                      void* stream) {
+    if (!op || !b || !x) return fail(H2BEM_ERR_ARG, "cg_hypersingular: NULL argument");
+    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "cg_hypersingular: needs a single-layer operator");
+    if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "cg_hypersingular: nrhs must be in 1..64");
+    if (ldb < op->nv || ldx < op->nv) return fail(H2BEM_ERR_ARG, "cg_hypersingular: leading dimensions must be >= nv");
+    if (!(rtol > 0.0) || maxit < 0) return fail(H2BEM_ERR_ARG, "cg_hypersingular: rtol must be > 0 and maxit >= 0");
+    if (!is_device_ptr(b) || !is_device_ptr(x) || (mvec && !is_device_ptr(mvec)))
+        return fail(H2BEM_ERR_ARG, "cg_hypersingular: b, x and m must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nv = (int)op->nv;
+    int rc;
+    if (!op->cg_d.p && (rc = op->cg_d.alloc(64 * sizeof(double)))) return rc;
+    double* d = op->cg_d.as<double>();
+    return cg_run(op, nv, [&](const double* p, double* q) {
+        int r2 = h2bem_apply_hypersingular(op, p, nv, nrhs, q, nv, stream);
+        if (r2 || !mvec) return r2;
+        CU(cudaMemsetAsync(d, 0, nrhs * sizeof(double), s));
+        h2::launch_dots(nv, nrhs, mvec, 0, p, nv, d, s);
+        h2::launch_rank1_add(nv, nrhs, mvec, d, q, nv, s);
+        CU(cudaGetLastError());
+        return (int)H2BEM_OK;
+    }, b, ldb, nrhs, x, ldx, rtol, maxit, iters, relres, s);
 }
 
 // ===========================================================================

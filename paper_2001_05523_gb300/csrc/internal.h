@@ -127,6 +127,8 @@ void launch_p1_sing_eval(const Geom& g, int np, const int* lo, const int* hi, co
                          int npts, double* vals, cudaStream_t s);
 void launch_p1_sing_apply(bool transpose, int n, int np, int NR, const int* lo, const int* hi, const int* code,
                           const double* vals, const double* xin, double* yout, cudaStream_t s);
+void launch_p1_mass(bool transpose, int n, int NR, double alpha, const double* area, const double* xin, double* yout,
+                    cudaStream_t s);
 void launch_leaf_forward_stored_acc(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool xh64,
                                     int NR, const double* B, const double* xp, void* xh, cudaStream_t s);
 
@@ -263,6 +265,7 @@ void launch_cg_step(int n, int nrhs, const double* alpha, const double* p, int64
                     double* x, int64_t ldx, double* res, int64_t ldr, cudaStream_t s);
 void launch_cg_dir(int n, int nrhs, const double* beta, const double* res, int64_t ldr, double* p, int64_t ldp,
                    cudaStream_t s);
+void launch_rank1_add(int n, int nrhs, const double* m, const double* d, double* q, int64_t ldq, cudaStream_t s);
 void launch_mass_add(int n, int nrhs, double alpha, const double* area_user, const double* x, int64_t ldx, double* y,
                      int64_t ldy, cudaStream_t s);
 void launch_area_user(int n, const int* perm, const double* area, double* out, cudaStream_t s);

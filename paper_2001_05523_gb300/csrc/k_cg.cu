@@ -52,6 +52,21 @@ __global__ void k_cg_dir(int n, int nrhs, const double* __restrict__ beta, const
     p[i + r * ldp] = fma(beta[r], p[i + r * ldp], res[i + r * ldr]);
 }
 
+// q += m d_r (a rank-one term m m^T p with d_r = m . p_r computed before)
+__global__ void k_rank1_add(int n, int nrhs, const double* __restrict__ m, const double* __restrict__ d,
+                            double* __restrict__ q, int64_t ldq) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * nrhs) return;
+    const int r = (int)(e / n), i = (int)(e % n);
+    q[i + r * ldq] = fma(m[i], d[r], q[i + r * ldq]);
+}
+
+void launch_rank1_add(int n, int nrhs, const double* m, const double* d, double* q, int64_t ldq, cudaStream_t s) {
+    const int64_t tot = (int64_t)n * nrhs;
+    if (tot <= 0) return;
+    k_rank1_add<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, nrhs, m, d, q, ldq);
+}
+
 // y += alpha |tau_i| x (P0 mass matrix); area in the caller's triangle order
 __global__ void k_mass_add(int n, int nrhs, double alpha, const double* __restrict__ area_user,
                            const double* __restrict__ x, int64_t ldx, double* __restrict__ y, int64_t ldy) {

@@ -248,7 +248,7 @@ __device__ __forceinline__ void stage_tile(T* dst, const T* src, size_t bytes) {
     }
 }
 
-template <typename TB, typename TA, int NR>
+template <typename TB, typename TA, int NR, bool ACC = false>
 __global__ void __launch_bounds__(128) k_leaf_fwd_st(Tree t, int k, const int* __restrict__ leaves,
                                                      const TB* __restrict__ B, const double* __restrict__ xp,
                                                      TA* __restrict__ xh) {
@@ -274,7 +274,8 @@ __global__ void __launch_bounds__(128) k_leaf_fwd_st(Tree t, int k, const int* _
         const int nu = e / NR, r = e % NR;
         TA acc = 0;
         for (int j = 0; j < R; ++j) acc += (TA)sB[j * k + nu] * sx[j * NR + r];
-        xh[((int64_t)s * k + nu) * NR + r] = acc;
+        if (ACC) xh[((int64_t)s * k + nu) * NR + r] += acc;
+        else xh[((int64_t)s * k + nu) * NR + r] = acc;
     }
 }
 
@@ -661,6 +662,34 @@ void launch_leaf_forward_stored(const Tree& t, int k, int max_leaf, int nleaves,
     if (nleaves <= 0) return;
     H2_NR_SWITCH(NR, (leaf_st_prec<R_>(true, basis32, xh64, t, k, max_leaf, nleaves, leaves, B, xp, xh, nullptr,
                                        nullptr, s)))
+}
+
+// x-hat_s += W^T x|_s with an FP64 basis (the per-corner bases of the
+// piecewise-linear double layer are summed this way, one corner at a time)
+void launch_leaf_forward_stored_acc(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool xh64,
+                                    int NR, const double* B, const double* xp, void* xh, cudaStream_t s) {
+    if (nleaves <= 0) return;
+    auto pick = [&](auto nr) {
+        constexpr int R_ = decltype(nr)::value;
+        const size_t sb = ((size_t)max_leaf * k * sizeof(double) + 15) & ~size_t(15);
+        if (xh64) {
+            const size_t smem = sb + (size_t)max_leaf * R_ * sizeof(double);
+            cudaFuncSetAttribute(k_leaf_fwd_st<double, double, R_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            k_leaf_fwd_st<double, double, R_, true><<<nleaves, 128, smem, s>>>(t, k, leaves, B, xp, (double*)xh);
+        } else {
+            const size_t smem = sb + (size_t)max_leaf * R_ * sizeof(float);
+            cudaFuncSetAttribute(k_leaf_fwd_st<double, float, R_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            k_leaf_fwd_st<double, float, R_, true><<<nleaves, 128, smem, s>>>(t, k, leaves, B, xp, (float*)xh);
+        }
+    };
+    switch (NR) {
+        case 1: pick(std::integral_constant<int, 1>{}); break;
+        case 4: pick(std::integral_constant<int, 4>{}); break;
+        case 8: pick(std::integral_constant<int, 8>{}); break;
+        default: pick(std::integral_constant<int, 16>{}); break;
+    }
 }
 
 void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,

@@ -29,7 +29,7 @@ EXPORTED = [
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
     "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad", "h2bem_apply_mass", "h2bem_apply_hypersingular",
-    "h2bem_cg", "h2bem_gca_bases",
+    "h2bem_cg", "h2bem_gca_bases", "h2bem_apply_dlp_p1", "h2bem_cg_hypersingular",
 ]
 
 
@@ -88,6 +88,8 @@ def lib():
             "h2bem_tree_destroy": [vp],
             "h2bem_blocks": [vp, d, vp, vp, vp, vp, vp, vp],
             "h2bem_gca_bases": [vp, vp, vp, vp, vp, vp],
+            "h2bem_apply_dlp_p1": [vp, d, vp, i64, i32, vp, i64, i32, vp],
+            "h2bem_cg_hypersingular": [vp, vp, vp, i64, i32, vp, i64, d, i32, vp, vp, vp],
             "h2bem_opts_default": [vp],
             "h2bem_operator_create": [vp, vp, i32, i32, d, vp, pp],
             "h2bem_operator_destroy": [vp],
@@ -297,6 +299,25 @@ def h2bem_apply_hypersingular(op, x, y, stream=None):
     _check(lib().h2bem_apply_hypersingular(op, px, lx, nr, py, ly, _stream(stream)))
 
 
+def h2bem_apply_dlp_p1(op, x, y, transpose: bool = False, alpha: float = 0.0, stream=None):
+    """y = K1 x + alpha M1 x (x: (nrhs, nv), y: (nrhs, n)) or K1^T x + alpha M1^T x (x: (nrhs, n),
+    y: (nrhs, nv)); device tensors."""
+    px, lx, nr, py, ly = _vec_args(x, y)
+    _check(lib().h2bem_apply_dlp_p1(op, ctypes.c_double(alpha), px, lx, nr, py, ly, int(transpose), _stream(stream)))
+
+
+def h2bem_cg_hypersingular(op, m, b, x, rtol=1e-8, maxit=1000, stream=None):
+    """CG for (W + m m^T) x = b on the vertices (device tensors (nrhs, nv); m: (nv,) or None);
+    returns (iterations, relres per column)."""
+    pb, lb, nr, px, lx = _vec_args(b, x)
+    pm = ctypes.c_void_p(m.data_ptr()) if m is not None else None
+    it = ctypes.c_int(0)
+    rel = (ctypes.c_double * nr)()
+    _check(lib().h2bem_cg_hypersingular(op, pm, pb, lb, nr, px, lx, ctypes.c_double(rtol), int(maxit),
+                                        ctypes.byref(it), rel, _stream(stream)))
+    return it.value, list(rel)
+
+
 def h2bem_cg(op, b, x, rtol=1e-8, maxit=1000, stream=None):
     """Conjugate gradients for G x = b (device buffers, (nrhs, n)); returns (iterations, relres per column)."""
     pb, lb, nr, px, lx = _vec_args(b, x)
@@ -371,6 +392,7 @@ class Operator:
                  gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
+        self.nv = int(np.asarray(vertices).shape[0])
         self.mesh = h2bem_mesh_create(vertices, triangles)
         self.tree = h2bem_tree_build(self.mesh, leaf_size)
         o = h2bem_opts_default()
