@@ -622,6 +622,92 @@ def main():
             "rayleigh_Y2": float(u @ wu[0] / uMu), "rayleigh_Y2_exact": 1.2,
             "W1_rel": float(np.abs(wu[1]).max() / np.abs(wu[0]).max())}
 
+    # double layer with piecewise-linear trial functions K1 (section 1, eq. (dlp) with
+    # the hat functions) on the same sphere: forward (vertices -> triangles) and
+    # transposed applies; its nearfield and Sauter-Schwab pairs are FP64 in every tier
+    if not args.no_fp64:
+        op1 = H.Operator(mesh.vertices, mesh.triangles, kernel="dlp", m=4, eta=2.0, leaf_size=32,
+                         precision=args.tier, autotune=args.autotune)
+        nv = mesh.vertices.shape[0]
+        xv1 = torch.from_numpy(I.rhs(nv, nrhs, seed=12)).to(dev)
+        yt1 = torch.empty((nrhs, n), dtype=torch.float64, device=dev)
+        yv1 = torch.empty_like(xv1)
+        k1 = {"vertices": nv, "rhs": nrhs, "tier": args.tier}
+        for tr, xin, yout in ((False, xv1, yt1), (True, yt1, yv1)):
+            H.h2bem_apply_dlp_p1(op1.op, xin, yout, transpose=tr, stream=stream)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.h2bem_apply_dlp_p1(op1.op, xin, yout, transpose=tr, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            k1["transpose_ms" if tr else "forward_ms"] = e0.elapsed_time(e1)
+        op1.close()
+        extra["dlp_p1_k1"] = k1
+
+    # Neumann-to-Dirichlet solve (section 1, eq. (neumann_to_dirichlet)):
+    # (W + m m^T) x = (M1^T / 2 - K1^T) b + m (m . u) with piecewise-constant
+    # Neumann data b (the L2 projection of du/dn) and piecewise-linear Dirichlet
+    # values x (m the P1 mass row sums, fixing the constant), by the library's
+    # conjugate gradients, mixed tier, for the same test functions; the L2 error
+    # of x against u at the vertices, two spheres one refinement apart
+    if not args.no_fp64:
+        def ntd_case(s_ntd, m_ntd, eta_ntd, rtol):
+            import scipy.sparse as sps
+
+            md = I.sphere(s_ntd)
+            v, tri = md.vertices, md.triangles
+            ta, tb, tc = (v[tri[:, q]] for q in range(3))
+            ar = 0.5 * np.linalg.norm(np.cross(tb - ta, tc - ta), axis=1)
+            pts = ta[:, None] + ru[None, :, None] * (tb - ta)[:, None] + rv[None, :, None] * (tc - ta)[:, None]
+            proj = pts / np.linalg.norm(pts, axis=-1, keepdims=True)
+            bn = np.stack([(u_dn(k, proj)[1] * rw[None, :]).sum(1) for k in range(3)])
+            uI = np.stack([u_dn(k, v)[0] for k in range(3)])
+            loc = np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]]) / 12.0
+            Mp = sps.csr_matrix((np.concatenate([ar * loc[a, c] for a in range(3) for c in range(3)]),
+                                 (np.concatenate([tri[:, a] for a in range(3) for _ in range(3)]),
+                                  np.concatenate([tri[:, c] for _ in range(3) for c in range(3)]))),
+                                shape=(md.nv, md.nv))
+            mv = np.asarray(Mp.sum(1)).ravel()
+            t_set = time.perf_counter()
+            opG = H.Operator(v, tri, kernel="slp", m=m_ntd, eta=eta_ntd, precision="mixed_fp32", autotune=1,
+                             store_near=True)
+            opK = H.Operator(v, tri, kernel="dlp", m=m_ntd, eta=eta_ntd, precision="mixed_fp32", autotune=1)
+            torch.cuda.synchronize(dev)
+            t_set = time.perf_counter() - t_set
+            bd = torch.from_numpy(np.ascontiguousarray(-bn)).to(dev)
+            mvd = torch.from_numpy(mv).to(dev)
+            ud = torch.from_numpy(uI).to(dev)
+            rhs_d = torch.empty((3, md.nv), dtype=torch.float64, device=dev)
+            xd_ = torch.empty_like(rhs_d)
+            H.h2bem_apply_dlp_p1(opK.op, bd, rhs_d, transpose=True, alpha=-0.5, stream=stream)
+            H.h2bem_cg_hypersingular(opG.op, mvd, rhs_d, xd_, rtol=1e-3, maxit=5, stream=stream)  # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            H.h2bem_apply_dlp_p1(opK.op, bd, rhs_d, transpose=True, alpha=-0.5, stream=stream)
+            rhs_d += (ud @ mvd)[:, None] * mvd[None, :]
+            its, rel = H.h2bem_cg_hypersingular(opG.op, mvd, rhs_d, xd_, rtol=rtol, maxit=3000, stream=stream)
+            torch.cuda.synchronize(dev)
+            t_solve = time.perf_counter() - t0
+            xs = xd_.cpu().numpy()
+            l2 = {}
+            for k, nm in enumerate(("u1", "u2", "u3")):
+                e = xs[k] - uI[k]
+                l2[nm] = float(np.sqrt(e @ (Mp @ e) / (uI[k] @ (Mp @ uI[k]))))
+            opG.close()
+            opK.close()
+            return {"triangles": md.nt, "vertices": md.nv, "m": m_ntd, "eta": eta_ntd, "rhs": 3,
+                    "iterations": its, "rtol": rtol, "relres": rel, "setup_s": t_set, "solve_s": t_solve,
+                    "ms_per_iteration": 1e3 * t_solve / max(its, 1), "dirichlet_l2_rel_err": l2}
+
+        coarse = ntd_case(64, 6, 1.0, 1e-9)
+        fine = ntd_case(128, 6, 1.0, 1e-9)
+        extra["ntd_cg_mixed"] = {
+            "coarse": coarse, "fine": fine,
+            "observed_order": {nm: float(np.log2(coarse["dirichlet_l2_rel_err"][nm] / fine["dirichlet_l2_rel_err"][nm]))
+                               for nm in ("u1", "u2", "u3")},
+            "expected_order": 2.0}
+
     # roofline of the dominant kernel of the headline tier
     pk = peaks()
     names = ["permute_in", "leaf_forward", "upward", "coupling", "downward", "leaf_backward", "near_regular",

@@ -120,6 +120,27 @@ def lib():
             L.or_gca_rowcount.argtypes = [vp, i64]
             L.or_gca_rowcount.restype = i64
             L.or_gca_matvec.argtypes = [vp, vp, i32, vp, i32]
+            L.or_hca_create.argtypes = [vp, i64, vp, i64, i32, d, i32, d, i32, d, i32, i32]
+            L.or_hca_create.restype = vp
+            L.or_hca_destroy.argtypes = [vp]
+            L.or_hca_sizes.argtypes = [vp, vp]
+            L.or_hca_ranks.argtypes = [vp, vp, vp]
+            L.or_hca_blocks.argtypes = [vp, vp, vp]
+            L.or_hca_cluster.argtypes = [vp, i64, vp]
+            L.or_hca_cluster.restype = i64
+            L.or_hca_block.argtypes = [vp, i64, vp, vp, vp]
+            L.or_hca_block.restype = i32
+            L.or_hca_node.argtypes = [vp, i64, i32, vp]
+            L.or_hca_kernel.argtypes = [vp, i64, vp, vp]
+            L.or_hca_kernel.restype = d
+            L.or_hca_block_matrix.argtypes = [vp, i64, vp]
+            L.or_hca_basis.argtypes = [vp, i64, vp]
+            L.or_hca_basis.restype = i32
+            L.or_hca_transfer.argtypes = [vp, i64, vp]
+            L.or_hca_transfer.restype = i32
+            L.or_hca_coupling.argtypes = [vp, i64, vp]
+            L.or_hca_coupling.restype = i32
+            L.or_hca_matvec.argtypes = [vp, vp, i32, vp, i32, i32]
             _lib = L
     return _lib
 
@@ -506,6 +527,108 @@ class GCA:
             x = x[None, :]
         y = np.zeros_like(x)
         lib().or_gca_matvec(self.h, _p(x), x.shape[0], _p(y), int(parts))
+        return y
+
+
+class HCA:
+    """The oracle's hybrid cross approximation of the single layer G (section 3)
+    and its compression into an H^2-matrix: interpolation order m for the
+    coupling matrix S of each block, cross approximation of S to eps_aca (at
+    most kaca steps), compression with relative truncation eps_c, cluster
+    ranks capped at kmax."""
+
+    def __init__(self, mesh, m: int = 4, eta: float = 2.0, leaf: int = 32, eps_aca: float = 1e-6, kaca: int = 64,
+                 eps_c: float = 1e-6, kmax: int = 64, q_ss: int = 5):
+        self.mesh = mesh
+        v = _f64(mesh.vertices)
+        t = np.ascontiguousarray(mesh.triangles, dtype=np.int32)
+        self._keep = (v, t)
+        h = lib().or_hca_create(_p(v), v.shape[0], _p(t), t.shape[0], m, float(eta), leaf, float(eps_aca), kaca,
+                                float(eps_c), kmax, q_ss)
+        if not h:
+            raise ValueError("or_hca_create failed")
+        self.h = ctypes.c_void_p(h)
+        sz = np.zeros(6, dtype=np.int64)
+        lib().or_hca_sizes(self.h, _p(sz))
+        self.nclusters, self.nfar, self.nnear, self.maxrank, self.k, self.maxblockrank = (int(a) for a in sz)
+        self.n = mesh.nt
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            lib().or_hca_destroy(h)
+            self.h = None
+
+    def ranks(self) -> np.ndarray:
+        r = np.zeros(self.nclusters, np.int32)
+        lib().or_hca_ranks(self.h, _p(r), None)
+        return r
+
+    def block_ranks(self) -> np.ndarray:
+        r = np.zeros(self.nfar, np.int32)
+        lib().or_hca_ranks(self.h, None, _p(r))
+        return r
+
+    def blocks(self):
+        ft = np.zeros(self.nfar, np.int64)
+        fs = np.zeros(self.nfar, np.int64)
+        lib().or_hca_blocks(self.h, _p(ft), _p(fs))
+        return ft, fs
+
+    def cluster(self, c: int) -> np.ndarray:
+        idx = np.zeros(self.n, np.int64)
+        cnt = int(lib().or_hca_cluster(self.h, c, _p(idx)))
+        return idx[:cnt].copy()
+
+    def block(self, b: int):
+        """(tau, sigma, C) of farfield block b."""
+        tau = np.zeros(self.k, np.int32)
+        sig = np.zeros(self.k, np.int32)
+        C = np.zeros(self.k * self.k)
+        r = int(lib().or_hca_block(self.h, b, _p(tau), _p(sig), _p(C)))
+        return tau[:r].copy(), sig[:r].copy(), C[:r * r].reshape(r, r).copy()
+
+    def node(self, c: int, nu: int) -> np.ndarray:
+        x = np.zeros(3)
+        lib().or_hca_node(self.h, c, nu, _p(x))
+        return x
+
+    def kernel(self, b: int, x, y) -> float:
+        return float(lib().or_hca_kernel(self.h, b, _p(_f64(x)), _p(_f64(y))))
+
+    def block_matrix(self, b: int) -> np.ndarray:
+        ft, fs = self.blocks()
+        nt_, ns = len(self.cluster(int(ft[b]))), len(self.cluster(int(fs[b])))
+        out = np.zeros((nt_, ns))
+        lib().or_hca_block_matrix(self.h, b, _p(out))
+        return out
+
+    def basis(self, c: int) -> np.ndarray:
+        Q = np.zeros((len(self.cluster(c)), int(self.ranks()[c])))
+        lib().or_hca_basis(self.h, c, _p(Q))
+        return Q
+
+    def transfer(self, c: int, parent: int) -> np.ndarray:
+        r = self.ranks()
+        E = np.zeros((int(r[c]), int(r[parent])))
+        if lib().or_hca_transfer(self.h, c, _p(E)):
+            raise ValueError("bad cluster")
+        return E
+
+    def coupling(self, b: int) -> np.ndarray:
+        ft, fs = self.blocks()
+        r = self.ranks()
+        S = np.zeros((int(r[ft[b]]), int(r[fs[b]])))
+        lib().or_hca_coupling(self.h, b, _p(S))
+        return S
+
+    def matvec(self, x: np.ndarray, parts: int = PART_ALL, hmatrix: bool = False) -> np.ndarray:
+        """x: (nrhs, n) -> (nrhs, n); hmatrix: the uncompressed HCA blocks."""
+        x = _f64(x)
+        if x.ndim == 1:
+            x = x[None, :]
+        y = np.zeros_like(x)
+        lib().or_hca_matvec(self.h, _p(x), x.shape[0], _p(y), int(parts), int(hmatrix))
         return y
 
 

@@ -2303,3 +2303,707 @@ void or_h2_matvec_subtree_from(const or_h2* H, int64_t c0, const double* xh_in, 
 void or_h2_matvec_subtree(const or_h2* H, int64_t c0, const double* x, int nrhs, double* y) {
     or_h2_matvec_subtree_from(H, c0, NULL, x, nrhs, y);
 }
+
+/* ========================================================================= */
+/* Hybrid cross approximation, HCA (section 3), single layer G, and its     */
+/* hierarchical compression into an H^2-matrix (end of section 3)           */
+/* ========================================================================= */
+/* Per farfield block b = (t, s):                                            */
+/*  1. S[nu,mu] = g(xi_{t,nu}, xi_{s,mu}) with the tensor Chebyshev nodes of */
+/*     the H^2 specification (k = m^3 per cluster).                          */
+/*  2. Cross approximation of S with full pivoting (the pivoted LU of       */
+/*     section 3; the pivot and stop rules of or_gca_aca) with tolerance     */
+/*     eps_aca and at most kaca steps: row pivots tau, column pivots sigma,  */
+/*     rank r_b.                                                             */
+/*  3. C_b = (S|_{tau x sigma})^{-1}, so that S ~ S|_{: x sigma} C_b         */
+/*     S|_{tau x :}; C_b is indexed [sigma position][tau position].          */
+/*  4. Take-back (eq. hca_discrete): A_b[i,kappa] = int_{tau_i}              */
+/*     g(x, xi_{s,sigma_kappa}) dx (i in t), B_b[j,lambda] = int_{tau_j}     */
+/*     g(xi_{t,tau_lambda}, y) dy (j in s), both by the 7-point rule (the    */
+/*     nodes lie in the partner's box, away from the triangle);              */
+/*     G|_{t x s} ~ A_b C_b B_b^T.                                           */
+/* Hierarchical compression (the paper cites it and leaves it open; this is  */
+/* the reading): orthonormal nested cluster bases from the HCA blocks,       */
+/* bottom-up over the cluster tree.                                          */
+/*  5. F_t = the farfield blocks (t*, s) with t* = t or an ancestor of t.   */
+/*     With B_b = Q R (thin QR) every block contributes the columns          */
+/*     A_b|_t W_b, W_b = C_b R^T: A_b|_t C_b B_b^T = (A_b|_t W_b) Q^T and Q^T */
+/*     has orthonormal rows, so Z_t = [A_b|_t W_b]_{b in F_t} has the left   */
+/*     singular vectors and values of the block row of t in the HCA matrix.  */
+/*  6. Leaf t: Q_t = the left singular vectors of Z_t whose singular values  */
+/*     exceed eps_c sigma_1(Z_t), at most kmax of them.  Parent t (children  */
+/*     t1, t2): P_t = the same for [Q_t1^T Z_t|_t1 ; Q_t2^T Z_t|_t2];        */
+/*     (E_t1 ; E_t2) = P_t split by rows, Q_t = [Q_t1 E_t1 ; Q_t2 E_t2].     */
+/*     Singular vectors: Householder QR of Z^T, then one-sided Jacobi        */
+/*     (Hestenes) on the triangular factor.                                  */
+/*  7. Coupling S_ts = (Q_t^T A_b) C_b (Q_s^T B_b)^T.                        */
+/* The H^2 product runs the passes of section 2 with V_t = Q_t (leaves),     */
+/* the transfers E and the couplings S; the nearfield as in the H^2 form.    */
+
+struct or_hca {
+    or_mesh mesh;
+    double* xyz;
+    int32_t* tri;
+    int m, k, kaca, kmax, q_ss;
+    double eta, eps_aca, eps_c;
+    tree_t T;
+    blist far, near;
+    int64_t *far_ptr, *far_col, *near_ptr, *near_col;
+    double* nodes;  /* per cluster 3 m Chebyshev nodes */
+    int* brank;     /* r_b per farfield block (far list order) */
+    int** btau;     /* row pivots (node indices of t) */
+    int** bsig;     /* column pivots (node indices of s) */
+    double** bC;    /* r_b x r_b, [sigma pos][tau pos] */
+    double** bW;    /* r_b x r_b, C_b R^T */
+    int* rank;      /* k_t */
+    double** Q;     /* every cluster: |t| x k_t, rows in tree order */
+    double** E;     /* non-root clusters: k_c x k_parent */
+    double** S;     /* farfield blocks: k_t x k_s */
+};
+
+/* node nu of cluster c */
+static void hca_node(const or_hca* H, int64_t c, int nu, double* x) {
+    const int m = H->m;
+    const double* z = H->nodes + c * 3 * m;
+    x[0] = z[nu % m];
+    x[1] = z[m + (nu / m) % m];
+    x[2] = z[2 * m + nu / (m * m)];
+}
+
+/* int_{tau_i} g(x, p) dx by the 7-point rule */
+static double hca_panel_potential(const or_mesh* M, int64_t i, const double* p) {
+    double X[9], area, nrm[3], uv[14], rw[7];
+    tri_vertices(M, i, X);
+    or_tri_geom(X, X + 3, X + 6, &area, nrm);
+    or_radon7(uv, rw);
+    double s = 0.0;
+    for (int q = 0; q < 7; ++q) {
+        double xq[3];
+        for (int d = 0; d < 3; ++d) xq[d] = X[d] + uv[2 * q] * (X[3 + d] - X[d]) + uv[2 * q + 1] * (X[6 + d] - X[d]);
+        s += rw[q] * kernel_slp(xq, p);
+    }
+    return area * s;
+}
+
+/* A_b (|t| x r, rows in tree order) of step 4 */
+static void hca_A(const or_hca* H, int64_t b, double* A) {
+    const int64_t t = H->far.t[b], s = H->far.s[b];
+    const int r = H->brank[b];
+    for (int64_t a = H->T.begin[t]; a < H->T.end[t]; ++a)
+        for (int kap = 0; kap < r; ++kap) {
+            double p[3];
+            hca_node(H, s, H->bsig[b][kap], p);
+            A[(a - H->T.begin[t]) * r + kap] = hca_panel_potential(&H->mesh, H->T.perm[a], p);
+        }
+}
+/* B_b (|s| x r) of step 4 */
+static void hca_B(const or_hca* H, int64_t b, double* B) {
+    const int64_t t = H->far.t[b], s = H->far.s[b];
+    const int r = H->brank[b];
+    for (int64_t a = H->T.begin[s]; a < H->T.end[s]; ++a)
+        for (int lam = 0; lam < r; ++lam) {
+            double p[3];
+            hca_node(H, t, H->btau[b][lam], p);
+            B[(a - H->T.begin[s]) * r + lam] = hca_panel_potential(&H->mesh, H->T.perm[a], p);
+        }
+}
+
+/* Inverse of the r x r matrix M (row-major) by Gauss-Jordan elimination with
+ * partial pivoting; returns -1 if a pivot is 0. */
+static int hca_inverse(const double* M, int r, double* Inv) {
+    double* W = malloc((size_t)r * 2 * r * sizeof(double) + 1);
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < 2 * r; ++j) W[i * 2 * r + j] = j < r ? M[i * r + j] : (j - r == i ? 1.0 : 0.0);
+    int bad = 0;
+    for (int c = 0; c < r; ++c) {
+        int p = c;
+        for (int i = c + 1; i < r; ++i)
+            if (fabs(W[i * 2 * r + c]) > fabs(W[p * 2 * r + c])) p = i;
+        if (W[p * 2 * r + c] == 0.0) { bad = 1; break; }
+        if (p != c)
+            for (int j = 0; j < 2 * r; ++j) {
+                double tmp = W[c * 2 * r + j];
+                W[c * 2 * r + j] = W[p * 2 * r + j];
+                W[p * 2 * r + j] = tmp;
+            }
+        const double d = W[c * 2 * r + c];
+        for (int j = 0; j < 2 * r; ++j) W[c * 2 * r + j] /= d;
+        for (int i = 0; i < r; ++i) {
+            if (i == c) continue;
+            const double f = W[i * 2 * r + c];
+            if (f != 0.0)
+                for (int j = 0; j < 2 * r; ++j) W[i * 2 * r + j] -= f * W[c * 2 * r + j];
+        }
+    }
+    for (int i = 0; i < r && !bad; ++i)
+        for (int j = 0; j < r; ++j) Inv[i * r + j] = W[i * 2 * r + r + j];
+    free(W);
+    return bad ? -1 : 0;
+}
+
+/* R of the thin Householder QR of the rows x cols matrix X (row-major),
+ * p = min(rows, cols): R is p x cols upper trapezoidal (row-major). */
+static void hca_qr_r(const double* X, int rows, int cols, double* R) {
+    double* A = malloc((size_t)rows * cols * sizeof(double) + 1);
+    double* v = malloc((size_t)rows * sizeof(double) + 1);
+    memcpy(A, X, (size_t)rows * cols * sizeof(double));
+    const int p = rows < cols ? rows : cols;
+    for (int j = 0; j < p; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < rows; ++i) nrm += A[(size_t)i * cols + j] * A[(size_t)i * cols + j];
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) continue;
+        const double alpha = A[(size_t)j * cols + j] > 0 ? -nrm : nrm;
+        for (int i = j; i < rows; ++i) v[i] = A[(size_t)i * cols + j];
+        v[j] -= alpha;
+        double vv = 0.0;
+        for (int i = j; i < rows; ++i) vv += v[i] * v[i];
+        if (vv == 0.0) continue;
+        for (int c = j; c < cols; ++c) {
+            double d = 0.0;
+            for (int i = j; i < rows; ++i) d += v[i] * A[(size_t)i * cols + c];
+            d = 2.0 * d / vv;
+            for (int i = j; i < rows; ++i) A[(size_t)i * cols + c] -= d * v[i];
+        }
+    }
+    for (int i = 0; i < p; ++i)
+        for (int c = 0; c < cols; ++c) R[(size_t)i * cols + c] = c < i ? 0.0 : A[(size_t)i * cols + c];
+    free(A);
+    free(v);
+}
+
+/* Left singular vectors and values of Z (r x cols, row-major): Householder
+ * QR of Z^T = Q R (R p x r), one-sided Jacobi on R: R V = U Sigma, so Z =
+ * V Sigma (Q U)^T.  U_out: r x r (column j = j-th left singular vector),
+ * sv: r values, in decreasing order. */
+static void hca_left_svd(const double* Z, int r, int cols, double* U_out, double* sv) {
+    const int p = r < cols ? r : cols;
+    double* Zt = malloc((size_t)cols * r * sizeof(double) + 1);
+    for (int i = 0; i < r; ++i)
+        for (int c = 0; c < cols; ++c) Zt[(size_t)c * r + i] = Z[(size_t)i * cols + c];
+    double* R = malloc((size_t)p * r * sizeof(double) + 1);
+    hca_qr_r(Zt, cols, r, R);
+    free(Zt);
+    double* V = calloc((size_t)r * r, sizeof(double));
+    for (int i = 0; i < r; ++i) V[i * r + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        int rotated = 0;
+        for (int i = 0; i < r - 1; ++i)
+            for (int j = i + 1; j < r; ++j) {
+                double a = 0.0, bq = 0.0, g = 0.0;
+                for (int q = 0; q < p; ++q) {
+                    a += R[q * r + i] * R[q * r + i];
+                    bq += R[q * r + j] * R[q * r + j];
+                    g += R[q * r + i] * R[q * r + j];
+                }
+                if (g == 0.0 || fabs(g) <= 1e-15 * sqrt(a * bq)) continue;
+                rotated = 1;
+                const double zeta = (bq - a) / (2.0 * g);
+                const double tn = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + tn * tn), sn = cs * tn;
+                for (int q = 0; q < p; ++q) {
+                    const double xi = R[q * r + i], xj = R[q * r + j];
+                    R[q * r + i] = cs * xi - sn * xj;
+                    R[q * r + j] = sn * xi + cs * xj;
+                }
+                for (int q = 0; q < r; ++q) {
+                    const double xi = V[q * r + i], xj = V[q * r + j];
+                    V[q * r + i] = cs * xi - sn * xj;
+                    V[q * r + j] = sn * xi + cs * xj;
+                }
+            }
+        if (!rotated) break;
+    }
+    double* nrm = malloc((size_t)r * sizeof(double) + 1);
+    int* ord = malloc((size_t)r * sizeof(int) + 1);
+    for (int j = 0; j < r; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < p; ++q) s += R[q * r + j] * R[q * r + j];
+        nrm[j] = sqrt(s);
+        ord[j] = j;
+    }
+    for (int a = 1; a < r; ++a)  /* insertion sort, decreasing, stable */
+        for (int b = a; b > 0 && nrm[ord[b]] > nrm[ord[b - 1]]; --b) {
+            int tmp = ord[b];
+            ord[b] = ord[b - 1];
+            ord[b - 1] = tmp;
+        }
+    for (int j = 0; j < r; ++j) {
+        sv[j] = nrm[ord[j]];
+        for (int q = 0; q < r; ++q) U_out[q * r + j] = V[q * r + ord[j]];
+    }
+    free(R); free(V); free(nrm); free(ord);
+}
+
+/* Steps 1-3 for farfield block b. */
+static void hca_block_aca(or_hca* H, int64_t b) {
+    const int k = H->k;
+    const int64_t t = H->far.t[b], s = H->far.s[b];
+    double* S = malloc((size_t)k * k * sizeof(double));
+    for (int nu = 0; nu < k; ++nu) {
+        double xt[3];
+        hca_node(H, t, nu, xt);
+        for (int mu = 0; mu < k; ++mu) {
+            double xs[3];
+            hca_node(H, s, mu, xs);
+            S[nu * k + mu] = kernel_slp(xt, xs);
+        }
+    }
+    int* tau = malloc((k + 1) * sizeof(int));
+    int* sig = malloc((k + 1) * sizeof(int));
+    int r = or_gca_aca(S, k, k, H->eps_aca, H->kaca, tau, sig);
+    double* M = malloc(((size_t)r * r + 1) * sizeof(double));
+    double* C = malloc(((size_t)r * r + 1) * sizeof(double));
+    for (int a = 0; a < r; ++a)
+        for (int c = 0; c < r; ++c) M[a * r + c] = S[tau[a] * k + sig[c]]; /* [tau pos][sigma pos] */
+    if (hca_inverse(M, r, C)) r = 0;                                       /* C: [sigma pos][tau pos] */
+    H->brank[b] = r;
+    H->btau[b] = tau;
+    H->bsig[b] = sig;
+    H->bC[b] = C;
+    free(M);
+    free(S);
+}
+
+/* W_b = C_b R^T with B_b = Q R (step 5). */
+static void hca_block_weight(or_hca* H, int64_t b) {
+    const int r = H->brank[b];
+    const int64_t s = H->far.s[b];
+    const int64_t ns = H->T.end[s] - H->T.begin[s];
+    double* W = calloc((size_t)r * r + 1, sizeof(double));
+    if (r > 0) {
+        double* B = malloc((size_t)ns * r * sizeof(double));
+        hca_B(H, b, B);
+        const int p = ns < r ? (int)ns : r;
+        double* R = malloc((size_t)p * r * sizeof(double));
+        hca_qr_r(B, (int)ns, r, R);
+        for (int a = 0; a < r; ++a)
+            for (int c = 0; c < p; ++c) { /* (C R^T)[a][c]; columns c >= p stay 0 */
+                double acc = 0.0;
+                for (int l = 0; l < r; ++l) acc += H->bC[b][a * r + l] * R[c * r + l];
+                W[a * r + c] = acc;
+            }
+        free(B);
+        free(R);
+    }
+    H->bW[b] = W;
+}
+
+/* Q_c^T A_b|_c (k_c x r) for a cluster c inside the row cluster of b. */
+static void hca_project_A(const or_hca* H, int64_t b, int64_t c, double* out) {
+    const int r = H->brank[b], kc = H->rank[c];
+    const int64_t s = H->far.s[b];
+    const int64_t nc_ = H->T.end[c] - H->T.begin[c];
+    for (int e = 0; e < kc * r; ++e) out[e] = 0.0;
+    for (int64_t a = 0; a < nc_; ++a)
+        for (int kap = 0; kap < r; ++kap) {
+            double p[3];
+            hca_node(H, s, H->bsig[b][kap], p);
+            const double v = hca_panel_potential(&H->mesh, H->T.perm[H->T.begin[c] + a], p);
+            for (int nu = 0; nu < kc; ++nu) out[nu * r + kap] += H->Q[c][a * kc + nu] * v;
+        }
+}
+
+/* Step 6 for cluster c (children done). */
+static void hca_compress_cluster(or_hca* H, int64_t c) {
+    const tree_t* T = &H->T;
+    const int leaf = T->child0[c] < 0;
+    const int64_t nct = T->end[c] - T->begin[c];
+    const int k1 = leaf ? 0 : H->rank[T->child0[c]];
+    const int rows = leaf ? (int)nct : k1 + H->rank[T->child1[c]];
+    /* F_c: the farfield blocks of c and of its ancestors */
+    int64_t nb = 0, cols = 0;
+    for (int64_t a = c; a >= 0; a = T->parent[a])
+        for (int64_t q = H->far_ptr[a]; q < H->far_ptr[a + 1]; ++q) {
+            ++nb;
+            cols += H->brank[H->far_col[q]];
+        }
+    double* Z = calloc((size_t)rows * cols + 1, sizeof(double));
+    int64_t off = 0;
+    for (int64_t a = c; a >= 0; a = T->parent[a])
+        for (int64_t q = H->far_ptr[a]; q < H->far_ptr[a + 1]; ++q) {
+            const int64_t b = H->far_col[q];
+            const int r = H->brank[b];
+            if (r == 0) continue;
+            double* Ah = malloc((size_t)rows * r * sizeof(double));
+            if (leaf) {
+                const int64_t s = H->far.s[b];
+                for (int64_t i = 0; i < nct; ++i)
+                    for (int kap = 0; kap < r; ++kap) {
+                        double p[3];
+                        hca_node(H, s, H->bsig[b][kap], p);
+                        Ah[i * r + kap] = hca_panel_potential(&H->mesh, T->perm[T->begin[c] + i], p);
+                    }
+            } else {
+                hca_project_A(H, b, T->child0[c], Ah);
+                hca_project_A(H, b, T->child1[c], Ah + (size_t)k1 * r);
+            }
+            for (int i = 0; i < rows; ++i)
+                for (int j = 0; j < r; ++j) {
+                    double acc = 0.0;
+                    for (int l = 0; l < r; ++l) acc += Ah[i * r + l] * H->bW[b][l * r + j];
+                    Z[(size_t)i * cols + off + j] = acc;
+                }
+            off += r;
+            free(Ah);
+        }
+    (void)nb;
+    int kt = 0;
+    double* U = malloc(((size_t)rows * rows + 1) * sizeof(double));
+    if (rows > 0 && cols > 0) {
+        double* sv = malloc((size_t)rows * sizeof(double));
+        hca_left_svd(Z, rows, (int)cols, U, sv);
+        const int lim = rows < cols ? rows : (int)cols;
+        if (sv[0] > 0.0)
+            while (kt < lim && kt < H->kmax && sv[kt] > H->eps_c * sv[0]) ++kt;
+        free(sv);
+    }
+    free(Z);
+    H->rank[c] = kt;
+    H->Q[c] = malloc(((size_t)nct * kt + 1) * sizeof(double));
+    if (leaf) {
+        for (int64_t i = 0; i < nct; ++i)
+            for (int j = 0; j < kt; ++j) H->Q[c][i * kt + j] = U[i * rows + j];
+    } else {
+        const int64_t ch[2] = {T->child0[c], T->child1[c]};
+        int roff = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int kc = H->rank[ch[h]];
+            H->E[ch[h]] = malloc(((size_t)kc * kt + 1) * sizeof(double));
+            for (int a = 0; a < kc; ++a)
+                for (int j = 0; j < kt; ++j) H->E[ch[h]][a * kt + j] = U[(roff + a) * rows + j];
+            /* Q_c restricted to the child: Q_child E_child */
+            const int64_t b0 = T->begin[ch[h]] - T->begin[c], nch = T->end[ch[h]] - T->begin[ch[h]];
+            for (int64_t i = 0; i < nch; ++i)
+                for (int j = 0; j < kt; ++j) {
+                    double acc = 0.0;
+                    for (int a = 0; a < kc; ++a) acc += H->Q[ch[h]][i * kc + a] * H->E[ch[h]][a * kt + j];
+                    H->Q[c][(b0 + i) * kt + j] = acc;
+                }
+            roff += kc;
+        }
+    }
+    free(U);
+}
+
+/* Step 7 for farfield block b. */
+static void hca_coupling(or_hca* H, int64_t b) {
+    const int64_t t = H->far.t[b], s = H->far.s[b];
+    const int r = H->brank[b], kt = H->rank[t], ks = H->rank[s];
+    const int64_t nt_ = H->T.end[t] - H->T.begin[t], ns = H->T.end[s] - H->T.begin[s];
+    double* Sb = calloc((size_t)kt * ks + 1, sizeof(double));
+    if (r > 0 && kt > 0 && ks > 0) {
+        double* A = malloc((size_t)nt_ * r * sizeof(double));
+        double* B = malloc((size_t)ns * r * sizeof(double));
+        hca_A(H, b, A);
+        hca_B(H, b, B);
+        double* QA = calloc((size_t)kt * r, sizeof(double));
+        double* QB = calloc((size_t)ks * r, sizeof(double));
+        for (int64_t i = 0; i < nt_; ++i)
+            for (int nu = 0; nu < kt; ++nu)
+                for (int l = 0; l < r; ++l) QA[nu * r + l] += H->Q[t][i * kt + nu] * A[i * r + l];
+        for (int64_t j = 0; j < ns; ++j)
+            for (int mu = 0; mu < ks; ++mu)
+                for (int l = 0; l < r; ++l) QB[mu * r + l] += H->Q[s][j * ks + mu] * B[j * r + l];
+        for (int nu = 0; nu < kt; ++nu)
+            for (int mu = 0; mu < ks; ++mu) {
+                double acc = 0.0;
+                for (int kap = 0; kap < r; ++kap)
+                    for (int lam = 0; lam < r; ++lam) acc += QA[nu * r + kap] * H->bC[b][kap * r + lam] * QB[mu * r + lam];
+                Sb[nu * ks + mu] = acc;
+            }
+        free(A); free(B); free(QA); free(QB);
+    }
+    H->S[b] = Sb;
+}
+
+or_hca* or_hca_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int m, double eta, int leaf,
+                      double eps_aca, int kaca, double eps_c, int kmax, int q_ss) {
+    if (m < 1 || m > 8 || leaf < 1 || nt < 1 || kmax < 1 || kaca < 1 || !(eps_aca >= 0.0) || !(eps_c >= 0.0))
+        return NULL;
+    or_hca* H = calloc(1, sizeof(or_hca));
+    H->xyz = malloc(3 * nv * sizeof(double));
+    H->tri = malloc(3 * nt * sizeof(int32_t));
+    memcpy(H->xyz, xyz, 3 * nv * sizeof(double));
+    memcpy(H->tri, tri, 3 * nt * sizeof(int32_t));
+    H->mesh.xyz = H->xyz;
+    H->mesh.tri = H->tri;
+    H->mesh.nv = nv;
+    H->mesh.nt = nt;
+    H->m = m;
+    H->k = m * m * m;
+    H->kaca = kaca < H->k ? kaca : H->k;
+    H->kmax = kmax;
+    H->q_ss = q_ss;
+    H->eta = eta;
+    H->eps_aca = eps_aca;
+    H->eps_c = eps_c;
+    tree_t* T = &H->T;
+    T->n = nt;
+    T->perm = malloc(nt * sizeof(int64_t));
+    for (int64_t i = 0; i < nt; ++i) T->perm[i] = i;
+    int64_t* tmp = malloc(nt * sizeof(int64_t));
+    tree_split(&H->mesh, T, 0, nt, -1, 0, leaf, tmp);
+    free(tmp);
+    block_build(T, eta, 0, 0, &H->far, &H->near);
+    const int64_t nc = T->count, nf = H->far.n;
+    int64_t* ids = malloc((nf ? nf : 1) * sizeof(int64_t));
+    for (int64_t b = 0; b < nf; ++b) ids[b] = b;
+    H->far_ptr = csr_from(nc, H->far.t, ids, nf, &H->far_col); /* block ids by row cluster */
+    free(ids);
+    H->near_ptr = csr_from(nc, H->near.t, H->near.s, H->near.n, &H->near_col);
+    H->nodes = malloc((size_t)nc * 3 * m * sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) cluster_nodes(T->bmin + 3 * c, T->bmax + 3 * c, m, H->nodes + c * 3 * m);
+    H->brank = calloc(nf + 1, sizeof(int));
+    H->btau = calloc(nf + 1, sizeof(int*));
+    H->bsig = calloc(nf + 1, sizeof(int*));
+    H->bC = calloc(nf + 1, sizeof(double*));
+    H->bW = calloc(nf + 1, sizeof(double*));
+    H->S = calloc(nf + 1, sizeof(double*));
+    H->rank = calloc(nc, sizeof(int));
+    H->Q = calloc(nc, sizeof(double*));
+    H->E = calloc(nc, sizeof(double*));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nf; ++b) {
+        hca_block_aca(H, b);
+        hca_block_weight(H, b);
+    }
+    int maxlev = 0;
+    for (int64_t c = 0; c < nc; ++c)
+        if (T->level[c] > maxlev) maxlev = T->level[c];
+    for (int lev = maxlev; lev >= 0; --lev) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t c = 0; c < nc; ++c)
+            if (T->level[c] == lev) hca_compress_cluster(H, c);
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nf; ++b) hca_coupling(H, b);
+    return H;
+}
+
+void or_hca_destroy(or_hca* H) {
+    if (!H) return;
+    tree_t* T = &H->T;
+    for (int64_t b = 0; b < H->far.n; ++b) {
+        free(H->btau[b]); free(H->bsig[b]); free(H->bC[b]); free(H->bW[b]); free(H->S[b]);
+    }
+    for (int64_t c = 0; c < T->count; ++c) {
+        free(H->Q[c]);
+        free(H->E[c]);
+    }
+    free(H->btau); free(H->bsig); free(H->bC); free(H->bW); free(H->S); free(H->brank);
+    free(H->Q); free(H->E); free(H->rank); free(H->nodes);
+    free(H->far_ptr); free(H->far_col); free(H->near_ptr); free(H->near_col);
+    free(H->far.t); free(H->far.s); free(H->near.t); free(H->near.s);
+    free(T->perm); free(T->begin); free(T->end); free(T->child0); free(T->child1); free(T->parent);
+    free(T->level); free(T->bmin); free(T->bmax);
+    free(H->xyz); free(H->tri);
+    free(H);
+}
+
+/* counts: clusters, farfield blocks, nearfield blocks, largest cluster rank,
+ * k = m^3, largest block rank */
+void or_hca_sizes(const or_hca* H, int64_t* out) {
+    out[0] = H->T.count;
+    out[1] = H->far.n;
+    out[2] = H->near.n;
+    int mx = 0, mb = 0;
+    for (int64_t c = 0; c < H->T.count; ++c)
+        if (H->rank[c] > mx) mx = H->rank[c];
+    for (int64_t b = 0; b < H->far.n; ++b)
+        if (H->brank[b] > mb) mb = H->brank[b];
+    out[3] = mx;
+    out[4] = H->k;
+    out[5] = mb;
+}
+void or_hca_ranks(const or_hca* H, int32_t* rank, int32_t* brank) {
+    if (rank)
+        for (int64_t c = 0; c < H->T.count; ++c) rank[c] = H->rank[c];
+    if (brank)
+        for (int64_t b = 0; b < H->far.n; ++b) brank[b] = H->brank[b];
+}
+/* farfield block list (row and column clusters) and the user triangle
+ * indices of cluster c in tree order (returns |c|) */
+void or_hca_blocks(const or_hca* H, int64_t* far_t, int64_t* far_s) {
+    for (int64_t b = 0; b < H->far.n; ++b) {
+        far_t[b] = H->far.t[b];
+        far_s[b] = H->far.s[b];
+    }
+}
+int64_t or_hca_cluster(const or_hca* H, int64_t c, int64_t* idx) {
+    for (int64_t a = H->T.begin[c]; a < H->T.end[c]; ++a) idx[a - H->T.begin[c]] = H->T.perm[a];
+    return H->T.end[c] - H->T.begin[c];
+}
+/* pivots (node indices) and C_b of block b; returns r_b */
+int or_hca_block(const or_hca* H, int64_t b, int32_t* tau, int32_t* sigma, double* C) {
+    const int r = H->brank[b];
+    for (int a = 0; a < r; ++a) {
+        if (tau) tau[a] = H->btau[b][a];
+        if (sigma) sigma[a] = H->bsig[b][a];
+    }
+    if (C) memcpy(C, H->bC[b], (size_t)r * r * sizeof(double));
+    return r;
+}
+/* the interpolation node nu of cluster c */
+void or_hca_node(const or_hca* H, int64_t c, int nu, double* x) { hca_node(H, c, nu, x); }
+/* g~_hca(x, y) of block b: sum over kappa, lambda of g(x, xi_{s,sigma_kappa})
+ * c_{kappa lambda} g(xi_{t,tau_lambda}, y) */
+double or_hca_kernel(const or_hca* H, int64_t b, const double* x, const double* y) {
+    const int r = H->brank[b];
+    double s = 0.0;
+    for (int kap = 0; kap < r; ++kap) {
+        double p[3];
+        hca_node(H, H->far.s[b], H->bsig[b][kap], p);
+        const double gx = kernel_slp(x, p);
+        for (int lam = 0; lam < r; ++lam) {
+            double q[3];
+            hca_node(H, H->far.t[b], H->btau[b][lam], q);
+            s += gx * H->bC[b][kap * r + lam] * kernel_slp(q, y);
+        }
+    }
+    return s;
+}
+/* A_b C_b B_b^T (|t| x |s|, tree order of both clusters) */
+void or_hca_block_matrix(const or_hca* H, int64_t b, double* out) {
+    const int64_t t = H->far.t[b], s = H->far.s[b];
+    const int r = H->brank[b];
+    const int64_t nt_ = H->T.end[t] - H->T.begin[t], ns = H->T.end[s] - H->T.begin[s];
+    double* A = malloc(((size_t)nt_ * r + 1) * sizeof(double));
+    double* B = malloc(((size_t)ns * r + 1) * sizeof(double));
+    hca_A(H, b, A);
+    hca_B(H, b, B);
+    for (int64_t i = 0; i < nt_; ++i)
+        for (int64_t j = 0; j < ns; ++j) {
+            double acc = 0.0;
+            for (int kap = 0; kap < r; ++kap)
+                for (int lam = 0; lam < r; ++lam) acc += A[i * r + kap] * H->bC[b][kap * r + lam] * B[j * r + lam];
+            out[i * ns + j] = acc;
+        }
+    free(A);
+    free(B);
+}
+/* Q_c (|c| x k_c), E_c (k_c x k_parent), S_b (k_t x k_s); -1 where absent */
+int or_hca_basis(const or_hca* H, int64_t c, double* out) {
+    if (c < 0 || c >= H->T.count) return -1;
+    memcpy(out, H->Q[c], (size_t)(H->T.end[c] - H->T.begin[c]) * H->rank[c] * sizeof(double));
+    return 0;
+}
+int or_hca_transfer(const or_hca* H, int64_t c, double* out) {
+    if (c <= 0 || c >= H->T.count) return -1;
+    memcpy(out, H->E[c], (size_t)H->rank[c] * H->rank[H->T.parent[c]] * sizeof(double));
+    return 0;
+}
+int or_hca_coupling(const or_hca* H, int64_t b, double* out) {
+    if (b < 0 || b >= H->far.n) return -1;
+    memcpy(out, H->S[b], (size_t)H->rank[H->far.t[b]] * H->rank[H->far.s[b]] * sizeof(double));
+    return 0;
+}
+
+/* y = G~ x (x, y column-major n x nrhs, user order).  hmatrix = 0: the
+ * compressed H^2 form (leaf forward x-hat_t = Q_t^T x|_t, upward through E,
+ * coupling S, downward, leaf backward y|_t += Q_t y-hat_t); hmatrix = 1: the
+ * HCA blocks themselves, y|_t += A_b C_b B_b^T x|_s.  parts selects the
+ * farfield / nearfield (nearfield: the Galerkin entries of the H^2 form). */
+void or_hca_matvec(const or_hca* H, const double* x, int nrhs, double* y, int parts, int hmatrix) {
+    const tree_t* T = &H->T;
+    const int64_t n = T->n, nc = T->count;
+    for (int64_t i = 0; i < n * nrhs; ++i) y[i] = 0.0;
+    if ((parts & OR_PART_FAR) && hmatrix) {
+        /* row clusters in parallel: every block of row t writes rows of t only */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t q = H->far_ptr[t]; q < H->far_ptr[t + 1]; ++q) {
+                const int64_t b = H->far_col[q], s = H->far.s[b];
+                const int r = H->brank[b];
+                const int64_t nt_ = T->end[t] - T->begin[t], ns = T->end[s] - T->begin[s];
+                double* A = malloc(((size_t)nt_ * r + 1) * sizeof(double));
+                double* B = malloc(((size_t)ns * r + 1) * sizeof(double));
+                double* u = calloc((size_t)r * nrhs + 1, sizeof(double));
+                double* v = calloc((size_t)r * nrhs + 1, sizeof(double));
+                hca_A(H, b, A);
+                hca_B(H, b, B);
+                for (int64_t j = 0; j < ns; ++j)
+                    for (int lam = 0; lam < r; ++lam)
+                        for (int rr = 0; rr < nrhs; ++rr) u[lam * nrhs + rr] += B[j * r + lam] * x[T->perm[T->begin[s] + j] + rr * n];
+                for (int kap = 0; kap < r; ++kap)
+                    for (int lam = 0; lam < r; ++lam)
+                        for (int rr = 0; rr < nrhs; ++rr) v[kap * nrhs + rr] += H->bC[b][kap * r + lam] * u[lam * nrhs + rr];
+                for (int64_t i = 0; i < nt_; ++i)
+                    for (int kap = 0; kap < r; ++kap)
+                        for (int rr = 0; rr < nrhs; ++rr) y[T->perm[T->begin[t] + i] + rr * n] += A[i * r + kap] * v[kap * nrhs + rr];
+                free(A); free(B); free(u); free(v);
+            }
+    }
+    if ((parts & OR_PART_FAR) && !hmatrix) {
+        int K = 1;
+        for (int64_t c = 0; c < nc; ++c)
+            if (H->rank[c] > K) K = H->rank[c];
+        double* xh = calloc((size_t)nc * K * nrhs, sizeof(double));
+        double* yh = calloc((size_t)nc * K * nrhs, sizeof(double));
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T->child0[c] >= 0) continue;
+            const int kc = H->rank[c];
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a)
+                for (int nu = 0; nu < kc; ++nu)
+                    for (int r = 0; r < nrhs; ++r)
+                        xh[(c * K + nu) * nrhs + r] += H->Q[c][(a - T->begin[c]) * kc + nu] * x[T->perm[a] + r * n];
+        }
+        for (int64_t c = nc - 1; c >= 1; --c) {
+            const int64_t p = T->parent[c];
+            const int kc = H->rank[c], kp = H->rank[p];
+            for (int nu = 0; nu < kp; ++nu)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int a = 0; a < kc; ++a) s += H->E[c][a * kp + nu] * xh[(c * K + a) * nrhs + r];
+                    xh[(p * K + nu) * nrhs + r] += s;
+                }
+        }
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t q = H->far_ptr[t]; q < H->far_ptr[t + 1]; ++q) {
+                const int64_t b = H->far_col[q], s = H->far.s[b];
+                const int kt = H->rank[t], ks = H->rank[s];
+                for (int nu = 0; nu < kt; ++nu)
+                    for (int mu = 0; mu < ks; ++mu)
+                        for (int r = 0; r < nrhs; ++r)
+                            yh[(t * K + nu) * nrhs + r] += H->S[b][nu * ks + mu] * xh[(s * K + mu) * nrhs + r];
+            }
+        for (int64_t c = 1; c < nc; ++c) {
+            const int64_t p = T->parent[c];
+            const int kc = H->rank[c], kp = H->rank[p];
+            for (int a = 0; a < kc; ++a)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < kp; ++nu) s += H->E[c][a * kp + nu] * yh[(p * K + nu) * nrhs + r];
+                    yh[(c * K + a) * nrhs + r] += s;
+                }
+        }
+        for (int64_t c = 0; c < nc; ++c) {
+            if (T->child0[c] >= 0) continue;
+            const int kc = H->rank[c];
+            for (int64_t a = T->begin[c]; a < T->end[c]; ++a)
+                for (int r = 0; r < nrhs; ++r) {
+                    double s = 0.0;
+                    for (int nu = 0; nu < kc; ++nu) s += H->Q[c][(a - T->begin[c]) * kc + nu] * yh[(c * K + nu) * nrhs + r];
+                    y[T->perm[a] + r * n] += s;
+                }
+        }
+        free(xh);
+        free(yh);
+    }
+    if (parts & OR_PART_NEAR) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nc; ++t)
+            for (int64_t b = H->near_ptr[t]; b < H->near_ptr[t + 1]; ++b) {
+                const int64_t s = H->near_col[b];
+                for (int64_t a = T->begin[t]; a < T->end[t]; ++a) {
+                    const int64_t i = T->perm[a];
+                    for (int64_t bb = T->begin[s]; bb < T->end[s]; ++bb) {
+                        const int64_t j = T->perm[bb];
+                        const double e = or_entry(OR_SLP, &H->mesh, i, j, H->q_ss);
+                        for (int r = 0; r < nrhs; ++r) y[i + r * n] += e * x[j + r * n];
+                    }
+                }
+            }
+    }
+}

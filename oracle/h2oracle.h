@@ -158,6 +158,26 @@ int64_t or_gca_L(const or_gca* G, int64_t c, int64_t* rows, double* L);
 int64_t or_gca_rowcount(const or_gca* G, int64_t c);
 void or_gca_matvec(const or_gca* G, const double* x, int nrhs, double* y, int parts);
 
+/* Hybrid cross approximation of the single layer G (section 3) and its
+ * hierarchical compression into an H^2-matrix; the specification is written
+ * out before struct or_hca in h2oracle.c. */
+typedef struct or_hca or_hca;
+or_hca* or_hca_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int m, double eta, int leaf,
+                      double eps_aca, int kaca, double eps_c, int kmax, int q_ss);
+void or_hca_destroy(or_hca* H);
+void or_hca_sizes(const or_hca* H, int64_t* out);
+void or_hca_ranks(const or_hca* H, int32_t* rank, int32_t* brank);
+void or_hca_blocks(const or_hca* H, int64_t* far_t, int64_t* far_s);
+int64_t or_hca_cluster(const or_hca* H, int64_t c, int64_t* idx);
+int or_hca_block(const or_hca* H, int64_t b, int32_t* tau, int32_t* sigma, double* C);
+void or_hca_node(const or_hca* H, int64_t c, int nu, double* x);
+double or_hca_kernel(const or_hca* H, int64_t b, const double* x, const double* y);
+void or_hca_block_matrix(const or_hca* H, int64_t b, double* out);
+int or_hca_basis(const or_hca* H, int64_t c, double* out);
+int or_hca_transfer(const or_hca* H, int64_t c, double* out);
+int or_hca_coupling(const or_hca* H, int64_t b, double* out);
+void or_hca_matvec(const or_hca* H, const double* x, int nrhs, double* y, int parts, int hmatrix);
+
 #ifdef __cplusplus
 }
 #endif
