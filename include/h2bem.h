@@ -73,6 +73,7 @@ extern "C" {
 /* cluster bases of the farfield (h2bem_opts.basis) */
 #define H2BEM_BASIS_CHEBYSHEV 0 /* tensor Chebyshev interpolation of order m (section 3) */
 #define H2BEM_BASIS_GCA 1       /* Green cross approximation (section 4)                 */
+#define H2BEM_BASIS_HCA 2       /* hybrid cross approximation, compressed to H^2 (section 3) */
 
 typedef struct h2bem_mesh h2bem_mesh;
 typedef struct h2bem_tree h2bem_tree;
@@ -139,6 +140,23 @@ typedef struct {
                         /*    reports H2BEM_ERR_TIMEOUT (its result is invalid)                   */
     double gca_eps;     /* GCA: ACA stops when a pivot falls to gca_eps times the first            */
                         /*    (>= 0, default 1e-6)                                                 */
+    /* basis = H2BEM_BASIS_HCA (single layer; FP64 and MIXED_FP32 tiers): for every farfield   */
+    /* block (t, s) the coupling matrix S = g(xi_t, xi_s) of the order-m Chebyshev nodes is     */
+    /* cross-approximated with full pivoting, S ~ S|sigma C S|tau with C = (S|tau,sigma)^-1,  */
+    /* and the interpolation "taken back": G|t x s ~ A C B^T with A = int g(x, xi_s,sigma),    */
+    /* B = int g(xi_t,tau, y) (eq. (hca_discrete), 7-point rule).  The blocks are then         */
+    /* compressed into orthonormal nested cluster bases Q_t (truncated singular vectors of    */
+    /* the block rows of t and its ancestors, from the leaves up) with couplings               */
+    /* Q_t^T A C B^T Q_s, stored in the tier's precision; the transposed apply uses stored     */
+    /* transposed couplings (the HCA matrix is not exactly symmetric).  Host construction    */
+    /* (OpenMP); its cost grows as n log n times the blocks per cluster row.                 */
+    int hca_kaca;       /* HCA: most cross-approximation steps per block (>= 1, at most m^3 are   */
+                        /*    taken; default 64)                                                   */
+    int hca_kmax;       /* HCA: largest rank of a compressed cluster basis (1..64, default 64)     */
+    double hca_eps_aca; /* HCA: a block's cross approximation stops when a pivot falls to          */
+                        /*    hca_eps_aca times the first (>= 0, default 1e-6)                     */
+    double hca_eps;     /* HCA: compression keeps the singular values above hca_eps times the      */
+                        /*    largest of each cluster's block row (>= 0, default 1e-6)             */
 } h2bem_opts;
 
 /* Statistics of an operator (counts are exact, from its own block lists). */
@@ -168,8 +186,9 @@ typedef struct {
     int64_t near_stored_bytes; /* device bytes of the stored nearfield blocks */
                                /* (opts.store_near), else 0                    */
     int64_t far_stored_bytes;  /* device bytes of stored farfield matrices     */
-                               /* (GCA: coupling and transfer matrices)        */
-    double mean_rank;          /* GCA: mean rank over the clusters; else k     */
+                               /* (GCA: coupling and transfer matrices; HCA:   */
+                               /* also the transposed couplings)               */
+    double mean_rank;          /* GCA, HCA: mean rank over the clusters; else k */
 } h2bem_stats;
 
 /* Message of the last failed call on the calling thread (empty if none).
@@ -229,13 +248,25 @@ int h2bem_blocks(const h2bem_tree* tree, double eta, int64_t* nfar, int64_t* nne
 int h2bem_gca_bases(const h2bem_mesh* mesh, const h2bem_tree* tree, const h2bem_opts* opts, int64_t* rank,
                     int64_t* npiv, int64_t* piv);
 
+/* ---- hybrid cross approximation (host only; section 3) -------------------- */
+/* The ranks of the HCA construction that h2bem_operator_create builds with
+ * opts->basis = H2BEM_BASIS_HCA for the single layer with interpolation order
+ * m and admissibility eta (hca_* fields of opts; the others are ignored):
+ * rank[c] of the compressed basis of every cluster (nclusters values) and
+ * brank[b] of the cross approximation of every farfield block, in the order
+ * of h2bem_blocks (nfar values).  Any output may be NULL.  Errors: ARG (NULL
+ * mesh, tree or opts, sizes, m, eta, hca_* fields). */
+int h2bem_hca_ranks(const h2bem_mesh* mesh, const h2bem_tree* tree, int m, double eta, const h2bem_opts* opts,
+                    int64_t* rank, int64_t* nfar, int64_t* brank);
+
 /* ---- operator -------------------------------------------------------------- */
 int h2bem_opts_default(h2bem_opts* opts);
 /* Selects G (H2BEM_SLP) or K (H2BEM_DLP), interpolation order m (1..6,
  * k = m^3, section 3) and admissibility eta; builds the block lists and
  * uploads mesh, tree and lists to the current CUDA device.  opts may be NULL
- * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts; GCA bases
- * with the double layer, a tensor-core tier or recompute_basis), OOM, CUDA. */
+ * (defaults).  Synchronous.  Errors: ARG (kernel, m, eta, opts; GCA or HCA
+ * bases with the double layer, a tensor-core tier or recompute_basis), OOM,
+ * CUDA. */
 int h2bem_operator_create(const h2bem_mesh* mesh, const h2bem_tree* tree, int kernel, int m, double eta,
                           const h2bem_opts* opts, h2bem_op** out);
 /* Many meshes as one operator (batching).  Builds the block-diagonal operator

@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libh2bem.so")
 PEAKS = os.path.join(OUT_DIR, "peaks")  # arithmetic-peak microbenchmark (csrc/peaks.cu)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "gca.cpp", "k_gca.cu", "k_misc.cu", "k_nearsym.cu", "k_sing.cu", "k_far.cu", "k_coupling.cu", "k_coupling_tc.cu", "k_cg.cu", "k_grad.cu", "k_nearstore.cu", "k_hyper.cu", "k_p1.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "gca.cpp", "hca.cpp", "k_gca.cu", "k_misc.cu", "k_nearsym.cu", "k_sing.cu", "k_far.cu", "k_coupling.cu", "k_coupling_tc.cu", "k_cg.cu", "k_grad.cu", "k_nearstore.cu", "k_hyper.cu", "k_p1.cu", "noalloc.cu"]
 
 
 def _nvcc() -> str:
@@ -30,7 +30,7 @@ def _flags(src: str):
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
     if src.endswith(".cu"):
         return ARCH + ["-lineinfo", "--expt-relaxed-constexpr", "-Xptxas", "-O3"] + common
-    if src == "gca.cpp":  # the host construction of the GCA bases runs on OpenMP threads
+    if src in ("gca.cpp", "hca.cpp"):  # the host constructions of the GCA / HCA bases run on OpenMP threads
         return common + ["-Xcompiler", "-fopenmp"]
     return common
 

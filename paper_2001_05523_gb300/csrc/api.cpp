@@ -692,6 +692,11 @@ struct h2bem_op {
     // stored compactly at eoff[c] / soff[b] (FP64, or FP32 in MIXED_FP32); the
     // leaf bases are basisV, zero-padded to k columns
     int gca = 0;
+    // hybrid cross approximation (opts.basis = HCA): the same stored passes as
+    // GCA (gca = 1), couplings from the host; the transposed apply runs the
+    // column-ordered blocks (far_t) with the transposed couplings at g_soff_t
+    int hca = 0;
+    DevBuf g_soff_t, g_St;
     int tc_wait_test = 0;  // opts.tc_wait_test (tests of the tensor-core timeout path)
     DevBuf g_rank, g_pivoff, g_piv, g_eoff, g_E, g_soff, g_S;
     int64_t gca_bytes = 0;
@@ -741,6 +746,10 @@ extern "C" int h2bem_opts_default(h2bem_opts* opts) {
     opts->gca_q = 4;
     opts->gca_kmax = h2::kGcaMaxRank;
     opts->gca_eps = 1e-6;
+    opts->hca_kaca = 64;
+    opts->hca_kmax = h2::kGcaMaxRank;
+    opts->hca_eps_aca = 1e-6;
+    opts->hca_eps = 1e-6;
     return H2BEM_OK;
 }
 
@@ -1049,6 +1058,184 @@ extern "C" int h2bem_gca_bases(const h2bem_mesh* mesh, const h2bem_tree* tree, c
     return H2BEM_OK;
 }
 
+// Radon's 7-point rule on the unit simplex (degree 5; weights sum to 1)
+static void radon7_rule(double* u, double* v, double* w) {
+    const double r15 = std::sqrt(15.0);
+    const double a = (6.0 - r15) / 21.0, b = (6.0 + r15) / 21.0;
+    const double wa = (155.0 - r15) / 1200.0, wb = (155.0 + r15) / 1200.0;
+    const double uu[7] = {1.0 / 3.0, a, 1.0 - 2.0 * a, a, b, 1.0 - 2.0 * b, b};
+    const double vv[7] = {1.0 / 3.0, a, a, 1.0 - 2.0 * a, b, b, 1.0 - 2.0 * b};
+    const double ww[7] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    for (int q = 0; q < 7; ++q) {
+        u[q] = uu[q];
+        v[q] = vv[q];
+        w[q] = ww[q];
+    }
+}
+
+static int check_hca_opts(const h2bem_opts& o, int m, const char* who) {
+    (void)m;
+    if (o.hca_kaca < 1) return fail(H2BEM_ERR_ARG, "%s: hca_kaca must be >= 1", who);
+    if (o.hca_kmax < 1 || o.hca_kmax > h2::kGcaMaxRank)
+        return fail(H2BEM_ERR_ARG, "%s: hca_kmax must be in 1..%d", who, h2::kGcaMaxRank);
+    if (!(o.hca_eps_aca >= 0.0) || !std::isfinite(o.hca_eps_aca) || !(o.hca_eps >= 0.0) || !std::isfinite(o.hca_eps))
+        return fail(H2BEM_ERR_ARG, "%s: hca_eps_aca and hca_eps must be finite and >= 0", who);
+    return H2BEM_OK;
+}
+
+static void hca_setup_fill(h2::HcaSetup& S, const h2bem_mesh* mesh, const h2bem_tree* tree, int m,
+                           const h2bem_opts& opts, const double* ru, const double* rv, const double* rw) {
+    S.xyz = mesh->xyz.data();
+    S.tri = mesh->tri.data();
+    S.n = tree->n;
+    S.nc = tree->nc;
+    S.perm = tree->perm.data();
+    S.begin = tree->begin.data();
+    S.end = tree->end.data();
+    S.child0 = tree->child0.data();
+    S.child1 = tree->child1.data();
+    S.level = tree->level.data();
+    S.bmin = tree->bmin.data();
+    S.bmax = tree->bmax.data();
+    S.m = m;
+    S.kaca = opts.hca_kaca;
+    S.kmax = opts.hca_kmax;
+    S.eps_aca = opts.hca_eps_aca;
+    S.eps_c = opts.hca_eps;
+    S.ru = ru;
+    S.rv = rv;
+    S.rw = rw;
+}
+
+// HCA bases of the operator: construction on the host for the blocks of the
+// farfield CSR, then leaf bases [pos][K] (zero-padded), transfers, couplings
+// in CSR order and transposed couplings in the order of far_t (column-major,
+// every block on a 16-byte boundary), uploaded in the tier's precision.
+static int hca_setup(h2bem_op* op, const h2bem_mesh* mesh, const h2bem_tree* tree, const h2bem_opts& opts) {
+    const int64_t n = op->n, nc = op->nc;
+    std::vector<int> bt, bs;
+    for (int r = 0; r < op->far.nrows(); ++r)
+        for (int b = op->far.ptr[r]; b < op->far.ptr[r + 1]; ++b) {
+            bt.push_back(op->far.rows[r]);
+            bs.push_back(op->far.col[b]);
+        }
+    double ru[7], rv[7], rw[7];
+    radon7_rule(ru, rv, rw);
+    h2::HcaSetup S{};
+    hca_setup_fill(S, mesh, tree, op->m, opts, ru, rv, rw);
+    S.nfar = (int64_t)bt.size();
+    S.far_t = bt.data();
+    S.far_s = bs.data();
+    h2::HcaResult R;
+    h2::hca_build(S, R);
+    int kmax = 1;
+    double rsum = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+        kmax = std::max(kmax, R.rank[c]);
+        rsum += R.rank[c];
+    }
+    op->gca = 1;
+    op->hca = 1;
+    op->gca_mean_rank = nc ? rsum / nc : 0.0;
+    const int K = (kmax + 3) / 4 * 4;
+    op->k = K;
+    const bool f32 = op->precision != H2BEM_FP64;
+    const size_t es = f32 ? sizeof(float) : sizeof(double);
+    std::vector<double> B((size_t)n * K, 0.0);
+    for (int64_t c = 0; c < nc; ++c) {
+        if (tree->child0[c] >= 0) continue;
+        const int rk = R.rank[c];
+        for (int64_t a = tree->begin[c]; a < tree->end[c]; ++a)
+            for (int nu = 0; nu < rk; ++nu) B[(size_t)a * K + nu] = R.V[R.voff[c] + (a - tree->begin[c]) * rk + nu];
+    }
+    std::vector<int64_t> eoff(nc, 0);
+    for (int64_t c = 0; c < nc; ++c) eoff[c] = R.eoff[c] < 0 ? 0 : R.eoff[c];
+    auto pad4 = [](int64_t e) { return (e + 3) / 4 * 4; };
+    // forward couplings in CSR order
+    const int64_t nf = (int64_t)bt.size();
+    std::vector<int64_t> soff(nf + 1, 0);
+    for (int64_t b = 0; b < nf; ++b) soff[b + 1] = soff[b] + pad4((int64_t)R.rank[bt[b]] * R.rank[bs[b]]);
+    // the coupling kernel streams every block column-major (entry (nu, mu) of
+    // a kt x ks block at mu kt + nu); hca_build returns them row-major
+    std::vector<double> Sf(std::max<int64_t>(soff[nf], 1), 0.0);
+    for (int64_t b = 0; b < nf; ++b) {
+        const int kt = R.rank[bt[b]], ks = R.rank[bs[b]];
+        for (int nu = 0; nu < kt; ++nu)
+            for (int mu = 0; mu < ks; ++mu) Sf[soff[b] + (int64_t)mu * kt + nu] = R.S[R.soff[b] + (int64_t)nu * ks + mu];
+    }
+    // transposed couplings in the order of far_t (row s, column t: S_(t,s)^T)
+    std::vector<int64_t> first(nc + 1, 0);  // forward blocks of row t: [first[t], first[t+1]) in CSR order
+    for (int64_t b = 0; b < nf; ++b) first[bt[b] + 1]++;
+    for (int64_t c = 0; c < nc; ++c) first[c + 1] += first[c];
+    const int64_t nft = (int64_t)op->far_t.col.size();
+    std::vector<int64_t> sofft(nft + 1, 0);
+    std::vector<int64_t> fwd(nft, -1);
+    for (int r = 0; r < op->far_t.nrows(); ++r) {
+        const int sc = op->far_t.rows[r];
+        for (int q = op->far_t.ptr[r]; q < op->far_t.ptr[r + 1]; ++q) {
+            const int tc = op->far_t.col[q];
+            for (int64_t b = first[tc]; b < first[tc + 1]; ++b)
+                if (bs[b] == sc) {
+                    fwd[q] = b;
+                    break;
+                }
+            if (fwd[q] < 0) return fail(H2BEM_ERR_STATE, "operator_create: HCA transposed block list is inconsistent");
+            sofft[q + 1] = sofft[q] + pad4((int64_t)R.rank[sc] * R.rank[tc]);
+        }
+    }
+    // S_b^T (ks x kt) column-major is S_b row-major
+    std::vector<double> St(std::max<int64_t>(sofft[nft], 1), 0.0);
+    for (int64_t q = 0; q < nft; ++q) {
+        const int64_t b = fwd[q];
+        std::copy(R.S.begin() + R.soff[b], R.S.begin() + R.soff[b + 1], St.begin() + sofft[q]);
+    }
+    int rc;
+    if (f32) {
+        std::vector<float> Bf(B.begin(), B.end()), Ef(R.E.begin(), R.E.end()), Sff(Sf.begin(), Sf.end()),
+            Stf(St.begin(), St.end());
+        if ((rc = upload(op->basisV, Bf)) || (rc = upload(op->g_E, Ef)) || (rc = upload(op->g_S, Sff)) ||
+            (rc = upload(op->g_St, Stf)))
+            return rc;
+    } else {
+        if ((rc = upload(op->basisV, B)) || (rc = upload(op->g_E, R.E)) || (rc = upload(op->g_S, Sf)) ||
+            (rc = upload(op->g_St, St)))
+            return rc;
+    }
+    if ((rc = upload(op->g_rank, R.rank)) || (rc = upload(op->g_eoff, eoff)) || (rc = upload(op->g_soff, soff)) ||
+        (rc = upload(op->g_soff_t, sofft)))
+        return rc;
+    op->gca_bytes = (int64_t)((soff[nf] + sofft[nft] + (int64_t)R.E.size()) * es);
+    return H2BEM_OK;
+}
+
+extern "C" int h2bem_hca_ranks(const h2bem_mesh* mesh, const h2bem_tree* tree, int m, double eta,
+                               const h2bem_opts* opts_in, int64_t* rank, int64_t* nfar, int64_t* brank) {
+    if (!mesh || !tree || !opts_in) return fail(H2BEM_ERR_ARG, "hca_ranks: NULL argument");
+    if (tree->n != mesh->nt) return fail(H2BEM_ERR_ARG, "hca_ranks: tree and mesh differ in size");
+    if (m < 1 || m > kMaxM) return fail(H2BEM_ERR_ARG, "hca_ranks: m must be in 1..%d", kMaxM);
+    if (!(eta >= 0.0) || !std::isfinite(eta)) return fail(H2BEM_ERR_ARG, "hca_ranks: eta must be finite and >= 0");
+    int rc;
+    if ((rc = check_hca_opts(*opts_in, m, "hca_ranks"))) return rc;
+    Blocks Bl;
+    build_blocks(*tree, eta, Bl);
+    std::vector<int> bt(Bl.ft.begin(), Bl.ft.end()), bs(Bl.fs.begin(), Bl.fs.end());
+    double ru[7], rv[7], rw[7];
+    radon7_rule(ru, rv, rw);
+    h2::HcaSetup S{};
+    hca_setup_fill(S, mesh, tree, m, *opts_in, ru, rv, rw);
+    S.nfar = (int64_t)bt.size();
+    S.far_t = bt.data();
+    S.far_s = bs.data();
+    h2::HcaResult R;
+    h2::hca_build(S, R);
+    if (rank)
+        for (int64_t c = 0; c < tree->nc; ++c) rank[c] = R.rank[c];
+    if (nfar) *nfar = S.nfar;
+    if (brank)
+        for (int64_t b = 0; b < S.nfar; ++b) brank[b] = R.brank[b];
+    return H2BEM_OK;
+}
+
 static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blocks* prebuilt, int kernel, int m,
                        double eta, const h2bem_opts* opts_in, h2bem_op** out) {
     if (!out) return fail(H2BEM_ERR_ARG, "operator_create: out is NULL");
@@ -1070,8 +1257,16 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         return fail(H2BEM_ERR_ARG, "operator_create: the tensor-core tiers need m <= 5 (k <= 128), got m = %d", m);
     if (opts.tc_wait_test != 0 && opts.tc_wait_test != 1)
         return fail(H2BEM_ERR_ARG, "operator_create: tc_wait_test must be 0 or 1");
-    if (opts.basis != H2BEM_BASIS_CHEBYSHEV && opts.basis != H2BEM_BASIS_GCA)
+    if (opts.basis != H2BEM_BASIS_CHEBYSHEV && opts.basis != H2BEM_BASIS_GCA && opts.basis != H2BEM_BASIS_HCA)
         return fail(H2BEM_ERR_ARG, "operator_create: unknown basis %d", opts.basis);
+    if (opts.basis == H2BEM_BASIS_HCA) {
+        if (kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "operator_create: HCA bases are built for the single layer");
+        if (opts.precision != H2BEM_FP64 && opts.precision != H2BEM_MIXED_FP32)
+            return fail(H2BEM_ERR_ARG, "operator_create: HCA bases run in the FP64 and MIXED_FP32 tiers");
+        if (opts.recompute_basis) return fail(H2BEM_ERR_ARG, "operator_create: HCA bases are stored (recompute_basis = 0)");
+        int rc;
+        if ((rc = check_hca_opts(opts, m, "operator_create"))) return rc;
+    }
     if (opts.basis == H2BEM_BASIS_GCA) {
         if (kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "operator_create: GCA bases are built for the single layer");
         if (opts.precision != H2BEM_FP64 && opts.precision != H2BEM_MIXED_FP32)
@@ -1419,6 +1614,8 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     for (int l : op->leaves_h) op->max_leaf = std::max(op->max_leaf, (int)(tree->end[l] - tree->begin[l]));
     if (opts.basis == H2BEM_BASIS_GCA) {
         if ((rc = gca_setup(op.get(), mesh, tree, opts))) return rc;
+    } else if (opts.basis == H2BEM_BASIS_HCA) {
+        if ((rc = hca_setup(op.get(), mesh, tree, opts))) return rc;
     } else if (!op->recompute_basis) {
         const bool v32 = op->precision != H2BEM_FP64;
         if ((rc = op->basisV.alloc((size_t)n * op->k * (v32 ? sizeof(float) : sizeof(double))))) return rc;
@@ -1765,8 +1962,12 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     const bool out_dlp = dlp && transpose;   // W_s on the output side
     const int near_ker = !dlp ? h2::SLP : transpose ? h2::DLP_T : h2::DLP;
     // GCA: the single layer is symmetric and its coupling matrices are stored
-    // for the blocks of `far`, so A^T x runs the forward farfield
-    const Csr& far = (transpose && !op->gca) ? op->far_t : op->far;
+    // for the blocks of `far`, so A^T x runs the forward farfield; HCA keeps
+    // transposed couplings for the blocks of `far_t`
+    const bool col_order = transpose && (!op->gca || op->hca);
+    const Csr& far = col_order ? op->far_t : op->far;
+    const DevBuf& g_soff = (transpose && op->hca) ? op->g_soff_t : op->g_soff;
+    const DevBuf& g_S = (transpose && op->hca) ? op->g_St : op->g_S;
     auto mark = [&](int i) {
         if (timed) cudaEventRecord(op->ev[i], s);
     };
@@ -1871,8 +2072,7 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
         if (op->gca)
             h2::launch_gca_coupling(fp32, NR, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
-                                    op->g_rank.as<int>(), op->g_soff.as<int64_t>(), op->g_S.p, (int)op->k, w.xh, w.yh,
-                                    s);
+                                    op->g_rank.as<int>(), g_soff.as<int64_t>(), g_S.p, (int)op->k, w.xh, w.yh, s);
         else
             run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, s);
         mark(4 + fo);

@@ -96,9 +96,11 @@ void L_row(const GcaSetup& S, int64_t pos, const Boundary& B, double* L) {
     }
 }
 
+}  // namespace
+
 // full-pivot cross approximation of the rows x cols matrix A (destroyed)
-int aca(std::vector<double>& A, int rows, int cols, double eps, int kmax, std::vector<int>& tau,
-        std::vector<int>& sigma) {
+int cross_approx(std::vector<double>& A, int rows, int cols, double eps, int kmax, std::vector<int>& tau,
+                 std::vector<int>& sigma) {
     tau.clear();
     sigma.clear();
     std::vector<double> cv(rows), rv(cols);
@@ -128,6 +130,7 @@ int aca(std::vector<double>& A, int rows, int cols, double eps, int kmax, std::v
     return (int)tau.size();
 }
 
+namespace {
 // V = L|_{: x sigma} (L|_{tau x sigma})^{-1}: LU with partial pivoting of
 // M = L|_{tau x sigma}, then V M = B row by row (B = L|_{: x sigma}).
 void interp(const std::vector<double>& L, int rows, int cols, const std::vector<int>& tau,
@@ -204,7 +207,7 @@ int gca_build(const GcaSetup& S, GcaResult& R) {
             for (int r = 0; r < nr; ++r) L_row(S, rows[r], B, &L[(size_t)r * cols]);
             std::vector<double> A = L;
             std::vector<int> tau, sigma;
-            const int rk = aca(A, nr, cols, S.eps, S.kmax, tau, sigma);
+            const int rk = cross_approx(A, nr, cols, S.eps, S.kmax, tau, sigma);
             std::vector<double> Vh;
             interp(L, nr, cols, tau, sigma, Vh);
             R.rank[c] = rk;

@@ -99,6 +99,41 @@ struct GcaResult {
 };
 int gca_build(const GcaSetup& setup, GcaResult& result);
 constexpr int kGcaMaxRank = 64;  // largest GCA rank the kernels stage
+// full-pivot cross approximation of the rows x cols matrix A (row-major,
+// destroyed): the pivot is the first entry in row-major order within a
+// relative 2^-40 of the largest residual entry; stop at rank kmax, at a zero
+// residual or when the pivot falls to eps times the first; row pivots tau,
+// column pivots sigma; returns the rank (gca.cpp)
+int cross_approx(std::vector<double>& A, int rows, int cols, double eps, int kmax, std::vector<int>& tau,
+                 std::vector<int>& sigma);
+// Hybrid cross approximation (section 3) of the single layer and its
+// compression into an H^2-matrix (hca.cpp): the tree as for GcaSetup, the
+// interpolation order m of the blocks' node grids, the farfield blocks
+// (far_t, far_s) in the order the coupling matrices are returned, the cross
+// approximation tolerance / step limit, the compression tolerance / rank cap
+// and the 7-point rule
+struct HcaSetup {
+    const double* xyz;
+    const int32_t* tri;
+    int64_t n, nc;
+    const int64_t *perm, *begin, *end, *child0, *child1, *level;
+    const double *bmin, *bmax;
+    int m, kaca, kmax;
+    double eps_aca, eps_c;
+    const double *ru, *rv, *rw;
+    int64_t nfar;
+    const int *far_t, *far_s;
+};
+// Result: rank per cluster and per block; leaf bases Q (|t| x rank_t
+// row-major, rows in tree order) at voff[t]; transfers E_c (rank_c x
+// rank_parent) at eoff[c] (-1 where absent); coupling S_b (rank_t x rank_s)
+// at soff[b]
+struct HcaResult {
+    std::vector<int> rank, brank;
+    std::vector<int64_t> voff, eoff, soff;
+    std::vector<double> V, E, S;
+};
+int hca_build(const HcaSetup& setup, HcaResult& result);
 // coupling matrices S_b = G|_{t^ x s^} of the farfield CSR (rows / ptr / col)
 // at element offsets soff[b], FP64 quadrature stored as FP32 (f32) or FP64
 void launch_gca_assemble(const Geom& g, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libh2bem.so")
 
 H2BEM_OK, H2BEM_ERR_ARG, H2BEM_ERR_MESH, H2BEM_ERR_OOM, H2BEM_ERR_CUDA, H2BEM_ERR_TIMEOUT, H2BEM_ERR_STATE = range(7)
 H2BEM_SLP, H2BEM_DLP = 0, 1
-H2BEM_BASIS_CHEBYSHEV, H2BEM_BASIS_GCA = 0, 1
+H2BEM_BASIS_CHEBYSHEV, H2BEM_BASIS_GCA, H2BEM_BASIS_HCA = 0, 1, 2
 H2BEM_FP64, H2BEM_MIXED_FP32, H2BEM_MIXED_TF32, H2BEM_MIXED_BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": H2BEM_FP64, "mixed_fp32": H2BEM_MIXED_FP32, "mixed_tf32": H2BEM_MIXED_TF32,
               "mixed_bf16": H2BEM_MIXED_BF16}
@@ -29,7 +29,7 @@ EXPORTED = [
     "h2bem_tree_info", "h2bem_tree_export", "h2bem_tree_destroy", "h2bem_blocks", "h2bem_opts_default",
     "h2bem_operator_create", "h2bem_operator_destroy", "h2bem_stats_get", "h2bem_apply", "h2bem_apply_transpose",
     "h2bem_apply_timed", "h2bem_apply_noalloc", "h2bem_batch_create", "h2bem_grad", "h2bem_apply_mass", "h2bem_apply_hypersingular",
-    "h2bem_cg", "h2bem_gca_bases", "h2bem_apply_dlp_p1", "h2bem_cg_hypersingular",
+    "h2bem_cg", "h2bem_gca_bases", "h2bem_apply_dlp_p1", "h2bem_cg_hypersingular", "h2bem_hca_ranks",
 ]
 
 
@@ -44,7 +44,9 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("singular_fp64", ctypes.c_int), ("recompute_basis", ctypes.c_int), ("store_near", ctypes.c_int),
                 ("basis", ctypes.c_int), ("gca_q", ctypes.c_int), ("gca_kmax", ctypes.c_int),
-                ("tc_wait_test", ctypes.c_int), ("gca_eps", ctypes.c_double)]
+                ("tc_wait_test", ctypes.c_int), ("gca_eps", ctypes.c_double),
+                ("hca_kaca", ctypes.c_int), ("hca_kmax", ctypes.c_int), ("hca_eps_aca", ctypes.c_double),
+                ("hca_eps", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +90,7 @@ def lib():
             "h2bem_tree_destroy": [vp],
             "h2bem_blocks": [vp, d, vp, vp, vp, vp, vp, vp],
             "h2bem_gca_bases": [vp, vp, vp, vp, vp, vp],
+            "h2bem_hca_ranks": [vp, vp, i32, d, vp, vp, vp, vp],
             "h2bem_apply_dlp_p1": [vp, d, vp, i64, i32, vp, i64, i32, vp],
             "h2bem_cg_hypersingular": [vp, vp, vp, i64, i32, vp, i64, d, i32, vp, vp, vp],
             "h2bem_opts_default": [vp],
@@ -189,6 +192,21 @@ def h2bem_gca_bases(mesh, tree, nclusters: int, q: int = 4, kmax: int = 64, eps:
     piv = np.zeros(npiv.value, np.int64)
     _check(lib().h2bem_gca_bases(mesh, tree, ctypes.byref(o), None, None, _np_ptr(piv)))
     return rank, piv
+
+
+def h2bem_hca_ranks(mesh, tree, nclusters: int, m: int = 4, eta: float = 2.0, kaca: int = 64, kmax: int = 64,
+                    eps_aca: float = 1e-6, eps: float = 1e-6):
+    """Ranks of the HCA construction on the host: per cluster (compressed bases)
+    and per farfield block in the order of h2bem_blocks (cross approximation)."""
+    o = h2bem_opts_default()
+    o.basis, o.hca_kaca, o.hca_kmax, o.hca_eps_aca, o.hca_eps = H2BEM_BASIS_HCA, int(kaca), int(kmax), float(eps_aca), float(eps)
+    rank = np.zeros(nclusters, np.int64)
+    nfar = ctypes.c_int64()
+    _check(lib().h2bem_hca_ranks(mesh, tree, int(m), float(eta), ctypes.byref(o), None, ctypes.byref(nfar), None))
+    brank = np.zeros(nfar.value, np.int64)
+    _check(lib().h2bem_hca_ranks(mesh, tree, int(m), float(eta), ctypes.byref(o), _np_ptr(rank), None,
+                                 _np_ptr(brank)))
+    return rank, brank
 
 
 def h2bem_opts_default() -> Opts:
@@ -336,7 +354,8 @@ class BatchOperator:
                  precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
                  recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
-                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False):
+                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False, hca: bool = False,
+                 hca_kaca: int = 64, hca_kmax: int = 64, hca_eps_aca: float = 1e-6, hca_eps: float = 1e-6):
         kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.meshes = [h2bem_mesh_create(mh.vertices, mh.triangles) for mh in meshes]
         self.sizes = [int(mh.nt) for mh in meshes]
@@ -354,6 +373,10 @@ class BatchOperator:
         if gca:
             o.basis = H2BEM_BASIS_GCA
             o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
+        if hca:
+            o.basis = H2BEM_BASIS_HCA
+            o.hca_kaca, o.hca_kmax = int(hca_kaca), int(hca_kmax)
+            o.hca_eps_aca, o.hca_eps = float(hca_eps_aca), float(hca_eps)
         o.tc_wait_test = int(tc_wait_test)
         self.op = h2bem_batch_create(self.meshes, leaf_size, kernel, m, eta, o)
 
@@ -389,7 +412,8 @@ class Operator:
                  leaf_size: int = 32, precision: str | int = "fp64", q_ss: int = 5, cache_singular: bool = False,
                  use_graph: bool = False, autotune: int = 0, singular_fp64: bool = False,
                  recompute_basis: bool = False, store_near: bool = False, gca: bool = False, gca_q: int = 4,
-                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False):
+                 gca_kmax: int = 64, gca_eps: float = 1e-6, tc_wait_test: bool = False, hca: bool = False,
+                 hca_kaca: int = 64, hca_kmax: int = 64, hca_eps_aca: float = 1e-6, hca_eps: float = 1e-6):
         self.kernel = {"slp": H2BEM_SLP, "dlp": H2BEM_DLP}.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self.n = int(np.asarray(triangles).shape[0])
         self.nv = int(np.asarray(vertices).shape[0])
@@ -407,6 +431,10 @@ class Operator:
         if gca:
             o.basis = H2BEM_BASIS_GCA
             o.gca_q, o.gca_kmax, o.gca_eps = int(gca_q), int(gca_kmax), float(gca_eps)
+        if hca:
+            o.basis = H2BEM_BASIS_HCA
+            o.hca_kaca, o.hca_kmax = int(hca_kaca), int(hca_kmax)
+            o.hca_eps_aca, o.hca_eps = float(hca_eps_aca), float(hca_eps)
         o.tc_wait_test = int(tc_wait_test)
         self.op = h2bem_operator_create(self.mesh, self.tree, self.kernel, m, eta, o)
 

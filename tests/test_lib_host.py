@@ -142,3 +142,33 @@ def test_gca_bases_match_oracle(H, orc, mk, q, kmax, eps):
         assert np.array_equal(tr["perm"][piv[off[c]:off[c + 1]]], G.pivots(c)), c
     H.h2bem_tree_destroy(th)
     H.h2bem_mesh_destroy(mh)
+
+
+@pytest.mark.parametrize("mk,m,eps_aca,eps", [
+    (lambda: I.sphere(12), 4, 1e-6, 1e-6),
+    (lambda: I.jitter(I.ellipsoid(10), 0.01, 3), 4, 1e-4, 1e-5),
+    (lambda: I.cube(8), 3, 1e-6, 1e-8),
+])
+def test_hca_ranks_match_oracle(H, orc, mk, m, eps_aca, eps):
+    """The library's host construction of the HCA blocks and their compression
+    (section 3) takes the same discrete decisions as the oracle: the rank of
+    every block's cross approximation (pivot rule within 2^-40 of the largest)
+    and of every cluster's truncated basis (singular values above eps times
+    the largest), although the two compute them with their own QR and Jacobi
+    codes."""
+    mesh = mk()
+    mh = H.h2bem_mesh_create(mesh.vertices, mesh.triangles)
+    th = H.h2bem_tree_build(mh, 32)
+    tr = H.h2bem_tree_export(th, mesh.nt)
+    nc = len(tr["begin"])
+    rank, brank = H.h2bem_hca_ranks(mh, th, nc, m=m, eta=2.0, eps_aca=eps_aca, eps=eps)
+    (ft, fs), _ = H.h2bem_blocks(th, 2.0)
+    Ho = orc.HCA(mesh, m=m, eps_aca=eps_aca, eps_c=eps)
+    assert np.array_equal(rank, Ho.ranks().astype(np.int64))
+    oft, ofs = Ho.blocks()
+    ob = dict(zip(zip(oft.tolist(), ofs.tolist()), Ho.block_ranks().tolist()))
+    assert len(ob) == len(brank)
+    for t, s, r in zip(ft.tolist(), fs.tolist(), brank.tolist()):
+        assert ob[(t, s)] == r, (t, s)
+    H.h2bem_tree_destroy(th)
+    H.h2bem_mesh_destroy(mh)
