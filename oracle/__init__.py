@@ -393,11 +393,11 @@ class H2:
         lib().or_h2_update_geometry(self.h, _p(v))
 
     def grad_vertices(self, w: np.ndarray, x: np.ndarray, parts: int = PART_ALL) -> np.ndarray:
-        """d/dX of sum_r <w_r, A x_r> (single layer), shape (nv, 3)."""
+        """d/dX of sum_r <w_r, A x_r> (single or double layer), shape (nv, 3)."""
         w, x = _f64(w), _f64(x)
         g = np.zeros((self.mesh.nv, 3))
         if lib().or_h2_grad(self.h, _p(w), _p(x), x.shape[0], _p(g), int(parts)):
-            raise ValueError("gradient is available for the single layer only")
+            raise ValueError("gradient is available for the single and double layer only")
         return g
 
     def matvec_subtree(self, c0: int, x: np.ndarray) -> np.ndarray:

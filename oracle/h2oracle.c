@@ -780,6 +780,43 @@ static void tensor_lagrange_grad(const double* z, int m, int nu, const double* x
     g[2] = la * lb * lagrange_deriv(z + 2 * m, m, c, x[2]);
 }
 
+/* second derivative of the 1-D Lagrange polynomial: the sum over ordered
+ * pairs k != l (both != nu) of the product with factors (x - z_o) / (z_nu -
+ * z_o) for the other nodes o and 1 / (z_nu - z_k), 1 / (z_nu - z_l) */
+static double lagrange_deriv2(const double* z, int m, int nu, double x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == nu) continue;
+        for (int l = 0; l < m; ++l) {
+            if (l == nu || l == k) continue;
+            double p = 1.0 / ((z[nu] - z[k]) * (z[nu] - z[l]));
+            for (int o = 0; o < m; ++o)
+                if (o != nu && o != k && o != l) p *= (x - z[o]) / (z[nu] - z[o]);
+            s += p;
+        }
+    }
+    return s;
+}
+/* Hessian of L_{t,nu} at x: h[3 d + e] = d^2 L / dx_d dx_e */
+static void tensor_lagrange_hess(const double* z, int m, int nu, const double* x, double* h) {
+    const int a[3] = {nu % m, (nu / m) % m, nu / (m * m)};
+    double l0[3], l1[3], l2[3];
+    for (int d = 0; d < 3; ++d) {
+        l0[d] = lagrange(z + d * m, m, a[d], x[d]);
+        l1[d] = lagrange_deriv(z + d * m, m, a[d], x[d]);
+        l2[d] = lagrange_deriv2(z + d * m, m, a[d], x[d]);
+    }
+    for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) {
+            double v = 1.0;
+            for (int f = 0; f < 3; ++f) {
+                if (d == e) v *= f == d ? l2[f] : l0[f];
+                else v *= (f == d || f == e) ? l1[f] : l0[f];
+            }
+            h[3 * d + e] = v;
+        }
+}
+
 static int64_t* csr_from(int64_t nrows, const int64_t* key, const int64_t* val, int64_t n, int64_t** col_out) {
     int64_t* ptr = calloc(nrows + 1, sizeof(int64_t));
     for (int64_t b = 0; b < n; ++b) ptr[key[b] + 1]++;
@@ -1489,6 +1526,147 @@ static void entry_grad_slp(const or_mesh* M, int64_t i, int64_t j, int q_ss, dou
     }
 }
 
+/* F(x, y, N) = (x - y).N / (4 pi |x - y|^3): its value, its gradient in x
+ * (the gradient in y is the negative) and in N */
+static double dlp_F(const double* x, const double* y, const double* N, double* gx, double* gN) {
+    double d[3];
+    sub3(x, y, d);
+    const double r2 = dot3(d, d), r = sqrt(r2);
+    const double i3 = OR_INV4PI / (r2 * r), dn = dot3(d, N);
+    for (int e = 0; e < 3; ++e) {
+        gx[e] = i3 * N[e] - 3.0 * i3 * dn * d[e] / r2;
+        gN[e] = i3 * d[e];
+    }
+    return i3 * dn;
+}
+
+/* d(g . N)/dY_k for the area-normal N = (Y1 - Y0) x (Y2 - Y0) / 2 of the
+ * triangle Y in its own vertex order: (Y_{k+1} - Y_{k+2}) x g / 2 */
+static void area_normal_grad(const double* Y, const double* g, double* out /* 9 */) {
+    for (int k = 0; k < 3; ++k) {
+        double e[3], c[3];
+        sub3(Y + 3 * ((k + 1) % 3), Y + 3 * ((k + 2) % 3), e);
+        cross3(e, g, c);
+        for (int d = 0; d < 3; ++d) out[3 * k + d] = 0.5 * c[d];
+    }
+}
+
+/* coef * d k_ij / d(vertices), double layer (eq. (dlp), piecewise constant):
+ * k_ij = |tau_i| sum w F(x, y, N_j) with N_j = |tau_j| n_j, so the entry
+ * depends on the points of both triangles, on |tau_i| and on N_j. */
+static void entry_grad_dlp(const or_mesh* M, int64_t i, int64_t j, int q_ss, double coef, double* gX) {
+    if (i == j) return; /* identical pair: 0 for every flat triangle */
+    double Yj[9], aj, nj[3], Nj[3];
+    tri_vertices(M, j, Yj);
+    or_tri_geom(Yj, Yj + 3, Yj + 6, &aj, nj);
+    for (int d = 0; d < 3; ++d) Nj[d] = aj * nj[d];
+    double Ssum = 0.0, gN[3] = {0, 0, 0};
+    double gxi[3][3] = {{0}}, gyj[3][3] = {{0}};  /* per listed corner of tau_i / tau_j */
+    int32_t iv[3], jv[3];
+    double ai, scale;
+    double Xi[9];
+    int ns = or_shared_vertices(M, i, j);
+    if (ns == 0) {
+        double ni[3], uv[14], w[7];
+        tri_vertices(M, i, Xi);
+        or_tri_geom(Xi, Xi + 3, Xi + 6, &ai, ni);
+        or_radon7(uv, w);
+        for (int k = 0; k < 3; ++k) {
+            iv[k] = M->tri[3 * i + k];
+            jv[k] = M->tri[3 * j + k];
+        }
+        for (int p = 0; p < 7; ++p)
+            for (int q = 0; q < 7; ++q) {
+                double x[3], y[3], gx[3], gn[3];
+                for (int d = 0; d < 3; ++d) {
+                    x[d] = Xi[d] + uv[2 * p] * (Xi[3 + d] - Xi[d]) + uv[2 * p + 1] * (Xi[6 + d] - Xi[d]);
+                    y[d] = Yj[d] + uv[2 * q] * (Yj[3 + d] - Yj[d]) + uv[2 * q + 1] * (Yj[6 + d] - Yj[d]);
+                }
+                const double wpq = w[p] * w[q];
+                Ssum += wpq * dlp_F(x, y, Nj, gx, gn);
+                const double lx[3] = {1.0 - uv[2 * p] - uv[2 * p + 1], uv[2 * p], uv[2 * p + 1]};
+                const double ly[3] = {1.0 - uv[2 * q] - uv[2 * q + 1], uv[2 * q], uv[2 * q + 1]};
+                for (int k = 0; k < 3; ++k)
+                    for (int d = 0; d < 3; ++d) {
+                        gxi[k][d] += wpq * lx[k] * gx[d];
+                        gyj[k][d] -= wpq * ly[k] * gx[d];
+                    }
+                for (int d = 0; d < 3; ++d) gN[d] += wpq * gn[d];
+            }
+        scale = 1.0;
+    } else {
+        /* canonical orientation: the outer panel P is tau_lo, Q is tau_hi */
+        const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+        double P[9], Q[9];
+        int type;
+        or_orient_pair(M, lo, hi, &type, P, Q);
+        int32_t pv[3], qv[3];
+        for (int k = 0; k < 3; ++k) {
+            pv[k] = qv[k] = -1;
+            for (int a = 0; a < 3; ++a) {
+                const double* va = M->xyz + 3 * (int64_t)M->tri[3 * lo + a];
+                const double* vb = M->xyz + 3 * (int64_t)M->tri[3 * hi + a];
+                if (va[0] == P[3 * k] && va[1] == P[3 * k + 1] && va[2] == P[3 * k + 2]) pv[k] = M->tri[3 * lo + a];
+                if (vb[0] == Q[3 * k] && vb[1] == Q[3 * k + 1] && vb[2] == Q[3 * k + 2]) qv[k] = M->tri[3 * hi + a];
+            }
+        }
+        const int ilo = i == lo;
+        const double* Xl = ilo ? P : Q; /* tau_i in its listed order */
+        for (int k = 0; k < 3; ++k) {
+            iv[k] = ilo ? pv[k] : qv[k];
+            jv[k] = ilo ? qv[k] : pv[k];
+        }
+        memcpy(Xi, Xl, sizeof Xi);
+        double ni[3];
+        or_tri_geom(Xi, Xi + 3, Xi + 6, &ai, ni);
+        double g[64], gw[64];
+        or_gauss_legendre01(q_ss, g, gw);
+        for (int i0 = 0; i0 < q_ss; ++i0)
+            for (int i1 = 0; i1 < q_ss; ++i1)
+                for (int i2 = 0; i2 < q_ss; ++i2)
+                    for (int i3 = 0; i3 < q_ss; ++i3) {
+                        const double wt = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                        double reg[6][5];
+                        const int nr = ss_regions(type, g[i0], g[i1], g[i2], g[i3], reg);
+                        for (int r = 0; r < nr; ++r) {
+                            double pp[3], qq[3], gx[3], gn[3];
+                            chi(P, reg[r][0], reg[r][1], pp);
+                            chi(Q, reg[r][2], reg[r][3], qq);
+                            const double c = wt * reg[r][4];
+                            const double lp[3] = {1.0 - reg[r][0], reg[r][0] - reg[r][1], reg[r][1]};
+                            const double lq[3] = {1.0 - reg[r][2], reg[r][2] - reg[r][3], reg[r][3]};
+                            const double* x = ilo ? pp : qq;
+                            const double* y = ilo ? qq : pp;
+                            const double* lx = ilo ? lp : lq;
+                            const double* ly = ilo ? lq : lp;
+                            Ssum += c * dlp_F(x, y, Nj, gx, gn);
+                            for (int k = 0; k < 3; ++k)
+                                for (int d = 0; d < 3; ++d) {
+                                    gxi[k][d] += c * lx[k] * gx[d];
+                                    gyj[k][d] -= c * ly[k] * gx[d];
+                                }
+                            for (int d = 0; d < 3; ++d) gN[d] += c * gn[d];
+                        }
+                    }
+        scale = 4.0; /* int_tau int_sigma = 4 |tau||sigma| int_T int_T, |sigma| inside N_j */
+    }
+    /* k_ij = scale |tau_i| Ssum */
+    double dAi[9], dN[9];
+    area_grad(Xi, dAi);
+    area_normal_grad(Yj, gN, dN);
+    for (int k = 0; k < 3; ++k) {
+        double vi[3], vj[3], vn[3];
+        for (int d = 0; d < 3; ++d) {
+            vi[d] = scale * (dAi[3 * k + d] * Ssum + ai * gxi[k][d]);
+            vj[d] = scale * ai * gyj[k][d];
+            vn[d] = scale * ai * dN[3 * k + d];
+        }
+        add_vertex(gX, iv[k], vi, coef);
+        add_vertex(gX, jv[k], vj, coef);
+        add_vertex(gX, M->tri[3 * j + k], vn, coef); /* N_j in tau_j's own vertex order */
+    }
+}
+
 /* nodes of cluster c along axis e, centre, floored half-width */
 static void box_ch(const tree_t* T, int64_t c, double* ctr, double* half, int* floored, int* amax) {
     double h[3], hmax = 0.0;
@@ -1509,7 +1687,8 @@ static void box_ch(const tree_t* T, int64_t c, double* ctr, double* half, int* f
 }
 
 int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, double* gX, int parts) {
-    if (H->kernel != OR_SLP) return -1;
+    if (H->kernel != OR_SLP && H->kernel != OR_DLP) return -1;
+    const int dlp = H->kernel == OR_DLP;
     const tree_t* T = &H->T;
     int64_t n = T->n, nc = T->count, nv = H->mesh.nv;
     int k = H->k, m = H->m;
@@ -1524,12 +1703,14 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
                         int64_t i = T->perm[a], j = T->perm[bb];
                         double c = 0.0;
                         for (int r = 0; r < nrhs; ++r) c += w[i + r * n] * x[j + r * n];
-                        entry_grad_slp(&H->mesh, i, j, H->q_ss, c, gX);
+                        if (dlp) entry_grad_dlp(&H->mesh, i, j, H->q_ss, c, gX);
+                        else entry_grad_slp(&H->mesh, i, j, H->q_ss, c, gX);
                     }
             }
     }
     if (!(parts & OR_PART_FAR) || H->far.n == 0) return 0;
-    /* forward quantities: xh = V^T x, wh = V^T w (upward), yh = S xh, zh = S^T wh, then downward */
+    /* forward quantities: xh = W^T x, wh = V^T w (upward), yh = S xh, zh = S^T wh, then downward
+     * (W = V for the single layer) */
     size_t vs = (size_t)nc * k * nrhs;
     double* xh = calloc(vs, sizeof(double));
     double* wh = calloc(vs, sizeof(double));
@@ -1543,7 +1724,7 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
             for (int r = 0; r < nrhs; ++r) {
                 double sx = 0.0, sw = 0.0;
                 for (int64_t a = 0; a < sz; ++a) {
-                    sx += H->V[c][a * k + nu] * x[T->perm[b + a] + r * n];
+                    sx += H->W[c][a * k + nu] * x[T->perm[b + a] + r * n];
                     sw += H->V[c][a * k + nu] * w[T->perm[b + a] + r * n];
                 }
                 xh[(c * k + nu) * nrhs + r] = sx;
@@ -1649,7 +1830,8 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
             }
         }
     }
-    /* leaf bases: L contains sum_i sum_nu V_c[i,nu] (x_i zh_c[nu] + w_i yh_c[nu]) */
+    /* leaf bases: L contains sum_i sum_nu V_c[i,nu] w_i yh_c[nu] + W_c[i,nu] x_i zh_c[nu]
+     * (W = V for the single layer) */
     double ruv[2 * 64 * 64], rw[64 * 64];
     int np = or_collapsed_rule(H->qb, ruv, rw);
     for (int64_t c = 0; c < nc; ++c) {
@@ -1660,12 +1842,15 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
         box_ch(T, c, cc, hc, fl, &am);
         for (int64_t a = T->begin[c]; a < T->end[c]; ++a) {
             int64_t i = T->perm[a];
-            double beta[512];
+            double beta[512], betaW[512];
             for (int nu = 0; nu < k; ++nu) {
-                double bsum = 0.0;
-                for (int r = 0; r < nrhs; ++r)
-                    bsum += x[i + r * n] * zh[(c * k + nu) * nrhs + r] + w[i + r * n] * yh[(c * k + nu) * nrhs + r];
-                beta[nu] = bsum;
+                double bv = 0.0, bw = 0.0;
+                for (int r = 0; r < nrhs; ++r) {
+                    bv += w[i + r * n] * yh[(c * k + nu) * nrhs + r];
+                    bw += x[i + r * n] * zh[(c * k + nu) * nrhs + r];
+                }
+                beta[nu] = dlp ? bv : bv + bw;
+                betaW[nu] = dlp ? bw : 0.0;
             }
             double X[9], area, nrm[3], dA[9];
             tri_vertices(&H->mesh, i, X);
@@ -1695,6 +1880,42 @@ int or_h2_grad(const or_h2* H, const double* w, const double* x, int nrhs, doubl
             for (int kk = 0; kk < 3; ++kk) {
                 double v[3];
                 for (int d = 0; d < 3; ++d) v[d] = dA[3 * kk + d] * Psum + area * gv[kk][d];
+                add_vertex(gX, H->tri[3 * i + kk], v, 1.0);
+            }
+            if (!dlp) continue;
+            /* double layer: sum_nu betaW[nu] W_c[i,nu] = sum_p rw_p N . grad Pw(y_p), with
+             * Pw = sum_nu betaW[nu] L_nu and N = area n (the rule's weights sum to 1) */
+            double N[3], G[3] = {0, 0, 0}, gw2[3][3] = {{0}};
+            for (int d = 0; d < 3; ++d) N[d] = area * nrm[d];
+            for (int pp = 0; pp < np; ++pp) {
+                double y[3];
+                for (int d = 0; d < 3; ++d)
+                    y[d] = X[d] + ruv[2 * pp] * (X[3 + d] - X[d]) + ruv[2 * pp + 1] * (X[6 + d] - X[d]);
+                double gP[3] = {0, 0, 0}, HN[3] = {0, 0, 0};
+                for (int nu = 0; nu < k; ++nu) {
+                    double gl[3], hl[9];
+                    tensor_lagrange_grad(z, m, nu, y, gl);
+                    tensor_lagrange_hess(z, m, nu, y, hl);
+                    for (int d = 0; d < 3; ++d) {
+                        gP[d] += betaW[nu] * gl[d];
+                        HN[d] += betaW[nu] * (hl[3 * d] * N[0] + hl[3 * d + 1] * N[1] + hl[3 * d + 2] * N[2]);
+                    }
+                }
+                const double lam[3] = {1.0 - ruv[2 * pp] - ruv[2 * pp + 1], ruv[2 * pp], ruv[2 * pp + 1]};
+                for (int d = 0; d < 3; ++d) {
+                    G[d] += rw[pp] * gP[d];
+                    for (int kk = 0; kk < 3; ++kk) gw2[kk][d] += rw[pp] * lam[kk] * HN[d];
+                    /* the nodes: d(grad L)/d centre = -Hess L; d(d_e L)/d h_d = -delta_de d_d L / h_d
+                     * - (y_d - c_d) / h_d d_d d_e L */
+                    gc[3 * c + d] -= rw[pp] * HN[d];
+                    gh[3 * c + d] -= rw[pp] * (N[d] * gP[d] + (y[d] - cc[d]) * HN[d]) / hc[d];
+                }
+            }
+            double dN[9];
+            area_normal_grad(X, G, dN);
+            for (int kk = 0; kk < 3; ++kk) {
+                double v[3];
+                for (int d = 0; d < 3; ++d) v[d] = dN[3 * kk + d] + gw2[kk][d];
                 add_vertex(gX, H->tri[3 * i + kk], v, 1.0);
             }
         }
