@@ -622,6 +622,56 @@ def main():
             "rayleigh_Y2": float(u @ wu[0] / uMu), "rayleigh_Y2_exact": 1.2,
             "W1_rel": float(np.abs(wu[1]).max() / np.abs(wu[0]).max())}
 
+    # hybrid cross approximation (section 3) compressed into an H^2-matrix, on the
+    # 131,072-triangle sphere (the host construction grows as n log n times the
+    # blocks per cluster row: ~30 s here): set-up, apply in both tiers, mean rank,
+    # stored bytes, the H^2 error against exact Galerkin rows beside the
+    # Chebyshev bases' on the same rows
+    if not args.no_fp64:
+        mh_ = I.sphere(128)
+        xh_ = torch.from_numpy(I.rhs(mh_.nt, nrhs, seed=13)).to(dev)
+        rows_h = np.random.default_rng(2).choice(mh_.nt, 24, replace=False)
+        dref_h = oracle.dense_rows(0, mh_, rows_h, xh_.cpu().numpy())
+
+        def rows_err(y_t):
+            yy = y_t.cpu().numpy()[:, rows_h]
+            return float(np.linalg.norm(yy - dref_h) / np.linalg.norm(dref_h))
+
+        hca = {"triangles": mh_.nt, "m": 4, "eps_aca": 1e-6, "eps": 1e-6, "rhs": nrhs}
+        y_h = {}
+        for prec in ("mixed_fp32", "fp64"):
+            t_set = time.perf_counter()
+            oh = H.Operator(mh_.vertices, mh_.triangles, kernel="slp", m=4, eta=2.0, precision=prec, hca=True)
+            torch.cuda.synchronize(dev)
+            t_set = time.perf_counter() - t_set
+            yh_ = torch.empty_like(xh_)
+            for _ in range(2):
+                H.h2bem_apply(oh.op, xh_, yh_, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(3):
+                H.h2bem_apply(oh.op, xh_, yh_, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            st_h = oh.stats()
+            oh.close()
+            y_h[prec] = yh_.clone()
+            hca[prec] = {"ms_per_apply": e0.elapsed_time(e1) / 3, "setup_s": round(t_set, 2),
+                         "triangles_rhs_per_s": mh_.nt * nrhs / (e0.elapsed_time(e1) / 3e3),
+                         "mean_rank": st_h["mean_rank"], "far_stored_bytes": st_h["far_stored_bytes"],
+                         "h2_error_vs_dense_rows": rows_err(yh_)}
+        hca["rel_err_mixed_vs_fp64"] = float(torch.linalg.norm(y_h["mixed_fp32"] - y_h["fp64"]) /
+                                             torch.linalg.norm(y_h["fp64"]))
+        oc = H.Operator(mh_.vertices, mh_.triangles, kernel="slp", m=4, eta=2.0, precision="fp64")
+        yc_ = torch.empty_like(xh_)
+        H.h2bem_apply(oc.op, xh_, yc_, stream)
+        torch.cuda.synchronize(dev)
+        oc.close()
+        hca["chebyshev_m4_h2_error_vs_dense_rows"] = rows_err(yc_)
+        extra["hca_sphere131k"] = hca
+        del y_h
+
     # double layer with piecewise-linear trial functions K1 (section 1, eq. (dlp) with
     # the hat functions) on the same sphere: forward (vertices -> triangles) and
     # transposed applies; its nearfield and Sauter-Schwab pairs are FP64 in every tier

@@ -304,21 +304,24 @@ int h2bem_apply(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y,
 /* y = A^T x, same conventions (transposed blocks, V and W exchanged). */
 int h2bem_apply_transpose(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy,
                           void* stream);
-/* Shape gradient of the single layer (section 1, eq. (slp), in its H^2 form of
- * section 2, eq. (vsw)): dxyz[3 v + d] = d/dX_{v,d} sum_r <w_r, G(X) x_r>,
- * the derivative with respect to vertex coordinate d of vertex v with the
- * cluster tree and the block lists held fixed.  It runs through the
- * nearfield quadrature (7-point rule and Sauter-Schwab, areas included), the
- * leaf bases, the transfer and coupling matrices and, through the Chebyshev
- * nodes, the cluster boxes (centre and floored half-width, section 3) down to
- * the vertices realising the box extremes.  FP64 in every precision tier.
+/* Shape gradient of the single or double layer (section 1, eq. (slp) /
+ * eq. (dlp), in their H^2 form of section 2, eq. (vsw)): dxyz[3 v + d] =
+ * d/dX_{v,d} sum_r <w_r, A(X) x_r>, A = G or K, the derivative with respect
+ * to vertex coordinate d of vertex v with the cluster tree and the block
+ * lists held fixed.  It runs through the nearfield quadrature (7-point rule
+ * and Sauter-Schwab, areas included; for K also the source triangles' normals
+ * through their area-normals), the leaf bases (for K the column basis
+ * W = int n . grad L through the Hessian of the Lagrange polynomials), the
+ * transfer and coupling matrices and, through the Chebyshev nodes, the
+ * cluster boxes (centre and floored half-width, section 3) down to the
+ * vertices realising the box extremes.  FP64 in every precision tier.
  *   w, x: n x nrhs (leading dimension ld >= n), 1 <= nrhs <= 64;
  *   dxyz: nv x 3 output (overwritten);
- *   dx: optional (NULL to skip) n x nrhs output (ld) = G^T w = d/dx, by
+ *   dx: optional (NULL to skip) n x nrhs output (ld) = A^T w = d/dx, by
  *   h2bem_apply_transpose in the operator's tier.
  * All buffers device memory; asynchronous on `stream`.  Work vectors are
- * allocated on the first call.  Errors: ARG (NULL, double-layer operator,
- * GCA bases, nrhs, ld, host pointers), CUDA, OOM. */
+ * allocated on the first call.  Errors: ARG (NULL, GCA or HCA bases, nrhs,
+ * ld, host pointers), CUDA, OOM. */
 int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz, double* dx,
                void* stream);
 /* y = W x, the hypersingular operator on continuous piecewise-linear

@@ -697,6 +697,9 @@ struct h2bem_op {
     // column-ordered blocks (far_t) with the transposed couplings at g_soff_t
     int hca = 0;
     DevBuf g_soff_t, g_St;
+    // double-layer shape gradient: full Sauter-Schwab tables (edge, vertex)
+    int gd_ready = 0, gd_npts[2] = {0, 0};
+    DevBuf gd_tab[2];
     int tc_wait_test = 0;  // opts.tc_wait_test (tests of the tensor-core timeout path)
     DevBuf g_rank, g_pivoff, g_piv, g_eoff, g_E, g_soff, g_S;
     int64_t gca_bytes = 0;
@@ -2617,8 +2620,8 @@ extern "C" int h2bem_cg_hypersingular(h2bem_op* op, const double* mvec, const do
 extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_t ld, int nrhs, double* dxyz,
                           double* dx, void* stream) {
     if (!op || !w || !x || !dxyz) return fail(H2BEM_ERR_ARG, "grad: NULL argument");
-    if (op->kernel != H2BEM_SLP) return fail(H2BEM_ERR_ARG, "grad: the shape gradient is available for the single layer");
-    if (op->gca) return fail(H2BEM_ERR_ARG, "grad: the shape gradient runs through Chebyshev bases, not GCA bases");
+    if (op->gca) return fail(H2BEM_ERR_ARG, "grad: the shape gradient runs through Chebyshev bases, not GCA or HCA bases");
+    const bool dlp = op->kernel == H2BEM_DLP;
     if (nrhs < 1 || nrhs > 64) return fail(H2BEM_ERR_ARG, "grad: nrhs must be in 1..64");
     if (ld < op->n) return fail(H2BEM_ERR_ARG, "grad: leading dimension must be >= n");
     if (!is_device_ptr(w) || !is_device_ptr(x) || !is_device_ptr(dxyz) || (dx && !is_device_ptr(dx)))
@@ -2636,6 +2639,16 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
             return rc;
         op->g_NR = NRmax;
     }
+    if (dlp && !op->gd_ready) {  // full Sauter-Schwab tables of the edge and vertex pairs
+        int rc;
+        for (int ty = 1; ty <= 2; ++ty) {
+            std::vector<double> tab;
+            ss_full_table(ty, op->q_ss, tab);
+            if ((rc = upload(op->gd_tab[ty - 1], tab))) return rc;
+            op->gd_npts[ty - 1] = (int)(tab.size() / 5);
+        }
+        op->gd_ready = 1;
+    }
     CU(cudaMemsetAsync(dxyz, 0, op->nv * 3 * sizeof(double), s));
     const h2::Geom g = op->geom();
     const h2::Tree t = op->tree();
@@ -2649,7 +2662,8 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
         h2::launch_permute_in(w + c0 * ld, ld, nr, NR, op->perm.as<int>(), n, wp, s);
         if (op->nfar > 0) {
             const size_t hv = (size_t)nc * k * NR * sizeof(double);
-            h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
+            // x-hat = W^T x (W = V for the single layer), w-hat = V^T w
+            h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), dlp,
                                     false, true, NR, xp, xh, s);
             h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), false,
                                     false, true, NR, wp, wh, s);
@@ -2673,8 +2687,21 @@ extern "C" int h2bem_grad(h2bem_op* op, const double* w, const double* x, int64_
             h2::launch_grad_transfer(t, c, op->nchildren, op->children.as<int>(), op->parent.as<int>(), NR, xh, wh, yh,
                                      zh, dbox, s);
             h2::launch_grad_leaf(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), NR, xp,
-                                 wp, yh, zh, dbox, dxyz, s);
+                                 wp, yh, dlp ? nullptr : zh, dbox, dxyz, s);
+            if (dlp)
+                h2::launch_grad_leaf_w(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(), NR,
+                                       xp, zh, dbox, dxyz, s);
             h2::launch_grad_box(nc, op->cext.as<int>(), op->cflag.as<int>(), dbox, dxyz, s);
+        }
+        if (dlp) {
+            h2::launch_grad_near_dlp(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+                                     op->near.dcol.as<int>(), NR, xp, wp, dxyz, s);
+            for (int ty = 1; ty <= 2; ++ty)  // identical pairs of the double layer vanish
+                h2::launch_grad_singular_dlp(g, (int)op->sp_count[ty], op->sp_lo[ty].as<int>(), op->sp_hi[ty].as<int>(),
+                                             op->sp_code[ty].as<int>(), op->gd_tab[ty - 1].as<double>(),
+                                             op->gd_npts[ty - 1], NR, xp, wp, dxyz, s);
+            CU(cudaGetLastError());
+            continue;
         }
         h2::launch_grad_near(g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
                              op->near.dcol.as<int>(), NR, xp, wp, dxyz, s);

@@ -289,6 +289,17 @@ void launch_grad_singular(const Geom& g, int type, int npairs, const int* lo, co
                           const double* tab, int npts, int NR, const double* xp, const double* wp, double* dX,
                           cudaStream_t s);
 void launch_grad_box(int nc, const int* cext, const int* cflag, const double* dbox, double* dX, cudaStream_t s);
+// the double layer's terms (k_grad_dlp.cu): column-side leaf basis W (beta =
+// x z-hat), regular nearfield (both sides of every ordered pair), Sauter-Schwab
+// edge / vertex pairs by the full tensor rule (x1, x2, y1, y2, weight x
+// Jacobian per point)
+void launch_grad_leaf_w(const Geom& g, const Tree& t, const Consts& c, const double* rule, int nl, const int* leaves,
+                        int NR, const double* xp, const double* zh, double* dbox, double* dX, cudaStream_t s);
+void launch_grad_near_dlp(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
+                          const int* col, int NR, const double* xp, const double* wp, double* dX, cudaStream_t s);
+void launch_grad_singular_dlp(const Geom& g, int npairs, const int* lo, const int* hi, const int* code,
+                              const double* tab, int npts, int NR, const double* xp, const double* wp, double* dX,
+                              cudaStream_t s);
 
 }  // namespace h2
 

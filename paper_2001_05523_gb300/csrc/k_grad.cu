@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(256) k_grad_transfer(Tree t, Consts c, const i
 
 // ---------------------------------------------------------------------------
 // leaf bases: one CTA per leaf; per triangle, thread nu forms
-// beta_nu = sum_r (x_i zh_c[nu] + w_i yh_c[nu]), thread p the interpolant
+// beta_nu = sum_r (x_i zh_c[nu] + w_i yh_c[nu]) (zh = NULL: the row side
+// w_i yh_c[nu] only, for the double layer), thread p the interpolant
 // P = sum beta_nu L_nu and its gradient at quadrature point p.
 // ---------------------------------------------------------------------------
 template <int NR>
@@ -237,9 +238,10 @@ __global__ void __launch_bounds__(256) k_grad_leaf(Geom g, Tree t, Consts c, con
         for (int nu = threadIdx.x; nu < k; nu += blockDim.x) {
             double s = 0.0;
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                s += xp[(int64_t)i * NR + r] * zh[((int64_t)cl * k + nu) * NR + r] +
-                     wp[(int64_t)i * NR + r] * yh[((int64_t)cl * k + nu) * NR + r];
+            for (int r = 0; r < NR; ++r) {
+                s += wp[(int64_t)i * NR + r] * yh[((int64_t)cl * k + nu) * NR + r];
+                if (zh) s += xp[(int64_t)i * NR + r] * zh[((int64_t)cl * k + nu) * NR + r];
+            }
             beta[nu] = s;
         }
         __syncthreads();

@@ -1,6 +1,7 @@
-"""GPU shape gradient d/dX sum_r <w_r, G x_r> (single layer, FP64, tree and
+"""GPU shape gradient d/dX sum_r <w_r, A x_r> (A = G or K, FP64, tree and
 blocks frozen) against the oracle's hand-derived gradient, which is itself
-pinned by central finite differences (tests/test_oracle_grad.py)."""
+pinned by central finite differences (tests/test_oracle_grad.py), and
+against central differences of the GPU apply."""
 import numpy as np
 import pytest
 
@@ -29,14 +30,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("nrhs", [1, 3])
-def test_shape_gradient_matches_oracle(H, orc, name, nrhs):
+def test_shape_gradient_matches_oracle(H, orc, name, nrhs, kernel):
     import torch
 
     mk, m, leaf = CASES[name]
     mesh = mk()
-    op = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=m, leaf_size=leaf)
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=m, leaf_size=leaf)
     w = I.rhs(mesh.nt, nrhs, seed=31)
     x = I.rhs(mesh.nt, nrhs, seed=32)
     wd, xd = torch.from_numpy(w).cuda(), torch.from_numpy(x).cuda()
@@ -44,24 +46,32 @@ def test_shape_gradient_matches_oracle(H, orc, name, nrhs):
     dx = torch.zeros_like(xd)
     H.h2bem_grad(op.op, wd, xd, g, dx)
     torch.cuda.synchronize()
-    ref = orc.H2(mesh, 0, m=m, leaf=leaf).grad_vertices(w, x)
+    ref = orc.H2(mesh, kernel, m=m, leaf=leaf).grad_vertices(w, x)
     gg = g.cpu().numpy()
-    assert np.abs(gg - ref).max() <= 1e-10 * np.abs(ref).max()
-    refx = orc.H2(mesh, 0, m=m, leaf=leaf).matvec(w, transpose=True)
+    err = np.abs(gg - ref).max() / np.abs(ref).max()
+    print(f"grad kernel {kernel} {name} nrhs {nrhs}: {err:.2e}")
+    # double layer: on the jittered cube's nearly coplanar face pairs the two
+    # orientations' terms (k_ij through the points, k_ji through the normal)
+    # cancel to a small part of their size, so the two codes' summation orders
+    # differ by more (measured 8.9e-11; 4e-13 to 4e-12 on the curved meshes)
+    assert err <= (3e-10 if kernel == 1 else 1e-10)
+    refx = orc.H2(mesh, kernel, m=m, leaf=leaf).matvec(w, transpose=True)
     assert np.linalg.norm(dx.cpu().numpy() - refx) / np.linalg.norm(refx) < 1e-10
     op.close()
 
 
-def test_shape_gradient_rejects_double_layer(H):
+def test_shape_gradient_rejects_stored_cross_approximation_bases(H):
     import torch
 
     mesh = I.sphere(3)
-    op = H.Operator(mesh.vertices, mesh.triangles, kernel=1, m=2)
-    z = torch.zeros((1, mesh.nt), dtype=torch.float64, device="cuda")
-    g = torch.zeros((mesh.nv, 3), dtype=torch.float64, device="cuda")
-    with pytest.raises(H.H2bemError):
-        H.h2bem_grad(op.op, z, z, g)
-    op.close()
+    for kw in ({"gca": True}, {"hca": True}):
+        op = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=2, **kw)
+        z = torch.zeros((1, mesh.nt), dtype=torch.float64, device="cuda")
+        g = torch.zeros((mesh.nv, 3), dtype=torch.float64, device="cuda")
+        with pytest.raises(H.H2bemError) as e:
+            H.h2bem_grad(op.op, z, z, g)
+        assert e.value.code == H.H2BEM_ERR_ARG
+        op.close()
 
 
 def test_autograd_shape_and_batch(H, orc):
@@ -93,8 +103,9 @@ def test_autograd_shape_and_batch(H, orc):
     B.close()
 
 
-def test_shape_gradient_matches_gpu_central_differences(H):
-    """32 sampled vertex coordinates: the gradient of sum_r <w_r, G(X) x_r>
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_shape_gradient_matches_gpu_central_differences(H, kernel):
+    """32 sampled vertex coordinates: the gradient of sum_r <w_r, A(X) x_r>
     against central differences (step 1e-6) of the GPU FP64 apply with the
     cluster tree held fixed (uploaded unchanged; boxes and blocks follow the
     moved vertices, and a coordinate whose move changes the block counts is
@@ -103,7 +114,7 @@ def test_shape_gradient_matches_gpu_central_differences(H):
 
     mesh = I.jitter(I.sphere(6), 0.03, 41)
     m, leaf, h = 3, 8, 1e-6
-    base = H.Operator(mesh.vertices, mesh.triangles, kernel=0, m=m, leaf_size=leaf)
+    base = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=m, leaf_size=leaf)
     tr = H.h2bem_tree_export(base.tree, mesh.nt)
     counts = (base.stats()["nfar"], base.stats()["nnear"])
     w = I.rhs(mesh.nt, 2, seed=51)
@@ -119,7 +130,7 @@ def test_shape_gradient_matches_gpu_central_differences(H):
         ms = H.h2bem_mesh_create(X, mesh.triangles)
         ts = H.h2bem_tree_upload(ms, tr["perm"], tr["begin"], tr["end"], tr["child0"], tr["child1"])
         o = H.h2bem_opts_default()
-        op = H.h2bem_operator_create(ms, ts, 0, m, 2.0, o)
+        op = H.h2bem_operator_create(ms, ts, kernel, m, 2.0, o)
         st = H.h2bem_stats_get(op)
         y = torch.empty_like(xd)
         H.h2bem_apply(op, xd, y)
