@@ -732,9 +732,16 @@ struct h2bem_op {
                         cchild1.as<const int>(), cbox.as<const double>(), czhl.as<const float2>(),
                         cetr.as<const float>()};
     }
+    // a second stream for the farfield passes, which run concurrently with the
+    // nearfield (fork and join events, no timing)
+    cudaStream_t s_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~h2bem_op() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s_far) cudaStreamDestroy(s_far);
         if (gexec) cudaGraphExecDestroy(gexec);
     }
 };
@@ -1665,6 +1672,13 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     if (op->store_near && (rc = build_near_store(op.get(), *tree, iperm, slo, shi))) return rc;
     CU(cudaDeviceSynchronize());
     for (auto& e : op->ev) CU(cudaEventCreate(&e));
+    {
+        int lo = 0, hi = 0;  // the farfield stream at the highest priority: its short
+        CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));  // dependent launches then start promptly
+        CU(cudaStreamCreateWithPriority(&op->s_far, cudaStreamNonBlocking, hi));
+        CU(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
+    }
     *out = op.release();
     return H2BEM_OK;
 }
@@ -2024,6 +2038,27 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
     }
     nl += 1;
     mark(1);
+    // the farfield passes up to the downward pass run on the operator's second
+    // stream, concurrently with the nearfield, which adds to y atomically; the
+    // leaf backward transformation (a plain add into y) follows both.  Timed
+    // and tuning applies stay on one stream, so that stage times mean what
+    // they say.
+    const bool overlap = !timed && !tune_now && !op->store_near && op->nfar > 0 && op->s_far;
+    cudaStream_t fs = s;
+    if (overlap) {
+        CU(cudaEventRecord(op->ev_fork, s));
+        CU(cudaStreamWaitEvent(op->s_far, op->ev_fork, 0));
+        fs = op->s_far;
+    }
+    auto leaf_backward = [&]() {
+        if (op->recompute_basis)
+            h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
+                                     out_dlp, fp32 && !out_dlp, yh64, NR, w.yh, w.yp, s);
+        else
+            h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
+                                            fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p,
+                                            w.yh, w.yp, s);
+    };
     // stored nearfield first (stage times are then mapped by the order of the events)
     const int fo = op->store_near ? 1 : 0;
     op->stage_order = fo;
@@ -2032,24 +2067,24 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         mark(2);
     }
     if (op->nfar > 0) {
-        CU(cudaMemsetAsync(w.yh, 0, (size_t)op->nc * op->k * NR * ysz, s));
+        CU(cudaMemsetAsync(w.yh, 0, (size_t)op->nc * op->k * NR * ysz, fs));
         // the double layer's differentiated basis is evaluated in FP64 in every tier
         if (op->recompute_basis)
             h2::launch_leaf_forward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
-                                    in_dlp, fp32 && !in_dlp, xh64, NR, w.xp, w.xh, s);
+                                    in_dlp, fp32 && !in_dlp, xh64, NR, w.xp, w.xh, fs);
         else
             h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                            fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
-                                           w.xp, w.xh, s);
+                                           w.xp, w.xh, fs);
         nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2 + fo);
         for (int L = (int)op->level_parents.size() - 1; L >= 0; --L) {
             if (op->gca)
                 h2::launch_gca_updown(true, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
                                       op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
-                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.xh, s);
+                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.xh, fs);
             else
-                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, s);
+                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, fs);
         }
         mark(3 + fo);
         if (tune_now && tu.coup.nsl == -1) {
@@ -2075,26 +2110,21 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         launch_cfgs(op, NR, transpose, cfg_near, cfg_coup);
         if (op->gca)
             h2::launch_gca_coupling(fp32, NR, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(),
-                                    op->g_rank.as<int>(), g_soff.as<int64_t>(), g_S.p, (int)op->k, w.xh, w.yh, s);
+                                    op->g_rank.as<int>(), g_soff.as<int64_t>(), g_S.p, (int)op->k, w.xh, w.yh, fs);
         else
-            run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, s);
+            run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, fs);
         mark(4 + fo);
         for (size_t L = 0; L < op->level_parents.size(); ++L) {
             if (op->gca)
                 h2::launch_gca_updown(false, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
                                       op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
-                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.yh, s);
+                                      op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.yh, fs);
             else
-                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, s);
+                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, fs);
         }
         mark(5 + fo);
-        if (op->recompute_basis)
-            h2::launch_leaf_backward(g, t, c, op->basis_rule.as<double>(), (int)op->nleaves, op->leaves.as<int>(),
-                                     out_dlp, fp32 && !out_dlp, yh64, NR, w.yh, w.yp, s);
-        else
-            h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
-                                            fp32 && !out_dlp, yh64, NR, out_dlp ? op->basisW.p : op->basisV.p,
-                                            w.yh, w.yp, s);
+        if (overlap) CU(cudaEventRecord(op->ev_join, fs));
+        else leaf_backward();
     } else {
         for (int i = 2 + fo; i <= 5 + fo; ++i) mark(i);
     }
@@ -2134,6 +2164,10 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
                                 NR, w.xp, w.yp, nullptr, nullptr, s);
     }
     mark(8);
+    if (overlap) {  // join the farfield stream, then its leaf backward transformation
+        CU(cudaStreamWaitEvent(s, op->ev_join, 0));
+        leaf_backward();
+    }
     h2::launch_permute_out(w.yp, NR, nrhs, op->iperm.as<int>(), n, y, ldy, s);
     nl += 1;
     op->launches += nl;
