@@ -864,6 +864,10 @@ void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, c
     int* work = cfg.work;
     const int nb = cfg.nb;
     if (nrows <= 0) return;
+    if (!fp32 && ker == SLP) {  // FP64 tier, single layer: double-float evaluation (k_near_df.cu)
+        launch_near_df(g, t, c, nrows, rows, ptr, col, NR, xp, yp, s);
+        return;
+    }
     switch (NR) {
         case 1: near_sym_nr<1>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
         case 4: near_sym_nr<4>(ker, fp32, nrows, s, g, t, c, rows, ptr, col, transpose, xp, xs, yp, work, nb); break;
