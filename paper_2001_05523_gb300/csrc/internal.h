@@ -185,11 +185,13 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 // a row is t itself).  ker: SLP or DLP; transpose applies K^T (double layer).
 // xs: x in FP32, rows of near_store_nx(true, NR) values (launch_store_x); read
 // by the FP32 single layer, which takes x from it instead of xp.
-// the FP64 tier's single-layer coupling by double-float arithmetic on the
-// FP32 pipe (k_coupling_df.cu), for m = 4, 5 and up to 8 right-hand sides
+// coupling by double-float arithmetic on the FP32 pipe (k_coupling_df.cu):
+// the FP64 tier's single layer and the mixed tiers' double layer (its FP64
+// side), for m = 4, 5 and up to 8 right-hand sides; xh64 / yh64: x-hat /
+// y-hat stored as double (else float)
 bool coupling_df_supported(int m, int NR);
 void launch_coupling_df(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                        int NR, const double* xh, double* yh, cudaStream_t s);
+                        int NR, bool xh64, bool yh64, const void* xh, void* yh, cudaStream_t s);
 // the FP64 tier's single-layer regular nearfield by double-float arithmetic
 // on the FP32 pipe (k_near_df.cu): the operation of launch_near_sym for SLP
 void launch_near_df(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,

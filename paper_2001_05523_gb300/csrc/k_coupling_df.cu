@@ -1,6 +1,7 @@
-// Coupling stage of the FP64 tier's single layer (section 2, eq. (vsw);
-// section 3, S_ts[nu,mu] = g(xi_{t,nu}, xi_{s,mu})) by double-float
-// arithmetic on the FP32 pipe:
+// Coupling stage of the FP64 tier's single layer, and of the double layer's
+// FP64 side in the mixed tiers (section 2, eq. (vsw); section 3,
+// S_ts[nu,mu] = g(xi_{t,nu}, xi_{s,mu})), by double-float arithmetic on the
+// FP32 pipe:
 //   yh_t[nu] = sum_{(t,s) farfield} sum_mu S_ts[nu,mu] xh_s[mu].
 // GB300 issues FP64 at about 1/74 of its FP32 rate, and the FP64 generation
 // and products (about 14 FP64 operations per entry at 8 right-hand sides)
@@ -13,7 +14,9 @@
 // are converted to FP64 once per row cluster.  Work layout as the SIMT
 // kernel's register-blocked variant: thread (row, slice) owns the m target
 // nodes nu = (a, b, c), a = 0..m-1, of one (b, c) row and the mu-rows
-// (jc, jb) of its slice; slices are reduced in shared memory (FP64).
+// (jc, jb) of its slice; slices are reduced in shared memory (FP64).  TX / TY:
+// storage of x-hat / y-hat (double, or float on the side of a mixed-tier
+// double layer that is not FP64).
 #include <algorithm>
 
 #include "internal.h"
@@ -30,10 +33,10 @@ __device__ __forceinline__ void tsum2(float a, float b, float& s, float& e) {
 }
 }  // namespace
 
-template <int NR, int M, int NSL>
+template <typename TX, typename TY, int NR, int M, int NSL>
 __global__ void __launch_bounds__(M * M * NSL) k_coupling_df(Tree t, Consts c, const int* __restrict__ rows,
                                                              const int* __restrict__ ptr, const int* __restrict__ col,
-                                                             const double* __restrict__ xh, double* __restrict__ yh) {
+                                                             const TX* __restrict__ xh, TY* __restrict__ yh) {
     constexpr int K = M * M * M, M2 = M * M, NT = M2 * NSL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* xd = reinterpret_cast<double*>(smem_raw);                    // [K][NR] x-hat of the block; reduction [NSL][K][NR]
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(M * M * NSL) k_coupling_df(Tree t, Consts c, c
             zs[e] = t.box[d * t.nc + s] + t.box[(3 + d) * t.nc + s] * c.cheb[a];
         }
         for (int e = threadIdx.x; e < K * NR; e += NT) {
-            const double v = xh[(int64_t)s * K * NR + e];
+            const double v = (double)xh[(int64_t)s * K * NR + e];
             const float h = (float)v;
             xsh[e] = h;
             xsl[e] = (float)(v - (double)h);
@@ -134,31 +137,40 @@ __global__ void __launch_bounds__(M * M * NSL) k_coupling_df(Tree t, Consts c, c
     for (int e = threadIdx.x; e < K * NR; e += NT) {
         double sum = 0.0;
         for (int q = 0; q < NSL; ++q) sum += xd[(size_t)q * K * NR + e];
-        yh[(int64_t)row * K * NR + e] = sum * kInv4PiC;
+        yh[(int64_t)row * K * NR + e] = (TY)(sum * kInv4PiC);
     }
 }
 
 bool coupling_df_supported(int m, int NR) { return (m == 4 || m == 5) && NR <= 8; }
 
-void launch_coupling_df(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
-                        int NR, const double* xh, double* yh, cudaStream_t s) {
-    if (nrows <= 0) return;
+template <typename TX, typename TY>
+static void coupling_df_go(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                           int NR, const void* xh, void* yh, cudaStream_t s) {
     auto go = [&](auto kern, int M, int nsl) {
         const int K = M * M * M;
-        // x-hat as double and as float pairs; the reduction area [NSL][K][NR] (double) reuses the front
+        // x-hat as float pairs behind the reduction area [NSL][K][NR] (double), which reuses the front
         const size_t smem = std::max((size_t)(8 + 8) * K * NR, (size_t)8 * nsl * K * NR);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<nrows, M * M * nsl, smem, s>>>(t, c, rows, ptr, col, xh, yh);
+        kern<<<nrows, M * M * nsl, smem, s>>>(t, c, rows, ptr, col, (const TX*)xh, (TY*)yh);
     };
     if (c.m == 4) {
-        if (NR == 1) go(k_coupling_df<1, 4, 4>, 4, 4);
-        else if (NR == 4) go(k_coupling_df<4, 4, 4>, 4, 4);
-        else go(k_coupling_df<8, 4, 4>, 4, 4);
+        if (NR == 1) go(k_coupling_df<TX, TY, 1, 4, 4>, 4, 4);
+        else if (NR == 4) go(k_coupling_df<TX, TY, 4, 4, 4>, 4, 4);
+        else go(k_coupling_df<TX, TY, 8, 4, 4>, 4, 4);
     } else {
-        if (NR == 1) go(k_coupling_df<1, 5, 4>, 5, 4);
-        else if (NR == 4) go(k_coupling_df<4, 5, 4>, 5, 4);
-        else go(k_coupling_df<8, 5, 4>, 5, 4);
+        if (NR == 1) go(k_coupling_df<TX, TY, 1, 5, 4>, 5, 4);
+        else if (NR == 4) go(k_coupling_df<TX, TY, 4, 5, 4>, 5, 4);
+        else go(k_coupling_df<TX, TY, 8, 5, 4>, 5, 4);
     }
+}
+
+void launch_coupling_df(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
+                        int NR, bool xh64, bool yh64, const void* xh, void* yh, cudaStream_t s) {
+    if (nrows <= 0) return;
+    if (xh64 && yh64) coupling_df_go<double, double>(t, c, nrows, rows, ptr, col, NR, xh, yh, s);
+    else if (xh64) coupling_df_go<double, float>(t, c, nrows, rows, ptr, col, NR, xh, yh, s);
+    else if (yh64) coupling_df_go<float, double>(t, c, nrows, rows, ptr, col, NR, xh, yh, s);
+    else coupling_df_go<float, float>(t, c, nrows, rows, ptr, col, NR, xh, yh, s);
 }
 
 }  // namespace h2
