@@ -1888,9 +1888,9 @@ static int tc_kind(const h2bem_op* op, bool xh64, bool yh64) {
 static void run_coupling(const h2bem_op* op, const h2::Tree& t, const h2::Consts& c, const Csr& far, bool xh64,
                          bool yh64, int NR, void* xh, void* yh, const h2::LaunchCfg& cfg, cudaStream_t s) {
     const int kind = tc_kind(op, xh64, yh64);
-    // double-float entries and sums on the FP32 pipe: the FP64 tier's single
-    // layer, and the double layer's FP64 side in the mixed tiers
-    const bool df = (op->precision == H2BEM_FP64 && op->kernel == H2BEM_SLP) ||
+    // double-float entries and sums on the FP32 pipe: the FP64 tier, and the
+    // double layer's FP64 side in the mixed tiers
+    const bool df = op->precision == H2BEM_FP64 ||
                     (op->precision != H2BEM_FP64 && op->kernel == H2BEM_DLP && (xh64 || yh64));
     if (df && h2::coupling_df_supported(op->m, NR)) {
         h2::launch_coupling_df(t, c, far.nrows(), far.drows.as<int>(), far.dptr.as<int>(), far.dcol.as<int>(), NR,
