@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--store-near", action="store_true",
                     help="timed operator with the stored nearfield (opts.store_near): entries evaluated at "
                          "set-up, streamed in every apply")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the headline tier and the FP64 tier only (no variants or other workloads)")
     ap.add_argument("--gca", action="store_true",
                     help="timed operator with Green-cross-approximation bases (opts.basis = GCA; q 4, eps 1e-6)")
     ap.add_argument("--autotune", type=int, default=1,
@@ -367,6 +369,7 @@ def main():
                          "stage_ms": [round(v, 3) for v in stage_d], "setup_s": round(setup_d, 2)}
         extra["speedup_mixed_vs_fp64"] = ms_d / ms_m
         extra["rel_err_mixed_vs_fp64"] = err_m
+    if not args.no_fp64 and not args.no_extras:
         # cached singular entries (x-independent): both tiers
         opc, y_c, ms_c, stage_c, _, _ = timed_tier("mixed_fp32", True, args.steps)
         opc.close()
@@ -399,7 +402,7 @@ def main():
         extra["stored_nearfield"] = stored
 
     # tensor-core tiers of the coupling (tcgen05): same workload, error against the FP64 tier
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         tiers = {}
         for prec in ("mixed_tf32", "mixed_bf16"):
             opt, y_t, ms_t, stage_t, _, _ = timed_tier(prec, False, args.steps)
@@ -474,7 +477,7 @@ def main():
         del y_k
 
     # other workloads of the benchmark family (reported beside the headline)
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         # 64 uneven jittered meshes (sphere / ellipsoid / cube, 2k-65k triangles) as one
         # block-diagonal operator: forward SLP apply and gradients in x and the vertices
         fam = I.batch_meshes(64)
@@ -533,7 +536,7 @@ def main():
     # with n); at a fixed m = 4 the Neumann error stops improving past ~32k
     # triangles.  Two spheres one refinement apart at m = 6, eta = 1 show the
     # O(h) rate of the L2 Neumann error.
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         ru = np.array([0.5, 0.5, 0.0])  # edge-midpoint rule (exact for degree 2)
         rv = np.array([0.0, 0.5, 0.5])
         rw = np.array([1 / 3, 1 / 3, 1 / 3])
@@ -598,7 +601,7 @@ def main():
     # apply with nrhs vertex vectors (3 nrhs single-layer columns), the Rayleigh
     # quotient of the interpolated harmonic Y_2 (exact value 6/5 on the unit sphere)
     # and W 1 (zero: W annihilates constants)
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         opw = H.Operator(mesh.vertices, mesh.triangles, kernel="slp", m=4, eta=2.0, leaf_size=32,
                          precision=args.tier, autotune=args.autotune)
         nv = mesh.vertices.shape[0]
@@ -637,7 +640,7 @@ def main():
     # blocks per cluster row: ~30 s here): set-up, apply in both tiers, mean rank,
     # stored bytes, the H^2 error against exact Galerkin rows beside the
     # Chebyshev bases' on the same rows
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         mh_ = I.sphere(128)
         xh_ = torch.from_numpy(I.rhs(mh_.nt, nrhs, seed=13)).to(dev)
         rows_h = np.random.default_rng(2).choice(mh_.nt, 24, replace=False)
@@ -685,7 +688,7 @@ def main():
     # double layer with piecewise-linear trial functions K1 (section 1, eq. (dlp) with
     # the hat functions) on the same sphere: forward (vertices -> triangles) and
     # transposed applies; its nearfield and Sauter-Schwab pairs are FP64 in every tier
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         op1 = H.Operator(mesh.vertices, mesh.triangles, kernel="dlp", m=4, eta=2.0, leaf_size=32,
                          precision=args.tier, autotune=args.autotune)
         nv = mesh.vertices.shape[0]
@@ -711,7 +714,7 @@ def main():
     # values x (m the P1 mass row sums, fixing the constant), by the library's
     # conjugate gradients, mixed tier, for the same test functions; the L2 error
     # of x against u at the vertices, two spheres one refinement apart
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_extras:
         def ntd_case(s_ntd, m_ntd, eta_ntd, rtol):
             import scipy.sparse as sps
 
