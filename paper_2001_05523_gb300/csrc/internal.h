@@ -192,10 +192,11 @@ void launch_permute_out(const double* yp, int NR, int nrhs, const int* iperm, in
 bool coupling_df_supported(int m, int NR);
 void launch_coupling_df(const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr, const int* col,
                         int NR, bool xh64, bool yh64, const void* xh, void* yh, cudaStream_t s);
-// the FP64 tier's single-layer regular nearfield by double-float arithmetic
-// on the FP32 pipe (k_near_df.cu): the operation of launch_near_sym for SLP
+// the FP64 tier's regular nearfield by double-float arithmetic on the FP32
+// pipe (k_near_df.cu): the operation of launch_near_sym (single or double
+// layer; transpose: K^T for the double layer)
 void launch_near_df(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
-                    const int* col, int NR, const double* xp, double* yp, cudaStream_t s);
+                    const int* col, bool dlp, bool transpose, int NR, const double* xp, double* yp, cudaStream_t s);
 void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows, const int* ptr,
                      const int* col, int ker, bool transpose, bool fp32, int NR, const double* xp, const float* xs,
                      double* yp, const LaunchCfg& cfg, cudaStream_t s);

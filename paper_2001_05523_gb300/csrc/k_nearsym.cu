@@ -864,8 +864,8 @@ void launch_near_sym(const Geom& g, const Tree& t, const Consts& c, int nrows, c
     int* work = cfg.work;
     const int nb = cfg.nb;
     if (nrows <= 0) return;
-    if (!fp32 && ker == SLP) {  // FP64 tier, single layer: double-float evaluation (k_near_df.cu)
-        launch_near_df(g, t, c, nrows, rows, ptr, col, NR, xp, yp, s);
+    if (!fp32) {  // FP64 tier: double-float evaluation (k_near_df.cu)
+        launch_near_df(g, t, c, nrows, rows, ptr, col, ker != SLP, transpose, NR, xp, yp, s);
         return;
     }
     switch (NR) {
