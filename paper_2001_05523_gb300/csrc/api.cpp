@@ -685,7 +685,7 @@ struct h2bem_op {
     // Sauter-Schwab values of the edge / vertex pairs (6 per pair), and corner
     // work vectors x3 / y3 [3][n][NR]
     int p1_ready = 0;
-    DevBuf p1_W1[3], p1_vals[2], p1_tab, p1_x3, p1_y3;
+    DevBuf p1_W1[3], p1_vals[2], p1_tab, p1_x3, p1_y3, p1_off;
     int64_t p1_cap = 0;
     // Green cross approximation (opts.basis = GCA): rank and pivot tree
     // positions per cluster, transfer matrices E_c and coupling matrices S_b
@@ -2449,6 +2449,10 @@ static int p1_setup(h2bem_op* op) {
                                 op->p1_tab.as<double>(), (int)(tab.size() / 5), op->p1_vals[ty - 1].as<double>(), 0);
         CU(cudaDeviceSynchronize());
     }
+    // point offsets from the centroids as float pairs, for the regular nearfield
+    if ((rc = op->p1_off.alloc((size_t)6 * n * 7 * sizeof(float)))) return rc;
+    h2::launch_p1_offsets((int)n, g.qa, g.ctr, op->p1_off.as<float>(), 0);
+    CU(cudaDeviceSynchronize());
     op->p1_ready = 1;
     return H2BEM_OK;
 }
@@ -2499,7 +2503,7 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
                                             yh64, NR, op->basisV.p, op->yh.p, yp, s);
         }
         h2::launch_p1_near(false, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
-                           op->near.dcol.as<int>(), x3, yp, s);
+                           op->near.dcol.as<int>(), op->p1_off.as<float>(), x3, yp, s);
         for (int ty = 1; ty <= 2; ++ty)
             h2::launch_p1_sing_apply(false, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),
                                      op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(),
@@ -2526,7 +2530,7 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
                                                 s);
         }
         h2::launch_p1_near(true, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
-                           op->near.dcol.as<int>(), xp, y3, s);
+                           op->near.dcol.as<int>(), op->p1_off.as<float>(), xp, y3, s);
         for (int ty = 1; ty <= 2; ++ty)
             h2::launch_p1_sing_apply(true, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),
                                      op->sp_hi[ty].as<int>(), op->sp_code[ty].as<int>(),

@@ -157,7 +157,10 @@ void launch_p1_gather(int n, int NR, int nrhs, const int* vid, const double* x, 
 void launch_p1_scatter(int nv, int n, int NR, int nrhs, const int* vptr, const int* inc, const int* iperm,
                        const double* y3, double* y, int64_t ldy, cudaStream_t s);
 void launch_p1_near(bool transpose, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
-                    const int* rows, const int* ptr, const int* col, const double* xin, double* yout, cudaStream_t s);
+                    const int* rows, const int* ptr, const int* col, const float* off, const double* xin,
+                    double* yout, cudaStream_t s);
+// point offsets from the centroid as float pairs ([6][n][7]: hi, then lo) for launch_p1_near
+void launch_p1_offsets(int n, const double* qa, const double* ctr, float* off, cudaStream_t s);
 void launch_p1_sing_eval(const Geom& g, int np, const int* lo, const int* hi, const int* code, const double* tab,
                          int npts, double* vals, cudaStream_t s);
 void launch_p1_sing_apply(bool transpose, int n, int np, int NR, const int* lo, const int* hi, const int* code,

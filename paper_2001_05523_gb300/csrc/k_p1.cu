@@ -7,8 +7,9 @@
 // contributes three values k^c_ij.  Here: the corner gather of x (vertex
 // values at the corners of every triangle, tree order), the vertex sum of
 // the transpose, the regular nearfield (7 x 7-point rule, lambda_c at the
-// source points) and the Sauter-Schwab pairs (the full tensor rule with the
-// source panel's barycentric coordinates as factors), all in FP64.  The
+// source points; double-float arithmetic on the FP32 pipe, see k_p1_near) and
+// the Sauter-Schwab pairs (the full tensor rule with the source panel's
+// barycentric coordinates as factors, FP64).  The
 // farfield uses the per-corner leaf bases W1_c = int n . grad L lambda_c
 // (k_far.cu's stored-basis kernels) and the passes of the double layer.
 #include <algorithm>
@@ -48,25 +49,80 @@ __global__ void k_p1_scatter(int nv, int n, int NR, int nrhs, const int* __restr
     y[v + r * ldy] = acc;
 }
 
+namespace {
+// float-pair arithmetic (Knuth's TwoSum, Dekker's product through the FMA residual)
+__device__ __forceinline__ void p1_tsum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void p1_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+    ph = __fmul_rn(ah, bh);
+    pl = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -ph)));
+}
+__device__ __forceinline__ void p1_acc(float& sh, float& sl, float ph, float pl) {
+    float e;
+    p1_tsum(sh, ph, sh, e);
+    sl = __fadd_rn(sl, __fadd_rn(e, pl));
+}
+}  // namespace
+
+// point offsets from the centroid, y_q - c, as float pairs: off[(d n + i) 7 + q]
+// (hi, d = 0..2) and off[((3 + d) n + i) 7 + q] (lo)
+__global__ void k_p1_offsets(int n, const double* __restrict__ qa, const double* __restrict__ ctr,
+                             float* __restrict__ off) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * (int64_t)n * 7) return;
+    const int64_t di = e / 7;  // d n + i
+    const double v = qa[e] - ctr[di];
+    const float h = (float)v;
+    off[e] = h;
+    off[3 * (int64_t)n * 7 + e] = (float)(v - (double)h);
+}
+
 // Regular pairs of the nearfield blocks (t, s) of row t (CSR rows / ptr / col):
 // forward (TR = false): y_i += sum_c k^c_ij x3_c[j], i in t, j in s;
 // transposed: y3_c[j] += k^c_ij x_i, j in t, i in s.  Thread (a, part): output
 // triangle a of t and the source triangles b = part, part + P, ... of each
 // block; the parts meet in shared memory.  Pairs sharing a vertex are left to
 // the Sauter-Schwab kernels.
+//   k^c_ij = |tau_i||tau_j| / (4 pi) sum_q w_q lambda_c(y_q) sum_p w_p h_p / r_pq^3,
+// h_p = (x_p - c_j) . n_j the height of the target point above the source's
+// plane (y_q lies on it).  Double-float arithmetic on the FP32 pipe: the
+// centroid difference formed in FP64 per pair and split, the point offsets as
+// float pairs (set-up), the heights as float-pair dot products with the split
+// normal, 1/r from the hardware reciprocal square root plus one Newton step,
+// 1/r^3 and the sums as float pairs (about 1e-13 relative per entry).
 template <int NR, bool TR>
-__global__ void __launch_bounds__(kThreadsP1) k_p1_near(Geom g, Tree t, Consts cst, const int* __restrict__ rows,
+__global__ void __launch_bounds__(kThreadsP1) k_p1_near(Geom g, Tree t, Consts c, const int* __restrict__ rows,
                                                         const int* __restrict__ ptr, const int* __restrict__ col,
+                                                        const float* __restrict__ off,
                                                         const double* __restrict__ xin, double* __restrict__ yout) {
     constexpr int NO = TR ? 3 * NR : NR;  // outputs per output triangle
     extern __shared__ __align__(16) double red[];  // [P][R][NO]
+    __shared__ float swh[7], swl[7], slh[21], sll[21];  // w_p; w_q lambda_c(q) at [3 q + c]
     const int tt = rows[blockIdx.x];
     const int tb = t.begin[tt], R = t.end[tt] - tb;
     const int n = g.n;
     const int tid = threadIdx.x;
+    if (tid < 7) {
+        const float h = (float)c.rw[tid];
+        swh[tid] = h;
+        swl[tid] = (float)(c.rw[tid] - (double)h);
+    }
+    if (tid < 21) {
+        const int q = tid / 3, cc = tid % 3;
+        const double lam = cc == 0 ? 1.0 - c.ru[q] - c.rv[q] : cc == 1 ? c.ru[q] : c.rv[q];
+        const double v = c.rw[q] * lam;
+        const float h = (float)v;
+        slh[tid] = h;
+        sll[tid] = (float)(v - (double)h);
+    }
+    __syncthreads();
     const int P = kThreadsP1 / R;
     const int a = tid % R, part = tid / R;
     const bool active = part < P;
+    const int64_t n7 = (int64_t)n * 7, lo7 = 3 * n7;
     double acc[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) acc[o] = 0.0;
@@ -82,41 +138,102 @@ __global__ void __launch_bounds__(kThreadsP1) k_p1_near(Geom g, Tree t, Consts c
                     for (int w = 0; w < 3; ++w) sing |= g.vid[u * n + ia] == g.vid[w * n + jb];
                 if (sing) continue;
                 const int it = TR ? jb : ia, js = TR ? ia : jb;  // target i, source j of k^c_ij
-                const double nj0 = g.nrm[js], nj1 = g.nrm[n + js], nj2 = g.nrm[2 * n + js];
-                double sc[3] = {0.0, 0.0, 0.0};
+                float Dh[3], Dl[3], nh[3], nl[3];
 #pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const double Dd = g.ctr[d * n + it] - g.ctr[d * n + js];
+                    Dh[d] = (float)Dd;
+                    Dl[d] = (float)(Dd - (double)Dh[d]);
+                    nh[d] = g.nef[d * n + js];
+                    nl[d] = g.nef[(3 + d) * n + js];
+                }
+                // target offsets a_p and the weighted heights w_p h_p, h_p = (a_p + D) . n_j
+                float aph[7][3], apl[7][3], whh[7], whl[7];
+#pragma unroll
+                for (int p = 0; p < 7; ++p) {
+                    float vh[3], vl[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        aph[p][d] = off[(d * (int64_t)n + it) * 7 + p];
+                        apl[p][d] = off[lo7 + (d * (int64_t)n + it) * 7 + p];
+                        float e;
+                        p1_tsum(aph[p][d], Dh[d], vh[d], e);
+                        vl[d] = __fadd_rn(__fadd_rn(apl[p][d], Dl[d]), e);
+                    }
+                    float p0, q0, p1, q1, p2, q2, s1, e1, e2;
+                    p1_mul(vh[0], vl[0], nh[0], nl[0], p0, q0);
+                    p1_mul(vh[1], vl[1], nh[1], nl[1], p1, q1);
+                    p1_mul(vh[2], vl[2], nh[2], nl[2], p2, q2);
+                    p1_tsum(p0, p1, s1, e1);
+                    float hh;
+                    p1_tsum(s1, p2, hh, e2);
+                    const float hl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(q0, q1), q2));
+                    p1_mul(swh[p], swl[p], hh, hl, whh[p], whl[p]);
+                }
+                float sch[3] = {0.0f, 0.0f, 0.0f}, scl[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
                 for (int q = 0; q < 7; ++q) {
-                    const double y0 = g.qa[((int64_t)0 * n + js) * 7 + q], y1 = g.qa[((int64_t)1 * n + js) * 7 + q],
-                                 y2 = g.qa[((int64_t)2 * n + js) * 7 + q];
-                    double sp = 0.0;
+                    // Y = D - (y_q - c_j)
+                    float Yh[3], Yl[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        float e;
+                        p1_tsum(Dh[d], -off[(d * (int64_t)n + js) * 7 + q], Yh[d], e);
+                        Yl[d] = __fadd_rn(__fsub_rn(Dl[d], off[lo7 + (d * (int64_t)n + js) * 7 + q]), e);
+                    }
+                    float Ah = 0.0f, Al = 0.0f;
 #pragma unroll
                     for (int p = 0; p < 7; ++p) {
-                        const double dx = g.qa[((int64_t)0 * n + it) * 7 + p] - y0,
-                                     dy = g.qa[((int64_t)1 * n + it) * 7 + p] - y1,
-                                     dz = g.qa[((int64_t)2 * n + it) * 7 + p] - y2;
-                        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                        const double ri = rsqrt_nr(r2);
-                        sp = fma(cst.rw[p] * (dx * nj0 + dy * nj1 + dz * nj2), ri * ri * ri, sp);
+                        float sq[3], sqe[3];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            float dh, e;
+                            p1_tsum(aph[p][d], Yh[d], dh, e);
+                            const float dl = __fadd_rn(__fadd_rn(apl[p][d], Yl[d]), e);
+                            sq[d] = __fmul_rn(dh, dh);
+                            sqe[d] = __fmaf_rn(2.0f * dh, dl, __fmaf_rn(dh, dh, -sq[d]));
+                        }
+                        float s1, e1, Rh, e2;
+                        p1_tsum(sq[0], sq[1], s1, e1);
+                        p1_tsum(s1, sq[2], Rh, e2);
+                        const float Rl = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(sqe[0], sqe[1]), sqe[2]));
+                        float y0;
+                        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(Rh));
+                        const float y2 = __fmul_rn(y0, y0);
+                        const float y2e = __fmaf_rn(y0, y0, -y2);
+                        const float tq = __fmaf_rn(-Rh, y2, 1.0f);
+                        const float ep = __fsub_rn(tq, __fmaf_rn(Rh, y2e, __fmul_rn(Rl, y2)));
+                        const float yc = __fmul_rn(__fmul_rn(0.5f, y0), ep);  // 1/r = y0 + yc
+                        const float yyl = __fmaf_rn(2.0f * y0, yc, y2e);       // (1/r)^2 = y2 + yyl
+                        float y3h, y3l, th, tl;
+                        p1_mul(y2, yyl, y0, yc, y3h, y3l);
+                        p1_mul(whh[p], whl[p], y3h, y3l, th, tl);
+                        p1_acc(Ah, Al, th, tl);
                     }
-                    const double wq = cst.rw[q] * sp;
-                    sc[0] = fma(wq, 1.0 - cst.ru[q] - cst.rv[q], sc[0]);
-                    sc[1] = fma(wq, cst.ru[q], sc[1]);
-                    sc[2] = fma(wq, cst.rv[q], sc[2]);
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        float th, tl;
+                        p1_mul(slh[3 * q + cc], sll[3 * q + cc], Ah, Al, th, tl);
+                        p1_acc(sch[cc], scl[cc], th, tl);
+                    }
                 }
+                double sc[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) sc[cc] = (double)sch[cc] + (double)scl[cc];
                 const double f = g.area[it] * g.area[js] * kInv4Pi;
                 if constexpr (!TR) {
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         double v = 0.0;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) v = fma(sc[c], xin[((int64_t)c * n + js) * NR + r], v);
+                        for (int cc = 0; cc < 3; ++cc) v = fma(sc[cc], xin[((int64_t)cc * n + js) * NR + r], v);
                         acc[r] = fma(f, v, acc[r]);
                     }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
+                    for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) acc[c * NR + r] = fma(f * sc[c], xin[(int64_t)it * NR + r], acc[c * NR + r]);
+                        for (int r = 0; r < NR; ++r) acc[cc * NR + r] = fma(f * sc[cc], xin[(int64_t)it * NR + r], acc[cc * NR + r]);
                 }
             }
         }
@@ -132,8 +249,8 @@ __global__ void __launch_bounds__(kThreadsP1) k_p1_near(Geom g, Tree t, Consts c
         if constexpr (!TR) {
             yout[(int64_t)(tb + aa) * NR + o] += s;
         } else {
-            const int c = o / NR, r = o % NR;
-            yout[((int64_t)c * n + tb + aa) * NR + r] += s;
+            const int cc = o / NR, r = o % NR;
+            yout[((int64_t)cc * n + tb + aa) * NR + r] += s;
         }
     }
 }
@@ -268,26 +385,33 @@ void launch_p1_scatter(int nv, int n, int NR, int nrhs, const int* vptr, const i
 
 template <int NR>
 static void p1_near_go(bool tr, const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows,
-                       const int* ptr, const int* col, const double* xin, double* yout, cudaStream_t s) {
+                       const int* ptr, const int* col, const float* off, const double* xin, double* yout,
+                       cudaStream_t s) {
     const size_t smem = sizeof(double) * (size_t)kThreadsP1 * (tr ? 3 : 1) * NR;
     if (tr) {
         cudaFuncSetAttribute(k_p1_near<NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_p1_near<NR, true><<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, xin, yout);
+        k_p1_near<NR, true><<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, off, xin, yout);
     } else {
         cudaFuncSetAttribute(k_p1_near<NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_p1_near<NR, false><<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, xin, yout);
+        k_p1_near<NR, false><<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, off, xin, yout);
     }
 }
 
+void launch_p1_offsets(int n, const double* qa, const double* ctr, float* off, cudaStream_t s) {
+    const int64_t tot = 3 * (int64_t)n * 7;
+    if (tot <= 0) return;
+    k_p1_offsets<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, qa, ctr, off);
+}
+
 void launch_p1_near(bool transpose, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
-                    const int* rows, const int* ptr, const int* col, const double* xin, double* yout,
-                    cudaStream_t s) {
+                    const int* rows, const int* ptr, const int* col, const float* off, const double* xin,
+                    double* yout, cudaStream_t s) {
     if (nrows <= 0) return;
     switch (NR) {
-        case 1: p1_near_go<1>(transpose, g, t, c, nrows, rows, ptr, col, xin, yout, s); break;
-        case 4: p1_near_go<4>(transpose, g, t, c, nrows, rows, ptr, col, xin, yout, s); break;
-        case 8: p1_near_go<8>(transpose, g, t, c, nrows, rows, ptr, col, xin, yout, s); break;
-        default: p1_near_go<16>(transpose, g, t, c, nrows, rows, ptr, col, xin, yout, s); break;
+        case 1: p1_near_go<1>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        case 4: p1_near_go<4>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        case 8: p1_near_go<8>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        default: p1_near_go<16>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
     }
 }
 
