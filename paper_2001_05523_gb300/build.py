@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libh2bem.so")
 PEAKS = os.path.join(OUT_DIR, "peaks")  # arithmetic-peak microbenchmark (csrc/peaks.cu)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "gca.cpp", "hca.cpp", "k_gca.cu", "k_misc.cu", "k_nearsym.cu", "k_near_df.cu", "k_sing.cu", "k_far.cu", "k_coupling.cu", "k_coupling_df.cu", "k_coupling_tc.cu", "k_cg.cu", "k_grad.cu", "k_grad_dlp.cu", "k_nearstore.cu", "k_hyper.cu", "k_p1.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "gca.cpp", "hca.cpp", "k_gca.cu", "k_misc.cu", "k_nearsym.cu", "k_near_df.cu", "k_sing.cu", "k_sing_df.cu", "k_far.cu", "k_coupling.cu", "k_coupling_df.cu", "k_coupling_tc.cu", "k_cg.cu", "k_grad.cu", "k_grad_dlp.cu", "k_nearstore.cu", "k_hyper.cu", "k_p1.cu", "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -1612,7 +1612,7 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
         (rc = op->nrm.alloc(3 * n * sizeof(double))) || (rc = op->ctr.alloc(3 * n * sizeof(double))) ||
         (rc = op->vid.alloc(3 * n * sizeof(int))) || (rc = op->qo.alloc(21 * n * sizeof(float))) ||
         (rc = op->qa.alloc(21 * n * sizeof(double))) || (rc = op->chl.alloc(6 * n * sizeof(float))) ||
-        (rc = op->plane.alloc(n * sizeof(double))) || (rc = op->nef.alloc(12 * n * sizeof(float))) ||
+        (rc = op->plane.alloc(n * sizeof(double))) || (rc = op->nef.alloc(18 * n * sizeof(float))) ||
         (rc = op->areaf.alloc(n * sizeof(float))))
         return rc;
     h2::launch_geom(op->xyz.as<double>(), op->tri.as<int>(), op->perm.as<int>(), (int)n, op->consts, op->v.as<double>(),

@@ -30,8 +30,9 @@ struct Geom {
     const double* qa;    // [3][n][7] FP64 points y_q
     const float* chl;    // [6][n] centroid split: hi = fl(c) (rows 0..2), lo = fl(c - hi) (rows 3..5)
     const double* plane; // [n] c . n (offset of the triangle's plane)
-    const float* nef;    // [12][n] FP32: normal hi (0..2) and lo = fl(n - hi) (3..5), edges E1 = b - a (6..8),
-                         // E2 = c - a (9..11), each rounded from FP64
+    const float* nef;    // [18][n] FP32: normal hi (0..2) and lo = fl(n - hi) (3..5), edges E1 = b - a (6..8),
+                         // E2 = c - a (9..11), each rounded from FP64, and their low parts fl(E - hi)
+                         // (12..14, 15..17)
     const float* areaf;  // [n] area rounded to FP32
 };
 
@@ -242,6 +243,10 @@ void launch_sing_scatter(bool f32, int np, const int64_t* pos0, const int64_t* p
 void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
                      const double* tab, int npts, int mode, bool fp32, bool transpose, int NR, const double* xp,
                      double* yp, double* val0, double* val1, cudaStream_t s);
+// FP64-class evaluation of modes 0 and 1 (double-float arithmetic, k_sing_df.cu)
+void launch_singular_df(const Geom& g, int type, int ker, int npairs, const int* lo, const int* hi, const int* code,
+                        const double* tab, int npts, int mode, bool transpose, int NR, const double* xp, double* yp,
+                        double* val0, double* val1, cudaStream_t s);
 // mode 3 of launch_singular (FP32 evaluation only): the pair's entries
 // a_{lo,hi}, a_{hi,lo} (swapped if transpose) as floats at the places
 // ((int2*)val1)[pid] = (position in row lo, position in row hi or -1) of

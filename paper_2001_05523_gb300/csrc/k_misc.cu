@@ -40,7 +40,8 @@ __global__ void k_permute_out(const double* __restrict__ yp, int NR, int nrhs, c
 // counter-clockwise seen from outside), the plane offset c . n, and the points
 // y_q = a + u_q (b-a) + v_q (c-a) of the 7-point rule, in FP64 and as FP32
 // offsets from the centroid, with a float split of the centroid; in FP32
-// also the normal as hi + lo, the edge vectors b - a, c - a and the area.
+// also the normal as hi + lo, the edge vectors b - a, c - a (with their low
+// parts fl(e - hi)) and the area.
 __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ tri, const int* __restrict__ perm,
                        int n, Consts c, double* __restrict__ v, double* __restrict__ area, double* __restrict__ nrm,
                        double* __restrict__ ctr, int* __restrict__ vid, float* __restrict__ qo,
@@ -73,8 +74,11 @@ __global__ void k_geom(const double* __restrict__ xyz, const int* __restrict__ t
         const float nh = (float)nd;
         nef[d * n + i] = nh;
         nef[(3 + d) * n + i] = (float)(nd - (double)nh);
-        nef[(6 + d) * n + i] = (float)e1[d];
-        nef[(9 + d) * n + i] = (float)e2[d];
+        const float e1h = (float)e1[d], e2h = (float)e2[d];
+        nef[(6 + d) * n + i] = e1h;
+        nef[(9 + d) * n + i] = e2h;
+        nef[(12 + d) * n + i] = (float)(e1[d] - (double)e1h);
+        nef[(15 + d) * n + i] = (float)(e2[d] - (double)e2h);
         const float h = (float)cd;
         chl[d * n + i] = h;
         chl[(3 + d) * n + i] = (float)(cd - (double)h);

@@ -1,6 +1,8 @@
 // Nearfield blocks, singular pairs (triangles sharing a vertex): Sauter-Schwab
-// quadrature (cited in sections 1 and 5).  k_singular: FP64 throughout (FP64
-// tier, or on request in every tier).  k_singular32 (mixed tiers): every pair
+// quadrature (cited in sections 1 and 5).  FP64-class points (FP64 tier, or
+// on request in every tier): k_singular_df (k_sing_df.cu), double-float
+// arithmetic on the FP32 pipe; k_singular_apply applies stored FP64 entries.
+// k_singular32 (mixed tiers): every pair
 // in FP32 - edge vectors as differences of the triangles' FP32 edge vectors
 // (quantities of size h, no cancellation), Gram entries, quadrature points
 // (hardware reciprocal square root, relative error below 2^-22) and sums; the
@@ -36,7 +38,6 @@
 // Single layer: a = 4 |P||Q| / (4 pi) sum_p W_p / |w_p|; g_ij = g_ji = a.
 // Double layer: V = sum_p W_p w_p / |w_p|^3 (a vector), then
 //   k_{lo,hi} = 4 |P||Q| / (4 pi)  V . n_hi,   k_{hi,lo} = -4 |P||Q| / (4 pi) V . n_lo.
-#include "dmath.cuh"
 #include "internal.h"
 
 namespace h2 {
@@ -45,12 +46,6 @@ namespace {
 constexpr double kInv4Pi = 0.07957747154594766788;
 constexpr int kThreads = 128;
 
-__device__ __forceinline__ void load_corner(const Geom& g, int i, int corner, double* out) {
-    out[0] = g.v[(3 * corner + 0) * g.n + i];
-    out[1] = g.v[(3 * corner + 1) * g.n + i];
-    out[2] = g.v[(3 * corner + 2) * g.n + i];
-}
-__device__ __forceinline__ double dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 }  // namespace
 
 __device__ __forceinline__ float rsqrt_f32(float a) {
@@ -59,209 +54,20 @@ __device__ __forceinline__ float rsqrt_f32(float a) {
     return y;
 }
 
-template <int NR, int TYPE, int KER, int MODE>
-__global__ void __launch_bounds__(kThreads) k_singular(Geom g, int npairs, const int* __restrict__ plo,
-                                                       const int* __restrict__ phi, const int* __restrict__ pcode,
-                                                       const double* __restrict__ tab, int npts, bool transpose,
-                                                       const double* __restrict__ xp, double* __restrict__ yp,
-                                                       double* __restrict__ val0, double* __restrict__ val1) {
-    constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;  // doubles per table point
-    extern __shared__ double stab[];
-    if (MODE != 2) {
-        for (int e = threadIdx.x; e < npts * W; e += blockDim.x) stab[e] = tab[e];
-        __syncthreads();
-    }
+// Stored FP64 entries of the canonical pairs (cache_singular) applied:
+// y_lo += a_{lo,hi} x_hi, y_hi += a_{hi,lo} x_lo (swapped if transpose), by
+// FP64 atomics; a pair with lo = hi adds once.  The FP64 evaluation itself is
+// k_singular_df (k_sing_df.cu).
+template <int NR>
+__global__ void __launch_bounds__(kThreads) k_singular_apply(int npairs, const int* __restrict__ plo,
+                                                             const int* __restrict__ phi, bool transpose,
+                                                             const double* __restrict__ xp, double* __restrict__ yp,
+                                                             const double* __restrict__ val0,
+                                                             const double* __restrict__ val1) {
     const int pid = blockIdx.x * blockDim.x + threadIdx.x;
     if (pid >= npairs) return;
     const int lo = plo[pid], hi = phi[pid];
-    double a01, a10;  // a_{lo,hi}, a_{hi,lo}
-    if (MODE == 2) {
-        a01 = val0[pid];
-        a10 = val1[pid];
-    } else {
-        const int code = pcode[pid];
-        const int rP = code & 3, q0 = (code >> 2) & 3, q1 = (code >> 4) & 3, q2 = (code >> 6) & 3;
-        double P0[3], P1[3], P2[3], Q0[3], Q1[3], Q2[3];
-        load_corner(g, lo, rP, P0);
-        load_corner(g, lo, (rP + 1) % 3, P1);
-        load_corner(g, lo, (rP + 2) % 3, P2);
-        load_corner(g, hi, q0, Q0);
-        load_corner(g, hi, q1, Q1);
-        load_corner(g, hi, q2, Q2);
-        double ea[3], eb[3], ec[3], ed[3];
-        for (int d = 0; d < 3; ++d) {
-            ea[d] = P1[d] - P0[d];
-            eb[d] = P2[d] - P1[d];
-            ec[d] = Q1[d] - Q0[d];
-            ed[d] = Q2[d] - Q1[d];
-        }
-        const double sc = 4.0 * g.area[lo] * g.area[hi] * kInv4Pi;
-        if (TYPE == IDENTICAL) {
-            const double aa = dot(ea, ea), ab = dot(ea, eb), bb = dot(eb, eb);
-            double s = 0.0;
-            for (int p = 0; p < npts; ++p) {
-                const double* T = stab + p * W;
-                const double r2 = T[0] * aa + T[1] * ab + T[2] * bb;
-                s += T[3] * rsqrt_nr(r2);
-            }
-            a01 = a10 = sc * s;
-        } else if (TYPE == EDGE) {
-            // vectors (a, b, d); stab holds (x_k, w_k, w_k / 2, w_k x_k / 2), npts = q.
-            // Region r: w = F(o) + t G(o) with the outer variable o and the inner t;
-            // coefficient triples over (a, b, d):
-            //   R1 (o = e2, t = e3, weight w_t):     F = (o, 0, o - 1),  G = (0, 1, 0)
-            //   R2 (o = e3, t = e2, weight w_t t):   F = (0, 1, 0),      G = (o, 0, o - 1)
-            //   R3:                                  F = (0, 1, 0),      G = (-1, -1, -o)
-            //   R4:                                  F = (0, 0, -1),     G = (-o, 1 - o, 0)
-            //   R5:                                  F = (0, 1, 0),      G = (-o, -o, -1)
-            const double Gm[3][3] = {{dot(ea, ea), dot(ea, eb), dot(ea, ed)},
-                                     {dot(ea, eb), dot(eb, eb), dot(eb, ed)},
-                                     {dot(ea, ed), dot(eb, ed), dot(ed, ed)}};
-            const int q = npts;
-            double s = 0.0, sa = 0.0, sb = 0.0, sd = 0.0;
-            for (int reg = 0; reg < 5; ++reg) {
-                for (int oi = 0; oi < q; ++oi) {
-                    const double o = stab[4 * oi], wo = stab[4 * oi + 1];
-                    double F[3], Gv[3];
-                    switch (reg) {
-                        case 0: F[0] = o; F[1] = 0.0; F[2] = o - 1.0; Gv[0] = 0.0; Gv[1] = 1.0; Gv[2] = 0.0; break;
-                        case 1: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = o; Gv[1] = 0.0; Gv[2] = o - 1.0; break;
-                        case 2: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = -1.0; Gv[1] = -1.0; Gv[2] = -o; break;
-                        case 3: F[0] = 0.0; F[1] = 0.0; F[2] = -1.0; Gv[0] = -o; Gv[1] = 1.0 - o; Gv[2] = 0.0; break;
-                        default: F[0] = 0.0; F[1] = 1.0; F[2] = 0.0; Gv[0] = -o; Gv[1] = -o; Gv[2] = -1.0; break;
-                    }
-                    double A = 0.0, B2 = 0.0, Cc = 0.0;
-                    for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v) {
-                            A += F[u] * Gm[u][v] * F[v];
-                            B2 += F[u] * Gm[u][v] * Gv[v];
-                            Cc += Gv[u] * Gm[u][v] * Gv[v];
-                        }
-                    B2 *= 2.0;
-                    double f0 = 0.0, f1 = 0.0;
-                    for (int k = 0; k < q; ++k) {
-                        const double tt = stab[4 * k];
-                        const double r2 = fma(tt, fma(tt, Cc, B2), A);
-                        if (KER == SLP) {
-                            // w_t / 2 (R1) or w_t t / 2 (R2-R5) times y (3 - r2 y^2): one Newton step folded in
-                            const double hw = reg == 0 ? stab[4 * k + 2] : stab[4 * k + 3];
-                            double y;
-                            asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
-                            const double tq = r2 * y;
-                            f0 = fma(hw * y, fma(-tq, y, 3.0), f0);
-                        } else {
-                            const double wt = reg == 0 ? stab[4 * k + 1] : 2.0 * stab[4 * k + 3];
-                            const double ri = rsqrt_nr(r2);
-                            const double f = wt * (ri * ri * ri);
-                            f0 += f;
-                            f1 = fma(f, tt, f1);
-                        }
-                    }
-                    if (KER == SLP) {
-                        s = fma(wo, f0, s);
-                    } else {
-                        // sum f w = f0 F + f1 G over (a, b, d)
-                        sa += wo * (f0 * F[0] + f1 * Gv[0]);
-                        sb += wo * (f0 * F[1] + f1 * Gv[1]);
-                        sd += wo * (f0 * F[2] + f1 * Gv[2]);
-                    }
-                }
-            }
-            if (KER == SLP) {
-                a01 = a10 = sc * s / 6.0;
-            } else {
-                double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sd * ed[d]);
-                double nlo[3], nhi[3];
-                for (int d = 0; d < 3; ++d) {
-                    nlo[d] = g.nrm[d * g.n + lo];
-                    nhi[d] = g.nrm[d * g.n + hi];
-                }
-                a01 = sc * dot(V, nhi);
-                a10 = -sc * dot(V, nlo);
-            }
-        } else {  // VERTEX: vectors (a, b, c, d); stab holds (x_k, w_k, w_k x_k / 2), npts = q
-            const double aa = dot(ea, ea), bb = dot(eb, eb), cc = dot(ec, ec), dd = dot(ed, ed);
-            const double ab = dot(ea, eb), ac = dot(ea, ec), ad = dot(ea, ed), bc = dot(eb, ec), bd = dot(eb, ed),
-                         cd = dot(ec, ed);
-            const int q = npts;
-            double s = 0.0, sa = 0.0, sb = 0.0, sc2 = 0.0, sd = 0.0;
-            for (int reg = 0; reg < 2; ++reg) {
-                // R1: U = a + e1 b, V = c + e3 d;  R2: U = c + e1 d, V = a + e3 b
-                const double uu = reg == 0 ? aa : cc, uv2 = reg == 0 ? ab : cd, vv2 = reg == 0 ? bb : dd;
-                const double pp = reg == 0 ? cc : aa, pq2 = reg == 0 ? cd : ab, qq2 = reg == 0 ? dd : bb;
-                const double b0 = ac, b1 = reg == 0 ? ad : bc, b2 = reg == 0 ? bc : ad;
-                for (int i = 0; i < q; ++i) {
-                    const double e1 = stab[3 * i], w1 = stab[3 * i + 1];
-                    const double A = fma(e1, fma(e1, vv2, 2.0 * uv2), uu);
-                    const double Bi0 = fma(e1, b2, b0), Bi1 = fma(e1, bd, b1);
-                    for (int l = 0; l < q; ++l) {
-                        const double e3 = stab[3 * l], w3 = stab[3 * l + 1];
-                        const double Cc = fma(e3, fma(e3, qq2, 2.0 * pq2), pp);
-                        const double m2B = -2.0 * fma(e3, Bi1, Bi0);
-                        double f0 = 0.0, f1 = 0.0;
-                        for (int k = 0; k < q; ++k) {
-                            const double e2 = stab[3 * k], hw = stab[3 * k + 2];
-                            const double r2 = fma(e2, fma(e2, Cc, m2B), A);
-                            if (KER == SLP) {
-                                // (w e2 / 2) y (3 - r2 y^2): one Newton step for 1/sqrt(r2) folded in
-                                double y;
-                            asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
-                                const double tq = r2 * y;
-                                f0 = fma(hw * y, fma(-tq, y, 3.0), f0);
-                            } else {
-                                const double ri = rsqrt_nr(r2);
-                                const double f = 2.0 * hw * (ri * ri * ri);
-                                f0 += f;
-                                f1 = fma(f, e2, f1);
-                            }
-                        }
-                        const double ww = w1 * w3;
-                        if (KER == SLP) {
-                            s = fma(ww, f0, s);
-                        } else {
-                            f0 *= ww;
-                            f1 *= ww;
-                            if (reg == 0) {  // w = a + e1 b - e2 c - e2 e3 d
-                                sa += f0;
-                                sb = fma(e1, f0, sb);
-                                sc2 -= f1;
-                                sd = fma(-e3, f1, sd);
-                            } else {         // w = e2 a + e2 e3 b - c - e1 d
-                                sa += f1;
-                                sb = fma(e3, f1, sb);
-                                sc2 -= f0;
-                                sd = fma(-e1, f0, sd);
-                            }
-                        }
-                    }
-                }
-            }
-            if (KER == SLP) {
-                a01 = a10 = sc * s / 3.0;
-            } else {
-                double V[3];
-                for (int d = 0; d < 3; ++d) V[d] = 0.5 * (sa * ea[d] + sb * eb[d] + sc2 * ec[d] + sd * ed[d]);
-                double nlo[3], nhi[3];
-                for (int d = 0; d < 3; ++d) {
-                    nlo[d] = g.nrm[d * g.n + lo];
-                    nhi[d] = g.nrm[d * g.n + hi];
-                }
-                a01 = sc * dot(V, nhi);
-                a10 = -sc * dot(V, nlo);
-            }
-        }
-        if (MODE == 1) {
-            val0[pid] = a01;
-            val1[pid] = a10;
-            return;
-        }
-    }
-    if (transpose) {
-        const double tmp = a01;
-        a01 = a10;
-        a10 = tmp;
-    }
+    const double a01 = transpose ? val1[pid] : val0[pid], a10 = transpose ? val0[pid] : val1[pid];
     if (lo == hi) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) atomicAdd(&yp[(int64_t)lo * NR + r], a01 * xp[(int64_t)lo * NR + r]);
@@ -510,56 +316,38 @@ __global__ void __launch_bounds__(kThreads) k_singular32(Geom g, int npairs, con
     }
 }
 
-template <int NR, int TYPE, int KER, bool F32>
-static void sing_mode(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
-                      const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
-                      double* v0, double* v1) {
+template <int NR, int TYPE, int KER>
+static void sing_mode32(int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
+                        const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
+                        double* v0, double* v1) {
     constexpr int W = TYPE == IDENTICAL ? 4 : TYPE == EDGE ? 4 : 3;
-    const size_t smem = mode == 2 ? 0 : (size_t)npts * W * sizeof(double);
+    const size_t smem = (size_t)npts * W * sizeof(double);
     dim3 grid((npairs + kThreads - 1) / kThreads);
-    if (mode == 2) {
-        k_singular<NR, TYPE, KER, 2><<<grid, kThreads, 0, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-        return;
-    }
-    if constexpr (F32) {
-        // the default 5 points per direction unrolled (edge and vertex pairs)
-        const bool q5 = TYPE != IDENTICAL && npts == 5;
-        auto k0 = q5 ? k_singular32<NR, TYPE, KER, 0, 5> : k_singular32<NR, TYPE, KER, 0>;
-        auto k1 = q5 ? k_singular32<NR, TYPE, KER, 1, 5> : k_singular32<NR, TYPE, KER, 1>;
-        auto k3 = q5 ? k_singular32<1, TYPE, KER, 3, 5> : k_singular32<1, TYPE, KER, 3>;
-        auto kern = mode == 0 ? k0 : mode == 1 ? k1 : k3;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    } else {
-        auto k0 = k_singular<NR, TYPE, KER, 0>;
-        auto k1 = k_singular<NR, TYPE, KER, 1>;
-        auto kern = mode == 0 ? k0 : k1;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    }
+    // the default 5 points per direction unrolled (edge and vertex pairs)
+    const bool q5 = TYPE != IDENTICAL && npts == 5;
+    auto k0 = q5 ? k_singular32<NR, TYPE, KER, 0, 5> : k_singular32<NR, TYPE, KER, 0>;
+    auto k1 = q5 ? k_singular32<NR, TYPE, KER, 1, 5> : k_singular32<NR, TYPE, KER, 1>;
+    auto k3 = q5 ? k_singular32<1, TYPE, KER, 3, 5> : k_singular32<1, TYPE, KER, 3>;
+    auto kern = mode == 0 ? k0 : mode == 1 ? k1 : k3;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, kThreads, smem, s>>>(g, npairs, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
 }
 
 template <int NR, int TYPE>
-static void sing_ker(int ker, bool f32, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo,
-                     const int* hi, const int* code, const double* tab, int npts, bool tr, const double* xp,
-                     double* yp, double* v0, double* v1) {
-    // mode 2 only reads cached values
-    if (f32 && mode != 2) {
-        if (ker == SLP) sing_mode<NR, TYPE, SLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-        else sing_mode<NR, TYPE, DLP, true>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    } else {
-        if (ker == SLP) sing_mode<NR, TYPE, SLP, false>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-        else sing_mode<NR, TYPE, DLP, false>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    }
+static void sing_ker32(int ker, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo, const int* hi,
+                       const int* code, const double* tab, int npts, bool tr, const double* xp, double* yp,
+                       double* v0, double* v1) {
+    if (ker == SLP) sing_mode32<NR, TYPE, SLP>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    else sing_mode32<NR, TYPE, DLP>(mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
 }
 
 template <int NR>
-static void sing_type(int type, int ker, bool f32, int mode, int npairs, cudaStream_t s, const Geom& g,
-                      const int* lo, const int* hi, const int* code, const double* tab, int npts, bool tr,
-                      const double* xp, double* yp, double* v0, double* v1) {
-    if (type == IDENTICAL) sing_ker<NR, IDENTICAL>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    else if (type == EDGE) sing_ker<NR, EDGE>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
-    else sing_ker<NR, VERTEX>(ker, f32, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+static void sing_type32(int type, int ker, int mode, int npairs, cudaStream_t s, const Geom& g, const int* lo,
+                        const int* hi, const int* code, const double* tab, int npts, bool tr, const double* xp,
+                        double* yp, double* v0, double* v1) {
+    if (type == IDENTICAL) sing_ker32<NR, IDENTICAL>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    else if (type == EDGE) sing_ker32<NR, EDGE>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
+    else sing_ker32<NR, VERTEX>(ker, mode, npairs, s, g, lo, hi, code, tab, npts, tr, xp, yp, v0, v1);
 }
 
 // Singular entries applied by rows: y_i += sum_e vals[e] x_{other[e]} over the
@@ -605,11 +393,25 @@ void launch_singular(const Geom& g, int type, int ker, int npairs, const int* lo
                      double* yp, double* val0, double* val1, cudaStream_t s) {
     if (npairs <= 0) return;
     if (ker == DLP_T) ker = DLP;  // the transposed double layer swaps the two values
+    if (mode == 2) {
+        const unsigned grid = (unsigned)((npairs + kThreads - 1) / kThreads);
+        switch (NR) {
+            case 1: k_singular_apply<1><<<grid, kThreads, 0, s>>>(npairs, lo, hi, transpose, xp, yp, val0, val1); break;
+            case 4: k_singular_apply<4><<<grid, kThreads, 0, s>>>(npairs, lo, hi, transpose, xp, yp, val0, val1); break;
+            case 8: k_singular_apply<8><<<grid, kThreads, 0, s>>>(npairs, lo, hi, transpose, xp, yp, val0, val1); break;
+            default: k_singular_apply<16><<<grid, kThreads, 0, s>>>(npairs, lo, hi, transpose, xp, yp, val0, val1); break;
+        }
+        return;
+    }
+    if (!fp32) {  // FP64-class points: double-float arithmetic (k_sing_df.cu)
+        launch_singular_df(g, type, ker, npairs, lo, hi, code, tab, npts, mode, transpose, NR, xp, yp, val0, val1, s);
+        return;
+    }
     switch (NR) {
-        case 1: sing_type<1>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        case 4: sing_type<4>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        case 8: sing_type<8>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
-        default: sing_type<16>(type, ker, fp32, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 1: sing_type32<1>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 4: sing_type32<4>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        case 8: sing_type32<8>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
+        default: sing_type32<16>(type, ker, mode, npairs, s, g, lo, hi, code, tab, npts, transpose, xp, yp, val0, val1); break;
     }
 }
 

@@ -132,6 +132,36 @@ def test_singular_orders(H, orc, q):
         close(y, ref, 1e-12)
 
 
+@pytest.mark.parametrize("q", [5, 3])
+@pytest.mark.parametrize("cache", [False, True])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp64_matrix_entry_by_entry(H, orc, kernel, cache, q):
+    """The whole FP64 Galerkin matrix of a jittered 200-triangle sphere (eta = 0:
+    every block nearfield; columns by unit vectors), entry by entry against the
+    oracle's dense matrix (eq. (slp) / eq. (dlp), Sauter-Schwab for the pairs
+    sharing a vertex).  Each entry within 1e-12 of itself (plus 1e-15 of the
+    largest entry, for double-layer entries that vanish on flat pairs): a
+    wrong region, weight or orientation of one singular pair class fails it."""
+    import torch
+
+    mesh = I.jitter(I.sphere(5), 0.02, 11)
+    n = mesh.nt
+    op = H.Operator(mesh.vertices, mesh.triangles, kernel=kernel, m=4, eta=0.0, leaf_size=32, precision="fp64",
+                    cache_singular=cache, q_ss=q)
+    E = np.eye(n)
+    # y[r, i] = sum_j A_ij x[r, j]: unit vectors x, 50 right-hand sides per apply
+    A = np.concatenate([op.apply(torch.from_numpy(E[c:c + 50].copy()).cuda()).cpu().numpy()
+                        for c in range(0, n, 50)]).T
+    op.close()
+    R = orc.dense_matrix(kernel, mesh, q_ss=q)
+    err = np.abs(A - R)
+    bound = 1e-12 * np.abs(R) + 1e-15 * np.abs(R).max()
+    sing = np.array([[orc.shared_vertices(mesh, i, j) > 0 for j in range(n)] for i in range(n)])
+    worst = float((err / (np.abs(R) + 1e-300))[sing & (np.abs(R) > 1e-6 * np.abs(R).max())].max())
+    print(f"max relative error of the singular entries {worst:.2e}")
+    assert (err <= bound).all(), f"{int((err > bound).sum())} entries off; worst {float((err - bound).max()):.2e}"
+
+
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_mixed_fp32_matches_oracle(H, orc, kernel):
     mesh = I.ellipsoid(14)
