@@ -630,6 +630,11 @@ struct h2bem_op {
     DevBuf basisV, basisW;          // stored leaf bases [pos][nu]: V (FP32 in the mixed tier), W (double layer, FP64)
     std::vector<std::vector<int>> level_parents;  // non-leaf clusters per level
     std::vector<DevBuf> dlevel;
+    // one launch each way for the top levels of the transfers (levels <
+    // tree_L0, each with at most kTreeTopParents parents): the clusters of level
+    // tree_L0 and the leaves above it, per-cluster arrival counts (upward)
+    int tree_L0 = 0, tree_nstart = 0;
+    DevBuf tree_start, tree_cnt;
     Csr far, far_t, near, near_u;  // near_u: the blocks (t, s) of near with s >= t
     // singular pairs by type (index 0: identical, 1: edge, 2: vertex)
     DevBuf sp_lo[3], sp_hi[3], sp_code[3], sp_tab[3], sp_v0[3], sp_v1[3], sp_gtab, sp_gtab_edge;
@@ -1494,6 +1499,23 @@ static int create_impl(const h2bem_mesh* mesh, const h2bem_tree* tree, const Blo
     for (size_t L = 0; L < op->level_parents.size(); ++L)
         if ((rc = upload(op->dlevel[L], op->level_parents[L]))) return rc;
     {
+        // the top levels: up to the first level with more than kTreeTopParents
+        // parents, at most kTreeTopLevels (the downward walk holds the path)
+        constexpr size_t kTreeTopParents = 1024;
+        constexpr int kTreeTopLevels = 32;
+        int L0 = 0;
+        while (L0 < (int)op->level_parents.size() && L0 < kTreeTopLevels &&
+               op->level_parents[L0].size() <= kTreeTopParents)
+            ++L0;
+        op->tree_L0 = L0;
+        std::vector<int> start;
+        for (int64_t cl = 0; cl < nc; ++cl)
+            if (tree->level[cl] == L0 || (c0[cl] < 0 && tree->level[cl] < L0)) start.push_back((int)cl);
+        op->tree_nstart = (int)start.size();
+        if ((rc = upload(op->tree_start, start)) || (rc = op->tree_cnt.alloc(nc * sizeof(unsigned)))) return rc;
+        CU(cudaMemset(op->tree_cnt.p, 0, nc * sizeof(unsigned)));
+    }
+    {
         // pairs the regular nearfield kernel evaluates: all pairs of the
         // blocks (t, s >= t) that share no vertex, both orders in s = t
         std::vector<int> leaf_of(n);
@@ -1885,6 +1907,39 @@ static int tc_kind(const h2bem_op* op, bool xh64, bool yh64) {
     return -1;
 }
 
+// Upward / downward pass of the Chebyshev bases: the wide levels (tree_L0 and
+// below) one launch per level, the levels above in one launch each way (FP32,
+// m = 4, up to 8 right-hand sides; else per level too).  Returns the launches
+// issued.
+static int64_t run_upward(h2bem_op* op, const h2::Tree& t, const h2::Consts& c, bool xh64, int NR, void* xh,
+                          cudaStream_t s) {
+    const int nlev = (int)op->level_parents.size();
+    int64_t nl = 0;
+    for (int L = nlev - 1; L >= op->tree_L0; --L, ++nl)
+        h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
+    if (op->tree_L0 > 0 && h2::launch_tree_updown(true, t, c, op->tree_nstart, op->tree_start.as<int>(),
+                                                  op->parent.as<int>(), op->tree_cnt.as<unsigned>(), xh64, NR, xh, s))
+        return nl + 1;
+    for (int L = op->tree_L0 - 1; L >= 0; --L, ++nl)
+        h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, xh, s);
+    return nl;
+}
+static int64_t run_downward(h2bem_op* op, const h2::Tree& t, const h2::Consts& c, bool yh64, int NR, void* yh,
+                            cudaStream_t s) {
+    const int nlev = (int)op->level_parents.size();
+    int64_t nl = 0;
+    if (op->tree_L0 > 0 && h2::launch_tree_updown(false, t, c, op->tree_nstart, op->tree_start.as<int>(),
+                                                  op->parent.as<int>(), nullptr, yh64, NR, yh, s)) {
+        nl = 1;
+    } else {
+        for (int L = 0; L < op->tree_L0; ++L, ++nl)
+            h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
+    }
+    for (int L = op->tree_L0; L < nlev; ++L, ++nl)
+        h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, yh, s);
+    return nl;
+}
+
 static void run_coupling(const h2bem_op* op, const h2::Tree& t, const h2::Consts& c, const Csr& far, bool xh64,
                          bool yh64, int NR, void* xh, void* yh, const h2::LaunchCfg& cfg, cudaStream_t s) {
     const int kind = tc_kind(op, xh64, yh64);
@@ -2085,15 +2140,16 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
             h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                            fp32 && !in_dlp, xh64, NR, in_dlp ? op->basisW.p : op->basisV.p,
                                            w.xp, w.xh, fs);
-        nl += 1 + 2 * (int64_t)op->level_parents.size() + (far.nrows() > 0 ? 1 : 0) + 1;
+        nl += 1 + (far.nrows() > 0 ? 1 : 0) + 1;
         mark(2 + fo);
-        for (int L = (int)op->level_parents.size() - 1; L >= 0; --L) {
-            if (op->gca)
+        if (op->gca) {
+            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
                 h2::launch_gca_updown(true, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
                                       op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
                                       op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.xh, fs);
-            else
-                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, w.xh, fs);
+            nl += (int64_t)op->level_parents.size();
+        } else {
+            nl += run_upward(op, t, c, xh64, NR, w.xh, fs);
         }
         mark(3 + fo);
         if (tune_now && tu.coup.nsl == -1) {
@@ -2123,13 +2179,14 @@ static int apply_chunk(h2bem_op* op, const double* x, int64_t ldx, int nrhs, dou
         else
             run_coupling(op, t, c, far, xh64, yh64, NR, w.xh, w.yh, cfg_coup, fs);
         mark(4 + fo);
-        for (size_t L = 0; L < op->level_parents.size(); ++L) {
-            if (op->gca)
+        if (op->gca) {
+            for (size_t L = 0; L < op->level_parents.size(); ++L)
                 h2::launch_gca_updown(false, fp32, NR, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(),
                                       op->cchild0.as<int>(), op->cchild1.as<int>(), op->g_rank.as<int>(),
                                       op->g_eoff.as<int64_t>(), op->g_E.p, (int)op->k, w.yh, fs);
-            else
-                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR, w.yh, fs);
+            nl += (int64_t)op->level_parents.size();
+        } else {
+            nl += run_downward(op, t, c, yh64, NR, w.yh, fs);
         }
         mark(5 + fo);
         if (overlap) CU(cudaEventRecord(op->ev_join, fs));
@@ -2492,13 +2549,9 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
                 h2::launch_leaf_forward_stored_acc(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                                    xh64, NR, op->p1_W1[cc].as<double>(), x3 + (size_t)cc * n * NR,
                                                    op->xh.p, s);
-            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p,
-                                  s);
+            run_upward(op, t, c, xh64, NR, op->xh.p, s);
             run_coupling(op, t, c, op->far, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
-            for (size_t L = 0; L < op->level_parents.size(); ++L)
-                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR,
-                                    op->yh.p, s);
+            run_downward(op, t, c, yh64, NR, op->yh.p, s);
             h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
                                             yh64, NR, op->basisV.p, op->yh.p, yp, s);
         }
@@ -2517,13 +2570,9 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
             CU(cudaMemsetAsync(op->yh.p, 0, (size_t)op->nc * op->k * NR * ysz, s));
             h2::launch_leaf_forward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
                                            xh64, NR, op->basisV.p, xp, op->xh.p, s);
-            for (int L = (int)op->level_parents.size() - 1; L >= 0; --L)
-                h2::launch_upward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), xh64, NR, op->xh.p,
-                                  s);
+            run_upward(op, t, c, xh64, NR, op->xh.p, s);
             run_coupling(op, t, c, op->far_t, xh64, yh64, NR, op->xh.p, op->yh.p, cfg_coup, s);
-            for (size_t L = 0; L < op->level_parents.size(); ++L)
-                h2::launch_downward(t, c, (int)op->level_parents[L].size(), op->dlevel[L].as<int>(), yh64, NR,
-                                    op->yh.p, s);
+            run_downward(op, t, c, yh64, NR, op->yh.p, s);
             for (int cc = 0; cc < 3; ++cc)
                 h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(),
                                                 false, yh64, NR, op->p1_W1[cc].p, op->yh.p, y3 + (size_t)cc * n * NR,

@@ -272,6 +272,14 @@ void launch_leaf_forward_stored(const Tree& t, int k, int max_leaf, int nleaves,
                                 bool xh64, int NR, const void* B, const double* xp, void* xh, cudaStream_t s);
 void launch_leaf_backward_stored(const Tree& t, int k, int max_leaf, int nleaves, const int* leaves, bool basis32,
                                  bool yh64, int NR, const void* B, const void* yh, double* yp, cudaStream_t s);
+// The transfers over the top levels of the tree in one launch (FP32 vectors,
+// m = 4, up to 8 right-hand sides; returns false otherwise: launch per level).
+// start: the clusters of the first per-level launch's level and the leaves
+// above it.  Upward (up = true): their x-hat is complete, the launch forms
+// every ancestor's (cnt: per-cluster arrival counts, zero at set-up).
+// Downward: adds to their y-hat what their ancestors pass down.
+bool launch_tree_updown(bool up, const Tree& t, const Consts& c, int n, const int* start, const int* parent,
+                        unsigned* cnt, bool v64, int NR, void* v, cudaStream_t s);
 void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,
                    cudaStream_t s);
 void launch_downward(const Tree& t, const Consts& c, int nparents, const int* parents, bool yh64, int NR, void* yh,

@@ -13,6 +13,7 @@
 //   leaf backward  y_i      += sum_nu B_t[i,nu] yh_t[nu]
 // with E_{t'}[nu',nu] = L_{t,nu}(xi_{t',nu'}) applied as a Kronecker product of
 // three m x m matrices.  Vectors xh, yh: [cluster][nu][r] with NR columns.
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -440,21 +441,22 @@ __global__ void __launch_bounds__(256) k_downward(Tree t, Consts c, const int* _
 // contraction, ~2 multiply-adds per thread each).  Up: the parent's sums are
 // kept in a fourth warp-private array over both children; down: each child's
 // block is added to its y-hat in place.  Same factors and summation order per
-// element as above.
-template <typename T, int NR, bool UP, int M>
-__global__ void __launch_bounds__(256) k_updown_w(Tree t, Consts c, int np, const int* __restrict__ parents,
-                                                  T* __restrict__ v) {
+// element as above.  CG: read the cluster vectors through L2 (ld.global.cg),
+// for the whole-tree kernels below, where another SM wrote them during the
+// same launch.
+template <typename T>
+__device__ __forceinline__ T ld_v(const T* p, bool cg) {
+    return cg ? __ldcg(p) : *p;
+}
+
+template <typename T, int NR, bool UP, int M, bool CG>
+__device__ __forceinline__ void updown_parent(const Tree& t, const Consts& c, int p, T* __restrict__ v, T* E1,
+                                              int lane) {
     constexpr int K = M * M * M, KN = K * NR, PER = (KN + 31) / 32, F = 3 * M * M;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* E1 = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (2 * F + 4 * KN);
     T* in = E1 + 2 * F;
     T* tmp1 = in + KN;
     T* tmp2 = tmp1 + KN;
     T* out = tmp2 + KN;  // parent's sums (up)
-    const int pi = blockIdx.x * W + warp;
-    if (pi >= np) return;  // no CTA-wide barrier in this kernel
-    const int p = parents[pi];
     const int ch[2] = {t.child0[p], t.child1[p]};
     // E1[q][d][a'][a] = L_{p,a}(z_{ch_q,d}[a']) as in transfer_1d
     for (int e = lane; e < 2 * F; e += 32) {
@@ -473,10 +475,10 @@ __global__ void __launch_bounds__(256) k_updown_w(Tree t, Consts c, int np, cons
         }
     }
     if (!UP)
-        for (int e = lane; e < KN; e += 32) in[e] = v[(int64_t)p * KN + e];
+        for (int e = lane; e < KN; e += 32) in[e] = ld_v(v + (int64_t)p * KN + e, CG);
     for (int q = 0; q < 2; ++q) {
         if (UP)
-            for (int e = lane; e < KN; e += 32) in[e] = v[(int64_t)ch[q] * KN + e];
+            for (int e = lane; e < KN; e += 32) in[e] = ld_v(v + (int64_t)ch[q] * KN + e, CG);
         __syncwarp();
         const T* Ex = E1 + q * F;
         const T* Ey = Ex + M * M;
@@ -516,13 +518,265 @@ __global__ void __launch_bounds__(256) k_updown_w(Tree t, Consts c, int np, cons
                 for (int w = 0; w < M; ++w)
                     sum += (UP ? Ez[w * M + cc] : Ez[cc * M + w]) * tmp2[((w * M * M) + ab) * NR + r];
                 if (UP) out[e] = q == 0 ? sum : out[e] + sum;
-                else v[(int64_t)ch[q] * KN + e] += sum;
+                else v[(int64_t)ch[q] * KN + e] = ld_v(v + (int64_t)ch[q] * KN + e, CG) + sum;
             }
         }
         __syncwarp();  // the next child overwrites in / tmp1 / tmp2
     }
     if (UP)
         for (int e = lane; e < KN; e += 32) v[(int64_t)p * KN + e] = out[e];
+}
+
+template <typename T, int NR, bool UP, int M>
+__global__ void __launch_bounds__(256) k_updown_w(Tree t, Consts c, int np, const int* __restrict__ parents,
+                                                  T* __restrict__ v) {
+    constexpr int KN = M * M * M * NR, F = 3 * M * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* E1 = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (2 * F + 4 * KN);
+    const int pi = blockIdx.x * W + warp;
+    if (pi >= np) return;  // no CTA-wide barrier in this kernel
+    updown_parent<T, NR, UP, M, false>(t, c, parents[pi], v, E1, lane);
+}
+
+// Warp-per-parent transfers for FP32, m = 4, 8 right-hand sides, in
+// registers: lane (c, r) = (lane / 8, lane % 8) holds the 4 x 4 plane
+// v[a + 4 b + 16 c][r] of a cluster vector, so the contractions in x and y
+// are lane-local and the one in z takes the other planes by warp shuffles.
+// The same factors (etr) and per-element summation order as k_updown_w, with
+// no shared memory.  Up: x-hat_p = sum_q E_q x-hat_{ch_q}; down: y-hat_{ch_q}
+// += E_q^T y-hat_p.
+template <bool UP>
+__global__ void __launch_bounds__(256) k_updown_r8(Tree t, int np, const int* __restrict__ parents,
+                                                   float* __restrict__ v) {
+    constexpr int KN = 64 * 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (pi >= np) return;
+    const int p = parents[pi];
+    const int r = lane & 7, cz = lane >> 3;
+    float pv[16];  // up: the parent's sums; down: the parent's y-hat
+    if (UP) {
+#pragma unroll
+        for (int ab = 0; ab < 16; ++ab) pv[ab] = 0.0f;
+    } else {
+#pragma unroll
+        for (int ab = 0; ab < 16; ++ab) pv[ab] = v[(int64_t)p * KN + (cz * 16 + ab) * 8 + r];
+    }
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const int ch = q == 0 ? t.child0[p] : t.child1[p];
+        // E[d][a'][a] = L_{p,a}(z_{ch,d}[a']): the x and y factors (32 values,
+        // the same for every lane) in registers, the lane's z factors below
+        const float* Eg = t.etr + (int64_t)ch * 48;
+        float E[32];
+        const float4* E4 = reinterpret_cast<const float4*>(Eg);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 e = E4[i];
+            E[4 * i] = e.x;
+            E[4 * i + 1] = e.y;
+            E[4 * i + 2] = e.z;
+            E[4 * i + 3] = e.w;
+        }
+        float in[16], t1[16], t2[16];
+        if (UP) {
+#pragma unroll
+            for (int ab = 0; ab < 16; ++ab) in[ab] = v[(int64_t)ch * KN + (cz * 16 + ab) * 8 + r];
+        } else {
+#pragma unroll
+            for (int ab = 0; ab < 16; ++ab) in[ab] = pv[ab];
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)  // contract x
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) sum += (UP ? E[w * 4 + a] : E[a * 4 + w]) * in[w + 4 * b];
+                t1[a + 4 * b] = sum;
+            }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)  // contract y
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) sum += (UP ? E[16 + w * 4 + b] : E[16 + b * 4 + w]) * t1[a + 4 * w];
+                t2[a + 4 * b] = sum;
+            }
+        // contract z: the planes of the other lanes with the same r
+        float zc[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) zc[w] = UP ? Eg[32 + w * 4 + cz] : Eg[32 + cz * 4 + w];
+#pragma unroll
+        for (int ab = 0; ab < 16; ++ab) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) sum += zc[w] * __shfl_sync(0xffffffffu, t2[ab], w * 8 + r);
+            if (UP) pv[ab] = q == 0 ? sum : pv[ab] + sum;
+            else v[(int64_t)ch * KN + (cz * 16 + ab) * 8 + r] += sum;
+        }
+    }
+    if (UP) {
+#pragma unroll
+        for (int ab = 0; ab < 16; ++ab) v[(int64_t)p * KN + (cz * 16 + ab) * 8 + r] = pv[ab];
+    }
+}
+
+// Upward pass over the top of the tree in one launch (section 2, eq.
+// (transfer): x-hat_p = sum over the children c of E_c x-hat_c).  Warp w
+// starts at cluster start[blockIdx.x * W + w], whose x-hat is complete (a
+// leaf's from the leaf transformation, the others' from the per-level
+// launches below), and climbs: it counts its arrival at the parent (cnt[p],
+// atomically; the count
+// keeps running over applies, so arrival a of an apply is the last one when
+// (a + 1) is a multiple of the number of children), and only the warp that
+// arrives last computes x-hat_p, from both children, and climbs on.  Nothing
+// waits: every other warp stops.  The children's vectors are written before a
+// fence that precedes the arrival, and read through L2 after it.
+template <typename T, int NR, int M>
+__global__ void __launch_bounds__(256) k_up_tree(Tree t, Consts c, int nstart, const int* __restrict__ start,
+                                                 const int* __restrict__ parent, unsigned* __restrict__ cnt,
+                                                 T* __restrict__ v) {
+    constexpr int KN = M * M * M * NR, F = 3 * M * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* E1 = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (2 * F + 4 * KN);
+    const int li = blockIdx.x * W + warp;
+    if (li >= nstart) return;  // no CTA-wide barrier in this kernel
+    int node = start[li];
+    for (;;) {
+        const int p = parent[node];
+        if (p < 0) break;
+        __threadfence();  // this warp's x-hat of node (when it computed it) is visible before the arrival
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            const unsigned nch = (t.child0[p] >= 0 ? 1u : 0u) + (t.child1[p] >= 0 ? 1u : 0u);
+            const unsigned a = atomicAdd(&cnt[p], 1u);
+            last = (a + 1u) % nch == 0u;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) break;
+        __threadfence();
+        updown_parent<T, NR, true, M, true>(t, c, p, v, E1, lane);
+        node = p;
+    }
+}
+
+// Downward pass over the top of the tree in one launch (section 2: y-hat_c +=
+// E_c^T y-hat_p, parents before children), without waits: warp w takes
+// cluster v = start[blockIdx.x * W + w] (a cluster of the first per-level
+// launch's level, or a leaf above it) and walks from its root down the path
+// to v, forming in shared memory z_0 = y-hat_root, z_i = y-hat_{a_i} +
+// E_{a_i}^T z_{i-1} for the ancestors a_1 .. a_k of v (their coupling sums,
+// which the coupling wrote, plus what their parents pass down), and adds
+// E_v^T z_k to y-hat_v.  Only y-hat_v is written; the ancestors' sums are
+// formed again by every cluster below them (the top levels hold few clusters:
+// a few transfers more per cluster, no launch per level and no inter-warp
+// dependence).  The factors are those of the per-level kernels.
+constexpr int kMaxDepth = 64;
+
+template <typename T, int NR, int M>
+__device__ __forceinline__ void down_one(const Tree& t, const Consts& c, int p, int ch, T* E1, const T* in, T* tmp1,
+                                         T* tmp2, T* out, int lane) {
+    constexpr int K = M * M * M, KN = K * NR, PER = (KN + 31) / 32, F = 3 * M * M;
+    for (int e = lane; e < F; e += 32) {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            E1[e] = t.etr[(int64_t)ch * F + e];
+        } else {
+            const int d = e / (M * M), ap = (e / M) % M, a = e % M;
+            const double yd = (t.box[d * t.nc + ch] - t.box[d * t.nc + p] + t.box[(3 + d) * t.nc + ch] * c.cheb[ap]) *
+                              t.box[(6 + d) * t.nc + p];
+            double pr = c.bary[a];
+            for (int b = 0; b < M; ++b)
+                if (b != a) pr *= yd - c.cheb[b];
+            E1[e] = (T)pr;
+        }
+    }
+    __syncwarp();
+    const T* Ex = E1;
+    const T* Ey = Ex + M * M;
+    const T* Ez = Ey + M * M;
+#pragma unroll 4
+    for (int j = 0; j < PER; ++j) {  // contract x
+        const int e = lane + 32 * j;
+        if (e < KN) {
+            const int r = e % NR, nu = e / NR, a = nu % M, rest = nu / M;
+            T sum = 0;
+#pragma unroll
+            for (int w = 0; w < M; ++w) sum += Ex[a * M + w] * in[((rest * M) + w) * NR + r];
+            tmp1[e] = sum;
+        }
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int j = 0; j < PER; ++j) {  // contract y
+        const int e = lane + 32 * j;
+        if (e < KN) {
+            const int r = e % NR, nu = e / NR, a = nu % M, b = (nu / M) % M, cc = nu / (M * M);
+            T sum = 0;
+#pragma unroll
+            for (int w = 0; w < M; ++w) sum += Ey[b * M + w] * tmp1[((cc * M + w) * M + a) * NR + r];
+            tmp2[e] = sum;
+        }
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int j = 0; j < PER; ++j) {  // contract z
+        const int e = lane + 32 * j;
+        if (e < KN) {
+            const int r = e % NR, nu = e / NR, ab = nu % (M * M), cc = nu / (M * M);
+            T sum = 0;
+#pragma unroll
+            for (int w = 0; w < M; ++w) sum += Ez[cc * M + w] * tmp2[((w * M * M) + ab) * NR + r];
+            out[e] = sum;
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, int NR, int M>
+__global__ void __launch_bounds__(256) k_down_top(Tree t, Consts c, int nstart, const int* __restrict__ start,
+                                                  const int* __restrict__ parent, T* __restrict__ v) {
+    constexpr int KN = M * M * M * NR, F = 3 * M * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* E1 = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (2 * F + 4 * KN);
+    T* z = E1 + 2 * F;
+    T* tmp1 = z + KN;
+    T* tmp2 = tmp1 + KN;
+    T* out = tmp2 + KN;
+    __shared__ int path[8][kMaxDepth];
+    const int li = blockIdx.x * W + warp;
+    if (li >= nstart || W > 8) return;  // no CTA-wide barrier in this kernel
+    const int node = start[li];
+    // the ancestors of node, root first (path[0]) to the parent (path[k - 1])
+    int k = 0;
+    if (lane == 0) {
+        for (int a = parent[node]; a >= 0 && k < kMaxDepth; a = parent[a]) path[warp][k++] = a;
+        for (int i = 0; i < k / 2; ++i) {
+            const int tmp = path[warp][i];
+            path[warp][i] = path[warp][k - 1 - i];
+            path[warp][k - 1 - i] = tmp;
+        }
+    }
+    k = __shfl_sync(0xffffffffu, k, 0);
+    __syncwarp();
+    if (k == 0) return;  // a root: its sums are final
+    for (int e = lane; e < KN; e += 32) z[e] = v[(int64_t)path[warp][0] * KN + e];
+    __syncwarp();
+    for (int i = 1; i <= k; ++i) {
+        const int p = path[warp][i - 1], ch = i < k ? path[warp][i] : node;
+        down_one<T, NR, M>(t, c, p, ch, E1, z, tmp1, tmp2, out, lane);
+        if (i < k) {
+            for (int e = lane; e < KN; e += 32) z[e] = v[(int64_t)ch * KN + e] + out[e];
+        } else {
+            for (int e = lane; e < KN; e += 32) v[(int64_t)ch * KN + e] += out[e];
+        }
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -705,6 +959,11 @@ static void updown_m(const Tree& t, const Consts& c, int np, const int* parents,
     // least 3 CTAs per SM); larger blocks (FP64, m = 5, 16 right-hand sides)
     // would leave too few warps per SM and keep the CTA per parent
     constexpr size_t per_warp = sizeof(T) * (2 * 3 * MM * MM + 4 * (size_t)MM * MM * MM * NR);
+    if constexpr (std::is_same_v<T, float> && MM == 4 && NR == 8) {
+        constexpr int W = 8;
+        k_updown_r8<UP><<<(np + W - 1) / W, 32 * W, 0, s>>>(t, np, parents, (float*)v);
+        return;
+    }
     if constexpr (MM > 0 && per_warp <= 9 * 1024) {
         constexpr int W = 8;
         auto kern = k_updown_w<T, NR, UP, MM>;
@@ -727,6 +986,44 @@ static void updown(const Tree& t, const Consts& c, int np, const int* parents, v
     if (c.m == 4) updown_m<T, NR, UP, 4>(t, c, np, parents, v, s);
     else if (c.m == 5) updown_m<T, NR, UP, 5>(t, c, np, parents, v, s);
     else updown_m<T, NR, UP, 0>(t, c, np, parents, v, s);
+}
+
+// Top-of-tree transfer launches (k_up_tree, k_down_top) where a warp's
+// arrays are small (as for k_updown_w: 8 warps per CTA within ~72 KB; FP32,
+// m = 4, up to 8 right-hand sides).  Larger blocks keep the per-level launches,
+// whose CTA-per-parent kernels finish one parent sooner, and the top levels
+// are a chain of single parents.
+template <typename T, int NR, int MM>
+constexpr size_t tree_per_warp() {
+    return sizeof(T) * (2 * 3 * MM * MM + 4 * (size_t)MM * MM * MM * NR);
+}
+
+template <typename T, int NR, int MM>
+static void tree_updown(bool up, const Tree& t, const Consts& c, int n, const int* start, const int* parent,
+                        unsigned* cnt, void* v, cudaStream_t s) {
+    constexpr int W = 8;
+    const size_t smem = W * tree_per_warp<T, NR, MM>();
+    if (up) {
+        auto kern = k_up_tree<T, NR, MM>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<(n + W - 1) / W, 32 * W, smem, s>>>(t, c, n, start, parent, cnt, (T*)v);
+    } else {
+        auto kern = k_down_top<T, NR, MM>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<(n + W - 1) / W, 32 * W, smem, s>>>(t, c, n, start, parent, (T*)v);
+    }
+}
+
+bool launch_tree_updown(bool up, const Tree& t, const Consts& c, int n, const int* start, const int* parent,
+                        unsigned* cnt, bool v64, int NR, void* v, cudaStream_t s) {
+    if (c.m != 4 || v64 || NR > 8) return false;
+    if (n <= 0) return true;
+    switch (NR) {
+        case 1: tree_updown<float, 1, 4>(up, t, c, n, start, parent, cnt, v, s); break;
+        case 4: tree_updown<float, 4, 4>(up, t, c, n, start, parent, cnt, v, s); break;
+        default: tree_updown<float, 8, 4>(up, t, c, n, start, parent, cnt, v, s); break;
+    }
+    return true;
 }
 
 void launch_upward(const Tree& t, const Consts& c, int nparents, const int* parents, bool xh64, int NR, void* xh,
