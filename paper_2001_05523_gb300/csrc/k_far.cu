@@ -315,6 +315,108 @@ __global__ void __launch_bounds__(128) k_leaf_bwd_st(Tree t, int k, const int* _
     }
 }
 
+// Register-tiled leaf transformations for an FP32 basis and FP32 cluster
+// vectors, NR a multiple of 4: each thread owns 2 x 4 outputs, so a step of
+// the sum takes one 8-byte basis pair and one 16-byte x (or y-hat) quad from
+// shared memory for 8 multiply-adds (the kernels above load both operands of
+// every multiply-add).  Same products and summation order per output.
+// Forward: thread (vp, g) owns x-hat_s[2 vp + (0, 1)][4 g + (0..3)], threads
+// ceil(k/2) x NR/4 rounded up to a warp.
+template <int NR>
+__global__ void __launch_bounds__(256) k_leaf_fwd_t4(Tree t, int k, const int* __restrict__ leaves,
+                                                     const float* __restrict__ B, const double* __restrict__ xp,
+                                                     float* __restrict__ xh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int s = leaves[blockIdx.x];
+    const int b = t.begin[s], R = t.end[s] - b;
+    float* sB = reinterpret_cast<float*>(smem_raw);                                         // [R][k]
+    float* sx = reinterpret_cast<float*>(smem_raw + (((size_t)R * k * 4 + 15) & ~size_t(15)));  // [R][NR]
+    stage_tile(sB, B + (int64_t)b * k, (size_t)R * k * sizeof(float));
+    const double2* x2 = reinterpret_cast<const double2*>(xp + (int64_t)b * NR);
+    for (int e = threadIdx.x; e < R * NR / 2; e += blockDim.x) {
+        const double2 v = x2[e];
+        sx[2 * e] = (float)v.x;
+        sx[2 * e + 1] = (float)v.y;
+    }
+    __syncthreads();
+    const int KP = (k + 1) / 2;
+    const int vp = threadIdx.x % KP, g = threadIdx.x / KP;
+    if (g >= NR / 4) return;
+    const int nu = 2 * vp;
+    const bool two = nu + 1 < k;
+    float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int j = 0; j < R; ++j) {
+        float b0, b1;
+        if ((k & 1) == 0) {
+            const float2 bb = *reinterpret_cast<const float2*>(sB + j * k + nu);
+            b0 = bb.x;
+            b1 = bb.y;
+        } else {
+            b0 = sB[j * k + nu];
+            b1 = two ? sB[j * k + nu + 1] : 0.0f;
+        }
+        const float4 xv = *reinterpret_cast<const float4*>(sx + j * NR + 4 * g);
+        a0[0] += b0 * xv.x;
+        a0[1] += b0 * xv.y;
+        a0[2] += b0 * xv.z;
+        a0[3] += b0 * xv.w;
+        a1[0] += b1 * xv.x;
+        a1[1] += b1 * xv.y;
+        a1[2] += b1 * xv.z;
+        a1[3] += b1 * xv.w;
+    }
+    float4* o = reinterpret_cast<float4*>(xh + ((int64_t)s * k + nu) * NR + 4 * g);
+    o[0] = make_float4(a0[0], a0[1], a0[2], a0[3]);
+    if (two) o[NR / 4] = make_float4(a1[0], a1[1], a1[2], a1[3]);
+}
+
+// Backward: y_{b+j} += sum_nu B[j][nu] y-hat_s[nu]; thread (j, g) owns row j
+// and right-hand sides 4 g + (0..3) (threads R x NR/4 rounded up to a warp):
+// per step one basis value and one 16-byte y-hat quad for 4 multiply-adds.
+// The basis block is staged transposed, [nu][j], by 16-byte loads of
+// four consecutive nu of a row, so that the threads of a warp (consecutive
+// rows) read consecutive words.
+template <int NR>
+__global__ void __launch_bounds__(256) k_leaf_bwd_t4(Tree t, int k, const int* __restrict__ leaves,
+                                                     const float* __restrict__ B, const float* __restrict__ yh,
+                                                     double* __restrict__ yp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int s = leaves[blockIdx.x];
+    const int b = t.begin[s], R = t.end[s] - b;
+    float* sBt = reinterpret_cast<float*>(smem_raw);                                         // [k][R]
+    float* sy = reinterpret_cast<float*>(smem_raw + (((size_t)k * R * 4 + 15) & ~size_t(15)));  // [k][NR]
+    const float* Bs = B + (int64_t)b * k;
+    if ((k & 3) == 0 && ((reinterpret_cast<uintptr_t>(Bs) & 15) == 0)) {
+        const int k4 = k / 4;
+        for (int e = threadIdx.x; e < R * k4; e += blockDim.x) {
+            const int j = e / k4, nu = 4 * (e - j * k4);
+            const float4 v = reinterpret_cast<const float4*>(Bs)[e];
+            sBt[nu * R + j] = v.x;
+            sBt[(nu + 1) * R + j] = v.y;
+            sBt[(nu + 2) * R + j] = v.z;
+            sBt[(nu + 3) * R + j] = v.w;
+        }
+    } else {
+        for (int e = threadIdx.x; e < R * k; e += blockDim.x) sBt[(e % k) * R + e / k] = Bs[e];
+    }
+    stage_tile(sy, yh + (int64_t)s * k * NR, (size_t)k * NR * sizeof(float));
+    __syncthreads();
+    const int j = threadIdx.x % R, g = threadIdx.x / R;
+    if (g >= NR / 4) return;
+    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int nu = 0; nu < k; ++nu) {
+        const float bv = sBt[nu * R + j];
+        const float4 yv = *reinterpret_cast<const float4*>(sy + nu * NR + 4 * g);
+        a[0] += bv * yv.x;
+        a[1] += bv * yv.y;
+        a[2] += bv * yv.z;
+        a[3] += bv * yv.w;
+    }
+    double* y0 = yp + (int64_t)(b + j) * NR + 4 * g;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) y0[r] += (double)a[r];
+}
+
 // ---------------------------------------------------------------------------
 // Transfers between a parent t and its children (Kronecker form).
 // E1[ch][d][a'][a] = L_{t,a}^{(d)}(z_{ch,d}[a']).
@@ -891,6 +993,26 @@ void launch_leaf_basis(const Geom& g, const Tree& t, const Consts& c, const doub
 template <typename TB, typename TA, int NR>
 static void leaf_st(bool fwd, const Tree& t, int k, int maxR, int nl, const int* leaves, const void* B,
                     const double* xp, void* xh, const void* yh, double* yp, cudaStream_t s) {
+    if constexpr (std::is_same_v<TB, float> && std::is_same_v<TA, float> && NR % 4 == 0) {
+        auto warps = [](int th) { return ((th + 31) / 32) * 32; };
+        if (fwd) {
+            const int th = warps(((k + 1) / 2) * (NR / 4));
+            const size_t smem = (((size_t)maxR * k * 4 + 15) & ~size_t(15)) + (size_t)maxR * NR * 4;
+            if (th <= 256) {
+                cudaFuncSetAttribute(k_leaf_fwd_t4<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_leaf_fwd_t4<NR><<<nl, th, smem, s>>>(t, k, leaves, (const float*)B, xp, (float*)xh);
+                return;
+            }
+        } else {
+            const int th = warps(maxR * (NR / 4));
+            const size_t smem = (((size_t)k * maxR * 4 + 15) & ~size_t(15)) + (size_t)k * NR * 4;
+            if (th <= 256) {
+                cudaFuncSetAttribute(k_leaf_bwd_t4<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_leaf_bwd_t4<NR><<<nl, th, smem, s>>>(t, k, leaves, (const float*)B, (const float*)yh, yp);
+                return;
+            }
+        }
+    }
     if (fwd) {
         const size_t smem = (((size_t)maxR * k * sizeof(TB) + 15) & ~size_t(15)) + (size_t)maxR * NR * sizeof(TA);
         cudaFuncSetAttribute(k_leaf_fwd_st<TB, TA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
