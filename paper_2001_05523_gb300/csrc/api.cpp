@@ -2555,7 +2555,7 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
             h2::launch_leaf_backward_stored(t, (int)op->k, op->max_leaf, (int)op->nleaves, op->leaves.as<int>(), fp32,
                                             yh64, NR, op->basisV.p, op->yh.p, yp, s);
         }
-        h2::launch_p1_near(false, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+        h2::launch_p1_near(false, fp32, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
                            op->near.dcol.as<int>(), op->p1_off.as<float>(), x3, yp, s);
         for (int ty = 1; ty <= 2; ++ty)
             h2::launch_p1_sing_apply(false, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),
@@ -2578,7 +2578,7 @@ static int apply_p1_chunk(h2bem_op* op, double alpha, const double* x, int64_t l
                                                 false, yh64, NR, op->p1_W1[cc].p, op->yh.p, y3 + (size_t)cc * n * NR,
                                                 s);
         }
-        h2::launch_p1_near(true, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
+        h2::launch_p1_near(true, fp32, NR, g, t, c, op->near.nrows(), op->near.drows.as<int>(), op->near.dptr.as<int>(),
                            op->near.dcol.as<int>(), op->p1_off.as<float>(), xp, y3, s);
         for (int ty = 1; ty <= 2; ++ty)
             h2::launch_p1_sing_apply(true, n, (int)op->sp_count[ty], NR, op->sp_lo[ty].as<int>(),

@@ -157,7 +157,8 @@ void launch_p1_gather(int n, int NR, int nrhs, const int* vid, const double* x, 
                       cudaStream_t s);
 void launch_p1_scatter(int nv, int n, int NR, int nrhs, const int* vptr, const int* inc, const int* iperm,
                        const double* y3, double* y, int64_t ldy, cudaStream_t s);
-void launch_p1_near(bool transpose, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
+// fp32: the mixed tiers' FP32 kernel (off unused), else double-float (FP64 tier)
+void launch_p1_near(bool transpose, bool fp32, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
                     const int* rows, const int* ptr, const int* col, const float* off, const double* xin,
                     double* yout, cudaStream_t s);
 // point offsets from the centroid as float pairs ([6][n][7]: hi, then lo) for launch_p1_near

@@ -7,11 +7,12 @@
 // contributes three values k^c_ij.  Here: the corner gather of x (vertex
 // values at the corners of every triangle, tree order), the vertex sum of
 // the transpose, the regular nearfield (7 x 7-point rule, lambda_c at the
-// source points; double-float arithmetic on the FP32 pipe, see k_p1_near) and
-// the Sauter-Schwab pairs (the full tensor rule with the source panel's
-// barycentric coordinates as factors, FP64).  The
-// farfield uses the per-corner leaf bases W1_c = int n . grad L lambda_c
-// (k_far.cu's stored-basis kernels) and the passes of the double layer.
+// source points; double-float arithmetic on the FP32 pipe in the FP64 tier,
+// see k_p1_near; FP32 with cancellation-free heights in the mixed tiers, see
+// k_p1_near32) and the Sauter-Schwab pairs (the full tensor rule with the
+// source panel's barycentric coordinates as factors, FP64).  The farfield
+// uses the per-corner leaf bases W1_c = int n . grad L lambda_c (k_far.cu's
+// stored-basis kernels) and the passes of the double layer.
 #include <algorithm>
 
 #include "dmath.cuh"
@@ -255,6 +256,136 @@ __global__ void __launch_bounds__(kThreadsP1) k_p1_near(Geom g, Tree t, Consts c
     }
 }
 
+// The same regular pairs in FP32 (mixed tiers).  The heights of the target
+// points above the source's plane are O(h^2 kappa) against coordinates O(h),
+// so they are formed without cancellation, as in the P0 double layer's FP32
+// kernel: with delta = n_j - n_i from the split normals and the target point
+// x_p = c_i + (u_p - 1/3) E1_i + (v_p - 1/3) E2_i (E1_i . n_i = E2_i . n_i = 0),
+//   h_p = D . n_j + (u_p - 1/3) E1_i . delta + (v_p - 1/3) E2_i . delta,
+// D = c_i - c_j from the centroids' float splits and D . n_j from Dekker's
+// products and TwoSum (the cancelling part).  Distances from the points'
+// FP32 offsets and D (hi difference exact for nearby centroids), 1/r the
+// hardware reciprocal square root; the sums over p and q and the corner sums
+// in FP32; the scale |tau_i||tau_j| / (4 pi) and the products with x in FP64.
+template <int NR, bool TR>
+__global__ void __launch_bounds__(kThreadsP1) k_p1_near32(Geom g, Tree t, Consts c, const int* __restrict__ rows,
+                                                          const int* __restrict__ ptr, const int* __restrict__ col,
+                                                          const double* __restrict__ xin, double* __restrict__ yout) {
+    constexpr int NO = TR ? 3 * NR : NR;  // outputs per output triangle
+    extern __shared__ __align__(16) double red[];  // [P][R][NO]
+    __shared__ float slw[21];                      // w_q lambda_c(q) at [3 q + c]
+    const int tt = rows[blockIdx.x];
+    const int tb = t.begin[tt], R = t.end[tt] - tb;
+    const int n = g.n;
+    const int tid = threadIdx.x;
+    if (tid < 21) {
+        const int q = tid / 3, cc = tid % 3;
+        const double lam = cc == 0 ? 1.0 - c.ru[q] - c.rv[q] : cc == 1 ? c.ru[q] : c.rv[q];
+        slw[tid] = (float)(c.rw[q] * lam);
+    }
+    __syncthreads();
+    const int P = kThreadsP1 / R;
+    const int a = tid % R, part = tid / R;
+    const bool active = part < P;
+    double acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = 0.0;
+    if (active) {
+        const int ia = tb + a;  // the output triangle (target forward, source transposed)
+        for (int blk = ptr[blockIdx.x]; blk < ptr[blockIdx.x + 1]; ++blk) {
+            const int s = col[blk];
+            for (int jb = t.begin[s] + part; jb < t.end[s]; jb += P) {
+                bool sing = false;
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+#pragma unroll
+                    for (int w = 0; w < 3; ++w) sing |= g.vid[u * n + ia] == g.vid[w * n + jb];
+                if (sing) continue;
+                const int it = TR ? jb : ia, js = TR ? ia : jb;  // target i, source j of k^c_ij
+                float Dh[3], Dl[3], nh[3], dl[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    Dh[d] = g.chl[d * n + it] - g.chl[d * n + js];
+                    Dl[d] = g.chl[(3 + d) * n + it] - g.chl[(3 + d) * n + js];
+                    nh[d] = g.nef[d * n + js];
+                    dl[d] = (nh[d] - g.nef[d * n + it]) + (g.nef[(3 + d) * n + js] - g.nef[(3 + d) * n + it]);
+                }
+                // H0 = D . n_j: exact products and sums of the cancelling hi part
+                const float p0 = __fmul_rn(Dh[0], nh[0]), p1 = __fmul_rn(Dh[1], nh[1]), p2 = __fmul_rn(Dh[2], nh[2]);
+                const float r0 = __fmaf_rn(Dh[0], nh[0], -p0), r1 = __fmaf_rn(Dh[1], nh[1], -p1),
+                            r2 = __fmaf_rn(Dh[2], nh[2], -p2);
+                float s1, t1, s2, t2;
+                p1_tsum(p0, p1, s1, t1);
+                p1_tsum(s1, p2, s2, t2);
+                float cr = (t1 + t2) + (r0 + r1 + r2);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) cr = fmaf(Dh[d], g.nef[(3 + d) * n + js], fmaf(Dl[d], nh[d], cr));
+                const float H0 = s2 + cr;
+                const float e1 = g.nef[6 * n + it] * dl[0] + g.nef[7 * n + it] * dl[1] + g.nef[8 * n + it] * dl[2];
+                const float e2 = g.nef[9 * n + it] * dl[0] + g.nef[10 * n + it] * dl[1] + g.nef[11 * n + it] * dl[2];
+                float ax[7], ay[7], az[7], wh[7];
+#pragma unroll
+                for (int p = 0; p < 7; ++p) {
+                    ax[p] = g.qo[((int64_t)0 * n + it) * 7 + p];
+                    ay[p] = g.qo[((int64_t)1 * n + it) * 7 + p];
+                    az[p] = g.qo[((int64_t)2 * n + it) * 7 + p];
+                    wh[p] = c.rwf[p] * fmaf(c.ruf[p], e1, fmaf(c.rvf[p], e2, H0));
+                }
+                const float Dx = Dh[0] + Dl[0], Dy = Dh[1] + Dl[1], Dz = Dh[2] + Dl[2];
+                float sc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    // Y = D - (y_q - c_j)
+                    const float Yx = Dx - g.qo[((int64_t)0 * n + js) * 7 + q];
+                    const float Yy = Dy - g.qo[((int64_t)1 * n + js) * 7 + q];
+                    const float Yz = Dz - g.qo[((int64_t)2 * n + js) * 7 + q];
+                    float A = 0.0f;
+#pragma unroll
+                    for (int p = 0; p < 7; ++p) {
+                        const float dx = ax[p] + Yx, dy = ay[p] + Yy, dz = az[p] + Yz;
+                        float y;
+                        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaf(dz, dz, fmaf(dy, dy, dx * dx))));
+                        A = fmaf(wh[p], (y * y) * y, A);
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) sc[cc] = fmaf(slw[3 * q + cc], A, sc[cc]);
+                }
+                const double f = g.area[it] * g.area[js] * kInv4Pi;
+                if constexpr (!TR) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        double v = 0.0;
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) v = fma((double)sc[cc], xin[((int64_t)cc * n + js) * NR + r], v);
+                        acc[r] = fma(f, v, acc[r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r)
+                            acc[cc * NR + r] = fma(f * (double)sc[cc], xin[(int64_t)it * NR + r], acc[cc * NR + r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+        if (active) red[((size_t)part * R + a) * NO + o] = acc[o];
+    __syncthreads();
+    for (int e = tid; e < R * NO; e += kThreadsP1) {
+        const int aa = e / NO, o = e % NO;
+        double sum = 0.0;
+        for (int q = 0; q < P; ++q) sum += red[((size_t)q * R + aa) * NO + o];
+        if constexpr (!TR) {
+            yout[(int64_t)(tb + aa) * NR + o] += sum;
+        } else {
+            const int cc = o / NR, r = o % NR;
+            yout[((int64_t)cc * n + tb + aa) * NR + r] += sum;
+        }
+    }
+}
+
 // Sauter-Schwab values of the canonical edge- and vertex-adjacent pairs
 // (lo, hi) with code (rP | q0 << 2 | q1 << 4 | q2 << 6): P = corners rP, rP+1,
 // rP+2 of lo, Q = corners q0, q1, q2 of hi, shared vertices first.  The full
@@ -384,10 +515,16 @@ void launch_p1_scatter(int nv, int n, int NR, int nrhs, const int* vptr, const i
 }
 
 template <int NR>
-static void p1_near_go(bool tr, const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows,
+static void p1_near_go(bool tr, bool fp32, const Geom& g, const Tree& t, const Consts& c, int nrows, const int* rows,
                        const int* ptr, const int* col, const float* off, const double* xin, double* yout,
                        cudaStream_t s) {
     const size_t smem = sizeof(double) * (size_t)kThreadsP1 * (tr ? 3 : 1) * NR;
+    if (fp32) {
+        auto kern = tr ? k_p1_near32<NR, true> : k_p1_near32<NR, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, xin, yout);
+        return;
+    }
     if (tr) {
         cudaFuncSetAttribute(k_p1_near<NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_p1_near<NR, true><<<nrows, kThreadsP1, smem, s>>>(g, t, c, rows, ptr, col, off, xin, yout);
@@ -403,15 +540,15 @@ void launch_p1_offsets(int n, const double* qa, const double* ctr, float* off, c
     k_p1_offsets<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, qa, ctr, off);
 }
 
-void launch_p1_near(bool transpose, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
+void launch_p1_near(bool transpose, bool fp32, int NR, const Geom& g, const Tree& t, const Consts& c, int nrows,
                     const int* rows, const int* ptr, const int* col, const float* off, const double* xin,
                     double* yout, cudaStream_t s) {
     if (nrows <= 0) return;
     switch (NR) {
-        case 1: p1_near_go<1>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
-        case 4: p1_near_go<4>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
-        case 8: p1_near_go<8>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
-        default: p1_near_go<16>(transpose, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        case 1: p1_near_go<1>(transpose, fp32, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        case 4: p1_near_go<4>(transpose, fp32, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        case 8: p1_near_go<8>(transpose, fp32, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
+        default: p1_near_go<16>(transpose, fp32, g, t, c, nrows, rows, ptr, col, off, xin, yout, s); break;
     }
 }
 
