@@ -298,7 +298,9 @@ int h2bem_stats_get(const h2bem_op* op, h2bem_stats* stats);
  *   cudaHostRegister) is read and written in place by the kernels, in the
  *   caller's order; other host memory is copied through device scratch.
  * Scratch device memory is allocated on the first call and grown when nrhs
- * grows; concurrent applies of one operator on different streams race on it.
+ * grows; concurrent applies of one operator on different streams race on it
+ * and on the operator's per-cluster arrival counts of the upward pass, so
+ * order the applies of one operator (one stream, or events between them).
  * Errors: ARG (null, nrhs, ld), CUDA, OOM. */
 int h2bem_apply(h2bem_op* op, const double* x, int64_t ldx, int nrhs, double* y, int64_t ldy, void* stream);
 /* y = A^T x, same conventions (transposed blocks, V and W exchanged). */
