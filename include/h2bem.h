@@ -103,9 +103,12 @@ typedef struct {
                         /*    where i = 0, 1, 2 selects 2, 4, 8 slices and j = 0, 1, 2 a          */
                         /*    nearfield register budget for 4, 3, 2 CTAs per SM (FP32 single     */
                         /*    layer)                                                               */
-    int singular_fp64;  /* 1: Sauter-Schwab quadrature points of edge- and vertex-adjacent pairs   */
-                        /*    in FP64 in every tier; 0 (default): FP32 points in the MIXED tiers  */
-                        /*    (Gram set-up, partial sums and accumulation stay FP64)              */
+    int singular_fp64;  /* 1: Sauter-Schwab quadrature points of pairs sharing a vertex at FP64-    */
+                        /*    class accuracy in every tier (double-float arithmetic on the FP32   */
+                        /*    pipe, relative error about 1e-14 per point; the area scale and the  */
+                        /*    accumulation into y in FP64), as the FP64 tier always does; 0       */
+                        /*    (default): FP32 points and sums in the MIXED tiers, FP64 area scale */
+                        /*    and accumulation                                                      */
     int recompute_basis; /* 1: no stored leaf bases; every apply re-evaluates the cluster-basis   */
                         /*    values by quadrature (saves n k values of device memory); 0         */
                         /*    (default): V (and W) evaluated once at set-up and stored             */
