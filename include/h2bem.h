@@ -61,11 +61,14 @@ extern "C" {
 #define H2BEM_SLP 0 /* single layer G, eq. (slp) */
 #define H2BEM_DLP 1 /* double layer K, eq. (dlp) */
 
-#define H2BEM_FP64 0       /* every step in FP64                                   */
-#define H2BEM_MIXED_FP32 1 /* FP32 farfield, regular and Sauter-Schwab pairs (FP64  */
-                           /* points with opts.singular_fp64); the double layer's  */
-                           /* differentiated-basis side and the accumulation into  */
-                           /* y in FP64                                            */
+#define H2BEM_FP64 0       /* every step at FP64 accuracy: FP64, or double-float    */
+                           /* arithmetic on the FP32 pipe (relative error about    */
+                           /* 1e-14) for the nearfield, the coupling and the       */
+                           /* Sauter-Schwab points                                  */
+#define H2BEM_MIXED_FP32 1 /* FP32 farfield, regular and Sauter-Schwab pairs (FP64- */
+                           /* class points with opts.singular_fp64); the double    */
+                           /* layer's differentiated-basis side and the            */
+                           /* accumulation into y in FP64                          */
 #define H2BEM_MIXED_TF32 2 /* as MIXED_FP32, coupling contraction on tensor cores  */
                            /* in TF32 with FP32 accumulation                        */
 #define H2BEM_MIXED_BF16 3 /* as MIXED_TF32 with BF16 operands                      */
