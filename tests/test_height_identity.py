@@ -77,7 +77,7 @@ def test_height_identity_fp32_keeps_small_heights(name):
     mesh = {"sphere": lambda: I.sphere(96), "ellipsoid": lambda: I.ellipsoid(64),
             "jitter": lambda: I.jitter(I.sphere(64), 0.01, 3)}[name]()
     V = mesh.vertices
-    # Radon's 7-point rule coordinates: centre and two orbits (the exact values are irrelevant here)
+    # seven points of the triangle, centre and off-centre (the identity holds for any point of it)
     uv = [(1 / 3, 1 / 3), (0.1, 0.45), (0.45, 0.1), (0.45, 0.45), (0.8, 0.1), (0.1, 0.8), (0.1, 0.1)]
     worst_id, worst_direct = 0.0, 0.0
     for i, j in _neighbour_pairs(mesh, 300, 7):
